@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the batched Bezier edge build + graph search on GB300.
+
+Metric: edge-feasibility checks per second (one check = one candidate pair
+(i, j) sharing a free polytope x one duration T) of plan_build_edges, with the
+shortest-path query time reported beside it (search_ms_per_query).
+
+Workload (one query per GPU): 3-D triple integrator (|v|<=3, |a|<=6,
+|jerk|<=30), 64 free polytopes of 6-12 rows in [0,20]^3, 8192 states, degree-7
+Bezier, 16 durations log-uniform in [0.1, 3], FP32; seeded synthetic inputs.
+A step = plan_build_edges + plan_search on HBM-resident inputs; each step is
+timed with CUDA events on the planner's stream after an L2 flush (a 256 MB
+write) outside the events.  N > 1 (torchrun): every rank runs its own query
+(seed + rank; weak scaling, no data-path collective), times are max-reduced.
+
+--impl reference times the FP64 CPU oracle (the plain definition) on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Bezier edge-feasibility checks/sec (+ search ms/query), 1 query per GPU"
+UNIT = "checks/s"
+WORKLOAD = "triple_integrator_3d N=8192 K=64 rows=6-12 nT=16 p=7 fp32"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-rows", type=int, default=0, help="rows of the oracle sample (0: auto)")
+    return ap.parse_args()
+
+
+def workload(seed):
+    from paper_2411_13507_gb300 import synth
+    return synth.triple_integrator_3d(seed=seed)
+
+
+def config(prob, extra=None):
+    c = {"workload": WORKLOAD, "N": prob.N, "K": prob.K, "nT": prob.nT, "degree": prob.model.degree,
+         "m": prob.model.m, "gamma": prob.model.gamma, "bounds": list(prob.model.bounds),
+         "l2": "flushed before every timed step (256 MB write)", "parallelism": "replicas (one query per GPU)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def pair_kernel_counters():
+    """DRAM traffic of the pair kernel from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    src = os.path.join(ROOT, "paper_2411_13507_gb300", "csrc", "plan_build.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "pair_kernel_counters.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("source_sha") == h:
+            return d, h
+    except Exception:
+        pass
+    return None, h
+
+
+def cpu_baseline(prob, budget_s=12.0, rows=0):
+    """The FP64 oracle as it stands, on a bounded sample of rows of the same query."""
+    import oracle
+    op = oracle.OracleProblem(prob)
+    op.membership()
+    cnt = op.candidate_counts()
+    nrows = rows
+    if nrows <= 0:
+        # calibrate on a few rows, then size the sample for ~budget_s of CPU time
+        probe = np.arange(0, prob.N, max(1, prob.N // 16), dtype=np.int32)[:16]
+        t0 = time.perf_counter()
+        op.edges(probe, with_detail=False)
+        dt = max(time.perf_counter() - t0, 1e-3)
+        per_row = dt / len(probe)
+        nrows = int(min(prob.N, max(16, budget_s / per_row)))
+    sel = np.linspace(0, prob.N - 1, nrows).astype(np.int32)
+    t0 = time.perf_counter()
+    e = op.edges(sel, with_detail=False)
+    dt = time.perf_counter() - t0
+    checks = int(e["i"].shape[0]) * prob.nT
+    return {"value": checks / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{nrows} of {prob.N} rows ({checks} checks, {dt:.2f} s, FP64 C oracle, OpenMP)",
+            "seconds": dt, "checks": checks, "full_checks": int(cnt.sum()) * prob.nT}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    prob = workload(args.seed)
+    import oracle
+    op = oracle.OracleProblem(prob)
+    op.membership()
+    # each step: a bounded row sample (~2 s) of the same workload
+    rng_rows = [np.arange(s % 37, prob.N, 37 * 4, dtype=np.int32) for s in range(args.warmup + args.steps)]
+    for s in range(args.warmup):
+        op.edges(rng_rows[s], with_detail=False)
+    tot_checks, tot_t = 0, 0.0
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        e = op.edges(rng_rows[args.warmup + s], with_detail=False)
+        tot_t += time.perf_counter() - t0
+        tot_checks += int(e["i"].shape[0]) * prob.nT
+    v = tot_checks / tot_t
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config(prob, {"sample": f"{len(rng_rows[0])} rows per step"}),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"~{len(rng_rows[0])} rows of {prob.N} per step, {args.steps} steps"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_2411_13507_gb300 import plan as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    # CPU baseline first (before heavy GPU work; threads, no fork)
+    prob = workload(args.seed + rank)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(prob, rows=args.cpu_sample_rows)
+
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        pl = P.Planner.for_problem(prob, arith="f32", input="f32", stream=stream)
+        dp = P.to_device(prob, input="f32")
+        graph = pl.build_edges(dp)           # sizes scratch and the output CSR
+        sres = pl.search(dp, graph)
+        info = pl.info()
+        cap = graph.cap
+        # algorithmic work of this query (untimed counting launch)
+        pl.set_accounting(True)
+        pl.build_edges(dp, graph=graph)
+        work = pl.info()
+        pl.set_accounting(False)
+        sbuf = pl.alloc_search(dp.N)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+        def step(evs):
+            evs[0].record(stream)
+            pl.build_edges_async(dp, graph)
+            evs[1].record(stream)
+            pl.search_async(dp, graph, dp.start_pos, dp.goal_pos, sbuf)
+            evs[2].record(stream)
+
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            step([torch.cuda.Event(enable_timing=True) for _ in range(3)])
+            st = pl.wait()
+            assert st == P.PLAN_OK, f"warm-up status {st}"
+        pl.set_timing(True)
+        pl.timing(reset=True)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            for s in range(args.steps):
+                flush.fill_(float(s))
+                step(evs[s])
+                st = pl.wait()
+                assert st == P.PLAN_OK, f"step {s}: status {st}"
+            torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        tm = pl.timing(reset=True)
+        pl.set_timing(False)
+        build_ms = [a.elapsed_time(b) for a, b, _ in evs]
+        search_ms = [b.elapsed_time(c) for _, b, c in evs]
+        step_ms = [a.elapsed_time(c) for a, _, c in evs]
+
+        # end to end: host (pinned) inputs -> C ABI -> host result, every step
+        h_states = torch.from_numpy(np.ascontiguousarray(prob.states, dtype=np.float32)).pin_memory()
+        h_off = torch.from_numpy(np.asarray(prob.poly_off, dtype=np.int32)).pin_memory()
+        h_A = torch.from_numpy(np.ascontiguousarray(prob.A, dtype=np.float32)).pin_memory()
+        h_b = torch.from_numpy(np.ascontiguousarray(prob.b, dtype=np.float32)).pin_memory()
+        h_path = torch.empty(dp.N, dtype=torch.int32).pin_memory()
+        h_cost = torch.empty(2, dtype=torch.float64).pin_memory()
+        h_E = torch.empty(1, dtype=torch.int64).pin_memory()
+        bi = sum(t.numel() * t.element_size() for t in (h_states, h_off, h_A, h_b))
+        e2e_ms = []
+        for s in range(args.warmup + args.steps):
+            flush.fill_(2.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dp.states.copy_(h_states, non_blocking=True)
+            dp.poly_off.copy_(h_off, non_blocking=True)
+            dp.A.copy_(h_A, non_blocking=True)
+            dp.b.copy_(h_b, non_blocking=True)
+            pl.build_edges_async(dp, graph)
+            pl.search_async(dp, graph, dp.start_pos, dp.goal_pos, sbuf)
+            h_path.copy_(sbuf["path"], non_blocking=True)
+            h_cost[:1].copy_(sbuf["cost"], non_blocking=True)
+            h_E.copy_(graph.count, non_blocking=True)
+            e1.record(stream)
+            st = pl.wait()
+            assert st == P.PLAN_OK
+            if s >= args.warmup:
+                e2e_ms.append(e0.elapsed_time(e1))
+        L = int(sbuf["path_len"].item())
+        bo = h_path.element_size() * dp.N + 8 + 8
+
+    checks = int(info["checks"])
+    t_build = sum(build_ms) / 1e3
+    t_step = sum(step_ms) / 1e3
+    t_search = sum(search_ms) / 1e3
+    t_e2e = sum(e2e_ms) / 1e3
+    if dist:
+        vals = torch.tensor([t_build, t_step, t_search, t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+        t_build, t_step, t_search, t_e2e = vals.tolist()
+        tot = torch.tensor([checks], dtype=torch.float64, device=dev)
+        dist.all_reduce(tot)
+        checks_all = float(tot.item())
+    else:
+        checks_all = float(checks)
+    value = checks_all * args.steps / t_build
+    e2e_value = checks_all * args.steps / t_e2e
+
+    # roofline of the dominant kernel (the pair kernel): ALU-bound
+    peaks, peak_src = measured_peaks()
+    g, p, m = prob.model.gamma, prob.model.degree, prob.model.m
+    n = m * g
+    ops_per_launch = (2 * work["work_reach_rows"] + 2 * work["work_free_rows"]
+                      + work["work_costs"] * p * (2 * n + 2))
+    pair_ms = tm["pair_ms"] / max(1, tm["pair_launches"])
+    achieved = ops_per_launch / (pair_ms / 1e3) / 1e12
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * sm_max * 1e6 / 1e12
+    counters, src_sha = pair_kernel_counters()
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_step / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config(prob, {"checks_per_query": checks, "candidates": int(info["candidates"]),
+                                "edges": int(info["edges"]), "rechecks": int(info["rechecks"])}),
+        "build_ms_per_query": 1e3 * t_build / args.steps,
+        "search_ms_per_query": 1e3 * t_search / args.steps,
+        "path_len": L,
+        "gpu_launches": int(tm["launches"]),
+        "clocks": clocks,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TOP/s",
+                     "frac": achieved / alu_peak,
+                     "traffic": counters.get("dram_bytes_per_launch") if counters else None,
+                     "kernel": "k_pairs_fast<3,3,7>", "kernel_ms": pair_ms,
+                     "ops_per_launch": ops_per_launch,
+                     "peak_note": f"FP32 lanes 152 SMs x 128 x {sm_max:.0f} MHz (unit counts and max clock; {peak_src} clock)",
+                     "work": {k: work[k] for k in ("work_reach_rows", "work_free_rows", "work_costs")}},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+                "ms_per_step": 1e3 * t_e2e / args.steps},
+        "cpu_baseline": ({k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")} if cpu else None),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    pl.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

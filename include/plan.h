@@ -1,0 +1,254 @@
+/*
+ * plan.h -- C ABI of the GB300 (sm_103a) reachable-Bezier-polytope planner.
+ *
+ * The library builds the kinodynamic Bezier graph of arXiv 2411.13507 and
+ * searches it on one GPU.  Every entry point is asynchronous on the stream
+ * given to plan_create(); device-detected conditions (capacity, timeout, no
+ * path) are written to a device status word that plan_wait() reads.  No entry
+ * point throws across the ABI; each returns a plan_status code.
+ *
+ * Memory: every array argument documented "device" is caller-owned device
+ * memory (e.g. a torch tensor); "host" arrays are read before the call
+ * returns.  The library never frees caller memory.  It allocates only its own
+ * context scratch (at plan_create and, when plan_wait reports that a call
+ * needed more, at the next call).
+ *
+ * Notation (paper, Sec. II): m outputs, relative degree g (gamma), state
+ * dimension n = m*g stacked x = [b; b'; ...; b^(g-1)] (Eq. BezDef), Bezier
+ * degree p, durations T_t.  For one axis a, xi = [x_i^(0..g-1)_a ; x_j^(0..g-1)_a].
+ */
+#ifndef PLAN_H
+#define PLAN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct plan_ctx plan_ctx;
+
+typedef enum {
+    PLAN_OK = 0,
+    PLAN_ERR_INVALID_ARG = 1,  /* bad pointer, size or model parameter */
+    PLAN_ERR_UNSUPPORTED = 2,  /* model outside the compiled set, or a polytope with > 16 rows */
+    PLAN_ERR_CAPACITY = 3,     /* output buffer (or internal scratch) too small; see plan_info */
+    PLAN_ERR_CUDA = 4,         /* a CUDA runtime call failed; see plan_last_error */
+    PLAN_ERR_TIMEOUT = 5,      /* a bounded device loop ran out of iterations */
+    PLAN_ERR_NO_PATH = 6,      /* goal vertex unreachable from the start vertex */
+    PLAN_ERR_NO_MEMORY = 7     /* context scratch could not be allocated */
+} plan_status;
+
+/* Arithmetic of the edge-build margins. */
+typedef enum {
+    PLAN_F64 = 0,   /* canonical FP64 evaluation (no re-check needed) */
+    PLAN_F32 = 1,   /* FP32 margins; any margin within its error band re-checked in FP64 */
+    PLAN_TF32 = 2,  /* control-point products on tensor cores, TF32 inputs, FP32 accumulate, FP64 re-check */
+    PLAN_BF16 = 3   /* as TF32 with BF16 inputs */
+} plan_arith;
+
+/* Storage type of states, A and b. */
+typedef enum { PLAN_IN_F64 = 0, PLAN_IN_F32 = 1 } plan_input;
+
+typedef enum { PLAN_COST_STATE = 0, PLAN_COST_POS = 1 } plan_cost_mode;
+
+/*
+ * Chain-of-integrators model (Eq. rom) and edge-test options.
+ *   m, gamma, degree : compiled combinations (m,gamma,p) in
+ *                      {(2,2,3),(2,2,5),(3,3,5),(3,3,7)}; others -> UNSUPPORTED.
+ *   bound[k-1]       : per-axis bound c_k on the k-th derivative, k = 1..gamma
+ *                      (k = gamma bounds the input u_d).  Theorem 1's F x <= G is
+ *                      taken as |Q^(k)_j| <= c_k on every hodograph control point.
+ *   tighten          : eps subtracted from every c_k and every b_r (Def. 1's
+ *                      tracking-error margin; 0 by default).
+ *   cost_mode        : PLAN_COST_STATE: polygon length of the n-row state-space
+ *                      control points (Eq. BezDef, Property 2); PLAN_COST_POS:
+ *                      position rows only.
+ */
+typedef struct {
+    int m;
+    int gamma;
+    int degree;
+    int arith;      /* plan_arith */
+    int input;      /* plan_input */
+    int cost_mode;  /* plan_cost_mode */
+    double bound[4];
+    double tighten;
+} plan_model;
+
+/*
+ * Feasible-edge graph in CSR form, sorted by (i asc, j asc).  All pointers
+ * are caller-owned device memory.
+ *   row_off [N+1] int32   (always written)
+ *   col     [cap] int32   end vertex j
+ *   w       [cap]         edge cost: double when arith == PLAN_F64, else float;
+ *                         min over feasible durations of the control-polygon
+ *                         length (Sec. III-C), ties to the lower duration index
+ *   tidx    [cap] uint8   index of that duration
+ *   mask    [cap] uint32  bit t set iff (i -> j, T_t) passes the reach test and
+ *                         fits a shared free polytope
+ *   count   [1]   int64   number of edges E (written even when E > cap; the
+ *                         CSR arrays are then left unwritten and the call
+ *                         reports PLAN_ERR_CAPACITY)
+ */
+typedef struct {
+    int32_t* row_off;
+    int32_t* col;
+    void* w;
+    uint8_t* tidx;
+    uint32_t* mask;
+    int64_t cap;
+    int64_t* count;
+} plan_edges;
+
+/* Counters of the last call, read by plan_wait (host struct). */
+typedef struct {
+    int32_t status;           /* plan_status of the device work */
+    int32_t detail;           /* which check raised it (library-internal code) */
+    int64_t memberships;      /* sum over polytopes of member counts */
+    int64_t slots;            /* sum over polytopes of (member count)^2 */
+    int64_t candidates;       /* distinct ordered pairs (i != j) sharing a polytope */
+    int64_t checks;           /* candidates * nT */
+    int64_t reach_pass;       /* (candidate, T) passing the reach test (owner block) */
+    int64_t feasible;         /* feasible (candidate, T) bits in the output */
+    int64_t rechecks;         /* (pair, T, polytope) evaluations re-done in FP64 */
+    int64_t edges;            /* E */
+    int64_t search_iters;     /* frontier sweeps of the last search */
+    int32_t start, goal;      /* vertices chosen by the last search */
+    int64_t need_slots, need_rechecks;  /* scratch sizes the last call needed */
+    /* with plan_set_accounting(ctx, 1): algorithmic work of the last build under
+     * short-circuit evaluation (reach rows up to the first violated one, free
+     * rows of reach-passing checks, cost evaluations of feasible checks) */
+    int64_t work_reach_rows, work_free_rows, work_costs;
+} plan_info;
+
+/* Create a context bound to the current CUDA device and the given stream
+ * (cudaStream_t; NULL = legacy default stream).  Validates the model. */
+int plan_create(plan_ctx** out, const plan_model* model, void* cuda_stream);
+
+/* Release the context and its scratch (synchronises its stream first). */
+void plan_destroy(plan_ctx* ctx);
+
+/*
+ * buildGraph + keep-in cut (Alg. 1 lines 2-3, Sec. III-A/B): for every ordered
+ * pair of states sharing at least one free polytope and every duration T_t,
+ * form the control points meeting the boundary conditions (Lemma 1, elevated
+ * to degree p), test the hodograph control points against the bounds
+ * (Theorem 1) and the control points against the shared polytope (Property 1),
+ * reduce to the feasibility mask and the edge cost, and compact the graph.
+ *
+ *   N         number of states (0 <= N <= 1<<20)
+ *   states    device [N][n], input type, x = [pos; vel; acc; ...] per state
+ *   nT, T     host [nT] durations, 1 <= nT <= 32, all > 0 and finite
+ *   K         number of free polytopes (0 <= K <= 1024)
+ *   poly_off  device int32 [K+1], rows of polytope k are poly_off[k]..poly_off[k+1]-1,
+ *             poly_off[0] = 0
+ *   max_rows  host bound on the rows of any polytope, 1..16 (sizes shared
+ *             memory; a polytope with more rows -> device status UNSUPPORTED)
+ *   A, b      device [R][m] and [R], input type; polytope k = {x : A_r x <= b_r}
+ *   out       caller-owned CSR (see plan_edges)
+ * Errors: INVALID_ARG / UNSUPPORTED on the host; CAPACITY, UNSUPPORTED (row
+ * count) on the device via plan_wait.  When internal scratch was too small,
+ * plan_wait returns PLAN_ERR_CAPACITY with need_* set and grows the scratch, so
+ * the caller simply repeats the call.
+ */
+int plan_build_edges(plan_ctx* ctx, int N, const void* states, int nT, const double* T, int K,
+                     const int32_t* poly_off, int max_rows, const void* A, const void* b,
+                     const plan_edges* out);
+
+/*
+ * findPath (Alg. 1 line 4, Sec. III-C, Problem 2): the start and goal vertices
+ * are the states nearest (Euclidean, positions only; ties to the lowest id) to
+ * start_pos and goal_pos; then shortest paths with Dijkstra semantics (FP64
+ * accumulation dist[u] + w; predecessor = the earliest-settled vertex that
+ * attains dist[v], i.e. the minimum (dist[u], u)).
+ *   states      device [N][n] (same array as the build)
+ *   edges       device CSR from plan_build_edges (count must be <= cap)
+ *   start_pos,
+ *   goal_pos    host [m] doubles
+ *   path        device int32 [path_cap]: vertex ids start..goal
+ *   path_len    device int32 [1]: number of vertices (0 if no path)
+ *   cost        device double [1]: path cost (+inf if no path)
+ * Device status NO_PATH when the goal is unreachable, TIMEOUT if the frontier
+ * loop exceeds N+1 sweeps, CAPACITY if the path is longer than path_cap.
+ */
+int plan_search(plan_ctx* ctx, int N, const void* states, const plan_edges* edges,
+                const double* start_pos, const double* goal_pos, int32_t* path, int path_cap,
+                int32_t* path_len, double* cost);
+
+/* Bounds of the search kernel's device loops: at most max_sweeps frontier
+ * sweeps (default N+1, the Bellman-Ford bound) and spin_limit polls of the
+ * grid barrier (default 2^24).  0 keeps the default.  When a bound runs out
+ * the kernel stops and plan_wait returns PLAN_ERR_TIMEOUT; the context stays
+ * usable. */
+int plan_set_search_limits(plan_ctx* ctx, int max_sweeps, int64_t spin_limit);
+
+/* Weights of the refinement objective (defaults 1, 1, 0.1). */
+typedef struct {
+    double w_snap;  /* weight of the snap energy */
+    double mu;      /* weight of the barrier terms */
+    double delta;   /* relaxation point of the log-barrier (> 0) */
+} plan_refine_weights;
+
+/*
+ * Differentiable refinement of Bezier segments (one free polytope each): for
+ * segment s with control points P_s (degree p = model degree, m axes), duration
+ * T_s and polytope {x : A x <= b},
+ *   loss_s = w_snap J_snap + mu sum phi_delta(margin)
+ * where the margins are c_k -/+ Q^(k)_j on every hodograph control point
+ * (Theorem 1 per axis, k = 1..gamma) and b_r - A_r P_l for the interior control
+ * points (Property 1); phi_delta is the log-barrier -log m relaxed to its C^2
+ * quadratic extension below delta; J_snap = integral over [0, T] of
+ * ||b''''(t)||^2 (exact Gram form of the degree p-4 fourth-derivative curve).
+ * Supported models: (m, gamma, p) in {(3,3,7), (2,2,5)}.
+ *   S         number of segments
+ *   P         device float [S][p+1][m]
+ *   T         device float [S], > 0
+ *   A, b      device float [S][rmax][m], [S][rmax]; rows >= nrows[s] ignored
+ *   nrows     device int32 [S], 0..rmax
+ *   weights   host (NULL: defaults)
+ *   grad_loss device float [S] upstream gradient, or NULL for the forward pass only
+ *   loss      device float [S] (may be NULL when grad_loss != NULL)
+ *   dP, dT    device float [S][p+1][m], [S]: d(sum_s grad_loss_s loss_s) with
+ *             respect to every control point and T (ignored when grad_loss is NULL)
+ */
+int plan_refine(plan_ctx* ctx, int S, const float* P, const float* T, const float* A, const float* b,
+                const int32_t* nrows, int rmax, const plan_refine_weights* weights, const float* grad_loss,
+                float* loss, float* dP, float* dT);
+
+/* Synchronise the context stream, return the device status of the work
+ * issued since the previous plan_wait, and fill *info (may be NULL). */
+int plan_wait(plan_ctx* ctx, plan_info* info);
+
+/*
+ * Host-only: the library's FP64 coefficient tables for nT durations (no GPU
+ * needed).  Each entry is the correctly rounded double of an exact rational
+ * function of T.
+ *   D [nT][p+1][2g]  control points (Lemma 1, degree-elevated to p)
+ *   H [nT][Rax][2g]  reach rows, Rax = sum_{k=1..g} (p-k+1), k-major then j
+ *   C [nT][g][p][2g] consecutive differences of the degree-p control points of
+ *                    b^(d), d = 0..g-1 (rows of Eq. BezDef's state-space matrix)
+ */
+int plan_model_tables(const plan_model* model, int nT, const double* T, double* D, double* H, double* C);
+
+/* Work accounting: when enabled, every plan_build_edges also launches an
+ * (untimed, extra) counting kernel whose totals plan_wait reports in
+ * plan_info.work_*.  Off by default. */
+int plan_set_accounting(plan_ctx* ctx, int enable);
+
+/* Per-kernel timing with CUDA events on the context stream (off by default).
+ * plan_timing returns the accumulated milliseconds and launch counts since
+ * the last reset (synchronises the stream). */
+int plan_set_timing(plan_ctx* ctx, int enable);
+int plan_timing(plan_ctx* ctx, double* pair_ms, int64_t* pair_launches, double* search_ms,
+                int64_t* search_launches, int64_t* total_launches, int reset);
+
+const char* plan_status_string(int status);
+const char* plan_last_error(plan_ctx* ctx);
+const char* plan_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLAN_H */

@@ -1,0 +1,1227 @@
+// Edge-build kernels for sm_103a: membership, per-polytope member lists, the
+// pair kernels (FP32 fast path with error bands, FP64 canonical path), the
+// FP64 re-check of ambiguous margins and the CSR compaction.
+//
+// Method (arXiv 2411.13507):
+//  * Sec. III-A buildGraph: e_ij exists iff F [v_i; v_j] <= G (Theorem 1),
+//    taken per axis as |Q^(k)_j| <= c_k on the hodograph control points of
+//    every derivative order k = 1..gamma of the Lemma-1 curve.
+//  * Property 1 + keep-in polytope: the curve stays in a shared free polytope
+//    when every control point satisfies A P_l <= b (interior l; the end points
+//    are the states, which are members).
+//  * Sec. III-C: edge cost = control-polygon length of the state-space
+//    control points (Property 2); one edge weight = min over feasible T.
+//
+// All four tests are linear in xi = [x_i; x_j], so every row value splits
+// into a start half (depends on x_i only) and an end half (x_j only).  The
+// halves of a tile of states are computed once per duration into shared
+// memory and each pair costs one add per row ("outer sum"), reduced with a
+// max in registers.  Canonical FP64 order (the definition of a bit-exact
+// result) is: each half summed left to right without FMA, then the two
+// halves added; see the FP64 kernel and the re-check kernel.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "plan_internal.h"
+
+namespace plan {
+
+#define DEVI __device__ __forceinline__
+
+// Error-band constants (multiples of the FP32 unit roundoff u = 2^-24).
+// Reach row: x~ (1) + coefficient (1) + product (1) + g-1 sums + final add
+// <= 7 roundings for g <= 4; factor 2 margin -> 16u.  Free row: adds the
+// control-point products, the polytope products (m-1 sums) and the bound:
+// <= 12 roundings -> 24u.  Membership: m products and sums + bound -> 16u.
+// The FP64 canonical value is within 4 * 2^-53 of the exact value, far inside
+// the margin.  A margin whose computed value is within band of zero is
+// re-evaluated in canonical FP64.
+constexpr float KU = 5.9604644775390625e-08f;  // 2^-24
+constexpr float KR = 16.f * KU;
+constexpr float KF = 24.f * KU;
+constexpr float KMEM = 16.f * KU;
+constexpr unsigned long long KEY_NONE = ~0ull;
+constexpr unsigned long long DINF_BITS = 0x7FF0000000000000ull;
+
+DEVI void set_status(DevInfo* info, int code, int detail) {
+    if (atomicCAS(&info->status, 0, code) == 0) atomicExch(&info->detail, detail);
+}
+DEVI bool has_failed(const DevInfo* info) { return *((volatile const int*)&info->status) != 0; }
+
+DEVI double ldv(const void* p, long long i, int f32) {
+    return f32 ? (double)((const float*)p)[i] : ((const double*)p)[i];
+}
+DEVI float ldf(const void* p, long long i, int f32) {
+    return f32 ? ((const float*)p)[i] : (float)((const double*)p)[i];
+}
+
+DEVI unsigned long long key_f32(float cost, int t) {
+    return ((unsigned long long)__float_as_uint(cost) << 32) | (unsigned)t;
+}
+DEVI unsigned long long key_f64(double cost, int t) {
+    return ((unsigned long long)__double_as_longlong(cost) & ~31ull) | (unsigned)t;
+}
+
+template <int G, int PD>
+struct Shape {
+    static constexpr int RAX = (G >= 1 ? PD : 0) + (G >= 2 ? PD - 1 : 0) + (G >= 3 ? PD - 2 : 0) + (G >= 4 ? PD - 3 : 0);
+    static constexpr int NI = PD - 1;
+    static constexpr int TG = 2 * G;
+};
+
+// ---------------------------------------------------------------------------
+// Rows of every polytope: FP32 copies, b - eps, row-count checks.
+// ---------------------------------------------------------------------------
+__global__ void k_prep(BuildParams P) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)P.K * P.max_rows) return;
+    int k = (int)(t / P.max_rows), rr = (int)(t % P.max_rows);
+    int r0 = P.poly_off[k], r1 = P.poly_off[k + 1];
+    if (rr == 0) {
+        int nr = r1 - r0;
+        if (nr < 0 || nr > P.max_rows || (k == 0 && r0 != 0)) set_status(P.info, PLAN_ERR_UNSUPPORTED, DET_ROWS);
+        atomicMax(&P.info->max_rows_seen, nr);
+    }
+    int r = r0 + rr;
+    if (r >= r1 || r >= P.R || r < 0) return;
+    double bl = __dsub_rn(ldv(P.b, r, P.in_f32), P.eps);
+    P.blim64[r] = bl;
+    P.blim32[r] = (float)bl;
+    for (int a = 0; a < P.m; ++a) P.A32[(long long)r * P.m + a] = ldf(P.A, (long long)r * P.m + a, P.in_f32);
+}
+
+// ---------------------------------------------------------------------------
+// A1 membership: bit k of state i set iff A_k x_i^(0) <= b_k - eps on every
+// row (canonical FP64 decision; FP32 first, FP64 only inside the band).
+// ---------------------------------------------------------------------------
+__global__ void k_member(BuildParams P) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)P.N * P.W || has_failed(P.info)) return;
+    const int i = (int)(t / P.W), w = (int)(t % P.W);
+    const int m = P.m, n = P.m * P.g;
+    double x64[4];
+    float x32[4];
+    for (int a = 0; a < m; ++a) {
+        x64[a] = ldv(P.states, (long long)i * n + a, P.in_f32);
+        x32[a] = (float)x64[a];
+    }
+    uint32_t word = 0;
+    const int kend = min(32, P.K - w * 32);
+    for (int kk = 0; kk < kend; ++kk) {
+        const int k = w * 32 + kk;
+        const int r0 = P.poly_off[k], r1 = P.poly_off[k + 1];
+        if (r1 - r0 > P.max_rows || r1 > P.R) continue;
+        bool in = true;
+        for (int r = r0; r < r1 && in; ++r) {
+            float s = 0.f, mag = 0.f;
+            for (int a = 0; a < m; ++a) {
+                float av = P.A32[(long long)r * m + a];
+                s = fmaf(av, x32[a], s);
+                mag = fmaf(fabsf(av), fabsf(x32[a]), mag);
+            }
+            const float lim = P.blim32[r];
+            const float d = s - lim;
+            const float band = KMEM * (mag + fabsf(lim));
+            if (!(d < -band)) {
+                if (d > band) {
+                    in = false;
+                } else {  // within the band (or NaN): canonical FP64 row
+                    double sd = 0.0;
+                    for (int a = 0; a < m; ++a)
+                        sd = __dadd_rn(sd, __dmul_rn(ldv(P.A, (long long)r * m + a, P.in_f32), x64[a]));
+                    if (!(sd <= P.blim64[r])) in = false;
+                }
+            }
+        }
+        if (in) word |= 1u << kk;
+    }
+    P.memMask[(long long)i * P.W + w] = word;
+}
+
+// ---------------------------------------------------------------------------
+// Ordered member list of each polytope (ascending state id), local indices,
+// block centre (first member's position) and centred FP32 bounds.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_lists(BuildParams P) {
+    const int k = blockIdx.x;
+    __shared__ int warpTot[32];
+    __shared__ int s_base;
+    __shared__ float s_c[4];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) s_base = 0;
+    __syncthreads();
+    const int w = k >> 5;
+    const uint32_t bit = 1u << (k & 31);
+    for (int i0 = 0; i0 < P.N; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const bool mem = i < P.N && (P.memMask[(long long)i * P.W + w] & bit);
+        const unsigned bal = __ballot_sync(0xffffffffu, mem);
+        const int pre = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) warpTot[wid] = __popc(bal);
+        __syncthreads();
+        if (wid == 0) {
+            int v = lane < nw ? warpTot[lane] : 0;
+            int inc = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane < nw) warpTot[lane] = inc - v;
+        }
+        __syncthreads();
+        if (mem) {
+            const int pos = s_base + warpTot[wid] + pre;
+            P.members[(long long)k * P.N + pos] = i;
+            P.localIdx[(long long)k * P.N + i] = pos;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_base += warpTot[wid] + pre + (mem ? 1 : 0);
+        __syncthreads();
+    }
+    const int nk = s_base;
+    if (threadIdx.x == 0) {
+        P.counts[k] = nk;
+        const int n = P.m * P.g;
+        for (int a = 0; a < 4; ++a) {
+            float c = 0.f;
+            if (nk > 0 && a < P.m) c = ldf(P.states, (long long)P.members[(long long)k * P.N] * n + a, P.in_f32);
+            s_c[a] = c;
+            P.centers[k * 4 + a] = c;
+        }
+    }
+    __syncthreads();
+    const int r0 = P.poly_off[k], r1 = P.poly_off[k + 1];
+    for (int r = r0 + threadIdx.x; r < r1 && r < P.R; r += blockDim.x) {
+        double s = 0.0;
+        for (int a = 0; a < P.m; ++a) s += ldv(P.A, (long long)r * P.m + a, P.in_f32) * (double)s_c[a];
+        P.bc32[r] = (float)(P.blim64[r] - s);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Work decomposition: per polytope, balanced square tiles of <= tile states;
+// prefix sums of slots (n_k^2) and tiles; capacity checks.
+// ---------------------------------------------------------------------------
+template <typename T>
+DEVI T block_exclusive_scan(T v, T* warpbuf, T* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warpbuf[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        T s = lane < nw ? warpbuf[lane] : (T)0;
+        T si = s;
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o) si += y;
+        }
+        if (lane < nw) warpbuf[lane] = si - s;
+        if (lane == 31) *total = si;
+    }
+    __syncthreads();
+    T r = warpbuf[wid] + inc - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(1024) k_setup(BuildParams P, int tile) {
+    __shared__ long long wb[32];
+    __shared__ long long tot;
+    const int k = threadIdx.x;
+    long long nk = (k < P.K) ? P.counts[k] : 0;
+    if (nk > NK_MAX) set_status(P.info, PLAN_ERR_UNSUPPORTED, DET_NK);
+    const int nt = nk > 0 ? (int)((nk + tile - 1) / tile) : 0;
+    const int ts = nt ? (int)((nk + nt - 1) / nt) : 0;
+    long long so = block_exclusive_scan<long long>(nk * nk, wb, &tot);
+    const long long slots = tot;
+    long long io = block_exclusive_scan<long long>((long long)nt * nt, wb, &tot);
+    const long long items = tot;
+    block_exclusive_scan<long long>(nk, wb, &tot);
+    const long long mem = tot;
+    if (k < P.K) {
+        P.resOff[k] = so;
+        P.itemOff[k] = (int)io;
+        P.ntile[k] = nt;
+        P.tsize[k] = ts;
+    }
+    if (k == 0) {
+        P.resOff[P.K] = slots;
+        P.itemOff[P.K] = (int)items;
+        P.info->slots = slots;
+        P.info->items = items;
+        P.info->memberships = mem;
+        if (slots > P.slotCap) {
+            P.info->need_slots = slots;
+            set_status(P.info, PLAN_ERR_CAPACITY, DET_SLOTS);
+        }
+    }
+}
+
+DEVI void item_decode(const BuildParams& P, int item, int& k, int& i0, int& j0, int& TI, int& TJ, int& nk) {
+    int lo = 0, hi = P.K;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (P.itemOff[mid] <= item) lo = mid;
+        else hi = mid;
+    }
+    k = lo;
+    const int loc = item - P.itemOff[k], nt = P.ntile[k], ts = P.tsize[k];
+    nk = P.counts[k];
+    const int ti = loc / nt, tj = loc % nt;
+    i0 = ti * ts;
+    j0 = tj * ts;
+    TI = min(ts, nk - i0);
+    TJ = min(ts, nk - j0);
+}
+
+DEVI void append_recheck(const BuildParams& P, int k, int li, int lj, int t) {
+    const unsigned long long idx = atomicAdd(&P.info->rechecks, 1ull);
+    if ((long long)idx < P.recheckCap) {
+        P.recheck[idx] = ((unsigned long long)k << 37) | ((unsigned long long)li << 21) |
+                         ((unsigned long long)lj << 5) | (unsigned long long)t;
+    } else {
+        atomicMax(&P.info->need_rechecks, idx + 1);
+        set_status(P.info, PLAN_ERR_CAPACITY, DET_RECHECK);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// A2/A3 FP32 pair kernel.  Persistent CTAs pull (polytope, i-tile, j-tile)
+// items; per duration the tile's halves go to shared memory and each thread
+// reduces a 4x4 micro-tile of pairs.  Reach rows are ordered so that the
+// rows most likely to fail (highest derivative, interior) come first, and a
+// thread stops the reach loop once all its pairs have definitely failed.
+// ---------------------------------------------------------------------------
+template <int M, int G, int PD>
+__global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
+    using S = Shape<G, PD>;
+    constexpr int N_ = M * G, RAX = S::RAX, RR = M * RAX, NI = S::NI, TG = S::TG;
+    constexpr int T = TILE;
+    extern __shared__ __align__(16) float sm[];
+    const int FRm = NI * P.max_rows;
+    const int DR = P.cost_mode == 1 ? 1 : G;
+    const int CRW = G * PD * M;
+    float* UL = sm;
+    float* UR = UL + RR * T;
+    float* FL = UR + RR * T;
+    float* FR = FL + FRm * T;
+    float* CL = FR + FRm * T;
+    float* CRr = CL + CRW * T;
+    float* magR = CRr + CRW * T;
+    float* magF = magR + 2 * T;
+    float* xs = magF + 2 * T;
+    float* xab = xs + 2 * T * N_;
+    float* tab = xab + 2 * T * G;
+    float* Ap = tab + P.L.f_stride;
+    float* bp = Ap + RMAX * M;
+    __shared__ int s_item;
+    __shared__ float s_rown1, s_bmax;
+
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int nitems = (int)P.info->items;
+    const TabLayout L = P.L;
+    unsigned long long rp_cnt = 0;
+
+    for (;;) {
+        if (tid == 0) {
+            const int it = (int)atomicAdd(&P.info->ticket, 1u);
+            s_item = has_failed(P.info) ? 0x7fffffff : it;  // one decision for the whole block
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item >= nitems) break;
+        int k, i0, j0, TI, TJ, nk;
+        item_decode(P, item, k, i0, j0, TI, TJ, nk);
+        const int ni4 = (TI + 3) & ~3, nj4 = (TJ + 3) & ~3;
+        const int r0 = P.poly_off[k], nr = P.poly_off[k + 1] - r0;
+        for (int u = tid; u < nr * M; u += nthr) Ap[u] = P.A32[(long long)r0 * M + u];
+        for (int u = tid; u < nr; u += nthr) bp[u] = P.bc32[r0 + u];
+        float cx[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) cx[a] = P.centers[k * 4 + a];
+        for (int u = tid; u < (ni4 + nj4) * N_; u += nthr) {
+            const int s = u / N_, e = u % N_;
+            const bool right = s >= ni4;
+            const int ls = right ? s - ni4 : s;
+            const int lidx = (right ? j0 : i0) + ls;
+            float v = 0.f;
+            if (ls < (right ? TJ : TI)) {
+                const long long id = P.members[(long long)k * P.N + lidx];
+                if (e < M) {
+                    if (P.in_f32) v = ((const float*)P.states)[id * N_ + e] - cx[e];
+                    else v = (float)(((const double*)P.states)[id * N_ + e] - (double)cx[e]);
+                } else {
+                    v = ldf(P.states, id * N_ + e, P.in_f32);
+                }
+            }
+            xs[(right ? T + ls : ls) * N_ + e] = v;
+        }
+        __syncthreads();
+        for (int s = tid; s < ni4 + nj4; s += nthr) {
+            const bool right = s >= ni4;
+            const int ls = right ? s - ni4 : s;
+            const float* x = xs + (right ? T + ls : ls) * N_;
+            float* xa = xab + (right ? T + ls : ls) * G;
+#pragma unroll
+            for (int c = 0; c < G; ++c) {
+                float mx = 0.f;
+#pragma unroll
+                for (int a = 0; a < M; ++a) mx = fmaxf(mx, fabsf(x[c * M + a]));
+                xa[c] = mx;
+            }
+        }
+        if (tid == 0) {
+            float rn = 0.f, bm = 0.f;
+            for (int r = 0; r < nr; ++r) {
+                float s1 = 0.f;
+                for (int a = 0; a < M; ++a) s1 += fabsf(Ap[r * M + a]);
+                rn = fmaxf(rn, s1);
+                bm = fmaxf(bm, fabsf(bp[r]));
+            }
+            s_rown1 = rn * 1.0001f;
+            s_bmax = bm;
+        }
+        __syncthreads();
+
+        const int ngi = ni4 >> 2, ngj = nj4 >> 2;
+        const bool act = tid < ngi * ngj;
+        const int gi = act ? tid / ngj : 0, gj = act ? tid % ngj : 0;
+        const bool diag_tile = (i0 == j0);
+        uint32_t vmask = 0, dmask = 0;  // valid pairs, diagonal pairs
+#pragma unroll
+        for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+            for (int qb = 0; qb < 4; ++qb) {
+                const int li = 4 * gi + qa, lj = 4 * gj + qb;
+                if (act && li < TI && lj < TJ) vmask |= 1u << (qa * 4 + qb);
+                if (diag_tile && li == lj) dmask |= 1u << (qa * 4 + qb);
+            }
+        uint32_t bits[16];
+        float bc[16];
+        int bt[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            bits[q] = 0;
+            bc[q] = __int_as_float(0x7f800000);
+            bt[q] = 0;
+        }
+
+        for (int t = 0; t < P.nT; ++t) {
+            for (int u = tid; u < L.f_stride; u += nthr) tab[u] = P.tab32[(long long)t * L.f_stride + u];
+            __syncthreads();
+            // reach and cost halves: one unit per (state, axis)
+            for (int u = tid; u < (ni4 + nj4) * M; u += nthr) {
+                const int s = u / M, a = u % M;
+                const bool right = s >= ni4;
+                const int ls = right ? s - ni4 : s;
+                const float* x = xs + (right ? T + ls : ls) * N_;
+                float xc[G];
+#pragma unroll
+                for (int c = 0; c < G; ++c) xc[c] = x[c * M + a];
+                const int co = right ? G : 0;
+                float* dU = right ? UR : UL;
+#pragma unroll 3
+                for (int r = 0; r < RAX; ++r) {
+                    const float* h = tab + L.f_H + r * TG + co;
+                    float v = h[0] * xc[0];
+#pragma unroll
+                    for (int c = 1; c < G; ++c) v = fmaf(h[c], xc[c], v);
+                    dU[(r * M + a) * T + ls] = v;
+                }
+                float* dC = right ? CRr : CL;
+                for (int d = 0; d < DR; ++d)
+                    for (int l = 0; l < PD; ++l) {
+                        const float* cc = tab + L.f_C + (d * PD + l) * TG + co;
+                        float v = cc[0] * xc[0];
+#pragma unroll
+                        for (int c = 1; c < G; ++c) v = fmaf(cc[c], xc[c], v);
+                        dC[((l * DR + d) * M + a) * T + ls] = v;
+                    }
+            }
+            // free-space halves: one unit per (state, interior control point)
+            for (int u = tid; u < (ni4 + nj4) * NI; u += nthr) {
+                const int s = u / NI, l = u % NI;
+                const bool right = s >= ni4;
+                const int ls = right ? s - ni4 : s;
+                const float* x = xs + (right ? T + ls : ls) * N_;
+                const float* dd = tab + L.f_D + l * TG + (right ? G : 0);
+                float pt[M];
+#pragma unroll
+                for (int a = 0; a < M; ++a) {
+                    float v = dd[0] * x[a];
+#pragma unroll
+                    for (int c = 1; c < G; ++c) v = fmaf(dd[c], x[c * M + a], v);
+                    pt[a] = v;
+                }
+                float* dF = right ? FR : FL;
+                for (int r = 0; r < nr; ++r) {
+                    float v = Ap[r * M] * pt[0];
+#pragma unroll
+                    for (int a = 1; a < M; ++a) v = fmaf(Ap[r * M + a], pt[a], v);
+                    if (!right) v -= bp[r];
+                    dF[(l * nr + r) * T + ls] = v;
+                }
+            }
+            // band magnitudes
+            for (int s = tid; s < ni4 + nj4; s += nthr) {
+                const bool right = s >= ni4;
+                const int ls = right ? s - ni4 : s;
+                const float* xa = xab + (right ? T + ls : ls) * G;
+                float mr = 0.f, md = 0.f;
+#pragma unroll
+                for (int c = 0; c < G; ++c) {
+                    mr = fmaf(tab[L.f_HC + (right ? G : 0) + c], xa[c], mr);
+                    md = fmaf(tab[L.f_DC + (right ? G : 0) + c], xa[c], md);
+                }
+                magR[(right ? T : 0) + ls] = mr;
+                magF[(right ? T : 0) + ls] = md * s_rown1 + (right ? 0.f : s_bmax);
+            }
+            __syncthreads();
+
+            if (act) {
+                float mRi[4], mRj[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    mRi[q] = magR[4 * gi + q];
+                    mRj[q] = magR[T + 4 * gj + q];
+                }
+                const float bmx = KR * (fmaxf(fmaxf(mRi[0], mRi[1]), fmaxf(mRi[2], mRi[3])) +
+                                        fmaxf(fmaxf(mRj[0], mRj[1]), fmaxf(mRj[2], mRj[3])));
+                float rm[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) rm[q] = ((vmask >> q) & 1u) && !((dmask >> q) & 1u) ? 0.f : __int_as_float(0x7f800000);
+                const float* ulp = UL + 4 * gi;
+                const float* urp = UR + 4 * gj;
+                bool dead = false;
+                for (int r = 0; r < RAX; ++r) {
+#pragma unroll
+                    for (int a = 0; a < M; ++a) {
+                        const float4 u = *reinterpret_cast<const float4*>(ulp + (r * M + a) * T);
+                        const float4 w = *reinterpret_cast<const float4*>(urp + (r * M + a) * T);
+                        const float uu[4] = {u.x, u.y, u.z, u.w};
+                        const float ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                        for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+                            for (int qb = 0; qb < 4; ++qb) rm[qa * 4 + qb] = fmaxf(rm[qa * 4 + qb], fabsf(uu[qa] + ww[qb]));
+                    }
+                    if ((r & 1) == 1) {
+                        float mn = rm[0];
+#pragma unroll
+                        for (int q = 1; q < 16; ++q) mn = fminf(mn, rm[q]);
+                        if (mn > 1.f + bmx) {
+                            dead = true;
+                            break;
+                        }
+                    }
+                }
+                if (!dead) {
+                    uint32_t rfail = 0, rpass = 0;
+#pragma unroll
+                    for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+                        for (int qb = 0; qb < 4; ++qb) {
+                            const int q = qa * 4 + qb;
+                            const float band = KR * (mRi[qa] + mRj[qb]);
+                            if (!(rm[q] <= 1.f + band)) rfail |= 1u << q;
+                            else if (rm[q] <= 1.f - band) rpass |= 1u << q;
+                        }
+                    rpass &= vmask & ~dmask;
+                    rfail |= ~vmask | dmask;
+                    rfail &= 0xFFFFu;
+                    rp_cnt += __popc(rpass);
+                    if (rfail != 0xFFFFu) {
+                        float fm[16];
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) fm[q] = -__int_as_float(0x7f800000);
+                        const float* flp = FL + 4 * gi;
+                        const float* frp = FR + 4 * gj;
+                        const int FRk = NI * nr;
+                        for (int r = 0; r < FRk; ++r) {
+                            const float4 u = *reinterpret_cast<const float4*>(flp + r * T);
+                            const float4 w = *reinterpret_cast<const float4*>(frp + r * T);
+                            const float uu[4] = {u.x, u.y, u.z, u.w};
+                            const float ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                            for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+                                for (int qb = 0; qb < 4; ++qb) fm[qa * 4 + qb] = fmaxf(fm[qa * 4 + qb], uu[qa] + ww[qb]);
+                        }
+                        uint32_t ffail = 0, fpass = 0;
+                        float mFi[4], mFj[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            mFi[q] = magF[4 * gi + q];
+                            mFj[q] = magF[T + 4 * gj + q];
+                        }
+#pragma unroll
+                        for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+                            for (int qb = 0; qb < 4; ++qb) {
+                                const int q = qa * 4 + qb;
+                                const float band = KF * (mFi[qa] + mFj[qb]);
+                                if (!(fm[q] <= band)) ffail |= 1u << q;
+                                else if (fm[q] <= -band) fpass |= 1u << q;
+                            }
+                        const uint32_t feas = rpass & fpass & ~rfail & ~ffail & 0xFFFFu;
+                        const uint32_t amb = ~(rfail | ffail) & ~feas & 0xFFFFu;
+                        if (feas) {
+                            float cs[16];
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) cs[q] = 0.f;
+                            const float* clp = CL + 4 * gi;
+                            const float* crp = CRr + 4 * gj;
+                            const int per_l = DR * M;
+                            for (int l = 0; l < PD; ++l) {
+                                float ss[16];
+#pragma unroll
+                                for (int q = 0; q < 16; ++q) ss[q] = 0.f;
+                                for (int e = 0; e < per_l; ++e) {
+                                    const int row = l * per_l + e;
+                                    const float4 u = *reinterpret_cast<const float4*>(clp + row * T);
+                                    const float4 w = *reinterpret_cast<const float4*>(crp + row * T);
+                                    const float uu[4] = {u.x, u.y, u.z, u.w};
+                                    const float ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                                    for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+                                        for (int qb = 0; qb < 4; ++qb) {
+                                            const float d = uu[qa] + ww[qb];
+                                            ss[qa * 4 + qb] = fmaf(d, d, ss[qa * 4 + qb]);
+                                        }
+                                }
+#pragma unroll
+                                for (int q = 0; q < 16; ++q) cs[q] += sqrtf(ss[q]);
+                            }
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) {
+                                if ((feas >> q) & 1u) {
+                                    bits[q] |= 1u << t;
+                                    if (cs[q] < bc[q]) {
+                                        bc[q] = cs[q];
+                                        bt[q] = t;
+                                    }
+                                }
+                            }
+                        }
+                        if (amb) {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q)
+                                if ((amb >> q) & 1u) append_recheck(P, k, i0 + 4 * gi + (q >> 2), j0 + 4 * gj + (q & 3), t);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (act) {
+            const long long base = P.resOff[k];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                if (!((vmask >> q) & 1u)) continue;
+                const int li = i0 + 4 * gi + (q >> 2), lj = j0 + 4 * gj + (q & 3);
+                const long long slot = base + (long long)li * nk + lj;
+                const bool dg = (dmask >> q) & 1u;
+                P.resBits[slot] = dg ? 0u : bits[q];
+                P.resKey[slot] = (dg || !bits[q]) ? KEY_NONE : key_f32(bc[q], bt[q]);
+            }
+        }
+        __syncthreads();
+    }
+    if (rp_cnt) atomicAdd(&P.info->reach_pass, rp_cnt);
+}
+
+// ---------------------------------------------------------------------------
+// Canonical FP64 helpers (must match the oracle's operation order exactly).
+// ---------------------------------------------------------------------------
+template <int G>
+DEVI double half_sum(const double* coef, const double* x, int stride) {
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < G; ++c) s = __dadd_rn(s, __dmul_rn(coef[c], x[c * stride]));
+    return s;
+}
+
+template <int G, int PD>
+DEVI int reach_order(int r) {  // derivative order k of canonical reach row r (k-major)
+    int k = 1, acc = PD;
+    while (r >= acc && k < G) {
+        ++k;
+        acc += PD - k + 1;
+    }
+    return k;
+}
+
+// A2/A3 FP64 canonical pair kernel: every decision is made in the canonical
+// order, so no re-check is needed.
+template <int M, int G, int PD>
+__global__ void __launch_bounds__(256) k_pairs_f64(BuildParams P) {
+    using S = Shape<G, PD>;
+    constexpr int N_ = M * G, RAX = S::RAX, RR = M * RAX, NI = S::NI, TG = S::TG;
+    constexpr int T = TILE64;
+    extern __shared__ __align__(16) double smd[];
+    const int DR = P.cost_mode == 1 ? 1 : G;
+    const int CRW = G * PD * M;
+    double* hL = smd;
+    double* hR = hL + RR * T;
+    double* cL = hR + RR * T;
+    double* cR = cL + NI * M * T;
+    double* kL = cR + NI * M * T;
+    double* kR = kL + CRW * T;
+    double* xs = kR + CRW * T;
+    double* tab = xs + 2 * T * N_;
+    double* Ap = tab + P.L.e_stride;
+    double* bl = Ap + RMAX * M;
+    double* limr = bl + RMAX;
+    double* bcs = limr + RAX;         // [T*T] best cost
+    uint32_t* bbits = (uint32_t*)(bcs + T * T);
+    uint8_t* bts = (uint8_t*)(bbits + T * T);
+    __shared__ int s_item;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int nitems = (int)P.info->items;
+    const TabLayout L = P.L;
+    unsigned long long rp_cnt = 0;
+    for (int r = tid; r < RAX; r += nthr) limr[r] = P.lim64[reach_order<G, PD>(r) - 1];
+    for (;;) {
+        if (tid == 0) {
+            const int it = (int)atomicAdd(&P.info->ticket, 1u);
+            s_item = has_failed(P.info) ? 0x7fffffff : it;  // one decision for the whole block
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item >= nitems) break;
+        int k, i0, j0, TI, TJ, nk;
+        item_decode(P, item, k, i0, j0, TI, TJ, nk);
+        const int r0 = P.poly_off[k], nr = P.poly_off[k + 1] - r0;
+        for (int u = tid; u < nr * M; u += nthr) Ap[u] = ldv(P.A, (long long)r0 * M + u, P.in_f32);
+        for (int u = tid; u < nr; u += nthr) bl[u] = P.blim64[r0 + u];
+        for (int u = tid; u < (TI + TJ) * N_; u += nthr) {
+            const int s = u / N_, e = u % N_;
+            const bool right = s >= TI;
+            const int ls = right ? s - TI : s;
+            const long long id = P.members[(long long)k * P.N + (right ? j0 : i0) + ls];
+            xs[(right ? T + ls : ls) * N_ + e] = ldv(P.states, id * N_ + e, P.in_f32);
+        }
+        for (int u = tid; u < T * T; u += nthr) {
+            bcs[u] = __longlong_as_double(DINF_BITS);
+            bbits[u] = 0;
+            bts[u] = 0;
+        }
+        __syncthreads();
+        for (int t = 0; t < P.nT; ++t) {
+            for (int u = tid; u < L.e_stride; u += nthr) tab[u] = P.tab64[(long long)t * L.e_stride + u];
+            __syncthreads();
+            for (int u = tid; u < (TI + TJ) * M; u += nthr) {
+                const int s = u / M, a = u % M;
+                const bool right = s >= TI;
+                const int ls = right ? s - TI : s;
+                const double* x = xs + (right ? T + ls : ls) * N_ + a;
+                const int co = right ? G : 0;
+                double* dh = right ? hR : hL;
+                for (int r = 0; r < RAX; ++r) dh[(r * M + a) * T + ls] = half_sum<G>(tab + L.e_H + r * TG + co, x, M);
+                double* dc = right ? cR : cL;
+                for (int l = 1; l <= NI; ++l)
+                    dc[((l - 1) * M + a) * T + ls] = half_sum<G>(tab + L.e_D + l * TG + co, x, M);
+                double* dk = right ? kR : kL;
+                for (int d = 0; d < DR; ++d)
+                    for (int l = 0; l < PD; ++l)
+                        dk[((l * DR + d) * M + a) * T + ls] = half_sum<G>(tab + L.e_C + (d * PD + l) * TG + co, x, M);
+            }
+            __syncthreads();
+            for (int pp = tid; pp < TI * TJ; pp += nthr) {
+                const int li = pp / TJ, lj = pp % TJ;
+                if (i0 + li == j0 + lj) continue;
+                bool ok = true;
+                for (int r = 0; r < RAX && ok; ++r) {
+                    const double lim = limr[r];
+#pragma unroll
+                    for (int a = 0; a < M; ++a) {
+                        const double s = __dadd_rn(hL[(r * M + a) * T + li], hR[(r * M + a) * T + lj]);
+                        if (!(fabs(s) <= lim)) ok = false;
+                    }
+                }
+                if (!ok) continue;
+                ++rp_cnt;
+                for (int l = 0; l < NI && ok; ++l) {
+                    double pt[M];
+#pragma unroll
+                    for (int a = 0; a < M; ++a) pt[a] = __dadd_rn(cL[(l * M + a) * T + li], cR[(l * M + a) * T + lj]);
+                    for (int r = 0; r < nr; ++r) {
+                        double s = 0.0;
+#pragma unroll
+                        for (int a = 0; a < M; ++a) s = __dadd_rn(s, __dmul_rn(Ap[r * M + a], pt[a]));
+                        if (!(s <= bl[r])) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                }
+                if (!ok) continue;
+                double cost = 0.0;
+                const int per_l = DR * M;
+                for (int l = 0; l < PD; ++l) {
+                    double ss = 0.0;
+                    for (int e = 0; e < per_l; ++e) {
+                        const int row = l * per_l + e;
+                        const double d = kL[row * T + li] + kR[row * T + lj];
+                        ss = fma(d, d, ss);
+                    }
+                    cost += sqrt(ss);
+                }
+                const int q = li * T + lj;
+                bbits[q] |= 1u << t;
+                if (cost < bcs[q]) {
+                    bcs[q] = cost;
+                    bts[q] = (uint8_t)t;
+                }
+            }
+            __syncthreads();
+        }
+        const long long base = P.resOff[k];
+        for (int pp = tid; pp < TI * TJ; pp += nthr) {
+            const int li = pp / TJ, lj = pp % TJ;
+            const int q = li * T + lj;
+            const long long slot = base + (long long)(i0 + li) * nk + (j0 + lj);
+            P.resBits[slot] = bbits[q];
+            P.resKey[slot] = bbits[q] ? key_f64(bcs[q], bts[q]) : KEY_NONE;
+        }
+        __syncthreads();
+    }
+    if (rp_cnt) atomicAdd(&P.info->reach_pass, rp_cnt);
+}
+
+// ---------------------------------------------------------------------------
+// A4 re-check: ambiguous (polytope, pair, T) entries evaluated in canonical
+// FP64 (reach rows, then the interior control points against polytope k).
+// ---------------------------------------------------------------------------
+template <int M, int G, int PD>
+__global__ void k_recheck(BuildParams P) {
+    using S = Shape<G, PD>;
+    constexpr int N_ = M * G, RAX = S::RAX, NI = S::NI, TG = S::TG;
+    if (has_failed(P.info)) return;
+    const long long n = min((long long)P.info->rechecks, P.recheckCap);
+    const int DR = P.cost_mode == 1 ? 1 : G;
+    const TabLayout L = P.L;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long en = P.recheck[e];
+        const int t = (int)(en & 31ull), lj = (int)((en >> 5) & 0xFFFFull), li = (int)((en >> 21) & 0xFFFFull);
+        const int k = (int)(en >> 37);
+        const int nk = P.counts[k];
+        const long long i = P.members[(long long)k * P.N + li], j = P.members[(long long)k * P.N + lj];
+        double xi[N_], xj[N_];
+#pragma unroll
+        for (int c = 0; c < N_; ++c) {
+            xi[c] = ldv(P.states, i * N_ + c, P.in_f32);
+            xj[c] = ldv(P.states, j * N_ + c, P.in_f32);
+        }
+        const double* tb = P.tab64 + (long long)t * L.e_stride;
+        bool ok = true;
+        for (int r = 0; r < RAX && ok; ++r) {
+            const double lim = P.lim64[reach_order<G, PD>(r) - 1];
+            for (int a = 0; a < M; ++a) {
+                const double s = __dadd_rn(half_sum<G>(tb + L.e_H + r * TG, xi + a, M),
+                                           half_sum<G>(tb + L.e_H + r * TG + G, xj + a, M));
+                if (!(fabs(s) <= lim)) ok = false;
+            }
+        }
+        const int r0 = P.poly_off[k], r1 = P.poly_off[k + 1];
+        for (int l = 1; l <= NI && ok; ++l) {
+            double pt[M];
+            for (int a = 0; a < M; ++a)
+                pt[a] = __dadd_rn(half_sum<G>(tb + L.e_D + l * TG, xi + a, M), half_sum<G>(tb + L.e_D + l * TG + G, xj + a, M));
+            for (int r = r0; r < r1; ++r) {
+                double s = 0.0;
+                for (int a = 0; a < M; ++a) s = __dadd_rn(s, __dmul_rn(ldv(P.A, (long long)r * M + a, P.in_f32), pt[a]));
+                if (!(s <= P.blim64[r])) {
+                    ok = false;
+                    break;
+                }
+            }
+        }
+        if (!ok) continue;
+        double cost = 0.0;
+        for (int l = 0; l < PD; ++l) {
+            double ss = 0.0;
+            for (int d = 0; d < DR; ++d)
+                for (int a = 0; a < M; ++a) {
+                    const double v = half_sum<G>(tb + L.e_C + (d * PD + l) * TG, xi + a, M) +
+                                     half_sum<G>(tb + L.e_C + (d * PD + l) * TG + G, xj + a, M);
+                    ss = fma(v, v, ss);
+                }
+            cost += sqrt(ss);
+        }
+        const long long slot = P.resOff[k] + (long long)li * nk + lj;
+        atomicOr(&P.resBits[slot], 1u << t);
+        atomicMin(&P.resKey[slot], key_f32((float)cost, t));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// A5 compaction.  The pair (i, j) is emitted by its lowest shared polytope
+// (its "owner"); bits are OR-ed and keys min-ed over all shared polytopes.
+// Pass 1 counts per row and stores, for each slot, the inclusive count of
+// emitted entries in its (row, polytope) segment; pass 2 places every entry
+// at its rank among the row's emitted ids (sorted by j).
+// ---------------------------------------------------------------------------
+DEVI int owner_of(const BuildParams& P, int i, int j, int& nshared) {
+    int owner = -1;
+    nshared = 0;
+    for (int w = 0; w < P.W; ++w) {
+        const uint32_t x = P.memMask[(long long)i * P.W + w] & P.memMask[(long long)j * P.W + w];
+        if (x && owner < 0) owner = w * 32 + __ffs(x) - 1;
+        nshared += __popc(x);
+    }
+    return owner;
+}
+
+DEVI void combine(const BuildParams& P, int i, int j, int k, uint32_t& bits, unsigned long long& key) {
+    for (int w = k >> 5; w < P.W; ++w) {
+        uint32_t x = P.memMask[(long long)i * P.W + w] & P.memMask[(long long)j * P.W + w];
+        if (w == (k >> 5)) x &= ~((2u << (k & 31)) - 1u);  // polytopes above k
+        while (x) {
+            const int k2 = w * 32 + __ffs(x) - 1;
+            x &= x - 1u;
+            const int n2 = P.counts[k2];
+            const long long s2 = P.resOff[k2] + (long long)P.localIdx[(long long)k2 * P.N + i] * n2 +
+                                 P.localIdx[(long long)k2 * P.N + j];
+            bits |= P.resBits[s2];
+            const unsigned long long k2v = P.resKey[s2];
+            if (k2v < key) key = k2v;
+        }
+    }
+}
+
+__global__ void k_compact_count(BuildParams P) {
+    const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= P.N || has_failed(P.info)) return;
+    const int i = warp;
+    long long total = 0, cand = 0, feas = 0;
+    for (int w = 0; w < P.W; ++w) {
+        uint32_t mw = P.memMask[(long long)i * P.W + w];
+        while (mw) {
+            const int k = w * 32 + __ffs(mw) - 1;
+            mw &= mw - 1u;
+            const int nk = P.counts[k];
+            const long long base = P.resOff[k] + (long long)P.localIdx[(long long)k * P.N + i] * nk;
+            int running = 0;
+            for (int lj0 = 0; lj0 < nk; lj0 += 32) {
+                const int lj = lj0 + lane;
+                bool emitted = false;
+                if (lj < nk) {
+                    const int j = P.members[(long long)k * P.N + lj];
+                    if (j != i) {
+                        int ns;
+                        if (owner_of(P, i, j, ns) == k) {
+                            ++cand;
+                            uint32_t bits = P.resBits[base + lj];
+                            unsigned long long key = P.resKey[base + lj];
+                            if (ns > 1) combine(P, i, j, k, bits, key);
+                            emitted = bits != 0;
+                            feas += __popc(bits);
+                        }
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, emitted);
+                if (lj < nk) P.emitPre[base + lj] = running + __popc(bal & ((2u << lane) - 1u));
+                running += __popc(bal);
+            }
+            total += running;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        cand += __shfl_down_sync(0xffffffffu, cand, o);
+        feas += __shfl_down_sync(0xffffffffu, feas, o);
+    }
+    if (lane == 0) {
+        P.rowCount[i] = (int)total;
+        if (cand) atomicAdd(&P.info->candidates, (unsigned long long)cand);
+        if (feas) atomicAdd(&P.info->feasible, (unsigned long long)feas);
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_scan(BuildParams P) {
+    __shared__ long long wb[32];
+    __shared__ long long tot;
+    if (has_failed(P.info)) return;
+    const int N = P.N;
+    const int per = (N + blockDim.x - 1) / blockDim.x;
+    const int s0 = threadIdx.x * per, s1 = min(N, s0 + per);
+    long long local = 0;
+    for (int i = s0; i < s1; ++i) local += P.rowCount[i];
+    long long run = block_exclusive_scan<long long>(local, wb, &tot);
+    const long long total = tot;
+    for (int i = s0; i < s1; ++i) {
+        P.row_off[i] = (int32_t)run;
+        run += P.rowCount[i];
+    }
+    if (threadIdx.x == 0) {
+        P.row_off[N] = (int32_t)total;
+        P.info->edges = total;
+        *P.count = total;
+        if (total > P.cap || total > 0x7fffffffLL) set_status(P.info, PLAN_ERR_CAPACITY, DET_OUTPUT);
+    }
+}
+
+DEVI int lower_bound_members(const int* mem, int n, int j) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (mem[mid] < j) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_compact_fill(BuildParams P) {
+    const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= P.N || has_failed(P.info)) return;
+    const int i = warp;
+    int npoly = 0;
+    for (int w = 0; w < P.W; ++w) npoly += __popc(P.memMask[(long long)i * P.W + w]);
+    const long long rbase = P.row_off[i];
+    const bool f64 = P.arith == PLAN_F64;
+    for (int w = 0; w < P.W; ++w) {
+        uint32_t mw = P.memMask[(long long)i * P.W + w];
+        while (mw) {
+            const int k = w * 32 + __ffs(mw) - 1;
+            mw &= mw - 1u;
+            const int nk = P.counts[k];
+            const long long base = P.resOff[k] + (long long)P.localIdx[(long long)k * P.N + i] * nk;
+            for (int lj = lane; lj < nk; lj += 32) {
+                const int j = P.members[(long long)k * P.N + lj];
+                if (j == i) continue;
+                const int pre = P.emitPre[base + lj];
+                const int prev = lj > 0 ? P.emitPre[base + lj - 1] : 0;
+                if (pre == prev) continue;  // not emitted here
+                int ns;
+                owner_of(P, i, j, ns);
+                uint32_t bits = P.resBits[base + lj];
+                unsigned long long key = P.resKey[base + lj];
+                if (ns > 1) combine(P, i, j, k, bits, key);
+                long long rank = prev;
+                if (npoly > 1) {
+                    for (int w2 = 0; w2 < P.W; ++w2) {
+                        uint32_t m2 = P.memMask[(long long)i * P.W + w2];
+                        while (m2) {
+                            const int k2 = w2 * 32 + __ffs(m2) - 1;
+                            m2 &= m2 - 1u;
+                            if (k2 == k) continue;
+                            const int n2 = P.counts[k2];
+                            const int pos = lower_bound_members(P.members + (long long)k2 * P.N, n2, j);
+                            if (pos > 0) {
+                                const long long b2 = P.resOff[k2] + (long long)P.localIdx[(long long)k2 * P.N + i] * n2;
+                                rank += P.emitPre[b2 + pos - 1];
+                            }
+                        }
+                    }
+                }
+                const long long o = rbase + rank;
+                P.col[o] = j;
+                P.mask[o] = bits;
+                const int tb = (int)(key & 31ull);
+                P.tidx[o] = (uint8_t)tb;
+                if (f64) ((double*)P.w)[o] = __longlong_as_double((long long)(key & ~31ull));
+                else ((float*)P.w)[o] = __uint_as_float((unsigned)(key >> 32));
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Work accounting (untimed, on request): the algorithmic work of the edge
+// build under short-circuit evaluation in the pair kernel's row order.  For
+// every distinct check (owner pair, T): reach rows (row, axis) are counted up
+// to and including the first violated one (all of them when the check passes
+// the reach test); a reach-passing check then counts free rows (control point
+// l, polytope row r) up to the first violated one for each shared polytope in
+// turn, stopping at the first polytope that contains the hull; a feasible
+// check counts one cost evaluation.  Margins use FP32 like the fast kernel.
+// ---------------------------------------------------------------------------
+template <int M, int G, int PD>
+__global__ void k_account(BuildParams P, unsigned long long* work) {
+    using S = Shape<G, PD>;
+    constexpr int N_ = M * G, RAX = S::RAX, NI = S::NI, TG = S::TG;
+    if (has_failed(P.info)) return;
+    const TabLayout L = P.L;
+    const long long total = (long long)P.info->slots;
+    unsigned long long wr = 0, wf = 0, wc = 0;
+    for (long long sidx = blockIdx.x * (long long)blockDim.x + threadIdx.x; sidx < total;
+         sidx += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = P.K;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (P.resOff[mid] <= sidx) lo = mid;
+            else hi = mid;
+        }
+        const int k = lo, nk = P.counts[k];
+        const long long loc = sidx - P.resOff[k];
+        const int li = (int)(loc / nk), lj = (int)(loc % nk);
+        const int i = P.members[(long long)k * P.N + li], j = P.members[(long long)k * P.N + lj];
+        if (i == j) continue;
+        int ns;
+        if (owner_of(P, i, j, ns) != k) continue;
+        float xi[N_], xj[N_];
+        for (int c = 0; c < N_; ++c) {
+            xi[c] = ldf(P.states, (long long)i * N_ + c, P.in_f32);
+            xj[c] = ldf(P.states, (long long)j * N_ + c, P.in_f32);
+        }
+        for (int t = 0; t < P.nT; ++t) {
+            const float* tb = P.tab32 + (long long)t * L.f_stride;
+            bool ok = true;
+            for (int r = 0; r < RAX && ok; ++r)
+                for (int a = 0; a < M && ok; ++a) {
+                    float s = 0.f;
+                    for (int c = 0; c < G; ++c) s += tb[L.f_H + r * TG + c] * xi[c * M + a] + tb[L.f_H + r * TG + G + c] * xj[c * M + a];
+                    ++wr;
+                    if (fabsf(s) > 1.f) ok = false;
+                }
+            if (!ok) continue;
+            float pt[NI][M];
+            for (int l = 0; l < NI; ++l)
+                for (int a = 0; a < M; ++a) {
+                    float s = 0.f;
+                    for (int c = 0; c < G; ++c) s += tb[L.f_D + l * TG + c] * xi[c * M + a] + tb[L.f_D + l * TG + G + c] * xj[c * M + a];
+                    pt[l][a] = s;
+                }
+            bool feas = false;
+            for (int w = 0; w < P.W && !feas; ++w) {
+                uint32_t x = P.memMask[(long long)i * P.W + w] & P.memMask[(long long)j * P.W + w];
+                while (x && !feas) {
+                    const int k2 = w * 32 + __ffs(x) - 1;
+                    x &= x - 1u;
+                    bool fok = true;
+                    for (int l = 0; l < NI && fok; ++l)
+                        for (int r = P.poly_off[k2]; r < P.poly_off[k2 + 1] && fok; ++r) {
+                            float s = 0.f;
+                            for (int a = 0; a < M; ++a) s += P.A32[(long long)r * M + a] * pt[l][a];
+                            ++wf;
+                            if (s > P.blim32[r]) fok = false;
+                        }
+                    feas = fok;
+                }
+            }
+            if (feas) ++wc;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        wr += __shfl_down_sync(0xffffffffu, wr, o);
+        wf += __shfl_down_sync(0xffffffffu, wf, o);
+        wc += __shfl_down_sync(0xffffffffu, wc, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&work[0], wr);
+        atomicAdd(&work[1], wf);
+        atomicAdd(&work[2], wc);
+    }
+}
+
+int launch_account(const BuildParams& P, void* stream, int num_sms, unsigned long long* work) {
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaMemsetAsync(work, 0, 3 * sizeof(unsigned long long), st);
+    const int nb = num_sms * 8;
+    if (P.m == 2 && P.g == 2 && P.p == 3) k_account<2, 2, 3><<<nb, 256, 0, st>>>(P, work);
+    else if (P.m == 2 && P.g == 2 && P.p == 5) k_account<2, 2, 5><<<nb, 256, 0, st>>>(P, work);
+    else if (P.m == 3 && P.g == 3 && P.p == 5) k_account<3, 3, 5><<<nb, 256, 0, st>>>(P, work);
+    else if (P.m == 3 && P.g == 3 && P.p == 7) k_account<3, 3, 7><<<nb, 256, 0, st>>>(P, work);
+    return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Launch sequence.
+// ---------------------------------------------------------------------------
+template <int M, int G, int PD>
+size_t smem_fast(const BuildParams& P) {
+    using S = Shape<G, PD>;
+    const int RR = M * S::RAX, FRm = S::NI * P.max_rows, CRW = G * PD * M;
+    size_t f = (size_t)(2 * RR + 2 * FRm + 2 * CRW + 4) * TILE + 2 * TILE * (M * G + G) + P.L.f_stride + RMAX * (M + 1);
+    return f * sizeof(float);
+}
+
+template <int M, int G, int PD>
+size_t smem_f64(const BuildParams& P) {
+    using S = Shape<G, PD>;
+    const int RR = M * S::RAX, CRW = G * PD * M;
+    size_t d = (size_t)(2 * RR + 2 * S::NI * M + 2 * CRW) * TILE64 + 2 * TILE64 * M * G + P.L.e_stride + RMAX * (M + 1) +
+               S::RAX + TILE64 * TILE64;
+    return d * sizeof(double) + TILE64 * TILE64 * (sizeof(uint32_t) + 1) + 16;
+}
+
+template <int M, int G, int PD>
+int launch_pairs(const BuildParams& P, cudaStream_t st, int num_sms, cudaEvent_t e0, cudaEvent_t e1, int* launches) {
+    if (P.arith == PLAN_F64) {
+        const size_t sm = smem_f64<M, G, PD>(P);
+        cudaFuncSetAttribute(k_pairs_f64<M, G, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pairs_f64<M, G, PD>, 256, sm);
+        if (occ < 1) occ = 1;
+        if (e0) cudaEventRecord(e0, st);
+        k_pairs_f64<M, G, PD><<<num_sms * occ, 256, sm, st>>>(P);
+        if (e1) cudaEventRecord(e1, st);
+        ++*launches;
+    } else {
+        const size_t sm = smem_fast<M, G, PD>(P);
+        cudaFuncSetAttribute(k_pairs_fast<M, G, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pairs_fast<M, G, PD>, 256, sm);
+        if (occ < 1) occ = 1;
+        if (e0) cudaEventRecord(e0, st);
+        k_pairs_fast<M, G, PD><<<num_sms * occ, 256, sm, st>>>(P);
+        if (e1) cudaEventRecord(e1, st);
+        ++*launches;
+        k_recheck<M, G, PD><<<num_sms * 4, 128, 0, st>>>(P);
+        ++*launches;
+    }
+    return (int)cudaGetLastError();
+}
+
+bool model_supported(int m, int g, int p) {
+    return (m == 2 && g == 2 && (p == 3 || p == 5)) || (m == 3 && g == 3 && (p == 5 || p == 7));
+}
+
+int launch_build(const BuildParams& P, void* stream, int num_sms, void* ev0, void* ev1, int* launches) {
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = (cudaEvent_t)ev0, e1 = (cudaEvent_t)ev1;
+    if (P.K > 0 && P.max_rows > 0) {
+        const long long nt = (long long)P.K * P.max_rows;
+        k_prep<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(P);
+        ++*launches;
+    }
+    if (P.N > 0 && P.K > 0) {
+        const long long nt = (long long)P.N * P.W;
+        k_member<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(P);
+        k_lists<<<P.K, 1024, 0, st>>>(P);
+        *launches += 2;
+    }
+    k_setup<<<1, 1024, 0, st>>>(P, P.arith == PLAN_F64 ? TILE64 : TILE);
+    ++*launches;
+    if (P.N > 0 && P.K > 0) {
+        int rc = 0;
+        if (P.m == 2 && P.g == 2 && P.p == 3) rc = launch_pairs<2, 2, 3>(P, st, num_sms, e0, e1, launches);
+        else if (P.m == 2 && P.g == 2 && P.p == 5) rc = launch_pairs<2, 2, 5>(P, st, num_sms, e0, e1, launches);
+        else if (P.m == 3 && P.g == 3 && P.p == 5) rc = launch_pairs<3, 3, 5>(P, st, num_sms, e0, e1, launches);
+        else if (P.m == 3 && P.g == 3 && P.p == 7) rc = launch_pairs<3, 3, 7>(P, st, num_sms, e0, e1, launches);
+        if (rc) return rc;
+        const long long thr = (long long)P.N * 32;
+        k_compact_count<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(P);
+        ++*launches;
+    } else if (P.N > 0) {
+        cudaMemsetAsync(P.rowCount, 0, sizeof(int) * (size_t)P.N, st);
+    }
+    k_scan<<<1, 1024, 0, st>>>(P);
+    ++*launches;
+    if (P.N > 0 && P.K > 0) {
+        const long long thr = (long long)P.N * 32;
+        k_compact_fill<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(P);
+        ++*launches;
+    }
+    return (int)cudaGetLastError();
+}
+
+}  // namespace plan

@@ -1,0 +1,184 @@
+// Internal definitions shared by the CUDA translation units of libplan.
+#pragma once
+
+#include <cstdint>
+
+#include "../../include/plan.h"
+
+namespace plan {
+
+constexpr int RMAX = 16;        // rows per free polytope (ABI limit)
+constexpr int NT_MAX = 32;      // durations per call (one bit each in the mask)
+constexpr int TILE = 64;        // tile side of the FP32 pair kernel (states per side)
+constexpr int TILE64 = 32;      // tile side of the FP64 pair kernel
+constexpr int NK_MAX = 65535;   // members per polytope (16-bit local index in re-check entries)
+
+// Host: FP64 tables (see plan_tables.cpp).
+int reach_rows(int g, int p);
+void exact_tables(int g, int p, int nT, const double* T, double* D, double* H, double* C);
+
+// Layout of the per-duration tables uploaded to the device (depends on g, p only).
+struct TabLayout {
+    int g, p, tg, rax, ni;
+    // FP32 fast table (floats): reach rows scaled by 1/(c_k - eps) in kernel
+    // order, interior control points, cost rows, column maxima for the bands.
+    int f_H, f_D, f_C, f_HC, f_DC, f_stride;
+    // FP64 canonical table (doubles): reach rows (k-major), all control points, cost rows.
+    int e_H, e_D, e_C, e_stride;
+};
+
+inline TabLayout tab_layout(int g, int p) {
+    TabLayout L;
+    L.g = g;
+    L.p = p;
+    L.tg = 2 * g;
+    L.rax = 0;
+    for (int k = 1; k <= g; ++k) L.rax += p - k + 1;
+    L.ni = p - 1;
+    L.f_H = 0;
+    L.f_D = L.f_H + L.rax * L.tg;
+    L.f_C = L.f_D + L.ni * L.tg;
+    L.f_HC = L.f_C + g * p * L.tg;
+    L.f_DC = L.f_HC + 2 * g;
+    L.f_stride = (L.f_DC + 2 * g + 3) & ~3;
+    L.e_H = 0;
+    L.e_D = L.e_H + L.rax * L.tg;
+    L.e_C = L.e_D + (p + 1) * L.tg;
+    L.e_stride = L.e_C + g * p * L.tg;
+    return L;
+}
+
+// Device-side counters and status of the current call (mirrors plan_info).
+struct DevInfo {
+    int status;
+    int detail;
+    unsigned long long memberships;
+    unsigned long long slots;
+    unsigned long long candidates;
+    unsigned long long reach_pass;
+    unsigned long long feasible;
+    unsigned long long rechecks;
+    unsigned long long edges;
+    unsigned long long search_iters;
+    unsigned long long need_slots;
+    unsigned long long need_rechecks;
+    unsigned long long items;
+    unsigned int ticket;
+    int max_rows_seen;
+    int start;
+    int goal;
+    // search scratch
+    unsigned long long near_d[2];
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    int changed[3];
+    int path_len;
+    unsigned long long work[3];
+};
+
+enum Detail {
+    DET_NONE = 0,
+    DET_SLOTS = 1,
+    DET_RECHECK = 2,
+    DET_OUTPUT = 3,
+    DET_ROWS = 4,
+    DET_NK = 5,
+    DET_PATHCAP = 6,
+    DET_BARRIER = 7,
+    DET_SWEEPS = 8,
+    DET_WALK = 9
+};
+
+// Everything a build kernel needs, passed by value.
+struct BuildParams {
+    int N, K, nT, W, R;        // W: 32-bit words per membership mask; R: row capacity
+    int m, g, p;
+    int cost_mode, in_f32, arith, max_rows;
+    double eps;
+    const void* states;
+    const int* poly_off;
+    const void* A;
+    const void* b;
+    const float* tab32;        // [nT][f_stride]
+    const double* tab64;       // [nT][e_stride]
+    double lim64[4];           // c_k - eps
+    TabLayout L;
+    // scratch
+    uint32_t* memMask;         // [N][W]
+    int* counts;               // [K]
+    int* members;              // [K][N]
+    int* localIdx;             // [K][N]
+    float* centers;            // [K][4] (FP32 position of the first member)
+    double* blim64;            // [R] b - eps
+    float* A32;                // [R][m]
+    float* blim32;             // [R]
+    float* bc32;               // [R] centred bound for the fast kernels
+    long long* resOff;         // [K+1]
+    int* itemOff;              // [K+1]
+    int* ntile;                // [K]
+    int* tsize;                // [K]
+    uint32_t* resBits;         // [slotCap]
+    unsigned long long* resKey;// [slotCap]
+    int* emitPre;              // [slotCap]
+    unsigned long long* recheck; // [recheckCap]
+    int* rowCount;             // [N]
+    long long slotCap, recheckCap;
+    DevInfo* info;
+    // output CSR
+    int32_t* row_off;
+    int32_t* col;
+    void* w;
+    uint8_t* tidx;
+    uint32_t* mask;
+    long long cap;
+    int64_t* count;
+};
+
+struct SearchParams {
+    int N, m, n, in_f32, w_f64;
+    const void* states;
+    const int32_t* row_off;
+    const int32_t* col;
+    const void* w;
+    const int64_t* count;
+    long long cap;
+    double start[4], goal[4];
+    unsigned long long* dist;  // [N] bit patterns of non-negative doubles
+    unsigned long long* bestU; // [N]
+    int* pred;                 // [N]
+    unsigned char* front;      // [2][N]
+    int32_t* path;
+    int path_cap;
+    int32_t* path_len;
+    double* cost;
+    DevInfo* info;
+    int max_sweeps;
+    long long spin_limit;
+};
+
+struct RefineParams {
+    long long S;
+    int m, g, p, rmax;
+    const float* P;        // [S][p+1][m]
+    const float* T;        // [S]
+    const float* A;        // [S][rmax][m]
+    const float* b;        // [S][rmax]
+    const int32_t* nrows;  // [S]
+    float bound[4];
+    float w_snap, mu, delta;
+    const float* grad_loss;  // [S] or null (forward only)
+    float* loss;           // [S] or null
+    float* dP;             // [S][p+1][m]
+    float* dT;             // [S]
+};
+
+// Launchers (plan_build.cu / plan_search.cu / plan_refine.cu); return cudaError_t as int.
+int launch_build(const BuildParams& P, void* stream, int num_sms, void* ev_pair_begin, void* ev_pair_end,
+                 int* launches);
+int launch_search(const SearchParams& P, void* stream, int num_sms, int* launches);
+int launch_account(const BuildParams& P, void* stream, int num_sms, unsigned long long* work);
+bool model_supported(int m, int g, int p);
+bool refine_supported(int m, int g, int p);
+int launch_refine(const RefineParams& R, void* stream, int* launches);
+
+}  // namespace plan

@@ -1,0 +1,255 @@
+// findPath for sm_103a (Sec. III-C, Problem 2): nearest start/goal vertices,
+// then single-source shortest paths with Dijkstra's semantics, all in one
+// cooperative kernel with a bounded software grid barrier.
+//
+// Distances are FP64 bit patterns (non-negative doubles order like unsigned
+// integers), relaxed with atomicMin by a frontier sweep (Bellman-Ford).  With
+// non-negative weights and round-to-nearest, fl(d + w) is monotone in d and
+// >= d, so the sweep's fixed point is the minimum over paths of the
+// left-to-right rounded path sum -- the same value Dijkstra produces.  The
+// predecessor of v is then the in-neighbour u attaining dist[v] that Dijkstra
+// (heap keyed (dist, id), strict-improvement relaxation) settles first: the
+// minimum (dist[u], u).
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "plan_internal.h"
+
+namespace plan {
+
+#define DEVI __device__ __forceinline__
+
+namespace {
+constexpr unsigned long long DINF = 0x7FF0000000000000ull;
+
+DEVI void set_status_s(DevInfo* info, int code, int detail) {
+    if (atomicCAS(&info->status, 0, code) == 0) atomicExch(&info->detail, detail);
+}
+DEVI bool failed_s(const DevInfo* info) {
+    const int s = *((volatile const int*)&info->status);
+    return s != 0 && s != PLAN_ERR_NO_PATH;
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).  The
+// spin is bounded: on expiry the block records PLAN_ERR_TIMEOUT and returns
+// false instead of waiting forever.
+DEVI bool grid_sync(DevInfo* info, unsigned nblocks, long long spin_limit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned* genp = &info->bar_gen;
+        const unsigned gen = *genp;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&info->bar_count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&info->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&info->bar_gen, 1u);
+        } else {
+            long long it = 0;
+            while (*genp == gen) {
+                if (++it > spin_limit) {
+                    set_status_s(info, PLAN_ERR_TIMEOUT, DET_BARRIER);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+DEVI double ldd(const void* p, long long i, int f32) {
+    return f32 ? (double)((const float*)p)[i] : ((const double*)p)[i];
+}
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_search(SearchParams P) {
+    const unsigned nb = gridDim.x;
+    const long long gtid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const long long gwarp = gtid >> 5, nwarps = nthr >> 5;
+    DevInfo* info = P.info;
+    const int N = P.N;
+
+    // phase 0: initialise scratch
+    if (gtid == 0) {
+        info->near_d[0] = ~0ull;
+        info->near_d[1] = ~0ull;
+        info->start = 0x7fffffff;
+        info->goal = 0x7fffffff;
+        info->changed[0] = 0;
+        info->changed[1] = 0;
+        info->changed[2] = 0;
+        const long long E = *P.count;
+        if (E < 0 || E > P.cap) set_status_s(info, PLAN_ERR_INVALID_ARG, DET_OUTPUT);
+    }
+    for (long long v = gtid; v < N; v += nthr) {
+        P.dist[v] = DINF;
+        P.bestU[v] = ~0ull;
+        P.pred[v] = 0x7fffffff;
+        P.front[v] = 0;
+        P.front[N + v] = 0;
+    }
+    if (!grid_sync(info, nb, P.spin_limit)) return;
+    if (failed_s(info)) return;
+
+    // A6: nearest vertex to the start and goal positions (canonical FP64
+    // squared distance summed left to right; ties to the lowest id)
+    for (long long v = gtid; v < N; v += nthr) {
+        double ds = 0.0, dg = 0.0;
+        for (int a = 0; a < P.m; ++a) {
+            const double x = ldd(P.states, v * P.n + a, P.in_f32);
+            const double ts = __dsub_rn(x, P.start[a]);
+            const double tg = __dsub_rn(x, P.goal[a]);
+            ds = __dadd_rn(ds, __dmul_rn(ts, ts));
+            dg = __dadd_rn(dg, __dmul_rn(tg, tg));
+        }
+        atomicMin(&info->near_d[0], (unsigned long long)__double_as_longlong(ds));
+        atomicMin(&info->near_d[1], (unsigned long long)__double_as_longlong(dg));
+    }
+    if (!grid_sync(info, nb, P.spin_limit)) return;
+    for (long long v = gtid; v < N; v += nthr) {
+        double ds = 0.0, dg = 0.0;
+        for (int a = 0; a < P.m; ++a) {
+            const double x = ldd(P.states, v * P.n + a, P.in_f32);
+            const double ts = __dsub_rn(x, P.start[a]);
+            const double tg = __dsub_rn(x, P.goal[a]);
+            ds = __dadd_rn(ds, __dmul_rn(ts, ts));
+            dg = __dadd_rn(dg, __dmul_rn(tg, tg));
+        }
+        if ((unsigned long long)__double_as_longlong(ds) == info->near_d[0]) atomicMin(&info->start, (int)v);
+        if ((unsigned long long)__double_as_longlong(dg) == info->near_d[1]) atomicMin(&info->goal, (int)v);
+    }
+    if (!grid_sync(info, nb, P.spin_limit)) return;
+    const int s = *((volatile int*)&info->start), g = *((volatile int*)&info->goal);
+    if (s < 0 || s >= N || g < 0 || g >= N) {
+        if (gtid == 0) set_status_s(info, PLAN_ERR_INVALID_ARG, DET_WALK);
+        return;
+    }
+    if (gtid == 0) {
+        P.dist[s] = 0ull;
+        P.front[s] = 1;
+    }
+    if (!grid_sync(info, nb, P.spin_limit)) return;
+
+    // A7: frontier sweeps until no distance changes
+    int cur = 0, it = 0;
+    volatile unsigned long long* vdist = P.dist;
+    for (;;) {
+        bool my_change = false;
+        for (long long v = gwarp; v < N; v += nwarps) {
+            if (!*((volatile unsigned char*)&P.front[cur * N + v])) continue;
+            __syncwarp();
+            if (lane == 0) P.front[cur * N + v] = 0;
+            const double dv = __longlong_as_double((long long)vdist[v]);
+            const long long e0 = P.row_off[v], e1 = P.row_off[v + 1];
+            for (long long e = e0 + lane; e < e1; e += 32) {
+                const int u = P.col[e];
+                if (u < 0 || u >= N) continue;
+                const double w = P.w_f64 ? ((const double*)P.w)[e] : (double)((const float*)P.w)[e];
+                const unsigned long long nd = (unsigned long long)__double_as_longlong(__dadd_rn(dv, w));
+                const unsigned long long old = atomicMin(&P.dist[u], nd);
+                if (nd < old) {
+                    P.front[(cur ^ 1) * N + u] = 1;
+                    my_change = true;
+                }
+            }
+        }
+        // flag of sweep j is changed[j % 3]: written during sweep j, read after
+        // its barrier, cleared during sweep j+2 (after every block has read it)
+        if (__any_sync(0xffffffffu, my_change) && lane == 0) atomicExch(&info->changed[it % 3], 1);
+        if (gtid == 0) info->changed[(it + 1) % 3] = 0;
+        if (!grid_sync(info, nb, P.spin_limit)) return;
+        const int ch = *((volatile int*)&info->changed[it % 3]);
+        ++it;
+        if (!ch) break;
+        if (it > P.max_sweeps) {
+            if (gtid == 0) set_status_s(info, PLAN_ERR_TIMEOUT, DET_SWEEPS);
+            return;
+        }
+        cur ^= 1;
+    }
+
+    // predecessor: minimum (dist[u], u) over in-neighbours attaining dist[v]
+    for (int pass = 0; pass < 2; ++pass) {
+        for (long long v = gwarp; v < N; v += nwarps) {
+            const unsigned long long dvb = vdist[v];
+            if (dvb >= DINF) continue;
+            const double dv = __longlong_as_double((long long)dvb);
+            const long long e0 = P.row_off[v], e1 = P.row_off[v + 1];
+            for (long long e = e0 + lane; e < e1; e += 32) {
+                const int u = P.col[e];
+                if (u < 0 || u >= N || u == s) continue;
+                const double w = P.w_f64 ? ((const double*)P.w)[e] : (double)((const float*)P.w)[e];
+                const unsigned long long nd = (unsigned long long)__double_as_longlong(__dadd_rn(dv, w));
+                if (nd != vdist[u]) continue;
+                if (pass == 0) atomicMin(&P.bestU[u], dvb);
+                else if (P.bestU[u] == dvb) atomicMin(&P.pred[u], (int)v);
+            }
+        }
+        if (!grid_sync(info, nb, P.spin_limit)) return;
+    }
+
+    // walk goal -> start
+    if (gtid == 0) {
+        info->search_iters = (unsigned long long)it;
+        const unsigned long long dg = vdist[g];
+        if (dg >= DINF) {
+            *P.path_len = 0;
+            *P.cost = __longlong_as_double((long long)DINF);
+            set_status_s(info, PLAN_ERR_NO_PATH, DET_NONE);
+        } else {
+            int len = 1, v = g;
+            bool okw = true;
+            while (v != s) {
+                v = P.pred[v];
+                if (v < 0 || v >= N || len > N) {
+                    okw = false;
+                    break;
+                }
+                ++len;
+            }
+            if (!okw) {
+                set_status_s(info, PLAN_ERR_INVALID_ARG, DET_WALK);
+                *P.path_len = 0;
+            } else if (len > P.path_cap) {
+                set_status_s(info, PLAN_ERR_CAPACITY, DET_PATHCAP);
+                *P.path_len = len;
+            } else {
+                v = g;
+                for (int q = len - 1; q >= 0; --q) {
+                    P.path[q] = v;
+                    if (q) v = P.pred[v];
+                }
+                *P.path_len = len;
+            }
+            *P.cost = __longlong_as_double((long long)dg);
+        }
+        info->path_len = *P.path_len;
+    }
+}
+
+int launch_search(const SearchParams& P, void* stream, int num_sms, int* launches) {
+    cudaStream_t st = (cudaStream_t)stream;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_search, 256, 0);
+    if (occ < 1) occ = 1;
+    if (occ > 2) occ = 2;
+    const int nb = num_sms * occ;
+    SearchParams Q = P;
+    void* args[] = {&Q};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_search, dim3(nb), dim3(256), args, 0, st);
+    ++*launches;
+    return (int)e;
+}
+
+}  // namespace plan

@@ -1,0 +1,348 @@
+"""Python binding of libplan (ctypes): argument marshalling only.
+
+Every step of the planner runs in the CUDA kernels behind the C ABI declared
+in ``include/plan.h``; this module allocates torch tensors for the outputs,
+passes raw pointers and the current CUDA stream, and reads statuses.  There is
+no CPU fallback: if ``libplan.so`` cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+PLAN_OK, PLAN_ERR_INVALID_ARG, PLAN_ERR_UNSUPPORTED, PLAN_ERR_CAPACITY = 0, 1, 2, 3
+PLAN_ERR_CUDA, PLAN_ERR_TIMEOUT, PLAN_ERR_NO_PATH, PLAN_ERR_NO_MEMORY = 4, 5, 6, 7
+ARITH = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3}
+INPUT = {"f64": 0, "f32": 1}
+COST = {"state": 0, "pos": 1}
+DET_SLOTS, DET_RECHECK, DET_OUTPUT = 1, 2, 3
+
+_lib = None
+
+
+class PlanError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        self.status = status
+        super().__init__(f"plan status {status} ({status_string(status)}){': ' + msg if msg else ''}")
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("gamma", ctypes.c_int), ("degree", ctypes.c_int),
+                ("arith", ctypes.c_int), ("input", ctypes.c_int), ("cost_mode", ctypes.c_int),
+                ("bound", ctypes.c_double * 4), ("tighten", ctypes.c_double)]
+
+
+class _Edges(ctypes.Structure):
+    _fields_ = [("row_off", ctypes.c_void_p), ("col", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("tidx", ctypes.c_void_p), ("mask", ctypes.c_void_p), ("cap", ctypes.c_int64),
+                ("count", ctypes.c_void_p)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("detail", ctypes.c_int32), ("memberships", ctypes.c_int64),
+                ("slots", ctypes.c_int64), ("candidates", ctypes.c_int64), ("checks", ctypes.c_int64),
+                ("reach_pass", ctypes.c_int64), ("feasible", ctypes.c_int64), ("rechecks", ctypes.c_int64),
+                ("edges", ctypes.c_int64), ("search_iters", ctypes.c_int64), ("start", ctypes.c_int32),
+                ("goal", ctypes.c_int32), ("need_slots", ctypes.c_int64), ("need_rechecks", ctypes.c_int64),
+                ("work_reach_rows", ctypes.c_int64), ("work_free_rows", ctypes.c_int64), ("work_costs", ctypes.c_int64)]
+
+
+class _RefineW(ctypes.Structure):
+    _fields_ = [("w_snap", ctypes.c_double), ("mu", ctypes.c_double), ("delta", ctypes.c_double)]
+
+
+EXPORTS = ["plan_create", "plan_destroy", "plan_build_edges", "plan_search", "plan_wait", "plan_model_tables",
+           "plan_set_search_limits", "plan_refine", "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_stale: bool = True):
+    """Load libplan.so (building it first when sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_stale and _build.is_stale():
+        _build.build()
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libplan.so not built ({path}); run paper_2411_13507_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+    lib.plan_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_Model), vp]
+    lib.plan_create.restype = i32
+    lib.plan_destroy.argtypes = [vp]
+    lib.plan_destroy.restype = None
+    lib.plan_build_edges.argtypes = [vp, i32, vp, i32, dp, i32, vp, i32, vp, vp, ctypes.POINTER(_Edges)]
+    lib.plan_build_edges.restype = i32
+    lib.plan_search.argtypes = [vp, i32, vp, ctypes.POINTER(_Edges), dp, dp, vp, i32, vp, vp]
+    lib.plan_search.restype = i32
+    lib.plan_wait.argtypes = [vp, ctypes.POINTER(_Info)]
+    lib.plan_wait.restype = i32
+    lib.plan_model_tables.argtypes = [ctypes.POINTER(_Model), i32, dp, dp, dp, dp]
+    lib.plan_model_tables.restype = i32
+    lib.plan_set_search_limits.argtypes = [vp, i32, i64]
+    lib.plan_set_search_limits.restype = i32
+    lib.plan_refine.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, ctypes.POINTER(_RefineW), vp, vp, vp, vp]
+    lib.plan_refine.restype = i32
+    lib.plan_set_accounting.argtypes = [vp, i32]
+    lib.plan_set_accounting.restype = i32
+    lib.plan_set_timing.argtypes = [vp, i32]
+    lib.plan_set_timing.restype = i32
+    lib.plan_timing.argtypes = [vp, dp, ctypes.POINTER(i64), dp, ctypes.POINTER(i64), ctypes.POINTER(i64), i32]
+    lib.plan_timing.restype = i32
+    lib.plan_status_string.argtypes = [i32]
+    lib.plan_status_string.restype = ctypes.c_char_p
+    lib.plan_last_error.argtypes = [vp]
+    lib.plan_last_error.restype = ctypes.c_char_p
+    lib.plan_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def status_string(s: int) -> str:
+    try:
+        return load().plan_status_string(int(s)).decode()
+    except Exception:
+        return "?"
+
+
+def _model(m, gamma, degree, bounds, arith="f64", input="f64", cost_mode="state", tighten=0.0) -> _Model:
+    b = (ctypes.c_double * 4)(*([float(x) for x in bounds] + [0.0] * (4 - len(bounds))))
+    return _Model(int(m), int(gamma), int(degree), ARITH[arith], INPUT[input], COST[cost_mode], b, float(tighten))
+
+
+def model_tables(gamma: int, degree: int, T: Sequence[float]):
+    """The library's FP64 coefficient tables (host only, no GPU): D, H, C."""
+    lib = load()
+    T = np.ascontiguousarray(np.asarray(T, dtype=np.float64))
+    g, p, nT = int(gamma), int(degree), T.shape[0]
+    rax = sum(p - k + 1 for k in range(1, g + 1))
+    D = np.zeros((nT, p + 1, 2 * g))
+    H = np.zeros((nT, rax, 2 * g))
+    C = np.zeros((nT, g, p, 2 * g))
+    mdl = _model(1, g, p, [1.0] * g)
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    rc = lib.plan_model_tables(ctypes.byref(mdl), nT, dp(T), dp(D), dp(H), dp(C))
+    if rc != 0:
+        raise PlanError(rc)
+    return {"D": D, "H": H, "C": C}
+
+
+@dataclass
+class Graph:
+    """Feasible-edge CSR on the device (torch tensors)."""
+    N: int
+    row_off: "torch.Tensor"
+    col: "torch.Tensor"
+    w: "torch.Tensor"
+    tidx: "torch.Tensor"
+    mask: "torch.Tensor"      # int32 storage of uint32 masks
+    count: "torch.Tensor"
+    cap: int
+
+    def cstruct(self) -> _Edges:
+        return _Edges(self.row_off.data_ptr(), self.col.data_ptr(), self.w.data_ptr(), self.tidx.data_ptr(),
+                      self.mask.data_ptr(), int(self.cap), self.count.data_ptr())
+
+    @property
+    def E(self) -> int:
+        return int(self.count.item())
+
+    def to_numpy(self) -> dict:
+        E = self.E
+        return {"row_off": self.row_off.cpu().numpy().astype(np.int64), "col": self.col[:E].cpu().numpy(),
+                "w": self.w[:E].cpu().numpy().astype(np.float64), "t": self.tidx[:E].cpu().numpy().astype(np.int32),
+                "mask": self.mask[:E].cpu().numpy().view(np.uint32)}
+
+
+@dataclass
+class DeviceProblem:
+    """Inputs of one query resident on the GPU."""
+    N: int
+    K: int
+    max_rows: int
+    states: "torch.Tensor"
+    poly_off: "torch.Tensor"
+    A: "torch.Tensor"
+    b: "torch.Tensor"
+    T: np.ndarray
+    start_pos: np.ndarray
+    goal_pos: np.ndarray
+
+
+def to_device(prob, input: str = "f64", device=None) -> DeviceProblem:
+    """Upload a generated problem (numpy arrays) to torch device tensors."""
+    import torch
+    dt = torch.float32 if input == "f32" else torch.float64
+    dev = device or torch.device("cuda")
+    off = np.asarray(prob.poly_off, dtype=np.int32)
+    K = off.shape[0] - 1
+    max_rows = int(np.max(np.diff(off))) if K > 0 else 1
+    st = torch.as_tensor(np.ascontiguousarray(prob.states), dtype=dt).to(dev)
+    return DeviceProblem(
+        N=int(prob.states.shape[0]), K=K, max_rows=max(1, max_rows),
+        states=st.contiguous(),
+        poly_off=torch.as_tensor(off).to(dev),
+        A=torch.as_tensor(np.ascontiguousarray(prob.A), dtype=dt).to(dev).contiguous(),
+        b=torch.as_tensor(np.ascontiguousarray(prob.b), dtype=dt).to(dev).contiguous(),
+        T=np.ascontiguousarray(np.asarray(prob.T, dtype=np.float64)),
+        start_pos=np.asarray(prob.start_pos, dtype=np.float64), goal_pos=np.asarray(prob.goal_pos, dtype=np.float64))
+
+
+class Planner:
+    """One libplan context bound to a CUDA stream."""
+
+    def __init__(self, m: int, gamma: int, degree: int, bounds: Sequence[float], arith: str = "f64",
+                 input: str = "f64", cost_mode: str = "state", tighten: float = 0.0, stream=None):
+        import torch
+        self.lib = load()
+        self.model = _model(m, gamma, degree, bounds, arith, input, cost_mode, tighten)
+        self.arith, self.input = arith, input
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        ctx = ctypes.c_void_p()
+        rc = self.lib.plan_create(ctypes.byref(ctx), ctypes.byref(self.model), ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != 0:
+            raise PlanError(rc, "plan_create")
+        self.ctx = ctx
+        self.last_info: Optional[_Info] = None
+
+    @classmethod
+    def for_problem(cls, prob, arith: str = None, input: str = None, **kw) -> "Planner":
+        mdl = prob.model
+        dt = getattr(prob, "dtype", "f64")
+        return cls(mdl.m, mdl.gamma, mdl.degree, mdl.bounds, arith=arith or dt, input=input or dt,
+                   cost_mode=mdl.cost_mode, tighten=mdl.tighten, **kw)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.plan_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _err(self, rc, what):
+        msg = self.lib.plan_last_error(self.ctx).decode() if self.ctx else ""
+        return PlanError(rc, f"{what}: {msg}")
+
+    def alloc_graph(self, N: int, cap: int) -> Graph:
+        import torch
+        dev = torch.device("cuda")
+        wdt = torch.float64 if self.arith == "f64" else torch.float32
+        cap = max(int(cap), 1)
+        return Graph(N=N, row_off=torch.zeros(N + 1, dtype=torch.int32, device=dev),
+                     col=torch.empty(cap, dtype=torch.int32, device=dev), w=torch.empty(cap, dtype=wdt, device=dev),
+                     tidx=torch.empty(cap, dtype=torch.uint8, device=dev), mask=torch.empty(cap, dtype=torch.int32, device=dev),
+                     count=torch.zeros(1, dtype=torch.int64, device=dev), cap=cap)
+
+    def wait(self) -> int:
+        info = _Info()
+        rc = self.lib.plan_wait(self.ctx, ctypes.byref(info))
+        self.last_info = info
+        return rc
+
+    def info(self) -> dict:
+        i = self.last_info
+        return {f: getattr(i, f) for f, _ in _Info._fields_} if i is not None else {}
+
+    def build_edges_async(self, dp: DeviceProblem, graph: Graph) -> None:
+        T = dp.T
+        rc = self.lib.plan_build_edges(self.ctx, dp.N, ctypes.c_void_p(dp.states.data_ptr()), int(T.shape[0]),
+                                       T.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), dp.K,
+                                       ctypes.c_void_p(dp.poly_off.data_ptr()), dp.max_rows,
+                                       ctypes.c_void_p(dp.A.data_ptr()), ctypes.c_void_p(dp.b.data_ptr()),
+                                       ctypes.byref(graph.cstruct()))
+        if rc != 0:
+            raise self._err(rc, "plan_build_edges")
+
+    def build_edges(self, dp: DeviceProblem, graph: Optional[Graph] = None, cap: Optional[int] = None) -> Graph:
+        """Build the feasible-edge graph, growing scratch/output and repeating on CAPACITY."""
+        if graph is None:
+            graph = self.alloc_graph(dp.N, cap if cap is not None else max(1024, 64 * dp.N))
+        for _ in range(6):
+            self.build_edges_async(dp, graph)
+            st = self.wait()
+            if st == PLAN_OK:
+                return graph
+            if st == PLAN_ERR_CAPACITY:
+                det = self.last_info.detail
+                if det == DET_OUTPUT:
+                    graph = self.alloc_graph(dp.N, int(self.last_info.edges * 1.1) + 1024)
+                continue
+            raise self._err(st, "build_edges")
+        raise self._err(PLAN_ERR_CAPACITY, "build_edges: capacity retries exhausted")
+
+    def search_async(self, dp: DeviceProblem, graph: Graph, start_pos, goal_pos, out: dict) -> None:
+        sp = np.ascontiguousarray(np.asarray(start_pos, dtype=np.float64))
+        gp = np.ascontiguousarray(np.asarray(goal_pos, dtype=np.float64))
+        rc = self.lib.plan_search(self.ctx, dp.N, ctypes.c_void_p(dp.states.data_ptr()), ctypes.byref(graph.cstruct()),
+                                  sp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  gp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  ctypes.c_void_p(out["path"].data_ptr()), int(out["path"].shape[0]),
+                                  ctypes.c_void_p(out["path_len"].data_ptr()), ctypes.c_void_p(out["cost"].data_ptr()))
+        if rc != 0:
+            raise self._err(rc, "plan_search")
+
+    def alloc_search(self, N: int, path_cap: Optional[int] = None) -> dict:
+        import torch
+        dev = torch.device("cuda")
+        return {"path": torch.empty(max(1, path_cap or N), dtype=torch.int32, device=dev),
+                "path_len": torch.zeros(1, dtype=torch.int32, device=dev),
+                "cost": torch.zeros(1, dtype=torch.float64, device=dev)}
+
+    def search(self, dp: DeviceProblem, graph: Graph, start_pos=None, goal_pos=None) -> dict:
+        out = self.alloc_search(dp.N)
+        self.search_async(dp, graph, dp.start_pos if start_pos is None else start_pos,
+                          dp.goal_pos if goal_pos is None else goal_pos, out)
+        st = self.wait()
+        info = self.last_info
+        res = {"status": st, "start": int(info.start), "goal": int(info.goal), "iters": int(info.search_iters)}
+        if st not in (PLAN_OK, PLAN_ERR_NO_PATH):
+            raise self._err(st, "search")
+        L = int(out["path_len"].item())
+        res["path"] = out["path"][:L].cpu().numpy().tolist() if st == PLAN_OK else None
+        res["cost"] = float(out["cost"].item())
+        return res
+
+    def set_search_limits(self, max_sweeps: int = 0, spin_limit: int = 0):
+        rc = self.lib.plan_set_search_limits(self.ctx, int(max_sweeps), int(spin_limit))
+        if rc != 0:
+            raise self._err(rc, "plan_set_search_limits")
+
+    def refine_async(self, P, T, A, b, nrows, weights=(1.0, 1.0, 0.1), grad_loss=None, loss=None, dP=None, dT=None):
+        """Launch the refinement loss (and, with grad_loss, its gradient) on device float tensors."""
+        S = int(P.shape[0])
+        w = _RefineW(*[float(x) for x in weights])
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        rc = self.lib.plan_refine(self.ctx, S, ptr(P), ptr(T), ptr(A), ptr(b), ptr(nrows), int(A.shape[1]),
+                                  ctypes.byref(w), ptr(grad_loss), ptr(loss), ptr(dP), ptr(dT))
+        if rc != 0:
+            raise self._err(rc, "plan_refine")
+
+    def set_accounting(self, on: bool):
+        self.lib.plan_set_accounting(self.ctx, 1 if on else 0)
+
+    def set_timing(self, on: bool):
+        self.lib.plan_set_timing(self.ctx, 1 if on else 0)
+
+    def timing(self, reset: bool = True) -> dict:
+        pm, sm = ctypes.c_double(), ctypes.c_double()
+        pl, sl, tl = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        rc = self.lib.plan_timing(self.ctx, ctypes.byref(pm), ctypes.byref(pl), ctypes.byref(sm), ctypes.byref(sl),
+                                  ctypes.byref(tl), 1 if reset else 0)
+        if rc != 0:
+            raise self._err(rc, "plan_timing")
+        return {"pair_ms": pm.value, "pair_launches": pl.value, "search_ms": sm.value,
+                "search_launches": sl.value, "launches": tl.value}
