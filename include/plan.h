@@ -156,6 +156,42 @@ int plan_build_edges(plan_ctx* ctx, int N, const void* states, int nT, const dou
                      const int32_t* poly_off, int max_rows, const void* A, const void* b,
                      const plan_edges* out);
 
+/* One query of a batched edge build (same fields as plan_build_edges). */
+typedef struct {
+    int N;
+    const void* states;     /* device [N][n] */
+    int nT;
+    const double* T;        /* host [nT]; read by plan_prepare_batched */
+    int K;
+    const int32_t* poly_off; /* device [K+1] */
+    const void* A;          /* device [R][m] */
+    const void* b;          /* device [R] */
+    plan_edges out;         /* caller-owned CSR of this query */
+} plan_query;
+
+/*
+ * Batching form: many independent queries of uneven size in one pass.
+ * plan_prepare_batched does the host work (argument checks, per-query
+ * offsets, coefficient tables for every query's durations, scratch sizing,
+ * descriptor upload; it may allocate and may wait for earlier uploads).
+ * plan_build_edges_batched then launches the whole edge build of every
+ * prepared query -- the pair work of all queries in ONE persistent launch --
+ * without any host synchronisation or allocation, so it can be captured in a
+ * CUDA graph and replayed (the device reads the queries' inputs at replay).
+ * Results, statuses and counters are those of plan_build_edges, summed over
+ * queries in plan_info; each query's edge count lands in its out.count.
+ * Q <= 65535; max_rows bounds the rows of every polytope of every query.
+ */
+int plan_prepare_batched(plan_ctx* ctx, int Q, const plan_query* queries, int max_rows);
+int plan_build_edges_batched(plan_ctx* ctx);
+
+/* Pair-kernel configuration: tile side (8..64, multiple of 4; 0 = 64) and
+ * CTAs per SM (0 = as many as fit).  plan_autotune times every candidate on
+ * the prepared batch (reps launches each, synchronising) and keeps the
+ * fastest; it reports the choice and its mean pair-kernel time. */
+int plan_set_tile(plan_ctx* ctx, int tile, int ctas_per_sm);
+int plan_autotune(plan_ctx* ctx, int reps, int* best_tile, int* best_ctas, double* best_ms);
+
 /*
  * findPath (Alg. 1 line 4, Sec. III-C, Problem 2): the start and goal vertices
  * are the states nearest (Euclidean, positions only; ties to the lowest id) to

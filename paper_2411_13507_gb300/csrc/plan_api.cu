@@ -35,8 +35,26 @@ struct plan_ctx {
     DevInfo* d_info = nullptr;
     DevInfo* h_info = nullptr;
     int last_nT = 0;
+    // batch state (host) and its device copies
+    int bQ = 0, b_max_rows = 1, b_tile = 0;
+    std::vector<QueryDesc> hq;
+    std::vector<long long> pfx;       // 4 x (Q+1): mask, poly, rows, N
+    long long totMask = 0, totPoly = 0, totRows = 0, totN = 0, totList = 0, totK1 = 0;
+    int maxK = 0;
+    std::vector<double> Tall;
+    QueryDesc* d_qd = nullptr;
+    long long* d_pfx = nullptr;
+    long long* d_qSlot = nullptr;
+    long long* d_qItem = nullptr;
+    long long capQ = -1;
+    char* h_stage = nullptr;
+    size_t stage_cap = 0;
+    cudaEvent_t stage_ev = nullptr;
+    bool stage_live = false;
+    std::vector<char> last_stage;
+    int tile = 0, ctas_per_sm = 0;    // pair-kernel configuration (0 = default)
     // host-sized scratch
-    long long capN = -1, capK = -1, capR = -1, capW = -1;
+    long long capN = -1, capK = -1, capR = -1, capW = -1, capL = -1;
     uint32_t* memMask = nullptr;
     int* counts = nullptr;
     int* members = nullptr;
@@ -118,29 +136,30 @@ int check_model(const plan_model* m) {
     return PLAN_OK;
 }
 
-// Build the per-duration device tables (FP64 canonical and FP32 fast) and
-// upload them asynchronously.
-int upload_tables(plan_ctx* c, int nT, const double* T) {
-    bool same = (int)c->Tcache.size() == nT;
-    for (int t = 0; same && t < nT; ++t) same = c->Tcache[t] == T[t];
-    if (same) return PLAN_OK;
+// Build the per-duration device tables (FP64 canonical and FP32 fast) for the
+// concatenated durations of all queries and upload them asynchronously.
+int upload_tables(plan_ctx* c, const std::vector<double>& Tall) {
+    if (Tall == c->Tcache) return PLAN_OK;
     const TabLayout& L = c->L;
     const int g = c->model.gamma, p = c->model.degree, tg = L.tg;
+    const int nT = (int)Tall.size();
+    if (c->tab_ev_live) cudaEventSynchronize(c->tab_ev);  // staging buffers free again
     if (nT > c->tab_nT_cap) {
-        if (c->tab_ev_live) cudaEventSynchronize(c->tab_ev);
         if (c->h_tab64) cudaFreeHost(c->h_tab64);
         if (c->h_tab32) cudaFreeHost(c->h_tab32);
         c->h_tab64 = nullptr;
         c->h_tab32 = nullptr;
-        if (!dalloc(c, &c->d_tab64, (long long)NT_MAX * L.e_stride) || !dalloc(c, &c->d_tab32, (long long)NT_MAX * L.f_stride))
+        c->tab_nT_cap = 0;
+        const int cap = nT < NT_MAX ? NT_MAX : nT;
+        if (!dalloc(c, &c->d_tab64, (long long)cap * L.e_stride) || !dalloc(c, &c->d_tab32, (long long)cap * L.f_stride))
             return PLAN_ERR_NO_MEMORY;
-        if (cudaMallocHost((void**)&c->h_tab64, sizeof(double) * NT_MAX * L.e_stride) != cudaSuccess ||
-            cudaMallocHost((void**)&c->h_tab32, sizeof(float) * NT_MAX * L.f_stride) != cudaSuccess)
+        if (cudaMallocHost((void**)&c->h_tab64, sizeof(double) * (size_t)cap * L.e_stride) != cudaSuccess ||
+            cudaMallocHost((void**)&c->h_tab32, sizeof(float) * (size_t)cap * L.f_stride) != cudaSuccess)
             return fail(c, PLAN_ERR_NO_MEMORY, "cudaMallocHost tables");
-        c->tab_nT_cap = NT_MAX;
+        c->tab_nT_cap = cap;
     }
-    if (c->tab_ev_live) cudaEventSynchronize(c->tab_ev);  // staging buffer free again
-    std::vector<double> D((size_t)(p + 1) * tg), H((size_t)L.rax * tg), C((size_t)g * p * tg);
+    std::vector<double> D((size_t)nT * (p + 1) * tg), H((size_t)nT * L.rax * tg), C((size_t)nT * g * p * tg);
+    exact_tables(g, p, nT, Tall.data(), D.data(), H.data(), C.data());
     std::vector<int> Hk;
     for (int k = 1; k <= g; ++k)
         for (int j = 0; j <= p - k; ++j) Hk.push_back(k);
@@ -155,18 +174,20 @@ int upload_tables(plan_ctx* c, int nT, const double* T) {
         if (p - k > 0) order.push_back(base + p - k);
     }
     for (int t = 0; t < nT; ++t) {
-        exact_tables(g, p, 1, &T[t], D.data(), H.data(), C.data());
+        const double* Dt = D.data() + (size_t)t * (p + 1) * tg;
+        const double* Ht = H.data() + (size_t)t * L.rax * tg;
+        const double* Ct = C.data() + (size_t)t * g * p * tg;
         double* e = c->h_tab64 + (size_t)t * L.e_stride;
         float* f = c->h_tab32 + (size_t)t * L.f_stride;
         memset(f, 0, sizeof(float) * L.f_stride);
-        for (int i = 0; i < L.rax * tg; ++i) e[L.e_H + i] = H[i];
-        for (int i = 0; i < (p + 1) * tg; ++i) e[L.e_D + i] = D[i];
-        for (int i = 0; i < g * p * tg; ++i) e[L.e_C + i] = C[i];
+        for (int i = 0; i < L.rax * tg; ++i) e[L.e_H + i] = Ht[i];
+        for (int i = 0; i < (p + 1) * tg; ++i) e[L.e_D + i] = Dt[i];
+        for (int i = 0; i < g * p * tg; ++i) e[L.e_C + i] = Ct[i];
         for (int rr = 0; rr < L.rax; ++rr) {
             const int r = order[rr];
             const double s = 1.0 / c->lim64[Hk[r] - 1];
             for (int col = 0; col < tg; ++col) {
-                const float v = (float)(H[(size_t)r * tg + col] * s);
+                const float v = (float)(Ht[(size_t)r * tg + col] * s);
                 f[L.f_H + rr * tg + col] = v;
                 float& mx = f[L.f_HC + col];
                 mx = fmaxf(mx, fabsf(v));
@@ -174,12 +195,12 @@ int upload_tables(plan_ctx* c, int nT, const double* T) {
         }
         for (int l = 1; l < p; ++l)
             for (int col = 0; col < tg; ++col) {
-                const float v = (float)D[(size_t)l * tg + col];
+                const float v = (float)Dt[(size_t)l * tg + col];
                 f[L.f_D + (l - 1) * tg + col] = v;
                 float& mx = f[L.f_DC + col];
                 mx = fmaxf(mx, fabsf(v));
             }
-        for (int i = 0; i < g * p * tg; ++i) f[L.f_C + i] = (float)C[i];
+        for (int i = 0; i < g * p * tg; ++i) f[L.f_C + i] = (float)Ct[i];
     }
     cudaError_t e1 = cudaMemcpyAsync(c->d_tab64, c->h_tab64, sizeof(double) * (size_t)nT * L.e_stride,
                                      cudaMemcpyHostToDevice, c->stream);
@@ -188,32 +209,34 @@ int upload_tables(plan_ctx* c, int nT, const double* T) {
     if (e1 != cudaSuccess || e2 != cudaSuccess) return cuda_fail(c, e1 != cudaSuccess ? e1 : e2, "table upload");
     cudaEventRecord(c->tab_ev, c->stream);
     c->tab_ev_live = true;
-    c->Tcache.assign(T, T + nT);
+    c->Tcache = Tall;
     return PLAN_OK;
 }
 
-int ensure_host_sized(plan_ctx* c, long long N, long long K, long long R, long long W) {
-    if (N > c->capN || K > c->capK || W > c->capW) {
-        const long long n2 = N > c->capN ? N : c->capN, k2 = K > c->capK ? K : c->capK;
-        const long long w2 = W > c->capW ? W : c->capW;
-        if (!dalloc(c, &c->memMask, n2 * w2) || !dalloc(c, &c->members, k2 * n2) ||
-            !dalloc(c, &c->localIdx, k2 * n2) || !dalloc(c, &c->rowCount, n2 + 1))
-            return PLAN_ERR_NO_MEMORY;
-        if (K > c->capK) {
-            if (!dalloc(c, &c->counts, k2 + 1) || !dalloc(c, &c->centers, 4 * (k2 + 1)) ||
-                !dalloc(c, &c->resOff, k2 + 1) || !dalloc(c, &c->itemOff, k2 + 1) ||
-                !dalloc(c, &c->ntile, k2 + 1) || !dalloc(c, &c->tsize, k2 + 1))
-                return PLAN_ERR_NO_MEMORY;
-        }
-        c->capN = n2;
-        c->capK = k2;
-        c->capW = w2;
+int ensure_host_sized(plan_ctx* c, long long mask, long long list, long long k1, long long rows, long long nrow) {
+    if (mask > c->capW) {
+        if (!dalloc(c, &c->memMask, mask)) return PLAN_ERR_NO_MEMORY;
+        c->capW = mask;
     }
-    if (R > c->capR) {
-        if (!dalloc(c, &c->blim64, R) || !dalloc(c, &c->A32, 4 * R) || !dalloc(c, &c->blim32, R) ||
-            !dalloc(c, &c->bc32, R))
+    if (list > c->capL) {
+        if (!dalloc(c, &c->members, list) || !dalloc(c, &c->localIdx, list)) return PLAN_ERR_NO_MEMORY;
+        c->capL = list;
+    }
+    if (k1 > c->capK) {
+        if (!dalloc(c, &c->counts, k1) || !dalloc(c, &c->centers, 4 * k1) || !dalloc(c, &c->resOff, k1) ||
+            !dalloc(c, &c->itemOff, k1) || !dalloc(c, &c->ntile, k1) || !dalloc(c, &c->tsize, k1))
             return PLAN_ERR_NO_MEMORY;
-        c->capR = R;
+        c->capK = k1;
+    }
+    if (rows > c->capR) {
+        if (!dalloc(c, &c->blim64, rows) || !dalloc(c, &c->A32, 4 * rows) || !dalloc(c, &c->blim32, rows) ||
+            !dalloc(c, &c->bc32, rows))
+            return PLAN_ERR_NO_MEMORY;
+        c->capR = rows;
+    }
+    if (nrow > c->capN) {
+        if (!dalloc(c, &c->rowCount, nrow)) return PLAN_ERR_NO_MEMORY;
+        c->capN = nrow;
     }
     return PLAN_OK;
 }
@@ -299,6 +322,7 @@ int plan_create(plan_ctx** out, const plan_model* model, void* cuda_stream) {
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_info, sizeof(DevInfo));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_info, sizeof(DevInfo));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->tab_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();
         plan_destroy(c);
@@ -314,12 +338,15 @@ void plan_destroy(plan_ctx* c) {
     if (c->stream || c->d_info) cudaStreamSynchronize(c->stream);
     void* dev[] = {c->d_tab64, c->d_tab32, c->d_info, c->memMask, c->counts, c->members, c->localIdx, c->centers,
                    c->blim64, c->A32, c->blim32, c->bc32, c->resOff, c->itemOff, c->ntile, c->tsize, c->rowCount,
-                   c->resBits, c->resKey, c->emitPre, c->recheck, c->sdist, c->sbest, c->spred, c->sfront};
+                   c->resBits, c->resKey, c->emitPre, c->recheck, c->sdist, c->sbest, c->spred, c->sfront,
+                   c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_tab64) cudaFreeHost(c->h_tab64);
     if (c->h_tab32) cudaFreeHost(c->h_tab32);
     if (c->h_info) cudaFreeHost(c->h_info);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->stage_ev) cudaEventDestroy(c->stage_ev);
     if (c->tab_ev) cudaEventDestroy(c->tab_ev);
     for (auto& pr : c->ev_pair) {
         cudaEventDestroy(pr.first);
@@ -333,57 +360,176 @@ void plan_destroy(plan_ctx* c) {
     delete c;
 }
 
-int plan_build_edges(plan_ctx* c, int N, const void* states, int nT, const double* T, int K,
-                     const int32_t* poly_off, int max_rows, const void* A, const void* b, const plan_edges* out) {
-    if (!c) return PLAN_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+int check_query(plan_ctx* c, const plan_query& q) {
+    if (q.N < 0 || q.N > (1 << 20)) return fail(c, PLAN_ERR_INVALID_ARG, "N out of range");
+    if (q.nT < 1 || q.nT > NT_MAX || !q.T) return fail(c, PLAN_ERR_INVALID_ARG, "nT must be 1..32 with a host T array");
+    for (int t = 0; t < q.nT; ++t)
+        if (!std::isfinite(q.T[t]) || !(q.T[t] > 0)) return fail(c, PLAN_ERR_INVALID_ARG, "durations must be finite and > 0");
+    if (q.K < 0 || q.K > 1024) return fail(c, PLAN_ERR_INVALID_ARG, "K must be 0..1024");
+    if ((q.N > 0 && !q.states) || (q.K > 0 && (!q.poly_off || !q.A || !q.b)))
+        return fail(c, PLAN_ERR_INVALID_ARG, "null input array");
+    const plan_edges& o = q.out;
+    if (!o.row_off || !o.count || o.cap < 0 || (o.cap > 0 && (!o.col || !o.w || !o.tidx || !o.mask)))
+        return fail(c, PLAN_ERR_INVALID_ARG, "bad output CSR");
+    if ((long long)q.K * q.N > (1LL << 31)) return fail(c, PLAN_ERR_INVALID_ARG, "K*N too large");
+    return PLAN_OK;
+}
+
+// Host work of a batch: validation, offsets, tables, scratch, descriptor upload.
+int prepare(plan_ctx* c, int Q, const plan_query* qs, int max_rows) {
     if (!model_supported(c->model.m, c->model.gamma, c->model.degree))
         return fail(c, PLAN_ERR_UNSUPPORTED, "edge build not compiled for this (m, gamma, p)");
-    if (N < 0 || N > (1 << 20)) return fail(c, PLAN_ERR_INVALID_ARG, "N out of range");
-    if (nT < 1 || nT > NT_MAX || !T) return fail(c, PLAN_ERR_INVALID_ARG, "nT must be 1..32 with a host T array");
-    for (int t = 0; t < nT; ++t)
-        if (!std::isfinite(T[t]) || !(T[t] > 0)) return fail(c, PLAN_ERR_INVALID_ARG, "durations must be finite and > 0");
-    if (K < 0 || K > 1024) return fail(c, PLAN_ERR_INVALID_ARG, "K must be 0..1024");
-    if (K > 0 && (max_rows < 1 || max_rows > RMAX)) return fail(c, PLAN_ERR_INVALID_ARG, "max_rows must be 1..16");
-    if ((N > 0 && !states) || (K > 0 && (!poly_off || !A || !b)))
-        return fail(c, PLAN_ERR_INVALID_ARG, "null input array");
-    if (!out || !out->row_off || !out->count || out->cap < 0 ||
-        (out->cap > 0 && (!out->col || !out->w || !out->tidx || !out->mask)))
-        return fail(c, PLAN_ERR_INVALID_ARG, "bad output CSR");
-    if ((long long)K * N > (1LL << 31)) return fail(c, PLAN_ERR_INVALID_ARG, "K*N too large");
-    int rc = upload_tables(c, nT, T);
+    if (Q < 1 || Q > 65535 || !qs) return fail(c, PLAN_ERR_INVALID_ARG, "need 1..65535 queries");
+    int anyK = 0;
+    for (int q = 0; q < Q; ++q) {
+        int rc = check_query(c, qs[q]);
+        if (rc != PLAN_OK) return rc;
+        anyK |= qs[q].K > 0;
+    }
+    if (anyK && (max_rows < 1 || max_rows > RMAX)) return fail(c, PLAN_ERR_INVALID_ARG, "max_rows must be 1..16");
+    if (!anyK) max_rows = 1;
+    std::vector<QueryDesc> hq(Q);
+    std::vector<long long> pfx(4 * (size_t)(Q + 1), 0);
+    std::vector<double> Tall;
+    long long mask = 0, poly = 0, rows = 0, nrow = 0, list = 0, k1 = 0;
+    int maxK = 0;
+    for (int q = 0; q < Q; ++q) {
+        const plan_query& in = qs[q];
+        QueryDesc& d = hq[q];
+        memset(&d, 0, sizeof(d));
+        d.N = in.N;
+        d.K = in.K;
+        d.nT = in.nT;
+        d.W = in.K > 0 ? (in.K + 31) / 32 : 1;
+        d.tabOff = (int)Tall.size();
+        d.kOff = (int)k1;
+        d.maskOff = mask;
+        d.listOff = list;
+        d.rowsOff = rows;
+        d.rowOff = nrow;
+        d.states = in.states;
+        d.poly_off = in.poly_off;
+        d.A = in.A;
+        d.b = in.b;
+        d.row_off = in.out.row_off;
+        d.col = in.out.col;
+        d.w = in.out.w;
+        d.tidx = in.out.tidx;
+        d.mask = in.out.mask;
+        d.cap = in.out.cap;
+        d.count = in.out.count;
+        Tall.insert(Tall.end(), in.T, in.T + in.nT);
+        pfx[0 * (Q + 1) + q] = mask;
+        pfx[1 * (Q + 1) + q] = poly;
+        pfx[2 * (Q + 1) + q] = rows;
+        pfx[3 * (Q + 1) + q] = nrow;
+        mask += (long long)in.N * d.W;
+        poly += in.K;
+        rows += (long long)in.K * max_rows;
+        nrow += in.N;
+        list += (long long)in.K * in.N;
+        k1 += in.K + 1;
+        if (in.K > maxK) maxK = in.K;
+    }
+    pfx[0 * (Q + 1) + Q] = mask;
+    pfx[1 * (Q + 1) + Q] = poly;
+    pfx[2 * (Q + 1) + Q] = rows;
+    pfx[3 * (Q + 1) + Q] = nrow;
+    if (Tall.size() > (size_t)(1 << 20)) return fail(c, PLAN_ERR_INVALID_ARG, "too many durations in the batch");
+    int rc = upload_tables(c, Tall);
     if (rc != PLAN_OK) return rc;
-    const long long W = K > 0 ? (K + 31) / 32 : 1;
-    const long long R = (long long)(K > 0 ? K : 1) * (max_rows > 0 ? max_rows : 1);
-    rc = ensure_host_sized(c, N, K, R, W);
+    rc = ensure_host_sized(c, mask, list, k1, rows, nrow);
     if (rc != PLAN_OK) return rc;
+    if (Q > c->capQ) {
+        if (c->stage_live) cudaEventSynchronize(c->stage_ev);
+        if (!dalloc(c, &c->d_qd, Q) || !dalloc(c, &c->d_pfx, 4LL * (Q + 1)) || !dalloc(c, &c->d_qSlot, Q + 1) ||
+            !dalloc(c, &c->d_qItem, Q + 1))
+            return PLAN_ERR_NO_MEMORY;
+        c->capQ = Q;
+        c->last_stage.clear();
+    }
     long long want_s = c->want_slots, want_r = c->want_rechecks;
-    if (want_s == 0) want_s = (long long)3 * N * (long long)N / (K > 0 ? K : 1) + 4096;
-    if (want_r == 0) want_r = (1 << 16);
+    if (want_s == 0) {
+        for (int q = 0; q < Q; ++q)
+            want_s += 3LL * qs[q].N * (long long)qs[q].N / (qs[q].K > 0 ? qs[q].K : 1) + 1024;
+    }
+    if (want_r == 0) want_r = 1 << 16;
     rc = ensure_device_sized(c, want_s, want_r);
     if (rc != PLAN_OK) return rc;
+    // descriptors + prefixes, uploaded only when they changed
+    const size_t bytes = sizeof(QueryDesc) * Q + sizeof(long long) * pfx.size();
+    std::vector<char> blob(bytes);
+    memcpy(blob.data(), hq.data(), sizeof(QueryDesc) * Q);
+    memcpy(blob.data() + sizeof(QueryDesc) * Q, pfx.data(), sizeof(long long) * pfx.size());
+    if (blob != c->last_stage) {
+        if (c->stage_live) cudaEventSynchronize(c->stage_ev);
+        if (bytes > c->stage_cap) {
+            if (c->h_stage) cudaFreeHost(c->h_stage);
+            c->h_stage = nullptr;
+            c->stage_cap = 0;
+            if (cudaMallocHost((void**)&c->h_stage, bytes) != cudaSuccess) return fail(c, PLAN_ERR_NO_MEMORY, "stage");
+            c->stage_cap = bytes;
+        }
+        memcpy(c->h_stage, blob.data(), bytes);
+        cudaError_t e1 = cudaMemcpyAsync(c->d_qd, c->h_stage, sizeof(QueryDesc) * Q, cudaMemcpyHostToDevice, c->stream);
+        cudaError_t e2 = cudaMemcpyAsync(c->d_pfx, c->h_stage + sizeof(QueryDesc) * Q, sizeof(long long) * pfx.size(),
+                                         cudaMemcpyHostToDevice, c->stream);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) return cuda_fail(c, e1 != cudaSuccess ? e1 : e2, "descriptor upload");
+        cudaEventRecord(c->stage_ev, c->stream);
+        c->stage_live = true;
+        c->last_stage.swap(blob);
+    }
+    c->bQ = Q;
+    c->b_max_rows = max_rows;
+    c->hq.swap(hq);
+    c->pfx.swap(pfx);
+    c->totMask = mask;
+    c->totPoly = poly;
+    c->totRows = rows;
+    c->totN = nrow;
+    c->totList = list;
+    c->totK1 = k1;
+    c->maxK = maxK;
+    c->last_nT = Q == 1 ? qs[0].nT : 0;
+    return PLAN_OK;
+}
+
+int default_tile(const plan_ctx* c) { return c->model.arith == PLAN_F64 ? TILE64 : TILE; }
+
+// Launch the prepared batch (no host synchronisation, no allocation).
+int issue(plan_ctx* c) {
+    if (c->bQ < 1) return fail(c, PLAN_ERR_INVALID_ARG, "no prepared batch");
     cudaError_t e = cudaMemsetAsync(c->d_info, 0, sizeof(DevInfo), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset info");
-    c->last_nT = nT;
-
+    const int Q = c->bQ;
     BuildParams P;
     memset(&P, 0, sizeof(P));
-    P.N = N;
-    P.K = K;
-    P.nT = nT;
-    P.W = (int)W;
-    P.R = (int)R;
+    P.Q = Q;
+    P.maxK = c->maxK;
     P.m = c->model.m;
     P.g = c->model.gamma;
     P.p = c->model.degree;
     P.cost_mode = c->model.cost_mode;
     P.in_f32 = c->model.input == PLAN_IN_F32;
     P.arith = c->model.arith;
-    P.max_rows = K > 0 ? max_rows : 1;
+    P.max_rows = c->b_max_rows;
+    P.tile = (c->model.arith == PLAN_F64) ? TILE64 : (c->tile > 0 ? c->tile : TILE);
     P.eps = c->model.tighten;
-    P.states = states;
-    P.poly_off = poly_off;
-    P.A = A;
-    P.b = b;
+    P.qd = c->d_qd;
+    P.pfxMask = c->d_pfx;
+    P.pfxPoly = c->d_pfx + (Q + 1);
+    P.pfxRows = c->d_pfx + 2 * (Q + 1);
+    P.pfxN = c->d_pfx + 3 * (Q + 1);
+    P.qSlot = c->d_qSlot;
+    P.qItem = c->d_qItem;
+    P.totMask = c->totMask;
+    P.totPoly = c->totPoly;
+    P.totRows = c->totRows;
+    P.totN = c->totN;
     P.tab32 = c->d_tab32;
     P.tab64 = c->d_tab64;
     for (int k = 0; k < 4; ++k) P.lim64[k] = c->lim64[k];
@@ -409,14 +555,6 @@ int plan_build_edges(plan_ctx* c, int N, const void* states, int nT, const doubl
     P.slotCap = c->slotCap;
     P.recheckCap = c->recheckCap;
     P.info = c->d_info;
-    P.row_off = out->row_off;
-    P.col = out->col;
-    P.w = out->w;
-    P.tidx = out->tidx;
-    P.mask = out->mask;
-    P.cap = out->cap;
-    P.count = out->count;
-
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->timing) {
         e0 = take_event(c);
@@ -424,13 +562,108 @@ int plan_build_edges(plan_ctx* c, int N, const void* states, int nT, const doubl
         c->ev_pair.emplace_back(e0, e1);
     }
     int launches = 0;
-    int ce = launch_build(P, c->stream, c->num_sms, e0, e1, &launches);
+    int ce = launch_build(P, c->stream, c->num_sms, c->ctas_per_sm, e0, e1, &launches);
     c->launches += launches;
     if (ce != 0) return cuda_fail(c, (cudaError_t)ce, "build launch");
-    if (c->accounting && N > 0 && K > 0) {
+    if (c->accounting && c->totN > 0 && c->totPoly > 0) {
         ce = launch_account(P, c->stream, c->num_sms, c->d_info->work);
         if (ce != 0) return cuda_fail(c, (cudaError_t)ce, "accounting launch");
     }
+    return PLAN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int plan_build_edges(plan_ctx* c, int N, const void* states, int nT, const double* T, int K,
+                     const int32_t* poly_off, int max_rows, const void* A, const void* b, const plan_edges* out) {
+    if (!c) return PLAN_ERR_INVALID_ARG;
+    if (!out) return fail(c, PLAN_ERR_INVALID_ARG, "bad output CSR");
+    plan_query q;
+    q.N = N;
+    q.states = states;
+    q.nT = nT;
+    q.T = T;
+    q.K = K;
+    q.poly_off = poly_off;
+    q.A = A;
+    q.b = b;
+    q.out = *out;
+    int rc = prepare(c, 1, &q, max_rows);
+    if (rc != PLAN_OK) return rc;
+    return issue(c);
+}
+
+int plan_prepare_batched(plan_ctx* c, int Q, const plan_query* queries, int max_rows) {
+    if (!c) return PLAN_ERR_INVALID_ARG;
+    return prepare(c, Q, queries, max_rows);
+}
+
+int plan_build_edges_batched(plan_ctx* c) {
+    if (!c) return PLAN_ERR_INVALID_ARG;
+    return issue(c);
+}
+
+int plan_set_tile(plan_ctx* c, int tile, int ctas_per_sm) {
+    if (!c || tile < 0 || ctas_per_sm < 0 || ctas_per_sm > 8) return PLAN_ERR_INVALID_ARG;
+    if (tile != 0 && (tile < 8 || tile > TILE || (tile & 3))) return fail(c, PLAN_ERR_INVALID_ARG, "tile must be 8..64, multiple of 4");
+    c->tile = tile;
+    c->ctas_per_sm = ctas_per_sm;
+    return PLAN_OK;
+}
+
+int plan_autotune(plan_ctx* c, int reps, int* best_tile, int* best_ctas, double* best_ms) {
+    if (!c || reps < 1) return PLAN_ERR_INVALID_ARG;
+    if (c->bQ < 1) return fail(c, PLAN_ERR_INVALID_ARG, "prepare a batch first");
+    if (c->model.arith == PLAN_F64) {
+        if (best_tile) *best_tile = TILE64;
+        if (best_ctas) *best_ctas = 0;
+        return PLAN_OK;
+    }
+    const bool was_timing = c->timing;
+    const int tiles[] = {32, 40, 48, 56, 64};
+    const int ctas[] = {0, 1, 2, 3, 4};
+    double best = 1e30;
+    int bt = TILE, bc = 0;
+    for (int cc : ctas)
+        for (int t : tiles) {
+            c->tile = t;
+            c->ctas_per_sm = cc;
+            // one untimed run sizes the scratch for this configuration
+            for (int tries = 0; tries < 4; ++tries) {
+                int rc = issue(c);
+                if (rc != PLAN_OK) return rc;
+                plan_info info;
+                rc = plan_wait(c, &info);
+                if (rc == PLAN_OK) break;
+                if (rc != PLAN_ERR_CAPACITY || info.detail == DET_OUTPUT) {
+                    c->timing = was_timing;
+                    return rc;
+                }
+            }
+            c->timing = true;
+            double pm = 0;
+            int64_t pl = 0;
+            plan_timing(c, nullptr, nullptr, nullptr, nullptr, nullptr, 1);
+            for (int r = 0; r < reps; ++r) {
+                int rc = issue(c);
+                if (rc != PLAN_OK) return rc;
+            }
+            plan_timing(c, &pm, &pl, nullptr, nullptr, nullptr, 1);
+            c->timing = was_timing;
+            const double ms = pl ? pm / pl : 1e30;
+            if (ms < best) {
+                best = ms;
+                bt = t;
+                bc = cc;
+            }
+        }
+    c->tile = bt;
+    c->ctas_per_sm = bc;
+    if (best_tile) *best_tile = bt;
+    if (best_ctas) *best_ctas = bc;
+    if (best_ms) *best_ms = best;
     return PLAN_OK;
 }
 
@@ -544,6 +777,9 @@ int plan_wait(plan_ctx* c, plan_info* info) {
     if (e != cudaSuccess) return cuda_fail(c, e, "stream sync");
     e = cudaMemcpy(c->h_info, c->d_info, sizeof(DevInfo), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "read status");
+    // the status covers the work issued since the previous plan_wait: clear it
+    e = cudaMemset(c->d_info, 0, 2 * sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(c, e, "clear status");
     const DevInfo& d = *c->h_info;
     if (d.status == PLAN_ERR_CAPACITY) {
         if (d.detail == DET_SLOTS) c->want_slots = (long long)(d.need_slots + d.need_slots / 4 + 1024);

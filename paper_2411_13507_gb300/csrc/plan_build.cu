@@ -70,25 +70,40 @@ struct Shape {
     static constexpr int TG = 2 * G;
 };
 
+// Largest q with pfx[q] <= x (pfx ascending, pfx[Q] > x): query of a global index.
+DEVI int find_q(const long long* pfx, int Q, long long x) {
+    int lo = 0, hi = Q;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pfx[mid] <= x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // ---------------------------------------------------------------------------
 // Rows of every polytope: FP32 copies, b - eps, row-count checks.
 // ---------------------------------------------------------------------------
 __global__ void k_prep(BuildParams P) {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= (long long)P.K * P.max_rows) return;
-    int k = (int)(t / P.max_rows), rr = (int)(t % P.max_rows);
-    int r0 = P.poly_off[k], r1 = P.poly_off[k + 1];
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= P.totRows) return;
+    const int q = find_q(P.pfxRows, P.Q, t);
+    const QueryDesc& Q = P.qd[q];
+    const long long loc = t - P.pfxRows[q];
+    const int k = (int)(loc / P.max_rows), rr = (int)(loc % P.max_rows);
+    const int r0 = Q.poly_off[k], r1 = Q.poly_off[k + 1];
     if (rr == 0) {
-        int nr = r1 - r0;
+        const int nr = r1 - r0;
         if (nr < 0 || nr > P.max_rows || (k == 0 && r0 != 0)) set_status(P.info, PLAN_ERR_UNSUPPORTED, DET_ROWS);
         atomicMax(&P.info->max_rows_seen, nr);
     }
-    int r = r0 + rr;
-    if (r >= r1 || r >= P.R || r < 0) return;
-    double bl = __dsub_rn(ldv(P.b, r, P.in_f32), P.eps);
-    P.blim64[r] = bl;
-    P.blim32[r] = (float)bl;
-    for (int a = 0; a < P.m; ++a) P.A32[(long long)r * P.m + a] = ldf(P.A, (long long)r * P.m + a, P.in_f32);
+    const int r = r0 + rr;
+    if (r >= r1 || r < 0 || r >= Q.K * P.max_rows) return;
+    const long long rg = Q.rowsOff + r;
+    const double bl = __dsub_rn(ldv(Q.b, r, P.in_f32), P.eps);
+    P.blim64[rg] = bl;
+    P.blim32[rg] = (float)bl;
+    for (int a = 0; a < P.m; ++a) P.A32[rg * P.m + a] = ldf(Q.A, (long long)r * P.m + a, P.in_f32);
 }
 
 // ---------------------------------------------------------------------------
@@ -96,31 +111,35 @@ __global__ void k_prep(BuildParams P) {
 // row (canonical FP64 decision; FP32 first, FP64 only inside the band).
 // ---------------------------------------------------------------------------
 __global__ void k_member(BuildParams P) {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= (long long)P.N * P.W || has_failed(P.info)) return;
-    const int i = (int)(t / P.W), w = (int)(t % P.W);
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= P.totMask || has_failed(P.info)) return;
+    const int q = find_q(P.pfxMask, P.Q, t);
+    const QueryDesc& Q = P.qd[q];
+    const long long loc = t - P.pfxMask[q];
+    const int i = (int)(loc / Q.W), w = (int)(loc % Q.W);
     const int m = P.m, n = P.m * P.g;
     double x64[4];
     float x32[4];
     for (int a = 0; a < m; ++a) {
-        x64[a] = ldv(P.states, (long long)i * n + a, P.in_f32);
+        x64[a] = ldv(Q.states, (long long)i * n + a, P.in_f32);
         x32[a] = (float)x64[a];
     }
     uint32_t word = 0;
-    const int kend = min(32, P.K - w * 32);
+    const int kend = min(32, Q.K - w * 32);
     for (int kk = 0; kk < kend; ++kk) {
         const int k = w * 32 + kk;
-        const int r0 = P.poly_off[k], r1 = P.poly_off[k + 1];
-        if (r1 - r0 > P.max_rows || r1 > P.R) continue;
+        const int r0 = Q.poly_off[k], r1 = Q.poly_off[k + 1];
+        if (r1 - r0 > P.max_rows || r1 > Q.K * P.max_rows || r0 < 0) continue;
         bool in = true;
         for (int r = r0; r < r1 && in; ++r) {
+            const long long rg = Q.rowsOff + r;
             float s = 0.f, mag = 0.f;
             for (int a = 0; a < m; ++a) {
-                float av = P.A32[(long long)r * m + a];
+                const float av = P.A32[rg * m + a];
                 s = fmaf(av, x32[a], s);
                 mag = fmaf(fabsf(av), fabsf(x32[a]), mag);
             }
-            const float lim = P.blim32[r];
+            const float lim = P.blim32[rg];
             const float d = s - lim;
             const float band = KMEM * (mag + fabsf(lim));
             if (!(d < -band)) {
@@ -129,14 +148,14 @@ __global__ void k_member(BuildParams P) {
                 } else {  // within the band (or NaN): canonical FP64 row
                     double sd = 0.0;
                     for (int a = 0; a < m; ++a)
-                        sd = __dadd_rn(sd, __dmul_rn(ldv(P.A, (long long)r * m + a, P.in_f32), x64[a]));
-                    if (!(sd <= P.blim64[r])) in = false;
+                        sd = __dadd_rn(sd, __dmul_rn(ldv(Q.A, (long long)r * m + a, P.in_f32), x64[a]));
+                    if (!(sd <= P.blim64[rg])) in = false;
                 }
             }
         }
         if (in) word |= 1u << kk;
     }
-    P.memMask[(long long)i * P.W + w] = word;
+    P.memMask[Q.maskOff + (long long)i * Q.W + w] = word;
 }
 
 // ---------------------------------------------------------------------------
@@ -144,7 +163,9 @@ __global__ void k_member(BuildParams P) {
 // block centre (first member's position) and centred FP32 bounds.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_lists(BuildParams P) {
-    const int k = blockIdx.x;
+    const int q = find_q(P.pfxPoly, P.Q, blockIdx.x);
+    const QueryDesc& Q = P.qd[q];
+    const int k = (int)(blockIdx.x - P.pfxPoly[q]);
     __shared__ int warpTot[32];
     __shared__ int s_base;
     __shared__ float s_c[4];
@@ -153,9 +174,11 @@ __global__ void __launch_bounds__(1024) k_lists(BuildParams P) {
     __syncthreads();
     const int w = k >> 5;
     const uint32_t bit = 1u << (k & 31);
-    for (int i0 = 0; i0 < P.N; i0 += blockDim.x) {
+    int* members = P.members + Q.listOff + (long long)k * Q.N;
+    int* localIdx = P.localIdx + Q.listOff + (long long)k * Q.N;
+    for (int i0 = 0; i0 < Q.N; i0 += blockDim.x) {
         const int i = i0 + threadIdx.x;
-        const bool mem = i < P.N && (P.memMask[(long long)i * P.W + w] & bit);
+        const bool mem = i < Q.N && (P.memMask[Q.maskOff + (long long)i * Q.W + w] & bit);
         const unsigned bal = __ballot_sync(0xffffffffu, mem);
         const int pre = __popc(bal & ((1u << lane) - 1u));
         if (lane == 0) warpTot[wid] = __popc(bal);
@@ -172,8 +195,8 @@ __global__ void __launch_bounds__(1024) k_lists(BuildParams P) {
         __syncthreads();
         if (mem) {
             const int pos = s_base + warpTot[wid] + pre;
-            P.members[(long long)k * P.N + pos] = i;
-            P.localIdx[(long long)k * P.N + i] = pos;
+            members[pos] = i;
+            localIdx[i] = pos;
         }
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) s_base += warpTot[wid] + pre + (mem ? 1 : 0);
@@ -181,21 +204,21 @@ __global__ void __launch_bounds__(1024) k_lists(BuildParams P) {
     }
     const int nk = s_base;
     if (threadIdx.x == 0) {
-        P.counts[k] = nk;
+        P.counts[Q.kOff + k] = nk;
         const int n = P.m * P.g;
         for (int a = 0; a < 4; ++a) {
             float c = 0.f;
-            if (nk > 0 && a < P.m) c = ldf(P.states, (long long)P.members[(long long)k * P.N] * n + a, P.in_f32);
+            if (nk > 0 && a < P.m) c = ldf(Q.states, (long long)members[0] * n + a, P.in_f32);
             s_c[a] = c;
-            P.centers[k * 4 + a] = c;
+            P.centers[(long long)(Q.kOff + k) * 4 + a] = c;
         }
     }
     __syncthreads();
-    const int r0 = P.poly_off[k], r1 = P.poly_off[k + 1];
-    for (int r = r0 + threadIdx.x; r < r1 && r < P.R; r += blockDim.x) {
-        double s = 0.0;
-        for (int a = 0; a < P.m; ++a) s += ldv(P.A, (long long)r * P.m + a, P.in_f32) * (double)s_c[a];
-        P.bc32[r] = (float)(P.blim64[r] - s);
+    const int r0 = Q.poly_off[k], r1 = Q.poly_off[k + 1];
+    for (int r = r0 + threadIdx.x; r < r1 && r < Q.K * P.max_rows; r += blockDim.x) {
+        double sacc = 0.0;
+        for (int a = 0; a < P.m; ++a) sacc += ldv(Q.A, (long long)r * P.m + a, P.in_f32) * (double)s_c[a];
+        P.bc32[Q.rowsOff + r] = (float)(P.blim64[Q.rowsOff + r] - sacc);
     }
 }
 
@@ -229,61 +252,115 @@ DEVI T block_exclusive_scan(T v, T* warpbuf, T* total) {
     return r;
 }
 
-__global__ void __launch_bounds__(1024) k_setup(BuildParams P, int tile) {
+// One CTA per query: balanced tiles and slot offsets of its polytopes.
+__global__ void __launch_bounds__(1024) k_setup(BuildParams P) {
     __shared__ long long wb[32];
     __shared__ long long tot;
-    const int k = threadIdx.x;
-    long long nk = (k < P.K) ? P.counts[k] : 0;
-    if (nk > NK_MAX) set_status(P.info, PLAN_ERR_UNSUPPORTED, DET_NK);
-    const int nt = nk > 0 ? (int)((nk + tile - 1) / tile) : 0;
-    const int ts = nt ? (int)((nk + nt - 1) / nt) : 0;
-    long long so = block_exclusive_scan<long long>(nk * nk, wb, &tot);
-    const long long slots = tot;
-    long long io = block_exclusive_scan<long long>((long long)nt * nt, wb, &tot);
-    const long long items = tot;
-    block_exclusive_scan<long long>(nk, wb, &tot);
-    const long long mem = tot;
-    if (k < P.K) {
-        P.resOff[k] = so;
-        P.itemOff[k] = (int)io;
-        P.ntile[k] = nt;
-        P.tsize[k] = ts;
+    const int q = blockIdx.x;
+    const QueryDesc& Q = P.qd[q];
+    const int tile = P.tile;
+    long long slots = 0, items = 0, mem = 0;
+    long long carry_s = 0, carry_i = 0, carry_m = 0;
+    for (int k0 = 0; k0 < Q.K; k0 += blockDim.x) {
+        const int k = k0 + threadIdx.x;
+        const long long nk = (k < Q.K) ? P.counts[Q.kOff + k] : 0;
+        if (nk > NK_MAX) set_status(P.info, PLAN_ERR_UNSUPPORTED, DET_NK);
+        const int nt = nk > 0 ? (int)((nk + tile - 1) / tile) : 0;
+        const int ts = nt ? (int)((nk + nt - 1) / nt) : 0;
+        const long long so = block_exclusive_scan<long long>(nk * nk, wb, &tot);
+        slots = tot;
+        const long long io = block_exclusive_scan<long long>((long long)nt * nt, wb, &tot);
+        items = tot;
+        block_exclusive_scan<long long>(nk, wb, &tot);
+        mem = tot;
+        if (k < Q.K) {
+            P.resOff[Q.kOff + k] = carry_s + so;
+            P.itemOff[Q.kOff + k] = (int)(carry_i + io);
+            P.ntile[Q.kOff + k] = nt;
+            P.tsize[Q.kOff + k] = ts;
+        }
+        carry_s += slots;
+        carry_i += items;
+        carry_m += mem;
     }
-    if (k == 0) {
-        P.resOff[P.K] = slots;
-        P.itemOff[P.K] = (int)items;
-        P.info->slots = slots;
-        P.info->items = items;
-        P.info->memberships = mem;
-        if (slots > P.slotCap) {
-            P.info->need_slots = slots;
+    if (threadIdx.x == 0) {
+        P.resOff[Q.kOff + Q.K] = carry_s;
+        P.itemOff[Q.kOff + Q.K] = (int)carry_i;
+        P.qSlot[q + 1] = carry_s;   // per-query totals; k_batch turns them into prefixes
+        P.qItem[q + 1] = carry_i;
+        atomicAdd(&P.info->memberships, (unsigned long long)carry_m);
+    }
+}
+
+// Prefix sums of the per-query slot and tile totals; scratch capacity check.
+__global__ void __launch_bounds__(1024) k_batch(BuildParams P) {
+    __shared__ long long wb[32];
+    __shared__ long long tot;
+    long long cs = 0, ci = 0;
+    for (int q0 = 0; q0 < P.Q; q0 += blockDim.x) {
+        const int q = q0 + threadIdx.x;
+        const long long vs = q < P.Q ? P.qSlot[q + 1] : 0;
+        const long long vi = q < P.Q ? P.qItem[q + 1] : 0;
+        __syncthreads();
+        const long long es = block_exclusive_scan<long long>(vs, wb, &tot);
+        const long long ts = tot;
+        const long long ei = block_exclusive_scan<long long>(vi, wb, &tot);
+        const long long ti = tot;
+        if (q < P.Q) {
+            P.qSlot[q + 1] = cs + es + vs;
+            P.qItem[q + 1] = ci + ei + vi;
+        }
+        cs += ts;
+        ci += ti;
+    }
+    if (threadIdx.x == 0) {
+        P.qSlot[0] = 0;
+        P.qItem[0] = 0;
+        P.info->slots = cs;
+        P.info->items = ci;
+        if (cs > P.slotCap) {
+            P.info->need_slots = cs;
             set_status(P.info, PLAN_ERR_CAPACITY, DET_SLOTS);
         }
+        if (ci > 0x7fffffffLL) set_status(P.info, PLAN_ERR_UNSUPPORTED, DET_NK);
     }
 }
 
-DEVI void item_decode(const BuildParams& P, int item, int& k, int& i0, int& j0, int& TI, int& TJ, int& nk) {
-    int lo = 0, hi = P.K;
+struct Item {
+    int q, k, i0, j0, TI, TJ, nk;
+    long long base;   // slot of member pair (0, 0) of polytope k
+};
+
+DEVI Item item_decode(const BuildParams& P, long long item) {
+    Item it;
+    it.q = find_q(P.qItem, P.Q, item);
+    const QueryDesc& Q = P.qd[it.q];
+    const int local = (int)(item - P.qItem[it.q]);
+    const int* io = P.itemOff + Q.kOff;
+    int lo = 0, hi = Q.K;
     while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (P.itemOff[mid] <= item) lo = mid;
+        const int mid = (lo + hi) >> 1;
+        if (io[mid] <= local) lo = mid;
         else hi = mid;
     }
-    k = lo;
-    const int loc = item - P.itemOff[k], nt = P.ntile[k], ts = P.tsize[k];
-    nk = P.counts[k];
+    it.k = lo;
+    const int loc = local - io[lo], nt = P.ntile[Q.kOff + lo], ts = P.tsize[Q.kOff + lo];
+    it.nk = P.counts[Q.kOff + lo];
     const int ti = loc / nt, tj = loc % nt;
-    i0 = ti * ts;
-    j0 = tj * ts;
-    TI = min(ts, nk - i0);
-    TJ = min(ts, nk - j0);
+    it.i0 = ti * ts;
+    it.j0 = tj * ts;
+    it.TI = min(ts, it.nk - it.i0);
+    it.TJ = min(ts, it.nk - it.j0);
+    it.base = P.qSlot[it.q] + P.resOff[Q.kOff + lo];
+    return it;
 }
 
-DEVI void append_recheck(const BuildParams& P, int k, int li, int lj, int t) {
+// Re-check entry: query (16 bits) | polytope (10) | li (16) | lj (16) | T (5).
+DEVI void append_recheck(const BuildParams& P, int q, int k, int li, int lj, int t) {
     const unsigned long long idx = atomicAdd(&P.info->rechecks, 1ull);
     if ((long long)idx < P.recheckCap) {
-        P.recheck[idx] = ((unsigned long long)k << 37) | ((unsigned long long)li << 21) |
-                         ((unsigned long long)lj << 5) | (unsigned long long)t;
+        P.recheck[idx] = ((unsigned long long)q << 47) | ((unsigned long long)k << 37) |
+                         ((unsigned long long)li << 21) | ((unsigned long long)lj << 5) | (unsigned long long)t;
     } else {
         atomicMax(&P.info->need_rechecks, idx + 1);
         set_status(P.info, PLAN_ERR_CAPACITY, DET_RECHECK);
@@ -301,7 +378,7 @@ template <int M, int G, int PD>
 __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
     using S = Shape<G, PD>;
     constexpr int N_ = M * G, RAX = S::RAX, RR = M * RAX, NI = S::NI, TG = S::TG;
-    constexpr int T = TILE;
+    const int T = P.tile;  // shared-memory stride = tile side (multiple of 4, <= TILE)
     extern __shared__ __align__(16) float sm[];
     const int FRm = NI * P.max_rows;
     const int DR = P.cost_mode == 1 ? 1 : G;
@@ -319,31 +396,34 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
     float* tab = xab + 2 * T * G;
     float* Ap = tab + P.L.f_stride;
     float* bp = Ap + RMAX * M;
-    __shared__ int s_item;
+    __shared__ long long s_item;
     __shared__ float s_rown1, s_bmax;
 
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int nitems = (int)P.info->items;
+    const long long nitems = (long long)P.info->items;
     const TabLayout L = P.L;
     unsigned long long rp_cnt = 0;
 
     for (;;) {
         if (tid == 0) {
-            const int it = (int)atomicAdd(&P.info->ticket, 1u);
-            s_item = has_failed(P.info) ? 0x7fffffff : it;  // one decision for the whole block
+            const long long it = (long long)atomicAdd(&P.info->ticket, 1u);
+            s_item = has_failed(P.info) ? 0x7fffffffffffLL : it;  // one decision for the whole block
         }
         __syncthreads();
-        const int item = s_item;
+        const long long item = s_item;
         if (item >= nitems) break;
-        int k, i0, j0, TI, TJ, nk;
-        item_decode(P, item, k, i0, j0, TI, TJ, nk);
+        const Item itd = item_decode(P, item);
+        const QueryDesc& Qd = P.qd[itd.q];
+        const int k = itd.k, i0 = itd.i0, j0 = itd.j0, TI = itd.TI, TJ = itd.TJ, nk = itd.nk;
         const int ni4 = (TI + 3) & ~3, nj4 = (TJ + 3) & ~3;
-        const int r0 = P.poly_off[k], nr = P.poly_off[k + 1] - r0;
-        for (int u = tid; u < nr * M; u += nthr) Ap[u] = P.A32[(long long)r0 * M + u];
-        for (int u = tid; u < nr; u += nthr) bp[u] = P.bc32[r0 + u];
+        const int r0 = Qd.poly_off[k], nr = Qd.poly_off[k + 1] - r0;
+        const long long rg0 = Qd.rowsOff + r0;
+        for (int u = tid; u < nr * M; u += nthr) Ap[u] = P.A32[rg0 * M + u];
+        for (int u = tid; u < nr; u += nthr) bp[u] = P.bc32[rg0 + u];
+        const int* members = P.members + Qd.listOff + (long long)k * Qd.N;
         float cx[M];
 #pragma unroll
-        for (int a = 0; a < M; ++a) cx[a] = P.centers[k * 4 + a];
+        for (int a = 0; a < M; ++a) cx[a] = P.centers[(long long)(Qd.kOff + k) * 4 + a];
         for (int u = tid; u < (ni4 + nj4) * N_; u += nthr) {
             const int s = u / N_, e = u % N_;
             const bool right = s >= ni4;
@@ -351,12 +431,12 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
             const int lidx = (right ? j0 : i0) + ls;
             float v = 0.f;
             if (ls < (right ? TJ : TI)) {
-                const long long id = P.members[(long long)k * P.N + lidx];
+                const long long id = members[lidx];
                 if (e < M) {
-                    if (P.in_f32) v = ((const float*)P.states)[id * N_ + e] - cx[e];
-                    else v = (float)(((const double*)P.states)[id * N_ + e] - (double)cx[e]);
+                    if (P.in_f32) v = ((const float*)Qd.states)[id * N_ + e] - cx[e];
+                    else v = (float)(((const double*)Qd.states)[id * N_ + e] - (double)cx[e]);
                 } else {
-                    v = ldf(P.states, id * N_ + e, P.in_f32);
+                    v = ldf(Qd.states, id * N_ + e, P.in_f32);
                 }
             }
             xs[(right ? T + ls : ls) * N_ + e] = v;
@@ -411,8 +491,8 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
             bt[q] = 0;
         }
 
-        for (int t = 0; t < P.nT; ++t) {
-            for (int u = tid; u < L.f_stride; u += nthr) tab[u] = P.tab32[(long long)t * L.f_stride + u];
+        for (int t = 0; t < Qd.nT; ++t) {
+            for (int u = tid; u < L.f_stride; u += nthr) tab[u] = P.tab32[(long long)(Qd.tabOff + t) * L.f_stride + u];
             __syncthreads();
             // reach and cost halves: one unit per (state, axis)
             for (int u = tid; u < (ni4 + nj4) * M; u += nthr) {
@@ -612,7 +692,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
                         if (amb) {
 #pragma unroll
                             for (int q = 0; q < 16; ++q)
-                                if ((amb >> q) & 1u) append_recheck(P, k, i0 + 4 * gi + (q >> 2), j0 + 4 * gj + (q & 3), t);
+                                if ((amb >> q) & 1u) append_recheck(P, itd.q, k, i0 + 4 * gi + (q >> 2), j0 + 4 * gj + (q & 3), t);
                         }
                     }
                 }
@@ -620,7 +700,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
             __syncthreads();
         }
         if (act) {
-            const long long base = P.resOff[k];
+            const long long base = itd.base;
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 if (!((vmask >> q) & 1u)) continue;
@@ -681,31 +761,33 @@ __global__ void __launch_bounds__(256) k_pairs_f64(BuildParams P) {
     double* bcs = limr + RAX;         // [T*T] best cost
     uint32_t* bbits = (uint32_t*)(bcs + T * T);
     uint8_t* bts = (uint8_t*)(bbits + T * T);
-    __shared__ int s_item;
+    __shared__ long long s_item;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int nitems = (int)P.info->items;
+    const long long nitems = (long long)P.info->items;
     const TabLayout L = P.L;
     unsigned long long rp_cnt = 0;
     for (int r = tid; r < RAX; r += nthr) limr[r] = P.lim64[reach_order<G, PD>(r) - 1];
     for (;;) {
         if (tid == 0) {
-            const int it = (int)atomicAdd(&P.info->ticket, 1u);
-            s_item = has_failed(P.info) ? 0x7fffffff : it;  // one decision for the whole block
+            const long long it = (long long)atomicAdd(&P.info->ticket, 1u);
+            s_item = has_failed(P.info) ? 0x7fffffffffffLL : it;  // one decision for the whole block
         }
         __syncthreads();
-        const int item = s_item;
+        const long long item = s_item;
         if (item >= nitems) break;
-        int k, i0, j0, TI, TJ, nk;
-        item_decode(P, item, k, i0, j0, TI, TJ, nk);
-        const int r0 = P.poly_off[k], nr = P.poly_off[k + 1] - r0;
-        for (int u = tid; u < nr * M; u += nthr) Ap[u] = ldv(P.A, (long long)r0 * M + u, P.in_f32);
-        for (int u = tid; u < nr; u += nthr) bl[u] = P.blim64[r0 + u];
+        const Item itd = item_decode(P, item);
+        const QueryDesc& Qd = P.qd[itd.q];
+        const int k = itd.k, i0 = itd.i0, j0 = itd.j0, TI = itd.TI, TJ = itd.TJ, nk = itd.nk;
+        const int r0 = Qd.poly_off[k], nr = Qd.poly_off[k + 1] - r0;
+        for (int u = tid; u < nr * M; u += nthr) Ap[u] = ldv(Qd.A, (long long)r0 * M + u, P.in_f32);
+        for (int u = tid; u < nr; u += nthr) bl[u] = P.blim64[Qd.rowsOff + r0 + u];
+        const int* members = P.members + Qd.listOff + (long long)k * Qd.N;
         for (int u = tid; u < (TI + TJ) * N_; u += nthr) {
             const int s = u / N_, e = u % N_;
             const bool right = s >= TI;
             const int ls = right ? s - TI : s;
-            const long long id = P.members[(long long)k * P.N + (right ? j0 : i0) + ls];
-            xs[(right ? T + ls : ls) * N_ + e] = ldv(P.states, id * N_ + e, P.in_f32);
+            const long long id = members[(right ? j0 : i0) + ls];
+            xs[(right ? T + ls : ls) * N_ + e] = ldv(Qd.states, id * N_ + e, P.in_f32);
         }
         for (int u = tid; u < T * T; u += nthr) {
             bcs[u] = __longlong_as_double(DINF_BITS);
@@ -713,8 +795,8 @@ __global__ void __launch_bounds__(256) k_pairs_f64(BuildParams P) {
             bts[u] = 0;
         }
         __syncthreads();
-        for (int t = 0; t < P.nT; ++t) {
-            for (int u = tid; u < L.e_stride; u += nthr) tab[u] = P.tab64[(long long)t * L.e_stride + u];
+        for (int t = 0; t < Qd.nT; ++t) {
+            for (int u = tid; u < L.e_stride; u += nthr) tab[u] = P.tab64[(long long)(Qd.tabOff + t) * L.e_stride + u];
             __syncthreads();
             for (int u = tid; u < (TI + TJ) * M; u += nthr) {
                 const int s = u / M, a = u % M;
@@ -782,7 +864,7 @@ __global__ void __launch_bounds__(256) k_pairs_f64(BuildParams P) {
             }
             __syncthreads();
         }
-        const long long base = P.resOff[k];
+        const long long base = itd.base;
         for (int pp = tid; pp < TI * TJ; pp += nthr) {
             const int li = pp / TJ, lj = pp % TJ;
             const int q = li * T + lj;
@@ -810,16 +892,18 @@ __global__ void k_recheck(BuildParams P) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const unsigned long long en = P.recheck[e];
         const int t = (int)(en & 31ull), lj = (int)((en >> 5) & 0xFFFFull), li = (int)((en >> 21) & 0xFFFFull);
-        const int k = (int)(en >> 37);
-        const int nk = P.counts[k];
-        const long long i = P.members[(long long)k * P.N + li], j = P.members[(long long)k * P.N + lj];
+        const int k = (int)((en >> 37) & 0x3FFull), q = (int)(en >> 47);
+        const QueryDesc& Q = P.qd[q];
+        const int nk = P.counts[Q.kOff + k];
+        const int* members = P.members + Q.listOff + (long long)k * Q.N;
+        const long long i = members[li], j = members[lj];
         double xi[N_], xj[N_];
 #pragma unroll
         for (int c = 0; c < N_; ++c) {
-            xi[c] = ldv(P.states, i * N_ + c, P.in_f32);
-            xj[c] = ldv(P.states, j * N_ + c, P.in_f32);
+            xi[c] = ldv(Q.states, i * N_ + c, P.in_f32);
+            xj[c] = ldv(Q.states, j * N_ + c, P.in_f32);
         }
-        const double* tb = P.tab64 + (long long)t * L.e_stride;
+        const double* tb = P.tab64 + (long long)(Q.tabOff + t) * L.e_stride;
         bool ok = true;
         for (int r = 0; r < RAX && ok; ++r) {
             const double lim = P.lim64[reach_order<G, PD>(r) - 1];
@@ -829,15 +913,15 @@ __global__ void k_recheck(BuildParams P) {
                 if (!(fabs(s) <= lim)) ok = false;
             }
         }
-        const int r0 = P.poly_off[k], r1 = P.poly_off[k + 1];
+        const int r0 = Q.poly_off[k], r1 = Q.poly_off[k + 1];
         for (int l = 1; l <= NI && ok; ++l) {
             double pt[M];
             for (int a = 0; a < M; ++a)
                 pt[a] = __dadd_rn(half_sum<G>(tb + L.e_D + l * TG, xi + a, M), half_sum<G>(tb + L.e_D + l * TG + G, xj + a, M));
             for (int r = r0; r < r1; ++r) {
                 double s = 0.0;
-                for (int a = 0; a < M; ++a) s = __dadd_rn(s, __dmul_rn(ldv(P.A, (long long)r * M + a, P.in_f32), pt[a]));
-                if (!(s <= P.blim64[r])) {
+                for (int a = 0; a < M; ++a) s = __dadd_rn(s, __dmul_rn(ldv(Q.A, (long long)r * M + a, P.in_f32), pt[a]));
+                if (!(s <= P.blim64[Q.rowsOff + r])) {
                     ok = false;
                     break;
                 }
@@ -855,7 +939,7 @@ __global__ void k_recheck(BuildParams P) {
                 }
             cost += sqrt(ss);
         }
-        const long long slot = P.resOff[k] + (long long)li * nk + lj;
+        const long long slot = P.qSlot[q] + P.resOff[Q.kOff + k] + (long long)li * nk + lj;
         atomicOr(&P.resBits[slot], 1u << t);
         atomicMin(&P.resKey[slot], key_f32((float)cost, t));
     }
@@ -868,27 +952,49 @@ __global__ void k_recheck(BuildParams P) {
 // emitted entries in its (row, polytope) segment; pass 2 places every entry
 // at its rank among the row's emitted ids (sorted by j).
 // ---------------------------------------------------------------------------
-DEVI int owner_of(const BuildParams& P, int i, int j, int& nshared) {
+struct QView {  // per-query pointers into the shared scratch
+    const QueryDesc* Q;
+    const uint32_t* mask;
+    const int* counts;
+    const int* members;
+    const int* localIdx;
+    const long long* resOff;
+    long long slot0;
+    __device__ QView(const BuildParams& P, int q) {
+        Q = &P.qd[q];
+        mask = P.memMask + Q->maskOff;
+        counts = P.counts + Q->kOff;
+        members = P.members + Q->listOff;
+        localIdx = P.localIdx + Q->listOff;
+        resOff = P.resOff + Q->kOff;
+        slot0 = P.qSlot[q];
+    }
+    __device__ long long seg(int k, int i) const {  // slot of (member i, member 0) in polytope k
+        return slot0 + resOff[k] + (long long)localIdx[(long long)k * Q->N + i] * counts[k];
+    }
+};
+
+DEVI int owner_of(const QView& V, int i, int j, int& nshared) {
     int owner = -1;
     nshared = 0;
-    for (int w = 0; w < P.W; ++w) {
-        const uint32_t x = P.memMask[(long long)i * P.W + w] & P.memMask[(long long)j * P.W + w];
+    const int W = V.Q->W;
+    for (int w = 0; w < W; ++w) {
+        const uint32_t x = V.mask[(long long)i * W + w] & V.mask[(long long)j * W + w];
         if (x && owner < 0) owner = w * 32 + __ffs(x) - 1;
         nshared += __popc(x);
     }
     return owner;
 }
 
-DEVI void combine(const BuildParams& P, int i, int j, int k, uint32_t& bits, unsigned long long& key) {
-    for (int w = k >> 5; w < P.W; ++w) {
-        uint32_t x = P.memMask[(long long)i * P.W + w] & P.memMask[(long long)j * P.W + w];
+DEVI void combine(const BuildParams& P, const QView& V, int i, int j, int k, uint32_t& bits, unsigned long long& key) {
+    const int W = V.Q->W;
+    for (int w = k >> 5; w < W; ++w) {
+        uint32_t x = V.mask[(long long)i * W + w] & V.mask[(long long)j * W + w];
         if (w == (k >> 5)) x &= ~((2u << (k & 31)) - 1u);  // polytopes above k
         while (x) {
             const int k2 = w * 32 + __ffs(x) - 1;
             x &= x - 1u;
-            const int n2 = P.counts[k2];
-            const long long s2 = P.resOff[k2] + (long long)P.localIdx[(long long)k2 * P.N + i] * n2 +
-                                 P.localIdx[(long long)k2 * P.N + j];
+            const long long s2 = V.seg(k2, i) + V.localIdx[(long long)k2 * V.Q->N + j];
             bits |= P.resBits[s2];
             const unsigned long long k2v = P.resKey[s2];
             if (k2v < key) key = k2v;
@@ -897,31 +1003,35 @@ DEVI void combine(const BuildParams& P, int i, int j, int k, uint32_t& bits, uns
 }
 
 __global__ void k_compact_count(BuildParams P) {
-    const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (warp >= P.N || has_failed(P.info)) return;
-    const int i = warp;
+    if (warp >= P.totN || has_failed(P.info)) return;
+    const int q = find_q(P.pfxN, P.Q, warp);
+    const QView V(P, q);
+    const int i = (int)(warp - P.pfxN[q]);
+    const int W = V.Q->W;
     long long total = 0, cand = 0, feas = 0;
-    for (int w = 0; w < P.W; ++w) {
-        uint32_t mw = P.memMask[(long long)i * P.W + w];
+    for (int w = 0; w < W; ++w) {
+        uint32_t mw = V.mask[(long long)i * W + w];
         while (mw) {
             const int k = w * 32 + __ffs(mw) - 1;
             mw &= mw - 1u;
-            const int nk = P.counts[k];
-            const long long base = P.resOff[k] + (long long)P.localIdx[(long long)k * P.N + i] * nk;
+            const int nk = V.counts[k];
+            const long long base = V.seg(k, i);
+            const int* mem = V.members + (long long)k * V.Q->N;
             int running = 0;
             for (int lj0 = 0; lj0 < nk; lj0 += 32) {
                 const int lj = lj0 + lane;
                 bool emitted = false;
                 if (lj < nk) {
-                    const int j = P.members[(long long)k * P.N + lj];
+                    const int j = mem[lj];
                     if (j != i) {
                         int ns;
-                        if (owner_of(P, i, j, ns) == k) {
+                        if (owner_of(V, i, j, ns) == k) {
                             ++cand;
                             uint32_t bits = P.resBits[base + lj];
                             unsigned long long key = P.resKey[base + lj];
-                            if (ns > 1) combine(P, i, j, k, bits, key);
+                            if (ns > 1) combine(P, V, i, j, k, bits, key);
                             emitted = bits != 0;
                             feas += __popc(bits);
                         }
@@ -939,32 +1049,35 @@ __global__ void k_compact_count(BuildParams P) {
         feas += __shfl_down_sync(0xffffffffu, feas, o);
     }
     if (lane == 0) {
-        P.rowCount[i] = (int)total;
+        P.rowCount[V.Q->rowOff + i] = (int)total;
         if (cand) atomicAdd(&P.info->candidates, (unsigned long long)cand);
         if (feas) atomicAdd(&P.info->feasible, (unsigned long long)feas);
     }
 }
 
+// One CTA per query: exclusive scan of the row counts into row_off, E, capacity.
 __global__ void __launch_bounds__(1024) k_scan(BuildParams P) {
     __shared__ long long wb[32];
     __shared__ long long tot;
     if (has_failed(P.info)) return;
-    const int N = P.N;
+    const QueryDesc& Q = P.qd[blockIdx.x];
+    const int N = Q.N;
+    const int* rc = P.rowCount + Q.rowOff;
     const int per = (N + blockDim.x - 1) / blockDim.x;
     const int s0 = threadIdx.x * per, s1 = min(N, s0 + per);
     long long local = 0;
-    for (int i = s0; i < s1; ++i) local += P.rowCount[i];
+    for (int i = s0; i < s1; ++i) local += rc[i];
     long long run = block_exclusive_scan<long long>(local, wb, &tot);
     const long long total = tot;
     for (int i = s0; i < s1; ++i) {
-        P.row_off[i] = (int32_t)run;
-        run += P.rowCount[i];
+        Q.row_off[i] = (int32_t)run;
+        run += rc[i];
     }
     if (threadIdx.x == 0) {
-        P.row_off[N] = (int32_t)total;
-        P.info->edges = total;
-        *P.count = total;
-        if (total > P.cap || total > 0x7fffffffLL) set_status(P.info, PLAN_ERR_CAPACITY, DET_OUTPUT);
+        Q.row_off[N] = (int32_t)total;
+        atomicAdd(&P.info->edges, (unsigned long long)total);
+        *Q.count = total;
+        if (total > Q.cap || total > 0x7fffffffLL) set_status(P.info, PLAN_ERR_CAPACITY, DET_OUTPUT);
     }
 }
 
@@ -979,56 +1092,57 @@ DEVI int lower_bound_members(const int* mem, int n, int j) {
 }
 
 __global__ void k_compact_fill(BuildParams P) {
-    const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (warp >= P.N || has_failed(P.info)) return;
-    const int i = warp;
+    if (warp >= P.totN || has_failed(P.info)) return;
+    const int q = find_q(P.pfxN, P.Q, warp);
+    const QView V(P, q);
+    const QueryDesc& Q = *V.Q;
+    const int i = (int)(warp - P.pfxN[q]);
+    const int W = Q.W;
     int npoly = 0;
-    for (int w = 0; w < P.W; ++w) npoly += __popc(P.memMask[(long long)i * P.W + w]);
-    const long long rbase = P.row_off[i];
+    for (int w = 0; w < W; ++w) npoly += __popc(V.mask[(long long)i * W + w]);
+    const long long rbase = Q.row_off[i];
     const bool f64 = P.arith == PLAN_F64;
-    for (int w = 0; w < P.W; ++w) {
-        uint32_t mw = P.memMask[(long long)i * P.W + w];
+    for (int w = 0; w < W; ++w) {
+        uint32_t mw = V.mask[(long long)i * W + w];
         while (mw) {
             const int k = w * 32 + __ffs(mw) - 1;
             mw &= mw - 1u;
-            const int nk = P.counts[k];
-            const long long base = P.resOff[k] + (long long)P.localIdx[(long long)k * P.N + i] * nk;
+            const int nk = V.counts[k];
+            const long long base = V.seg(k, i);
+            const int* mem = V.members + (long long)k * Q.N;
             for (int lj = lane; lj < nk; lj += 32) {
-                const int j = P.members[(long long)k * P.N + lj];
+                const int j = mem[lj];
                 if (j == i) continue;
                 const int pre = P.emitPre[base + lj];
                 const int prev = lj > 0 ? P.emitPre[base + lj - 1] : 0;
                 if (pre == prev) continue;  // not emitted here
                 int ns;
-                owner_of(P, i, j, ns);
+                owner_of(V, i, j, ns);
                 uint32_t bits = P.resBits[base + lj];
                 unsigned long long key = P.resKey[base + lj];
-                if (ns > 1) combine(P, i, j, k, bits, key);
+                if (ns > 1) combine(P, V, i, j, k, bits, key);
                 long long rank = prev;
                 if (npoly > 1) {
-                    for (int w2 = 0; w2 < P.W; ++w2) {
-                        uint32_t m2 = P.memMask[(long long)i * P.W + w2];
+                    for (int w2 = 0; w2 < W; ++w2) {
+                        uint32_t m2 = V.mask[(long long)i * W + w2];
                         while (m2) {
                             const int k2 = w2 * 32 + __ffs(m2) - 1;
                             m2 &= m2 - 1u;
                             if (k2 == k) continue;
-                            const int n2 = P.counts[k2];
-                            const int pos = lower_bound_members(P.members + (long long)k2 * P.N, n2, j);
-                            if (pos > 0) {
-                                const long long b2 = P.resOff[k2] + (long long)P.localIdx[(long long)k2 * P.N + i] * n2;
-                                rank += P.emitPre[b2 + pos - 1];
-                            }
+                            const int n2 = V.counts[k2];
+                            const int pos = lower_bound_members(V.members + (long long)k2 * Q.N, n2, j);
+                            if (pos > 0) rank += P.emitPre[V.seg(k2, i) + pos - 1];
                         }
                     }
                 }
                 const long long o = rbase + rank;
-                P.col[o] = j;
-                P.mask[o] = bits;
-                const int tb = (int)(key & 31ull);
-                P.tidx[o] = (uint8_t)tb;
-                if (f64) ((double*)P.w)[o] = __longlong_as_double((long long)(key & ~31ull));
-                else ((float*)P.w)[o] = __uint_as_float((unsigned)(key >> 32));
+                Q.col[o] = j;
+                Q.mask[o] = bits;
+                Q.tidx[o] = (uint8_t)(key & 31ull);
+                if (f64) ((double*)Q.w)[o] = __longlong_as_double((long long)(key & ~31ull));
+                else ((float*)Q.w)[o] = __uint_as_float((unsigned)(key >> 32));
             }
         }
     }
@@ -1054,26 +1168,31 @@ __global__ void k_account(BuildParams P, unsigned long long* work) {
     unsigned long long wr = 0, wf = 0, wc = 0;
     for (long long sidx = blockIdx.x * (long long)blockDim.x + threadIdx.x; sidx < total;
          sidx += (long long)gridDim.x * blockDim.x) {
-        int lo = 0, hi = P.K;
+        const int q = find_q(P.qSlot, P.Q, sidx);
+        const QView V(P, q);
+        const QueryDesc& Q = *V.Q;
+        const long long ls = sidx - V.slot0;
+        int lo = 0, hi = Q.K;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
-            if (P.resOff[mid] <= sidx) lo = mid;
+            if (V.resOff[mid] <= ls) lo = mid;
             else hi = mid;
         }
-        const int k = lo, nk = P.counts[k];
-        const long long loc = sidx - P.resOff[k];
+        const int k = lo, nk = V.counts[k];
+        if (nk == 0) continue;
+        const long long loc = ls - V.resOff[k];
         const int li = (int)(loc / nk), lj = (int)(loc % nk);
-        const int i = P.members[(long long)k * P.N + li], j = P.members[(long long)k * P.N + lj];
+        const int i = V.members[(long long)k * Q.N + li], j = V.members[(long long)k * Q.N + lj];
         if (i == j) continue;
         int ns;
-        if (owner_of(P, i, j, ns) != k) continue;
+        if (owner_of(V, i, j, ns) != k) continue;
         float xi[N_], xj[N_];
         for (int c = 0; c < N_; ++c) {
-            xi[c] = ldf(P.states, (long long)i * N_ + c, P.in_f32);
-            xj[c] = ldf(P.states, (long long)j * N_ + c, P.in_f32);
+            xi[c] = ldf(Q.states, (long long)i * N_ + c, P.in_f32);
+            xj[c] = ldf(Q.states, (long long)j * N_ + c, P.in_f32);
         }
-        for (int t = 0; t < P.nT; ++t) {
-            const float* tb = P.tab32 + (long long)t * L.f_stride;
+        for (int t = 0; t < Q.nT; ++t) {
+            const float* tb = P.tab32 + (long long)(Q.tabOff + t) * L.f_stride;
             bool ok = true;
             for (int r = 0; r < RAX && ok; ++r)
                 for (int a = 0; a < M && ok; ++a) {
@@ -1091,18 +1210,18 @@ __global__ void k_account(BuildParams P, unsigned long long* work) {
                     pt[l][a] = s;
                 }
             bool feas = false;
-            for (int w = 0; w < P.W && !feas; ++w) {
-                uint32_t x = P.memMask[(long long)i * P.W + w] & P.memMask[(long long)j * P.W + w];
+            for (int w = 0; w < Q.W && !feas; ++w) {
+                uint32_t x = V.mask[(long long)i * Q.W + w] & V.mask[(long long)j * Q.W + w];
                 while (x && !feas) {
                     const int k2 = w * 32 + __ffs(x) - 1;
                     x &= x - 1u;
                     bool fok = true;
                     for (int l = 0; l < NI && fok; ++l)
-                        for (int r = P.poly_off[k2]; r < P.poly_off[k2 + 1] && fok; ++r) {
+                        for (int r = Q.poly_off[k2]; r < Q.poly_off[k2 + 1] && fok; ++r) {
                             float s = 0.f;
-                            for (int a = 0; a < M; ++a) s += P.A32[(long long)r * M + a] * pt[l][a];
+                            for (int a = 0; a < M; ++a) s += P.A32[(Q.rowsOff + r) * M + a] * pt[l][a];
                             ++wf;
-                            if (s > P.blim32[r]) fok = false;
+                            if (s > P.blim32[Q.rowsOff + r]) fok = false;
                         }
                     feas = fok;
                 }
@@ -1124,7 +1243,6 @@ __global__ void k_account(BuildParams P, unsigned long long* work) {
 
 int launch_account(const BuildParams& P, void* stream, int num_sms, unsigned long long* work) {
     cudaStream_t st = (cudaStream_t)stream;
-    cudaMemsetAsync(work, 0, 3 * sizeof(unsigned long long), st);
     const int nb = num_sms * 8;
     if (P.m == 2 && P.g == 2 && P.p == 3) k_account<2, 2, 3><<<nb, 256, 0, st>>>(P, work);
     else if (P.m == 2 && P.g == 2 && P.p == 5) k_account<2, 2, 5><<<nb, 256, 0, st>>>(P, work);
@@ -1140,7 +1258,8 @@ template <int M, int G, int PD>
 size_t smem_fast(const BuildParams& P) {
     using S = Shape<G, PD>;
     const int RR = M * S::RAX, FRm = S::NI * P.max_rows, CRW = G * PD * M;
-    size_t f = (size_t)(2 * RR + 2 * FRm + 2 * CRW + 4) * TILE + 2 * TILE * (M * G + G) + P.L.f_stride + RMAX * (M + 1);
+    const size_t T = (size_t)P.tile;
+    size_t f = (size_t)(2 * RR + 2 * FRm + 2 * CRW + 4) * T + 2 * T * (M * G + G) + P.L.f_stride + RMAX * (M + 1);
     return f * sizeof(float);
 }
 
@@ -1154,7 +1273,8 @@ size_t smem_f64(const BuildParams& P) {
 }
 
 template <int M, int G, int PD>
-int launch_pairs(const BuildParams& P, cudaStream_t st, int num_sms, cudaEvent_t e0, cudaEvent_t e1, int* launches) {
+int launch_pairs(const BuildParams& P, cudaStream_t st, int num_sms, int ctas_per_sm, cudaEvent_t e0, cudaEvent_t e1,
+                 int* launches) {
     if (P.arith == PLAN_F64) {
         const size_t sm = smem_f64<M, G, PD>(P);
         cudaFuncSetAttribute(k_pairs_f64<M, G, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1167,12 +1287,14 @@ int launch_pairs(const BuildParams& P, cudaStream_t st, int num_sms, cudaEvent_t
         ++*launches;
     } else {
         const size_t sm = smem_fast<M, G, PD>(P);
+        const int threads = (P.tile / 4) * (P.tile / 4);
         cudaFuncSetAttribute(k_pairs_fast<M, G, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pairs_fast<M, G, PD>, 256, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pairs_fast<M, G, PD>, threads, sm);
         if (occ < 1) occ = 1;
+        if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
         if (e0) cudaEventRecord(e0, st);
-        k_pairs_fast<M, G, PD><<<num_sms * occ, 256, sm, st>>>(P);
+        k_pairs_fast<M, G, PD><<<num_sms * occ, threads, sm, st>>>(P);
         if (e1) cudaEventRecord(e1, st);
         ++*launches;
         k_recheck<M, G, PD><<<num_sms * 4, 128, 0, st>>>(P);
@@ -1185,39 +1307,40 @@ bool model_supported(int m, int g, int p) {
     return (m == 2 && g == 2 && (p == 3 || p == 5)) || (m == 3 && g == 3 && (p == 5 || p == 7));
 }
 
-int launch_build(const BuildParams& P, void* stream, int num_sms, void* ev0, void* ev1, int* launches) {
+int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_sm, void* ev0, void* ev1, int* launches) {
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t e0 = (cudaEvent_t)ev0, e1 = (cudaEvent_t)ev1;
-    if (P.K > 0 && P.max_rows > 0) {
-        const long long nt = (long long)P.K * P.max_rows;
-        k_prep<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(P);
+    if (P.Q <= 0) return 0;
+    if (P.totRows > 0) {
+        k_prep<<<(unsigned)((P.totRows + 255) / 256), 256, 0, st>>>(P);
         ++*launches;
     }
-    if (P.N > 0 && P.K > 0) {
-        const long long nt = (long long)P.N * P.W;
-        k_member<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(P);
-        k_lists<<<P.K, 1024, 0, st>>>(P);
+    if (P.totMask > 0 && P.totPoly > 0) {
+        k_member<<<(unsigned)((P.totMask + 255) / 256), 256, 0, st>>>(P);
+        k_lists<<<(unsigned)P.totPoly, 1024, 0, st>>>(P);
         *launches += 2;
     }
-    k_setup<<<1, 1024, 0, st>>>(P, P.arith == PLAN_F64 ? TILE64 : TILE);
-    ++*launches;
-    if (P.N > 0 && P.K > 0) {
+    k_setup<<<P.Q, 1024, 0, st>>>(P);
+    k_batch<<<1, 1024, 0, st>>>(P);
+    *launches += 2;
+    if (P.totN > 0 && P.totPoly > 0) {
         int rc = 0;
-        if (P.m == 2 && P.g == 2 && P.p == 3) rc = launch_pairs<2, 2, 3>(P, st, num_sms, e0, e1, launches);
-        else if (P.m == 2 && P.g == 2 && P.p == 5) rc = launch_pairs<2, 2, 5>(P, st, num_sms, e0, e1, launches);
-        else if (P.m == 3 && P.g == 3 && P.p == 5) rc = launch_pairs<3, 3, 5>(P, st, num_sms, e0, e1, launches);
-        else if (P.m == 3 && P.g == 3 && P.p == 7) rc = launch_pairs<3, 3, 7>(P, st, num_sms, e0, e1, launches);
+        if (P.m == 2 && P.g == 2 && P.p == 3) rc = launch_pairs<2, 2, 3>(P, st, num_sms, ctas_per_sm, e0, e1, launches);
+        else if (P.m == 2 && P.g == 2 && P.p == 5) rc = launch_pairs<2, 2, 5>(P, st, num_sms, ctas_per_sm, e0, e1, launches);
+        else if (P.m == 3 && P.g == 3 && P.p == 5) rc = launch_pairs<3, 3, 5>(P, st, num_sms, ctas_per_sm, e0, e1, launches);
+        else if (P.m == 3 && P.g == 3 && P.p == 7) rc = launch_pairs<3, 3, 7>(P, st, num_sms, ctas_per_sm, e0, e1, launches);
         if (rc) return rc;
-        const long long thr = (long long)P.N * 32;
+    }
+    if (P.totN > 0) {
+        // rows of queries without polytopes have no members: their counts stay 0
+        const long long thr = P.totN * 32;
         k_compact_count<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(P);
         ++*launches;
-    } else if (P.N > 0) {
-        cudaMemsetAsync(P.rowCount, 0, sizeof(int) * (size_t)P.N, st);
     }
-    k_scan<<<1, 1024, 0, st>>>(P);
+    k_scan<<<P.Q, 1024, 0, st>>>(P);
     ++*launches;
-    if (P.N > 0 && P.K > 0) {
-        const long long thr = (long long)P.N * 32;
+    if (P.totN > 0 && P.totPoly > 0) {
+        const long long thr = P.totN * 32;
         k_compact_fill<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(P);
         ++*launches;
     }

@@ -89,42 +89,20 @@ enum Detail {
     DET_WALK = 9
 };
 
-// Everything a build kernel needs, passed by value.
-struct BuildParams {
-    int N, K, nT, W, R;        // W: 32-bit words per membership mask; R: row capacity
-    int m, g, p;
-    int cost_mode, in_f32, arith, max_rows;
-    double eps;
+// One query of a batch (device array; host-known offsets into the shared
+// scratch, caller-owned input/output pointers).
+struct QueryDesc {
+    int N, K, nT, W;           // W: 32-bit words per membership mask
+    int tabOff;                // first duration of this query in the table arrays
+    int kOff;                  // per-polytope arrays (counts, centers, ...), K+1 entries each
+    long long maskOff;         // memMask   [N][W]
+    long long listOff;         // members / localIdx [K][N]
+    long long rowsOff;         // row arrays [K * max_rows]
+    long long rowOff;          // rowCount  [N]
     const void* states;
     const int* poly_off;
     const void* A;
     const void* b;
-    const float* tab32;        // [nT][f_stride]
-    const double* tab64;       // [nT][e_stride]
-    double lim64[4];           // c_k - eps
-    TabLayout L;
-    // scratch
-    uint32_t* memMask;         // [N][W]
-    int* counts;               // [K]
-    int* members;              // [K][N]
-    int* localIdx;             // [K][N]
-    float* centers;            // [K][4] (FP32 position of the first member)
-    double* blim64;            // [R] b - eps
-    float* A32;                // [R][m]
-    float* blim32;             // [R]
-    float* bc32;               // [R] centred bound for the fast kernels
-    long long* resOff;         // [K+1]
-    int* itemOff;              // [K+1]
-    int* ntile;                // [K]
-    int* tsize;                // [K]
-    uint32_t* resBits;         // [slotCap]
-    unsigned long long* resKey;// [slotCap]
-    int* emitPre;              // [slotCap]
-    unsigned long long* recheck; // [recheckCap]
-    int* rowCount;             // [N]
-    long long slotCap, recheckCap;
-    DevInfo* info;
-    // output CSR
     int32_t* row_off;
     int32_t* col;
     void* w;
@@ -132,6 +110,49 @@ struct BuildParams {
     uint32_t* mask;
     long long cap;
     int64_t* count;
+};
+
+// Everything a build kernel needs, passed by value.
+struct BuildParams {
+    int Q;                     // queries in the batch
+    int maxK;                  // max K over queries
+    int m, g, p;
+    int cost_mode, in_f32, arith, max_rows;
+    int tile;                  // tile side of the pair kernel (autotuned, <= TILE)
+    double eps;
+    const QueryDesc* qd;       // [Q]
+    const long long* pfxMask;  // [Q+1] prefix of N*W        (membership threads)
+    const long long* pfxPoly;  // [Q+1] prefix of K          (one CTA per polytope)
+    const long long* pfxRows;  // [Q+1] prefix of K*max_rows (row threads)
+    const long long* pfxN;     // [Q+1] prefix of N          (one warp per row)
+    long long* qSlot;          // [Q+1] device-computed prefix of slots
+    long long* qItem;          // [Q+1] device-computed prefix of tiles
+    long long totMask, totPoly, totRows, totN;
+    const float* tab32;        // [nT_total][f_stride]
+    const double* tab64;       // [nT_total][e_stride]
+    double lim64[4];           // c_k - eps
+    TabLayout L;
+    // scratch (shared by all queries, indexed with the descriptor offsets)
+    uint32_t* memMask;
+    int* counts;
+    int* members;
+    int* localIdx;
+    float* centers;            // [kOff][4]
+    double* blim64;
+    float* A32;                // [rows][m]
+    float* blim32;
+    float* bc32;
+    long long* resOff;         // [kOff] slot offset of each polytope, relative to qSlot[q]
+    int* itemOff;
+    int* ntile;
+    int* tsize;
+    uint32_t* resBits;
+    unsigned long long* resKey;
+    int* emitPre;
+    unsigned long long* recheck;
+    int* rowCount;
+    long long slotCap, recheckCap;
+    DevInfo* info;
 };
 
 struct SearchParams {
@@ -173,8 +194,8 @@ struct RefineParams {
 };
 
 // Launchers (plan_build.cu / plan_search.cu / plan_refine.cu); return cudaError_t as int.
-int launch_build(const BuildParams& P, void* stream, int num_sms, void* ev_pair_begin, void* ev_pair_end,
-                 int* launches);
+int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_sm, void* ev_pair_begin,
+                 void* ev_pair_end, int* launches);
 int launch_search(const SearchParams& P, void* stream, int num_sms, int* launches);
 int launch_account(const BuildParams& P, void* stream, int num_sms, unsigned long long* work);
 bool model_supported(int m, int g, int p);

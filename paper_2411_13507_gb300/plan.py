@@ -53,12 +53,19 @@ class _Info(ctypes.Structure):
                 ("work_reach_rows", ctypes.c_int64), ("work_free_rows", ctypes.c_int64), ("work_costs", ctypes.c_int64)]
 
 
+class _Query(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("states", ctypes.c_void_p), ("nT", ctypes.c_int),
+                ("T", ctypes.POINTER(ctypes.c_double)), ("K", ctypes.c_int), ("poly_off", ctypes.c_void_p),
+                ("A", ctypes.c_void_p), ("b", ctypes.c_void_p), ("out", _Edges)]
+
+
 class _RefineW(ctypes.Structure):
     _fields_ = [("w_snap", ctypes.c_double), ("mu", ctypes.c_double), ("delta", ctypes.c_double)]
 
 
 EXPORTS = ["plan_create", "plan_destroy", "plan_build_edges", "plan_search", "plan_wait", "plan_model_tables",
-           "plan_set_search_limits", "plan_refine", "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
+           "plan_set_search_limits", "plan_refine", "plan_prepare_batched", "plan_build_edges_batched",
+           "plan_set_tile", "plan_autotune", "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
 
 
 def lib_path() -> str:
@@ -91,6 +98,14 @@ def load(build_if_stale: bool = True):
     lib.plan_model_tables.restype = i32
     lib.plan_set_search_limits.argtypes = [vp, i32, i64]
     lib.plan_set_search_limits.restype = i32
+    lib.plan_prepare_batched.argtypes = [vp, i32, ctypes.POINTER(_Query), i32]
+    lib.plan_prepare_batched.restype = i32
+    lib.plan_build_edges_batched.argtypes = [vp]
+    lib.plan_build_edges_batched.restype = i32
+    lib.plan_set_tile.argtypes = [vp, i32, i32]
+    lib.plan_set_tile.restype = i32
+    lib.plan_autotune.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), dp]
+    lib.plan_autotune.restype = i32
     lib.plan_refine.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, ctypes.POINTER(_RefineW), vp, vp, vp, vp]
     lib.plan_refine.restype = i32
     lib.plan_set_accounting.argtypes = [vp, i32]
@@ -320,6 +335,58 @@ class Planner:
         rc = self.lib.plan_set_search_limits(self.ctx, int(max_sweeps), int(spin_limit))
         if rc != 0:
             raise self._err(rc, "plan_set_search_limits")
+
+    # ---- batching form -------------------------------------------------
+    def prepare_batched(self, dps, graphs) -> None:
+        """Host work of a batch (tables, offsets, scratch, descriptor upload)."""
+        qs = (_Query * len(dps))()
+        self._batch_keep = []
+        max_rows = 1
+        for q, (dp, g) in enumerate(zip(dps, graphs)):
+            T = np.ascontiguousarray(dp.T, dtype=np.float64)
+            self._batch_keep.append(T)
+            qs[q] = _Query(dp.N, dp.states.data_ptr(), int(T.shape[0]), T.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                           dp.K, dp.poly_off.data_ptr(), dp.A.data_ptr(), dp.b.data_ptr(), g.cstruct())
+            max_rows = max(max_rows, dp.max_rows)
+        rc = self.lib.plan_prepare_batched(self.ctx, len(dps), qs, max_rows)
+        if rc != 0:
+            raise self._err(rc, "plan_prepare_batched")
+
+    def build_batched_async(self) -> None:
+        rc = self.lib.plan_build_edges_batched(self.ctx)
+        if rc != 0:
+            raise self._err(rc, "plan_build_edges_batched")
+
+    def build_batched(self, dps, graphs=None, cap_per_state: int = 64):
+        """Edge graphs of many queries in one pass (grows scratch/outputs on CAPACITY)."""
+        if graphs is None:
+            graphs = [self.alloc_graph(dp.N, max(1024, cap_per_state * dp.N)) for dp in dps]
+        for _ in range(8):
+            self.prepare_batched(dps, graphs)
+            self.build_batched_async()
+            st = self.wait()
+            if st == PLAN_OK:
+                return graphs
+            if st == PLAN_ERR_CAPACITY:
+                if self.last_info.detail == DET_OUTPUT:
+                    graphs = [g if g.E <= g.cap else self.alloc_graph(dp.N, int(g.E * 1.1) + 1024)
+                              for dp, g in zip(dps, graphs)]
+                continue
+            raise self._err(st, "build_batched")
+        raise self._err(PLAN_ERR_CAPACITY, "build_batched: capacity retries exhausted")
+
+    def set_tile(self, tile: int = 0, ctas_per_sm: int = 0) -> None:
+        rc = self.lib.plan_set_tile(self.ctx, int(tile), int(ctas_per_sm))
+        if rc != 0:
+            raise self._err(rc, "plan_set_tile")
+
+    def autotune(self, reps: int = 3) -> dict:
+        """Time every (tile, CTAs/SM) candidate on the prepared batch; keep the best."""
+        t, c, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        rc = self.lib.plan_autotune(self.ctx, int(reps), ctypes.byref(t), ctypes.byref(c), ctypes.byref(ms))
+        if rc != 0:
+            raise self._err(rc, "plan_autotune")
+        return {"tile": t.value, "ctas_per_sm": c.value, "pair_ms": ms.value}
 
     def refine_async(self, P, T, A, b, nrows, weights=(1.0, 1.0, 0.1), grad_loss=None, loss=None, dP=None, dT=None):
         """Launch the refinement loss (and, with grad_loss, its gradient) on device float tensors."""

@@ -27,11 +27,16 @@ def compare_rows(gpu: dict, orc_edges: dict, rows, nT: int, arith: str) -> dict:
     om, ow, ot = orc_edges["mask"][keep], orc_edges["w"][keep], orc_edges["t"][keep]
     oc = orc_edges["costs"][keep] if "costs" in orc_edges else None
     ro = gpu["row_off"]
+    order = np.argsort(oi, kind="stable")       # oracle rows are grouped; keep j order
+    oi, oj, om, ow, ot = oi[order], oj[order], om[order], ow[order], ot[order]
+    if oc is not None:
+        oc = oc[order]
     for i in rows:
-        sel = oi == i
+        lo_, hi_ = np.searchsorted(oi, i, "left"), np.searchsorted(oi, i, "right")
+        sel = slice(lo_, hi_)
         a, b = int(ro[i]), int(ro[i + 1])
         gj = gpu["col"][a:b]
-        assert np.array_equal(gj, oj[sel]), f"row {i}: edge set differs ({len(gj)} vs {int(sel.sum())})"
+        assert np.array_equal(gj, oj[sel]), f"row {i}: edge set differs ({len(gj)} vs {hi_ - lo_})"
         gm = gpu["mask"][a:b]
         bad = np.nonzero(gm != om[sel])[0]
         assert bad.size == 0, f"row {i}: mask differs at j={gj[bad[:5]]}: gpu {gm[bad[:5]]} oracle {om[sel][bad[:5]]}"
@@ -40,20 +45,21 @@ def compare_rows(gpu: dict, orc_edges: dict, rows, nT: int, arith: str) -> dict:
         if rel.size:
             stats["max_rel_w"] = max(stats["max_rel_w"], float(rel.max()))
         assert np.all(rel <= tol), f"row {i}: weight rel err {rel.max():.3e} > {tol}"
-        stats["edges"] += int(sel.sum())
-        if oc is not None:
+        stats["edges"] += hi_ - lo_
+        if oc is not None and hi_ > lo_:
             gt = gpu["t"][a:b]
-            for q in range(int(sel.sum())):
-                costs = oc[sel][q]
-                mk = int(om[sel][q])
-                feas = [t for t in range(nT) if (mk >> t) & 1]
-                best = int(ot[sel][q])
-                others = [costs[t] for t in feas if t != best]
-                if all(c > costs[best] * (1 + 2 * tol) for c in others):
-                    stats["tidx_checked"] += 1
-                    assert int(gt[q]) == best, f"row {i} col {gj[q]}: tidx {gt[q]} vs {best}"
-                else:
-                    stats["tidx_tied"] += 1
+            costs = oc[sel]                                   # [e][nT]
+            mk = om[sel].astype(np.int64)
+            bits = ((mk[:, None] >> np.arange(nT)[None, :]) & 1).astype(bool)
+            best = ot[sel]
+            bc = costs[np.arange(costs.shape[0]), best]
+            others = np.where(bits, costs, np.inf)
+            others[np.arange(costs.shape[0]), best] = np.inf
+            untied = np.all(others > (bc * (1 + 2 * tol))[:, None], axis=1)
+            stats["tidx_checked"] += int(untied.sum())
+            stats["tidx_tied"] += int((~untied).sum())
+            bad = np.nonzero(untied & (gt != best))[0]
+            assert bad.size == 0, f"row {i}: tidx differs at j={gj[bad[:5]]}: {gt[bad[:5]]} vs {best[bad[:5]]}"
     return stats
 
 
