@@ -252,6 +252,30 @@ int plan_refine(plan_ctx* ctx, int S, const float* P, const float* T, const floa
                 const int32_t* nrows, int rmax, const plan_refine_weights* weights, const float* grad_loss,
                 float* loss, float* dP, float* dT);
 
+/* One query of a batched search. */
+typedef struct {
+    int N;
+    const void* states;      /* device [N][n] */
+    plan_edges edges;        /* device CSR of this query */
+    double start_pos[4];     /* host, first m used */
+    double goal_pos[4];
+    int32_t* path;           /* device [path_cap] */
+    int path_cap;
+    int32_t* path_len;       /* device [1] */
+    double* cost;            /* device [1] */
+    int32_t* status;         /* device [1]: OK, NO_PATH, CAPACITY (path_len = needed), TIMEOUT, INVALID_ARG */
+} plan_search_query;
+
+/*
+ * Batched findPath: the same computation as plan_search for many queries, one
+ * 1024-thread block per query (block barriers, no grid barrier).  Per-query
+ * outcomes go to each query's status word; NO_PATH is not a batch error.
+ * plan_prepare_search_batched uploads the descriptors (may allocate/wait);
+ * plan_search_batched only launches (capturable in a CUDA graph).
+ */
+int plan_prepare_search_batched(plan_ctx* ctx, int Q, const plan_search_query* queries);
+int plan_search_batched(plan_ctx* ctx);
+
 /* Synchronise the context stream, return the device status of the work
  * issued since the previous plan_wait, and fill *info (may be NULL). */
 int plan_wait(plan_ctx* ctx, plan_info* info);

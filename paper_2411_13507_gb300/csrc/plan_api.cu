@@ -53,6 +53,17 @@ struct plan_ctx {
     bool stage_live = false;
     std::vector<char> last_stage;
     int tile = 0, ctas_per_sm = 0;    // pair-kernel configuration (0 = default)
+    // batched search
+    int sQ = 0;
+    long long sTotN = 0;
+    int sMaxN = 0;
+    SearchQueryDesc* d_sqd = nullptr;
+    long long capSQ = -1;
+    char* h_sstage = nullptr;
+    size_t sstage_cap = 0;
+    cudaEvent_t sstage_ev = nullptr;
+    bool sstage_live = false;
+    std::vector<char> last_sstage;
     // host-sized scratch
     long long capN = -1, capK = -1, capR = -1, capW = -1, capL = -1;
     uint32_t* memMask = nullptr;
@@ -323,6 +334,7 @@ int plan_create(plan_ctx** out, const plan_model* model, void* cuda_stream) {
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_info, sizeof(DevInfo));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->tab_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->sstage_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();
         plan_destroy(c);
@@ -339,7 +351,7 @@ void plan_destroy(plan_ctx* c) {
     void* dev[] = {c->d_tab64, c->d_tab32, c->d_info, c->memMask, c->counts, c->members, c->localIdx, c->centers,
                    c->blim64, c->A32, c->blim32, c->bc32, c->resOff, c->itemOff, c->ntile, c->tsize, c->rowCount,
                    c->resBits, c->resKey, c->emitPre, c->recheck, c->sdist, c->sbest, c->spred, c->sfront,
-                   c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem};
+                   c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem, c->d_sqd};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_tab64) cudaFreeHost(c->h_tab64);
@@ -347,6 +359,8 @@ void plan_destroy(plan_ctx* c) {
     if (c->h_info) cudaFreeHost(c->h_info);
     if (c->h_stage) cudaFreeHost(c->h_stage);
     if (c->stage_ev) cudaEventDestroy(c->stage_ev);
+    if (c->h_sstage) cudaFreeHost(c->h_sstage);
+    if (c->sstage_ev) cudaEventDestroy(c->sstage_ev);
     if (c->tab_ev) cudaEventDestroy(c->tab_ev);
     for (auto& pr : c->ev_pair) {
         cudaEventDestroy(pr.first);
@@ -726,6 +740,114 @@ int plan_search(plan_ctx* c, int N, const void* states, const plan_edges* edges,
     if (c->timing) cudaEventRecord(e1, c->stream);
     c->launches += launches;
     if (ce != 0) return cuda_fail(c, (cudaError_t)ce, "search launch");
+    return PLAN_OK;
+}
+
+int plan_prepare_search_batched(plan_ctx* c, int Q, const plan_search_query* qs) {
+    if (!c) return PLAN_ERR_INVALID_ARG;
+    if (Q < 1 || Q > 65535 || !qs) return fail(c, PLAN_ERR_INVALID_ARG, "need 1..65535 queries");
+    std::vector<SearchQueryDesc> hq(Q);
+    long long tot = 0;
+    int maxN = 0;
+    for (int q = 0; q < Q; ++q) {
+        const plan_search_query& in = qs[q];
+        if (in.N < 1 || in.N > (1 << 20) || !in.states) return fail(c, PLAN_ERR_INVALID_ARG, "need N >= 1 states");
+        const plan_edges& e = in.edges;
+        if (!e.row_off || !e.count || e.cap < 0 || (e.cap > 0 && (!e.col || !e.w)))
+            return fail(c, PLAN_ERR_INVALID_ARG, "bad CSR");
+        if (!in.path || in.path_cap < 1 || !in.path_len || !in.cost || !in.status)
+            return fail(c, PLAN_ERR_INVALID_ARG, "bad search output");
+        for (int a2 = 0; a2 < c->model.m; ++a2)
+            if (!std::isfinite(in.start_pos[a2]) || !std::isfinite(in.goal_pos[a2]))
+                return fail(c, PLAN_ERR_INVALID_ARG, "start/goal must be finite");
+        SearchQueryDesc& d = hq[q];
+        memset(&d, 0, sizeof(d));
+        d.N = in.N;
+        d.off = tot;
+        d.states = in.states;
+        d.row_off = e.row_off;
+        d.col = e.col;
+        d.w = e.w;
+        d.count = e.count;
+        d.cap = e.cap;
+        for (int a2 = 0; a2 < 4; ++a2) {
+            d.start[a2] = a2 < c->model.m ? in.start_pos[a2] : 0.0;
+            d.goal[a2] = a2 < c->model.m ? in.goal_pos[a2] : 0.0;
+        }
+        d.path = in.path;
+        d.path_cap = in.path_cap;
+        d.path_len = in.path_len;
+        d.cost = in.cost;
+        d.status = in.status;
+        tot += in.N;
+        if (in.N > maxN) maxN = in.N;
+    }
+    if (tot > c->capS) {
+        if (!dalloc(c, &c->sdist, tot) || !dalloc(c, &c->sbest, tot) || !dalloc(c, &c->spred, tot) ||
+            !dalloc(c, &c->sfront, 2LL * tot))
+            return PLAN_ERR_NO_MEMORY;
+        c->capS = tot;
+    }
+    if (Q > c->capSQ) {
+        if (c->sstage_live) cudaEventSynchronize(c->sstage_ev);
+        if (!dalloc(c, &c->d_sqd, Q)) return PLAN_ERR_NO_MEMORY;
+        c->capSQ = Q;
+        c->last_sstage.clear();
+    }
+    const size_t bytes = sizeof(SearchQueryDesc) * Q;
+    std::vector<char> blob(bytes);
+    memcpy(blob.data(), hq.data(), bytes);
+    if (blob != c->last_sstage) {
+        if (c->sstage_live) cudaEventSynchronize(c->sstage_ev);
+        if (bytes > c->sstage_cap) {
+            if (c->h_sstage) cudaFreeHost(c->h_sstage);
+            c->h_sstage = nullptr;
+            c->sstage_cap = 0;
+            if (cudaMallocHost((void**)&c->h_sstage, bytes) != cudaSuccess) return fail(c, PLAN_ERR_NO_MEMORY, "stage");
+            c->sstage_cap = bytes;
+        }
+        memcpy(c->h_sstage, blob.data(), bytes);
+        cudaError_t e = cudaMemcpyAsync(c->d_sqd, c->h_sstage, bytes, cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "search descriptor upload");
+        cudaEventRecord(c->sstage_ev, c->stream);
+        c->sstage_live = true;
+        c->last_sstage.swap(blob);
+    }
+    c->sQ = Q;
+    c->sTotN = tot;
+    c->sMaxN = maxN;
+    return PLAN_OK;
+}
+
+int plan_search_batched(plan_ctx* c) {
+    if (!c) return PLAN_ERR_INVALID_ARG;
+    if (c->sQ < 1) return fail(c, PLAN_ERR_INVALID_ARG, "no prepared search batch");
+    BatchSearchParams B;
+    memset(&B, 0, sizeof(B));
+    B.Q = c->sQ;
+    B.m = c->model.m;
+    B.n = c->model.m * c->model.gamma;
+    B.in_f32 = c->model.input == PLAN_IN_F32;
+    B.w_f64 = c->model.arith == PLAN_F64;
+    B.max_sweeps = c->max_sweeps > 0 ? c->max_sweeps : c->sMaxN + 1;
+    B.qd = c->d_sqd;
+    B.dist = c->sdist;
+    B.bestU = c->sbest;
+    B.pred = c->spred;
+    B.front = c->sfront;
+    B.info = c->d_info;
+    int launches = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->timing) {
+        e0 = take_event(c);
+        e1 = take_event(c);
+        c->ev_search.emplace_back(e0, e1);
+        cudaEventRecord(e0, c->stream);
+    }
+    int ce = launch_search_batched(B, c->stream, &launches);
+    if (c->timing) cudaEventRecord(e1, c->stream);
+    c->launches += launches;
+    if (ce != 0) return cuda_fail(c, (cudaError_t)ce, "batched search launch");
     return PLAN_OK;
 }
 

@@ -1315,10 +1315,13 @@ int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_s
         k_prep<<<(unsigned)((P.totRows + 255) / 256), 256, 0, st>>>(P);
         ++*launches;
     }
-    if (P.totMask > 0 && P.totPoly > 0) {
+    if (P.totMask > 0) {  // also writes the (zero) masks of queries without polytopes
         k_member<<<(unsigned)((P.totMask + 255) / 256), 256, 0, st>>>(P);
+        ++*launches;
+    }
+    if (P.totPoly > 0) {
         k_lists<<<(unsigned)P.totPoly, 1024, 0, st>>>(P);
-        *launches += 2;
+        ++*launches;
     }
     k_setup<<<P.Q, 1024, 0, st>>>(P);
     k_batch<<<1, 1024, 0, st>>>(P);

@@ -177,6 +177,34 @@ struct SearchParams {
     long long spin_limit;
 };
 
+// One query of a batched search (device array).
+struct SearchQueryDesc {
+    int N, pad;
+    long long off;             // scratch offset (prefix of N)
+    const void* states;
+    const int32_t* row_off;
+    const int32_t* col;
+    const void* w;
+    const int64_t* count;
+    long long cap;
+    double start[4], goal[4];
+    int32_t* path;
+    int path_cap, pad2;
+    int32_t* path_len;
+    double* cost;
+    int32_t* status;           // per-query plan_status (OK, NO_PATH, CAPACITY, TIMEOUT, INVALID_ARG)
+};
+
+struct BatchSearchParams {
+    int Q, m, n, in_f32, w_f64, max_sweeps;
+    const SearchQueryDesc* qd;
+    unsigned long long* dist;
+    unsigned long long* bestU;
+    int* pred;
+    unsigned char* front;      // [2 * total N]
+    DevInfo* info;
+};
+
 struct RefineParams {
     long long S;
     int m, g, p, rmax;
@@ -197,6 +225,7 @@ struct RefineParams {
 int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_sm, void* ev_pair_begin,
                  void* ev_pair_end, int* launches);
 int launch_search(const SearchParams& P, void* stream, int num_sms, int* launches);
+int launch_search_batched(const BatchSearchParams& P, void* stream, int* launches);
 int launch_account(const BuildParams& P, void* stream, int num_sms, unsigned long long* work);
 bool model_supported(int m, int g, int p);
 bool refine_supported(int m, int g, int p);

@@ -238,6 +238,176 @@ __global__ void __launch_bounds__(256) k_search(SearchParams P) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Batched search: one 1024-thread CTA per query; the same phases as k_search
+// with block barriers in place of the grid barrier.  Per-query status: OK,
+// NO_PATH (path_len 0, cost +inf), CAPACITY (path longer than path_cap;
+// path_len = the length needed), TIMEOUT (sweep bound), INVALID_ARG.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_search_batched(BatchSearchParams B) {
+    const SearchQueryDesc& Q = B.qd[blockIdx.x];
+    const int N = Q.N;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    unsigned long long* dist = B.dist + Q.off;
+    unsigned long long* best = B.bestU + Q.off;
+    int* pred = B.pred + Q.off;
+    unsigned char* front = B.front + 2 * Q.off;
+    __shared__ unsigned long long s_nd[2];
+    __shared__ int s_id[2];
+    __shared__ int s_changed;
+    __shared__ int s_bad;
+    if (tid == 0) {
+        s_nd[0] = s_nd[1] = ~0ull;
+        s_id[0] = s_id[1] = 0x7fffffff;
+        s_bad = 0;
+        const long long E = *Q.count;
+        if (N < 1 || E < 0 || E > Q.cap) s_bad = 1;
+    }
+    for (int v = tid; v < N; v += blockDim.x) {
+        dist[v] = DINF;
+        best[v] = ~0ull;
+        pred[v] = 0x7fffffff;
+        front[v] = 0;
+        front[N + v] = 0;
+    }
+    __syncthreads();
+    if (s_bad) {
+        if (tid == 0) {
+            *Q.status = PLAN_ERR_INVALID_ARG;
+            if (N >= 1) *Q.path_len = 0;
+        }
+        return;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int v = tid; v < N; v += blockDim.x) {
+            double ds = 0.0, dg = 0.0;
+            for (int a = 0; a < B.m; ++a) {
+                const double x = ldd(Q.states, (long long)v * B.n + a, B.in_f32);
+                const double ts = __dsub_rn(x, Q.start[a]);
+                const double tg = __dsub_rn(x, Q.goal[a]);
+                ds = __dadd_rn(ds, __dmul_rn(ts, ts));
+                dg = __dadd_rn(dg, __dmul_rn(tg, tg));
+            }
+            const unsigned long long bs = (unsigned long long)__double_as_longlong(ds);
+            const unsigned long long bg = (unsigned long long)__double_as_longlong(dg);
+            if (pass == 0) {
+                atomicMin(&s_nd[0], bs);
+                atomicMin(&s_nd[1], bg);
+            } else {
+                if (bs == s_nd[0]) atomicMin(&s_id[0], v);
+                if (bg == s_nd[1]) atomicMin(&s_id[1], v);
+            }
+        }
+        __syncthreads();
+    }
+    const int s = s_id[0], g = s_id[1];
+    if (tid == 0) {
+        dist[s] = 0ull;
+        front[s] = 1;
+    }
+    int cur = 0, it = 0;
+    volatile unsigned long long* vdist = dist;
+    for (;;) {
+        if (tid == 0) s_changed = 0;
+        __syncthreads();
+        bool my_change = false;
+        for (int v = wid; v < N; v += nw) {
+            if (!front[cur * N + v]) continue;
+            __syncwarp();
+            if (lane == 0) front[cur * N + v] = 0;
+            const double dv = __longlong_as_double((long long)vdist[v]);
+            const long long e0 = Q.row_off[v], e1 = Q.row_off[v + 1];
+            for (long long e = e0 + lane; e < e1; e += 32) {
+                const int u = Q.col[e];
+                if (u < 0 || u >= N) continue;
+                const double w = B.w_f64 ? ((const double*)Q.w)[e] : (double)((const float*)Q.w)[e];
+                const unsigned long long nd = (unsigned long long)__double_as_longlong(__dadd_rn(dv, w));
+                const unsigned long long old = atomicMin(&dist[u], nd);
+                if (nd < old) {
+                    front[(cur ^ 1) * N + u] = 1;
+                    my_change = true;
+                }
+            }
+        }
+        if (__any_sync(0xffffffffu, my_change) && lane == 0) s_changed = 1;
+        __syncthreads();
+        const int ch = s_changed;
+        ++it;
+        if (!ch) break;
+        if (it > B.max_sweeps) {
+            if (tid == 0) {
+                *Q.status = PLAN_ERR_TIMEOUT;
+                *Q.path_len = 0;
+            }
+            return;
+        }
+        cur ^= 1;
+        __syncthreads();
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int v = wid; v < N; v += nw) {
+            const unsigned long long dvb = vdist[v];
+            if (dvb >= DINF) continue;
+            const double dv = __longlong_as_double((long long)dvb);
+            const long long e0 = Q.row_off[v], e1 = Q.row_off[v + 1];
+            for (long long e = e0 + lane; e < e1; e += 32) {
+                const int u = Q.col[e];
+                if (u < 0 || u >= N || u == s) continue;
+                const double w = B.w_f64 ? ((const double*)Q.w)[e] : (double)((const float*)Q.w)[e];
+                const unsigned long long nd = (unsigned long long)__double_as_longlong(__dadd_rn(dv, w));
+                if (nd != vdist[u]) continue;
+                if (pass == 0) atomicMin(&best[u], dvb);
+                else if (best[u] == dvb) atomicMin(&pred[u], v);
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const unsigned long long dg = vdist[g];
+        int st = PLAN_OK;
+        if (dg >= DINF) {
+            *Q.path_len = 0;
+            *Q.cost = __longlong_as_double((long long)DINF);
+            st = PLAN_ERR_NO_PATH;
+        } else {
+            int len = 1, v = g;
+            bool okw = true;
+            while (v != s) {
+                v = pred[v];
+                if (v < 0 || v >= N || len > N) {
+                    okw = false;
+                    break;
+                }
+                ++len;
+            }
+            if (!okw) {
+                st = PLAN_ERR_INVALID_ARG;
+                *Q.path_len = 0;
+            } else if (len > Q.path_cap) {
+                st = PLAN_ERR_CAPACITY;
+                *Q.path_len = len;
+            } else {
+                v = g;
+                for (int q = len - 1; q >= 0; --q) {
+                    Q.path[q] = v;
+                    if (q) v = pred[v];
+                }
+                *Q.path_len = len;
+            }
+            *Q.cost = __longlong_as_double((long long)dg);
+        }
+        *Q.status = st;
+        atomicAdd(&B.info->search_iters, (unsigned long long)it);
+    }
+}
+
+int launch_search_batched(const BatchSearchParams& P, void* stream, int* launches) {
+    if (P.Q <= 0) return 0;
+    k_search_batched<<<P.Q, 1024, 0, (cudaStream_t)stream>>>(P);
+    ++*launches;
+    return (int)cudaGetLastError();
+}
+
 int launch_search(const SearchParams& P, void* stream, int num_sms, int* launches) {
     cudaStream_t st = (cudaStream_t)stream;
     int occ = 0;

@@ -59,13 +59,20 @@ class _Query(ctypes.Structure):
                 ("A", ctypes.c_void_p), ("b", ctypes.c_void_p), ("out", _Edges)]
 
 
+class _SearchQuery(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("states", ctypes.c_void_p), ("edges", _Edges),
+                ("start_pos", ctypes.c_double * 4), ("goal_pos", ctypes.c_double * 4),
+                ("path", ctypes.c_void_p), ("path_cap", ctypes.c_int), ("path_len", ctypes.c_void_p),
+                ("cost", ctypes.c_void_p), ("status", ctypes.c_void_p)]
+
+
 class _RefineW(ctypes.Structure):
     _fields_ = [("w_snap", ctypes.c_double), ("mu", ctypes.c_double), ("delta", ctypes.c_double)]
 
 
 EXPORTS = ["plan_create", "plan_destroy", "plan_build_edges", "plan_search", "plan_wait", "plan_model_tables",
            "plan_set_search_limits", "plan_refine", "plan_prepare_batched", "plan_build_edges_batched",
-           "plan_set_tile", "plan_autotune", "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
+           "plan_set_tile", "plan_autotune", "plan_prepare_search_batched", "plan_search_batched", "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
 
 
 def lib_path() -> str:
@@ -102,6 +109,10 @@ def load(build_if_stale: bool = True):
     lib.plan_prepare_batched.restype = i32
     lib.plan_build_edges_batched.argtypes = [vp]
     lib.plan_build_edges_batched.restype = i32
+    lib.plan_prepare_search_batched.argtypes = [vp, i32, ctypes.POINTER(_SearchQuery)]
+    lib.plan_prepare_search_batched.restype = i32
+    lib.plan_search_batched.argtypes = [vp]
+    lib.plan_search_batched.restype = i32
     lib.plan_set_tile.argtypes = [vp, i32, i32]
     lib.plan_set_tile.restype = i32
     lib.plan_autotune.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), dp]
@@ -374,6 +385,47 @@ class Planner:
                 continue
             raise self._err(st, "build_batched")
         raise self._err(PLAN_ERR_CAPACITY, "build_batched: capacity retries exhausted")
+
+    def prepare_search_batched(self, dps, graphs, outs) -> None:
+        qs = (_SearchQuery * len(dps))()
+        for q, (dp, g, o) in enumerate(zip(dps, graphs, outs)):
+            sp = (ctypes.c_double * 4)(*([float(x) for x in dp.start_pos] + [0.0] * (4 - len(dp.start_pos))))
+            gp = (ctypes.c_double * 4)(*([float(x) for x in dp.goal_pos] + [0.0] * (4 - len(dp.goal_pos))))
+            qs[q] = _SearchQuery(dp.N, dp.states.data_ptr(), g.cstruct(), sp, gp, o["path"].data_ptr(),
+                                 int(o["path"].shape[0]), o["path_len"].data_ptr(), o["cost"].data_ptr(),
+                                 o["status"].data_ptr())
+        rc = self.lib.plan_prepare_search_batched(self.ctx, len(dps), qs)
+        if rc != 0:
+            raise self._err(rc, "plan_prepare_search_batched")
+
+    def search_batched_async(self) -> None:
+        rc = self.lib.plan_search_batched(self.ctx)
+        if rc != 0:
+            raise self._err(rc, "plan_search_batched")
+
+    def alloc_search_batched(self, dps) -> list:
+        import torch
+        outs = []
+        for dp in dps:
+            o = self.alloc_search(dp.N)
+            o["status"] = torch.zeros(1, dtype=torch.int32, device=o["path"].device)
+            outs.append(o)
+        return outs
+
+    def search_batched(self, dps, graphs) -> list:
+        outs = self.alloc_search_batched(dps)
+        self.prepare_search_batched(dps, graphs, outs)
+        self.search_batched_async()
+        st = self.wait()
+        if st != PLAN_OK:
+            raise self._err(st, "search_batched")
+        res = []
+        for o in outs:
+            s = int(o["status"].item())
+            L = int(o["path_len"].item())
+            res.append({"status": s, "path": o["path"][:L].cpu().numpy().tolist() if s == PLAN_OK else None,
+                        "cost": float(o["cost"].item())})
+        return res
 
     def set_tile(self, tile: int = 0, ctas_per_sm: int = 0) -> None:
         rc = self.lib.plan_set_tile(self.ctx, int(tile), int(ctas_per_sm))

@@ -111,3 +111,25 @@ def test_autotune_choice_keeps_results(tmp_path):
         graphs3 = pl.build_batched(dps)
         for r, g in zip(ref, graphs3):
             same_graph(g.to_numpy(), r)
+
+
+def test_batched_search_matches_oracle():
+    probs = small_batch(seed=13, Q=6)
+    pl = P.Planner.for_problem(probs[0], arith="f32", input="f32")
+    dps = [P.to_device(p, input="f32") for p in probs]
+    graphs = pl.build_batched(dps)
+    res = pl.search_batched(dps, graphs)
+    kinds = []
+    for p, g, r in zip(probs, graphs, res):
+        op = oracle.OracleProblem(p)
+        csr = op.csr(with_detail=True)
+        orc = oracle.search(op, csr, p.start_pos, p.goal_pos)
+        # start/goal ids are not returned per query; the path's end points are
+        if orc["path"] is None:
+            assert r["status"] == P.PLAN_ERR_NO_PATH and r["path"] is None
+            kinds.append("no-path")
+            continue
+        assert r["status"] == P.PLAN_OK
+        kinds.append(parity.compare_search({"start": r["path"][0], "goal": r["path"][-1], "path": r["path"],
+                                            "cost": r["cost"]}, orc, csr, "f32"))
+    assert len(kinds) == 6
