@@ -143,7 +143,8 @@ int check_model(const plan_model* m) {
         if (!std::isfinite(m->bound[k]) || !(m->bound[k] - m->tighten > 0)) return PLAN_ERR_INVALID_ARG;
     if (!model_supported(m->m, m->gamma, m->degree) && !refine_supported(m->m, m->gamma, m->degree))
         return PLAN_ERR_UNSUPPORTED;
-    if (m->arith == PLAN_TF32 || m->arith == PLAN_BF16) return PLAN_ERR_UNSUPPORTED;
+    if ((m->arith == PLAN_TF32 || m->arith == PLAN_BF16) && !tc_supported(m->m, m->gamma, m->degree))
+        return PLAN_ERR_UNSUPPORTED;
     return PLAN_OK;
 }
 
@@ -531,7 +532,9 @@ int issue(plan_ctx* c) {
     P.in_f32 = c->model.input == PLAN_IN_F32;
     P.arith = c->model.arith;
     P.max_rows = c->b_max_rows;
-    P.tile = (c->model.arith == PLAN_F64) ? TILE64 : (c->tile > 0 ? c->tile : TILE);
+    P.tile = (c->model.arith == PLAN_F64) ? TILE64
+             : (c->model.arith == PLAN_F32) ? (c->tile > 0 ? c->tile : TILE)
+                                            : TILE;  // tensor-core form: 64-state tiles, 256 threads
     P.eps = c->model.tighten;
     P.qd = c->d_qd;
     P.pfxMask = c->d_pfx;

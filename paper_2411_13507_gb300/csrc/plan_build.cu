@@ -19,6 +19,7 @@
 // max in registers.  Canonical FP64 order (the definition of a bit-exact
 // result) is: each half summed left to right without FMA, then the two
 // halves added; see the FP64 kernel and the re-check kernel.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -374,6 +375,155 @@ DEVI void append_recheck(const BuildParams& P, int q, int k, int li, int lj, int
 // rows most likely to fail (highest derivative, interior) come first, and a
 // thread stops the reach loop once all its pairs have definitely failed.
 // ---------------------------------------------------------------------------
+// Pair phase of one duration for a thread's 4x4 micro-tile (shared by the
+// FP32 kernel and the tensor-core kernel): reach rows (add, |.|, max) with an
+// early stop once all 16 pairs definitely fail, free rows (add, max), cost of
+// the feasible pairs; ambiguous pairs go to the FP64 re-check.
+template <int M, int G, int PD>
+DEVI void pair_phase(const BuildParams& P, const Item& itd, int t, int T, int gi, int gj, uint32_t vmask, uint32_t dmask,
+                     int nr, int DR, const float* UL, const float* UR, const float* FL, const float* FR,
+                     const float* CL, const float* CRr, const float* magR, const float* magF, float KRb, float KFb,
+                     uint32_t (&bits)[16], float (&bc)[16], int (&bt)[16], unsigned long long& rp_cnt) {
+    using S = Shape<G, PD>;
+    constexpr int RAX = S::RAX, NI = S::NI;
+    const int k = itd.k, i0 = itd.i0, j0 = itd.j0;
+    const float KR = KRb, KF = KFb;
+    {
+        float mRi[4], mRj[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            mRi[q] = magR[4 * gi + q];
+            mRj[q] = magR[T + 4 * gj + q];
+        }
+        const float bmx = KR * (fmaxf(fmaxf(mRi[0], mRi[1]), fmaxf(mRi[2], mRi[3])) +
+                                fmaxf(fmaxf(mRj[0], mRj[1]), fmaxf(mRj[2], mRj[3])));
+        float rm[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) rm[q] = ((vmask >> q) & 1u) && !((dmask >> q) & 1u) ? 0.f : __int_as_float(0x7f800000);
+        const float* ulp = UL + 4 * gi;
+        const float* urp = UR + 4 * gj;
+        bool dead = false;
+        for (int r = 0; r < RAX; ++r) {
+#pragma unroll
+            for (int a = 0; a < M; ++a) {
+                const float4 u = *reinterpret_cast<const float4*>(ulp + (r * M + a) * T);
+                const float4 w = *reinterpret_cast<const float4*>(urp + (r * M + a) * T);
+                const float uu[4] = {u.x, u.y, u.z, u.w};
+                const float ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+                    for (int qb = 0; qb < 4; ++qb) rm[qa * 4 + qb] = fmaxf(rm[qa * 4 + qb], fabsf(uu[qa] + ww[qb]));
+            }
+            if ((r & 1) == 1) {
+                float mn = rm[0];
+#pragma unroll
+                for (int q = 1; q < 16; ++q) mn = fminf(mn, rm[q]);
+                if (mn > 1.f + bmx) {
+                    dead = true;
+                    break;
+                }
+            }
+        }
+        if (!dead) {
+            uint32_t rfail = 0, rpass = 0;
+#pragma unroll
+            for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+                for (int qb = 0; qb < 4; ++qb) {
+                    const int q = qa * 4 + qb;
+                    const float band = KR * (mRi[qa] + mRj[qb]);
+                    if (!(rm[q] <= 1.f + band)) rfail |= 1u << q;
+                    else if (rm[q] <= 1.f - band) rpass |= 1u << q;
+                }
+            rpass &= vmask & ~dmask;
+            rfail |= ~vmask | dmask;
+            rfail &= 0xFFFFu;
+            rp_cnt += __popc(rpass);
+            if (rfail != 0xFFFFu) {
+                float fm[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) fm[q] = -__int_as_float(0x7f800000);
+                const float* flp = FL + 4 * gi;
+                const float* frp = FR + 4 * gj;
+                const int FRk = NI * nr;
+                for (int r = 0; r < FRk; ++r) {
+                    const float4 u = *reinterpret_cast<const float4*>(flp + r * T);
+                    const float4 w = *reinterpret_cast<const float4*>(frp + r * T);
+                    const float uu[4] = {u.x, u.y, u.z, u.w};
+                    const float ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+                        for (int qb = 0; qb < 4; ++qb) fm[qa * 4 + qb] = fmaxf(fm[qa * 4 + qb], uu[qa] + ww[qb]);
+                }
+                uint32_t ffail = 0, fpass = 0;
+                float mFi[4], mFj[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    mFi[q] = magF[4 * gi + q];
+                    mFj[q] = magF[T + 4 * gj + q];
+                }
+#pragma unroll
+                for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+                    for (int qb = 0; qb < 4; ++qb) {
+                        const int q = qa * 4 + qb;
+                        const float band = KF * (mFi[qa] + mFj[qb]);
+                        if (!(fm[q] <= band)) ffail |= 1u << q;
+                        else if (fm[q] <= -band) fpass |= 1u << q;
+                    }
+                const uint32_t feas = rpass & fpass & ~rfail & ~ffail & 0xFFFFu;
+                const uint32_t amb = ~(rfail | ffail) & ~feas & 0xFFFFu;
+                if (feas) {
+                    float cs[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) cs[q] = 0.f;
+                    const float* clp = CL + 4 * gi;
+                    const float* crp = CRr + 4 * gj;
+                    const int per_l = DR * M;
+                    for (int l = 0; l < PD; ++l) {
+                        float ss[16];
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) ss[q] = 0.f;
+                        for (int e = 0; e < per_l; ++e) {
+                            const int row = l * per_l + e;
+                            const float4 u = *reinterpret_cast<const float4*>(clp + row * T);
+                            const float4 w = *reinterpret_cast<const float4*>(crp + row * T);
+                            const float uu[4] = {u.x, u.y, u.z, u.w};
+                            const float ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                            for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+                                for (int qb = 0; qb < 4; ++qb) {
+                                    const float d = uu[qa] + ww[qb];
+                                    ss[qa * 4 + qb] = fmaf(d, d, ss[qa * 4 + qb]);
+                                }
+                        }
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) cs[q] += sqrtf(ss[q]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        if ((feas >> q) & 1u) {
+                            bits[q] |= 1u << t;
+                            if (cs[q] < bc[q]) {
+                                bc[q] = cs[q];
+                                bt[q] = t;
+                            }
+                        }
+                    }
+                }
+                if (amb) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        if ((amb >> q) & 1u) append_recheck(P, itd.q, k, i0 + 4 * gi + (q >> 2), j0 + 4 * gj + (q & 3), t);
+                }
+            }
+        }
+    }
+}
+
 template <int M, int G, int PD>
 __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
     using S = Shape<G, PD>;
@@ -563,140 +713,9 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
             }
             __syncthreads();
 
-            if (act) {
-                float mRi[4], mRj[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    mRi[q] = magR[4 * gi + q];
-                    mRj[q] = magR[T + 4 * gj + q];
-                }
-                const float bmx = KR * (fmaxf(fmaxf(mRi[0], mRi[1]), fmaxf(mRi[2], mRi[3])) +
-                                        fmaxf(fmaxf(mRj[0], mRj[1]), fmaxf(mRj[2], mRj[3])));
-                float rm[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) rm[q] = ((vmask >> q) & 1u) && !((dmask >> q) & 1u) ? 0.f : __int_as_float(0x7f800000);
-                const float* ulp = UL + 4 * gi;
-                const float* urp = UR + 4 * gj;
-                bool dead = false;
-                for (int r = 0; r < RAX; ++r) {
-#pragma unroll
-                    for (int a = 0; a < M; ++a) {
-                        const float4 u = *reinterpret_cast<const float4*>(ulp + (r * M + a) * T);
-                        const float4 w = *reinterpret_cast<const float4*>(urp + (r * M + a) * T);
-                        const float uu[4] = {u.x, u.y, u.z, u.w};
-                        const float ww[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                        for (int qa = 0; qa < 4; ++qa)
-#pragma unroll
-                            for (int qb = 0; qb < 4; ++qb) rm[qa * 4 + qb] = fmaxf(rm[qa * 4 + qb], fabsf(uu[qa] + ww[qb]));
-                    }
-                    if ((r & 1) == 1) {
-                        float mn = rm[0];
-#pragma unroll
-                        for (int q = 1; q < 16; ++q) mn = fminf(mn, rm[q]);
-                        if (mn > 1.f + bmx) {
-                            dead = true;
-                            break;
-                        }
-                    }
-                }
-                if (!dead) {
-                    uint32_t rfail = 0, rpass = 0;
-#pragma unroll
-                    for (int qa = 0; qa < 4; ++qa)
-#pragma unroll
-                        for (int qb = 0; qb < 4; ++qb) {
-                            const int q = qa * 4 + qb;
-                            const float band = KR * (mRi[qa] + mRj[qb]);
-                            if (!(rm[q] <= 1.f + band)) rfail |= 1u << q;
-                            else if (rm[q] <= 1.f - band) rpass |= 1u << q;
-                        }
-                    rpass &= vmask & ~dmask;
-                    rfail |= ~vmask | dmask;
-                    rfail &= 0xFFFFu;
-                    rp_cnt += __popc(rpass);
-                    if (rfail != 0xFFFFu) {
-                        float fm[16];
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) fm[q] = -__int_as_float(0x7f800000);
-                        const float* flp = FL + 4 * gi;
-                        const float* frp = FR + 4 * gj;
-                        const int FRk = NI * nr;
-                        for (int r = 0; r < FRk; ++r) {
-                            const float4 u = *reinterpret_cast<const float4*>(flp + r * T);
-                            const float4 w = *reinterpret_cast<const float4*>(frp + r * T);
-                            const float uu[4] = {u.x, u.y, u.z, u.w};
-                            const float ww[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                            for (int qa = 0; qa < 4; ++qa)
-#pragma unroll
-                                for (int qb = 0; qb < 4; ++qb) fm[qa * 4 + qb] = fmaxf(fm[qa * 4 + qb], uu[qa] + ww[qb]);
-                        }
-                        uint32_t ffail = 0, fpass = 0;
-                        float mFi[4], mFj[4];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            mFi[q] = magF[4 * gi + q];
-                            mFj[q] = magF[T + 4 * gj + q];
-                        }
-#pragma unroll
-                        for (int qa = 0; qa < 4; ++qa)
-#pragma unroll
-                            for (int qb = 0; qb < 4; ++qb) {
-                                const int q = qa * 4 + qb;
-                                const float band = KF * (mFi[qa] + mFj[qb]);
-                                if (!(fm[q] <= band)) ffail |= 1u << q;
-                                else if (fm[q] <= -band) fpass |= 1u << q;
-                            }
-                        const uint32_t feas = rpass & fpass & ~rfail & ~ffail & 0xFFFFu;
-                        const uint32_t amb = ~(rfail | ffail) & ~feas & 0xFFFFu;
-                        if (feas) {
-                            float cs[16];
-#pragma unroll
-                            for (int q = 0; q < 16; ++q) cs[q] = 0.f;
-                            const float* clp = CL + 4 * gi;
-                            const float* crp = CRr + 4 * gj;
-                            const int per_l = DR * M;
-                            for (int l = 0; l < PD; ++l) {
-                                float ss[16];
-#pragma unroll
-                                for (int q = 0; q < 16; ++q) ss[q] = 0.f;
-                                for (int e = 0; e < per_l; ++e) {
-                                    const int row = l * per_l + e;
-                                    const float4 u = *reinterpret_cast<const float4*>(clp + row * T);
-                                    const float4 w = *reinterpret_cast<const float4*>(crp + row * T);
-                                    const float uu[4] = {u.x, u.y, u.z, u.w};
-                                    const float ww[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                                    for (int qa = 0; qa < 4; ++qa)
-#pragma unroll
-                                        for (int qb = 0; qb < 4; ++qb) {
-                                            const float d = uu[qa] + ww[qb];
-                                            ss[qa * 4 + qb] = fmaf(d, d, ss[qa * 4 + qb]);
-                                        }
-                                }
-#pragma unroll
-                                for (int q = 0; q < 16; ++q) cs[q] += sqrtf(ss[q]);
-                            }
-#pragma unroll
-                            for (int q = 0; q < 16; ++q) {
-                                if ((feas >> q) & 1u) {
-                                    bits[q] |= 1u << t;
-                                    if (cs[q] < bc[q]) {
-                                        bc[q] = cs[q];
-                                        bt[q] = t;
-                                    }
-                                }
-                            }
-                        }
-                        if (amb) {
-#pragma unroll
-                            for (int q = 0; q < 16; ++q)
-                                if ((amb >> q) & 1u) append_recheck(P, itd.q, k, i0 + 4 * gi + (q >> 2), j0 + 4 * gj + (q & 3), t);
-                        }
-                    }
-                }
-            }
+            if (act)
+                pair_phase<M, G, PD>(P, itd, t, T, gi, gj, vmask, dmask, nr, DR, UL, UR, FL, FR, CL, CRr, magR, magF, KR, KF,
+                                     bits, bc, bt, rp_cnt);
             __syncthreads();
         }
         if (act) {
@@ -714,6 +733,400 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
         __syncthreads();
     }
     if (rp_cnt) atomicAdd(&P.info->reach_pass, rp_cnt);
+}
+
+// ---------------------------------------------------------------------------
+// Precision form: the per-state products (the halves: reach rows, polytope
+// rows of the control points, cost rows) on the 5th-generation tensor cores.
+// Per item and duration one CTA builds, in shared memory, the operand
+//   A [128 x K] : rows 0..63 the centred start states x~_i, rows 64..127 the
+//                 end states x~_j, features (c, a) and a constant 1,
+//   B [N x K]   : row n < NRp the start-half coefficients of output row n,
+//                 row NRp + n the end-half coefficients,
+// both TF32 (kind::tf32) or BF16 (kind::f16) and K-major without swizzle
+// (8-row x 16-byte core matrices; LBO = K-chunk stride, SBO = row-group
+// stride), and one thread issues tcgen05.mma (M = 128, N <= 256, FP32
+// accumulators in tensor memory) and commits to an mbarrier.  The warps read
+// the accumulators back with tcgen05.ld (warp w reads lanes 32 (w % 4) ..) and
+// scatter the halves into the same shared-memory arrays the FP32 kernel uses;
+// the pair phase is shared.  The error bands grow with the input rounding
+// (2^-11 TF32, 2^-8 BF16) and every ambiguous margin is re-checked in FP64.
+// ---------------------------------------------------------------------------
+namespace tc {
+
+DEVI uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+DEVI void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(slot)), "r"(ncols)
+                 : "memory");
+}
+DEVI void tmem_relinquish() { asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory"); }
+DEVI void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+DEVI void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+DEVI bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+DEVI void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+DEVI void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+DEVI void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+DEVI void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+template <bool BF>
+DEVI void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accumulate) {
+    if (BF)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+}
+DEVI void commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+                 : "memory");
+}
+DEVI void ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+        "[%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+// Shared-memory matrix descriptor: start >> 4 (bits 0-13), LBO >> 4 (16-29),
+// SBO >> 4 (32-45), descriptor version 1 (46-47), no swizzle (61-63 = 0).
+DEVI uint64_t desc(uint32_t saddr_bytes, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr_bytes >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+// Instruction descriptor (kind::f16 / kind::tf32): D = F32 (bits 4-5 = 1),
+// A/B format (bits 7-9, 10-12: BF16 = 1, TF32 = 2), both K-major (bits 15,
+// 16 = 0), N >> 3 (bits 17-22), M >> 4 (bits 24-28).
+DEVI uint32_t idesc(int Mdim, int Ndim, bool bf) {
+    const uint32_t fmt = bf ? 1u : 2u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(Ndim >> 3) << 17) | ((uint32_t)(Mdim >> 4) << 24);
+}
+}  // namespace tc
+
+template <int M, int G, int PD, bool BF>
+__global__ void __launch_bounds__(256, 2) k_pairs_tc(BuildParams P) {
+    using S = Shape<G, PD>;
+    constexpr int N_ = M * G, RAX = S::RAX, RR = M * RAX, NI = S::NI, TG = S::TG;
+    constexpr int KFEAT = N_ + 1;
+    constexpr int KI = BF ? 16 : 8;
+    constexpr int KP = (KFEAT + KI - 1) / KI * KI;
+    constexpr int ESZ = BF ? 2 : 4;
+    constexpr int CHUNKS = KP * ESZ / 16;
+    constexpr uint32_t LBO = 128, SBO = CHUNKS * 128;
+    constexpr int KSTEPS = KP / KI;
+    constexpr uint32_t TMEM_COLS = 256;
+    const int T = P.tile;
+    extern __shared__ __align__(1024) float sm[];
+    const int FRm = NI * P.max_rows;
+    const int DR = P.cost_mode == 1 ? 1 : G;
+    const int CRW = G * PD * M;
+    // operands first (1024-byte aligned), then the FP32 kernel's arrays
+    unsigned char* Aop = reinterpret_cast<unsigned char*>(sm);
+    const int NRcap = RR + FRm + CRW;
+    const int NRp_cap = (NRcap + 7) & ~7;
+    const int Ncap = (2 * NRp_cap + 15) & ~15;
+    unsigned char* Bop = Aop + ((128 * KP * ESZ + 1023) & ~1023);
+    float* UL = reinterpret_cast<float*>(Bop + ((Ncap * KP * ESZ + 1023) & ~1023));
+    float* UR = UL + RR * T;
+    float* FL = UR + RR * T;
+    float* FR = FL + FRm * T;
+    float* CL = FR + FRm * T;
+    float* CRr = CL + CRW * T;
+    float* magR = CRr + CRW * T;
+    float* magF = magR + 2 * T;
+    float* xs = magF + 2 * T;
+    float* xab = xs + 2 * T * N_;
+    float* tab = xab + 2 * T * G;
+    float* Ap = tab + P.L.f_stride;
+    float* bp = Ap + RMAX * M;
+    __shared__ long long s_item;
+    __shared__ float s_rown1, s_bmax;
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, lane = tid & 31;
+    const long long nitems = (long long)P.info->items;
+    const TabLayout L = P.L;
+    const float kin = BF ? 0.00390625f : 0.00048828125f;  // 2^-8, 2^-11
+    // input rounding of both factors (2 kin; 3 kin for the A (x) D coefficient)
+    // plus a generous allowance for the tensor core's FP32 accumulation
+    const float KRt = 2.f * (2.f * kin + 64.f * KU);
+    const float KFt = 2.f * (3.f * kin + 64.f * KU);
+    unsigned long long rp_cnt = 0;
+    uint32_t phase = 0;
+
+    if (warp == 0) {
+        tc::tmem_alloc(&s_tmem, TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(&s_mbar, 1);
+        tc::fence_mbar_init();
+        s_abort = 0;
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = s_tmem;
+
+    auto put = [&](unsigned char* base, int row, int k, float v) {
+        const int chunk = (k * ESZ) >> 4, within = (k * ESZ) & 15;
+        unsigned char* p = base + (row >> 3) * SBO + chunk * LBO + (row & 7) * 16 + within;
+        if (BF) {
+            *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(v);
+        } else {
+            uint32_t r;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+            *reinterpret_cast<uint32_t*>(p) = r;
+        }
+    };
+
+    for (;;) {
+        if (tid == 0) {
+            const long long it = (long long)atomicAdd(&P.info->ticket, 1u);
+            s_item = (has_failed(P.info) || s_abort) ? 0x7fffffffffffLL : it;
+        }
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= nitems) break;
+        const Item itd = item_decode(P, item);
+        const QueryDesc& Qd = P.qd[itd.q];
+        const int k = itd.k, i0 = itd.i0, j0 = itd.j0, TI = itd.TI, TJ = itd.TJ, nk = itd.nk;
+        const int ni4 = (TI + 3) & ~3, nj4 = (TJ + 3) & ~3;
+        const int r0 = Qd.poly_off[k], nr = Qd.poly_off[k + 1] - r0;
+        const int NR = RR + NI * nr + DR * PD * M;
+        const int NRp = (NR + 7) & ~7;
+        const int Ntot = (2 * NRp + 15) & ~15;
+        const long long rg0 = Qd.rowsOff + r0;
+        for (int u = tid; u < nr * M; u += nthr) Ap[u] = P.A32[rg0 * M + u];
+        for (int u = tid; u < nr; u += nthr) bp[u] = P.bc32[rg0 + u];
+        const int* members = P.members + Qd.listOff + (long long)k * Qd.N;
+        float cx[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) cx[a] = P.centers[(long long)(Qd.kOff + k) * 4 + a];
+        for (int u = tid; u < (ni4 + nj4) * N_; u += nthr) {
+            const int s = u / N_, e = u % N_;
+            const bool right = s >= ni4;
+            const int ls = right ? s - ni4 : s;
+            const int lidx = (right ? j0 : i0) + ls;
+            float v = 0.f;
+            if (ls < (right ? TJ : TI)) {
+                const long long id = members[lidx];
+                if (e < M) {
+                    if (P.in_f32) v = ((const float*)Qd.states)[id * N_ + e] - cx[e];
+                    else v = (float)(((const double*)Qd.states)[id * N_ + e] - (double)cx[e]);
+                } else {
+                    v = ldf(Qd.states, id * N_ + e, P.in_f32);
+                }
+            }
+            xs[(right ? T + ls : ls) * N_ + e] = v;
+        }
+        __syncthreads();
+        for (int s = tid; s < ni4 + nj4; s += nthr) {
+            const bool right = s >= ni4;
+            const int ls = right ? s - ni4 : s;
+            const float* x = xs + (right ? T + ls : ls) * N_;
+            float* xa = xab + (right ? T + ls : ls) * G;
+#pragma unroll
+            for (int c = 0; c < G; ++c) {
+                float mx = 0.f;
+#pragma unroll
+                for (int a = 0; a < M; ++a) mx = fmaxf(mx, fabsf(x[c * M + a]));
+                xa[c] = mx;
+            }
+        }
+        // operand A: 64 start rows, 64 end rows, features x~ then the constant 1
+        for (int u = tid; u < 128 * KP; u += nthr) {
+            const int row = u / KP, f = u % KP;
+            const bool right = row >= 64;
+            const int ls = right ? row - 64 : row;
+            float v = 0.f;
+            if (ls < (right ? nj4 : ni4)) {
+                if (f < N_) v = xs[(right ? T + ls : ls) * N_ + f];
+                else if (f == N_) v = 1.f;
+            }
+            put(Aop, row, f, v);
+        }
+        if (tid == 0) {
+            float rn = 0.f, bm = 0.f;
+            for (int r = 0; r < nr; ++r) {
+                float s1 = 0.f;
+                for (int a = 0; a < M; ++a) s1 += fabsf(Ap[r * M + a]);
+                rn = fmaxf(rn, s1);
+                bm = fmaxf(bm, fabsf(bp[r]));
+            }
+            s_rown1 = rn * 1.0001f;
+            s_bmax = bm;
+        }
+        __syncthreads();
+
+        const int ngi = ni4 >> 2, ngj = nj4 >> 2;
+        const bool act = tid < ngi * ngj;
+        const int gi = act ? tid / ngj : 0, gj = act ? tid % ngj : 0;
+        const bool diag_tile = (i0 == j0);
+        uint32_t vmask = 0, dmask = 0;
+#pragma unroll
+        for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+            for (int qb = 0; qb < 4; ++qb) {
+                const int li = 4 * gi + qa, lj = 4 * gj + qb;
+                if (act && li < TI && lj < TJ) vmask |= 1u << (qa * 4 + qb);
+                if (diag_tile && li == lj) dmask |= 1u << (qa * 4 + qb);
+            }
+        uint32_t bits[16];
+        float bc[16];
+        int bt[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            bits[q] = 0;
+            bc[q] = __int_as_float(0x7f800000);
+            bt[q] = 0;
+        }
+        for (int t = 0; t < Qd.nT; ++t) {
+            for (int u = tid; u < L.f_stride; u += nthr) tab[u] = P.tab32[(long long)(Qd.tabOff + t) * L.f_stride + u];
+            __syncthreads();
+            // operand B: coefficient rows (start halves, then end halves)
+            for (int u = tid; u < Ntot * KP; u += nthr) {
+                const int n = u / KP, f = u % KP;
+                const bool right = n >= NRp;
+                const int o = right ? n - NRp : n;
+                const int co = right ? G : 0;
+                float v = 0.f;
+                if (o < NR && f <= N_) {
+                    const int c = f / M, a = f % M;
+                    if (o < RR) {  // reach row (r, axis)
+                        const int r = o / M, ra = o % M;
+                        if (f < N_ && a == ra) v = tab[L.f_H + r * TG + co + c];
+                    } else if (o < RR + NI * nr) {  // free row (l, polytope row)
+                        const int q = o - RR, l = q / nr, rr = q % nr;
+                        if (f < N_) v = Ap[rr * M + a] * tab[L.f_D + l * TG + co + c];
+                        else if (!right) v = -bp[rr];
+                    } else {  // cost row ((l, d), axis)
+                        const int q = o - RR - NI * nr;
+                        const int la = q / M, ca = q % M, l = la / DR, d = la % DR;
+                        if (f < N_ && a == ca) v = tab[L.f_C + (d * PD + l) * TG + co + c];
+                    }
+                }
+                put(Bop, n, f, v);
+            }
+            for (int s = tid; s < ni4 + nj4; s += nthr) {
+                const bool right = s >= ni4;
+                const int ls = right ? s - ni4 : s;
+                const float* xa = xab + (right ? T + ls : ls) * G;
+                float mr = 0.f, md = 0.f;
+#pragma unroll
+                for (int c = 0; c < G; ++c) {
+                    mr = fmaf(tab[L.f_HC + (right ? G : 0) + c], xa[c], mr);
+                    md = fmaf(tab[L.f_DC + (right ? G : 0) + c], xa[c], md);
+                }
+                magR[(right ? T : 0) + ls] = mr;
+                magF[(right ? T : 0) + ls] = md * s_rown1 + (right ? 0.f : s_bmax);
+            }
+            tc::fence_async_smem();
+            tc::fence_before();
+            __syncthreads();
+            tc::fence_after();
+            if (tid == 0) {
+                const uint32_t id = tc::idesc(128, Ntot, BF);
+#pragma unroll
+                for (int st = 0; st < KSTEPS; ++st) {
+                    const uint64_t ad = tc::desc(tc::saddr(Aop) + st * 2 * LBO, LBO, SBO);
+                    const uint64_t bd = tc::desc(tc::saddr(Bop) + st * 2 * LBO, LBO, SBO);
+                    tc::mma<BF>(tbase, ad, bd, id, st > 0 ? 1u : 0u);
+                }
+                tc::commit(&s_mbar);
+            }
+            {
+                long long spins = 0;
+                while (!tc::mbar_try_wait(&s_mbar, phase)) {
+                    if (++spins > (1LL << 26)) {
+                        set_status(P.info, PLAN_ERR_TIMEOUT, DET_BARRIER);
+                        s_abort = 1;
+                        break;
+                    }
+                }
+                phase ^= 1u;
+            }
+            tc::fence_after();
+            // accumulators -> halves: warp w reads lanes 32 (w % 4) + lane
+            {
+                const int quarter = warp & 3;
+                const int row = quarter * 32 + lane;
+                const bool right = row >= 64;
+                const int ls = right ? row - 64 : row;
+                const bool live = ls < (right ? nj4 : ni4);
+                const int c0 = right ? NRp : 0;
+                const int nchunk = (NR + 15) >> 4;
+                for (int ch = (warp >> 2); ch < nchunk; ch += (nthr >> 7)) {
+                    float v[16];
+                    tc::ld16(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(c0 + ch * 16), v);
+                    if (live) {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const int o = ch * 16 + q;
+                            if (o >= NR) break;
+                            if (o < RR) {
+                                (right ? UR : UL)[o * T + ls] = v[q];
+                            } else if (o < RR + NI * nr) {
+                                (right ? FR : FL)[(o - RR) * T + ls] = v[q];
+                            } else {
+                                (right ? CRr : CL)[(o - RR - NI * nr) * T + ls] = v[q];
+                            }
+                        }
+                    }
+                }
+            }
+            tc::fence_before();
+            __syncthreads();
+            if (act)
+                pair_phase<M, G, PD>(P, itd, t, T, gi, gj, vmask, dmask, nr, DR, UL, UR, FL, FR, CL, CRr, magR, magF,
+                                     KRt, KFt, bits, bc, bt, rp_cnt);
+            __syncthreads();
+        }
+        if (act) {
+            const long long base = itd.base;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                if (!((vmask >> q) & 1u)) continue;
+                const int li = i0 + 4 * gi + (q >> 2), lj = j0 + 4 * gj + (q & 3);
+                const long long slot = base + (long long)li * nk + lj;
+                const bool dg = (dmask >> q) & 1u;
+                P.resBits[slot] = dg ? 0u : bits[q];
+                P.resKey[slot] = (dg || !bits[q]) ? KEY_NONE : key_f32(bc[q], bt[q]);
+            }
+        }
+        __syncthreads();
+    }
+    if (rp_cnt) atomicAdd(&P.info->reach_pass, rp_cnt);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 0) tc::tmem_dealloc(tbase, TMEM_COLS);
 }
 
 // ---------------------------------------------------------------------------
@@ -1272,9 +1685,45 @@ size_t smem_f64(const BuildParams& P) {
     return d * sizeof(double) + TILE64 * TILE64 * (sizeof(uint32_t) + 1) + 16;
 }
 
+template <int M, int G, int PD, bool BF>
+size_t smem_tc(const BuildParams& P) {
+    using S = Shape<G, PD>;
+    constexpr int N_ = M * G, KI = BF ? 16 : 8, KP = (N_ + 1 + KI - 1) / KI * KI, ESZ = BF ? 2 : 4;
+    const int RR = M * S::RAX, FRm = S::NI * P.max_rows, CRW = G * PD * M;
+    const int NRp = (RR + FRm + CRW + 7) & ~7, Ncap = (2 * NRp + 15) & ~15;
+    const size_t ops = (size_t)((128 * KP * ESZ + 1023) & ~1023) + (size_t)((Ncap * KP * ESZ + 1023) & ~1023);
+    return ops + smem_fast<M, G, PD>(P);
+}
+
+template <int M, int G, int PD, bool BF>
+int launch_tc(const BuildParams& P, cudaStream_t st, int num_sms, int ctas_per_sm, cudaEvent_t e0, cudaEvent_t e1,
+              int* launches) {
+    const size_t sm = smem_tc<M, G, PD, BF>(P);
+    cudaFuncSetAttribute(k_pairs_tc<M, G, PD, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pairs_tc<M, G, PD, BF>, 256, sm);
+    if (occ < 1) occ = 1;
+    if (occ > 2) occ = 2;  // two 256-column tensor-memory allocations per SM
+    if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
+    if (e0) cudaEventRecord(e0, st);
+    k_pairs_tc<M, G, PD, BF><<<num_sms * occ, 256, sm, st>>>(P);
+    if (e1) cudaEventRecord(e1, st);
+    ++*launches;
+    k_recheck<M, G, PD><<<num_sms * 4, 128, 0, st>>>(P);
+    ++*launches;
+    return (int)cudaGetLastError();
+}
+
 template <int M, int G, int PD>
 int launch_pairs(const BuildParams& P, cudaStream_t st, int num_sms, int ctas_per_sm, cudaEvent_t e0, cudaEvent_t e1,
                  int* launches) {
+    if (P.arith == PLAN_TF32 || P.arith == PLAN_BF16) {
+        if constexpr (M == 2 && G == 2) {
+            if (P.arith == PLAN_BF16) return launch_tc<M, G, PD, true>(P, st, num_sms, ctas_per_sm, e0, e1, launches);
+            return launch_tc<M, G, PD, false>(P, st, num_sms, ctas_per_sm, e0, e1, launches);
+        }
+        return (int)cudaErrorInvalidValue;
+    }
     if (P.arith == PLAN_F64) {
         const size_t sm = smem_f64<M, G, PD>(P);
         cudaFuncSetAttribute(k_pairs_f64<M, G, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1306,6 +1755,10 @@ int launch_pairs(const BuildParams& P, cudaStream_t st, int num_sms, int ctas_pe
 bool model_supported(int m, int g, int p) {
     return (m == 2 && g == 2 && (p == 3 || p == 5)) || (m == 3 && g == 3 && (p == 5 || p == 7));
 }
+
+// Tensor-core precision form: the start and end halves share one M=128 x
+// N<=256 accumulator, which the 2-D models fit.
+bool tc_supported(int m, int g, int p) { return m == 2 && g == 2 && (p == 3 || p == 5); }
 
 int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_sm, void* ev0, void* ev1, int* launches) {
     cudaStream_t st = (cudaStream_t)stream;

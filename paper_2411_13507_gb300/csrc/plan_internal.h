@@ -228,6 +228,7 @@ int launch_search(const SearchParams& P, void* stream, int num_sms, int* launche
 int launch_search_batched(const BatchSearchParams& P, void* stream, int* launches);
 int launch_account(const BuildParams& P, void* stream, int num_sms, unsigned long long* work);
 bool model_supported(int m, int g, int p);
+bool tc_supported(int m, int g, int p);
 bool refine_supported(int m, int g, int p);
 int launch_refine(const RefineParams& R, void* stream, int* launches);
 
