@@ -276,6 +276,39 @@ typedef struct {
 int plan_prepare_search_batched(plan_ctx* ctx, int Q, const plan_search_query* queries);
 int plan_search_batched(plan_ctx* ctx);
 
+/*
+ * plan_search_noalloc -- the search of plan_search for callers that cannot
+ * allocate device memory while they plan.  The paper has no counterpart; it is
+ * a deployment variant.  Typical callers: a replanning loop with a hard
+ * per-tick deadline (cudaMalloc/cudaFree may block, and cudaFree synchronises
+ * the whole device), code issuing work while a stream is being captured into
+ * a CUDA graph, and processes whose device memory belongs to a pool allocator.
+ *
+ * No context is needed and nothing is allocated: all scratch (status word,
+ * grid-barrier counters, distance / predecessor / frontier arrays) lives in
+ * one static device array sized for N <= 65536 vertices (about 1.4 MB, held by
+ * every GPU that loads the library until the process exits).  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress) and
+ * caches it; make that first call before any stream capture.  Every call on a
+ * device shares the array and it keeps the last call's contents (the call
+ * clears the status and barrier words itself), so calls whose work overlaps on
+ * the GPU race: issue them on one stream or order them with events.
+ *
+ *   m, gamma     model (positions are the first m entries of each state)
+ *   input        PLAN_IN_F64 / PLAN_IN_F32 storage of states
+ *   w_f64        1 if edges->w holds doubles, 0 for floats
+ *   N, states, edges, start_pos, goal_pos, path, path_cap, path_len, cost:
+ *                as plan_search
+ *   status       device int32 [1]: the device status (OK, NO_PATH, TIMEOUT,
+ *                CAPACITY, INVALID_ARG), written on the stream
+ *   cuda_stream  cudaStream_t (NULL = legacy default stream)
+ * Returns PLAN_ERR_CAPACITY (before launching anything) when N > 65536,
+ * PLAN_ERR_INVALID_ARG for bad arguments, PLAN_ERR_CUDA if a launch fails.
+ */
+int plan_search_noalloc(int m, int gamma, int input, int w_f64, int N, const void* states, const plan_edges* edges,
+                        const double* start_pos, const double* goal_pos, int32_t* path, int path_cap,
+                        int32_t* path_len, double* cost, int32_t* status, void* cuda_stream);
+
 /* Synchronise the context stream, return the device status of the work
  * issued since the previous plan_wait, and fill *info (may be NULL). */
 int plan_wait(plan_ctx* ctx, plan_info* info);

@@ -14,6 +14,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cmath>
+#include <cstring>
+#include <mutex>
 
 #include "plan_internal.h"
 
@@ -422,4 +425,112 @@ int launch_search(const SearchParams& P, void* stream, int num_sms, int* launche
     return (int)e;
 }
 
+// ---------------------------------------------------------------------------
+// Search that allocates nothing (plan_search_noalloc).
+//
+// Some callers cannot allocate device memory when they plan: a replanning
+// loop that must answer within a few milliseconds (cudaMalloc and cudaFree
+// can block and cudaFree synchronises the device), code that runs while a
+// stream is being captured into a CUDA graph, or a process whose device
+// memory is owned entirely by a pool allocator.  This variant of the search
+// keeps all of its scratch -- the status word and grid-barrier counters, the
+// distance, predecessor and frontier arrays -- in one file-scope __device__
+// array sized for NOALLOC_MAX_N vertices (about 1.4 MB), which every GPU that
+// loads the library holds until the process exits.  The caller passes only
+// inputs and outputs.
+// ---------------------------------------------------------------------------
+constexpr int NOALLOC_MAX_N = 65536;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+struct NoAllocScratch {
+    DevInfo info;
+    unsigned long long dist[NOALLOC_MAX_N];
+    unsigned long long best[NOALLOC_MAX_N];
+    int pred[NOALLOC_MAX_N];
+    unsigned char front[2 * NOALLOC_MAX_N];
+};
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device.  The symbol's
+// name is only a host-side stand-in; the address is looked up once per device
+// (with that device current) and cached.
+cudaError_t noalloc_scratch(NoAllocScratch** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = reinterpret_cast<NoAllocScratch*>(g_noalloc_addr[dev]);
+    return cudaSuccess;
+}
+}  // namespace
+
 }  // namespace plan
+
+extern "C" int plan_search_noalloc(int m, int gamma, int input, int w_f64, int N, const void* states,
+                                   const plan_edges* edges, const double* start_pos, const double* goal_pos,
+                                   int32_t* path, int path_cap, int32_t* path_len, double* cost, int32_t* status,
+                                   void* cuda_stream) {
+    using namespace plan;
+    if (m < 1 || m > 4 || gamma < 1 || gamma > 4 || (input != PLAN_IN_F64 && input != PLAN_IN_F32)) return PLAN_ERR_INVALID_ARG;
+    if (N < 1 || !states || !edges || !edges->row_off || !edges->count || edges->cap < 0 ||
+        (edges->cap > 0 && (!edges->col || !edges->w)))
+        return PLAN_ERR_INVALID_ARG;
+    if (!start_pos || !goal_pos || !path || path_cap < 1 || !path_len || !cost || !status) return PLAN_ERR_INVALID_ARG;
+    for (int a = 0; a < m; ++a)
+        if (!std::isfinite(start_pos[a]) || !std::isfinite(goal_pos[a])) return PLAN_ERR_INVALID_ARG;
+    if (N > NOALLOC_MAX_N) return PLAN_ERR_CAPACITY;  // more vertices than the static scratch holds
+    NoAllocScratch* scr = nullptr;
+    if (noalloc_scratch(&scr) != cudaSuccess) return PLAN_ERR_CUDA;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PLAN_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // the status word and the grid-barrier counters must start at zero; the
+    // kernel initialises the per-vertex arrays itself
+    if (cudaMemsetAsync(&scr->info, 0, sizeof(DevInfo), st) != cudaSuccess) return PLAN_ERR_CUDA;
+    SearchParams S;
+    memset(&S, 0, sizeof(S));
+    S.N = N;
+    S.m = m;
+    S.n = m * gamma;
+    S.in_f32 = input == PLAN_IN_F32;
+    S.w_f64 = w_f64 != 0;
+    S.states = states;
+    S.row_off = edges->row_off;
+    S.col = edges->col;
+    S.w = edges->w;
+    S.count = edges->count;
+    S.cap = edges->cap;
+    for (int a = 0; a < m; ++a) {
+        S.start[a] = start_pos[a];
+        S.goal[a] = goal_pos[a];
+    }
+    S.dist = scr->dist;
+    S.bestU = scr->best;
+    S.pred = scr->pred;
+    S.front = scr->front;
+    S.path = path;
+    S.path_cap = path_cap;
+    S.path_len = path_len;
+    S.cost = cost;
+    S.info = &scr->info;
+    S.max_sweeps = N + 1;
+    S.spin_limit = 1LL << 24;
+    int launches = 0;
+    if (launch_search(S, st, sms, &launches) != 0) return PLAN_ERR_CUDA;
+    if (cudaMemcpyAsync(status, &scr->info.status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return PLAN_ERR_CUDA;
+    return PLAN_OK;
+}

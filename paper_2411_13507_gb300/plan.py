@@ -72,7 +72,8 @@ class _RefineW(ctypes.Structure):
 
 EXPORTS = ["plan_create", "plan_destroy", "plan_build_edges", "plan_search", "plan_wait", "plan_model_tables",
            "plan_set_search_limits", "plan_refine", "plan_prepare_batched", "plan_build_edges_batched",
-           "plan_set_tile", "plan_autotune", "plan_prepare_search_batched", "plan_search_batched", "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
+           "plan_set_tile", "plan_autotune", "plan_prepare_search_batched", "plan_search_batched",
+           "plan_search_noalloc", "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
 
 
 def lib_path() -> str:
@@ -113,6 +114,8 @@ def load(build_if_stale: bool = True):
     lib.plan_prepare_search_batched.restype = i32
     lib.plan_search_batched.argtypes = [vp]
     lib.plan_search_batched.restype = i32
+    lib.plan_search_noalloc.argtypes = [i32, i32, i32, i32, i32, vp, ctypes.POINTER(_Edges), dp, dp, vp, i32, vp, vp, vp, vp]
+    lib.plan_search_noalloc.restype = i32
     lib.plan_set_tile.argtypes = [vp, i32, i32]
     lib.plan_set_tile.restype = i32
     lib.plan_autotune.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), dp]
@@ -161,6 +164,25 @@ def model_tables(gamma: int, degree: int, T: Sequence[float]):
     if rc != 0:
         raise PlanError(rc)
     return {"D": D, "H": H, "C": C}
+
+
+def search_noalloc(m: int, gamma: int, input: str, w_f64: bool, dp, graph, start_pos, goal_pos, out: dict,
+                   stream=None) -> int:
+    """plan_search_noalloc through the C ABI: a search that allocates no device
+    memory (its scratch is a static device array of the library, N <= 65536).
+    ``out`` holds device tensors path, path_len, cost and an int32 status.
+    Returns the host status of the call; the device status lands in out["status"]."""
+    import torch
+    lib = load()
+    sp = np.ascontiguousarray(np.asarray(start_pos, dtype=np.float64))
+    gp = np.ascontiguousarray(np.asarray(goal_pos, dtype=np.float64))
+    st = stream if stream is not None else torch.cuda.current_stream()
+    dptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return lib.plan_search_noalloc(int(m), int(gamma), INPUT[input], 1 if w_f64 else 0, int(dp.N),
+                                   ctypes.c_void_p(dp.states.data_ptr()), ctypes.byref(graph.cstruct()), dptr(sp), dptr(gp),
+                                   ctypes.c_void_p(out["path"].data_ptr()), int(out["path"].shape[0]),
+                                   ctypes.c_void_p(out["path_len"].data_ptr()), ctypes.c_void_p(out["cost"].data_ptr()),
+                                   ctypes.c_void_p(out["status"].data_ptr()), ctypes.c_void_p(st.cuda_stream))
 
 
 @dataclass
