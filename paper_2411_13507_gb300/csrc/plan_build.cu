@@ -736,8 +736,9 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
 }
 
 // ---------------------------------------------------------------------------
-// Precision form: the per-state products (the halves: reach rows, polytope
-// rows of the control points, cost rows) on the 5th-generation tensor cores.
+// Precision form: the per-state products H xi and A p (the halves of the reach
+// rows and of the polytope rows of the control points) on the 5th-generation
+// tensor cores; the cost halves stay FP32 FMAs (computed while the MMA runs).
 // Per item and duration one CTA builds, in shared memory, the operand
 //   A [128 x K] : rows 0..63 the centred start states x~_i, rows 64..127 the
 //                 end states x~_j, features (c, a) and a constant 1,
@@ -846,7 +847,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_tc(BuildParams P) {
     const int CRW = G * PD * M;
     // operands first (1024-byte aligned), then the FP32 kernel's arrays
     unsigned char* Aop = reinterpret_cast<unsigned char*>(sm);
-    const int NRcap = RR + FRm + CRW;
+    const int NRcap = RR + FRm;  // reach and free rows go through the tensor cores
     const int NRp_cap = (NRcap + 7) & ~7;
     const int Ncap = (2 * NRp_cap + 15) & ~15;
     unsigned char* Bop = Aop + ((128 * KP * ESZ + 1023) & ~1023);
@@ -919,7 +920,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_tc(BuildParams P) {
         const int k = itd.k, i0 = itd.i0, j0 = itd.j0, TI = itd.TI, TJ = itd.TJ, nk = itd.nk;
         const int ni4 = (TI + 3) & ~3, nj4 = (TJ + 3) & ~3;
         const int r0 = Qd.poly_off[k], nr = Qd.poly_off[k + 1] - r0;
-        const int NR = RR + NI * nr + DR * PD * M;
+        const int NR = RR + NI * nr;
         const int NRp = (NR + 7) & ~7;
         const int Ntot = (2 * NRp + 15) & ~15;
         const long long rg0 = Qd.rowsOff + r0;
@@ -1022,14 +1023,10 @@ __global__ void __launch_bounds__(256, 2) k_pairs_tc(BuildParams P) {
                     if (o < RR) {  // reach row (r, axis)
                         const int r = o / M, ra = o % M;
                         if (f < N_ && a == ra) v = tab[L.f_H + r * TG + co + c];
-                    } else if (o < RR + NI * nr) {  // free row (l, polytope row)
+                    } else {  // free row (l, polytope row)
                         const int q = o - RR, l = q / nr, rr = q % nr;
                         if (f < N_) v = Ap[rr * M + a] * tab[L.f_D + l * TG + co + c];
                         else if (!right) v = -bp[rr];
-                    } else {  // cost row ((l, d), axis)
-                        const int q = o - RR - NI * nr;
-                        const int la = q / M, ca = q % M, l = la / DR, d = la % DR;
-                        if (f < N_ && a == ca) v = tab[L.f_C + (d * PD + l) * TG + co + c];
                     }
                 }
                 put(Bop, n, f, v);
@@ -1061,6 +1058,26 @@ __global__ void __launch_bounds__(256, 2) k_pairs_tc(BuildParams P) {
                 }
                 tc::commit(&s_mbar);
             }
+            // cost halves stay FP32 (FMA), computed while the MMA runs
+            for (int u = tid; u < (ni4 + nj4) * M; u += nthr) {
+                const int s = u / M, a = u % M;
+                const bool right = s >= ni4;
+                const int ls = right ? s - ni4 : s;
+                const float* x = xs + (right ? T + ls : ls) * N_;
+                float xc[G];
+#pragma unroll
+                for (int c = 0; c < G; ++c) xc[c] = x[c * M + a];
+                const int co = right ? G : 0;
+                float* dC = right ? CRr : CL;
+                for (int d = 0; d < DR; ++d)
+                    for (int l = 0; l < PD; ++l) {
+                        const float* cc = tab + L.f_C + (d * PD + l) * TG + co;
+                        float v = cc[0] * xc[0];
+#pragma unroll
+                        for (int c = 1; c < G; ++c) v = fmaf(cc[c], xc[c], v);
+                        dC[((l * DR + d) * M + a) * T + ls] = v;
+                    }
+            }
             {
                 long long spins = 0;
                 while (!tc::mbar_try_wait(&s_mbar, phase)) {
@@ -1090,13 +1107,8 @@ __global__ void __launch_bounds__(256, 2) k_pairs_tc(BuildParams P) {
                         for (int q = 0; q < 16; ++q) {
                             const int o = ch * 16 + q;
                             if (o >= NR) break;
-                            if (o < RR) {
-                                (right ? UR : UL)[o * T + ls] = v[q];
-                            } else if (o < RR + NI * nr) {
-                                (right ? FR : FL)[(o - RR) * T + ls] = v[q];
-                            } else {
-                                (right ? CRr : CL)[(o - RR - NI * nr) * T + ls] = v[q];
-                            }
+                            if (o < RR) (right ? UR : UL)[o * T + ls] = v[q];
+                            else (right ? FR : FL)[(o - RR) * T + ls] = v[q];
                         }
                     }
                 }
@@ -1689,8 +1701,8 @@ template <int M, int G, int PD, bool BF>
 size_t smem_tc(const BuildParams& P) {
     using S = Shape<G, PD>;
     constexpr int N_ = M * G, KI = BF ? 16 : 8, KP = (N_ + 1 + KI - 1) / KI * KI, ESZ = BF ? 2 : 4;
-    const int RR = M * S::RAX, FRm = S::NI * P.max_rows, CRW = G * PD * M;
-    const int NRp = (RR + FRm + CRW + 7) & ~7, Ncap = (2 * NRp + 15) & ~15;
+    const int RR = M * S::RAX, FRm = S::NI * P.max_rows;
+    const int NRp = (RR + FRm + 7) & ~7, Ncap = (2 * NRp + 15) & ~15;
     const size_t ops = (size_t)((128 * KP * ESZ + 1023) & ~1023) + (size_t)((Ncap * KP * ESZ + 1023) & ~1023);
     return ops + smem_fast<M, G, PD>(P);
 }
