@@ -185,12 +185,13 @@ typedef struct {
 int plan_prepare_batched(plan_ctx* ctx, int Q, const plan_query* queries, int max_rows);
 int plan_build_edges_batched(plan_ctx* ctx);
 
-/* Pair-kernel configuration: tile side (8..64, multiple of 4; 0 = 64) and
- * CTAs per SM (0 = as many as fit).  plan_autotune times every candidate on
- * the prepared batch (reps launches each, synchronising) and keeps the
- * fastest; it reports the choice and its mean pair-kernel time. */
-int plan_set_tile(plan_ctx* ctx, int tile, int ctas_per_sm);
-int plan_autotune(plan_ctx* ctx, int reps, int* best_tile, int* best_ctas, double* best_ms);
+/* FP32 pair-kernel configuration: tile side (8..64, multiple of 4; 0 = 64),
+ * CTAs per SM (0 = as many as fit) and duration chunks per tile (work items
+ * are tiles x chunks, longest durations first; 0 = 4).  plan_autotune times
+ * every candidate on the prepared batch (reps launches each, synchronising)
+ * and keeps the fastest; it reports the choice and its mean pair-kernel time. */
+int plan_set_tile(plan_ctx* ctx, int tile, int ctas_per_sm, int tchunks);
+int plan_autotune(plan_ctx* ctx, int reps, int* best_tile, int* best_ctas, int* best_chunks, double* best_ms);
 
 /*
  * findPath (Alg. 1 line 4, Sec. III-C, Problem 2): the start and goal vertices

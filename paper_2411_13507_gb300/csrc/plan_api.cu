@@ -40,7 +40,7 @@ struct plan_ctx {
     std::vector<QueryDesc> hq;
     std::vector<long long> pfx;       // 4 x (Q+1): mask, poly, rows, N
     long long totMask = 0, totPoly = 0, totRows = 0, totN = 0, totList = 0, totK1 = 0;
-    int maxK = 0;
+    int maxK = 0, maxN = 0;
     std::vector<double> Tall;
     QueryDesc* d_qd = nullptr;
     long long* d_pfx = nullptr;
@@ -53,6 +53,7 @@ struct plan_ctx {
     bool stage_live = false;
     std::vector<char> last_stage;
     int tile = 0, ctas_per_sm = 0;    // pair-kernel configuration (0 = default)
+    int tchunks = 0;                  // duration chunks per tile (0 = default 4)
     // batched search
     int sQ = 0;
     long long sTotN = 0;
@@ -411,7 +412,7 @@ int prepare(plan_ctx* c, int Q, const plan_query* qs, int max_rows) {
     std::vector<long long> pfx(4 * (size_t)(Q + 1), 0);
     std::vector<double> Tall;
     long long mask = 0, poly = 0, rows = 0, nrow = 0, list = 0, k1 = 0;
-    int maxK = 0;
+    int maxK = 0, maxN = 0;
     for (int q = 0; q < Q; ++q) {
         const plan_query& in = qs[q];
         QueryDesc& d = hq[q];
@@ -449,6 +450,7 @@ int prepare(plan_ctx* c, int Q, const plan_query* qs, int max_rows) {
         list += (long long)in.K * in.N;
         k1 += in.K + 1;
         if (in.K > maxK) maxK = in.K;
+        if (in.N > maxN) maxN = in.N;
     }
     pfx[0 * (Q + 1) + Q] = mask;
     pfx[1 * (Q + 1) + Q] = poly;
@@ -509,6 +511,7 @@ int prepare(plan_ctx* c, int Q, const plan_query* qs, int max_rows) {
     c->totList = list;
     c->totK1 = k1;
     c->maxK = maxK;
+    c->maxN = maxN;
     c->last_nT = Q == 1 ? qs[0].nT : 0;
     return PLAN_OK;
 }
@@ -525,6 +528,7 @@ int issue(plan_ctx* c) {
     memset(&P, 0, sizeof(P));
     P.Q = Q;
     P.maxK = c->maxK;
+    P.maxN = c->maxN;
     P.m = c->model.m;
     P.g = c->model.gamma;
     P.p = c->model.degree;
@@ -535,6 +539,7 @@ int issue(plan_ctx* c) {
     P.tile = (c->model.arith == PLAN_F64) ? TILE64
              : (c->model.arith == PLAN_F32) ? (c->tile > 0 ? c->tile : TILE)
                                             : TILE;  // tensor-core form: 64-state tiles, 256 threads
+    P.tchunks = (c->model.arith == PLAN_F64) ? 1 : (c->tchunks > 0 ? c->tchunks : 4);
     P.eps = c->model.tighten;
     P.qd = c->d_qd;
     P.pfxMask = c->d_pfx;
@@ -622,31 +627,37 @@ int plan_build_edges_batched(plan_ctx* c) {
     return issue(c);
 }
 
-int plan_set_tile(plan_ctx* c, int tile, int ctas_per_sm) {
-    if (!c || tile < 0 || ctas_per_sm < 0 || ctas_per_sm > 8) return PLAN_ERR_INVALID_ARG;
+int plan_set_tile(plan_ctx* c, int tile, int ctas_per_sm, int tchunks) {
+    if (!c || tile < 0 || ctas_per_sm < 0 || ctas_per_sm > 8 || tchunks < 0 || tchunks > NT_MAX)
+        return PLAN_ERR_INVALID_ARG;
     if (tile != 0 && (tile < 8 || tile > TILE || (tile & 3))) return fail(c, PLAN_ERR_INVALID_ARG, "tile must be 8..64, multiple of 4");
     c->tile = tile;
     c->ctas_per_sm = ctas_per_sm;
+    c->tchunks = tchunks;
     return PLAN_OK;
 }
 
-int plan_autotune(plan_ctx* c, int reps, int* best_tile, int* best_ctas, double* best_ms) {
+int plan_autotune(plan_ctx* c, int reps, int* best_tile, int* best_ctas, int* best_chunks, double* best_ms) {
     if (!c || reps < 1) return PLAN_ERR_INVALID_ARG;
     if (c->bQ < 1) return fail(c, PLAN_ERR_INVALID_ARG, "prepare a batch first");
-    if (c->model.arith == PLAN_F64) {
-        if (best_tile) *best_tile = TILE64;
+    if (c->model.arith != PLAN_F32) {  // the FP64 and tensor-core kernels have fixed tiles
+        if (best_tile) *best_tile = c->model.arith == PLAN_F64 ? TILE64 : TILE;
         if (best_ctas) *best_ctas = 0;
+        if (best_chunks) *best_chunks = c->model.arith == PLAN_F64 ? 1 : 4;
         return PLAN_OK;
     }
     const bool was_timing = c->timing;
-    const int tiles[] = {32, 40, 48, 56, 64};
-    const int ctas[] = {0, 1, 2, 3, 4};
+    const int tiles[] = {32, 48, 64};
+    const int ctas[] = {0, 1};
+    const int chunks[] = {1, 2, 4, 8};
     double best = 1e30;
-    int bt = TILE, bc = 0;
+    int bt = TILE, bc = 0, bk = 4;
     for (int cc : ctas)
+        for (int ch : chunks)
         for (int t : tiles) {
             c->tile = t;
             c->ctas_per_sm = cc;
+            c->tchunks = ch;
             // one untimed run sizes the scratch for this configuration
             for (int tries = 0; tries < 4; ++tries) {
                 int rc = issue(c);
@@ -674,12 +685,15 @@ int plan_autotune(plan_ctx* c, int reps, int* best_tile, int* best_ctas, double*
                 best = ms;
                 bt = t;
                 bc = cc;
+                bk = ch;
             }
         }
     c->tile = bt;
     c->ctas_per_sm = bc;
+    c->tchunks = bk;
     if (best_tile) *best_tile = bt;
     if (best_ctas) *best_ctas = bc;
+    if (best_chunks) *best_chunks = bk;
     if (best_ms) *best_ms = best;
     return PLAN_OK;
 }

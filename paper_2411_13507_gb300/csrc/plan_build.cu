@@ -112,7 +112,8 @@ __global__ void k_prep(BuildParams P) {
 // row (canonical FP64 decision; FP32 first, FP64 only inside the band).
 // ---------------------------------------------------------------------------
 __global__ void k_member(BuildParams P) {
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;  // one warp per (state, word)
+    const int lane = threadIdx.x & 31;
     if (t >= P.totMask || has_failed(P.info)) return;
     const int q = find_q(P.pfxMask, P.Q, t);
     const QueryDesc& Q = P.qd[q];
@@ -125,13 +126,11 @@ __global__ void k_member(BuildParams P) {
         x64[a] = ldv(Q.states, (long long)i * n + a, P.in_f32);
         x32[a] = (float)x64[a];
     }
-    uint32_t word = 0;
-    const int kend = min(32, Q.K - w * 32);
-    for (int kk = 0; kk < kend; ++kk) {
-        const int k = w * 32 + kk;
+    const int k = w * 32 + lane;  // this lane's polytope
+    bool in = k < Q.K;
+    if (in) {
         const int r0 = Q.poly_off[k], r1 = Q.poly_off[k + 1];
-        if (r1 - r0 > P.max_rows || r1 > Q.K * P.max_rows || r0 < 0) continue;
-        bool in = true;
+        if (r1 - r0 > P.max_rows || r1 > Q.K * P.max_rows || r0 < 0) in = false;
         for (int r = r0; r < r1 && in; ++r) {
             const long long rg = Q.rowsOff + r;
             float s = 0.f, mag = 0.f;
@@ -154,9 +153,9 @@ __global__ void k_member(BuildParams P) {
                 }
             }
         }
-        if (in) word |= 1u << kk;
     }
-    P.memMask[Q.maskOff + (long long)i * Q.W + w] = word;
+    const uint32_t word = __ballot_sync(0xffffffffu, in);
+    if (lane == 0) P.memMask[Q.maskOff + (long long)i * Q.W + w] = word;
 }
 
 // ---------------------------------------------------------------------------
@@ -318,7 +317,7 @@ __global__ void __launch_bounds__(1024) k_batch(BuildParams P) {
         P.qSlot[0] = 0;
         P.qItem[0] = 0;
         P.info->slots = cs;
-        P.info->items = ci;
+        P.info->items = ci * P.tchunks;
         if (cs > P.slotCap) {
             P.info->need_slots = cs;
             set_status(P.info, PLAN_ERR_CAPACITY, DET_SLOTS);
@@ -356,6 +355,37 @@ DEVI Item item_decode(const BuildParams& P, long long item) {
     return it;
 }
 
+// Work item of the FP32 / tensor-core kernels: a tile and a chunk of
+// durations [t0, t1).  Chunks of the longest durations (where pairs survive
+// the reach test and the free and cost rows run) come first, so the costly
+// items start early and the short ones fill the tail.
+struct ItemT {
+    Item it;
+    int t0, t1;
+};
+
+DEVI ItemT item_decode_chunk(const BuildParams& P, long long item) {
+    const long long tiles = P.qItem[P.Q];
+    const int c = P.tchunks - 1 - (int)(item / tiles);
+    ItemT r;
+    r.it = item_decode(P, item % tiles);
+    const int nT = P.qd[r.it.q].nT;
+    r.t0 = (c * nT) / P.tchunks;
+    r.t1 = ((c + 1) * nT) / P.tchunks;
+    return r;
+}
+
+// Slots start empty (no feasible duration, no key); the pair kernels merge
+// into them with atomics.
+__global__ void k_zero_slots(BuildParams P) {
+    if (has_failed(P.info)) return;
+    const long long n = (long long)P.info->slots;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        P.resBits[s] = 0u;
+        P.resKey[s] = KEY_NONE;
+    }
+}
+
 // Re-check entry: query (16 bits) | polytope (10) | li (16) | lj (16) | T (5).
 DEVI void append_recheck(const BuildParams& P, int q, int k, int li, int lj, int t) {
     const unsigned long long idx = atomicAdd(&P.info->rechecks, 1ull);
@@ -383,7 +413,7 @@ template <int M, int G, int PD>
 DEVI void pair_phase(const BuildParams& P, const Item& itd, int t, int T, int gi, int gj, uint32_t vmask, uint32_t dmask,
                      int nr, int DR, const float* UL, const float* UR, const float* FL, const float* FR,
                      const float* CL, const float* CRr, const float* magR, const float* magF, float KRb, float KFb,
-                     uint32_t (&bits)[16], float (&bc)[16], int (&bt)[16], unsigned long long& rp_cnt) {
+                     unsigned long long& rp_cnt) {
     using S = Shape<G, PD>;
     constexpr int RAX = S::RAX, NI = S::NI;
     const int k = itd.k, i0 = itd.i0, j0 = itd.j0;
@@ -506,11 +536,10 @@ DEVI void pair_phase(const BuildParams& P, const Item& itd, int t, int T, int gi
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         if ((feas >> q) & 1u) {
-                            bits[q] |= 1u << t;
-                            if (cs[q] < bc[q]) {
-                                bc[q] = cs[q];
-                                bt[q] = t;
-                            }
+                            const long long slot =
+                                itd.base + (long long)(i0 + 4 * gi + (q >> 2)) * itd.nk + (j0 + 4 * gj + (q & 3));
+                            atomicOr(&P.resBits[slot], 1u << t);
+                            atomicMin(&P.resKey[slot], key_f32(cs[q], t));
                         }
                     }
                 }
@@ -543,8 +572,8 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
     float* magF = magR + 2 * T;
     float* xs = magF + 2 * T;
     float* xab = xs + 2 * T * N_;
-    float* tab = xab + 2 * T * G;
-    float* Ap = tab + P.L.f_stride;
+    float* tabs = xab + 2 * T * G;       // two duration tables (double buffer)
+    float* Ap = tabs + 2 * P.L.f_stride;
     float* bp = Ap + RMAX * M;
     __shared__ long long s_item;
     __shared__ float s_rown1, s_bmax;
@@ -562,7 +591,12 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
         __syncthreads();
         const long long item = s_item;
         if (item >= nitems) break;
-        const Item itd = item_decode(P, item);
+        const ItemT itc = item_decode_chunk(P, item);
+        const Item& itd = itc.it;
+        if (itc.t0 >= itc.t1) {  // empty chunk (nT < number of chunks)
+            __syncthreads();     // everyone has read s_item before it is rewritten
+            continue;
+        }
         const QueryDesc& Qd = P.qd[itd.q];
         const int k = itd.k, i0 = itd.i0, j0 = itd.j0, TI = itd.TI, TJ = itd.TJ, nk = itd.nk;
         const int ni4 = (TI + 3) & ~3, nj4 = (TJ + 3) & ~3;
@@ -631,19 +665,10 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
                 if (act && li < TI && lj < TJ) vmask |= 1u << (qa * 4 + qb);
                 if (diag_tile && li == lj) dmask |= 1u << (qa * 4 + qb);
             }
-        uint32_t bits[16];
-        float bc[16];
-        int bt[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            bits[q] = 0;
-            bc[q] = __int_as_float(0x7f800000);
-            bt[q] = 0;
-        }
-
-        for (int t = 0; t < Qd.nT; ++t) {
-            for (int u = tid; u < L.f_stride; u += nthr) tab[u] = P.tab32[(long long)(Qd.tabOff + t) * L.f_stride + u];
-            __syncthreads();
+        for (int u = tid; u < L.f_stride; u += nthr) tabs[u] = P.tab32[(long long)(Qd.tabOff + itc.t0) * L.f_stride + u];
+        __syncthreads();
+        for (int t = itc.t0; t < itc.t1; ++t) {
+            const float* tab = tabs + ((t - itc.t0) & 1) * L.f_stride;
             // reach and cost halves: one unit per (state, axis)
             for (int u = tid; u < (ni4 + nj4) * M; u += nthr) {
                 const int s = u / M, a = u % M;
@@ -713,24 +738,16 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
             }
             __syncthreads();
 
+            // the next duration's table goes to the other buffer while the pairs run
+            if (t + 1 < itc.t1) {
+                float* nxt = tabs + ((t + 1 - itc.t0) & 1) * L.f_stride;
+                for (int u = tid; u < L.f_stride; u += nthr) nxt[u] = P.tab32[(long long)(Qd.tabOff + t + 1) * L.f_stride + u];
+            }
             if (act)
                 pair_phase<M, G, PD>(P, itd, t, T, gi, gj, vmask, dmask, nr, DR, UL, UR, FL, FR, CL, CRr, magR, magF, KR, KF,
-                                     bits, bc, bt, rp_cnt);
+                                     rp_cnt);
             __syncthreads();
         }
-        if (act) {
-            const long long base = itd.base;
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                if (!((vmask >> q) & 1u)) continue;
-                const int li = i0 + 4 * gi + (q >> 2), lj = j0 + 4 * gj + (q & 3);
-                const long long slot = base + (long long)li * nk + lj;
-                const bool dg = (dmask >> q) & 1u;
-                P.resBits[slot] = dg ? 0u : bits[q];
-                P.resKey[slot] = (dg || !bits[q]) ? KEY_NONE : key_f32(bc[q], bt[q]);
-            }
-        }
-        __syncthreads();
     }
     if (rp_cnt) atomicAdd(&P.info->reach_pass, rp_cnt);
 }
@@ -915,7 +932,12 @@ __global__ void __launch_bounds__(256, 2) k_pairs_tc(BuildParams P) {
         __syncthreads();
         const long long item = s_item;
         if (item >= nitems) break;
-        const Item itd = item_decode(P, item);
+        const ItemT itc = item_decode_chunk(P, item);
+        const Item& itd = itc.it;
+        if (itc.t0 >= itc.t1) {
+            __syncthreads();
+            continue;
+        }
         const QueryDesc& Qd = P.qd[itd.q];
         const int k = itd.k, i0 = itd.i0, j0 = itd.j0, TI = itd.TI, TJ = itd.TJ, nk = itd.nk;
         const int ni4 = (TI + 3) & ~3, nj4 = (TJ + 3) & ~3;
@@ -999,16 +1021,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_tc(BuildParams P) {
                 if (act && li < TI && lj < TJ) vmask |= 1u << (qa * 4 + qb);
                 if (diag_tile && li == lj) dmask |= 1u << (qa * 4 + qb);
             }
-        uint32_t bits[16];
-        float bc[16];
-        int bt[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            bits[q] = 0;
-            bc[q] = __int_as_float(0x7f800000);
-            bt[q] = 0;
-        }
-        for (int t = 0; t < Qd.nT; ++t) {
+        for (int t = itc.t0; t < itc.t1; ++t) {
             for (int u = tid; u < L.f_stride; u += nthr) tab[u] = P.tab32[(long long)(Qd.tabOff + t) * L.f_stride + u];
             __syncthreads();
             // operand B: coefficient rows (start halves, then end halves)
@@ -1117,22 +1130,9 @@ __global__ void __launch_bounds__(256, 2) k_pairs_tc(BuildParams P) {
             __syncthreads();
             if (act)
                 pair_phase<M, G, PD>(P, itd, t, T, gi, gj, vmask, dmask, nr, DR, UL, UR, FL, FR, CL, CRr, magR, magF,
-                                     KRt, KFt, bits, bc, bt, rp_cnt);
+                                     KRt, KFt, rp_cnt);
             __syncthreads();
         }
-        if (act) {
-            const long long base = itd.base;
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                if (!((vmask >> q) & 1u)) continue;
-                const int li = i0 + 4 * gi + (q >> 2), lj = j0 + 4 * gj + (q & 3);
-                const long long slot = base + (long long)li * nk + lj;
-                const bool dg = (dmask >> q) & 1u;
-                P.resBits[slot] = dg ? 0u : bits[q];
-                P.resKey[slot] = (dg || !bits[q]) ? KEY_NONE : key_f32(bc[q], bt[q]);
-            }
-        }
-        __syncthreads();
     }
     if (rp_cnt) atomicAdd(&P.info->reach_pass, rp_cnt);
     tc::fence_before();
@@ -1308,13 +1308,17 @@ __global__ void __launch_bounds__(256) k_pairs_f64(BuildParams P) {
 // ---------------------------------------------------------------------------
 template <int M, int G, int PD>
 __global__ void k_recheck(BuildParams P) {
+    // one warp per entry; lanes take the rows (each row in canonical order)
     using S = Shape<G, PD>;
     constexpr int N_ = M * G, RAX = S::RAX, NI = S::NI, TG = S::TG;
     if (has_failed(P.info)) return;
     const long long n = min((long long)P.info->rechecks, P.recheckCap);
     const int DR = P.cost_mode == 1 ? 1 : G;
     const TabLayout L = P.L;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long e = wid; e < n; e += nw) {
         const unsigned long long en = P.recheck[e];
         const int t = (int)(en & 31ull), lj = (int)((en >> 5) & 0xFFFFull), li = (int)((en >> 21) & 0xFFFFull);
         const int k = (int)((en >> 37) & 0x3FFull), q = (int)(en >> 47);
@@ -1330,43 +1334,45 @@ __global__ void k_recheck(BuildParams P) {
         }
         const double* tb = P.tab64 + (long long)(Q.tabOff + t) * L.e_stride;
         bool ok = true;
-        for (int r = 0; r < RAX && ok; ++r) {
-            const double lim = P.lim64[reach_order<G, PD>(r) - 1];
-            for (int a = 0; a < M; ++a) {
-                const double s = __dadd_rn(half_sum<G>(tb + L.e_H + r * TG, xi + a, M),
-                                           half_sum<G>(tb + L.e_H + r * TG + G, xj + a, M));
-                if (!(fabs(s) <= lim)) ok = false;
-            }
+        for (int u = lane; u < RAX * M; u += 32) {
+            const int r = u / M, a = u % M;
+            const double s = __dadd_rn(half_sum<G>(tb + L.e_H + r * TG, xi + a, M),
+                                       half_sum<G>(tb + L.e_H + r * TG + G, xj + a, M));
+            if (!(fabs(s) <= P.lim64[reach_order<G, PD>(r) - 1])) ok = false;
         }
-        const int r0 = Q.poly_off[k], r1 = Q.poly_off[k + 1];
-        for (int l = 1; l <= NI && ok; ++l) {
-            double pt[M];
-            for (int a = 0; a < M; ++a)
-                pt[a] = __dadd_rn(half_sum<G>(tb + L.e_D + l * TG, xi + a, M), half_sum<G>(tb + L.e_D + l * TG + G, xj + a, M));
-            for (int r = r0; r < r1; ++r) {
-                double s = 0.0;
-                for (int a = 0; a < M; ++a) s = __dadd_rn(s, __dmul_rn(ldv(Q.A, (long long)r * M + a, P.in_f32), pt[a]));
-                if (!(s <= P.blim64[Q.rowsOff + r])) {
-                    ok = false;
-                    break;
-                }
-            }
-        }
+        ok = __all_sync(0xffffffffu, ok);
         if (!ok) continue;
-        double cost = 0.0;
-        for (int l = 0; l < PD; ++l) {
+        const int r0 = Q.poly_off[k], nr = Q.poly_off[k + 1] - r0;
+        for (int u = lane; u < NI * nr; u += 32) {
+            const int l = 1 + u / nr, r = r0 + u % nr;
+            double s = 0.0;
+            for (int a = 0; a < M; ++a) {
+                const double pa = __dadd_rn(half_sum<G>(tb + L.e_D + l * TG, xi + a, M),
+                                            half_sum<G>(tb + L.e_D + l * TG + G, xj + a, M));
+                s = __dadd_rn(s, __dmul_rn(ldv(Q.A, (long long)r * M + a, P.in_f32), pa));
+            }
+            if (!(s <= P.blim64[Q.rowsOff + r])) ok = false;
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) continue;
+        double seg = 0.0;  // lane l < PD: length of control-polygon segment l
+        if (lane < PD) {
             double ss = 0.0;
             for (int d = 0; d < DR; ++d)
                 for (int a = 0; a < M; ++a) {
-                    const double v = half_sum<G>(tb + L.e_C + (d * PD + l) * TG, xi + a, M) +
-                                     half_sum<G>(tb + L.e_C + (d * PD + l) * TG + G, xj + a, M);
+                    const double v = half_sum<G>(tb + L.e_C + (d * PD + lane) * TG, xi + a, M) +
+                                     half_sum<G>(tb + L.e_C + (d * PD + lane) * TG + G, xj + a, M);
                     ss = fma(v, v, ss);
                 }
-            cost += sqrt(ss);
+            seg = sqrt(ss);
         }
-        const long long slot = P.qSlot[q] + P.resOff[Q.kOff + k] + (long long)li * nk + lj;
-        atomicOr(&P.resBits[slot], 1u << t);
-        atomicMin(&P.resKey[slot], key_f32((float)cost, t));
+        double cost = 0.0;
+        for (int l = 0; l < PD; ++l) cost += __shfl_sync(0xffffffffu, seg, l);
+        if (lane == 0) {
+            const long long slot = P.qSlot[q] + P.resOff[Q.kOff + k] + (long long)li * nk + lj;
+            atomicOr(&P.resBits[slot], 1u << t);
+            atomicMin(&P.resKey[slot], key_f32((float)cost, t));
+        }
     }
 }
 
@@ -1516,9 +1522,14 @@ DEVI int lower_bound_members(const int* mem, int n, int j) {
     return lo;
 }
 
-__global__ void k_compact_fill(BuildParams P) {
+// Rank of an emitted entry among its row's emitted ids: for a row in one
+// polytope the segment prefix; for a row in several polytopes a per-warp
+// shared-memory bitmap of the row's emitted ids (rank = prefix popcount), or,
+// for very large N, binary searches in the other segments.
+__global__ void __launch_bounds__(256) k_compact_fill(BuildParams P, int bm_words) {
+    extern __shared__ uint32_t bmem[];
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     if (warp >= P.totN || has_failed(P.info)) return;
     const int q = find_q(P.pfxN, P.Q, warp);
     const QView V(P, q);
@@ -1529,6 +1540,49 @@ __global__ void k_compact_fill(BuildParams P) {
     for (int w = 0; w < W; ++w) npoly += __popc(V.mask[(long long)i * W + w]);
     const long long rbase = Q.row_off[i];
     const bool f64 = P.arith == PLAN_F64;
+    const int nwords = (Q.N + 31) >> 5;
+    const bool use_bm = npoly > 1 && nwords <= bm_words;
+    uint32_t* bits_m = bmem + (size_t)wib * 2 * bm_words;
+    uint32_t* pre_m = bits_m + bm_words;
+    if (use_bm) {
+        for (int w = lane; w < nwords; w += 32) bits_m[w] = 0u;
+        __syncwarp();
+        for (int w = 0; w < W; ++w) {
+            uint32_t mw = V.mask[(long long)i * W + w];
+            while (mw) {
+                const int k = w * 32 + __ffs(mw) - 1;
+                mw &= mw - 1u;
+                const int nk = V.counts[k];
+                const long long base = V.seg(k, i);
+                const int* mem = V.members + (long long)k * Q.N;
+                for (int lj = lane; lj < nk; lj += 32) {
+                    const int pre = P.emitPre[base + lj];
+                    const int prev = lj > 0 ? P.emitPre[base + lj - 1] : 0;
+                    if (pre != prev) {
+                        const int j = mem[lj];
+                        atomicOr(&bits_m[j >> 5], 1u << (j & 31));
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        // exclusive prefix popcount over the words
+        const int per = (nwords + 31) >> 5;
+        const int w0 = lane * per, w1 = min(nwords, w0 + per);
+        int local = 0;
+        for (int w = w0; w < w1; ++w) local += __popc(bits_m[w]);
+        int inc = local;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        int run = inc - local;
+        for (int w = w0; w < w1; ++w) {
+            pre_m[w] = (uint32_t)run;
+            run += __popc(bits_m[w]);
+        }
+        __syncwarp();
+    }
     for (int w = 0; w < W; ++w) {
         uint32_t mw = V.mask[(long long)i * W + w];
         while (mw) {
@@ -1549,7 +1603,9 @@ __global__ void k_compact_fill(BuildParams P) {
                 unsigned long long key = P.resKey[base + lj];
                 if (ns > 1) combine(P, V, i, j, k, bits, key);
                 long long rank = prev;
-                if (npoly > 1) {
+                if (use_bm) {
+                    rank = (long long)pre_m[j >> 5] + __popc(bits_m[j >> 5] & ((1u << (j & 31)) - 1u));
+                } else if (npoly > 1) {
                     for (int w2 = 0; w2 < W; ++w2) {
                         uint32_t m2 = V.mask[(long long)i * W + w2];
                         while (m2) {
@@ -1684,7 +1740,7 @@ size_t smem_fast(const BuildParams& P) {
     using S = Shape<G, PD>;
     const int RR = M * S::RAX, FRm = S::NI * P.max_rows, CRW = G * PD * M;
     const size_t T = (size_t)P.tile;
-    size_t f = (size_t)(2 * RR + 2 * FRm + 2 * CRW + 4) * T + 2 * T * (M * G + G) + P.L.f_stride + RMAX * (M + 1);
+    size_t f = (size_t)(2 * RR + 2 * FRm + 2 * CRW + 4) * T + 2 * T * (M * G + G) + 2 * P.L.f_stride + RMAX * (M + 1);
     return f * sizeof(float);
 }
 
@@ -1721,7 +1777,7 @@ int launch_tc(const BuildParams& P, cudaStream_t st, int num_sms, int ctas_per_s
     k_pairs_tc<M, G, PD, BF><<<num_sms * occ, 256, sm, st>>>(P);
     if (e1) cudaEventRecord(e1, st);
     ++*launches;
-    k_recheck<M, G, PD><<<num_sms * 4, 128, 0, st>>>(P);
+    k_recheck<M, G, PD><<<num_sms * 4, 256, 0, st>>>(P);
     ++*launches;
     return (int)cudaGetLastError();
 }
@@ -1758,7 +1814,7 @@ int launch_pairs(const BuildParams& P, cudaStream_t st, int num_sms, int ctas_pe
         k_pairs_fast<M, G, PD><<<num_sms * occ, threads, sm, st>>>(P);
         if (e1) cudaEventRecord(e1, st);
         ++*launches;
-        k_recheck<M, G, PD><<<num_sms * 4, 128, 0, st>>>(P);
+        k_recheck<M, G, PD><<<num_sms * 4, 256, 0, st>>>(P);
         ++*launches;
     }
     return (int)cudaGetLastError();
@@ -1781,7 +1837,7 @@ int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_s
         ++*launches;
     }
     if (P.totMask > 0) {  // also writes the (zero) masks of queries without polytopes
-        k_member<<<(unsigned)((P.totMask + 255) / 256), 256, 0, st>>>(P);
+        k_member<<<(unsigned)((P.totMask * 32 + 255) / 256), 256, 0, st>>>(P);
         ++*launches;
     }
     if (P.totPoly > 0) {
@@ -1792,6 +1848,10 @@ int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_s
     k_batch<<<1, 1024, 0, st>>>(P);
     *launches += 2;
     if (P.totN > 0 && P.totPoly > 0) {
+        if (P.arith != PLAN_F64) {
+            k_zero_slots<<<num_sms * 8, 256, 0, st>>>(P);
+            ++*launches;
+        }
         int rc = 0;
         if (P.m == 2 && P.g == 2 && P.p == 3) rc = launch_pairs<2, 2, 3>(P, st, num_sms, ctas_per_sm, e0, e1, launches);
         else if (P.m == 2 && P.g == 2 && P.p == 5) rc = launch_pairs<2, 2, 5>(P, st, num_sms, ctas_per_sm, e0, e1, launches);
@@ -1809,7 +1869,11 @@ int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_s
     ++*launches;
     if (P.totN > 0 && P.totPoly > 0) {
         const long long thr = P.totN * 32;
-        k_compact_fill<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(P);
+        const int words = (P.maxN + 31) / 32;
+        const int bm_words = (words <= 1024) ? words : 0;  // bitmap ranks up to N = 32768
+        const size_t smem = (size_t)8 * 2 * bm_words * sizeof(uint32_t);
+        if (smem > 48 * 1024) cudaFuncSetAttribute(k_compact_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_compact_fill<<<(unsigned)((thr + 255) / 256), 256, smem, st>>>(P, bm_words);
         ++*launches;
     }
     return (int)cudaGetLastError();

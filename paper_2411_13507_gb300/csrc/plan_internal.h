@@ -116,9 +116,11 @@ struct QueryDesc {
 struct BuildParams {
     int Q;                     // queries in the batch
     int maxK;                  // max K over queries
+    int maxN;                  // max N over queries
     int m, g, p;
     int cost_mode, in_f32, arith, max_rows;
     int tile;                  // tile side of the pair kernel (autotuned, <= TILE)
+    int tchunks;               // duration chunks per tile (work items = tiles x tchunks)
     double eps;
     const QueryDesc* qd;       // [Q]
     const long long* pfxMask;  // [Q+1] prefix of N*W        (membership threads)
