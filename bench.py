@@ -47,6 +47,11 @@ def parse():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=0, help="rows of the oracle sample (0: auto)")
+    ap.add_argument("--form", default="plain", choices=["plain", "fp64", "tf32", "bf16", "batched", "refine"],
+                    help="plain: 3-D FP32 workload (the default line); fp64: 2-D FP64 plain method; tf32/bf16: "
+                         "precision form on the 2-D workload; batched: 256 uneven queries in one graph replay; "
+                         "refine: 65536-segment forward+backward")
+    ap.add_argument("--queries", type=int, default=256)
     return ap.parse_args()
 
 
@@ -200,10 +205,122 @@ def run_reference(args):
     return 0
 
 
+def timed(fn, stream, steps, warmup, flush=None):
+    """Device time per call (CUDA events on the stream), L2 flushed before each call."""
+    import torch
+    for _ in range(warmup):
+        if flush is not None:
+            flush.fill_(1.0)
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for s in range(steps):
+        if flush is not None:
+            flush.fill_(float(s))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms
+
+
+def run_form(args):
+    """Lines for the other configurations (precision, batching, differentiation, FP64 plain)."""
+    import torch
+    from paper_2411_13507_gb300 import plan as P
+    from paper_2411_13507_gb300 import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    line = {"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "data": "synthetic", "form": args.form}
+    with torch.cuda.stream(stream):
+        if args.form in ("fp64", "tf32", "bf16"):
+            prob = synth.double_integrator_2d(seed=1)
+            pl = P.Planner.for_problem(prob, arith=args.form, input="f64", stream=stream)
+            dp = P.to_device(prob, input="f64")
+            g = pl.build_edges(dp)
+            info = pl.info()
+            sbuf = pl.alloc_search(dp.N)
+            pl.set_timing(True)
+            pl.timing(reset=True)
+            bms = timed(lambda: pl.build_edges_async(dp, g), stream, args.steps, args.warmup, flush)
+            t = pl.timing(reset=True)
+            sms = timed(lambda: pl.search_async(dp, g, dp.start_pos, dp.goal_pos, sbuf), stream, args.steps,
+                        args.warmup, flush)
+            assert pl.wait() == P.PLAN_OK
+            checks = info["checks"]
+            line.update({"metric": "edge-feasibility checks/sec, 2-D double integrator (N=512, K=16, nT=8, p=5)",
+                         "value": checks * 1e3 / statistics.mean(bms), "unit": UNIT, "dtype": args.form,
+                         "ms_per_step": statistics.mean(bms) + statistics.mean(sms),
+                         "build_ms_per_query": statistics.mean(bms), "search_ms_per_query": statistics.mean(sms),
+                         "pair_kernel_ms": t["pair_ms"] / max(1, t["pair_launches"]),
+                         "config": {"workload": "double_integrator_2d seed 1", "checks": checks,
+                                    "rechecks": info["rechecks"], "recheck_frac": info["rechecks"] / max(1, checks),
+                                    "edges": info["edges"]}})
+        elif args.form == "batched":
+            probs = synth.batched_queries(seed=args.seed, Q=args.queries)
+            pl = P.Planner.for_problem(probs[0], arith="f32", input="f32", stream=stream)
+            dps = [P.to_device(p, input="f32") for p in probs]
+            graphs = pl.build_batched(dps)
+            info = pl.info()
+            from paper_2411_13507_gb300 import autotune
+            tune = autotune.tune(pl, f"batched{args.queries}", reps=2)
+            graphs = pl.build_batched(dps, graphs)      # re-prepare with the tuned tiles
+            outs = pl.alloc_search_batched(dps)
+            pl.prepare_search_batched(dps, graphs, outs)
+            cg = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(cg, stream=stream):
+                pl.build_batched_async()
+            sg = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(sg, stream=stream):
+                pl.search_batched_async()
+            bms = timed(cg.replay, stream, args.steps, args.warmup, flush)
+            sms = timed(sg.replay, stream, args.steps, args.warmup, flush)
+            assert pl.wait() == P.PLAN_OK
+            checks = int(info["checks"])
+            line.update({"metric": f"edge-feasibility checks/sec, {args.queries} uneven 3-D queries in one captured graph",
+                         "value": checks * 1e3 / statistics.mean(bms),
+                         "unit": UNIT, "dtype": "f32", "ms_per_step": statistics.mean(bms) + statistics.mean(sms),
+                         "build_ms_per_batch": statistics.mean(bms),
+                         "search_ms_per_query": statistics.mean(sms) / len(probs),
+                         "config": {"workload": f"batched_queries seed {args.seed}", "queries": len(probs),
+                                    "N_total": sum(p.N for p in probs), "checks": checks,
+                                    "candidates": int(info["candidates"]),
+                                    "edges": int(info["edges"]), "rechecks": int(info["rechecks"]), "autotune": tune}})
+        elif args.form == "refine":
+            from paper_2411_13507_gb300 import refine as RF
+            rb = synth.refine_segments(seed=args.seed, S=65536)
+            f = lambda x: torch.as_tensor(np.asarray(x, dtype=np.float32)).to(dev).contiguous()
+            Pt, Tt, At, bt = f(rb.P), f(rb.T), f(rb.A), f(rb.b)
+            nr = torch.as_tensor(rb.nrows, dtype=torch.int32).to(dev)
+            refiner = RF.Refiner(stream=stream)
+            up = torch.ones(Pt.shape[0], device=dev)
+
+            def fb():
+                refiner.forward(Pt, Tt, At, bt, nr)
+                refiner.backward(Pt, Tt, At, bt, nr, up)
+            ms = timed(fb, stream, args.steps, args.warmup, flush)
+            refiner.check()
+            S = Pt.shape[0]
+            line.update({"metric": "refinement segments/sec (forward + backward), 65536 degree-7 3-D segments",
+                         "value": S * 1e3 / statistics.mean(ms), "unit": "segments/s", "dtype": "f32",
+                         "ms_per_step": statistics.mean(ms),
+                         "config": {"workload": "refine_segments", "segments": S}})
+    return line
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.form != "plain":
+        line = run_form(args)
+        print(json.dumps(line), flush=True)
+        return 0
     import torch
     from paper_2411_13507_gb300 import plan as P
 

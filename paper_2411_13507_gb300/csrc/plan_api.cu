@@ -934,7 +934,7 @@ int plan_wait(plan_ctx* c, plan_info* info) {
         info->memberships = (int64_t)d.memberships;
         info->slots = (int64_t)d.slots;
         info->candidates = (int64_t)d.candidates;
-        info->checks = (int64_t)d.candidates * c->last_nT;
+        info->checks = (int64_t)d.checks;
         info->reach_pass = (int64_t)d.reach_pass;
         info->feasible = (int64_t)d.feasible;
         info->rechecks = (int64_t)d.rechecks;

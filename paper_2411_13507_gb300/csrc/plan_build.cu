@@ -71,6 +71,13 @@ struct Shape {
     static constexpr int TG = 2 * G;
 };
 
+// Member-list entries carry the state id in bits 0..30 and, in bit 31, whether
+// the state lies in more than one polytope (only then can a pair be shared by
+// several polytopes).
+constexpr int MULTI_BIT = (int)0x80000000u;
+DEVI int mem_id(int v) { return v & 0x7fffffff; }
+DEVI bool mem_multi(int v) { return v < 0; }
+
 // Largest q with pfx[q] <= x (pfx ascending, pfx[Q] > x): query of a global index.
 DEVI int find_q(const long long* pfx, int Q, long long x) {
     int lo = 0, hi = Q;
@@ -195,7 +202,9 @@ __global__ void __launch_bounds__(1024) k_lists(BuildParams P) {
         __syncthreads();
         if (mem) {
             const int pos = s_base + warpTot[wid] + pre;
-            members[pos] = i;
+            int npoly = 0;
+            for (int w2 = 0; w2 < Q.W; ++w2) npoly += __popc(P.memMask[Q.maskOff + (long long)i * Q.W + w2]);
+            members[pos] = i | (npoly > 1 ? MULTI_BIT : 0);
             localIdx[i] = pos;
         }
         __syncthreads();
@@ -208,7 +217,7 @@ __global__ void __launch_bounds__(1024) k_lists(BuildParams P) {
         const int n = P.m * P.g;
         for (int a = 0; a < 4; ++a) {
             float c = 0.f;
-            if (nk > 0 && a < P.m) c = ldf(Q.states, (long long)members[0] * n + a, P.in_f32);
+            if (nk > 0 && a < P.m) c = ldf(Q.states, (long long)mem_id(members[0]) * n + a, P.in_f32);
             s_c[a] = c;
             P.centers[(long long)(Q.kOff + k) * 4 + a] = c;
         }
@@ -615,7 +624,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
             const int lidx = (right ? j0 : i0) + ls;
             float v = 0.f;
             if (ls < (right ? TJ : TI)) {
-                const long long id = members[lidx];
+                const long long id = mem_id(members[lidx]);
                 if (e < M) {
                     if (P.in_f32) v = ((const float*)Qd.states)[id * N_ + e] - cx[e];
                     else v = (float)(((const double*)Qd.states)[id * N_ + e] - (double)cx[e]);
@@ -959,7 +968,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_tc(BuildParams P) {
             const int lidx = (right ? j0 : i0) + ls;
             float v = 0.f;
             if (ls < (right ? TJ : TI)) {
-                const long long id = members[lidx];
+                const long long id = mem_id(members[lidx]);
                 if (e < M) {
                     if (P.in_f32) v = ((const float*)Qd.states)[id * N_ + e] - cx[e];
                     else v = (float)(((const double*)Qd.states)[id * N_ + e] - (double)cx[e]);
@@ -1211,7 +1220,7 @@ __global__ void __launch_bounds__(256) k_pairs_f64(BuildParams P) {
             const int s = u / N_, e = u % N_;
             const bool right = s >= TI;
             const int ls = right ? s - TI : s;
-            const long long id = members[(right ? j0 : i0) + ls];
+            const long long id = mem_id(members[(right ? j0 : i0) + ls]);
             xs[(right ? T + ls : ls) * N_ + e] = ldv(Qd.states, id * N_ + e, P.in_f32);
         }
         for (int u = tid; u < T * T; u += nthr) {
@@ -1325,7 +1334,7 @@ __global__ void k_recheck(BuildParams P) {
         const QueryDesc& Q = P.qd[q];
         const int nk = P.counts[Q.kOff + k];
         const int* members = P.members + Q.listOff + (long long)k * Q.N;
-        const long long i = members[li], j = members[lj];
+        const long long i = mem_id(members[li]), j = mem_id(members[lj]);
         double xi[N_], xj[N_];
 #pragma unroll
         for (int c = 0; c < N_; ++c) {
@@ -1441,6 +1450,9 @@ __global__ void k_compact_count(BuildParams P) {
     const QView V(P, q);
     const int i = (int)(warp - P.pfxN[q]);
     const int W = V.Q->W;
+    int npi = 0;
+    for (int w = 0; w < W; ++w) npi += __popc(V.mask[(long long)i * W + w]);
+    const bool multi_i = npi > 1;
     long long total = 0, cand = 0, feas = 0;
     for (int w = 0; w < W; ++w) {
         uint32_t mw = V.mask[(long long)i * W + w];
@@ -1455,10 +1467,11 @@ __global__ void k_compact_count(BuildParams P) {
                 const int lj = lj0 + lane;
                 bool emitted = false;
                 if (lj < nk) {
-                    const int j = mem[lj];
+                    const int jm = mem[lj], j = mem_id(jm);
                     if (j != i) {
-                        int ns;
-                        if (owner_of(V, i, j, ns) == k) {
+                        int ns = 1;
+                        // a pair can be shared by several polytopes only if both states are
+                        if (!(multi_i && mem_multi(jm)) || owner_of(V, i, j, ns) == k) {
                             ++cand;
                             uint32_t bits = P.resBits[base + lj];
                             unsigned long long key = P.resKey[base + lj];
@@ -1481,7 +1494,10 @@ __global__ void k_compact_count(BuildParams P) {
     }
     if (lane == 0) {
         P.rowCount[V.Q->rowOff + i] = (int)total;
-        if (cand) atomicAdd(&P.info->candidates, (unsigned long long)cand);
+        if (cand) {
+            atomicAdd(&P.info->candidates, (unsigned long long)cand);
+            atomicAdd(&P.info->checks, (unsigned long long)cand * (unsigned long long)V.Q->nT);
+        }
         if (feas) atomicAdd(&P.info->feasible, (unsigned long long)feas);
     }
 }
@@ -1516,7 +1532,7 @@ DEVI int lower_bound_members(const int* mem, int n, int j) {
     int lo = 0, hi = n;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (mem[mid] < j) lo = mid + 1;
+        if (mem_id(mem[mid]) < j) lo = mid + 1;
         else hi = mid;
     }
     return lo;
@@ -1559,7 +1575,7 @@ __global__ void __launch_bounds__(256) k_compact_fill(BuildParams P, int bm_word
                     const int pre = P.emitPre[base + lj];
                     const int prev = lj > 0 ? P.emitPre[base + lj - 1] : 0;
                     if (pre != prev) {
-                        const int j = mem[lj];
+                        const int j = mem_id(mem[lj]);
                         atomicOr(&bits_m[j >> 5], 1u << (j & 31));
                     }
                 }
@@ -1592,13 +1608,13 @@ __global__ void __launch_bounds__(256) k_compact_fill(BuildParams P, int bm_word
             const long long base = V.seg(k, i);
             const int* mem = V.members + (long long)k * Q.N;
             for (int lj = lane; lj < nk; lj += 32) {
-                const int j = mem[lj];
+                const int jm = mem[lj], j = mem_id(jm);
                 if (j == i) continue;
                 const int pre = P.emitPre[base + lj];
                 const int prev = lj > 0 ? P.emitPre[base + lj - 1] : 0;
                 if (pre == prev) continue;  // not emitted here
-                int ns;
-                owner_of(V, i, j, ns);
+                int ns = 1;
+                if (npoly > 1 && mem_multi(jm)) owner_of(V, i, j, ns);
                 uint32_t bits = P.resBits[base + lj];
                 unsigned long long key = P.resKey[base + lj];
                 if (ns > 1) combine(P, V, i, j, k, bits, key);
@@ -1663,7 +1679,7 @@ __global__ void k_account(BuildParams P, unsigned long long* work) {
         if (nk == 0) continue;
         const long long loc = ls - V.resOff[k];
         const int li = (int)(loc / nk), lj = (int)(loc % nk);
-        const int i = V.members[(long long)k * Q.N + li], j = V.members[(long long)k * Q.N + lj];
+        const int i = mem_id(V.members[(long long)k * Q.N + li]), j = mem_id(V.members[(long long)k * Q.N + lj]);
         if (i == j) continue;
         int ns;
         if (owner_of(V, i, j, ns) != k) continue;

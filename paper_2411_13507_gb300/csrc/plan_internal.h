@@ -55,6 +55,7 @@ struct DevInfo {
     unsigned long long memberships;
     unsigned long long slots;
     unsigned long long candidates;
+    unsigned long long checks;       // sum over queries of candidates * nT
     unsigned long long reach_pass;
     unsigned long long feasible;
     unsigned long long rechecks;

@@ -59,7 +59,7 @@ DEVI bool grid_sync(DevInfo* info, unsigned nblocks, long long spin_limit) {
                     ok = 0;
                     break;
                 }
-                __nanosleep(100);
+                __nanosleep(32);
             }
         }
         __threadfence();
@@ -74,7 +74,7 @@ DEVI double ldd(const void* p, long long i, int f32) {
 }
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_search(SearchParams P) {
+__global__ void __launch_bounds__(1024) k_search(SearchParams P) {
     const unsigned nb = gridDim.x;
     const long long gtid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long nthr = (long long)gridDim.x * blockDim.x;
@@ -144,7 +144,9 @@ __global__ void __launch_bounds__(256) k_search(SearchParams P) {
     }
     if (!grid_sync(info, nb, P.spin_limit)) return;
 
-    // A7: frontier sweeps until no distance changes
+    // A7: frontier sweeps until no distance changes.  A relaxation reads the
+    // current dist[u] first and only then issues a non-returning atomicMin,
+    // so a warp's edge chunks need no round trip through the atomic unit.
     int cur = 0, it = 0;
     volatile unsigned long long* vdist = P.dist;
     for (;;) {
@@ -155,15 +157,30 @@ __global__ void __launch_bounds__(256) k_search(SearchParams P) {
             if (lane == 0) P.front[cur * N + v] = 0;
             const double dv = __longlong_as_double((long long)vdist[v]);
             const long long e0 = P.row_off[v], e1 = P.row_off[v + 1];
-            for (long long e = e0 + lane; e < e1; e += 32) {
-                const int u = P.col[e];
-                if (u < 0 || u >= N) continue;
-                const double w = P.w_f64 ? ((const double*)P.w)[e] : (double)((const float*)P.w)[e];
-                const unsigned long long nd = (unsigned long long)__double_as_longlong(__dadd_rn(dv, w));
-                const unsigned long long old = atomicMin(&P.dist[u], nd);
-                if (nd < old) {
-                    P.front[(cur ^ 1) * N + u] = 1;
-                    my_change = true;
+            for (long long eb = e0; eb < e1; eb += 128) {
+                int uu[4];
+                double ww[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const long long e = eb + c * 32 + lane;
+                    uu[c] = -1;
+                    if (e < e1) {
+                        uu[c] = P.col[e];
+                        ww[c] = P.w_f64 ? ((const double*)P.w)[e] : (double)((const float*)P.w)[e];
+                    }
+                }
+                unsigned long long cu[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) cu[c] = (uu[c] >= 0 && uu[c] < N) ? vdist[uu[c]] : 0ull;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (uu[c] < 0 || uu[c] >= N) continue;
+                    const unsigned long long nd = (unsigned long long)__double_as_longlong(__dadd_rn(dv, ww[c]));
+                    if (nd < cu[c]) {
+                        atomicMin(&P.dist[uu[c]], nd);
+                        P.front[(cur ^ 1) * N + uu[c]] = 1;
+                        my_change = true;
+                    }
                 }
             }
         }
@@ -414,13 +431,13 @@ int launch_search_batched(const BatchSearchParams& P, void* stream, int* launche
 int launch_search(const SearchParams& P, void* stream, int num_sms, int* launches) {
     cudaStream_t st = (cudaStream_t)stream;
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_search, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_search, 1024, 0);
     if (occ < 1) occ = 1;
     if (occ > 2) occ = 2;
     const int nb = num_sms * occ;
     SearchParams Q = P;
     void* args[] = {&Q};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_search, dim3(nb), dim3(256), args, 0, st);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_search, dim3(nb), dim3(1024), args, 0, st);
     ++*launches;
     return (int)e;
 }
