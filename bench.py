@@ -240,7 +240,8 @@ def run_form(args):
     with torch.cuda.stream(stream):
         if args.form in ("fp64", "tf32", "bf16"):
             prob = synth.double_integrator_2d(seed=1)
-            pl = P.Planner.for_problem(prob, arith=args.form, input="f64", stream=stream)
+            arith = {"fp64": "f64", "tf32": "tf32", "bf16": "bf16"}[args.form]
+            pl = P.Planner.for_problem(prob, arith=arith, input="f64", stream=stream)
             dp = P.to_device(prob, input="f64")
             g = pl.build_edges(dp)
             info = pl.info()
@@ -254,7 +255,7 @@ def run_form(args):
             assert pl.wait() == P.PLAN_OK
             checks = info["checks"]
             line.update({"metric": "edge-feasibility checks/sec, 2-D double integrator (N=512, K=16, nT=8, p=5)",
-                         "value": checks * 1e3 / statistics.mean(bms), "unit": UNIT, "dtype": args.form,
+                         "value": checks * 1e3 / statistics.mean(bms), "unit": UNIT, "dtype": arith,
                          "ms_per_step": statistics.mean(bms) + statistics.mean(sms),
                          "build_ms_per_query": statistics.mean(bms), "search_ms_per_query": statistics.mean(sms),
                          "pair_kernel_ms": t["pair_ms"] / max(1, t["pair_launches"]),
@@ -428,15 +429,9 @@ def main():
     t_step = sum(step_ms) / 1e3
     t_search = sum(search_ms) / 1e3
     t_e2e = sum(e2e_ms) / 1e3
-    if dist:
-        vals = torch.tensor([t_build, t_step, t_search, t_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-        t_build, t_step, t_search, t_e2e = vals.tolist()
-        tot = torch.tensor([checks], dtype=torch.float64, device=dev)
-        dist.all_reduce(tot)
-        checks_all = float(tot.item())
-    else:
-        checks_all = float(checks)
+    from paper_2411_13507_gb300 import shard
+    (t_build, t_step, t_search, t_e2e), checks_all = shard.aggregate(
+        [t_build, t_step, t_search, t_e2e], float(checks), dist, device=dev)
     value = checks_all * args.steps / t_build
     e2e_value = checks_all * args.steps / t_e2e
 
