@@ -435,12 +435,18 @@ def main():
     value = checks_all * args.steps / t_build
     e2e_value = checks_all * args.steps / t_e2e
 
-    # roofline of the dominant kernel (the pair kernel): ALU-bound
+    # roofline of the dominant kernel (the pair kernel): ALU-bound.  Algorithmic
+    # work per check = the dense separable form: every reach row (add, |.|,
+    # compare, min), every free row (add, max), every cost segment (n adds, n
+    # FMAs, sqrt, add); times the checks of one launch.
     peaks, peak_src = measured_peaks()
     g, p, m = prob.model.gamma, prob.model.degree, prob.model.m
     n = m * g
-    ops_per_launch = (2 * work["work_reach_rows"] + 2 * work["work_free_rows"]
-                      + work["work_costs"] * p * (2 * n + 2))
+    rax = sum(p - k + 1 for k in range(1, g + 1))
+    rows_mean = float(np.mean(np.diff(prob.poly_off)))
+    ops_per_check = 4 * m * rax + 2 * (p - 1) * rows_mean + p * (2 * n + 2)
+    ops_per_launch = ops_per_check * checks
+    sc_ops = (2 * work["work_reach_rows"] + 2 * work["work_free_rows"] + work["work_costs"] * p * (2 * n + 2))
     pair_ms = tm["pair_ms"] / max(1, tm["pair_launches"])
     achieved = ops_per_launch / (pair_ms / 1e3) / 1e12
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -462,9 +468,13 @@ def main():
                      "frac": achieved / alu_peak,
                      "traffic": counters.get("dram_bytes_per_launch") if counters else None,
                      "kernel": "k_pairs_fast<3,3,7>", "kernel_ms": pair_ms,
-                     "ops_per_launch": ops_per_launch,
+                     "ops_per_check": ops_per_check, "ops_per_launch": ops_per_launch,
+                     "work_model": "dense separable form per check (all reach, free and cost rows)",
                      "peak_note": f"FP32 lanes 152 SMs x 128 x {sm_max:.0f} MHz (unit counts and max clock; {peak_src} clock)",
-                     "work": {k: work[k] for k in ("work_reach_rows", "work_free_rows", "work_costs")}},
+                     "short_circuit": {"ops_per_launch": sc_ops, "frac": sc_ops / (pair_ms / 1e3) / 1e12 / alu_peak,
+                                       "note": "work left after the early exits (reach rows up to the first violated "
+                                               "one, free rows of reach-passing checks, costs of feasible ones)",
+                                       **{k: work[k] for k in ("work_reach_rows", "work_free_rows", "work_costs")}}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
                 "ms_per_step": 1e3 * t_e2e / args.steps},
         "cpu_baseline": ({k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")} if cpu else None),
