@@ -187,7 +187,7 @@ int plan_build_edges_batched(plan_ctx* ctx);
 
 /* FP32 pair-kernel configuration: tile side (8..64, multiple of 4; 0 = 64),
  * CTAs per SM (0 = as many as fit) and duration chunks per tile (work items
- * are tiles x chunks, longest durations first; 0 = 4).  plan_autotune times
+ * are tiles x chunks, longest durations first; 0 = 2).  plan_autotune times
  * every candidate on the prepared batch (reps launches each, synchronising)
  * and keeps the fastest; it reports the choice and its mean pair-kernel time. */
 int plan_set_tile(plan_ctx* ctx, int tile, int ctas_per_sm, int tchunks);

@@ -46,6 +46,7 @@ struct plan_ctx {
     long long* d_pfx = nullptr;
     long long* d_qSlot = nullptr;
     long long* d_qItem = nullptr;
+    long long* d_qMem = nullptr;
     long long capQ = -1;
     char* h_stage = nullptr;
     size_t stage_cap = 0;
@@ -80,6 +81,7 @@ struct plan_ctx {
     int* itemOff = nullptr;
     int* ntile = nullptr;
     int* tsize = nullptr;
+    int* memOff = nullptr;
     int* rowCount = nullptr;
     // device-sized scratch
     long long slotCap = 0, recheckCap = 0;
@@ -237,7 +239,8 @@ int ensure_host_sized(plan_ctx* c, long long mask, long long list, long long k1,
     }
     if (k1 > c->capK) {
         if (!dalloc(c, &c->counts, k1) || !dalloc(c, &c->centers, 4 * k1) || !dalloc(c, &c->resOff, k1) ||
-            !dalloc(c, &c->itemOff, k1) || !dalloc(c, &c->ntile, k1) || !dalloc(c, &c->tsize, k1))
+            !dalloc(c, &c->itemOff, k1) || !dalloc(c, &c->ntile, k1) || !dalloc(c, &c->tsize, k1) ||
+            !dalloc(c, &c->memOff, k1))
             return PLAN_ERR_NO_MEMORY;
         c->capK = k1;
     }
@@ -353,7 +356,7 @@ void plan_destroy(plan_ctx* c) {
     void* dev[] = {c->d_tab64, c->d_tab32, c->d_info, c->memMask, c->counts, c->members, c->localIdx, c->centers,
                    c->blim64, c->A32, c->blim32, c->bc32, c->resOff, c->itemOff, c->ntile, c->tsize, c->rowCount,
                    c->resBits, c->resKey, c->emitPre, c->recheck, c->sdist, c->sbest, c->spred, c->sfront,
-                   c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem, c->d_sqd};
+                   c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem, c->d_qMem, c->d_sqd, c->memOff};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_tab64) cudaFreeHost(c->h_tab64);
@@ -464,7 +467,7 @@ int prepare(plan_ctx* c, int Q, const plan_query* qs, int max_rows) {
     if (Q > c->capQ) {
         if (c->stage_live) cudaEventSynchronize(c->stage_ev);
         if (!dalloc(c, &c->d_qd, Q) || !dalloc(c, &c->d_pfx, 4LL * (Q + 1)) || !dalloc(c, &c->d_qSlot, Q + 1) ||
-            !dalloc(c, &c->d_qItem, Q + 1))
+            !dalloc(c, &c->d_qItem, Q + 1) || !dalloc(c, &c->d_qMem, Q + 1))
             return PLAN_ERR_NO_MEMORY;
         c->capQ = Q;
         c->last_stage.clear();
@@ -539,7 +542,7 @@ int issue(plan_ctx* c) {
     P.tile = (c->model.arith == PLAN_F64) ? TILE64
              : (c->model.arith == PLAN_F32) ? (c->tile > 0 ? c->tile : TILE)
                                             : TILE;  // tensor-core form: 64-state tiles, 256 threads
-    P.tchunks = (c->model.arith == PLAN_F64) ? 1 : (c->tchunks > 0 ? c->tchunks : 4);
+    P.tchunks = (c->model.arith == PLAN_F64) ? 1 : (c->tchunks > 0 ? c->tchunks : 2);
     P.eps = c->model.tighten;
     P.qd = c->d_qd;
     P.pfxMask = c->d_pfx;
@@ -548,6 +551,7 @@ int issue(plan_ctx* c) {
     P.pfxN = c->d_pfx + 3 * (Q + 1);
     P.qSlot = c->d_qSlot;
     P.qItem = c->d_qItem;
+    P.qMem = c->d_qMem;
     P.totMask = c->totMask;
     P.totPoly = c->totPoly;
     P.totRows = c->totRows;
@@ -569,6 +573,7 @@ int issue(plan_ctx* c) {
     P.itemOff = c->itemOff;
     P.ntile = c->ntile;
     P.tsize = c->tsize;
+    P.memOff = c->memOff;
     P.resBits = c->resBits;
     P.resKey = c->resKey;
     P.emitPre = c->emitPre;

@@ -280,9 +280,10 @@ __global__ void __launch_bounds__(1024) k_setup(BuildParams P) {
         slots = tot;
         const long long io = block_exclusive_scan<long long>((long long)nt * nt, wb, &tot);
         items = tot;
-        block_exclusive_scan<long long>(nk, wb, &tot);
+        const long long mo = block_exclusive_scan<long long>(nk, wb, &tot);
         mem = tot;
         if (k < Q.K) {
+            P.memOff[Q.kOff + k] = (int)(carry_m + mo);
             P.resOff[Q.kOff + k] = carry_s + so;
             P.itemOff[Q.kOff + k] = (int)(carry_i + io);
             P.ntile[Q.kOff + k] = nt;
@@ -295,8 +296,10 @@ __global__ void __launch_bounds__(1024) k_setup(BuildParams P) {
     if (threadIdx.x == 0) {
         P.resOff[Q.kOff + Q.K] = carry_s;
         P.itemOff[Q.kOff + Q.K] = (int)carry_i;
+        P.memOff[Q.kOff + Q.K] = (int)carry_m;
         P.qSlot[q + 1] = carry_s;   // per-query totals; k_batch turns them into prefixes
         P.qItem[q + 1] = carry_i;
+        P.qMem[q + 1] = carry_m;
         atomicAdd(&P.info->memberships, (unsigned long long)carry_m);
     }
 }
@@ -305,26 +308,32 @@ __global__ void __launch_bounds__(1024) k_setup(BuildParams P) {
 __global__ void __launch_bounds__(1024) k_batch(BuildParams P) {
     __shared__ long long wb[32];
     __shared__ long long tot;
-    long long cs = 0, ci = 0;
+    long long cs = 0, ci = 0, cm = 0;
     for (int q0 = 0; q0 < P.Q; q0 += blockDim.x) {
         const int q = q0 + threadIdx.x;
         const long long vs = q < P.Q ? P.qSlot[q + 1] : 0;
         const long long vi = q < P.Q ? P.qItem[q + 1] : 0;
+        const long long vm = q < P.Q ? P.qMem[q + 1] : 0;
         __syncthreads();
         const long long es = block_exclusive_scan<long long>(vs, wb, &tot);
         const long long ts = tot;
         const long long ei = block_exclusive_scan<long long>(vi, wb, &tot);
         const long long ti = tot;
+        const long long em = block_exclusive_scan<long long>(vm, wb, &tot);
+        const long long tmm = tot;
         if (q < P.Q) {
             P.qSlot[q + 1] = cs + es + vs;
             P.qItem[q + 1] = ci + ei + vi;
+            P.qMem[q + 1] = cm + em + vm;
         }
         cs += ts;
         ci += ti;
+        cm += tmm;
     }
     if (threadIdx.x == 0) {
         P.qSlot[0] = 0;
         P.qItem[0] = 0;
+        P.qMem[0] = 0;
         P.info->slots = cs;
         P.info->items = ci * P.tchunks;
         if (cs > P.slotCap) {
@@ -1442,63 +1451,94 @@ DEVI void combine(const BuildParams& P, const QView& V, int i, int j, int k, uin
     }
 }
 
-__global__ void k_compact_count(BuildParams P) {
-    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= P.totN || has_failed(P.info)) return;
-    const int q = find_q(P.pfxN, P.Q, warp);
-    const QView V(P, q);
-    const int i = (int)(warp - P.pfxN[q]);
-    const int W = V.Q->W;
-    int npi = 0;
-    for (int w = 0; w < W; ++w) npi += __popc(V.mask[(long long)i * W + w]);
-    const bool multi_i = npi > 1;
-    long long total = 0, cand = 0, feas = 0;
-    for (int w = 0; w < W; ++w) {
-        uint32_t mw = V.mask[(long long)i * W + w];
-        while (mw) {
-            const int k = w * 32 + __ffs(mw) - 1;
-            mw &= mw - 1u;
-            const int nk = V.counts[k];
-            const long long base = V.seg(k, i);
-            const int* mem = V.members + (long long)k * V.Q->N;
-            int running = 0;
-            for (int lj0 = 0; lj0 < nk; lj0 += 32) {
-                const int lj = lj0 + lane;
-                bool emitted = false;
-                if (lj < nk) {
-                    const int jm = mem[lj], j = mem_id(jm);
-                    if (j != i) {
-                        int ns = 1;
-                        // a pair can be shared by several polytopes only if both states are
-                        if (!(multi_i && mem_multi(jm)) || owner_of(V, i, j, ns) == k) {
-                            ++cand;
-                            uint32_t bits = P.resBits[base + lj];
-                            unsigned long long key = P.resKey[base + lj];
-                            if (ns > 1) combine(P, V, i, j, k, bits, key);
-                            emitted = bits != 0;
-                            feas += __popc(bits);
-                        }
-                    }
-                }
-                const unsigned bal = __ballot_sync(0xffffffffu, emitted);
-                if (lj < nk) P.emitPre[base + lj] = running + __popc(bal & ((2u << lane) - 1u));
-                running += __popc(bal);
-            }
-            total += running;
+// Pass 1, one thread per slot (balanced): is this slot the pair's owner, and
+// is the pair feasible for some duration?  The owner slot receives the pair's
+// result combined over all shared polytopes; emitPre[slot] gets the flag.
+__global__ void k_emit(BuildParams P) {
+    if (has_failed(P.info)) return;
+    const long long total = (long long)P.info->slots;
+    unsigned long long cand = 0, chk = 0, feas = 0;
+    for (long long sidx = blockIdx.x * (long long)blockDim.x + threadIdx.x; sidx < total;
+         sidx += (long long)gridDim.x * blockDim.x) {
+        const int q = find_q(P.qSlot, P.Q, sidx);
+        const QView V(P, q);
+        const QueryDesc& Q = *V.Q;
+        const long long ls = sidx - V.slot0;
+        int lo = 0, hi = Q.K;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (V.resOff[mid] <= ls) lo = mid;
+            else hi = mid;
         }
+        const int k = lo, nk = V.counts[k];
+        int flag = 0;
+        if (nk > 0) {
+            const long long loc = ls - V.resOff[k];
+            const int li = (int)(loc / nk), lj = (int)(loc % nk);
+            const int im = V.members[(long long)k * Q.N + li], jm = V.members[(long long)k * Q.N + lj];
+            const int i = mem_id(im), j = mem_id(jm);
+            if (i != j) {
+                int ns = 1;
+                if (!(mem_multi(im) && mem_multi(jm)) || owner_of(V, i, j, ns) == k) {
+                    ++cand;
+                    chk += Q.nT;
+                    uint32_t bits = P.resBits[sidx];
+                    unsigned long long key = P.resKey[sidx];
+                    if (ns > 1) {
+                        combine(P, V, i, j, k, bits, key);
+                        P.resBits[sidx] = bits;
+                        P.resKey[sidx] = key;
+                    }
+                    flag = bits != 0;
+                    feas += __popc(bits);
+                }
+            }
+        }
+        P.emitPre[sidx] = flag;
     }
     for (int o = 16; o > 0; o >>= 1) {
         cand += __shfl_down_sync(0xffffffffu, cand, o);
+        chk += __shfl_down_sync(0xffffffffu, chk, o);
         feas += __shfl_down_sync(0xffffffffu, feas, o);
     }
-    if (lane == 0) {
-        P.rowCount[V.Q->rowOff + i] = (int)total;
-        if (cand) {
-            atomicAdd(&P.info->candidates, (unsigned long long)cand);
-            atomicAdd(&P.info->checks, (unsigned long long)cand * (unsigned long long)V.Q->nT);
+    if ((threadIdx.x & 31) == 0 && cand) {
+        atomicAdd(&P.info->candidates, cand);
+        atomicAdd(&P.info->checks, chk);
+        atomicAdd(&P.info->feasible, feas);
+    }
+}
+
+// Pass 2, one warp per row segment (state i in polytope k): inclusive prefix
+// of the emitted flags within the segment; the segment total adds to row i.
+__global__ void k_segscan(BuildParams P) {
+    if (has_failed(P.info)) return;
+    const long long nseg = (long long)P.info->memberships;
+    const int lane = threadIdx.x & 31;
+    for (long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; g < nseg;
+         g += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const int q = find_q(P.qMem, P.Q, g);
+        const QView V(P, q);
+        const QueryDesc& Q = *V.Q;
+        const int loc = (int)(g - P.qMem[q]);
+        const int* mo = P.memOff + Q.kOff;
+        int lo = 0, hi = Q.K;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (mo[mid] <= loc) lo = mid;
+            else hi = mid;
         }
-        if (feas) atomicAdd(&P.info->feasible, (unsigned long long)feas);
+        const int k = lo, li = loc - mo[k], nk = V.counts[k];
+        const int i = mem_id(V.members[(long long)k * Q.N + li]);
+        const long long base = V.slot0 + V.resOff[k] + (long long)li * nk;
+        int running = 0;
+        for (int lj0 = 0; lj0 < nk; lj0 += 32) {
+            const int lj = lj0 + lane;
+            const int f = lj < nk ? P.emitPre[base + lj] : 0;
+            const unsigned bal = __ballot_sync(0xffffffffu, f != 0);
+            if (lj < nk) P.emitPre[base + lj] = running + __popc(bal & ((2u << lane) - 1u));
+            running += __popc(bal);
+        }
+        if (lane == 0 && running) atomicAdd(&P.rowCount[Q.rowOff + i], running);
     }
 }
 
@@ -1613,11 +1653,9 @@ __global__ void __launch_bounds__(256) k_compact_fill(BuildParams P, int bm_word
                 const int pre = P.emitPre[base + lj];
                 const int prev = lj > 0 ? P.emitPre[base + lj - 1] : 0;
                 if (pre == prev) continue;  // not emitted here
-                int ns = 1;
-                if (npoly > 1 && mem_multi(jm)) owner_of(V, i, j, ns);
-                uint32_t bits = P.resBits[base + lj];
-                unsigned long long key = P.resKey[base + lj];
-                if (ns > 1) combine(P, V, i, j, k, bits, key);
+                (void)jm;
+                const uint32_t bits = P.resBits[base + lj];          // combined by k_emit
+                const unsigned long long key = P.resKey[base + lj];
                 long long rank = prev;
                 if (use_bm) {
                     rank = (long long)pre_m[j >> 5] + __popc(bits_m[j >> 5] & ((1u << (j & 31)) - 1u));
@@ -1876,10 +1914,12 @@ int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_s
         if (rc) return rc;
     }
     if (P.totN > 0) {
-        // rows of queries without polytopes have no members: their counts stay 0
-        const long long thr = P.totN * 32;
-        k_compact_count<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(P);
-        ++*launches;
+        cudaMemsetAsync(P.rowCount, 0, sizeof(int) * (size_t)P.totN, st);
+        if (P.totPoly > 0) {
+            k_emit<<<num_sms * 8, 256, 0, st>>>(P);
+            k_segscan<<<num_sms * 8, 256, 0, st>>>(P);
+            *launches += 2;
+        }
     }
     k_scan<<<P.Q, 1024, 0, st>>>(P);
     ++*launches;

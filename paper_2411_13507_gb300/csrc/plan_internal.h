@@ -130,6 +130,7 @@ struct BuildParams {
     const long long* pfxN;     // [Q+1] prefix of N          (one warp per row)
     long long* qSlot;          // [Q+1] device-computed prefix of slots
     long long* qItem;          // [Q+1] device-computed prefix of tiles
+    long long* qMem;           // [Q+1] device-computed prefix of memberships (row segments)
     long long totMask, totPoly, totRows, totN;
     const float* tab32;        // [nT_total][f_stride]
     const double* tab64;       // [nT_total][e_stride]
@@ -146,6 +147,7 @@ struct BuildParams {
     float* blim32;
     float* bc32;
     long long* resOff;         // [kOff] slot offset of each polytope, relative to qSlot[q]
+    int* memOff;               // [kOff] membership offset of each polytope, relative to qMem[q]
     int* itemOff;
     int* ntile;
     int* tsize;
