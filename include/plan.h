@@ -186,12 +186,16 @@ int plan_prepare_batched(plan_ctx* ctx, int Q, const plan_query* queries, int ma
 int plan_build_edges_batched(plan_ctx* ctx);
 
 /* FP32 pair-kernel configuration: tile side (8..64, multiple of 4; 0 = 64),
- * CTAs per SM (0 = as many as fit) and duration chunks per tile (work items
- * are tiles x chunks, longest durations first; 0 = 2).  plan_autotune times
+ * CTAs per SM (0 = as many as fit), duration chunks per tile (work items are
+ * tiles x chunks, longest durations first; 0 = 2) and pipeline (1: the
+ * warp-specialised kernel -- producer warps compute the next duration's halves
+ * while consumer warps reduce the current one; used with 64-state tiles when
+ * its two stages fit in shared memory; 0: one warp group).  plan_autotune times
  * every candidate on the prepared batch (reps launches each, synchronising)
  * and keeps the fastest; it reports the choice and its mean pair-kernel time. */
-int plan_set_tile(plan_ctx* ctx, int tile, int ctas_per_sm, int tchunks);
-int plan_autotune(plan_ctx* ctx, int reps, int* best_tile, int* best_ctas, int* best_chunks, double* best_ms);
+int plan_set_tile(plan_ctx* ctx, int tile, int ctas_per_sm, int tchunks, int pipeline);
+int plan_autotune(plan_ctx* ctx, int reps, int* best_tile, int* best_ctas, int* best_chunks, int* best_pipeline,
+                  double* best_ms);
 
 /*
  * findPath (Alg. 1 line 4, Sec. III-C, Problem 2): the start and goal vertices

@@ -54,7 +54,8 @@ struct plan_ctx {
     bool stage_live = false;
     std::vector<char> last_stage;
     int tile = 0, ctas_per_sm = 0;    // pair-kernel configuration (0 = default)
-    int tchunks = 0;                  // duration chunks per tile (0 = default 4)
+    int tchunks = 0;                  // duration chunks per tile (0 = default 2)
+    int pipeline = 1;                 // warp-specialised FP32 pair kernel when it fits
     // batched search
     int sQ = 0;
     long long sTotN = 0;
@@ -543,6 +544,7 @@ int issue(plan_ctx* c) {
              : (c->model.arith == PLAN_F32) ? (c->tile > 0 ? c->tile : TILE)
                                             : TILE;  // tensor-core form: 64-state tiles, 256 threads
     P.tchunks = (c->model.arith == PLAN_F64) ? 1 : (c->tchunks > 0 ? c->tchunks : 2);
+    P.pipeline = c->pipeline;
     P.eps = c->model.tighten;
     P.qd = c->d_qd;
     P.pfxMask = c->d_pfx;
@@ -632,9 +634,11 @@ int plan_build_edges_batched(plan_ctx* c) {
     return issue(c);
 }
 
-int plan_set_tile(plan_ctx* c, int tile, int ctas_per_sm, int tchunks) {
-    if (!c || tile < 0 || ctas_per_sm < 0 || ctas_per_sm > 8 || tchunks < 0 || tchunks > NT_MAX)
+int plan_set_tile(plan_ctx* c, int tile, int ctas_per_sm, int tchunks, int pipeline) {
+    if (!c || tile < 0 || ctas_per_sm < 0 || ctas_per_sm > 8 || tchunks < 0 || tchunks > NT_MAX || pipeline < 0 ||
+        pipeline > 1)
         return PLAN_ERR_INVALID_ARG;
+    c->pipeline = pipeline;
     if (tile != 0 && (tile < 8 || tile > TILE || (tile & 3))) return fail(c, PLAN_ERR_INVALID_ARG, "tile must be 8..64, multiple of 4");
     c->tile = tile;
     c->ctas_per_sm = ctas_per_sm;
@@ -642,24 +646,29 @@ int plan_set_tile(plan_ctx* c, int tile, int ctas_per_sm, int tchunks) {
     return PLAN_OK;
 }
 
-int plan_autotune(plan_ctx* c, int reps, int* best_tile, int* best_ctas, int* best_chunks, double* best_ms) {
+int plan_autotune(plan_ctx* c, int reps, int* best_tile, int* best_ctas, int* best_chunks, int* best_pipeline,
+                  double* best_ms) {
     if (!c || reps < 1) return PLAN_ERR_INVALID_ARG;
     if (c->bQ < 1) return fail(c, PLAN_ERR_INVALID_ARG, "prepare a batch first");
     if (c->model.arith != PLAN_F32) {  // the FP64 and tensor-core kernels have fixed tiles
         if (best_tile) *best_tile = c->model.arith == PLAN_F64 ? TILE64 : TILE;
         if (best_ctas) *best_ctas = 0;
-        if (best_chunks) *best_chunks = c->model.arith == PLAN_F64 ? 1 : 4;
+        if (best_chunks) *best_chunks = c->model.arith == PLAN_F64 ? 1 : 2;
+        if (best_pipeline) *best_pipeline = 0;
         return PLAN_OK;
     }
     const bool was_timing = c->timing;
-    const int tiles[] = {32, 48, 64};
-    const int ctas[] = {0, 1};
+    // candidates: the warp-specialised kernel (64-state tiles) and the
+    // one-group kernel over tile sides; every one over duration chunks
+    struct Cand { int pipe, tile, ctas; };
+    const Cand cands[] = {{1, 64, 0}, {0, 64, 0}, {0, 48, 0}, {0, 32, 0}};
     const int chunks[] = {1, 2, 4, 8};
     double best = 1e30;
-    int bt = TILE, bc = 0, bk = 4;
-    for (int cc : ctas)
-        for (int ch : chunks)
-        for (int t : tiles) {
+    int bt = TILE, bc = 0, bk = 2, bp = 1;
+    for (const Cand& cd : cands)
+        for (int ch : chunks) {
+            const int cc = cd.ctas, t = cd.tile;
+            c->pipeline = cd.pipe;
             c->tile = t;
             c->ctas_per_sm = cc;
             c->tchunks = ch;
@@ -691,14 +700,17 @@ int plan_autotune(plan_ctx* c, int reps, int* best_tile, int* best_ctas, int* be
                 bt = t;
                 bc = cc;
                 bk = ch;
+                bp = cd.pipe;
             }
         }
     c->tile = bt;
     c->ctas_per_sm = bc;
     c->tchunks = bk;
+    c->pipeline = bp;
     if (best_tile) *best_tile = bt;
     if (best_ctas) *best_ctas = bc;
     if (best_chunks) *best_chunks = bk;
+    if (best_pipeline) *best_pipeline = bp;
     if (best_ms) *best_ms = best;
     return PLAN_OK;
 }

@@ -771,6 +771,333 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
 }
 
 // ---------------------------------------------------------------------------
+// Warp-specialised FP32 pair kernel.  Eight producer warps stage an item's
+// states and compute the halves of one duration into one of two shared-memory
+// stages; eight consumer warps (one 4x4 micro-tile per thread, 64x64 tiles)
+// reduce the pairs of the other stage.  Stages change hands through mbarriers
+// (producers: "stage s holds duration t", consumers: "stage s is free"), so the
+// groups never meet at a CTA-wide barrier and consumers that finish a duration
+// early move on instead of waiting for the slowest warp.  Every wait is
+// bounded; on expiry the kernel records PLAN_ERR_TIMEOUT and stops.
+// ---------------------------------------------------------------------------
+struct StageMeta {
+    int end;
+    int q, k, i0, j0, TI, TJ, nk, nr, t;
+    long long base;
+};
+
+namespace ws {
+DEVI uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+DEVI void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+DEVI void mbar_arrive(uint64_t* bar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n}\n" ::"r"(saddr(bar)) : "memory");
+}
+DEVI bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false (and PLAN_ERR_TIMEOUT recorded) if the phase never completes
+DEVI bool mbar_wait(uint64_t* bar, uint32_t parity, DevInfo* info) {
+    long long spins = 0;
+    while (!mbar_try(bar, parity)) {
+        if (++spins > (1LL << 22)) {
+            set_status(info, PLAN_ERR_TIMEOUT, DET_BARRIER);
+            return false;
+        }
+    }
+    return true;
+}
+DEVI void bar_producers() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+}  // namespace ws
+
+template <int M, int G, int PD>
+__global__ void __launch_bounds__(512, 1) k_pairs_ws(BuildParams P) {
+    using S = Shape<G, PD>;
+    constexpr int N_ = M * G, RAX = S::RAX, RR = M * RAX, NI = S::NI, TG = S::TG;
+    constexpr int T = TILE;
+    constexpr int NCW = 8;  // consumer warps (warps 8..15); warps 0..7 produce
+    extern __shared__ __align__(16) float sm[];
+    const int FRm = NI * P.max_rows;
+    const int DR = P.cost_mode == 1 ? 1 : G;
+    const int CRW = G * PD * M;
+    const int stage_floats = (2 * RR + 2 * FRm + 2 * CRW + 4) * T;
+    float* xs = sm + 2 * stage_floats;
+    float* xab = xs + 2 * T * N_;
+    float* tabs = xab + 2 * T * G;
+    float* Ap = tabs + 2 * P.L.f_stride;
+    float* bp = Ap + RMAX * M;
+    __shared__ StageMeta meta[2];
+    __shared__ __align__(8) uint64_t full[2];
+    __shared__ __align__(8) uint64_t empty[2];
+    __shared__ long long s_item;
+    __shared__ float s_rown1, s_bmax;
+    __shared__ int s_stop;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long nitems = (long long)P.info->items;
+    const TabLayout L = P.L;
+    if (tid == 0) {
+        ws::mbar_init(&full[0], 1);
+        ws::mbar_init(&full[1], 1);
+        ws::mbar_init(&empty[0], NCW);
+        ws::mbar_init(&empty[1], NCW);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_stop = 0;
+    }
+    __syncthreads();
+
+    auto stage_ptr = [&](int st, float*& UL, float*& UR, float*& FL, float*& FR, float*& CL, float*& CRr,
+                         float*& magR, float*& magF) {
+        float* b = sm + st * stage_floats;
+        UL = b;
+        UR = UL + RR * T;
+        FL = UR + RR * T;
+        FR = FL + FRm * T;
+        CL = FR + FRm * T;
+        CRr = CL + CRW * T;
+        magR = CRr + CRW * T;
+        magF = magR + 2 * T;
+    };
+
+    if (warp < 8) {
+        // ------------------------------ producers ------------------------------
+        const int ptid = tid, pn = 256;
+        int stage = 0;
+        uint32_t uses[2] = {0u, 0u};
+        bool ok = true;
+        for (;;) {
+            if (ptid == 0) {
+                const long long it = (long long)atomicAdd(&P.info->ticket, 1u);
+                s_item = (has_failed(P.info) || *(volatile int*)&s_stop) ? 0x7fffffffffffLL : it;
+            }
+            ws::bar_producers();
+            const long long item = s_item;
+            if (item >= nitems) break;
+            const ItemT itc = item_decode_chunk(P, item);
+            const Item& itd = itc.it;
+            if (itc.t0 >= itc.t1) {
+                ws::bar_producers();
+                continue;
+            }
+            const QueryDesc& Qd = P.qd[itd.q];
+            const int k = itd.k, i0 = itd.i0, j0 = itd.j0, TI = itd.TI, TJ = itd.TJ;
+            const int ni4 = (TI + 3) & ~3, nj4 = (TJ + 3) & ~3;
+            const int r0 = Qd.poly_off[k], nr = Qd.poly_off[k + 1] - r0;
+            const long long rg0 = Qd.rowsOff + r0;
+            for (int u = ptid; u < nr * M; u += pn) Ap[u] = P.A32[rg0 * M + u];
+            for (int u = ptid; u < nr; u += pn) bp[u] = P.bc32[rg0 + u];
+            const int* members = P.members + Qd.listOff + (long long)k * Qd.N;
+            float cx[M];
+#pragma unroll
+            for (int a = 0; a < M; ++a) cx[a] = P.centers[(long long)(Qd.kOff + k) * 4 + a];
+            for (int u = ptid; u < (ni4 + nj4) * N_; u += pn) {
+                const int s = u / N_, e = u % N_;
+                const bool right = s >= ni4;
+                const int ls = right ? s - ni4 : s;
+                const int lidx = (right ? j0 : i0) + ls;
+                float v = 0.f;
+                if (ls < (right ? TJ : TI)) {
+                    const long long id = mem_id(members[lidx]);
+                    if (e < M) {
+                        if (P.in_f32) v = ((const float*)Qd.states)[id * N_ + e] - cx[e];
+                        else v = (float)(((const double*)Qd.states)[id * N_ + e] - (double)cx[e]);
+                    } else {
+                        v = ldf(Qd.states, id * N_ + e, P.in_f32);
+                    }
+                }
+                xs[(right ? T + ls : ls) * N_ + e] = v;
+            }
+            for (int u = ptid; u < L.f_stride; u += pn) tabs[u] = P.tab32[(long long)(Qd.tabOff + itc.t0) * L.f_stride + u];
+            ws::bar_producers();
+            for (int s = ptid; s < ni4 + nj4; s += pn) {
+                const bool right = s >= ni4;
+                const int ls = right ? s - ni4 : s;
+                const float* x = xs + (right ? T + ls : ls) * N_;
+                float* xa = xab + (right ? T + ls : ls) * G;
+#pragma unroll
+                for (int c = 0; c < G; ++c) {
+                    float mx = 0.f;
+#pragma unroll
+                    for (int a = 0; a < M; ++a) mx = fmaxf(mx, fabsf(x[c * M + a]));
+                    xa[c] = mx;
+                }
+            }
+            if (ptid == 0) {
+                float rn = 0.f, bm = 0.f;
+                for (int r = 0; r < nr; ++r) {
+                    float s1 = 0.f;
+                    for (int a = 0; a < M; ++a) s1 += fabsf(Ap[r * M + a]);
+                    rn = fmaxf(rn, s1);
+                    bm = fmaxf(bm, fabsf(bp[r]));
+                }
+                s_rown1 = rn * 1.0001f;
+                s_bmax = bm;
+            }
+            ws::bar_producers();
+            for (int t = itc.t0; t < itc.t1 && ok; ++t) {
+                const float* tab = tabs + ((t - itc.t0) & 1) * L.f_stride;
+                if (uses[stage] > 0 && !ws::mbar_wait(&empty[stage], (uses[stage] - 1) & 1u, P.info)) {
+                    ok = false;
+                    break;
+                }
+                float *UL, *UR, *FL, *FR, *CL, *CRr, *magR, *magF;
+                stage_ptr(stage, UL, UR, FL, FR, CL, CRr, magR, magF);
+                for (int u = ptid; u < (ni4 + nj4) * M; u += pn) {
+                    const int s = u / M, a = u % M;
+                    const bool right = s >= ni4;
+                    const int ls = right ? s - ni4 : s;
+                    const float* x = xs + (right ? T + ls : ls) * N_;
+                    float xc[G];
+#pragma unroll
+                    for (int c = 0; c < G; ++c) xc[c] = x[c * M + a];
+                    const int co = right ? G : 0;
+                    float* dU = right ? UR : UL;
+#pragma unroll 3
+                    for (int r = 0; r < RAX; ++r) {
+                        const float* h = tab + L.f_H + r * TG + co;
+                        float v = h[0] * xc[0];
+#pragma unroll
+                        for (int c = 1; c < G; ++c) v = fmaf(h[c], xc[c], v);
+                        dU[(r * M + a) * T + ls] = v;
+                    }
+                    float* dC = right ? CRr : CL;
+                    for (int d = 0; d < DR; ++d)
+                        for (int l = 0; l < PD; ++l) {
+                            const float* cc = tab + L.f_C + (d * PD + l) * TG + co;
+                            float v = cc[0] * xc[0];
+#pragma unroll
+                            for (int c = 1; c < G; ++c) v = fmaf(cc[c], xc[c], v);
+                            dC[((l * DR + d) * M + a) * T + ls] = v;
+                        }
+                }
+                for (int u = ptid; u < (ni4 + nj4) * NI; u += pn) {
+                    const int s = u / NI, l = u % NI;
+                    const bool right = s >= ni4;
+                    const int ls = right ? s - ni4 : s;
+                    const float* x = xs + (right ? T + ls : ls) * N_;
+                    const float* dd = tab + L.f_D + l * TG + (right ? G : 0);
+                    float pt[M];
+#pragma unroll
+                    for (int a = 0; a < M; ++a) {
+                        float v = dd[0] * x[a];
+#pragma unroll
+                        for (int c = 1; c < G; ++c) v = fmaf(dd[c], x[c * M + a], v);
+                        pt[a] = v;
+                    }
+                    float* dF = right ? FR : FL;
+                    for (int r = 0; r < nr; ++r) {
+                        float v = Ap[r * M] * pt[0];
+#pragma unroll
+                        for (int a = 1; a < M; ++a) v = fmaf(Ap[r * M + a], pt[a], v);
+                        if (!right) v -= bp[r];
+                        dF[(l * nr + r) * T + ls] = v;
+                    }
+                }
+                for (int s = ptid; s < ni4 + nj4; s += pn) {
+                    const bool right = s >= ni4;
+                    const int ls = right ? s - ni4 : s;
+                    const float* xa = xab + (right ? T + ls : ls) * G;
+                    float mr = 0.f, md = 0.f;
+#pragma unroll
+                    for (int c = 0; c < G; ++c) {
+                        mr = fmaf(tab[L.f_HC + (right ? G : 0) + c], xa[c], mr);
+                        md = fmaf(tab[L.f_DC + (right ? G : 0) + c], xa[c], md);
+                    }
+                    magR[(right ? T : 0) + ls] = mr;
+                    magF[(right ? T : 0) + ls] = md * s_rown1 + (right ? 0.f : s_bmax);
+                }
+                if (t + 1 < itc.t1) {
+                    float* nxt = tabs + ((t + 1 - itc.t0) & 1) * L.f_stride;
+                    for (int u = ptid; u < L.f_stride; u += pn) nxt[u] = P.tab32[(long long)(Qd.tabOff + t + 1) * L.f_stride + u];
+                }
+                if (ptid == 0) {
+                    StageMeta& mt = meta[stage];
+                    mt.end = 0;
+                    mt.q = itd.q;
+                    mt.k = k;
+                    mt.i0 = i0;
+                    mt.j0 = j0;
+                    mt.TI = TI;
+                    mt.TJ = TJ;
+                    mt.nk = itd.nk;
+                    mt.nr = nr;
+                    mt.t = t;
+                    mt.base = itd.base;
+                }
+                ws::bar_producers();  // halves, next table and metadata written
+                if (ptid == 0) ws::mbar_arrive(&full[stage]);
+                ++uses[stage];
+                stage ^= 1;
+            }
+            if (!ok) break;
+        }
+        // end of work: hand the consumers an end marker
+        if (ptid == 0) {
+            bool wok = true;
+            if (uses[stage] > 0) wok = ws::mbar_wait(&empty[stage], (uses[stage] - 1) & 1u, P.info);
+            meta[stage].end = 1;
+            (void)wok;
+            ws::mbar_arrive(&full[stage]);
+        }
+    } else {
+        // ------------------------------ consumers ------------------------------
+        const int ctid = tid - 256;
+        int stage = 0;
+        uint32_t uses[2] = {0u, 0u};
+        unsigned long long rp_cnt = 0;
+        for (;;) {
+            if (!ws::mbar_wait(&full[stage], uses[stage] & 1u, P.info)) {
+                s_stop = 1;
+                break;
+            }
+            const StageMeta mt = meta[stage];
+            if (mt.end) break;
+            float *UL, *UR, *FL, *FR, *CL, *CRr, *magR, *magF;
+            stage_ptr(stage, UL, UR, FL, FR, CL, CRr, magR, magF);
+            const int ni4 = (mt.TI + 3) & ~3, nj4 = (mt.TJ + 3) & ~3;
+            const int ngi = ni4 >> 2, ngj = nj4 >> 2;
+            const bool act = ctid < ngi * ngj;
+            const int gi = act ? ctid / ngj : 0, gj = act ? ctid % ngj : 0;
+            const bool diag_tile = (mt.i0 == mt.j0);
+            uint32_t vmask = 0, dmask = 0;
+#pragma unroll
+            for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+                for (int qb = 0; qb < 4; ++qb) {
+                    const int li = 4 * gi + qa, lj = 4 * gj + qb;
+                    if (act && li < mt.TI && lj < mt.TJ) vmask |= 1u << (qa * 4 + qb);
+                    if (diag_tile && li == lj) dmask |= 1u << (qa * 4 + qb);
+                }
+            if (act) {
+                Item itd;
+                itd.q = mt.q;
+                itd.k = mt.k;
+                itd.i0 = mt.i0;
+                itd.j0 = mt.j0;
+                itd.TI = mt.TI;
+                itd.TJ = mt.TJ;
+                itd.nk = mt.nk;
+                itd.base = mt.base;
+                pair_phase<M, G, PD>(P, itd, mt.t, T, gi, gj, vmask, dmask, mt.nr, DR, UL, UR, FL, FR, CL, CRr, magR,
+                                     magF, KR, KF, rp_cnt);
+            }
+            __syncwarp();
+            if (lane == 0) ws::mbar_arrive(&empty[stage]);
+            ++uses[stage];
+            stage ^= 1;
+        }
+        if (rp_cnt) atomicAdd(&P.info->reach_pass, rp_cnt);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Precision form: the per-state products H xi and A p (the halves of the reach
 // rows and of the polytope rows of the control points) on the 5th-generation
 // tensor cores; the cost halves stay FP32 FMAs (computed while the MMA runs).
@@ -1112,7 +1439,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_tc(BuildParams P) {
             {
                 long long spins = 0;
                 while (!tc::mbar_try_wait(&s_mbar, phase)) {
-                    if (++spins > (1LL << 26)) {
+                    if (++spins > (1LL << 22)) {
                         set_status(P.info, PLAN_ERR_TIMEOUT, DET_BARRIER);
                         s_abort = 1;
                         break;
@@ -1799,6 +2126,15 @@ size_t smem_fast(const BuildParams& P) {
 }
 
 template <int M, int G, int PD>
+size_t smem_ws(const BuildParams& P) {
+    using S = Shape<G, PD>;
+    const int RR = M * S::RAX, FRm = S::NI * P.max_rows, CRW = G * PD * M;
+    const size_t T = TILE;
+    size_t f = 2 * (size_t)(2 * RR + 2 * FRm + 2 * CRW + 4) * T + 2 * T * (M * G + G) + 2 * P.L.f_stride + RMAX * (M + 1);
+    return f * sizeof(float);
+}
+
+template <int M, int G, int PD>
 size_t smem_f64(const BuildParams& P) {
     using S = Shape<G, PD>;
     const int RR = M * S::RAX, CRW = G * PD * M;
@@ -1855,6 +2191,15 @@ int launch_pairs(const BuildParams& P, cudaStream_t st, int num_sms, int ctas_pe
         if (e0) cudaEventRecord(e0, st);
         k_pairs_f64<M, G, PD><<<num_sms * occ, 256, sm, st>>>(P);
         if (e1) cudaEventRecord(e1, st);
+        ++*launches;
+    } else if (P.pipeline && P.tile == TILE && smem_ws<M, G, PD>(P) <= 227 * 1024) {
+        const size_t sm = smem_ws<M, G, PD>(P);
+        cudaFuncSetAttribute(k_pairs_ws<M, G, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e0) cudaEventRecord(e0, st);
+        k_pairs_ws<M, G, PD><<<num_sms, 512, sm, st>>>(P);
+        if (e1) cudaEventRecord(e1, st);
+        ++*launches;
+        k_recheck<M, G, PD><<<num_sms * 4, 256, 0, st>>>(P);
         ++*launches;
     } else {
         const size_t sm = smem_fast<M, G, PD>(P);

@@ -116,9 +116,10 @@ def load(build_if_stale: bool = True):
     lib.plan_search_batched.restype = i32
     lib.plan_search_noalloc.argtypes = [i32, i32, i32, i32, i32, vp, ctypes.POINTER(_Edges), dp, dp, vp, i32, vp, vp, vp, vp]
     lib.plan_search_noalloc.restype = i32
-    lib.plan_set_tile.argtypes = [vp, i32, i32, i32]
+    lib.plan_set_tile.argtypes = [vp, i32, i32, i32, i32]
     lib.plan_set_tile.restype = i32
-    lib.plan_autotune.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32), dp]
+    lib.plan_autotune.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                  ctypes.POINTER(i32), dp]
     lib.plan_autotune.restype = i32
     lib.plan_refine.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, ctypes.POINTER(_RefineW), vp, vp, vp, vp]
     lib.plan_refine.restype = i32
@@ -449,18 +450,19 @@ class Planner:
                         "cost": float(o["cost"].item())})
         return res
 
-    def set_tile(self, tile: int = 0, ctas_per_sm: int = 0, tchunks: int = 0) -> None:
-        rc = self.lib.plan_set_tile(self.ctx, int(tile), int(ctas_per_sm), int(tchunks))
+    def set_tile(self, tile: int = 0, ctas_per_sm: int = 0, tchunks: int = 0, pipeline: int = 1) -> None:
+        rc = self.lib.plan_set_tile(self.ctx, int(tile), int(ctas_per_sm), int(tchunks), int(pipeline))
         if rc != 0:
             raise self._err(rc, "plan_set_tile")
 
     def autotune(self, reps: int = 3) -> dict:
         """Time every (tile, CTAs/SM) candidate on the prepared batch; keep the best."""
-        t, c, k, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
-        rc = self.lib.plan_autotune(self.ctx, int(reps), ctypes.byref(t), ctypes.byref(c), ctypes.byref(k), ctypes.byref(ms))
+        t, c, k, pp, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        rc = self.lib.plan_autotune(self.ctx, int(reps), ctypes.byref(t), ctypes.byref(c), ctypes.byref(k),
+                                    ctypes.byref(pp), ctypes.byref(ms))
         if rc != 0:
             raise self._err(rc, "plan_autotune")
-        return {"tile": t.value, "ctas_per_sm": c.value, "tchunks": k.value, "pair_ms": ms.value}
+        return {"tile": t.value, "ctas_per_sm": c.value, "tchunks": k.value, "pipeline": pp.value, "pair_ms": ms.value}
 
     def refine_async(self, P, T, A, b, nrows, weights=(1.0, 1.0, 0.1), grad_loss=None, loss=None, dP=None, dT=None):
         """Launch the refinement loss (and, with grad_loss, its gradient) on device float tensors."""
