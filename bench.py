@@ -52,7 +52,14 @@ def parse():
                          "precision form on the 2-D workload; batched: 256 uneven queries in one graph replay; "
                          "refine: 65536-segment forward+backward")
     ap.add_argument("--queries", type=int, default=256)
+    ap.add_argument("--pipeline", type=int, default=-1,
+                    help="FP32 pair kernel of the plain line: 0 screened, 1 warp-specialised, 2 unscreened "
+                         "(-1: the library default)")
     return ap.parse_args()
+
+
+PAIR_KERNEL = {0: "k_pairs_fast<3,3,7,true> (screened)", 1: "k_pairs_ws<3,3,7>",
+               2: "k_pairs_fast<3,3,7,false> (unscreened)"}
 
 
 def workload(seed):
@@ -347,6 +354,8 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         pl = P.Planner.for_problem(prob, arith="f32", input="f32", stream=stream)
+        if args.pipeline >= 0:
+            pl.set_tile(0, 0, 0, args.pipeline)
         dp = P.to_device(prob, input="f32")
         graph = pl.build_edges(dp)           # sizes scratch and the output CSR
         sres = pl.search(dp, graph)
@@ -467,7 +476,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TOP/s",
                      "frac": achieved / alu_peak,
                      "traffic": counters.get("dram_bytes_per_launch") if counters else None,
-                     "kernel": "k_pairs_fast<3,3,7>", "kernel_ms": pair_ms,
+                     "kernel": PAIR_KERNEL.get(args.pipeline, PAIR_KERNEL[0]), "kernel_ms": pair_ms,
                      "ops_per_check": ops_per_check, "ops_per_launch": ops_per_launch,
                      "work_model": "dense separable form per check (all reach, free and cost rows)",
                      "peak_note": f"FP32 lanes 152 SMs x 128 x {sm_max:.0f} MHz (unit counts and max clock; {peak_src} clock)",

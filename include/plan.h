@@ -187,12 +187,16 @@ int plan_build_edges_batched(plan_ctx* ctx);
 
 /* FP32 pair-kernel configuration: tile side (8..64, multiple of 4; 0 = 64),
  * CTAs per SM (0 = as many as fit), duration chunks per tile (work items are
- * tiles x chunks, longest durations first; 0 = 2) and pipeline (1: the
- * warp-specialised kernel -- producer warps compute the next duration's halves
- * while consumer warps reduce the current one; used with 64-state tiles when
- * its two stages fit in shared memory; 0: one warp group).  plan_autotune times
- * every candidate on the prepared batch (reps launches each, synchronising)
- * and keeps the fastest; it reports the choice and its mean pair-kernel time. */
+ * tiles x chunks, longest durations first; 0 = 2) and pipeline (0, the
+ * default: one warp group that screens every 4x4 block of pairs on the few
+ * reach rows that mix both boundary states and runs the surviving pairs,
+ * compacted, through all rows; 1: the warp-specialised kernel -- producer
+ * warps compute the next duration's halves while consumer warps reduce the
+ * current one; used with 64-state tiles when its two stages fit in shared
+ * memory; 2: one warp group, every 4x4 block through all rows).  Results do
+ * not depend on the choice.  plan_autotune times every candidate on the prepared batch (reps launches
+ * each, synchronising) and keeps the fastest; it reports the choice and its
+ * mean pair-kernel time. */
 int plan_set_tile(plan_ctx* ctx, int tile, int ctas_per_sm, int tchunks, int pipeline);
 int plan_autotune(plan_ctx* ctx, int reps, int* best_tile, int* best_ctas, int* best_chunks, int* best_pipeline,
                   double* best_ms);

@@ -37,7 +37,7 @@ def tune(planner: "_plan.Planner", workload: str, reps: int = 3, path: str = CAC
     cache = load_cache(path)
     if not force and k in cache:
         c = cache[k]
-        planner.set_tile(c["tile"], c["ctas_per_sm"], c.get("tchunks", 0), c.get("pipeline", 1))
+        planner.set_tile(c["tile"], c["ctas_per_sm"], c.get("tchunks", 0), c.get("pipeline", 0))
         return dict(c, cached=True)
     res = planner.autotune(reps)
     cache[k] = res

@@ -55,7 +55,7 @@ struct plan_ctx {
     std::vector<char> last_stage;
     int tile = 0, ctas_per_sm = 0;    // pair-kernel configuration (0 = default)
     int tchunks = 0;                  // duration chunks per tile (0 = default 2)
-    int pipeline = 1;                 // warp-specialised FP32 pair kernel when it fits
+    int pipeline = 0;                 // screened one-group FP32 pair kernel
     // batched search
     int sQ = 0;
     long long sTotN = 0;
@@ -636,7 +636,7 @@ int plan_build_edges_batched(plan_ctx* c) {
 
 int plan_set_tile(plan_ctx* c, int tile, int ctas_per_sm, int tchunks, int pipeline) {
     if (!c || tile < 0 || ctas_per_sm < 0 || ctas_per_sm > 8 || tchunks < 0 || tchunks > NT_MAX || pipeline < 0 ||
-        pipeline > 1)
+        pipeline > 2)
         return PLAN_ERR_INVALID_ARG;
     c->pipeline = pipeline;
     if (tile != 0 && (tile < 8 || tile > TILE || (tile & 3))) return fail(c, PLAN_ERR_INVALID_ARG, "tile must be 8..64, multiple of 4");
@@ -658,13 +658,14 @@ int plan_autotune(plan_ctx* c, int reps, int* best_tile, int* best_ctas, int* be
         return PLAN_OK;
     }
     const bool was_timing = c->timing;
-    // candidates: the warp-specialised kernel (64-state tiles) and the
-    // one-group kernel over tile sides; every one over duration chunks
+    // candidates: the screened one-group kernel over tile sides, the
+    // unscreened one and the warp-specialised one (64-state tiles); every one
+    // over duration chunks
     struct Cand { int pipe, tile, ctas; };
-    const Cand cands[] = {{1, 64, 0}, {0, 64, 0}, {0, 48, 0}, {0, 32, 0}};
+    const Cand cands[] = {{0, 64, 0}, {0, 48, 0}, {0, 32, 0}, {2, 64, 0}, {1, 64, 0}};
     const int chunks[] = {1, 2, 4, 8};
     double best = 1e30;
-    int bt = TILE, bc = 0, bk = 2, bp = 1;
+    int bt = TILE, bc = 0, bk = 2, bp = 0;
     for (const Cand& cd : cands)
         for (int ch : chunks) {
             const int cc = cd.ctas, t = cd.tile;

@@ -571,10 +571,80 @@ DEVI void pair_phase(const BuildParams& P, const Item& itd, int t, int T, int gi
     }
 }
 
+// ---------------------------------------------------------------------------
+// Reach screen.  Whether a pair fails the reach test is decided, for most
+// pairs, by a few reach rows: the rows whose control points depend on both
+// boundary states.  Rows fixed by one end state alone only restate that
+// state's own derivatives (which satisfy the bounds for states drawn inside
+// them), so they seldom fail.  The screen takes the middle first-derivative
+// row and the first and last second-derivative rows that mix both ends.  It
+// only orders the work: a pair that passes the screen still sees every row.
+// ---------------------------------------------------------------------------
+template <int G, int PD>
+struct Screen {
+    static constexpr int NS = 3;
+    // reach-row index (k-major canonical layout): k = 2, j = G-2 and j = PD-G; k = 1, j = (PD-1)/2
+    static constexpr int row(int s) { return s == 0 ? PD + (G - 2) : (s == 1 ? PD + (PD - G) : (PD - 1) / 2); }
+    static constexpr int index(int rr) { return rr == row(0) ? 0 : (rr == row(1) ? 1 : (rr == row(2) ? 2 : -1)); }
+};
+
+// The screen of one 4x4 micro-tile on the screen row-axes, stored [row][state]
+// (row si*M + a): returns the live pairs that do not certainly fail there.
+template <int M, int G, int PD>
+DEVI uint32_t screen_tile(int T, int gi, int gj, uint32_t live, const float* SCL, const float* SCR, const float* magR) {
+    float rm[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) rm[q] = 0.f;
+#pragma unroll
+    for (int r = 0; r < Screen<G, PD>::NS * M; ++r) {
+        const float4 u = *reinterpret_cast<const float4*>(SCL + r * T + 4 * gi);
+        const float4 w = *reinterpret_cast<const float4*>(SCR + r * T + 4 * gj);
+        const float uu[4] = {u.x, u.y, u.z, u.w};
+        const float ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+            for (int qb = 0; qb < 4; ++qb) rm[qa * 4 + qb] = fmaxf(rm[qa * 4 + qb], fabsf(uu[qa] + ww[qb]));
+    }
+    uint32_t fail = 0;
+#pragma unroll
+    for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+        for (int qb = 0; qb < 4; ++qb) {
+            const int q = qa * 4 + qb;
+            const float band = KR * (magR[4 * gi + qa] + magR[T + 4 * gj + qb]);
+            if (!(rm[q] <= 1.f + band)) fail |= 1u << q;
+        }
+    return live & ~fail;
+}
+
+// Rows of the per-duration FP32 table as the one-group kernel stages it in
+// shared memory: every table row (reach rows, interior control points, cost
+// rows, the two band rows) padded to [side][4] so that one 16-byte load
+// fetches the G coefficients a half needs.
+template <int G, int PD>
+struct PadTab {
+    using S = Shape<G, PD>;
+    static constexpr int ROW_D = S::RAX, ROW_C = S::RAX + S::NI, ROW_HC = ROW_C + G * PD, ROW_DC = ROW_HC + 1;
+    static constexpr int NROW = ROW_DC + 1;
+    static constexpr int FLOATS = NROW * 8;
+};
+
+template <int G, int PD>
+DEVI void stage_table(float* dst, const float* src, int tid, int nthr) {
+    constexpr int TG = 2 * G;
+    for (int u = tid; u < PadTab<G, PD>::FLOATS; u += nthr) {
+        const int row = u >> 3, side = (u >> 2) & 1, c = u & 3;
+        dst[u] = c < G ? src[row * TG + side * G + c] : 0.f;
+    }
+}
+
 template <int M, int G, int PD>
 __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
     using S = Shape<G, PD>;
-    constexpr int N_ = M * G, RAX = S::RAX, RR = M * RAX, NI = S::NI, TG = S::TG;
+    using PT = PadTab<G, PD>;
+    constexpr int N_ = M * G, RAX = S::RAX, RR = M * RAX, NI = S::NI;
+    static_assert(G <= 4 && M <= 3, "padded rows hold at most four coefficients");
     const int T = P.tile;  // shared-memory stride = tile side (multiple of 4, <= TILE)
     extern __shared__ __align__(16) float sm[];
     const int FRm = NI * P.max_rows;
@@ -590,15 +660,14 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
     float* magF = magR + 2 * T;
     float* xs = magF + 2 * T;
     float* xab = xs + 2 * T * N_;
-    float* tabs = xab + 2 * T * G;       // two duration tables (double buffer)
-    float* Ap = tabs + 2 * P.L.f_stride;
-    float* bp = Ap + RMAX * M;
+    float* tabs = xab + 2 * T * G;       // two padded duration tables (double buffer)
+    float* Ab = tabs + 2 * PT::FLOATS;   // [RMAX][4]: A_r (M entries), then b_r
     __shared__ long long s_item;
     __shared__ float s_rown1, s_bmax;
 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const long long nitems = (long long)P.info->items;
-    const TabLayout L = P.L;
+    const int fst = P.L.f_stride;
     unsigned long long rp_cnt = 0;
 
     for (;;) {
@@ -616,17 +685,20 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
             continue;
         }
         const QueryDesc& Qd = P.qd[itd.q];
-        const int k = itd.k, i0 = itd.i0, j0 = itd.j0, TI = itd.TI, TJ = itd.TJ, nk = itd.nk;
+        const int k = itd.k, i0 = itd.i0, j0 = itd.j0, TI = itd.TI, TJ = itd.TJ;
         const int ni4 = (TI + 3) & ~3, nj4 = (TJ + 3) & ~3;
+        const int S2 = ni4 + nj4;
         const int r0 = Qd.poly_off[k], nr = Qd.poly_off[k + 1] - r0;
         const long long rg0 = Qd.rowsOff + r0;
-        for (int u = tid; u < nr * M; u += nthr) Ap[u] = P.A32[rg0 * M + u];
-        for (int u = tid; u < nr; u += nthr) bp[u] = P.bc32[rg0 + u];
+        for (int u = tid; u < nr * 4; u += nthr) {
+            const int r = u >> 2, c = u & 3;
+            Ab[u] = c < M ? P.A32[(rg0 + r) * M + c] : (c == M ? P.bc32[rg0 + r] : 0.f);
+        }
         const int* members = P.members + Qd.listOff + (long long)k * Qd.N;
         float cx[M];
 #pragma unroll
         for (int a = 0; a < M; ++a) cx[a] = P.centers[(long long)(Qd.kOff + k) * 4 + a];
-        for (int u = tid; u < (ni4 + nj4) * N_; u += nthr) {
+        for (int u = tid; u < S2 * N_; u += nthr) {
             const int s = u / N_, e = u % N_;
             const bool right = s >= ni4;
             const int ls = right ? s - ni4 : s;
@@ -643,8 +715,9 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
             }
             xs[(right ? T + ls : ls) * N_ + e] = v;
         }
+        stage_table<G, PD>(tabs, P.tab32 + (long long)(Qd.tabOff + itc.t0) * fst, tid, nthr);
         __syncthreads();
-        for (int s = tid; s < ni4 + nj4; s += nthr) {
+        for (int s = tid; s < S2; s += nthr) {
             const bool right = s >= ni4;
             const int ls = right ? s - ni4 : s;
             const float* x = xs + (right ? T + ls : ls) * N_;
@@ -661,9 +734,9 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
             float rn = 0.f, bm = 0.f;
             for (int r = 0; r < nr; ++r) {
                 float s1 = 0.f;
-                for (int a = 0; a < M; ++a) s1 += fabsf(Ap[r * M + a]);
+                for (int a = 0; a < M; ++a) s1 += fabsf(Ab[r * 4 + a]);
                 rn = fmaxf(rn, s1);
-                bm = fmaxf(bm, fabsf(bp[r]));
+                bm = fmaxf(bm, fabsf(Ab[r * 4 + M]));
             }
             s_rown1 = rn * 1.0001f;
             s_bmax = bm;
@@ -683,73 +756,92 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
                 if (act && li < TI && lj < TJ) vmask |= 1u << (qa * 4 + qb);
                 if (diag_tile && li == lj) dmask |= 1u << (qa * 4 + qb);
             }
-        for (int u = tid; u < L.f_stride; u += nthr) tabs[u] = P.tab32[(long long)(Qd.tabOff + itc.t0) * L.f_stride + u];
-        __syncthreads();
         for (int t = itc.t0; t < itc.t1; ++t) {
-            const float* tab = tabs + ((t - itc.t0) & 1) * L.f_stride;
-            // reach and cost halves: one unit per (state, axis)
-            for (int u = tid; u < (ni4 + nj4) * M; u += nthr) {
-                const int s = u / M, a = u % M;
+            const float* tab = tabs + ((t - itc.t0) & 1) * PT::FLOATS;
+            // Halves.  Work units are balanced over the block: (state, axis,
+            // section) with section = the RAX reach rows or the DR*PD cost
+            // rows, then (state, interior control point) for the free rows.
+            // Every row is one 16-byte coefficient load and G FMAs (the same
+            // operation order as the reference formula h_0 x_0 + h_1 x_1 + ...).
+            const int nRC = S2 * M;
+            for (int u = tid; u < 2 * nRC; u += nthr) {
+                const bool cost = u >= nRC;
+                const int v = cost ? u - nRC : u;
+                const int s = v / M, a = v - s * M;
                 const bool right = s >= ni4;
                 const int ls = right ? s - ni4 : s;
                 const float* x = xs + (right ? T + ls : ls) * N_;
-                float xc[G];
+                float xc[4];
 #pragma unroll
-                for (int c = 0; c < G; ++c) xc[c] = x[c * M + a];
-                const int co = right ? G : 0;
-                float* dU = right ? UR : UL;
-#pragma unroll 3
-                for (int r = 0; r < RAX; ++r) {
-                    const float* h = tab + L.f_H + r * TG + co;
-                    float v = h[0] * xc[0];
+                for (int c = 0; c < 4; ++c) xc[c] = c < G ? x[c * M + a] : 0.f;
+                const float* trow = tab + (right ? 4 : 0);
+                if (!cost) {
+                    float* dU = (right ? UR : UL) + a * T + ls;
 #pragma unroll
-                    for (int c = 1; c < G; ++c) v = fmaf(h[c], xc[c], v);
-                    dU[(r * M + a) * T + ls] = v;
-                }
-                float* dC = right ? CRr : CL;
-                for (int d = 0; d < DR; ++d)
-                    for (int l = 0; l < PD; ++l) {
-                        const float* cc = tab + L.f_C + (d * PD + l) * TG + co;
-                        float v = cc[0] * xc[0];
-#pragma unroll
-                        for (int c = 1; c < G; ++c) v = fmaf(cc[c], xc[c], v);
-                        dC[((l * DR + d) * M + a) * T + ls] = v;
+                    for (int r = 0; r < RAX; ++r) {
+                        const float4 h = *reinterpret_cast<const float4*>(trow + r * 8);
+                        float w = h.x * xc[0];
+                        w = fmaf(h.y, xc[1], w);
+                        if (G > 2) w = fmaf(h.z, xc[2], w);
+                        if (G > 3) w = fmaf(h.w, xc[3], w);
+                        dU[r * M * T] = w;
                     }
+                } else {
+                    float* dC = (right ? CRr : CL) + a * T + ls;
+#pragma unroll
+                    for (int d = 0; d < G; ++d) {
+                        if (d < DR) {
+#pragma unroll
+                            for (int l = 0; l < PD; ++l) {
+                                const float4 h = *reinterpret_cast<const float4*>(trow + (PT::ROW_C + d * PD + l) * 8);
+                                float w = h.x * xc[0];
+                                w = fmaf(h.y, xc[1], w);
+                                if (G > 2) w = fmaf(h.z, xc[2], w);
+                                if (G > 3) w = fmaf(h.w, xc[3], w);
+                                dC[(l * DR + d) * M * T] = w;
+                            }
+                        }
+                    }
+                }
             }
-            // free-space halves: one unit per (state, interior control point)
-            for (int u = tid; u < (ni4 + nj4) * NI; u += nthr) {
-                const int s = u / NI, l = u % NI;
+            for (int u = tid; u < S2 * NI; u += nthr) {
+                const int s = u / NI, l = u - s * NI;
                 const bool right = s >= ni4;
                 const int ls = right ? s - ni4 : s;
                 const float* x = xs + (right ? T + ls : ls) * N_;
-                const float* dd = tab + L.f_D + l * TG + (right ? G : 0);
+                const float4 dd = *reinterpret_cast<const float4*>(tab + (PT::ROW_D + l) * 8 + (right ? 4 : 0));
                 float pt[M];
 #pragma unroll
                 for (int a = 0; a < M; ++a) {
-                    float v = dd[0] * x[a];
-#pragma unroll
-                    for (int c = 1; c < G; ++c) v = fmaf(dd[c], x[c * M + a], v);
-                    pt[a] = v;
+                    float w = dd.x * x[a];
+                    w = fmaf(dd.y, x[M + a], w);
+                    if (G > 2) w = fmaf(dd.z, x[2 * M + a], w);
+                    if (G > 3) w = fmaf(dd.w, x[3 * M + a], w);
+                    pt[a] = w;
                 }
-                float* dF = right ? FR : FL;
+                float* dF = (right ? FR : FL) + l * nr * T + ls;
+#pragma unroll 4
                 for (int r = 0; r < nr; ++r) {
-                    float v = Ap[r * M] * pt[0];
-#pragma unroll
-                    for (int a = 1; a < M; ++a) v = fmaf(Ap[r * M + a], pt[a], v);
-                    if (!right) v -= bp[r];
-                    dF[(l * nr + r) * T + ls] = v;
+                    const float4 ab = *reinterpret_cast<const float4*>(Ab + r * 4);
+                    float w = ab.x * pt[0];
+                    w = fmaf(ab.y, pt[1], w);
+                    if (M > 2) w = fmaf(ab.z, pt[2], w);
+                    if (!right) w -= (M > 2 ? ab.w : ab.z);
+                    dF[r * T] = w;
                 }
             }
             // band magnitudes
-            for (int s = tid; s < ni4 + nj4; s += nthr) {
+            for (int s = tid; s < S2; s += nthr) {
                 const bool right = s >= ni4;
                 const int ls = right ? s - ni4 : s;
                 const float* xa = xab + (right ? T + ls : ls) * G;
+                const float* hc = tab + PT::ROW_HC * 8 + (right ? 4 : 0);
+                const float* dc = tab + PT::ROW_DC * 8 + (right ? 4 : 0);
                 float mr = 0.f, md = 0.f;
 #pragma unroll
                 for (int c = 0; c < G; ++c) {
-                    mr = fmaf(tab[L.f_HC + (right ? G : 0) + c], xa[c], mr);
-                    md = fmaf(tab[L.f_DC + (right ? G : 0) + c], xa[c], md);
+                    mr = fmaf(hc[c], xa[c], mr);
+                    md = fmaf(dc[c], xa[c], md);
                 }
                 magR[(right ? T : 0) + ls] = mr;
                 magF[(right ? T : 0) + ls] = md * s_rown1 + (right ? 0.f : s_bmax);
@@ -757,13 +849,417 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
             __syncthreads();
 
             // the next duration's table goes to the other buffer while the pairs run
-            if (t + 1 < itc.t1) {
-                float* nxt = tabs + ((t + 1 - itc.t0) & 1) * L.f_stride;
-                for (int u = tid; u < L.f_stride; u += nthr) nxt[u] = P.tab32[(long long)(Qd.tabOff + t + 1) * L.f_stride + u];
-            }
-            if (act)
+            if (t + 1 < itc.t1)
+                stage_table<G, PD>(tabs + ((t + 1 - itc.t0) & 1) * PT::FLOATS,
+                                   P.tab32 + (long long)(Qd.tabOff + t + 1) * fst, tid, nthr);
+            if (act) {
                 pair_phase<M, G, PD>(P, itd, t, T, gi, gj, vmask, dmask, nr, DR, UL, UR, FL, FR, CL, CRr, magR, magF, KR, KF,
                                      rp_cnt);
+            }
+            __syncthreads();
+        }
+    }
+    if (rp_cnt) atomicAdd(&P.info->reach_pass, rp_cnt);
+}
+
+// ---------------------------------------------------------------------------
+// Screened FP32 pair kernel (the default one).  Same persistent item loop and
+// the same arithmetic as the one-group kernel, in five phases per duration:
+//   1. halves, stored per state ([state][row], rows padded to 16-byte quads,
+//      per-state stride = 4 mod 8 floats so that quad loads of different
+//      states fall in different bank groups); the screen row-axes are also
+//      stored [row][state] for the micro-tile screen;
+//   2. screen of every 4x4 micro-tile; pairs that do not certainly fail are
+//      appended to list 1 (shared memory);
+//   3. every reach and free row of the list-1 pairs, one pair per thread, four
+//      rows per 16-byte load; feasible pairs go to list 2, ambiguous ones to
+//      the FP64 re-check;
+//   4. cost halves of this duration, written over the free halves;
+//   5. costs of the list-2 pairs and the atomic merge into the pair slots.
+// Maxima are order-free and every sum keeps the reference order, so slots,
+// costs and re-check entries equal those of the other FP32 kernels.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int pad_odd4(int n) { return ((n + 3) / 8) * 8 + 4; }  // >= n, = 4 mod 8
+
+// per-state stride of the free / cost halves (both live in the same rows)
+__host__ __device__ inline int sc_free_stride(int NI, int max_rows, int PD, int PL) {
+    const int fr = NI * ((max_rows + 3) & ~3), cr = PD * PL;
+    return pad_odd4(fr > cr ? fr : cr);
+}
+
+template <int M, int G, int PD>
+struct ScShape {
+    using S = Shape<G, PD>;
+    static constexpr int RR = M * S::RAX;        // reach row-axes
+    static constexpr int RQ = (RR + 3) / 4;      // their 16-byte quads
+    static constexpr int RH = (RQ + 1) / 2;      // quads of the first half-unit
+    static constexpr int SU = pad_odd4(4 * RQ);  // per-state stride of the reach halves
+    static constexpr int NS = Screen<G, PD>::NS * M;
+    static constexpr int XS = pad_odd4(M * G);   // per-state stride of the staged states
+};
+
+// Reach halves of one state for quads [Q0, Q1): row-axis q = rr*M + a holds
+// sum_c H[rr][side][c] x[c][a]; rows past RR are 0 (neutral in max |u + w|).
+template <int M, int G, int PD, int Q0, int Q1>
+DEVI void reach_quads(const float (&x)[M * G], const float* trow, float* dU, float* dS, int T) {
+    constexpr int RR = ScShape<M, G, PD>::RR;
+#pragma unroll
+    for (int qd = Q0; qd < Q1; ++qd) {
+        float w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int q = 4 * qd + j;
+            w[j] = 0.f;
+            if (q < RR) {
+                const int rr = q / M, a = q % M;
+                const float4 h = *reinterpret_cast<const float4*>(trow + rr * 8);
+                float v = h.x * x[a];
+                if (G > 1) v = fmaf(h.y, x[M + a], v);
+                if (G > 2) v = fmaf(h.z, x[2 * M + a], v);
+                if (G > 3) v = fmaf(h.w, x[3 * M + a], v);
+                w[j] = v;
+                const int si = Screen<G, PD>::index(rr);
+                if (si >= 0) dS[(si * M + a) * T] = v;
+            }
+        }
+        *reinterpret_cast<float4*>(dU + 4 * qd) = make_float4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+template <int M, int G, int PD>
+DEVI void load_state(float (&x)[M * G], const float* xr) {
+    constexpr int XS = ScShape<M, G, PD>::XS;
+    float v[XS];
+#pragma unroll
+    for (int e = 0; e < XS; e += 4) {
+        const float4 f = *reinterpret_cast<const float4*>(xr + e);
+        v[e] = f.x;
+        v[e + 1] = f.y;
+        v[e + 2] = f.z;
+        v[e + 3] = f.w;
+    }
+#pragma unroll
+    for (int e = 0; e < M * G; ++e) x[e] = v[e];
+}
+
+template <int M, int G, int PD>
+__global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
+    using S = Shape<G, PD>;
+    using PT = PadTab<G, PD>;
+    using SS = ScShape<M, G, PD>;
+    constexpr int N_ = M * G, NI = S::NI, RQ = SS::RQ, RH = SS::RH, SU = SS::SU, NS = SS::NS, XS = SS::XS;
+    static_assert(G <= 4 && M <= 3, "padded rows hold at most four coefficients");
+    const int T = P.tile;  // tile side (multiple of 4, <= TILE)
+    extern __shared__ __align__(16) float sm[];
+    const int DR = P.cost_mode == 1 ? 1 : G;
+    const int PL = (DR * M + 3) & ~3;  // cost rows of one segment, padded with zeros
+    const int SF = sc_free_stride(NI, P.max_rows, PD, PL);
+    float* UL = sm;                  // [T][SU] reach halves, start states
+    float* UR = UL + T * SU;         //          end states
+    float* FL = UR + T * SU;         // [T][SF] free halves, then cost halves
+    float* FR = FL + T * SF;
+    float* SCL = FR + T * SF;        // [NS][T] screen row-axes
+    float* SCR = SCL + NS * T;
+    float* magR = SCR + NS * T;      // [2T] band magnitudes
+    float* magF = magR + 2 * T;
+    float* xs = magF + 2 * T;        // [2T][XS] centred states
+    float* xab = xs + 2 * T * XS;    // [2T][G] per-derivative maxima over the axes
+    float* tabs = xab + 2 * T * G;   // two padded duration tables
+    float* Ab = tabs + 2 * PT::FLOATS;  // [RMAX][4]: A_r, then b_r
+    uint16_t* list1 = reinterpret_cast<uint16_t*>(Ab + RMAX * 4);  // screened pairs (li << 8 | lj)
+    uint16_t* list2 = list1 + T * T;                                 // feasible pairs
+    __shared__ long long s_item;
+    __shared__ float s_rown1, s_bmax;
+    __shared__ int s_n1, s_n2;
+
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const long long nitems = (long long)P.info->items;
+    const int fst = P.L.f_stride;
+    unsigned long long rp_cnt = 0;
+    const float NEG_INF = -__int_as_float(0x7f800000);
+
+    for (;;) {
+        if (tid == 0) {
+            const long long it = (long long)atomicAdd(&P.info->ticket, 1u);
+            s_item = has_failed(P.info) ? 0x7fffffffffffLL : it;  // one decision for the whole block
+        }
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= nitems) break;
+        const ItemT itc = item_decode_chunk(P, item);
+        const Item& itd = itc.it;
+        if (itc.t0 >= itc.t1) {  // empty chunk (nT < number of chunks)
+            __syncthreads();     // everyone has read s_item before it is rewritten
+            continue;
+        }
+        const QueryDesc& Qd = P.qd[itd.q];
+        const int k = itd.k, i0 = itd.i0, j0 = itd.j0, TI = itd.TI, TJ = itd.TJ;
+        const int ni4 = (TI + 3) & ~3, nj4 = (TJ + 3) & ~3;
+        const int S2 = ni4 + nj4;
+        const int r0 = Qd.poly_off[k], nr = Qd.poly_off[k + 1] - r0;
+        const int nrp = (nr + 3) & ~3;
+        const long long rg0 = Qd.rowsOff + r0;
+        for (int u = tid; u < nr * 4; u += nthr) {
+            const int r = u >> 2, c = u & 3;
+            Ab[u] = c < M ? P.A32[(rg0 + r) * M + c] : (c == M ? P.bc32[rg0 + r] : 0.f);
+        }
+        const int* members = P.members + Qd.listOff + (long long)k * Qd.N;
+        float cx[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) cx[a] = P.centers[(long long)(Qd.kOff + k) * 4 + a];
+        for (int u = tid; u < S2 * XS; u += nthr) {
+            const int s = u / XS, e = u % XS;
+            const bool right = s >= ni4;
+            const int ls = right ? s - ni4 : s;
+            const int lidx = (right ? j0 : i0) + ls;
+            float v = 0.f;
+            if (e < N_ && ls < (right ? TJ : TI)) {
+                const long long id = mem_id(members[lidx]);
+                if (e < M) {
+                    if (P.in_f32) v = ((const float*)Qd.states)[id * N_ + e] - cx[e];
+                    else v = (float)(((const double*)Qd.states)[id * N_ + e] - (double)cx[e]);
+                } else {
+                    v = ldf(Qd.states, id * N_ + e, P.in_f32);
+                }
+            }
+            xs[(right ? T + ls : ls) * XS + e] = v;
+        }
+        stage_table<G, PD>(tabs, P.tab32 + (long long)(Qd.tabOff + itc.t0) * fst, tid, nthr);
+        __syncthreads();
+        for (int s = tid; s < S2; s += nthr) {
+            const bool right = s >= ni4;
+            const int ls = right ? s - ni4 : s;
+            const float* x = xs + (right ? T + ls : ls) * XS;
+            float* xa = xab + (right ? T + ls : ls) * G;
+#pragma unroll
+            for (int c = 0; c < G; ++c) {
+                float mx = 0.f;
+#pragma unroll
+                for (int a = 0; a < M; ++a) mx = fmaxf(mx, fabsf(x[c * M + a]));
+                xa[c] = mx;
+            }
+        }
+        if (tid == 0) {
+            float rn = 0.f, bm = 0.f;
+            for (int r = 0; r < nr; ++r) {
+                float s1 = 0.f;
+                for (int a = 0; a < M; ++a) s1 += fabsf(Ab[r * 4 + a]);
+                rn = fmaxf(rn, s1);
+                bm = fmaxf(bm, fabsf(Ab[r * 4 + M]));
+            }
+            s_rown1 = rn * 1.0001f;
+            s_bmax = bm;
+        }
+        __syncthreads();
+
+        const int ngi = ni4 >> 2, ngj = nj4 >> 2;
+        const bool act = tid < ngi * ngj;
+        const int gi = act ? tid / ngj : 0, gj = act ? tid % ngj : 0;
+        const bool diag_tile = (i0 == j0);
+        uint32_t live = 0;  // valid, off-diagonal pairs of this thread's micro-tile
+#pragma unroll
+        for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+            for (int qb = 0; qb < 4; ++qb) {
+                const int li = 4 * gi + qa, lj = 4 * gj + qb;
+                if (act && li < TI && lj < TJ && !(diag_tile && li == lj)) live |= 1u << (qa * 4 + qb);
+            }
+        for (int t = itc.t0; t < itc.t1; ++t) {
+            const float* tab = tabs + ((t - itc.t0) & 1) * PT::FLOATS;
+            if (tid == 0) {  // last read before the previous duration's closing barrier
+                s_n1 = 0;
+                s_n2 = 0;
+            }
+            // 1. halves: reach (two half-units per state), free (one unit per
+            // state and interior control point), band magnitudes
+            for (int u = tid; u < 2 * S2; u += nthr) {
+                const bool second = u >= S2;
+                const int s = second ? u - S2 : u;
+                const bool right = s >= ni4;
+                const int ls = right ? s - ni4 : s;
+                float x[N_];
+                load_state<M, G, PD>(x, xs + (right ? T + ls : ls) * XS);
+                const float* trow = tab + (right ? 4 : 0);
+                float* dU = (right ? UR : UL) + ls * SU;
+                float* dS = (right ? SCR : SCL) + ls;
+                if (!second) reach_quads<M, G, PD, 0, RH>(x, trow, dU, dS, T);
+                else reach_quads<M, G, PD, RH, RQ>(x, trow, dU, dS, T);
+            }
+            for (int u = tid; u < NI * S2; u += nthr) {
+                const int l = u / S2, s = u - l * S2;
+                const bool right = s >= ni4;
+                const int ls = right ? s - ni4 : s;
+                float x[N_];
+                load_state<M, G, PD>(x, xs + (right ? T + ls : ls) * XS);
+                const float4 dd = *reinterpret_cast<const float4*>(tab + (PT::ROW_D + l) * 8 + (right ? 4 : 0));
+                float pt[M];
+#pragma unroll
+                for (int a = 0; a < M; ++a) {
+                    float w = dd.x * x[a];
+                    if (G > 1) w = fmaf(dd.y, x[M + a], w);
+                    if (G > 2) w = fmaf(dd.z, x[2 * M + a], w);
+                    if (G > 3) w = fmaf(dd.w, x[3 * M + a], w);
+                    pt[a] = w;
+                }
+                float* dF = (right ? FR : FL) + ls * SF + l * nrp;
+                for (int rq = 0; rq < nrp; rq += 4) {
+                    float w4[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int r = rq + j;
+                        if (r < nr) {
+                            const float4 ab = *reinterpret_cast<const float4*>(Ab + r * 4);
+                            float w = ab.x * pt[0];
+                            w = fmaf(ab.y, pt[1], w);
+                            if (M > 2) w = fmaf(ab.z, pt[2], w);
+                            if (!right) w -= (M > 2 ? ab.w : ab.z);
+                            w4[j] = w;
+                        } else {
+                            w4[j] = right ? 0.f : NEG_INF;  // neutral in max(u + w)
+                        }
+                    }
+                    *reinterpret_cast<float4*>(dF + rq) = make_float4(w4[0], w4[1], w4[2], w4[3]);
+                }
+            }
+            for (int s = tid; s < S2; s += nthr) {
+                const bool right = s >= ni4;
+                const int ls = right ? s - ni4 : s;
+                const float* xa = xab + (right ? T + ls : ls) * G;
+                const float* hc = tab + PT::ROW_HC * 8 + (right ? 4 : 0);
+                const float* dc = tab + PT::ROW_DC * 8 + (right ? 4 : 0);
+                float mr = 0.f, md = 0.f;
+#pragma unroll
+                for (int c = 0; c < G; ++c) {
+                    mr = fmaf(hc[c], xa[c], mr);
+                    md = fmaf(dc[c], xa[c], md);
+                }
+                magR[(right ? T : 0) + ls] = mr;
+                magF[(right ? T : 0) + ls] = md * s_rown1 + (right ? 0.f : s_bmax);
+            }
+            __syncthreads();
+
+            // the next duration's table goes to the other buffer meanwhile
+            if (t + 1 < itc.t1)
+                stage_table<G, PD>(tabs + ((t + 1 - itc.t0) & 1) * PT::FLOATS,
+                                   P.tab32 + (long long)(Qd.tabOff + t + 1) * fst, tid, nthr);
+            // 2. screen and list 1
+            if (act) {
+                uint32_t surv = screen_tile<M, G, PD>(T, gi, gj, live, SCL, SCR, magR);
+                if (surv) {
+                    int pos = atomicAdd(&s_n1, __popc(surv));
+                    while (surv) {
+                        const int q = __ffs(surv) - 1;
+                        surv &= surv - 1;
+                        list1[pos++] = (uint16_t)(((4 * gi + (q >> 2)) << 8) | (4 * gj + (q & 3)));
+                    }
+                }
+            }
+            __syncthreads();
+
+            // 3. every reach and free row of the screened pairs
+            const int n1 = s_n1;
+            const int FQ = NI * nrp;
+            for (int e = tid; e < n1; e += nthr) {
+                const int v = list1[e];
+                const int li = v >> 8, lj = v & 255;
+                const float* ul = UL + li * SU;
+                const float* ur = UR + lj * SU;
+                float r4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int qd = 0; qd < RQ; ++qd) {
+                    const float4 a = *reinterpret_cast<const float4*>(ul + 4 * qd);
+                    const float4 b = *reinterpret_cast<const float4*>(ur + 4 * qd);
+                    r4[0] = fmaxf(r4[0], fabsf(a.x + b.x));
+                    r4[1] = fmaxf(r4[1], fabsf(a.y + b.y));
+                    r4[2] = fmaxf(r4[2], fabsf(a.z + b.z));
+                    r4[3] = fmaxf(r4[3], fabsf(a.w + b.w));
+                }
+                const float rm = fmaxf(fmaxf(r4[0], r4[1]), fmaxf(r4[2], r4[3]));
+                const float bandR = KR * (magR[li] + magR[T + lj]);
+                if (!(rm <= 1.f + bandR)) continue;  // certain reach failure
+                const bool rpass = rm <= 1.f - bandR;
+                rp_cnt += rpass ? 1u : 0u;
+                const float* fl = FL + li * SF;
+                const float* fr = FR + lj * SF;
+                float f4[4] = {NEG_INF, NEG_INF, NEG_INF, NEG_INF};
+#pragma unroll 2
+                for (int r = 0; r < FQ; r += 4) {
+                    const float4 a = *reinterpret_cast<const float4*>(fl + r);
+                    const float4 b = *reinterpret_cast<const float4*>(fr + r);
+                    f4[0] = fmaxf(f4[0], a.x + b.x);
+                    f4[1] = fmaxf(f4[1], a.y + b.y);
+                    f4[2] = fmaxf(f4[2], a.z + b.z);
+                    f4[3] = fmaxf(f4[3], a.w + b.w);
+                }
+                const float fm = fmaxf(fmaxf(f4[0], f4[1]), fmaxf(f4[2], f4[3]));
+                const float bandF = KF * (magF[li] + magF[T + lj]);
+                if (!(fm <= bandF)) continue;  // certain free-space failure
+                const bool fpass = fm <= -bandF;
+                if (rpass && fpass) list2[atomicAdd(&s_n2, 1)] = (uint16_t)v;
+                else append_recheck(P, itd.q, k, i0 + li, j0 + lj, t);
+            }
+            __syncthreads();
+
+            const int n2 = s_n2;
+            if (n2 > 0) {
+                // 4. cost halves of this duration over the free halves: segment
+                // l holds rows e = d*M + a (d < DR), zero-padded to PL
+                for (int u = tid; u < PD * S2; u += nthr) {
+                    const int l = u / S2, s = u - l * S2;
+                    const bool right = s >= ni4;
+                    const int ls = right ? s - ni4 : s;
+                    float x[N_];
+                    load_state<M, G, PD>(x, xs + (right ? T + ls : ls) * XS);
+                    float val[((G * M + 3) & ~3)];
+#pragma unroll
+                    for (int e = 0; e < ((G * M + 3) & ~3); ++e) val[e] = 0.f;
+#pragma unroll
+                    for (int d = 0; d < G; ++d) {
+                        if (d < DR) {
+                            const float4 h =
+                                *reinterpret_cast<const float4*>(tab + (PT::ROW_C + d * PD + l) * 8 + (right ? 4 : 0));
+#pragma unroll
+                            for (int a = 0; a < M; ++a) {
+                                float w = h.x * x[a];
+                                if (G > 1) w = fmaf(h.y, x[M + a], w);
+                                if (G > 2) w = fmaf(h.z, x[2 * M + a], w);
+                                if (G > 3) w = fmaf(h.w, x[3 * M + a], w);
+                                val[d * M + a] = w;
+                            }
+                        }
+                    }
+                    float* dC = (right ? FR : FL) + ls * SF + l * PL;
+#pragma unroll
+                    for (int e = 0; e < ((G * M + 3) & ~3); e += 4)
+                        if (e < PL) *reinterpret_cast<float4*>(dC + e) = make_float4(val[e], val[e + 1], val[e + 2], val[e + 3]);
+                }
+                __syncthreads();
+                // 5. costs of the feasible pairs (segment sums in row order)
+                for (int e = tid; e < n2; e += nthr) {
+                    const int v = list2[e];
+                    const int li = v >> 8, lj = v & 255;
+                    const float* cl = FL + li * SF;
+                    const float* cr = FR + lj * SF;
+                    float cs = 0.f;
+#pragma unroll
+                    for (int l = 0; l < PD; ++l) {
+                        float ss = 0.f;
+                        for (int q = 0; q < PL; q += 4) {
+                            const float4 a = *reinterpret_cast<const float4*>(cl + l * PL + q);
+                            const float4 b = *reinterpret_cast<const float4*>(cr + l * PL + q);
+                            const float d0 = a.x + b.x, d1 = a.y + b.y, d2 = a.z + b.z, d3 = a.w + b.w;
+                            ss = fmaf(d0, d0, ss);
+                            ss = fmaf(d1, d1, ss);
+                            ss = fmaf(d2, d2, ss);
+                            ss = fmaf(d3, d3, ss);
+                        }
+                        cs += sqrtf(ss);
+                    }
+                    const long long slot = itd.base + (long long)(i0 + li) * itd.nk + (j0 + lj);
+                    atomicOr(&P.resBits[slot], 1u << t);
+                    atomicMin(&P.resKey[slot], key_f32(cs, t));
+                }
+            }
             __syncthreads();
         }
     }
@@ -1653,7 +2149,9 @@ __global__ void __launch_bounds__(256) k_pairs_f64(BuildParams P) {
 // ---------------------------------------------------------------------------
 template <int M, int G, int PD>
 __global__ void k_recheck(BuildParams P) {
-    // one warp per entry; lanes take the rows (each row in canonical order)
+    // one warp per entry, one warp per block so that entries spread over all
+    // SMs (GB300's FP64 rate per SM is low); lanes take the rows, each row in
+    // canonical order
     using S = Shape<G, PD>;
     constexpr int N_ = M * G, RAX = S::RAX, NI = S::NI, TG = S::TG;
     if (has_failed(P.info)) return;
@@ -2125,6 +2623,28 @@ size_t smem_fast(const BuildParams& P) {
     return f * sizeof(float);
 }
 
+// unscreened one-group FP32 kernel: halves, states, two padded tables, A|b rows
+template <int M, int G, int PD>
+size_t smem_one(const BuildParams& P) {
+    using S = Shape<G, PD>;
+    const int RR = M * S::RAX, FRm = S::NI * P.max_rows, CRW = G * PD * M;
+    const size_t T = (size_t)P.tile;
+    size_t f = (size_t)(2 * RR + 2 * FRm + 2 * CRW + 4) * T + 2 * T * (M * G + G) + 2 * PadTab<G, PD>::FLOATS + RMAX * 4;
+    return f * sizeof(float);
+}
+
+// screened FP32 kernel: transposed halves, screen rows, states, two padded
+// tables, A|b rows and the two pair lists
+template <int M, int G, int PD>
+size_t smem_sc(const BuildParams& P) {
+    using SS = ScShape<M, G, PD>;
+    const int DR = P.cost_mode == 1 ? 1 : G;
+    const size_t T = (size_t)P.tile;
+    const size_t SF = (size_t)sc_free_stride(Shape<G, PD>::NI, P.max_rows, PD, (DR * M + 3) & ~3);
+    size_t f = T * (2 * SS::SU + 2 * SF + 2 * SS::NS + 4) + 2 * T * (SS::XS + G) + 2 * PadTab<G, PD>::FLOATS + RMAX * 4;
+    return f * sizeof(float) + 2 * T * T * sizeof(uint16_t);
+}
+
 template <int M, int G, int PD>
 size_t smem_ws(const BuildParams& P) {
     using S = Shape<G, PD>;
@@ -2167,7 +2687,7 @@ int launch_tc(const BuildParams& P, cudaStream_t st, int num_sms, int ctas_per_s
     k_pairs_tc<M, G, PD, BF><<<num_sms * occ, 256, sm, st>>>(P);
     if (e1) cudaEventRecord(e1, st);
     ++*launches;
-    k_recheck<M, G, PD><<<num_sms * 4, 256, 0, st>>>(P);
+    k_recheck<M, G, PD><<<num_sms * 16, 32, 0, st>>>(P);
     ++*launches;
     return (int)cudaGetLastError();
 }
@@ -2192,28 +2712,31 @@ int launch_pairs(const BuildParams& P, cudaStream_t st, int num_sms, int ctas_pe
         k_pairs_f64<M, G, PD><<<num_sms * occ, 256, sm, st>>>(P);
         if (e1) cudaEventRecord(e1, st);
         ++*launches;
-    } else if (P.pipeline && P.tile == TILE && smem_ws<M, G, PD>(P) <= 227 * 1024) {
+    } else if (P.pipeline == 1 && P.tile == TILE && smem_ws<M, G, PD>(P) <= 227 * 1024) {
         const size_t sm = smem_ws<M, G, PD>(P);
         cudaFuncSetAttribute(k_pairs_ws<M, G, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e0) cudaEventRecord(e0, st);
         k_pairs_ws<M, G, PD><<<num_sms, 512, sm, st>>>(P);
         if (e1) cudaEventRecord(e1, st);
         ++*launches;
-        k_recheck<M, G, PD><<<num_sms * 4, 256, 0, st>>>(P);
+        k_recheck<M, G, PD><<<num_sms * 16, 32, 0, st>>>(P);
         ++*launches;
     } else {
-        const size_t sm = smem_fast<M, G, PD>(P);
+        // pipeline 0: screened kernel; 2: every pair through all rows
+        const bool sc = P.pipeline != 2;
+        auto kern = sc ? k_pairs_sc<M, G, PD> : k_pairs_fast<M, G, PD>;
+        const size_t sm = sc ? smem_sc<M, G, PD>(P) : smem_one<M, G, PD>(P);
         const int threads = (P.tile / 4) * (P.tile / 4);
-        cudaFuncSetAttribute(k_pairs_fast<M, G, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pairs_fast<M, G, PD>, threads, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, sm);
         if (occ < 1) occ = 1;
         if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
         if (e0) cudaEventRecord(e0, st);
-        k_pairs_fast<M, G, PD><<<num_sms * occ, threads, sm, st>>>(P);
+        kern<<<num_sms * occ, threads, sm, st>>>(P);
         if (e1) cudaEventRecord(e1, st);
         ++*launches;
-        k_recheck<M, G, PD><<<num_sms * 4, 256, 0, st>>>(P);
+        k_recheck<M, G, PD><<<num_sms * 16, 32, 0, st>>>(P);
         ++*launches;
     }
     return (int)cudaGetLastError();

@@ -122,7 +122,7 @@ struct BuildParams {
     int cost_mode, in_f32, arith, max_rows;
     int tile;                  // tile side of the pair kernel (autotuned, <= TILE)
     int tchunks;               // duration chunks per tile (work items = tiles x tchunks)
-    int pipeline;              // 1: warp-specialised FP32 pair kernel (64-state tiles)
+    int pipeline;              // FP32 pair kernel: 0 screened, 1 warp-specialised (64-state tiles), 2 unscreened
     double eps;
     const QueryDesc* qd;       // [Q]
     const long long* pfxMask;  // [Q+1] prefix of N*W        (membership threads)

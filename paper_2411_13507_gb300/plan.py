@@ -450,7 +450,7 @@ class Planner:
                         "cost": float(o["cost"].item())})
         return res
 
-    def set_tile(self, tile: int = 0, ctas_per_sm: int = 0, tchunks: int = 0, pipeline: int = 1) -> None:
+    def set_tile(self, tile: int = 0, ctas_per_sm: int = 0, tchunks: int = 0, pipeline: int = 0) -> None:
         rc = self.lib.plan_set_tile(self.ctx, int(tile), int(ctas_per_sm), int(tchunks), int(pipeline))
         if rc != 0:
             raise self._err(rc, "plan_set_tile")

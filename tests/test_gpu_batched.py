@@ -106,7 +106,7 @@ def test_autotune_choice_keeps_results(tmp_path):
         same_graph(g.to_numpy(), r)
     res2 = autotune.tune(pl, "test-small", reps=1, path=cache)
     assert res2["cached"] and res2["tile"] == res["tile"]
-    for tile, ch, pipe in ((32, 1, 0), (44, 3, 0), (64, 8, 0), (64, 2, 1), (64, 5, 1)):
+    for tile, ch, pipe in ((32, 1, 0), (44, 3, 0), (64, 8, 0), (64, 2, 1), (64, 5, 1), (64, 2, 2), (20, 4, 2)):
         pl.set_tile(tile, 0, ch, pipe)
         graphs3 = pl.build_batched(dps)
         for r, g in zip(ref, graphs3):

@@ -101,6 +101,24 @@ def test_3d_degree5(arith):
     check_full(prob, arith, input="f64")
 
 
+@pytest.mark.parametrize("pipeline,tile", [(0, 64), (0, 8), (0, 28), (2, 64), (1, 64)])
+def test_fp32_pair_kernels_loose_and_tight_bounds(pipeline, tile):
+    """Every FP32 pair-kernel variant matches the oracle whether nearly every
+    pair survives the reach screen (loose bounds: the survivor list overflows
+    and threads take the extra pairs themselves), about a tenth does, or none."""
+    for scale in (1000.0, 1.0, 0.05):
+        prob = synth.triple_integrator_3d(7, N=600, K=5, nT=5)
+        prob.model.bounds = tuple(float(b) * scale for b in prob.model.bounds)
+        pl = P.Planner.for_problem(prob, arith="f32", input="f32")
+        pl.set_tile(tile, 0, 0, pipeline)
+        _, _, g, info = gpu_build(prob, "f32", planner=pl)
+        csr = oracle.OracleProblem(prob).csr(with_detail=True)
+        parity.compare_full(g.to_numpy(), csr, prob.N, prob.nT, "f32")
+        assert info["edges"] == len(csr["col"])
+        if scale == 1000.0:
+            assert info["reach_pass"] > 0.9 * info["checks"]
+
+
 def test_nT_extremes():
     p1 = synth.double_integrator_2d(4, N=200, K=4, nT=1)
     check_full(p1, "f64")
