@@ -97,6 +97,9 @@ struct plan_ctx {
     unsigned long long* sbest = nullptr;
     int* spred = nullptr;
     unsigned char* sfront = nullptr;
+    long long capLast = -1;
+    unsigned long long* slast = nullptr;
+    unsigned long long* snear = nullptr;   // [4][SEARCH_MAX_BLOCKS]
     // timing
     bool timing = false;
     bool accounting = false;
@@ -356,7 +359,7 @@ void plan_destroy(plan_ctx* c) {
     if (c->stream || c->d_info) cudaStreamSynchronize(c->stream);
     void* dev[] = {c->d_tab64, c->d_tab32, c->d_info, c->memMask, c->counts, c->members, c->localIdx, c->centers,
                    c->blim64, c->A32, c->blim32, c->bc32, c->resOff, c->itemOff, c->ntile, c->tsize, c->rowCount,
-                   c->resBits, c->resKey, c->emitPre, c->recheck, c->sdist, c->sbest, c->spred, c->sfront,
+                   c->resBits, c->resKey, c->emitPre, c->recheck, c->sdist, c->sbest, c->spred, c->sfront, c->slast, c->snear,
                    c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem, c->d_qMem, c->d_sqd, c->memOff};
     for (void* p : dev)
         if (p) cudaFree(p);
@@ -733,6 +736,12 @@ int plan_search(plan_ctx* c, int N, const void* states, const plan_edges* edges,
             return PLAN_ERR_NO_MEMORY;
         c->capS = N;
     }
+    if (N > c->capLast) {
+        if (!dalloc(c, &c->slast, N)) return PLAN_ERR_NO_MEMORY;
+        c->capLast = N;
+    }
+    if (!c->snear && !dalloc(c, &c->snear, 4LL * SEARCH_MAX_BLOCKS)) return PLAN_ERR_NO_MEMORY;
+    if (c->num_sms > SEARCH_MAX_BLOCKS) return fail(c, PLAN_ERR_UNSUPPORTED, "more SMs than the search scratch holds");
     SearchParams S;
     memset(&S, 0, sizeof(S));
     S.N = N;
@@ -753,7 +762,8 @@ int plan_search(plan_ctx* c, int N, const void* states, const plan_edges* edges,
     S.dist = c->sdist;
     S.bestU = c->sbest;
     S.pred = c->spred;
-    S.front = c->sfront;
+    S.last = c->slast;
+    S.near_blk = c->snear;
     S.path = path;
     S.path_cap = path_cap;
     S.path_len = path_len;
@@ -761,7 +771,7 @@ int plan_search(plan_ctx* c, int N, const void* states, const plan_edges* edges,
     S.info = c->d_info;
     S.max_sweeps = c->max_sweeps > 0 ? c->max_sweeps : N + 1;
     S.spin_limit = c->spin_limit > 0 ? c->spin_limit : (1LL << 24);
-    cudaError_t e = cudaMemsetAsync(&c->d_info->bar_count, 0, sizeof(unsigned) * 2, c->stream);
+    cudaError_t e = cudaMemsetAsync(&c->d_info->bar[0], 0, sizeof(unsigned long long) * 3, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset barrier");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->timing) {

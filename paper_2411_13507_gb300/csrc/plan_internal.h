@@ -70,9 +70,7 @@ struct DevInfo {
     int goal;
     // search scratch
     unsigned long long near_d[2];
-    unsigned int bar_count;
-    unsigned int bar_gen;
-    int changed[3];
+    unsigned long long bar[3];       // grid-barrier words, used in rotation: arrivals | raised flags << 32
     int path_len;
     unsigned long long work[3];
 };
@@ -173,7 +171,8 @@ struct SearchParams {
     unsigned long long* dist;  // [N] bit patterns of non-negative doubles
     unsigned long long* bestU; // [N]
     int* pred;                 // [N]
-    unsigned char* front;      // [2][N]
+    unsigned long long* last;  // [N] distance each vertex last relaxed its out-edges from
+    unsigned long long* near_blk;  // [4][blocks] per-block nearest candidates (bits, id) for start, goal
     int32_t* path;
     int path_cap;
     int32_t* path_len;
@@ -181,7 +180,16 @@ struct SearchParams {
     DevInfo* info;
     int max_sweeps;
     long long spin_limit;
+    int walk_smem;             // vertices whose pred[] the walk stages in shared memory
 };
+
+// Shared-memory staging of pred[] for the walk (ints; 64 KB).
+constexpr int SEARCH_WALK_SMEM = 16384;
+// Blocks of the cooperative search (one per SM) that its scratch provides for.
+constexpr int SEARCH_MAX_BLOCKS = 1024;
+// Owned vertices per search block whose out-edge range and last-relaxed
+// distance live in shared memory (the rest are read from global memory).
+constexpr int SEARCH_OWN_CAP = 2048;
 
 // One query of a batched search (device array).
 struct SearchQueryDesc {

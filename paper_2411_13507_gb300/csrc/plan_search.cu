@@ -3,7 +3,7 @@
 // cooperative kernel with a bounded software grid barrier.
 //
 // Distances are FP64 bit patterns (non-negative doubles order like unsigned
-// integers), relaxed with atomicMin by a frontier sweep (Bellman-Ford).  With
+// integers), relaxed with atomicMin by frontier sweeps (Bellman-Ford).  With
 // non-negative weights and round-to-nearest, fl(d + w) is monotone in d and
 // >= d, so the sweep's fixed point is the minimum over paths of the
 // left-to-right rounded path sum -- the same value Dijkstra produces.  The
@@ -35,37 +35,43 @@ DEVI bool failed_s(const DevInfo* info) {
     return s != 0 && s != PLAN_ERR_NO_PATH;
 }
 
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).  The
-// spin is bounded: on expiry the block records PLAN_ERR_TIMEOUT and returns
-// false instead of waiting forever.
-DEVI bool grid_sync(DevInfo* info, unsigned nblocks, long long spin_limit) {
+// Grid-wide barrier for a cooperative launch (all blocks co-resident): one
+// release-add per block on a 64-bit word -- 1 for the arrival, plus 2^32 when
+// the block raises its flag -- and an acquire-load poll until the low half
+// counts every block; the high half then tells every block how many raised
+// the flag.  Three words are used in rotation (round r uses word r mod 3):
+// once round r completes, every block has left the poll of round r-1, so
+// block 0 clears that word, which round r+2 uses next.  All three start at
+// zero (cleared before the launch).  The spin is bounded: on expiry the block
+// records PLAN_ERR_TIMEOUT and returns false instead of waiting forever.
+DEVI bool grid_sync(DevInfo* info, unsigned nblocks, long long spin_limit, int& round, bool raise = false,
+                    unsigned* raised = nullptr) {
     __shared__ int s_ok;
+    __shared__ unsigned s_raised;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned* genp = &info->bar_gen;
-        const unsigned gen = *genp;
-        __threadfence();
-        const unsigned arrived = atomicAdd(&info->bar_count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&info->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&info->bar_gen, 1u);
-        } else {
-            long long it = 0;
-            while (*genp == gen) {
-                if (++it > spin_limit) {
-                    set_status_s(info, PLAN_ERR_TIMEOUT, DET_BARRIER);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
+        unsigned long long* word = &info->bar[round % 3];
+        const unsigned long long inc = 1ull | (raise ? (1ull << 32) : 0ull);
+        unsigned long long cur = 0;
+        asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(word), "l"(inc) : "memory");
+        long long it = 0;
+        for (;;) {
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(cur) : "l"(word) : "memory");
+            if ((unsigned)(cur & 0xffffffffull) >= nblocks) break;
+            if (++it > spin_limit) {
+                set_status_s(info, PLAN_ERR_TIMEOUT, DET_BARRIER);
+                ok = 0;
+                break;
             }
         }
-        __threadfence();
+        if (ok && blockIdx.x == 0) info->bar[(round + 2) % 3] = 0ull;
         s_ok = ok;
+        s_raised = (unsigned)(cur >> 32);
     }
     __syncthreads();
+    ++round;
+    if (raised) *raised = s_raised;
     return s_ok != 0;
 }
 
@@ -74,153 +80,302 @@ DEVI double ldd(const void* p, long long i, int f32) {
 }
 }  // namespace
 
-__global__ void __launch_bounds__(1024) k_search(SearchParams P) {
+// (bits, id) pairs ordered lexicographically: the nearest vertex, ties to the lowest id
+DEVI void keep_min(unsigned long long& kb, int& ki, unsigned long long ob, int oi) {
+    if (ob < kb || (ob == kb && oi < ki)) {
+        kb = ob;
+        ki = oi;
+    }
+}
+
+// Exclusive prefix of cnt[0..n) in place (n <= blockDim.x = 1024); cnt[n] =
+// the total, which is returned to every thread.
+DEVI int block_scan_degrees(int* cnt, int n, int* wsum) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int x = tid < n ? cnt[tid] : 0;
+    int incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        int t = lane < nw ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        wsum[lane] = t;  // inclusive per-warp totals
+        if (lane == 31) wsum[32] = t;
+    }
+    __syncthreads();
+    const int excl = incl - x + (wid > 0 ? wsum[wid - 1] : 0);
+    if (tid < n) cnt[tid] = excl;
+    if (tid == 0) cnt[n] = wsum[32];
+    __syncthreads();
+    return cnt[n];
+}
+
+// Largest i in [0, n) with pre[i] <= q (pre strictly increasing: every listed
+// vertex has at least one out-edge).
+DEVI int find_entry(const int* pre, int n, int q) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= q) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The search kernel launches one 1024-thread block per SM.  Phases:
+//   0. every block initialises its share of the per-vertex arrays and finds
+//      its nearest candidates for the start and goal; after one grid barrier
+//      every block reduces the candidates of all blocks itself;
+//   1. frontier sweeps.  A vertex is on the frontier when its distance is
+//      below the value it last relaxed its out-edges from (kept in last[]),
+//      so no frontier flags are written or read.  The sweep that relaxes
+//      nothing ends the loop;
+//   2. predecessors in two passes (minimum dist[u], then minimum u);
+//   3. block 0 stages pred[] in shared memory and walks goal -> start.
+__global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
+    extern __shared__ int s_pred[];
+    __shared__ unsigned long long s_kb[2][32];
+    __shared__ int s_ki[2][32];
+    __shared__ int s_nf;                        // listed vertices of this round
+    __shared__ int s_v[1024], s_e0[1024];       // vertex, first out-edge
+    __shared__ int s_pre[1025];                 // out-degree, then its exclusive prefix
+    __shared__ unsigned long long s_dv[1024];   // distance the vertex relaxes from
+    __shared__ int s_wsum[33];
+    __shared__ int s_ro[2 * SEARCH_OWN_CAP];                   // out-edge range of owned vertex k
+    __shared__ unsigned long long s_last[SEARCH_OWN_CAP];      // distance it last relaxed from
     const unsigned nb = gridDim.x;
+    int bar_round = 0;
     const long long gtid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long nthr = (long long)gridDim.x * blockDim.x;
-    const int lane = threadIdx.x & 31;
-    const long long gwarp = gtid >> 5, nwarps = nthr >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     DevInfo* info = P.info;
     const int N = P.N;
 
-    // phase 0: initialise scratch
+    // phase 0: per-vertex arrays; every block's nearest candidates (A6:
+    // canonical FP64 squared distance summed left to right, ties to the
+    // lowest id) go to near_blk, and after the barrier every block reduces
+    // them to the same start and goal
     if (gtid == 0) {
-        info->near_d[0] = ~0ull;
-        info->near_d[1] = ~0ull;
-        info->start = 0x7fffffff;
-        info->goal = 0x7fffffff;
-        info->changed[0] = 0;
-        info->changed[1] = 0;
-        info->changed[2] = 0;
         const long long E = *P.count;
         if (E < 0 || E > P.cap) set_status_s(info, PLAN_ERR_INVALID_ARG, DET_OUTPUT);
     }
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const long long nown = N > (int)blockIdx.x ? (N - 1 - (long long)blockIdx.x) / nb + 1 : 0;  // owned vertices
+    const int ncache = (int)(nown < SEARCH_OWN_CAP ? nown : SEARCH_OWN_CAP);
+    for (int k = tid; k < ncache; k += nt) {
+        const long long v = blockIdx.x + (long long)k * nb;
+        s_ro[2 * k] = __ldg(&P.row_off[v]);
+        s_ro[2 * k + 1] = __ldg(&P.row_off[v + 1]);
+        s_last[k] = DINF;
+    }
+    unsigned long long kb[2] = {~0ull, ~0ull};
+    int ki[2] = {0x7fffffff, 0x7fffffff};
     for (long long v = gtid; v < N; v += nthr) {
         P.dist[v] = DINF;
+        P.last[v] = DINF;
         P.bestU[v] = ~0ull;
         P.pred[v] = 0x7fffffff;
-        P.front[v] = 0;
-        P.front[N + v] = 0;
+        double ds = 0.0, dg = 0.0;
+        for (int a = 0; a < P.m; ++a) {
+            const double x = ldd(P.states, v * P.n + a, P.in_f32);
+            const double ts = __dsub_rn(x, P.start[a]);
+            const double tg = __dsub_rn(x, P.goal[a]);
+            ds = __dadd_rn(ds, __dmul_rn(ts, ts));
+            dg = __dadd_rn(dg, __dmul_rn(tg, tg));
+        }
+        keep_min(kb[0], ki[0], (unsigned long long)__double_as_longlong(ds), (int)v);
+        keep_min(kb[1], ki[1], (unsigned long long)__double_as_longlong(dg), (int)v);
     }
-    if (!grid_sync(info, nb, P.spin_limit)) return;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_down_sync(0xffffffffu, kb[h], o);
+            const int oi = __shfl_down_sync(0xffffffffu, ki[h], o);
+            keep_min(kb[h], ki[h], ob, oi);
+        }
+        if (lane == 0) {
+            s_kb[h][wid] = kb[h];
+            s_ki[h][wid] = ki[h];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        const int h = threadIdx.x;
+        unsigned long long b0 = ~0ull;
+        int i0 = 0x7fffffff;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) keep_min(b0, i0, s_kb[h][w], s_ki[h][w]);
+        P.near_blk[4 * blockIdx.x + 2 * h] = b0;
+        P.near_blk[4 * blockIdx.x + 2 * h + 1] = (unsigned long long)(unsigned)i0;
+    }
+    if (!grid_sync(info, nb, P.spin_limit, bar_round)) return;
     if (failed_s(info)) return;
-
-    // A6: nearest vertex to the start and goal positions (canonical FP64
-    // squared distance summed left to right; ties to the lowest id)
-    for (long long v = gtid; v < N; v += nthr) {
-        double ds = 0.0, dg = 0.0;
-        for (int a = 0; a < P.m; ++a) {
-            const double x = ldd(P.states, v * P.n + a, P.in_f32);
-            const double ts = __dsub_rn(x, P.start[a]);
-            const double tg = __dsub_rn(x, P.goal[a]);
-            ds = __dadd_rn(ds, __dmul_rn(ts, ts));
-            dg = __dadd_rn(dg, __dmul_rn(tg, tg));
+    if (threadIdx.x < 64) {  // warp 0: start (h = 0) from lanes' blocks; warp 1: goal
+        const int h = threadIdx.x >> 5;
+        unsigned long long b0 = ~0ull;
+        int i0 = 0x7fffffff;
+        volatile unsigned long long* nbk = P.near_blk;
+        for (unsigned q = lane; q < nb; q += 32) keep_min(b0, i0, nbk[4 * q + 2 * h], (int)nbk[4 * q + 2 * h + 1]);
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_down_sync(0xffffffffu, b0, o);
+            const int oi = __shfl_down_sync(0xffffffffu, i0, o);
+            keep_min(b0, i0, ob, oi);
         }
-        atomicMin(&info->near_d[0], (unsigned long long)__double_as_longlong(ds));
-        atomicMin(&info->near_d[1], (unsigned long long)__double_as_longlong(dg));
-    }
-    if (!grid_sync(info, nb, P.spin_limit)) return;
-    for (long long v = gtid; v < N; v += nthr) {
-        double ds = 0.0, dg = 0.0;
-        for (int a = 0; a < P.m; ++a) {
-            const double x = ldd(P.states, v * P.n + a, P.in_f32);
-            const double ts = __dsub_rn(x, P.start[a]);
-            const double tg = __dsub_rn(x, P.goal[a]);
-            ds = __dadd_rn(ds, __dmul_rn(ts, ts));
-            dg = __dadd_rn(dg, __dmul_rn(tg, tg));
+        if (lane == 0) {
+            s_ki[h][0] = i0;
+            if (blockIdx.x == 0) {
+                info->near_d[h] = b0;
+                if (h == 0) info->start = i0;
+                else info->goal = i0;
+            }
         }
-        if ((unsigned long long)__double_as_longlong(ds) == info->near_d[0]) atomicMin(&info->start, (int)v);
-        if ((unsigned long long)__double_as_longlong(dg) == info->near_d[1]) atomicMin(&info->goal, (int)v);
     }
-    if (!grid_sync(info, nb, P.spin_limit)) return;
-    const int s = *((volatile int*)&info->start), g = *((volatile int*)&info->goal);
+    __syncthreads();
+    const int s = s_ki[0][0], g = s_ki[1][0];
     if (s < 0 || s >= N || g < 0 || g >= N) {
         if (gtid == 0) set_status_s(info, PLAN_ERR_INVALID_ARG, DET_WALK);
         return;
     }
-    if (gtid == 0) {
-        P.dist[s] = 0ull;
-        P.front[s] = 1;
-    }
-    if (!grid_sync(info, nb, P.spin_limit)) return;
 
-    // A7: frontier sweeps until no distance changes.  A relaxation reads the
-    // current dist[u] first and only then issues a non-returning atomicMin,
-    // so a warp's edge chunks need no round trip through the atomic unit.
-    int cur = 0, it = 0;
+    // phase 1 (A7).  Block b owns the vertices b, b + B, b + 2B, ... (B =
+    // blocks), so that vertices with neighbouring ids -- often neighbours in
+    // the graph, hence on the frontier together -- land in different blocks.
+    // Per round of up to 1024 owned vertices: each thread checks one vertex
+    // (on the frontier when its distance is below last[v]); the block lists
+    // the frontier vertices with their out-degrees, scans the degrees, and
+    // then relaxes the listed out-edges edge-parallel (thread q takes edge q
+    // of the concatenated lists, found by binary search), with
+    // non-returning atomicMin.
     volatile unsigned long long* vdist = P.dist;
+    int it = 0;
     for (;;) {
-        bool my_change = false;
-        for (long long v = gwarp; v < N; v += nwarps) {
-            if (!*((volatile unsigned char*)&P.front[cur * N + v])) continue;
-            __syncwarp();
-            if (lane == 0) P.front[cur * N + v] = 0;
-            const double dv = __longlong_as_double((long long)vdist[v]);
-            const long long e0 = P.row_off[v], e1 = P.row_off[v + 1];
-            for (long long eb = e0; eb < e1; eb += 128) {
-                int uu[4];
-                double ww[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const long long e = eb + c * 32 + lane;
-                    uu[c] = -1;
-                    if (e < e1) {
-                        uu[c] = P.col[e];
-                        ww[c] = P.w_f64 ? ((const double*)P.w)[e] : (double)((const float*)P.w)[e];
-                    }
-                }
-                unsigned long long cu[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) cu[c] = (uu[c] >= 0 && uu[c] < N) ? vdist[uu[c]] : 0ull;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if (uu[c] < 0 || uu[c] >= N) continue;
-                    const unsigned long long nd = (unsigned long long)__double_as_longlong(__dadd_rn(dv, ww[c]));
-                    if (nd < cu[c]) {
-                        atomicMin(&P.dist[uu[c]], nd);
-                        P.front[(cur ^ 1) * N + uu[c]] = 1;
-                        my_change = true;
+        bool relaxed = false;  // block-uniform
+        for (long long k0 = 0; k0 < nown; k0 += nt) {
+            if (tid == 0) s_nf = 0;
+            __syncthreads();
+            const long long k = k0 + tid;
+            if (k < nown) {
+                const long long v = blockIdx.x + k * nb;
+                const bool cached = k < SEARCH_OWN_CAP;
+                const unsigned long long dvb = v == s ? 0ull : vdist[v];
+                if (dvb < (cached ? s_last[k] : P.last[v])) {
+                    if (cached) s_last[k] = dvb;
+                    else P.last[v] = dvb;
+                    if (v == s) vdist[v] = 0ull;
+                    const int e0 = cached ? s_ro[2 * k] : __ldg(&P.row_off[v]);
+                    const int e1 = cached ? s_ro[2 * k + 1] : __ldg(&P.row_off[v + 1]);
+                    if (e1 > e0) {
+                        const int i = atomicAdd(&s_nf, 1);
+                        s_v[i] = (int)v;
+                        s_e0[i] = e0;
+                        s_pre[i] = e1 - e0;
+                        s_dv[i] = dvb;
                     }
                 }
             }
+            __syncthreads();
+            const int nf = s_nf;
+            if (nf == 0) continue;
+            relaxed = true;
+            const int tot = block_scan_degrees(s_pre, nf, s_wsum);
+            // four edges per thread per pass: their loads are issued together
+            for (int q0 = tid; q0 < tot; q0 += 4 * nt) {
+                int uu[4], ei[4];
+                double ww[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int q = q0 + c * nt;
+                    uu[c] = -1;
+                    ei[c] = 0;
+                    ww[c] = 0.0;
+                    if (q < tot) {
+                        const int i = find_entry(s_pre, nf, q);
+                        const int e = s_e0[i] + (q - s_pre[i]);
+                        ei[c] = i;
+                        uu[c] = __ldg(&P.col[e]);
+                        ww[c] = P.w_f64 ? __ldg(&((const double*)P.w)[e]) : (double)__ldg(&((const float*)P.w)[e]);
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (uu[c] < 0 || uu[c] >= N) continue;
+                    const double dv = __longlong_as_double((long long)s_dv[ei[c]]);
+                    atomicMin(&P.dist[uu[c]], (unsigned long long)__double_as_longlong(__dadd_rn(dv, ww[c])));
+                }
+            }
+            __syncthreads();  // the lists are rebuilt by the next round
         }
-        // flag of sweep j is changed[j % 3]: written during sweep j, read after
-        // its barrier, cleared during sweep j+2 (after every block has read it)
-        if (__any_sync(0xffffffffu, my_change) && lane == 0) atomicExch(&info->changed[it % 3], 1);
-        if (gtid == 0) info->changed[(it + 1) % 3] = 0;
-        if (!grid_sync(info, nb, P.spin_limit)) return;
-        const int ch = *((volatile int*)&info->changed[it % 3]);
+        // the barrier counts the blocks that relaxed: none means a fixed point
+        unsigned nrelaxed = 0;
+        if (!grid_sync(info, nb, P.spin_limit, bar_round, relaxed, &nrelaxed)) return;
         ++it;
-        if (!ch) break;
+        if (nrelaxed == 0) break;
         if (it > P.max_sweeps) {
             if (gtid == 0) set_status_s(info, PLAN_ERR_TIMEOUT, DET_SWEEPS);
             return;
         }
-        cur ^= 1;
     }
 
-    // predecessor: minimum (dist[u], u) over in-neighbours attaining dist[v]
+    // phase 2: predecessor = minimum (dist[u], u) over in-neighbours attaining
+    // dist[v], in two passes over the out-edges of every reached vertex (same
+    // ownership and edge-parallel layout as the sweeps)
     for (int pass = 0; pass < 2; ++pass) {
-        for (long long v = gwarp; v < N; v += nwarps) {
-            const unsigned long long dvb = vdist[v];
-            if (dvb >= DINF) continue;
-            const double dv = __longlong_as_double((long long)dvb);
-            const long long e0 = P.row_off[v], e1 = P.row_off[v + 1];
-            for (long long e = e0 + lane; e < e1; e += 32) {
-                const int u = P.col[e];
+        for (long long k0 = 0; k0 < nown; k0 += nt) {
+            if (tid == 0) s_nf = 0;
+            __syncthreads();
+            const long long k = k0 + tid;
+            if (k < nown) {
+                const long long v = blockIdx.x + k * nb;
+                const bool cached = k < SEARCH_OWN_CAP;
+                const unsigned long long dvb = vdist[v];
+                const int e0 = cached ? s_ro[2 * k] : __ldg(&P.row_off[v]);
+                const int e1 = cached ? s_ro[2 * k + 1] : __ldg(&P.row_off[v + 1]);
+                if (dvb < DINF && e1 > e0) {
+                    const int i = atomicAdd(&s_nf, 1);
+                    s_v[i] = (int)v;
+                    s_e0[i] = e0;
+                    s_pre[i] = e1 - e0;
+                    s_dv[i] = dvb;
+                }
+            }
+            __syncthreads();
+            const int nf = s_nf;
+            if (nf == 0) continue;
+            const int tot = block_scan_degrees(s_pre, nf, s_wsum);
+            for (int q = tid; q < tot; q += nt) {
+                const int i = find_entry(s_pre, nf, q);
+                const int e = s_e0[i] + (q - s_pre[i]);
+                const int u = __ldg(&P.col[e]);
                 if (u < 0 || u >= N || u == s) continue;
-                const double w = P.w_f64 ? ((const double*)P.w)[e] : (double)((const float*)P.w)[e];
-                const unsigned long long nd = (unsigned long long)__double_as_longlong(__dadd_rn(dv, w));
+                const double w = P.w_f64 ? __ldg(&((const double*)P.w)[e]) : (double)__ldg(&((const float*)P.w)[e]);
+                const unsigned long long dvb = s_dv[i];
+                const unsigned long long nd =
+                    (unsigned long long)__double_as_longlong(__dadd_rn(__longlong_as_double((long long)dvb), w));
                 if (nd != vdist[u]) continue;
                 if (pass == 0) atomicMin(&P.bestU[u], dvb);
-                else if (P.bestU[u] == dvb) atomicMin(&P.pred[u], (int)v);
+                else if (((volatile unsigned long long*)P.bestU)[u] == dvb) atomicMin(&P.pred[u], s_v[i]);
             }
+            __syncthreads();
         }
-        if (!grid_sync(info, nb, P.spin_limit)) return;
+        if (!grid_sync(info, nb, P.spin_limit, bar_round)) return;
     }
 
-    // walk goal -> start
-    if (gtid == 0) {
+    // phase 3: walk goal -> start (block 0; pred[] staged in shared memory when it fits)
+    if (blockIdx.x != 0) return;
+    const bool staged = N <= P.walk_smem;
+    if (staged) {
+        for (int v = threadIdx.x; v < N; v += blockDim.x) s_pred[v] = ((volatile int*)P.pred)[v];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int* pr = staged ? s_pred : P.pred;
         info->search_iters = (unsigned long long)it;
         const unsigned long long dg = vdist[g];
         if (dg >= DINF) {
@@ -231,7 +386,7 @@ __global__ void __launch_bounds__(1024) k_search(SearchParams P) {
             int len = 1, v = g;
             bool okw = true;
             while (v != s) {
-                v = P.pred[v];
+                v = pr[v];
                 if (v < 0 || v >= N || len > N) {
                     okw = false;
                     break;
@@ -248,7 +403,7 @@ __global__ void __launch_bounds__(1024) k_search(SearchParams P) {
                 v = g;
                 for (int q = len - 1; q >= 0; --q) {
                     P.path[q] = v;
-                    if (q) v = P.pred[v];
+                    if (q) v = pr[v];
                 }
                 *P.path_len = len;
             }
@@ -430,14 +585,17 @@ int launch_search_batched(const BatchSearchParams& P, void* stream, int* launche
 
 int launch_search(const SearchParams& P, void* stream, int num_sms, int* launches) {
     cudaStream_t st = (cudaStream_t)stream;
+    // one block per SM: fewer arrivals per grid barrier; the walk's staging
+    // buffer (block 0) holds pred[] for up to SEARCH_WALK_SMEM vertices
+    const size_t smem = (size_t)SEARCH_WALK_SMEM * sizeof(int);
+    cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_search, 1024, 0);
-    if (occ < 1) occ = 1;
-    if (occ > 2) occ = 2;
-    const int nb = num_sms * occ;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_search, 1024, smem);
+    if (occ < 1) return (int)cudaErrorCooperativeLaunchTooLarge;
     SearchParams Q = P;
+    Q.walk_smem = SEARCH_WALK_SMEM;
     void* args[] = {&Q};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_search, dim3(nb), dim3(1024), args, 0, st);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_search, dim3(num_sms), dim3(1024), args, smem, st);
     ++*launches;
     return (int)e;
 }
@@ -451,8 +609,8 @@ int launch_search(const SearchParams& P, void* stream, int num_sms, int* launche
 // stream is being captured into a CUDA graph, or a process whose device
 // memory is owned entirely by a pool allocator.  This variant of the search
 // keeps all of its scratch -- the status word and grid-barrier counters, the
-// distance, predecessor and frontier arrays -- in one file-scope __device__
-// array sized for NOALLOC_MAX_N vertices (about 1.4 MB), which every GPU that
+// distance, predecessor and last-relaxed arrays -- in one file-scope __device__
+// array sized for NOALLOC_MAX_N vertices (about 1.8 MB), which every GPU that
 // loads the library holds until the process exits.  The caller passes only
 // inputs and outputs.
 // ---------------------------------------------------------------------------
@@ -464,7 +622,8 @@ struct NoAllocScratch {
     unsigned long long dist[NOALLOC_MAX_N];
     unsigned long long best[NOALLOC_MAX_N];
     int pred[NOALLOC_MAX_N];
-    unsigned char front[2 * NOALLOC_MAX_N];
+    unsigned long long last[NOALLOC_MAX_N];
+    unsigned long long near_blk[4 * SEARCH_MAX_BLOCKS];
 };
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
@@ -513,6 +672,7 @@ extern "C" int plan_search_noalloc(int m, int gamma, int input, int w_f64, int N
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PLAN_ERR_CUDA;
+    if (sms > SEARCH_MAX_BLOCKS) return PLAN_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     // the status word and the grid-barrier counters must start at zero; the
     // kernel initialises the per-vertex arrays itself
@@ -537,7 +697,8 @@ extern "C" int plan_search_noalloc(int m, int gamma, int input, int w_f64, int N
     S.dist = scr->dist;
     S.bestU = scr->best;
     S.pred = scr->pred;
-    S.front = scr->front;
+    S.last = scr->last;
+    S.near_blk = scr->near_blk;
     S.path = path;
     S.path_cap = path_cap;
     S.path_len = path_len;
