@@ -73,6 +73,7 @@ struct plan_ctx {
     int* counts = nullptr;
     int* members = nullptr;
     int* localIdx = nullptr;
+    int* segKL = nullptr;
     float* centers = nullptr;
     double* blim64 = nullptr;
     float* A32 = nullptr;
@@ -238,7 +239,8 @@ int ensure_host_sized(plan_ctx* c, long long mask, long long list, long long k1,
         c->capW = mask;
     }
     if (list > c->capL) {
-        if (!dalloc(c, &c->members, list) || !dalloc(c, &c->localIdx, list)) return PLAN_ERR_NO_MEMORY;
+        if (!dalloc(c, &c->members, list) || !dalloc(c, &c->localIdx, list) || !dalloc(c, &c->segKL, list))
+            return PLAN_ERR_NO_MEMORY;
         c->capL = list;
     }
     if (k1 > c->capK) {
@@ -357,7 +359,7 @@ int plan_create(plan_ctx** out, const plan_model* model, void* cuda_stream) {
 void plan_destroy(plan_ctx* c) {
     if (!c) return;
     if (c->stream || c->d_info) cudaStreamSynchronize(c->stream);
-    void* dev[] = {c->d_tab64, c->d_tab32, c->d_info, c->memMask, c->counts, c->members, c->localIdx, c->centers,
+    void* dev[] = {c->d_tab64, c->d_tab32, c->d_info, c->memMask, c->counts, c->members, c->localIdx, c->segKL, c->centers,
                    c->blim64, c->A32, c->blim32, c->bc32, c->resOff, c->itemOff, c->ntile, c->tsize, c->rowCount,
                    c->resBits, c->resKey, c->emitPre, c->recheck, c->sdist, c->sbest, c->spred, c->sfront, c->slast, c->snear,
                    c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem, c->d_qMem, c->d_sqd, c->memOff};
@@ -569,6 +571,7 @@ int issue(plan_ctx* c) {
     P.counts = c->counts;
     P.members = c->members;
     P.localIdx = c->localIdx;
+    P.segKL = c->segKL;
     P.centers = c->centers;
     P.blim64 = c->blim64;
     P.A32 = c->A32;

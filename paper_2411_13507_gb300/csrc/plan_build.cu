@@ -50,6 +50,37 @@ DEVI void set_status(DevInfo* info, int code, int detail) {
 }
 DEVI bool has_failed(const DevInfo* info) { return *((volatile const int*)&info->status) != 0; }
 
+// The call's status and one of its counters, read by one thread per block and
+// shared: thousands of warps reading the same word would all queue at one L2
+// slice.  Every thread of the block must call it (it holds a barrier).
+DEVI bool block_failed(const DevInfo* info, const unsigned long long* counter, long long* n) {
+    __shared__ int s_fail;
+    __shared__ long long s_n;
+    if (threadIdx.x == 0) {
+        s_fail = has_failed(info);
+        s_n = counter ? (long long)*(volatile const unsigned long long*)counter : 0;
+    }
+    __syncthreads();
+    if (n) *n = s_n;
+    return s_fail != 0;
+}
+
+// Adds every thread's v to *dst with one global atomic per block (shared
+// atomics first).  Every thread of the block must call it.
+DEVI void block_add(unsigned long long* dst, unsigned long long v) {
+    __shared__ unsigned long long s_acc;
+    if (threadIdx.x == 0) s_acc = 0;
+    __syncthreads();
+    if ((blockDim.x & 31) == 0) {  // whole warps: reduce in registers first
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_acc, v);
+    } else if (v) {
+        atomicAdd(&s_acc, v);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_acc) atomicAdd(dst, s_acc);
+}
+
 DEVI double ldv(const void* p, long long i, int f32) {
     return f32 ? (double)((const float*)p)[i] : ((const double*)p)[i];
 }
@@ -121,7 +152,7 @@ __global__ void k_prep(BuildParams P) {
 __global__ void k_member(BuildParams P) {
     const long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;  // one warp per (state, word)
     const int lane = threadIdx.x & 31;
-    if (t >= P.totMask || has_failed(P.info)) return;
+    if (block_failed(P.info, nullptr, nullptr) || t >= P.totMask) return;
     const int q = find_q(P.pfxMask, P.Q, t);
     const QueryDesc& Q = P.qd[q];
     const long long loc = t - P.pfxMask[q];
@@ -395,12 +426,25 @@ DEVI ItemT item_decode_chunk(const BuildParams& P, long long item) {
 
 // Slots start empty (no feasible duration, no key); the pair kernels merge
 // into them with atomics.
+// Clears the pair slots and writes the row-segment table (segment g -> its
+// polytope and local index), one warp per polytope.
 __global__ void k_zero_slots(BuildParams P) {
-    if (has_failed(P.info)) return;
-    const long long n = (long long)P.info->slots;
+    long long n = 0;
+    if (block_failed(P.info, &P.info->slots, &n)) return;
+    if (P.arith == PLAN_F64) n = 0;  // the FP64 kernel writes every result slot itself
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
         P.resBits[s] = 0u;
         P.resKey[s] = KEY_NONE;
+    }
+    const int lane = threadIdx.x & 31;
+    for (long long gp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; gp < P.totPoly;
+         gp += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const int q = find_q(P.pfxPoly, P.Q, gp);
+        const QueryDesc& Q = P.qd[q];
+        const int k = (int)(gp - P.pfxPoly[q]);
+        const long long start = P.qMem[q] + P.memOff[Q.kOff + k];
+        const int nk = P.counts[Q.kOff + k];
+        for (int li = lane; li < nk; li += 32) P.segKL[start + li] = (k << 16) | li;
     }
 }
 
@@ -859,7 +903,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
             __syncthreads();
         }
     }
-    if (rp_cnt) atomicAdd(&P.info->reach_pass, rp_cnt);
+    block_add(&P.info->reach_pass, rp_cnt);
 }
 
 // ---------------------------------------------------------------------------
@@ -1263,7 +1307,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
             __syncthreads();
         }
     }
-    if (rp_cnt) atomicAdd(&P.info->reach_pass, rp_cnt);
+    block_add(&P.info->reach_pass, rp_cnt);
 }
 
 // ---------------------------------------------------------------------------
@@ -1589,7 +1633,8 @@ __global__ void __launch_bounds__(512, 1) k_pairs_ws(BuildParams P) {
             ++uses[stage];
             stage ^= 1;
         }
-        if (rp_cnt) atomicAdd(&P.info->reach_pass, rp_cnt);
+        for (int o = 16; o > 0; o >>= 1) rp_cnt += __shfl_down_sync(0xffffffffu, rp_cnt, o);
+        if (lane == 0 && rp_cnt) atomicAdd(&P.info->reach_pass, rp_cnt);
     }
 }
 
@@ -1975,7 +2020,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_tc(BuildParams P) {
             __syncthreads();
         }
     }
-    if (rp_cnt) atomicAdd(&P.info->reach_pass, rp_cnt);
+    block_add(&P.info->reach_pass, rp_cnt);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
@@ -2140,7 +2185,7 @@ __global__ void __launch_bounds__(256) k_pairs_f64(BuildParams P) {
         }
         __syncthreads();
     }
-    if (rp_cnt) atomicAdd(&P.info->reach_pass, rp_cnt);
+    block_add(&P.info->reach_pass, rp_cnt);
 }
 
 // ---------------------------------------------------------------------------
@@ -2154,8 +2199,9 @@ __global__ void k_recheck(BuildParams P) {
     // canonical order
     using S = Shape<G, PD>;
     constexpr int N_ = M * G, RAX = S::RAX, NI = S::NI, TG = S::TG;
-    if (has_failed(P.info)) return;
-    const long long n = min((long long)P.info->rechecks, P.recheckCap);
+    long long n = 0;
+    if (block_failed(P.info, &P.info->rechecks, &n)) return;
+    n = min(n, P.recheckCap);
     const int DR = P.cost_mode == 1 ? 1 : G;
     const TabLayout L = P.L;
     const int lane = threadIdx.x & 31;
@@ -2276,95 +2322,90 @@ DEVI void combine(const BuildParams& P, const QView& V, int i, int j, int k, uin
     }
 }
 
-// Pass 1, one thread per slot (balanced): is this slot the pair's owner, and
-// is the pair feasible for some duration?  The owner slot receives the pair's
-// result combined over all shared polytopes; emitPre[slot] gets the flag.
-__global__ void k_emit(BuildParams P) {
-    if (has_failed(P.info)) return;
-    const long long total = (long long)P.info->slots;
-    unsigned long long cand = 0, chk = 0, feas = 0;
-    for (long long sidx = blockIdx.x * (long long)blockDim.x + threadIdx.x; sidx < total;
-         sidx += (long long)gridDim.x * blockDim.x) {
-        const int q = find_q(P.qSlot, P.Q, sidx);
-        const QView V(P, q);
-        const QueryDesc& Q = *V.Q;
-        const long long ls = sidx - V.slot0;
-        int lo = 0, hi = Q.K;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (V.resOff[mid] <= ls) lo = mid;
-            else hi = mid;
-        }
-        const int k = lo, nk = V.counts[k];
-        int flag = 0;
-        if (nk > 0) {
-            const long long loc = ls - V.resOff[k];
-            const int li = (int)(loc / nk), lj = (int)(loc % nk);
-            const int im = V.members[(long long)k * Q.N + li], jm = V.members[(long long)k * Q.N + lj];
-            const int i = mem_id(im), j = mem_id(jm);
-            if (i != j) {
-                int ns = 1;
-                if (!(mem_multi(im) && mem_multi(jm)) || owner_of(V, i, j, ns) == k) {
-                    ++cand;
-                    chk += Q.nT;
-                    uint32_t bits = P.resBits[sidx];
-                    unsigned long long key = P.resKey[sidx];
-                    if (ns > 1) {
-                        combine(P, V, i, j, k, bits, key);
-                        P.resBits[sidx] = bits;
-                        P.resKey[sidx] = key;
-                    }
-                    flag = bits != 0;
-                    feas += __popc(bits);
-                }
-            }
-        }
-        P.emitPre[sidx] = flag;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        cand += __shfl_down_sync(0xffffffffu, cand, o);
-        chk += __shfl_down_sync(0xffffffffu, chk, o);
-        feas += __shfl_down_sync(0xffffffffu, feas, o);
-    }
-    if ((threadIdx.x & 31) == 0 && cand) {
-        atomicAdd(&P.info->candidates, cand);
-        atomicAdd(&P.info->checks, chk);
-        atomicAdd(&P.info->feasible, feas);
-    }
+// Segment of the flat membership index g: query, polytope k and the state's
+// local index li in it.
+struct SegRef {
+    int q, k, li;
+};
+DEVI SegRef seg_of(const BuildParams& P, long long g) {
+    SegRef r;
+    r.q = P.Q == 1 ? 0 : find_q(P.qMem, P.Q, g);
+    const int v = P.segKL[g];
+    r.k = v >> 16;
+    r.li = v & 0xffff;
+    return r;
 }
 
-// Pass 2, one warp per row segment (state i in polytope k): inclusive prefix
-// of the emitted flags within the segment; the segment total adds to row i.
-__global__ void k_segscan(BuildParams P) {
-    if (has_failed(P.info)) return;
-    const long long nseg = (long long)P.info->memberships;
+// Pass 1, one warp per row segment (state i in polytope k, its slots (i, j)
+// for the polytope's members j): is each slot the pair's owner (the lowest
+// polytope both states contain -- only pairs of states that both lie in
+// several polytopes can be shared), and is the pair feasible for some
+// duration?  The owner slot receives the pair's result combined over all
+// shared polytopes; emitPre gets the inclusive prefix of the emitted flags
+// within the segment, and the segment total adds to row i's count.
+__global__ void k_emit(BuildParams P) {
+    long long nseg = 0;
+    if (block_failed(P.info, &P.info->memberships, &nseg)) return;
     const int lane = threadIdx.x & 31;
+    unsigned long long cand = 0, chk = 0, feas = 0;
     for (long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; g < nseg;
          g += ((long long)gridDim.x * blockDim.x) >> 5) {
-        const int q = find_q(P.qMem, P.Q, g);
-        const QView V(P, q);
+        const SegRef sr = seg_of(P, g);
+        const QView V(P, sr.q);
         const QueryDesc& Q = *V.Q;
-        const int loc = (int)(g - P.qMem[q]);
-        const int* mo = P.memOff + Q.kOff;
-        int lo = 0, hi = Q.K;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (mo[mid] <= loc) lo = mid;
-            else hi = mid;
-        }
-        const int k = lo, li = loc - mo[k], nk = V.counts[k];
-        const int i = mem_id(V.members[(long long)k * Q.N + li]);
-        const long long base = V.slot0 + V.resOff[k] + (long long)li * nk;
+        const int k = sr.k, nk = V.counts[k];
+        const int* mem = V.members + (long long)k * Q.N;
+        const int im = mem[sr.li];
+        const int i = mem_id(im);
+        const long long base = V.slot0 + V.resOff[k] + (long long)sr.li * nk;
         int running = 0;
-        for (int lj0 = 0; lj0 < nk; lj0 += 32) {
-            const int lj = lj0 + lane;
-            const int f = lj < nk ? P.emitPre[base + lj] : 0;
-            const unsigned bal = __ballot_sync(0xffffffffu, f != 0);
-            if (lj < nk) P.emitPre[base + lj] = running + __popc(bal & ((2u << lane) - 1u));
-            running += __popc(bal);
+        for (int lg = 0; lg < nk; lg += 128) {
+            // four chunks of 32 slots: every load of the group is issued first
+            int jv[4];
+            uint32_t bv[4];
+            unsigned long long kv[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int lj = lg + 32 * c + lane;
+                const bool in = lj < nk;
+                jv[c] = in ? mem[lj] : 0;
+                bv[c] = in ? P.resBits[base + lj] : 0u;
+                kv[c] = in ? P.resKey[base + lj] : 0ull;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int lj = lg + 32 * c + lane;
+                if (lg + 32 * c >= nk) break;  // warp-uniform
+                int flag = 0;
+                if (lj < nk) {
+                    const int jm = jv[c], j = mem_id(jm);
+                    if (i != j) {
+                        int ns = 1;
+                        if (!(mem_multi(im) && mem_multi(jm)) || owner_of(V, i, j, ns) == k) {
+                            ++cand;
+                            chk += Q.nT;
+                            uint32_t bits = bv[c];
+                            if (ns > 1) {
+                                unsigned long long key = kv[c];
+                                combine(P, V, i, j, k, bits, key);
+                                P.resBits[base + lj] = bits;
+                                P.resKey[base + lj] = key;
+                            }
+                            flag = bits != 0;
+                            feas += __popc(bits);
+                        }
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, flag != 0);
+                if (lj < nk) P.emitPre[base + lj] = running + __popc(bal & ((2u << lane) - 1u));
+                running += __popc(bal);
+            }
         }
         if (lane == 0 && running) atomicAdd(&P.rowCount[Q.rowOff + i], running);
     }
+    block_add(&P.info->candidates, cand);
+    block_add(&P.info->checks, chk);
+    block_add(&P.info->feasible, feas);
 }
 
 // One CTA per query: exclusive scan of the row counts into row_off, E, capacity.
@@ -2403,31 +2444,113 @@ DEVI int lower_bound_members(const int* mem, int n, int j) {
     return lo;
 }
 
-// Rank of an emitted entry among its row's emitted ids: for a row in one
-// polytope the segment prefix; for a row in several polytopes a per-warp
-// shared-memory bitmap of the row's emitted ids (rank = prefix popcount), or,
-// for very large N, binary searches in the other segments.
-__global__ void __launch_bounds__(256) k_compact_fill(BuildParams P, int bm_words) {
+DEVI void write_edge(const BuildParams& P, const QueryDesc& Q, long long o, int j, uint32_t bits,
+                      unsigned long long key) {
+    Q.col[o] = j;
+    Q.mask[o] = bits;
+    Q.tidx[o] = (uint8_t)(key & 31ull);
+    if (P.arith == PLAN_F64) ((double*)Q.w)[o] = __longlong_as_double((long long)(key & ~31ull));
+    else ((float*)Q.w)[o] = __uint_as_float((unsigned)(key >> 32));
+}
+
+// Output pass.  Work items [0, memberships) are row segments: a state that
+// lies in one polytope only has its whole row there, so an emitted entry's
+// rank in the row is the segment prefix -- one warp per segment.  Items
+// [memberships, memberships + rows) are rows of states in several polytopes:
+// one warp per row merges its segments by rank in a per-warp shared-memory
+// bitmap of the row's emitted ids (rank = prefix popcount), or, for very
+// large N, by binary searches in the other segments.
+__global__ void __launch_bounds__(256, 4) k_compact_fill(BuildParams P, int bm_words) {
     extern __shared__ uint32_t bmem[];
-    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    if (warp >= P.totN || has_failed(P.info)) return;
-    const int q = find_q(P.pfxN, P.Q, warp);
-    const QView V(P, q);
-    const QueryDesc& Q = *V.Q;
-    const int i = (int)(warp - P.pfxN[q]);
-    const int W = Q.W;
-    int npoly = 0;
-    for (int w = 0; w < W; ++w) npoly += __popc(V.mask[(long long)i * W + w]);
-    const long long rbase = Q.row_off[i];
-    const bool f64 = P.arith == PLAN_F64;
-    const int nwords = (Q.N + 31) >> 5;
-    const bool use_bm = npoly > 1 && nwords <= bm_words;
+    long long nseg = 0;
+    if (block_failed(P.info, &P.info->memberships, &nseg)) return;
+    const long long nitem = nseg + P.totN;
     uint32_t* bits_m = bmem + (size_t)wib * 2 * bm_words;
     uint32_t* pre_m = bits_m + bm_words;
-    if (use_bm) {
-        for (int w = lane; w < nwords; w += 32) bits_m[w] = 0u;
-        __syncwarp();
+    for (long long it = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; it < nitem;
+         it += ((long long)gridDim.x * blockDim.x) >> 5) {
+        if (it < nseg) {
+            const SegRef sr = seg_of(P, it);
+            const QView V(P, sr.q);
+            const QueryDesc& Q = *V.Q;
+            const int* mem = V.members + (long long)sr.k * Q.N;
+            const int im = mem[sr.li];
+            if (mem_multi(im)) continue;  // the row item handles it
+            const int nk = V.counts[sr.k];
+            const long long base = V.slot0 + V.resOff[sr.k] + (long long)sr.li * nk;
+            const long long rbase = Q.row_off[mem_id(im)];
+            for (int lg = 0; lg < nk; lg += 128) {
+                int pv[4], pp[4], jv[4];
+                uint32_t bv[4];
+                unsigned long long kv[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {  // every load of the group first
+                    const int lj = lg + 32 * c + lane;
+                    const bool in = lj < nk;
+                    pv[c] = in ? P.emitPre[base + lj] : 0;
+                    pp[c] = in && lj > 0 ? P.emitPre[base + lj - 1] : 0;
+                    jv[c] = in ? mem[lj] : 0;
+                    bv[c] = in ? P.resBits[base + lj] : 0u;
+                    kv[c] = in ? P.resKey[base + lj] : 0ull;
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (pv[c] != pp[c]) write_edge(P, Q, rbase + pp[c], mem_id(jv[c]), bv[c], kv[c]);
+            }
+            continue;
+        }
+        const long long row = it - nseg;
+        const int q = find_q(P.pfxN, P.Q, row);
+        const QView V(P, q);
+        const QueryDesc& Q = *V.Q;
+        const int i = (int)(row - P.pfxN[q]);
+        const int W = Q.W;
+        int npoly = 0;
+        for (int w = 0; w < W; ++w) npoly += __popc(V.mask[(long long)i * W + w]);
+        if (npoly < 2) continue;  // a segment item handled it
+        const long long rbase = Q.row_off[i];
+        const int nwords = (Q.N + 31) >> 5;
+        const bool use_bm = nwords <= bm_words;
+        if (use_bm) {
+            for (int w = lane; w < nwords; w += 32) bits_m[w] = 0u;
+            __syncwarp();
+            for (int w = 0; w < W; ++w) {
+                uint32_t mw = V.mask[(long long)i * W + w];
+                while (mw) {
+                    const int k = w * 32 + __ffs(mw) - 1;
+                    mw &= mw - 1u;
+                    const int nk = V.counts[k];
+                    const long long base = V.seg(k, i);
+                    const int* mem = V.members + (long long)k * Q.N;
+                    for (int lj = lane; lj < nk; lj += 32) {
+                        const int pre = P.emitPre[base + lj];
+                        const int prev = lj > 0 ? P.emitPre[base + lj - 1] : 0;
+                        if (pre != prev) {
+                            const int j = mem_id(mem[lj]);
+                            atomicOr(&bits_m[j >> 5], 1u << (j & 31));
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            // exclusive prefix popcount over the words
+            const int per = (nwords + 31) >> 5;
+            const int w0 = lane * per, w1 = min(nwords, w0 + per);
+            int local = 0;
+            for (int w = w0; w < w1; ++w) local += __popc(bits_m[w]);
+            int inc = local;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            int run = inc - local;
+            for (int w = w0; w < w1; ++w) {
+                pre_m[w] = (uint32_t)run;
+                run += __popc(bits_m[w]);
+            }
+            __syncwarp();
+        }
         for (int w = 0; w < W; ++w) {
             uint32_t mw = V.mask[(long long)i * W + w];
             while (mw) {
@@ -2437,74 +2560,32 @@ __global__ void __launch_bounds__(256) k_compact_fill(BuildParams P, int bm_word
                 const long long base = V.seg(k, i);
                 const int* mem = V.members + (long long)k * Q.N;
                 for (int lj = lane; lj < nk; lj += 32) {
+                    const int j = mem_id(mem[lj]);
+                    if (j == i) continue;
                     const int pre = P.emitPre[base + lj];
                     const int prev = lj > 0 ? P.emitPre[base + lj - 1] : 0;
-                    if (pre != prev) {
-                        const int j = mem_id(mem[lj]);
-                        atomicOr(&bits_m[j >> 5], 1u << (j & 31));
-                    }
-                }
-            }
-        }
-        __syncwarp();
-        // exclusive prefix popcount over the words
-        const int per = (nwords + 31) >> 5;
-        const int w0 = lane * per, w1 = min(nwords, w0 + per);
-        int local = 0;
-        for (int w = w0; w < w1; ++w) local += __popc(bits_m[w]);
-        int inc = local;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        int run = inc - local;
-        for (int w = w0; w < w1; ++w) {
-            pre_m[w] = (uint32_t)run;
-            run += __popc(bits_m[w]);
-        }
-        __syncwarp();
-    }
-    for (int w = 0; w < W; ++w) {
-        uint32_t mw = V.mask[(long long)i * W + w];
-        while (mw) {
-            const int k = w * 32 + __ffs(mw) - 1;
-            mw &= mw - 1u;
-            const int nk = V.counts[k];
-            const long long base = V.seg(k, i);
-            const int* mem = V.members + (long long)k * Q.N;
-            for (int lj = lane; lj < nk; lj += 32) {
-                const int jm = mem[lj], j = mem_id(jm);
-                if (j == i) continue;
-                const int pre = P.emitPre[base + lj];
-                const int prev = lj > 0 ? P.emitPre[base + lj - 1] : 0;
-                if (pre == prev) continue;  // not emitted here
-                (void)jm;
-                const uint32_t bits = P.resBits[base + lj];          // combined by k_emit
-                const unsigned long long key = P.resKey[base + lj];
-                long long rank = prev;
-                if (use_bm) {
-                    rank = (long long)pre_m[j >> 5] + __popc(bits_m[j >> 5] & ((1u << (j & 31)) - 1u));
-                } else if (npoly > 1) {
-                    for (int w2 = 0; w2 < W; ++w2) {
-                        uint32_t m2 = V.mask[(long long)i * W + w2];
-                        while (m2) {
-                            const int k2 = w2 * 32 + __ffs(m2) - 1;
-                            m2 &= m2 - 1u;
-                            if (k2 == k) continue;
-                            const int n2 = V.counts[k2];
-                            const int pos = lower_bound_members(V.members + (long long)k2 * Q.N, n2, j);
-                            if (pos > 0) rank += P.emitPre[V.seg(k2, i) + pos - 1];
+                    if (pre == prev) continue;  // not emitted here
+                    long long rank = prev;
+                    if (use_bm) {
+                        rank = (long long)pre_m[j >> 5] + __popc(bits_m[j >> 5] & ((1u << (j & 31)) - 1u));
+                    } else {
+                        for (int w2 = 0; w2 < W; ++w2) {
+                            uint32_t m2 = V.mask[(long long)i * W + w2];
+                            while (m2) {
+                                const int k2 = w2 * 32 + __ffs(m2) - 1;
+                                m2 &= m2 - 1u;
+                                if (k2 == k) continue;
+                                const int n2 = V.counts[k2];
+                                const int pos = lower_bound_members(V.members + (long long)k2 * Q.N, n2, j);
+                                if (pos > 0) rank += P.emitPre[V.seg(k2, i) + pos - 1];
+                            }
                         }
                     }
+                    write_edge(P, Q, rbase + rank, j, P.resBits[base + lj], P.resKey[base + lj]);
                 }
-                const long long o = rbase + rank;
-                Q.col[o] = j;
-                Q.mask[o] = bits;
-                Q.tidx[o] = (uint8_t)(key & 31ull);
-                if (f64) ((double*)Q.w)[o] = __longlong_as_double((long long)(key & ~31ull));
-                else ((float*)Q.w)[o] = __uint_as_float((unsigned)(key >> 32));
             }
         }
+        __syncwarp();  // the bitmap is rebuilt by this warp's next row
     }
 }
 
@@ -2770,10 +2851,8 @@ int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_s
     k_batch<<<1, 1024, 0, st>>>(P);
     *launches += 2;
     if (P.totN > 0 && P.totPoly > 0) {
-        if (P.arith != PLAN_F64) {
-            k_zero_slots<<<num_sms * 8, 256, 0, st>>>(P);
-            ++*launches;
-        }
+        k_zero_slots<<<num_sms * 8, 256, 0, st>>>(P);
+        ++*launches;
         int rc = 0;
         if (P.m == 2 && P.g == 2 && P.p == 3) rc = launch_pairs<2, 2, 3>(P, st, num_sms, ctas_per_sm, e0, e1, launches);
         else if (P.m == 2 && P.g == 2 && P.p == 5) rc = launch_pairs<2, 2, 5>(P, st, num_sms, ctas_per_sm, e0, e1, launches);
@@ -2784,20 +2863,18 @@ int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_s
     if (P.totN > 0) {
         cudaMemsetAsync(P.rowCount, 0, sizeof(int) * (size_t)P.totN, st);
         if (P.totPoly > 0) {
-            k_emit<<<num_sms * 8, 256, 0, st>>>(P);
-            k_segscan<<<num_sms * 8, 256, 0, st>>>(P);
-            *launches += 2;
+            k_emit<<<num_sms * 16, 256, 0, st>>>(P);
+            ++*launches;
         }
     }
     k_scan<<<P.Q, 1024, 0, st>>>(P);
     ++*launches;
     if (P.totN > 0 && P.totPoly > 0) {
-        const long long thr = P.totN * 32;
         const int words = (P.maxN + 31) / 32;
         const int bm_words = (words <= 1024) ? words : 0;  // bitmap ranks up to N = 32768
         const size_t smem = (size_t)8 * 2 * bm_words * sizeof(uint32_t);
         if (smem > 48 * 1024) cudaFuncSetAttribute(k_compact_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_compact_fill<<<(unsigned)((thr + 255) / 256), 256, smem, st>>>(P, bm_words);
+        k_compact_fill<<<num_sms * 16, 256, smem, st>>>(P, bm_words);
         ++*launches;
     }
     return (int)cudaGetLastError();

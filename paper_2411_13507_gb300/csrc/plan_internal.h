@@ -140,6 +140,7 @@ struct BuildParams {
     int* counts;
     int* members;
     int* localIdx;
+    int* segKL;                // [memberships] row segment g -> polytope k << 16 | local index li
     float* centers;            // [kOff][4]
     double* blim64;
     float* A32;                // [rows][m]

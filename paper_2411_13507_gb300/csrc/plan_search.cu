@@ -43,7 +43,8 @@ DEVI bool failed_s(const DevInfo* info) {
 // once round r completes, every block has left the poll of round r-1, so
 // block 0 clears that word, which round r+2 uses next.  All three start at
 // zero (cleared before the launch).  The spin is bounded: on expiry the block
-// records PLAN_ERR_TIMEOUT and returns false instead of waiting forever.
+// records PLAN_ERR_TIMEOUT and returns false instead of waiting forever; it
+// also returns false when a failure was recorded before the barrier.
 DEVI bool grid_sync(DevInfo* info, unsigned nblocks, long long spin_limit, int& round, bool raise = false,
                     unsigned* raised = nullptr) {
     __shared__ int s_ok;
@@ -66,6 +67,7 @@ DEVI bool grid_sync(DevInfo* info, unsigned nblocks, long long spin_limit, int& 
             }
         }
         if (ok && blockIdx.x == 0) info->bar[(round + 2) % 3] = 0ull;
+        if (ok && failed_s(info)) ok = 0;  // a failure recorded before the barrier stops every block
         s_ok = ok;
         s_raised = (unsigned)(cur >> 32);
     }
@@ -79,6 +81,8 @@ DEVI double ldd(const void* p, long long i, int f32) {
     return f32 ? (double)((const float*)p)[i] : ((const double*)p)[i];
 }
 }  // namespace
+
+constexpr int SWEEP_ROUNDS = 2;
 
 // (bits, id) pairs ordered lexicographically: the nearest vertex, ties to the lowest id
 DEVI void keep_min(unsigned long long& kb, int& ki, unsigned long long ob, int oi) {
@@ -154,7 +158,6 @@ __global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
     const unsigned nb = gridDim.x;
     int bar_round = 0;
     const long long gtid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long nthr = (long long)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     DevInfo* info = P.info;
     const int N = P.N;
@@ -178,7 +181,8 @@ __global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
     }
     unsigned long long kb[2] = {~0ull, ~0ull};
     int ki[2] = {0x7fffffff, 0x7fffffff};
-    for (long long v = gtid; v < N; v += nthr) {
+    for (long long k = tid; k < nown; k += nt) {  // owned vertices: the FP64 work spreads over every SM
+        const long long v = blockIdx.x + k * nb;
         P.dist[v] = DINF;
         P.last[v] = DINF;
         P.bestU[v] = ~0ull;
@@ -216,7 +220,6 @@ __global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
         P.near_blk[4 * blockIdx.x + 2 * h + 1] = (unsigned long long)(unsigned)i0;
     }
     if (!grid_sync(info, nb, P.spin_limit, bar_round)) return;
-    if (failed_s(info)) return;
     if (threadIdx.x < 64) {  // warp 0: start (h = 0) from lanes' blocks; warp 1: goal
         const int h = threadIdx.x >> 5;
         unsigned long long b0 = ~0ull;
@@ -257,6 +260,9 @@ __global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
     int it = 0;
     for (;;) {
         bool relaxed = false;  // block-uniform
+        // SWEEP_ROUNDS check-and-relax rounds per barrier: the later rounds
+        // pick up what other blocks relaxed meanwhile
+        for (int rep = 0; rep < SWEEP_ROUNDS; ++rep)
         for (long long k0 = 0; k0 < nown; k0 += nt) {
             if (tid == 0) s_nf = 0;
             __syncthreads();
