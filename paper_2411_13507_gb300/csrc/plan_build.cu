@@ -2457,19 +2457,24 @@ DEVI void write_edge(const BuildParams& P, const QueryDesc& Q, long long o, int 
 // lies in one polytope only has its whole row there, so an emitted entry's
 // rank in the row is the segment prefix -- one warp per segment.  Items
 // [memberships, memberships + rows) are rows of states in several polytopes:
-// one warp per row merges its segments by rank in a per-warp shared-memory
-// bitmap of the row's emitted ids (rank = prefix popcount), or, for very
-// large N, by binary searches in the other segments.
-__global__ void __launch_bounds__(256, 4) k_compact_fill(BuildParams P, int bm_words) {
+// one warp per row merges its segments' emitted ids (each segment already in
+// ascending order) by rank, with the segments' ids staged in shared memory,
+// or, when they do not fit, by binary searches in the other segments' member
+// lists.
+__global__ void __launch_bounds__(256, 4) k_compact_fill(BuildParams P, int run_cap) {
     extern __shared__ uint32_t bmem[];
+    __shared__ int s_meta[8][32 * 4 + 1];
+    __shared__ long long s_metab[8][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     long long nseg = 0;
     if (block_failed(P.info, &P.info->memberships, &nseg)) return;
     const long long nitem = nseg + P.totN;
-    uint32_t* bits_m = bmem + (size_t)wib * 2 * bm_words;
-    uint32_t* pre_m = bits_m + bm_words;
-    for (long long it = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; it < nitem;
-         it += ((long long)gridDim.x * blockDim.x) >> 5) {
+    int* runs = reinterpret_cast<int*>(bmem) + (size_t)wib * run_cap;  // this warp's staged ids
+    for (long long it0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; it0 < nitem;
+         it0 += ((long long)gridDim.x * blockDim.x) >> 5) {
+        // rows first: the long multi-polytope rows start early instead of
+        // forming the tail
+        const long long it = it0 < P.totN ? nseg + it0 : it0 - P.totN;
         if (it < nseg) {
             const SegRef sr = seg_of(P, it);
             const QView V(P, sr.q);
@@ -2510,11 +2515,120 @@ __global__ void __launch_bounds__(256, 4) k_compact_fill(BuildParams P, int bm_w
         for (int w = 0; w < W; ++w) npoly += __popc(V.mask[(long long)i * W + w]);
         if (npoly < 2) continue;  // a segment item handled it
         const long long rbase = Q.row_off[i];
-        const int nwords = (Q.N + 31) >> 5;
-        const bool use_bm = nwords <= bm_words;
-        if (use_bm) {
-            for (int w = lane; w < nwords; w += 32) bits_m[w] = 0u;
+        // Segment metadata (lane t: the row's t-th polytope): base slot, size,
+        // emitted count (the segment prefix at its last slot), run offset.
+        int* s_k = s_meta[wib];
+        int* s_nk = s_k + 32;
+        int* s_e = s_k + 64;
+        int* s_off = s_k + 96;  // 33 entries
+        long long* s_base = s_metab[wib];
+        int total = 0x7fffffff;
+        if (npoly <= 32) {
+            if (lane == 0) {
+                int t = 0;
+                for (int w = 0; w < W; ++w) {
+                    uint32_t mw = V.mask[(long long)i * W + w];
+                    while (mw) {
+                        s_k[t++] = w * 32 + __ffs(mw) - 1;
+                        mw &= mw - 1u;
+                    }
+                }
+            }
             __syncwarp();
+            if (lane < npoly) {
+                const int k = s_k[lane], nk = V.counts[k];
+                const long long base = V.seg(k, i);
+                s_nk[lane] = nk;
+                s_base[lane] = base;
+                s_e[lane] = nk > 0 ? P.emitPre[base + nk - 1] : 0;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                int run = 0;
+                for (int t = 0; t < npoly; ++t) {
+                    s_off[t] = run;
+                    run += s_e[t];
+                }
+                s_off[npoly] = run;
+            }
+            __syncwarp();
+            total = s_off[npoly];
+        }
+        if (total <= run_cap / 2) {
+            // Runs: each segment's emitted ids, in slot order (ascending ids), in
+            // shared memory; an entry's rank in the row is its segment prefix
+            // plus, for every other segment, the number of its ids below it
+            // (binary search in shared memory).
+            int* runj = runs + run_cap / 2;  // slot index (within its segment) of each staged id
+            for (int t = 0; t < npoly; ++t) {
+                const int nk = s_nk[t];
+                const long long base = s_base[t];
+                const int* mem = V.members + (long long)s_k[t] * Q.N;
+                const int off = s_off[t];
+                for (int lg = 0; lg < nk; lg += 128) {
+                    int pv[4], pp[4], jv[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {  // every load of the group first
+                        const int lj = lg + 32 * c + lane;
+                        const bool in = lj < nk;
+                        pv[c] = in ? P.emitPre[base + lj] : 0;
+                        pp[c] = in && lj > 0 ? P.emitPre[base + lj - 1] : 0;
+                        jv[c] = in ? mem[lj] : 0;
+                    }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (pv[c] != pp[c]) {
+                            runs[off + pp[c]] = mem_id(jv[c]);
+                            runj[off + pp[c]] = lg + 32 * c + lane;
+                        }
+                }
+            }
+            __syncwarp();
+            // every staged entry: rank = its segment prefix + the other
+            // segments' ids below it; then its result slot is copied out
+            for (int e0 = 0; e0 < total; e0 += 64) {
+                long long rk[2], slot[2];
+                int jj[2];
+                uint32_t bv[2];
+                unsigned long long kv[2];
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int e = e0 + 32 * c + lane;
+                    rk[c] = -1;
+                    if (e < total) {
+                        int t = 0;
+                        while (t + 1 < npoly && s_off[t + 1] <= e) ++t;
+                        const int j = runs[e];
+                        long long rank = e - s_off[t];
+                        for (int b = 0; b < npoly; ++b) {
+                            if (b == t) continue;
+                            const int* rb = runs + s_off[b];
+                            int lo = 0, hi = s_e[b];
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (rb[mid] < j) lo = mid + 1;
+                                else hi = mid;
+                            }
+                            rank += lo;
+                        }
+                        rk[c] = rank;
+                        jj[c] = j;
+                        slot[c] = s_base[t] + runj[e];
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    bv[c] = rk[c] >= 0 ? P.resBits[slot[c]] : 0u;
+                    kv[c] = rk[c] >= 0 ? P.resKey[slot[c]] : 0ull;
+                }
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+                    if (rk[c] >= 0) write_edge(P, Q, rbase + rk[c], jj[c], bv[c], kv[c]);
+            }
+        } else {
+            // too many polytopes or entries for the shared-memory runs: count
+            // the other segments' ids below j by binary search in their member
+            // lists (global memory)
             for (int w = 0; w < W; ++w) {
                 uint32_t mw = V.mask[(long long)i * W + w];
                 while (mw) {
@@ -2526,49 +2640,9 @@ __global__ void __launch_bounds__(256, 4) k_compact_fill(BuildParams P, int bm_w
                     for (int lj = lane; lj < nk; lj += 32) {
                         const int pre = P.emitPre[base + lj];
                         const int prev = lj > 0 ? P.emitPre[base + lj - 1] : 0;
-                        if (pre != prev) {
-                            const int j = mem_id(mem[lj]);
-                            atomicOr(&bits_m[j >> 5], 1u << (j & 31));
-                        }
-                    }
-                }
-            }
-            __syncwarp();
-            // exclusive prefix popcount over the words
-            const int per = (nwords + 31) >> 5;
-            const int w0 = lane * per, w1 = min(nwords, w0 + per);
-            int local = 0;
-            for (int w = w0; w < w1; ++w) local += __popc(bits_m[w]);
-            int inc = local;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += y;
-            }
-            int run = inc - local;
-            for (int w = w0; w < w1; ++w) {
-                pre_m[w] = (uint32_t)run;
-                run += __popc(bits_m[w]);
-            }
-            __syncwarp();
-        }
-        for (int w = 0; w < W; ++w) {
-            uint32_t mw = V.mask[(long long)i * W + w];
-            while (mw) {
-                const int k = w * 32 + __ffs(mw) - 1;
-                mw &= mw - 1u;
-                const int nk = V.counts[k];
-                const long long base = V.seg(k, i);
-                const int* mem = V.members + (long long)k * Q.N;
-                for (int lj = lane; lj < nk; lj += 32) {
-                    const int j = mem_id(mem[lj]);
-                    if (j == i) continue;
-                    const int pre = P.emitPre[base + lj];
-                    const int prev = lj > 0 ? P.emitPre[base + lj - 1] : 0;
-                    if (pre == prev) continue;  // not emitted here
-                    long long rank = prev;
-                    if (use_bm) {
-                        rank = (long long)pre_m[j >> 5] + __popc(bits_m[j >> 5] & ((1u << (j & 31)) - 1u));
-                    } else {
+                        if (pre == prev) continue;  // not emitted here
+                        const int j = mem_id(mem[lj]);
+                        long long rank = prev;
                         for (int w2 = 0; w2 < W; ++w2) {
                             uint32_t m2 = V.mask[(long long)i * W + w2];
                             while (m2) {
@@ -2580,12 +2654,12 @@ __global__ void __launch_bounds__(256, 4) k_compact_fill(BuildParams P, int bm_w
                                 if (pos > 0) rank += P.emitPre[V.seg(k2, i) + pos - 1];
                             }
                         }
+                        write_edge(P, Q, rbase + rank, j, P.resBits[base + lj], P.resKey[base + lj]);
                     }
-                    write_edge(P, Q, rbase + rank, j, P.resBits[base + lj], P.resKey[base + lj]);
                 }
             }
         }
-        __syncwarp();  // the bitmap is rebuilt by this warp's next row
+        __syncwarp();  // the runs are rebuilt by this warp's next row
     }
 }
 
@@ -2870,11 +2944,12 @@ int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_s
     k_scan<<<P.Q, 1024, 0, st>>>(P);
     ++*launches;
     if (P.totN > 0 && P.totPoly > 0) {
-        const int words = (P.maxN + 31) / 32;
-        const int bm_words = (words <= 1024) ? words : 0;  // bitmap ranks up to N = 32768
-        const size_t smem = (size_t)8 * 2 * bm_words * sizeof(uint32_t);
-        if (smem > 48 * 1024) cudaFuncSetAttribute(k_compact_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_compact_fill<<<num_sms * 16, 256, smem, st>>>(P, bm_words);
+        // staged ids and slot indices per warp (a row holds fewer than N entries)
+        const int run_cap = 2 * (P.maxN < 1024 ? (P.maxN > 32 ? P.maxN : 32) : 1024);
+        const size_t smem = ((size_t)8 * run_cap * sizeof(int) + 1023) & ~(size_t)1023;
+        const cudaError_t ea = cudaFuncSetAttribute(k_compact_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (ea != cudaSuccess) return (int)ea;
+        k_compact_fill<<<num_sms * 16, 256, smem, st>>>(P, run_cap);
         ++*launches;
     }
     return (int)cudaGetLastError();

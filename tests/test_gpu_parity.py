@@ -119,6 +119,30 @@ def test_fp32_pair_kernels_loose_and_tight_bounds(pipeline, tile):
             assert info["reach_pass"] > 0.9 * info["checks"]
 
 
+def test_states_in_many_polytopes():
+    """Rows of states that lie in more than 32 overlapping polytopes (the output
+    pass merges such rows through the other segments' member lists) and in a
+    handful of them (merged in shared memory)."""
+    prob = synth.double_integrator_2d(9, N=260, K=40, nT=4)
+    rng = np.random.default_rng(9)
+    K = 40
+    A = np.zeros((4 * K, 2))
+    b = np.zeros(4 * K)
+    for k in range(K):
+        lo = rng.uniform(1.0, 4.0, 2)
+        hi = rng.uniform(6.0, 9.0, 2)
+        A[4 * k:4 * k + 4] = [[1, 0], [-1, 0], [0, 1], [0, -1]]
+        b[4 * k:4 * k + 4] = [hi[0], -lo[0], hi[1], -lo[1]]
+    prob.A, prob.b = A, b
+    prob.poly_off = np.arange(0, 4 * K + 1, 4, dtype=np.int32)
+    for i in range(prob.N):  # most states in the common core [4, 6]^2, some outside it
+        prob.states[i, :2] = rng.uniform(4.0, 6.0, 2) if i % 3 else rng.uniform(1.5, 8.5, 2)
+    prob.start_pos = np.array([4.5, 4.5])
+    prob.goal_pos = np.array([5.5, 5.5])
+    check_full(prob, "f64")
+    check_full(prob, "f32", input="f64")
+
+
 def test_nT_extremes():
     p1 = synth.double_integrator_2d(4, N=200, K=4, nT=1)
     check_full(p1, "f64")
