@@ -986,6 +986,84 @@ DEVI void load_state(float (&x)[M * G], const float* xr) {
     for (int e = 0; e < M * G; ++e) x[e] = v[e];
 }
 
+// Free halves of one state for interior control points [L0, L1): the point
+// P_l = sum_c D[l][side][c] x[c] per axis, then every polytope row
+// A_r . P_l (- b_r for the start side) in rows l*nrp + r, four rows per
+// 16-byte store; rows r >= nr are padding, neutral in max(u + w).
+template <int M, int G, int PD, int L0, int L1>
+DEVI void free_points(const float (&x)[M * G], const float* tab, const float* Ab, int nr, int nrp, bool right,
+                      float* dF, float neg_inf) {
+    constexpr int NL = L1 - L0;
+    float pt[NL > 0 ? NL : 1][M];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        const float4 dd = *reinterpret_cast<const float4*>(tab + (PadTab<G, PD>::ROW_D + L0 + l) * 8 + (right ? 4 : 0));
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            float w = dd.x * x[a];
+            if (G > 1) w = fmaf(dd.y, x[M + a], w);
+            if (G > 2) w = fmaf(dd.z, x[2 * M + a], w);
+            if (G > 3) w = fmaf(dd.w, x[3 * M + a], w);
+            pt[l][a] = w;
+        }
+    }
+    for (int rq = 0; rq < nrp; rq += 4) {
+        float w4[NL > 0 ? NL : 1][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = rq + j;
+            if (r < nr) {
+                const float4 ab = *reinterpret_cast<const float4*>(Ab + r * 4);
+#pragma unroll
+                for (int l = 0; l < NL; ++l) {
+                    float w = ab.x * pt[l][0];
+                    w = fmaf(ab.y, pt[l][1], w);
+                    if (M > 2) w = fmaf(ab.z, pt[l][2], w);
+                    if (!right) w -= (M > 2 ? ab.w : ab.z);
+                    w4[l][j] = w;
+                }
+            } else {
+#pragma unroll
+                for (int l = 0; l < NL; ++l) w4[l][j] = right ? 0.f : neg_inf;
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < NL; ++l)
+            *reinterpret_cast<float4*>(dF + (L0 + l) * nrp + rq) = make_float4(w4[l][0], w4[l][1], w4[l][2], w4[l][3]);
+    }
+}
+
+// Cost halves of one state for segments [L0, L1): segment l holds rows
+// e = d*M + a (d < DR) of sum_c C[d][l][side][c] x[c][a], zero-padded to PL.
+template <int M, int G, int PD, int L0, int L1>
+DEVI void cost_segments(const float (&x)[M * G], const float* tab, int DR, int PL, bool right, float* dC) {
+    constexpr int PLM = (G * M + 3) & ~3;
+#pragma unroll
+    for (int l = L0; l < L1; ++l) {
+        float val[PLM];
+#pragma unroll
+        for (int e = 0; e < PLM; ++e) val[e] = 0.f;
+#pragma unroll
+        for (int d = 0; d < G; ++d) {
+            if (d < DR) {
+                const float4 h =
+                    *reinterpret_cast<const float4*>(tab + (PadTab<G, PD>::ROW_C + d * PD + l) * 8 + (right ? 4 : 0));
+#pragma unroll
+                for (int a = 0; a < M; ++a) {
+                    float w = h.x * x[a];
+                    if (G > 1) w = fmaf(h.y, x[M + a], w);
+                    if (G > 2) w = fmaf(h.z, x[2 * M + a], w);
+                    if (G > 3) w = fmaf(h.w, x[3 * M + a], w);
+                    val[d * M + a] = w;
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < PLM; e += 4)
+            if (e < PL) *reinterpret_cast<float4*>(dC + l * PL + e) = make_float4(val[e], val[e + 1], val[e + 2], val[e + 3]);
+    }
+}
+
 template <int M, int G, int PD>
 __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
     using S = Shape<G, PD>;
@@ -1114,8 +1192,9 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                 s_n1 = 0;
                 s_n2 = 0;
             }
-            // 1. halves: reach (two half-units per state), free (one unit per
-            // state and interior control point), band magnitudes
+            // 1. halves: two units per state, each loading the state once --
+            // the first takes reach quads [0, RH), interior points [0, NI/2)
+            // and the band magnitudes, the second the rest
             for (int u = tid; u < 2 * S2; u += nthr) {
                 const bool second = u >= S2;
                 const int s = second ? u - S2 : u;
@@ -1126,59 +1205,25 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                 const float* trow = tab + (right ? 4 : 0);
                 float* dU = (right ? UR : UL) + ls * SU;
                 float* dS = (right ? SCR : SCL) + ls;
-                if (!second) reach_quads<M, G, PD, 0, RH>(x, trow, dU, dS, T);
-                else reach_quads<M, G, PD, RH, RQ>(x, trow, dU, dS, T);
-            }
-            for (int u = tid; u < NI * S2; u += nthr) {
-                const int l = u / S2, s = u - l * S2;
-                const bool right = s >= ni4;
-                const int ls = right ? s - ni4 : s;
-                float x[N_];
-                load_state<M, G, PD>(x, xs + (right ? T + ls : ls) * XS);
-                const float4 dd = *reinterpret_cast<const float4*>(tab + (PT::ROW_D + l) * 8 + (right ? 4 : 0));
-                float pt[M];
+                float* dF = (right ? FR : FL) + ls * SF;
+                if (!second) {
+                    reach_quads<M, G, PD, 0, RH>(x, trow, dU, dS, T);
+                    free_points<M, G, PD, 0, NI / 2>(x, tab, Ab, nr, nrp, right, dF, NEG_INF);
+                    const float* xa = xab + (right ? T + ls : ls) * G;
+                    const float* hc = tab + PT::ROW_HC * 8 + (right ? 4 : 0);
+                    const float* dc = tab + PT::ROW_DC * 8 + (right ? 4 : 0);
+                    float mr = 0.f, md = 0.f;
 #pragma unroll
-                for (int a = 0; a < M; ++a) {
-                    float w = dd.x * x[a];
-                    if (G > 1) w = fmaf(dd.y, x[M + a], w);
-                    if (G > 2) w = fmaf(dd.z, x[2 * M + a], w);
-                    if (G > 3) w = fmaf(dd.w, x[3 * M + a], w);
-                    pt[a] = w;
-                }
-                float* dF = (right ? FR : FL) + ls * SF + l * nrp;
-                for (int rq = 0; rq < nrp; rq += 4) {
-                    float w4[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int r = rq + j;
-                        if (r < nr) {
-                            const float4 ab = *reinterpret_cast<const float4*>(Ab + r * 4);
-                            float w = ab.x * pt[0];
-                            w = fmaf(ab.y, pt[1], w);
-                            if (M > 2) w = fmaf(ab.z, pt[2], w);
-                            if (!right) w -= (M > 2 ? ab.w : ab.z);
-                            w4[j] = w;
-                        } else {
-                            w4[j] = right ? 0.f : NEG_INF;  // neutral in max(u + w)
-                        }
+                    for (int c = 0; c < G; ++c) {
+                        mr = fmaf(hc[c], xa[c], mr);
+                        md = fmaf(dc[c], xa[c], md);
                     }
-                    *reinterpret_cast<float4*>(dF + rq) = make_float4(w4[0], w4[1], w4[2], w4[3]);
+                    magR[(right ? T : 0) + ls] = mr;
+                    magF[(right ? T : 0) + ls] = md * s_rown1 + (right ? 0.f : s_bmax);
+                } else {
+                    reach_quads<M, G, PD, RH, RQ>(x, trow, dU, dS, T);
+                    free_points<M, G, PD, NI / 2, NI>(x, tab, Ab, nr, nrp, right, dF, NEG_INF);
                 }
-            }
-            for (int s = tid; s < S2; s += nthr) {
-                const bool right = s >= ni4;
-                const int ls = right ? s - ni4 : s;
-                const float* xa = xab + (right ? T + ls : ls) * G;
-                const float* hc = tab + PT::ROW_HC * 8 + (right ? 4 : 0);
-                const float* dc = tab + PT::ROW_DC * 8 + (right ? 4 : 0);
-                float mr = 0.f, md = 0.f;
-#pragma unroll
-                for (int c = 0; c < G; ++c) {
-                    mr = fmaf(hc[c], xa[c], mr);
-                    md = fmaf(dc[c], xa[c], md);
-                }
-                magR[(right ? T : 0) + ls] = mr;
-                magF[(right ? T : 0) + ls] = md * s_rown1 + (right ? 0.f : s_bmax);
             }
             __syncthreads();
 
@@ -1186,16 +1231,24 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
             if (t + 1 < itc.t1)
                 stage_table<G, PD>(tabs + ((t + 1 - itc.t0) & 1) * PT::FLOATS,
                                    P.tab32 + (long long)(Qd.tabOff + t + 1) * fst, tid, nthr);
-            // 2. screen and list 1
-            if (act) {
-                uint32_t surv = screen_tile<M, G, PD>(T, gi, gj, live, SCL, SCR, magR);
-                if (surv) {
-                    int pos = atomicAdd(&s_n1, __popc(surv));
-                    while (surv) {
-                        const int q = __ffs(surv) - 1;
-                        surv &= surv - 1;
-                        list1[pos++] = (uint16_t)(((4 * gi + (q >> 2)) << 8) | (4 * gj + (q & 3)));
-                    }
+            // 2. screen and list 1 (positions by a warp prefix of the survivor
+            // counts and one shared atomic per warp; the block is whole warps)
+            {
+                uint32_t surv = act ? screen_tile<M, G, PD>(T, gi, gj, live, SCL, SCR, magR) : 0u;
+                const int cnt = __popc(surv);
+                int inc = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if ((tid & 31) >= o) inc += y;
+                }
+                int wbase = 0;
+                if ((tid & 31) == 31 && inc) wbase = atomicAdd(&s_n1, inc);
+                int pos = __shfl_sync(0xffffffffu, wbase, 31) + inc - cnt;
+                while (surv) {
+                    const int q = __ffs(surv) - 1;
+                    surv &= surv - 1;
+                    list1[pos++] = (uint16_t)(((4 * gi + (q >> 2)) << 8) | (4 * gj + (q & 3)));
                 }
             }
             __syncthreads();
@@ -1220,62 +1273,54 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                 }
                 const float rm = fmaxf(fmaxf(r4[0], r4[1]), fmaxf(r4[2], r4[3]));
                 const float bandR = KR * (magR[li] + magR[T + lj]);
-                if (!(rm <= 1.f + bandR)) continue;  // certain reach failure
-                const bool rpass = rm <= 1.f - bandR;
-                rp_cnt += rpass ? 1u : 0u;
-                const float* fl = FL + li * SF;
-                const float* fr = FR + lj * SF;
-                float f4[4] = {NEG_INF, NEG_INF, NEG_INF, NEG_INF};
+                int outcome = 0;  // 0 certain failure, 1 certainly feasible, 2 ambiguous
+                if (rm <= 1.f + bandR) {
+                    const bool rpass = rm <= 1.f - bandR;
+                    rp_cnt += rpass ? 1u : 0u;
+                    const float* fl = FL + li * SF;
+                    const float* fr = FR + lj * SF;
+                    float f4[4] = {NEG_INF, NEG_INF, NEG_INF, NEG_INF};
 #pragma unroll 2
-                for (int r = 0; r < FQ; r += 4) {
-                    const float4 a = *reinterpret_cast<const float4*>(fl + r);
-                    const float4 b = *reinterpret_cast<const float4*>(fr + r);
-                    f4[0] = fmaxf(f4[0], a.x + b.x);
-                    f4[1] = fmaxf(f4[1], a.y + b.y);
-                    f4[2] = fmaxf(f4[2], a.z + b.z);
-                    f4[3] = fmaxf(f4[3], a.w + b.w);
+                    for (int r = 0; r < FQ; r += 4) {
+                        const float4 a = *reinterpret_cast<const float4*>(fl + r);
+                        const float4 b = *reinterpret_cast<const float4*>(fr + r);
+                        f4[0] = fmaxf(f4[0], a.x + b.x);
+                        f4[1] = fmaxf(f4[1], a.y + b.y);
+                        f4[2] = fmaxf(f4[2], a.z + b.z);
+                        f4[3] = fmaxf(f4[3], a.w + b.w);
+                    }
+                    const float fm = fmaxf(fmaxf(f4[0], f4[1]), fmaxf(f4[2], f4[3]));
+                    const float bandF = KF * (magF[li] + magF[T + lj]);
+                    if (fm <= bandF) outcome = (rpass && fm <= -bandF) ? 1 : 2;
                 }
-                const float fm = fmaxf(fmaxf(f4[0], f4[1]), fmaxf(f4[2], f4[3]));
-                const float bandF = KF * (magF[li] + magF[T + lj]);
-                if (!(fm <= bandF)) continue;  // certain free-space failure
-                const bool fpass = fm <= -bandF;
-                if (rpass && fpass) list2[atomicAdd(&s_n2, 1)] = (uint16_t)v;
-                else append_recheck(P, itd.q, k, i0 + li, j0 + lj, t);
+                // list 2 positions: one shared atomic per warp
+                const unsigned am = __activemask();
+                const unsigned fb = __ballot_sync(am, outcome == 1);
+                if (fb) {
+                    const int lane = tid & 31, leader = __ffs(fb) - 1;
+                    int b2 = 0;
+                    if (lane == leader) b2 = atomicAdd(&s_n2, __popc(fb));
+                    b2 = __shfl_sync(am, b2, leader);
+                    if (outcome == 1) list2[b2 + __popc(fb & ((1u << lane) - 1u))] = (uint16_t)v;
+                }
+                if (outcome == 2) append_recheck(P, itd.q, k, i0 + li, j0 + lj, t);
             }
             __syncthreads();
 
             const int n2 = s_n2;
             if (n2 > 0) {
-                // 4. cost halves of this duration over the free halves: segment
-                // l holds rows e = d*M + a (d < DR), zero-padded to PL
-                for (int u = tid; u < PD * S2; u += nthr) {
-                    const int l = u / S2, s = u - l * S2;
+                // 4. cost halves of this duration over the free halves: two
+                // units per state (segments [0, (PD+1)/2) and the rest)
+                for (int u = tid; u < 2 * S2; u += nthr) {
+                    const bool second = u >= S2;
+                    const int s = second ? u - S2 : u;
                     const bool right = s >= ni4;
                     const int ls = right ? s - ni4 : s;
                     float x[N_];
                     load_state<M, G, PD>(x, xs + (right ? T + ls : ls) * XS);
-                    float val[((G * M + 3) & ~3)];
-#pragma unroll
-                    for (int e = 0; e < ((G * M + 3) & ~3); ++e) val[e] = 0.f;
-#pragma unroll
-                    for (int d = 0; d < G; ++d) {
-                        if (d < DR) {
-                            const float4 h =
-                                *reinterpret_cast<const float4*>(tab + (PT::ROW_C + d * PD + l) * 8 + (right ? 4 : 0));
-#pragma unroll
-                            for (int a = 0; a < M; ++a) {
-                                float w = h.x * x[a];
-                                if (G > 1) w = fmaf(h.y, x[M + a], w);
-                                if (G > 2) w = fmaf(h.z, x[2 * M + a], w);
-                                if (G > 3) w = fmaf(h.w, x[3 * M + a], w);
-                                val[d * M + a] = w;
-                            }
-                        }
-                    }
-                    float* dC = (right ? FR : FL) + ls * SF + l * PL;
-#pragma unroll
-                    for (int e = 0; e < ((G * M + 3) & ~3); e += 4)
-                        if (e < PL) *reinterpret_cast<float4*>(dC + e) = make_float4(val[e], val[e + 1], val[e + 2], val[e + 3]);
+                    float* dC = (right ? FR : FL) + ls * SF;
+                    if (!second) cost_segments<M, G, PD, 0, (PD + 1) / 2>(x, tab, DR, PL, right, dC);
+                    else cost_segments<M, G, PD, (PD + 1) / 2, PD>(x, tab, DR, PL, right, dC);
                 }
                 __syncthreads();
                 // 5. costs of the feasible pairs (segment sums in row order)
@@ -2881,7 +2926,8 @@ int launch_pairs(const BuildParams& P, cudaStream_t st, int num_sms, int ctas_pe
         const bool sc = P.pipeline != 2;
         auto kern = sc ? k_pairs_sc<M, G, PD> : k_pairs_fast<M, G, PD>;
         const size_t sm = sc ? smem_sc<M, G, PD>(P) : smem_one<M, G, PD>(P);
-        const int threads = (P.tile / 4) * (P.tile / 4);
+        int threads = (P.tile / 4) * (P.tile / 4);  // one thread per 4x4 micro-tile
+        if (sc) threads = (threads + 31) & ~31;      // whole warps (warp-level list positions)
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, sm);
