@@ -77,7 +77,7 @@ def config(prob, extra=None):
 
 
 class ClockSampler:
-    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks/throttle reasons sampled every 50 ms around the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -91,7 +91,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -111,10 +111,13 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
+    def count(self) -> int:
+        return len(self.lines)
+
+    def summary(self, since: int = 0):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[since:]:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -381,23 +384,39 @@ def main():
             step([torch.cuda.Event(enable_timing=True) for _ in range(3)])
             st = pl.wait()
             assert st == P.PLAN_OK, f"warm-up status {st}"
-        pl.set_timing(True)
-        pl.timing(reset=True)
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
+
+        def untimed_until(cond, limit_s):
+            t0 = time.time()
+            while not cond() and time.time() - t0 < limit_s:
+                flush.fill_(1.0)
+                step([torch.cuda.Event(enable_timing=True) for _ in range(3)])
+                assert pl.wait() == P.PLAN_OK
+
         with ClockSampler(torch.cuda.current_device()) as clk:
+            # the sampler comes up while the same steps run untimed; its samples
+            # from the last one before the timed steps to the first one after
+            # their start (the steps keep running untimed until it arrives)
+            # describe the clocks of the timed region
+            untimed_until(lambda: clk.count() >= 1, 10.0)
+            mark = max(0, clk.count() - 1)
+            pl.set_timing(True)
+            pl.timing(reset=True)
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
             for s in range(args.steps):
                 flush.fill_(float(s))
                 step(evs[s])
                 st = pl.wait()
                 assert st == P.PLAN_OK, f"step {s}: status {st}"
             torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        tm = pl.timing(reset=True)
-        pl.set_timing(False)
+            if dist:
+                dist.barrier()
+            tm = pl.timing(reset=True)
+            pl.set_timing(False)
+            untimed_until(lambda: clk.count() >= mark + 2, 5.0)
+        clocks = clk.summary(since=mark)
         build_ms = [a.elapsed_time(b) for a, b, _ in evs]
         search_ms = [b.elapsed_time(c) for _, b, c in evs]
         step_ms = [a.elapsed_time(c) for a, _, c in evs]
@@ -456,12 +475,17 @@ def main():
     ops_per_check = 4 * m * rax + 2 * (p - 1) * rows_mean + p * (2 * n + 2)
     ops_per_launch = ops_per_check * checks
     sc_ops = (2 * work["work_reach_rows"] + 2 * work["work_free_rows"] + work["work_costs"] * p * (2 * n + 2))
+    # work the screened kernel executes: the screen rows (3 reach rows per axis)
+    # of every ordered pair in every polytope and duration, every reach and free
+    # row of the pairs it passes on, one cost per feasible check
+    screened = int(info.get("screened", 0))
+    ex_ops = (2 * 3 * m * (int(info["slots"]) - int(info["memberships"])) * prob.nT
+              + 2 * (m * rax + (p - 1) * rows_mean) * screened + p * (2 * n + 2) * int(info["feasible"]))
     pair_ms = tm["pair_ms"] / max(1, tm["pair_launches"])
     achieved = ops_per_launch / (pair_ms / 1e3) / 1e12
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = 152 * 128 * sm_max * 1e6 / 1e12
     counters, src_sha = pair_kernel_counters()
-    clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_step / args.steps, "higher_is_better": True,
@@ -480,6 +504,10 @@ def main():
                      "ops_per_check": ops_per_check, "ops_per_launch": ops_per_launch,
                      "work_model": "dense separable form per check (all reach, free and cost rows)",
                      "peak_note": f"FP32 lanes 152 SMs x 128 x {sm_max:.0f} MHz (unit counts and max clock; {peak_src} clock)",
+                     "executed": {"ops_per_launch": ex_ops, "frac": ex_ops / (pair_ms / 1e3) / 1e12 / alu_peak,
+                                  "screened_checks": screened,
+                                  "note": "ops the screened kernel performs: screen rows of every pair and duration, "
+                                          "all reach and free rows of the screened checks, costs of feasible ones"},
                      "short_circuit": {"ops_per_launch": sc_ops, "frac": sc_ops / (pair_ms / 1e3) / 1e12 / alu_peak,
                                        "note": "work left after the early exits (reach rows up to the first violated "
                                                "one, free rows of reach-passing checks, costs of feasible ones)",

@@ -120,6 +120,9 @@ typedef struct {
      * short-circuit evaluation (reach rows up to the first violated one, free
      * rows of reach-passing checks, cost evaluations of feasible checks) */
     int64_t work_reach_rows, work_free_rows, work_costs;
+    /* (pair, T) that the FP32 reach screen passed on to the full rows (the
+     * screened pair kernel only; 0 otherwise) */
+    int64_t screened;
 } plan_info;
 
 /* Create a context bound to the current CUDA device and the given stream

@@ -978,6 +978,7 @@ int plan_wait(plan_ctx* c, plan_info* info) {
         info->work_reach_rows = (int64_t)d.work[0];
         info->work_free_rows = (int64_t)d.work[1];
         info->work_costs = (int64_t)d.work[2];
+        info->screened = (int64_t)d.screened;
     }
     return d.status;
 }

@@ -1097,7 +1097,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     const long long nitems = (long long)P.info->items;
     const int fst = P.L.f_stride;
-    unsigned long long rp_cnt = 0;
+    unsigned long long rp_cnt = 0, nscreened = 0;
     const float NEG_INF = -__int_as_float(0x7f800000);
 
     for (;;) {
@@ -1255,6 +1255,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
 
             // 3. every reach and free row of the screened pairs
             const int n1 = s_n1;
+            if (tid == 0) nscreened += (unsigned long long)n1;
             const int FQ = NI * nrp;
             for (int e = tid; e < n1; e += nthr) {
                 const int v = list1[e];
@@ -1353,6 +1354,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
         }
     }
     block_add(&P.info->reach_pass, rp_cnt);
+    block_add(&P.info->screened, nscreened);
 }
 
 // ---------------------------------------------------------------------------

@@ -64,6 +64,7 @@ struct DevInfo {
     unsigned long long need_slots;
     unsigned long long need_rechecks;
     unsigned long long items;
+    unsigned long long screened;     // pairs the reach screen passed to the full rows
     unsigned int ticket;
     int max_rows_seen;
     int start;

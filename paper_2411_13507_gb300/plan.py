@@ -50,7 +50,8 @@ class _Info(ctypes.Structure):
                 ("reach_pass", ctypes.c_int64), ("feasible", ctypes.c_int64), ("rechecks", ctypes.c_int64),
                 ("edges", ctypes.c_int64), ("search_iters", ctypes.c_int64), ("start", ctypes.c_int32),
                 ("goal", ctypes.c_int32), ("need_slots", ctypes.c_int64), ("need_rechecks", ctypes.c_int64),
-                ("work_reach_rows", ctypes.c_int64), ("work_free_rows", ctypes.c_int64), ("work_costs", ctypes.c_int64)]
+                ("work_reach_rows", ctypes.c_int64), ("work_free_rows", ctypes.c_int64), ("work_costs", ctypes.c_int64),
+                ("screened", ctypes.c_int64)]
 
 
 class _Query(ctypes.Structure):
