@@ -64,7 +64,14 @@ typedef enum { PLAN_COST_STATE = 0, PLAN_COST_POS = 1 } plan_cost_mode;
  *   cost_mode        : PLAN_COST_STATE: polygon length of the n-row state-space
  *                      control points (Eq. BezDef, Property 2); PLAN_COST_POS:
  *                      position rows only.
+ *   interior         : for degree > 2 gamma - 1 Lemma 1 fixes only the first and
+ *                      last gamma control points.  PLAN_INTERIOR_ELEVATE (0): the
+ *                      unique minimal-degree curve, degree-elevated (same curve);
+ *                      PLAN_INTERIOR_MINSNAP (1): interior points minimising the
+ *                      integral of |b^(gamma+1)|^2 over [0, T].
  */
+typedef enum { PLAN_INTERIOR_ELEVATE = 0, PLAN_INTERIOR_MINSNAP = 1 } plan_interior;
+
 typedef struct {
     int m;
     int gamma;
@@ -74,6 +81,7 @@ typedef struct {
     int cost_mode;  /* plan_cost_mode */
     double bound[4];
     double tighten;
+    int interior;   /* plan_interior */
 } plan_model;
 
 /*

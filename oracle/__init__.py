@@ -111,7 +111,8 @@ class OracleProblem:
         self.eps = float(getattr(mdl, "tighten", 0.0))
         self.cost_mode = 1 if getattr(mdl, "cost_mode", "state") == "pos" else 0
         self.N, self.K, self.nT = self.states.shape[0], self.poly_off.shape[0] - 1, self.T.shape[0]
-        tb = tables if tables is not None else _tables.tables(self.gamma, self.p, self.T)
+        self.interior = getattr(mdl, "interior", "elevate")
+        tb = tables if tables is not None else _tables.tables(self.gamma, self.p, self.T, self.interior)
         self.D = np.ascontiguousarray(tb["D"], dtype=np.float64)
         self.H = np.ascontiguousarray(tb["H"], dtype=np.float64)
         self.C = np.ascontiguousarray(tb["C"], dtype=np.float64)

@@ -18,7 +18,9 @@ converted to the Bernstein basis of the required degree with the identity
 u^s = sum_{l>=s} C(l,s)/C(P,s) B_l^P(u).
 
 Tables (per duration T):
-  D  [(p+1)][2g]      control points of b(t) in degree p (Lemma 1; Sec. II-B).
+  D  [(p+1)][2g]      control points of b(t) in degree p (Lemma 1; Sec. II-B);
+                      for p > 2g-1 either the elevated minimal-degree curve or
+                      the minimum-energy interior points (minsnap_monomial).
   H  [Rax][2g]        reach rows: control points of b^(k)(t) in degree p-k,
                       k = 1..g, j = 0..p-k (Theorem 1 read as per-axis bounds
                       |b^(k)| <= c_k on the hodograph control points).
@@ -74,6 +76,42 @@ def hermite_monomial(gamma: int, T: Fraction) -> List[List[Fraction]]:
     return [[cols[c][s] for c in range(2 * g)] for s in range(q + 1)]
 
 
+def minsnap_monomial(gamma: int, p: int, T: Fraction) -> List[List[Fraction]]:
+    """Monomial coefficients (in u = t/T) of the degree-p curve meeting the
+    Lemma 1 end conditions with minimal energy int_0^T |b^(g+1)(t)|^2 dt.
+
+    Route (independent of the Bernstein normal equations a GPU table generator
+    would use): Lagrange conditions of the equality-constrained quadratic
+    programme in the p+1 monomial coefficients,
+        [2Q  M^T] [a ]   [0  ]
+        [M   0  ] [mu] = [rhs],
+    with Q_st = int_0^1 s!/(s-g-1)! t!/(t-g-1)! u^(s+t-2g-2) du (the factor
+    T^(1-2(g+1)) is a positive constant and does not move the minimiser) and M
+    the 2g end conditions of hermite_monomial, solved exactly per column.
+    """
+    g = gamma
+    ne = 2 * g
+    nv = p + 1
+
+    def dfac(s):
+        return Fraction(factorial(s), factorial(s - g - 1)) if s >= g + 1 else Fraction(0)
+
+    Q = [[(dfac(s) * dfac(t) / (s + t - 2 * g - 1)) if (s >= g + 1 and t >= g + 1) else Fraction(0)
+          for t in range(nv)] for s in range(nv)]
+    M = []
+    for c in range(g):
+        M.append([Fraction(factorial(s), factorial(s - c)) / T ** c if s == c else Fraction(0) for s in range(nv)])
+    for c in range(g):
+        M.append([Fraction(factorial(s), factorial(s - c)) / T ** c if s >= c else Fraction(0) for s in range(nv)])
+    K = [[2 * Q[r][c] for c in range(nv)] + [M[e][r] for e in range(ne)] for r in range(nv)]
+    K += [[M[e][c] for c in range(nv)] + [Fraction(0)] * ne for e in range(ne)]
+    cols = []
+    for c in range(ne):
+        rhs = [Fraction(0)] * nv + [Fraction(1) if e == c else Fraction(0) for e in range(ne)]
+        cols.append(_solve_exact(K, rhs)[:nv])
+    return [[cols[c][s] for c in range(ne)] for s in range(nv)]
+
+
 def derivative_monomial(a: List[List[Fraction]], k: int, T: Fraction) -> List[List[Fraction]]:
     """Monomial coefficients of d^k b/dt^k: a'_r = T^{-k} (r+k)!/r! a_{r+k}."""
     deg = len(a) - 1
@@ -99,11 +137,19 @@ def monomial_to_bernstein(a: List[List[Fraction]], P: int) -> List[List[Fraction
     return out
 
 
-def exact_tables(gamma: int, p: int, T: float) -> Dict[str, List]:
-    """Exact (Fraction) tables for one duration T (T is taken as its exact binary value)."""
+def exact_tables(gamma: int, p: int, T: float, interior: str = "elevate") -> Dict[str, List]:
+    """Exact (Fraction) tables for one duration T (T is taken as its exact binary value).
+
+    interior = "elevate": the minimal-degree Hermite curve in degree p (Lemma 1
+    plus degree elevation); "minsnap": the degree-p curve with the same end
+    conditions and minimal int |b^(g+1)|^2 (equal to "elevate" at p = 2g-1).
+    """
     assert p >= 2 * gamma - 1
     Tq = Fraction(T)
-    a = hermite_monomial(gamma, Tq)
+    if interior == "minsnap" and p > 2 * gamma - 1:
+        a = minsnap_monomial(gamma, p, Tq)
+    else:
+        a = hermite_monomial(gamma, Tq)
     D = monomial_to_bernstein(a, p)
     H: List[List[Fraction]] = []
     for k in range(1, gamma + 1):
@@ -121,11 +167,11 @@ def _to_float(x):
     return float(x)   # Fraction -> double: correctly rounded (int true division)
 
 
-def tables(gamma: int, p: int, Ts) -> Dict[str, np.ndarray]:
+def tables(gamma: int, p: int, Ts, interior: str = "elevate") -> Dict[str, np.ndarray]:
     """Double tables for all durations: D [nT][p+1][2g], H [nT][Rax][2g], C [nT][g][p][2g]."""
     Ds, Hs, Cs = [], [], []
     for T in Ts:
-        t = exact_tables(gamma, p, float(T))
+        t = exact_tables(gamma, p, float(T), interior)
         Ds.append(_to_float(t["D"]))
         Hs.append(_to_float(t["H"]))
         Cs.append(_to_float(t["C"]))

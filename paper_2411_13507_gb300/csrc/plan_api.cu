@@ -146,6 +146,7 @@ int check_model(const plan_model* m) {
     if (m->arith < PLAN_F64 || m->arith > PLAN_BF16) return PLAN_ERR_INVALID_ARG;
     if (m->input != PLAN_IN_F64 && m->input != PLAN_IN_F32) return PLAN_ERR_INVALID_ARG;
     if (m->cost_mode != PLAN_COST_STATE && m->cost_mode != PLAN_COST_POS) return PLAN_ERR_INVALID_ARG;
+    if (m->interior != PLAN_INTERIOR_ELEVATE && m->interior != PLAN_INTERIOR_MINSNAP) return PLAN_ERR_INVALID_ARG;
     if (!std::isfinite(m->tighten) || m->tighten < 0) return PLAN_ERR_INVALID_ARG;
     for (int k = 0; k < m->gamma; ++k)
         if (!std::isfinite(m->bound[k]) || !(m->bound[k] - m->tighten > 0)) return PLAN_ERR_INVALID_ARG;
@@ -179,7 +180,7 @@ int upload_tables(plan_ctx* c, const std::vector<double>& Tall) {
         c->tab_nT_cap = cap;
     }
     std::vector<double> D((size_t)nT * (p + 1) * tg), H((size_t)nT * L.rax * tg), C((size_t)nT * g * p * tg);
-    exact_tables(g, p, nT, Tall.data(), D.data(), H.data(), C.data());
+    exact_tables(g, p, c->model.interior, nT, Tall.data(), D.data(), H.data(), C.data());
     std::vector<int> Hk;
     for (int k = 1; k <= g; ++k)
         for (int j = 0; j <= p - k; ++j) Hk.push_back(k);
@@ -317,11 +318,15 @@ const char* plan_last_error(plan_ctx* ctx) { return ctx ? ctx->last_error.c_str(
 int plan_model_tables(const plan_model* model, int nT, const double* T, double* D, double* H, double* C) {
     if (!model || model->gamma < 1 || model->gamma > 4 || model->degree < 2 * model->gamma - 1 || model->degree > 15)
         return PLAN_ERR_INVALID_ARG;
+    // the minimum-energy solve stays within exact 128-bit rationals up to degree 9
+    if (model->interior != PLAN_INTERIOR_ELEVATE &&
+        (model->interior != PLAN_INTERIOR_MINSNAP || model->degree > 9))
+        return PLAN_ERR_INVALID_ARG;
     if (nT < 0 || (nT > 0 && (!T || !D || !H || !C))) return PLAN_ERR_INVALID_ARG;
     for (int t = 0; t < nT; ++t)
         if (!std::isfinite(T[t]) || !(T[t] > 0)) return PLAN_ERR_INVALID_ARG;
     try {
-        exact_tables(model->gamma, model->degree, nT, T, D, H, C);
+        exact_tables(model->gamma, model->degree, model->interior, nT, T, D, H, C);
     } catch (...) {
         return PLAN_ERR_NO_MEMORY;
     }

@@ -42,6 +42,13 @@ constexpr float KU = 5.9604644775390625e-08f;  // 2^-24
 constexpr float KR = 16.f * KU;
 constexpr float KF = 24.f * KU;
 constexpr float KMEM = 16.f * KU;
+// FP32 cost conditioning.  A cost is a sum of segment norms of (start half +
+// end half) rows; its rounding error stays below about 1.2 u times the sum of
+// |half| over all rows (measured over every feasible check of the 2-D and 3-D
+// workloads, both interior readings), so a cost whose half-magnitude sum
+// exceeds COST_RHO times the cost (error bound ~3.5e-6 relative, e.g. two
+// nearly equal states whose halves cancel) is recomputed in FP64 instead.
+constexpr float COST_RHO = 48.f;
 constexpr unsigned long long KEY_NONE = ~0ull;
 constexpr unsigned long long DINF_BITS = 0x7FF0000000000000ull;
 
@@ -448,12 +455,15 @@ __global__ void k_zero_slots(BuildParams P) {
     }
 }
 
-// Re-check entry: query (16 bits) | polytope (10) | li (16) | lj (16) | T (5).
-DEVI void append_recheck(const BuildParams& P, int q, int k, int li, int lj, int t) {
+// Re-check entry: cost-only flag (1 bit) | query (16 bits) | polytope (10) | li (16) | lj (16) | T (5).
+// Bit 63 marks a check that is certainly feasible and needs only its cost in
+// FP64 (an ill-conditioned FP32 cost).
+DEVI void append_recheck(const BuildParams& P, int q, int k, int li, int lj, int t, bool cost_only = false) {
     const unsigned long long idx = atomicAdd(&P.info->rechecks, 1ull);
     if ((long long)idx < P.recheckCap) {
-        P.recheck[idx] = ((unsigned long long)q << 47) | ((unsigned long long)k << 37) |
-                         ((unsigned long long)li << 21) | ((unsigned long long)lj << 5) | (unsigned long long)t;
+        P.recheck[idx] = ((unsigned long long)cost_only << 63) | ((unsigned long long)q << 47) |
+                         ((unsigned long long)k << 37) | ((unsigned long long)li << 21) |
+                         ((unsigned long long)lj << 5) | (unsigned long long)t;
     } else {
         atomicMax(&P.info->need_rechecks, idx + 1);
         set_status(P.info, PLAN_ERR_CAPACITY, DET_RECHECK);
@@ -574,6 +584,7 @@ DEVI void pair_phase(const BuildParams& P, const Item& itd, int t, int T, int gi
                     const float* clp = CL + 4 * gi;
                     const float* crp = CRr + 4 * gj;
                     const int per_l = DR * M;
+                    float mL[4] = {0.f, 0.f, 0.f, 0.f}, mR[4] = {0.f, 0.f, 0.f, 0.f};  // sum |half| per state
                     for (int l = 0; l < PD; ++l) {
                         float ss[16];
 #pragma unroll
@@ -585,12 +596,15 @@ DEVI void pair_phase(const BuildParams& P, const Item& itd, int t, int T, int gi
                             const float uu[4] = {u.x, u.y, u.z, u.w};
                             const float ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-                            for (int qa = 0; qa < 4; ++qa)
+                            for (int qa = 0; qa < 4; ++qa) {
+                                mL[qa] += fabsf(uu[qa]);
+                                mR[qa] += fabsf(ww[qa]);
 #pragma unroll
                                 for (int qb = 0; qb < 4; ++qb) {
                                     const float d = uu[qa] + ww[qb];
                                     ss[qa * 4 + qb] = fmaf(d, d, ss[qa * 4 + qb]);
                                 }
+                            }
                         }
 #pragma unroll
                         for (int q = 0; q < 16; ++q) cs[q] += sqrtf(ss[q]);
@@ -598,10 +612,14 @@ DEVI void pair_phase(const BuildParams& P, const Item& itd, int t, int T, int gi
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         if ((feas >> q) & 1u) {
-                            const long long slot =
-                                itd.base + (long long)(i0 + 4 * gi + (q >> 2)) * itd.nk + (j0 + 4 * gj + (q & 3));
-                            atomicOr(&P.resBits[slot], 1u << t);
-                            atomicMin(&P.resKey[slot], key_f32(cs[q], t));
+                            const int li = i0 + 4 * gi + (q >> 2), lj = j0 + 4 * gj + (q & 3);
+                            if (mL[q >> 2] + mR[q & 3] <= COST_RHO * cs[q]) {
+                                const long long slot = itd.base + (long long)li * itd.nk + lj;
+                                atomicOr(&P.resBits[slot], 1u << t);
+                                atomicMin(&P.resKey[slot], key_f32(cs[q], t));
+                            } else {
+                                append_recheck(P, itd.q, k, li, lj, t, true);  // ill-conditioned FP32 cost
+                            }
                         }
                     }
                 }
@@ -682,6 +700,25 @@ DEVI void stage_table(float* dst, const float* src, int tid, int nthr) {
         dst[u] = c < G ? src[row * TG + side * G + c] : 0.f;
     }
 }
+
+// The same staging with asynchronous 4-byte copies (cp.async): the issuing
+// thread does not wait for the global loads; cp.async.wait_all before the
+// block barrier that precedes the table's first use completes them.
+template <int G, int PD>
+DEVI void stage_table_async(float* dst, const float* src, int tid, int nthr) {
+    constexpr int TG = 2 * G;
+    for (int u = tid; u < PadTab<G, PD>::FLOATS; u += nthr) {
+        const int row = u >> 3, side = (u >> 2) & 1, c = u & 3;
+        if (c < G) {
+            const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + u);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src + row * TG + side * G + c)
+                         : "memory");
+        } else {
+            dst[u] = 0.f;
+        }
+    }
+}
+DEVI void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <int M, int G, int PD>
 __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
@@ -1035,9 +1072,11 @@ DEVI void free_points(const float (&x)[M * G], const float* tab, const float* Ab
 
 // Cost halves of one state for segments [L0, L1): segment l holds rows
 // e = d*M + a (d < DR) of sum_c C[d][l][side][c] x[c][a], zero-padded to PL.
+// Returns the sum of |half| over the rows written.
 template <int M, int G, int PD, int L0, int L1>
-DEVI void cost_segments(const float (&x)[M * G], const float* tab, int DR, int PL, bool right, float* dC) {
+DEVI float cost_segments(const float (&x)[M * G], const float* tab, int DR, int PL, bool right, float* dC) {
     constexpr int PLM = (G * M + 3) & ~3;
+    float mag = 0.f;
 #pragma unroll
     for (int l = L0; l < L1; ++l) {
         float val[PLM];
@@ -1055,6 +1094,7 @@ DEVI void cost_segments(const float (&x)[M * G], const float* tab, int DR, int P
                     if (G > 2) w = fmaf(h.z, x[2 * M + a], w);
                     if (G > 3) w = fmaf(h.w, x[3 * M + a], w);
                     val[d * M + a] = w;
+                    mag += fabsf(w);
                 }
             }
         }
@@ -1062,6 +1102,7 @@ DEVI void cost_segments(const float (&x)[M * G], const float* tab, int DR, int P
         for (int e = 0; e < PLM; e += 4)
             if (e < PL) *reinterpret_cast<float4*>(dC + l * PL + e) = make_float4(val[e], val[e + 1], val[e + 2], val[e + 3]);
     }
+    return mag;
 }
 
 template <int M, int G, int PD>
@@ -1084,7 +1125,8 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
     float* SCR = SCL + NS * T;
     float* magR = SCR + NS * T;      // [2T] band magnitudes
     float* magF = magR + 2 * T;
-    float* xs = magF + 2 * T;        // [2T][XS] centred states
+    float* magC = magF + 2 * T;      // [2T] sum of |cost half| per state-side (cost conditioning)
+    float* xs = magC + 2 * T;        // [2T][XS] centred states
     float* xab = xs + 2 * T * XS;    // [2T][G] per-derivative maxima over the axes
     float* tabs = xab + 2 * T * G;   // two padded duration tables
     float* Ab = tabs + 2 * PT::FLOATS;  // [RMAX][4]: A_r, then b_r
@@ -1207,6 +1249,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                 float* dS = (right ? SCR : SCL) + ls;
                 float* dF = (right ? FR : FL) + ls * SF;
                 if (!second) {
+                    magC[(right ? T : 0) + ls] = 0.f;  // summed by the cost-halves units
                     reach_quads<M, G, PD, 0, RH>(x, trow, dU, dS, T);
                     free_points<M, G, PD, 0, NI / 2>(x, tab, Ab, nr, nrp, right, dF, NEG_INF);
                     const float* xa = xab + (right ? T + ls : ls) * G;
@@ -1229,8 +1272,8 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
 
             // the next duration's table goes to the other buffer meanwhile
             if (t + 1 < itc.t1)
-                stage_table<G, PD>(tabs + ((t + 1 - itc.t0) & 1) * PT::FLOATS,
-                                   P.tab32 + (long long)(Qd.tabOff + t + 1) * fst, tid, nthr);
+                stage_table_async<G, PD>(tabs + ((t + 1 - itc.t0) & 1) * PT::FLOATS,
+                                         P.tab32 + (long long)(Qd.tabOff + t + 1) * fst, tid, nthr);
             // 2. screen and list 1 (positions by a warp prefix of the survivor
             // counts and one shared atomic per warp; the block is whole warps)
             {
@@ -1320,8 +1363,9 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                     float x[N_];
                     load_state<M, G, PD>(x, xs + (right ? T + ls : ls) * XS);
                     float* dC = (right ? FR : FL) + ls * SF;
-                    if (!second) cost_segments<M, G, PD, 0, (PD + 1) / 2>(x, tab, DR, PL, right, dC);
-                    else cost_segments<M, G, PD, (PD + 1) / 2, PD>(x, tab, DR, PL, right, dC);
+                    const float mg = !second ? cost_segments<M, G, PD, 0, (PD + 1) / 2>(x, tab, DR, PL, right, dC)
+                                             : cost_segments<M, G, PD, (PD + 1) / 2, PD>(x, tab, DR, PL, right, dC);
+                    atomicAdd(&magC[(right ? T : 0) + ls], mg);  // two units per state-side
                 }
                 __syncthreads();
                 // 5. costs of the feasible pairs (segment sums in row order)
@@ -1345,11 +1389,16 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                         }
                         cs += sqrtf(ss);
                     }
-                    const long long slot = itd.base + (long long)(i0 + li) * itd.nk + (j0 + lj);
-                    atomicOr(&P.resBits[slot], 1u << t);
-                    atomicMin(&P.resKey[slot], key_f32(cs, t));
+                    if (magC[li] + magC[T + lj] <= COST_RHO * cs) {
+                        const long long slot = itd.base + (long long)(i0 + li) * itd.nk + (j0 + lj);
+                        atomicOr(&P.resBits[slot], 1u << t);
+                        atomicMin(&P.resKey[slot], key_f32(cs, t));
+                    } else {
+                        append_recheck(P, itd.q, k, i0 + li, j0 + lj, t, true);  // ill-conditioned FP32 cost
+                    }
                 }
             }
+            cp_async_wait_all();  // the next duration's table
             __syncthreads();
         }
     }
@@ -2257,7 +2306,8 @@ __global__ void k_recheck(BuildParams P) {
     for (long long e = wid; e < n; e += nw) {
         const unsigned long long en = P.recheck[e];
         const int t = (int)(en & 31ull), lj = (int)((en >> 5) & 0xFFFFull), li = (int)((en >> 21) & 0xFFFFull);
-        const int k = (int)((en >> 37) & 0x3FFull), q = (int)(en >> 47);
+        const int k = (int)((en >> 37) & 0x3FFull), q = (int)((en >> 47) & 0xFFFFull);
+        const bool cost_only = (en >> 63) != 0;  // feasible for certain: only the cost in FP64
         const QueryDesc& Q = P.qd[q];
         const int nk = P.counts[Q.kOff + k];
         const int* members = P.members + Q.listOff + (long long)k * Q.N;
@@ -2270,7 +2320,7 @@ __global__ void k_recheck(BuildParams P) {
         }
         const double* tb = P.tab64 + (long long)(Q.tabOff + t) * L.e_stride;
         bool ok = true;
-        for (int u = lane; u < RAX * M; u += 32) {
+        for (int u = cost_only ? RAX * M : lane; u < RAX * M; u += 32) {
             const int r = u / M, a = u % M;
             const double s = __dadd_rn(half_sum<G>(tb + L.e_H + r * TG, xi + a, M),
                                        half_sum<G>(tb + L.e_H + r * TG + G, xj + a, M));
@@ -2279,7 +2329,7 @@ __global__ void k_recheck(BuildParams P) {
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) continue;
         const int r0 = Q.poly_off[k], nr = Q.poly_off[k + 1] - r0;
-        for (int u = lane; u < NI * nr; u += 32) {
+        for (int u = cost_only ? NI * nr : lane; u < NI * nr; u += 32) {
             const int l = 1 + u / nr, r = r0 + u % nr;
             double s = 0.0;
             for (int a = 0; a < M; ++a) {
@@ -2835,15 +2885,15 @@ size_t smem_one(const BuildParams& P) {
     return f * sizeof(float);
 }
 
-// screened FP32 kernel: transposed halves, screen rows, states, two padded
-// tables, A|b rows and the two pair lists
+// screened FP32 kernel: transposed halves, screen rows, band and cost
+// magnitudes, states, two padded tables, A|b rows and the two pair lists
 template <int M, int G, int PD>
 size_t smem_sc(const BuildParams& P) {
     using SS = ScShape<M, G, PD>;
     const int DR = P.cost_mode == 1 ? 1 : G;
     const size_t T = (size_t)P.tile;
     const size_t SF = (size_t)sc_free_stride(Shape<G, PD>::NI, P.max_rows, PD, (DR * M + 3) & ~3);
-    size_t f = T * (2 * SS::SU + 2 * SF + 2 * SS::NS + 4) + 2 * T * (SS::XS + G) + 2 * PadTab<G, PD>::FLOATS + RMAX * 4;
+    size_t f = T * (2 * SS::SU + 2 * SF + 2 * SS::NS + 6) + 2 * T * (SS::XS + G) + 2 * PadTab<G, PD>::FLOATS + RMAX * 4;
     return f * sizeof(float) + 2 * T * T * sizeof(uint16_t);
 }
 

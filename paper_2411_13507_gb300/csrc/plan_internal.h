@@ -15,7 +15,7 @@ constexpr int NK_MAX = 65535;   // members per polytope (16-bit local index in r
 
 // Host: FP64 tables (see plan_tables.cpp).
 int reach_rows(int g, int p);
-void exact_tables(int g, int p, int nT, const double* T, double* D, double* H, double* C);
+void exact_tables(int g, int p, int interior, int nT, const double* T, double* D, double* H, double* C);
 
 // Layout of the per-duration tables uploaded to the device (depends on g, p only).
 struct TabLayout {

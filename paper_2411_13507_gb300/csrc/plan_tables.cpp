@@ -17,6 +17,12 @@
 //      Q^(k)_j = p!/(p-k)! T^-k sum_s (-1)^{k-s} C(k,s) P_{j+s},  k = 1..g.
 //  * Eq. (BezDef) / Property 2: the degree-p control points of b^(d) are Q^(d)
 //    elevated by d; cost rows are their consecutive differences.
+//  * Interior points for p > 2g-1 (Lemma 1 fixes only the first and last g
+//    control points of a degree-p curve): either the elevated minimal-degree
+//    curve (default) or the points minimising int_0^T |b^(g+1)|^2 dt with the
+//    2g end points fixed (PLAN_INTERIOR_MINSNAP).  The energy is a quadratic
+//    form in Delta^(g+1) P with the Bernstein Gram matrix of degree p-g-1, so
+//    the minimiser is free = S fixed for a rational S independent of T.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -174,7 +180,88 @@ struct RhoTables {
     std::vector<int> Hk;  // derivative order of each reach row
 };
 
-RhoTables rho_tables(int g, int p) {
+// Solves A X = B in place for square A (exact rationals, partial pivoting on
+// non-zero); B has ncol columns.
+void solve_rat(std::vector<std::vector<Rat>>& A, std::vector<std::vector<Rat>>& B) {
+    const int n = (int)A.size(), ncol = n ? (int)B[0].size() : 0;
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        while (piv < n && A[piv][col].n == 0) ++piv;
+        std::swap(A[col], A[piv]);
+        std::swap(B[col], B[piv]);
+        const Rat inv(A[col][col].d, A[col][col].n);
+        for (int c = 0; c < n; ++c) A[col][c] = A[col][c] * inv;
+        for (int c = 0; c < ncol; ++c) B[col][c] = B[col][c] * inv;
+        for (int r = 0; r < n; ++r) {
+            if (r == col || A[r][col].n == 0) continue;
+            const Rat f = A[r][col];
+            for (int c = 0; c < n; ++c) A[r][c] = A[r][c] - f * A[col][c];
+            for (int c = 0; c < ncol; ++c) B[r][c] = B[r][c] - f * B[col][c];
+        }
+    }
+}
+
+// Control points of the degree-p curve with interior points of minimal
+// (g+1)-th-derivative energy: first g and last g points from the end
+// conditions (the end-point difference relations at degree p), the rest from
+// the normal equations of the energy.
+std::vector<std::vector<Rat>> minsnap_points(int g, int p) {
+    const int tg = 2 * g;
+    std::vector<std::vector<Rat>> P(p + 1, std::vector<Rat>(tg));
+    for (int k = 0; k < g; ++k) {  // start side
+        std::vector<Rat> v(tg);
+        v[k] = Rat(fact(p - k), fact(p));
+        for (int s = 0; s < k; ++s) {
+            Rat w(((k - s) % 2 ? -1 : 1) * binom(k, s));
+            for (int c = 0; c < tg; ++c) v[c] = v[c] - w * P[s][c];
+        }
+        P[k] = v;
+    }
+    for (int k = 0; k < g; ++k) {  // end side
+        std::vector<Rat> v(tg);
+        v[g + k] = Rat(fact(p - k), fact(p));
+        for (int s = 0; s < k; ++s) {
+            Rat w((s % 2 ? -1 : 1) * binom(k, s));
+            for (int c = 0; c < tg; ++c) v[c] = v[c] - w * P[p - s][c];
+        }
+        Rat sg(k % 2 ? -1 : 1);
+        for (int c = 0; c < tg; ++c) v[c] = sg * v[c];
+        P[p - k] = v;
+    }
+    const int nf = p - 2 * g + 1, qd = p - g - 1;  // free points g..p-g; Delta^(g+1) P has qd+1 rows
+    if (nf <= 0) return P;
+    // E: Delta^(g+1) as a (qd+1) x (p+1) matrix; Gram of the degree-qd Bernstein basis
+    std::vector<std::vector<Rat>> E(qd + 1, std::vector<Rat>(p + 1)), Gm(qd + 1, std::vector<Rat>(qd + 1));
+    for (int j = 0; j <= qd; ++j)
+        for (int s = 0; s <= g + 1; ++s) E[j][j + s] = Rat(((g + 1 - s) % 2 ? -1 : 1) * binom(g + 1, s));
+    for (int j = 0; j <= qd; ++j)
+        for (int l = 0; l <= qd; ++l)
+            Gm[j][l] = Rat(binom(qd, j) * binom(qd, l), (2 * qd + 1) * binom(2 * qd, j + l));
+    // (E_z^T G E_z) z = -E_z^T G (E_f f), f = the fixed points (as maps of xi)
+    std::vector<std::vector<Rat>> GE(qd + 1, std::vector<Rat>(p + 1));  // G E
+    for (int j = 0; j <= qd; ++j)
+        for (int c = 0; c <= p; ++c)
+            for (int l = 0; l <= qd; ++l) GE[j][c] = GE[j][c] + Gm[j][l] * E[l][c];
+    std::vector<std::vector<Rat>> Az(nf, std::vector<Rat>(nf)), Bz(nf, std::vector<Rat>(tg));
+    for (int a = 0; a < nf; ++a) {
+        const int za = g + a;
+        for (int b = 0; b < nf; ++b) {
+            const int zb = g + b;
+            for (int j = 0; j <= qd; ++j) Az[a][b] = Az[a][b] + E[j][za] * GE[j][zb];
+        }
+        for (int c = 0; c <= p; ++c) {
+            if (c >= g && c <= p - g) continue;  // fixed points only
+            Rat m;  // (E_z^T G E)[a][c]
+            for (int j = 0; j <= qd; ++j) m = m + E[j][za] * GE[j][c];
+            for (int x = 0; x < tg; ++x) Bz[a][x] = Bz[a][x] - m * P[c][x];
+        }
+    }
+    solve_rat(Az, Bz);
+    for (int a = 0; a < nf; ++a) P[g + a] = Bz[a];
+    return P;
+}
+
+RhoTables rho_tables(int g, int p, int interior) {
     RhoTables R;
     R.g = g;
     R.p = p;
@@ -201,15 +288,19 @@ RhoTables rho_tables(int g, int p) {
         for (int c = 0; c < tg; ++c) v[c] = sg * v[c];
         beta[q - k] = v;
     }
-    // degree elevation q -> p
+    // degree elevation q -> p, or the minimum-energy interior points
     std::vector<std::vector<Rat>> P(p + 1, std::vector<Rat>(tg));
-    for (int l = 0; l <= p; ++l)
-        for (int s = 0; s <= q; ++s) {
-            int64_t num = binom(q, s) * binom(p - q, l - s);
-            if (!num) continue;
-            Rat w(num, binom(p, l));
-            for (int c = 0; c < tg; ++c) P[l][c] = P[l][c] + w * beta[s][c];
-        }
+    if (interior == 1 && p > q) {
+        P = minsnap_points(g, p);
+    } else {
+        for (int l = 0; l <= p; ++l)
+            for (int s = 0; s <= q; ++s) {
+                int64_t num = binom(q, s) * binom(p - q, l - s);
+                if (!num) continue;
+                Rat w(num, binom(p, l));
+                for (int c = 0; c < tg; ++c) P[l][c] = P[l][c] + w * beta[s][c];
+            }
+    }
     R.D.resize((size_t)(p + 1) * tg);
     for (int l = 0; l <= p; ++l)
         for (int c = 0; c < tg; ++c) R.D[(size_t)l * tg + c] = P[l][c];
@@ -258,8 +349,8 @@ int reach_rows(int g, int p) {
     return r;
 }
 
-void exact_tables(int g, int p, int nT, const double* T, double* D, double* H, double* C) {
-    RhoTables R = rho_tables(g, p);
+void exact_tables(int g, int p, int interior, int nT, const double* T, double* D, double* H, double* C) {
+    RhoTables R = rho_tables(g, p, interior);
     const int tg = 2 * g;
     for (int t = 0; t < nT; ++t) {
         double Tv = T[t];

@@ -35,7 +35,7 @@ class PlanError(RuntimeError):
 class _Model(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("gamma", ctypes.c_int), ("degree", ctypes.c_int),
                 ("arith", ctypes.c_int), ("input", ctypes.c_int), ("cost_mode", ctypes.c_int),
-                ("bound", ctypes.c_double * 4), ("tighten", ctypes.c_double)]
+                ("bound", ctypes.c_double * 4), ("tighten", ctypes.c_double), ("interior", ctypes.c_int)]
 
 
 class _Edges(ctypes.Structure):
@@ -146,12 +146,17 @@ def status_string(s: int) -> str:
         return "?"
 
 
-def _model(m, gamma, degree, bounds, arith="f64", input="f64", cost_mode="state", tighten=0.0) -> _Model:
+INTERIOR = {"elevate": 0, "minsnap": 1}
+
+
+def _model(m, gamma, degree, bounds, arith="f64", input="f64", cost_mode="state", tighten=0.0,
+           interior="elevate") -> _Model:
     b = (ctypes.c_double * 4)(*([float(x) for x in bounds] + [0.0] * (4 - len(bounds))))
-    return _Model(int(m), int(gamma), int(degree), ARITH[arith], INPUT[input], COST[cost_mode], b, float(tighten))
+    return _Model(int(m), int(gamma), int(degree), ARITH[arith], INPUT[input], COST[cost_mode], b, float(tighten),
+                  INTERIOR[interior])
 
 
-def model_tables(gamma: int, degree: int, T: Sequence[float]):
+def model_tables(gamma: int, degree: int, T: Sequence[float], interior: str = "elevate"):
     """The library's FP64 coefficient tables (host only, no GPU): D, H, C."""
     lib = load()
     T = np.ascontiguousarray(np.asarray(T, dtype=np.float64))
@@ -160,7 +165,7 @@ def model_tables(gamma: int, degree: int, T: Sequence[float]):
     D = np.zeros((nT, p + 1, 2 * g))
     H = np.zeros((nT, rax, 2 * g))
     C = np.zeros((nT, g, p, 2 * g))
-    mdl = _model(1, g, p, [1.0] * g)
+    mdl = _model(1, g, p, [1.0] * g, interior=interior)
     dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     rc = lib.plan_model_tables(ctypes.byref(mdl), nT, dp(T), dp(D), dp(H), dp(C))
     if rc != 0:
@@ -252,10 +257,11 @@ class Planner:
     """One libplan context bound to a CUDA stream."""
 
     def __init__(self, m: int, gamma: int, degree: int, bounds: Sequence[float], arith: str = "f64",
-                 input: str = "f64", cost_mode: str = "state", tighten: float = 0.0, stream=None):
+                 input: str = "f64", cost_mode: str = "state", tighten: float = 0.0, stream=None,
+                 interior: str = "elevate"):
         import torch
         self.lib = load()
-        self.model = _model(m, gamma, degree, bounds, arith, input, cost_mode, tighten)
+        self.model = _model(m, gamma, degree, bounds, arith, input, cost_mode, tighten, interior)
         self.arith, self.input = arith, input
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         ctx = ctypes.c_void_p()
@@ -270,7 +276,7 @@ class Planner:
         mdl = prob.model
         dt = getattr(prob, "dtype", "f64")
         return cls(mdl.m, mdl.gamma, mdl.degree, mdl.bounds, arith=arith or dt, input=input or dt,
-                   cost_mode=mdl.cost_mode, tighten=mdl.tighten, **kw)
+                   cost_mode=mdl.cost_mode, tighten=mdl.tighten, interior=getattr(mdl, "interior", "elevate"), **kw)
 
     def close(self):
         if getattr(self, "ctx", None):

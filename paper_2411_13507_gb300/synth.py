@@ -94,6 +94,7 @@ class Model:
     bounds: Sequence[float]
     tighten: float = 0.0
     cost_mode: str = "state"   # "state": all n rows of the state-space control points; "pos": position only
+    interior: str = "elevate"  # interior control points for degree > 2*gamma-1: "elevate" or "minsnap"
 
     @property
     def n(self) -> int:

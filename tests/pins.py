@@ -153,12 +153,73 @@ def pin_cost_rows(gamma, p, T, D, C, rng, trials=6, samples=65):
     return worst
 
 
-def all_table_pins(gamma, p, T, tb, seed=0):
+def energy(P: np.ndarray, T: float, k: int) -> float:
+    """int_0^T |b^(k)(t)|^2 dt by Gauss-Legendre quadrature, exact for the
+    polynomial degree of the integrand (numpy's derivative of the power form)."""
+    deg = len(P) - 1
+    npts = max(1, deg - k + 1)
+    x, w = np.polynomial.legendre.leggauss(npts)
+    u = 0.5 * (x + 1.0)
+    v = t_derivative_at(P, T, k, u)
+    return float(0.5 * T * np.sum(w * v * v))
+
+
+def pin_minsnap_optimal(gamma, p, T, D, rng, trials=6):
+    """Minimum-energy interior points: every interior control point is at a
+    stationary point of int |b^(g+1)|^2 (central difference of the energy is
+    zero to first order, curvature positive), and the energy is at most that
+    of the elevated minimal-degree curve with the same end conditions."""
+    worst = 0.0
+    k = gamma + 1
+    for _ in range(trials):
+        xi = _rand_xi(rng, gamma, 3.0)
+        P = D @ xi
+        J0 = energy(P, T, k)
+        scale = max(J0, 1e-300)
+        for l in range(gamma, p - gamma + 1):
+            h = 1e-3 * (1.0 + abs(P[l]))
+            Pp, Pm = P.copy(), P.copy()
+            Pp[l] += h
+            Pm[l] -= h
+            Jp, Jm = energy(Pp, T, k), energy(Pm, T, k)
+            curv = Jp + Jm - 2 * J0
+            assert curv > 0
+            worst = max(worst, abs(Jp - Jm) / curv)   # 0 at the minimiser (J is exactly quadratic)
+        if gamma in (2, 3):
+            ref = elevate(textbook_hermite(gamma, T, xi), p - (2 * gamma - 1))
+            worst = max(worst, max(0.0, J0 - energy(ref, T, k)) / scale)
+    return worst
+
+
+def pin_minsnap_natural(gamma, p, T, D, rng, trials=6):
+    """At p = 2g+1 the minimiser has b^(g+1) = 0 at both ends (the natural
+    boundary conditions of the variational problem; for g = 1 this makes the
+    cubic a straight line: P_l = xL + l (xR - xL) / 3)."""
+    worst = 0.0
+    if p != 2 * gamma + 1:
+        return worst
+    for _ in range(trials):
+        xi = _rand_xi(rng, gamma, 3.0)
+        P = D @ xi
+        ends = t_derivative_at(P, T, gamma + 1, np.array([0.0, 1.0]))
+        mid = t_derivative_at(P, T, gamma + 1, np.linspace(0.0, 1.0, 9))
+        worst = max(worst, float(np.max(np.abs(ends))) / max(1.0, float(np.max(np.abs(mid)))))
+        if gamma == 1:
+            line = xi[0] + np.arange(p + 1) / p * (xi[1] - xi[0])
+            worst = max(worst, _rel(P, line))
+    return worst
+
+
+def all_table_pins(gamma, p, T, tb, seed=0, interior="elevate"):
     rng = np.random.default_rng(seed)
     res = {"endpoints": pin_endpoints(gamma, p, T, tb["D"], rng),
            "hodograph": pin_hodograph(gamma, p, T, tb["D"], tb["H"], rng),
-           "cost_rows": pin_cost_rows(gamma, p, T, tb["D"], tb["C"], rng),
-           "elevation": pin_elevation(gamma, p, T, tb["D"], rng)}
+           "cost_rows": pin_cost_rows(gamma, p, T, tb["D"], tb["C"], rng)}
+    if interior == "minsnap" and p > 2 * gamma - 1:
+        res["minsnap_optimal"] = pin_minsnap_optimal(gamma, p, T, tb["D"], rng)
+        res["minsnap_natural"] = pin_minsnap_natural(gamma, p, T, tb["D"], rng)
+    else:
+        res["elevation"] = pin_elevation(gamma, p, T, tb["D"], rng)
     if p == 2 * gamma - 1:
         res["minimal"] = pin_minimal_degree(gamma, T, tb["D"], rng)
     return res

@@ -143,6 +143,41 @@ def test_states_in_many_polytopes():
     check_full(prob, "f32", input="f64")
 
 
+@pytest.mark.parametrize("arith", ["f64", "f32"])
+def test_minsnap_interior_points(arith):
+    """Interior control points of minimal (gamma+1)-th-derivative energy
+    (model flag interior = minsnap): the whole path against the oracle built
+    on its own, independently derived minimum-energy tables."""
+    prob = synth.double_integrator_2d(12, N=300, K=6)
+    prob.model.interior = "minsnap"
+    st, info, _ = check_full(prob, arith, input="f64")
+    assert st["edges"] > 100
+    prob3 = synth.triple_integrator_3d(12, N=500, K=5, nT=6)
+    prob3.model.interior = "minsnap"
+    st3, _, _ = check_full(prob3, arith, input="f32" if arith == "f32" else "f64")
+    assert st3["edges"] > 50
+    # a different curve: the edge set differs from the elevated reading's
+    prob_e = synth.double_integrator_2d(12, N=300, K=6)
+    e_csr = oracle.OracleProblem(prob_e).csr()
+    m_csr = oracle.OracleProblem(prob).csr()
+    assert not (np.array_equal(e_csr["row_off"], m_csr["row_off"]) and np.array_equal(e_csr["col"], m_csr["col"]))
+
+
+@pytest.mark.parametrize("arith,input", [("f32", "f64"), ("f32", "f32")])
+def test_near_duplicate_states_cost_accuracy(arith, input):
+    """Pairs of nearly equal states: their FP32 cost halves cancel, so the
+    FP32 cost is re-done in FP64 (cost conditioning test) and the weights
+    still meet the 1e-5 bar."""
+    prob = synth.double_integrator_2d(21, N=260, K=5)
+    rng = np.random.default_rng(21)
+    for i in range(0, 120, 2):  # state i+1 = state i moved by ~1e-3
+        prob.states[i + 1] = prob.states[i] + rng.normal(0, 1e-3, prob.states.shape[1])
+    if input == "f32":
+        prob.states = prob.states.astype(np.float32).astype(np.float64)
+    st, info, _ = check_full(prob, arith, input=input)
+    assert st["max_rel_w"] <= 1e-5 and info["rechecks"] > 0
+
+
 def test_nT_extremes():
     p1 = synth.double_integrator_2d(4, N=200, K=4, nT=1)
     check_full(p1, "f64")

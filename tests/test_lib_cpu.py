@@ -35,13 +35,16 @@ def test_library_exports_every_declared_symbol():
     assert b"sm_103a" in lib.plan_version()
 
 
-@pytest.mark.parametrize("gamma,p", [(2, 3), (2, 5), (3, 5), (3, 7), (1, 3), (4, 9)])
-def test_tables_bitwise_equal_to_oracle(gamma, p):
+@pytest.mark.parametrize("gamma,p,interior", [(2, 3, "elevate"), (2, 5, "elevate"), (3, 5, "elevate"),
+                                               (3, 7, "elevate"), (1, 3, "elevate"), (4, 9, "elevate"),
+                                               (2, 5, "minsnap"), (3, 7, "minsnap"), (1, 3, "minsnap"),
+                                               (2, 7, "minsnap"), (3, 9, "minsnap")])
+def test_tables_bitwise_equal_to_oracle(gamma, p, interior):
     rng = np.random.default_rng(gamma * 31 + p)
     Ts = np.concatenate([[0.1, 0.2, 0.5, 1.0, 2.0, 3.0, 1e-3, 37.5], np.exp(rng.uniform(np.log(0.05), np.log(5.0), 24))])
     Ts = np.concatenate([Ts, Ts.astype(np.float32).astype(np.float64)])
-    lib = P.model_tables(gamma, p, Ts)
-    orc = OT.tables(gamma, p, Ts)
+    lib = P.model_tables(gamma, p, Ts, interior=interior)
+    orc = OT.tables(gamma, p, Ts, interior)
     for key in ("D", "H", "C"):
         a, b = lib[key], orc[key]
         assert a.shape == b.shape, key
@@ -61,6 +64,12 @@ def test_model_tables_rejects_bad_input():
     bad = P._model(1, 3, 4, [1.0] * 3)   # degree below 2*gamma-1
     T = np.array([1.0])
     assert lib.plan_model_tables(ctypes.byref(bad), 1, dp(T), dp(z), dp(z), dp(z)) == P.PLAN_ERR_INVALID_ARG
+    big = P._model(1, 2, 11, [1.0] * 2, interior="minsnap")   # beyond the exact minimum-energy solve
+    zz = np.zeros(4096)
+    assert lib.plan_model_tables(ctypes.byref(big), 1, dp(T), dp(zz), dp(zz), dp(zz)) == P.PLAN_ERR_INVALID_ARG
+    odd = P._model(1, 2, 5, [1.0] * 2)
+    odd.interior = 7
+    assert lib.plan_model_tables(ctypes.byref(odd), 1, dp(T), dp(zz), dp(zz), dp(zz)) == P.PLAN_ERR_INVALID_ARG
 
 
 def test_status_strings():

@@ -27,6 +27,45 @@ def test_table_pins(gamma, p, T):
         assert worst < 1e-9, (name, worst)
 
 
+MINSNAP_CASES = [(1, 3), (2, 5), (3, 7), (2, 7)]
+
+
+@pytest.mark.parametrize("gamma,p", MINSNAP_CASES)
+@pytest.mark.parametrize("T", DURATIONS)
+def test_minsnap_table_pins(gamma, p, T):
+    """Minimum-energy interior points: end conditions, hodograph and cost
+    identities as for the elevated curve, plus stationarity of the energy in
+    every interior point, energy <= the elevated curve's, and the natural
+    boundary conditions b^(g+1)(0) = b^(g+1)(T) = 0 at p = 2g+1."""
+    tb = {k: v[0] for k, v in T_.tables(gamma, p, [T], "minsnap").items()}
+    res = pins.all_table_pins(gamma, p, T, tb, seed=gamma * 100 + p + 7, interior="minsnap")
+    assert "minsnap_optimal" in res
+    for name, worst in res.items():
+        assert worst < 1e-6, (name, worst)
+
+
+def test_minsnap_equals_elevate_at_minimal_degree():
+    for gamma, p in [(2, 3), (3, 5)]:
+        a = T_.tables(gamma, p, [0.7], "minsnap")
+        b = T_.tables(gamma, p, [0.7], "elevate")
+        assert all(np.array_equal(a[k], b[k]) for k in "DHC")
+
+
+def test_minsnap_pins_catch_planted_mistakes():
+    """A perturbed interior row (a plausible slip in the normal equations) is
+    caught by the stationarity pin; an elevated-curve table passed off as the
+    minimiser is caught too."""
+    gamma, p, T = 2, 5, 0.8
+    good = {k: v[0] for k, v in T_.tables(gamma, p, [T], "minsnap").items()}
+    bad = {k: v.copy() for k, v in good.items()}
+    bad["D"][2, 0] *= 1.001
+    res = pins.all_table_pins(gamma, p, T, bad, seed=3, interior="minsnap")
+    assert res["minsnap_optimal"] > 1e-4
+    elev = {k: v[0] for k, v in T_.tables(gamma, p, [T], "elevate").items()}
+    res = pins.all_table_pins(gamma, p, T, elev, seed=3, interior="minsnap")
+    assert max(res["minsnap_optimal"], res["minsnap_natural"]) > 1e-4
+
+
 def test_shapes():
     tb = T_.tables(3, 7, [0.5, 1.0])
     assert tb["D"].shape == (2, 8, 6)
