@@ -232,6 +232,49 @@ def make_problem(name: str, seed: int, model: Model, N: int, K: int, T: np.ndarr
                    start_pos=_round(sg[0], dtype), goal_pos=_round(sg[1], dtype), domain=domain)
 
 
+@dataclass
+class Obstacles:
+    """Convex obstacle polytopes {z : A z <= b} in position space (CSR rows)."""
+    off: np.ndarray                 # int32 [n+1]
+    A: np.ndarray                   # float64 [R][m]
+    b: np.ndarray                   # float64 [R]
+
+    @property
+    def n(self) -> int:
+        return int(self.off.shape[0] - 1)
+
+
+def obstacles(seed: int, n: int, m: int, domain=(0.0, 20.0), side=(0.3, 1.2), max_cuts: int = 3,
+              dtype: str = "f64") -> Obstacles:
+    """n random convex obstacles: axis boxes (centre U(domain), side U(side))
+    cut by 0..max_cuts random planes, as for the free polytopes."""
+    off, A, b, _ = _polytopes(SplitMix64(seed, 4), m, n, domain, side, max_cuts, dtype)
+    return Obstacles(off, A, b)
+
+
+def keepout_2d(seed: int = 1, N: int = 5000, n_obst: int = 500, T: float = 0.5, width: float = 5.0,
+               dtype: str = "f64"):
+    """The keep-out setting of the paper's experiments: 2-D double integrator
+    (|v| <= 2, |a| <= 4, degree 5), one free box [0, width]^2, N states with
+    uniform positions and velocities U[-1, 1], curves of one duration T (the
+    defaults give about 5000 nodes and 46,000 edges, the scale of the paper's
+    maze and random-obstacle runs), and n_obst random convex obstacles with
+    sides U[0.01, 0.04] * width.  Returns (problem, obstacles)."""
+    model = Model(2, 2, 5, (2.0, 4.0))
+    rng = SplitMix64(seed, 2)
+    states = np.zeros((N, 4))
+    states[:, :2] = rng.uniform(N * 2, 0.0, width).reshape(N, 2)
+    states[:, 2:] = rng.uniform(N * 2, -1.0, 1.0).reshape(N, 2)
+    A = np.array([[1.0, 0.0], [-1.0, 0.0], [0.0, 1.0], [0.0, -1.0]])
+    b = np.array([width, 0.0, width, 0.0])
+    rq = SplitMix64(seed, 3)
+    sg = rq.uniform(4, 0.05 * width, 0.95 * width).reshape(2, 2)
+    prob = Problem(name="keepout_2d", seed=seed, model=model, dtype=dtype, states=_round(states, dtype),
+                   T=_round(np.array([T], dtype=np.float64), dtype), poly_off=np.array([0, 4], dtype=np.int32),
+                   A=A, b=b, start_pos=_round(sg[0], dtype), goal_pos=_round(sg[1], dtype), domain=(0.0, width))
+    return prob, obstacles(seed, n_obst, 2, (0.0, width), (0.01 * width, 0.04 * width), 3, dtype)
+
+
 def double_integrator_2d(seed: int = 1, N: int = 512, K: int = 16, nT: int = 8,
                          degree: int = 5, dtype: str = "f64") -> Problem:
     """2-D double integrator, |v| <= 2, |a| <= 4, domain [0,10]^2, 4-8 rows per polytope."""
