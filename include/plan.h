@@ -131,6 +131,12 @@ typedef struct {
     /* (pair, T) that the FP32 reach screen passed on to the full rows (the
      * screened pair kernel only; 0 otherwise) */
     int64_t screened;
+    /* keep-out cut (plan_cut_edges): (edge, T) checked; (edge, T, obstacle)
+     * evaluated; of those, missed by the bounding-box screen, hit by a control
+     * point inside and missed by one separating facet (FP32, decided within
+     * error bands); entries of the FP32 matrix-game pass and of the FP64 pass;
+     * FP64 games that no certificate decided (|delta*| at rounding level) */
+    int64_t cut_units, cut_tests, cut_box, cut_step1, cut_step2, cut_lp, cut_lp64, cut_ties;
 } plan_info;
 
 /* Create a context bound to the current CUDA device and the given stream
@@ -238,6 +244,57 @@ int plan_search(plan_ctx* ctx, int N, const void* states, const plan_edges* edge
  * the kernel stops and plan_wait returns PLAN_ERR_TIMEOUT; the context stays
  * usable. */
 int plan_set_search_limits(plan_ctx* ctx, int max_sweeps, int64_t spin_limit);
+
+/* Convex obstacles in position space for the keep-out cut (Assumption 1):
+ * obstacle o = {z in R^m : A_r z <= b_r, r = off[o] .. off[o+1]-1}. */
+typedef struct {
+    int n;                 /* number of obstacles, 0 .. 1<<20 */
+    const int32_t* off;    /* device int32 [n+1], off[0] = 0, non-decreasing */
+    int max_rows;          /* host bound on the rows of any obstacle, 1..16 */
+    const void* A;         /* device [R][m], the model's input type (may be NULL when R = 0) */
+    const void* b;         /* device [R], the model's input type (may be NULL when R = 0) */
+} plan_obstacles;
+
+/*
+ * cutGraph (Alg. 1 line 3, Sec. III-B, Algorithm 2 cutHeuristic, Cut-QP):
+ * remove from a built graph every (edge, duration) whose curve may meet an
+ * obstacle.  By Property 1 a curve is collision-free when the convex hull of
+ * its control points P_0..P_p misses the obstacle; with the margins
+ * G[l][r] = A_r . P_l - b_r the hull meets obstacle O iff
+ *     delta* = min over lambda in the simplex of max_r (G^T lambda)_r <= 0,
+ * the feasibility question that the Cut-QP's slack answers (touching counts as
+ * meeting).  The control points are those of the edge build (Lemma 1, the
+ * model's interior reading); the margins are defined in the canonical FP64
+ * order (each half summed left to right, halves added, facet products summed
+ * left to right, then b subtracted).  Algorithm 2's checks (a control point
+ * with every margin <= 0: hit; a facet with every margin > 0: miss) and a
+ * bounding-box screen decide most (edge, obstacle) pairs in FP32 within
+ * proven error bands; the rest go through the matrix game solved in FP32, then
+ * FP64, each answer accepted only with a weak-duality certificate.  A game that
+ * no FP64 certificate decides (|delta*| at the FP64 rounding level) is decided
+ * by the sign of its computed value and counted in plan_info.cut_ties.
+ * The obstacles are taken as given (no tightening: inflate b to add a margin).
+ *
+ *   N, states  the states the graph was built on (device [N][n])
+ *   nT, T      host [nT]: the durations the graph was built with (bit t of an
+ *              edge mask refers to T[t])
+ *   in         device CSR from plan_build_edges (read only; its count must be
+ *              <= in->cap, else device status INVALID_ARG)
+ *   obst       obstacles (see plan_obstacles); an obstacle with 0 rows is the
+ *              whole space and cuts every edge
+ *   out        caller-owned device CSR, no array shared with in: the edges with
+ *              at least one duration left, sorted as in; mask = in.mask with the
+ *              colliding durations cleared; w, tidx = the cheapest remaining
+ *              duration (copied when in's best duration survives, else re-costed
+ *              in canonical FP64, ties to the lower index); out->cap >= in's
+ *              count always suffices
+ * Errors: INVALID_ARG / UNSUPPORTED on the host; on the device (plan_wait):
+ * CAPACITY with detail OUTPUT when out->cap is too small (count written), or
+ * when the context's game lists were too small (they grow at plan_wait: repeat
+ * the call); UNSUPPORTED if an obstacle has more than max_rows rows.
+ */
+int plan_cut_edges(plan_ctx* ctx, int N, const void* states, int nT, const double* T, const plan_edges* in,
+                   const plan_obstacles* obst, const plan_edges* out);
 
 /* Weights of the refinement objective (defaults 1, 1, 0.1). */
 typedef struct {

@@ -38,31 +38,28 @@ import numpy as np
 
 
 def control_points(D: np.ndarray, g: int, m: int, xi: np.ndarray, xj: np.ndarray) -> np.ndarray:
-    """Position control points [p+1][m] in the canonical FP64 order."""
-    p1 = D.shape[0]
-    P = np.zeros((p1, m))
-    for l in range(p1):
-        for a in range(m):
-            sl = 0.0
-            for c in range(g):
-                sl = sl + D[l][c] * xi[c * m + a]
-            sr = 0.0
-            for c in range(g):
-                sr = sr + D[l][g + c] * xj[c * m + a]
-            P[l, a] = sl + sr
-    return P
+    """Position control points [p+1][m] in the canonical FP64 order: for every
+    (l, a) at once, each half accumulated over c = 0..g-1 from 0.0 (numpy
+    rounds every product and sum on its own), then the halves added."""
+    xi = np.asarray(xi, dtype=np.float64).reshape(g, m)
+    xj = np.asarray(xj, dtype=np.float64).reshape(g, m)
+    sl = np.zeros((D.shape[0], m))
+    sr = np.zeros((D.shape[0], m))
+    for c in range(g):
+        sl = sl + D[:, c:c + 1] * xi[c][None, :]
+    for c in range(g):
+        sr = sr + D[:, g + c:g + c + 1] * xj[c][None, :]
+    return sl + sr
 
 
 def margins(P: np.ndarray, A: np.ndarray, b: np.ndarray) -> np.ndarray:
-    """G[l][r] = A_r . P_l - b_r, axes summed left to right, then b subtracted."""
-    G = np.zeros((P.shape[0], A.shape[0]))
-    for l in range(P.shape[0]):
-        for r in range(A.shape[0]):
-            s = 0.0
-            for a in range(P.shape[1]):
-                s = s + A[r, a] * P[l, a]
-            G[l, r] = s - b[r]
-    return G
+    """G[l][r] = A_r . P_l - b_r: for every (l, r) at once, the products over
+    the axes a = 0..m-1 accumulated from 0.0, then b subtracted."""
+    A = np.asarray(A, dtype=np.float64).reshape(-1, P.shape[1])
+    s = np.zeros((P.shape[0], A.shape[0]))
+    for a in range(P.shape[1]):
+        s = s + P[:, a:a + 1] * A[None, :, a]
+    return s - np.asarray(b, dtype=np.float64)[None, :]
 
 
 def game_value(G: np.ndarray) -> Tuple[Fraction, List[Fraction], List[Fraction]]:
@@ -124,23 +121,44 @@ def obstacle_hit(G: np.ndarray) -> Tuple[bool, int, Optional[Fraction]]:
     return v <= 0, 3, v
 
 
-def cut(op, csr_detail: dict, obst_off, A_o, b_o) -> dict:
+def edge_decisions(G: np.ndarray, off: np.ndarray):
+    """Algorithm 2 for one curve against every obstacle, in obstacle order,
+    stopping at the first hit.  G holds the margins of all obstacles' rows
+    side by side (obstacle o: columns off[o]..off[o+1]-1).  Returns (hit,
+    per-step counts, exact delta* of every matrix game solved)."""
+    steps = {1: 0, 2: 0, 3: 0}
+    deltas = []
+    for o in range(len(off) - 1):
+        hit, st, v = obstacle_hit(G[:, off[o]:off[o + 1]])
+        steps[st] += 1
+        if v is not None:
+            deltas.append(v)
+        if hit:
+            return True, steps, deltas
+    return False, steps, deltas
+
+
+def cut(op, csr_detail: dict, obst_off, A_o, b_o, rows=None) -> dict:
     """Cut of an oracle graph (OracleProblem.csr(with_detail=True)) against
-    obstacles given as CSR polytopes.  Returns the new CSR and per-step counts."""
-    g, m, p = op.gamma, op.m, op.p
-    n = op.n
+    obstacles given as CSR polytopes, for the edges of the given rows (all by
+    default).  Returns the new CSR (row offsets only when every row is cut),
+    the kept edges' start vertices and per-duration costs (for comparisons),
+    the per-step counts and the exact delta* of every game."""
+    g, m = op.gamma, op.m
     X = op.states
     off = np.asarray(obst_off, dtype=np.int64)
     A_o = np.asarray(A_o, dtype=np.float64).reshape(-1, m)
     b_o = np.asarray(b_o, dtype=np.float64)
     e = csr_detail["all"]
     keep = e["mask"] != 0
+    if rows is not None:
+        keep &= np.isin(e["i"], np.asarray(rows))
     I, J, Mk, C = e["i"][keep], e["j"][keep], e["mask"][keep], e["costs"][keep]
     order = np.lexsort((J, I))
     I, J, Mk, C = I[order], J[order], Mk[order], C[order]
     steps = {1: 0, 2: 0, 3: 0}
     deltas = []
-    rows_col, rows_w, rows_t, rows_m, rows_i = [], [], [], [], []
+    out = {"i": [], "j": [], "w": [], "t": [], "mask": [], "costs": []}
     for idx in range(len(I)):
         i, j, mask = int(I[idx]), int(J[idx]), int(Mk[idx])
         newmask = 0
@@ -148,29 +166,28 @@ def cut(op, csr_detail: dict, obst_off, A_o, b_o) -> dict:
             if not (mask >> t) & 1:
                 continue
             P = control_points(op.D[t], g, m, X[i], X[j])
-            ok = True
-            for o in range(len(off) - 1):
-                G = margins(P, A_o[off[o]:off[o + 1]], b_o[off[o]:off[o + 1]])
-                hit, st, v = obstacle_hit(G)
-                steps[st] += 1
-                if v is not None:
-                    deltas.append(float(v))
-                if hit:
-                    ok = False
-                    break
-            if ok:
+            hit, st, dl = edge_decisions(margins(P, A_o, b_o), off)
+            for k in steps:
+                steps[k] += st[k]
+            deltas += dl
+            if not hit:
                 newmask |= 1 << t
         if newmask:
             costs = C[idx]
             best = min((t for t in range(op.nT) if (newmask >> t) & 1), key=lambda t: (costs[t], t))
-            rows_i.append(i)
-            rows_col.append(j)
-            rows_m.append(newmask)
-            rows_w.append(costs[best])
-            rows_t.append(best)
+            out["i"].append(i)
+            out["j"].append(j)
+            out["mask"].append(newmask)
+            out["w"].append(costs[best])
+            out["t"].append(best)
+            out["costs"].append(costs)
     N = op.N
-    cnt = np.bincount(np.asarray(rows_i, dtype=np.int64), minlength=N)
-    row_off = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int32)
-    return {"row_off": row_off, "col": np.asarray(rows_col, dtype=np.int32), "w": np.asarray(rows_w),
-            "t": np.asarray(rows_t, dtype=np.uint8), "mask": np.asarray(rows_m, dtype=np.uint32),
-            "steps": steps, "deltas": np.asarray(deltas)}
+    res = {"i": np.asarray(out["i"], dtype=np.int64), "j": np.asarray(out["j"], dtype=np.int32),
+           "col": np.asarray(out["j"], dtype=np.int32), "w": np.asarray(out["w"], dtype=np.float64),
+           "t": np.asarray(out["t"], dtype=np.int32), "mask": np.asarray(out["mask"], dtype=np.uint32),
+           "costs": np.asarray(out["costs"], dtype=np.float64).reshape(-1, op.nT),
+           "steps": steps, "deltas": np.asarray([float(d) for d in deltas])}
+    if rows is None:
+        cnt = np.bincount(res["i"], minlength=N)
+        res["row_off"] = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
+    return res

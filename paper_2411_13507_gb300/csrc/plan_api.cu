@@ -101,6 +101,25 @@ struct plan_ctx {
     long long capLast = -1;
     unsigned long long* slast = nullptr;
     unsigned long long* snear = nullptr;   // [4][SEARCH_MAX_BLOCKS]
+    // keep-out cut
+    std::vector<double> cutT;
+    int cut_nT_cap = 0;
+    double* d_cut64 = nullptr;
+    float* d_cut32 = nullptr;
+    double* h_cut64 = nullptr;
+    float* h_cut32 = nullptr;
+    cudaEvent_t cut_ev = nullptr;
+    bool cut_ev_live = false;
+    long long capCutE = -1, capCutO = -1, capCutR = -1;
+    int32_t* cut_src = nullptr;
+    uint32_t* cut_hit = nullptr;
+    int32_t* cut_pos = nullptr;
+    long long* cut_chunk = nullptr;
+    float* cut_orow = nullptr;
+    int* cut_ocount = nullptr;
+    long long cut32Cap = 0, cut64Cap = 0, want_cut32 = 0, want_cut64 = 0;
+    unsigned long long* cut_list32 = nullptr;
+    unsigned long long* cut_list64 = nullptr;
     // timing
     bool timing = false;
     bool accounting = false;
@@ -351,6 +370,7 @@ int plan_create(plan_ctx** out, const plan_model* model, void* cuda_stream) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->tab_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->sstage_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->cut_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();
         plan_destroy(c);
@@ -367,12 +387,17 @@ void plan_destroy(plan_ctx* c) {
     void* dev[] = {c->d_tab64, c->d_tab32, c->d_info, c->memMask, c->counts, c->members, c->localIdx, c->segKL, c->centers,
                    c->blim64, c->A32, c->blim32, c->bc32, c->resOff, c->itemOff, c->ntile, c->tsize, c->rowCount,
                    c->resBits, c->resKey, c->emitPre, c->recheck, c->sdist, c->sbest, c->spred, c->sfront, c->slast, c->snear,
-                   c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem, c->d_qMem, c->d_sqd, c->memOff};
+                   c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem, c->d_qMem, c->d_sqd, c->memOff,
+                   c->d_cut64, c->d_cut32, c->cut_src, c->cut_hit, c->cut_pos, c->cut_chunk, c->cut_orow,
+                   c->cut_ocount, c->cut_list32, c->cut_list64};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_tab64) cudaFreeHost(c->h_tab64);
     if (c->h_tab32) cudaFreeHost(c->h_tab32);
     if (c->h_info) cudaFreeHost(c->h_info);
+    if (c->h_cut64) cudaFreeHost(c->h_cut64);
+    if (c->h_cut32) cudaFreeHost(c->h_cut32);
+    if (c->cut_ev) cudaEventDestroy(c->cut_ev);
     if (c->h_stage) cudaFreeHost(c->h_stage);
     if (c->stage_ev) cudaEventDestroy(c->stage_ev);
     if (c->h_sstage) cudaFreeHost(c->h_sstage);
@@ -796,6 +821,177 @@ int plan_search(plan_ctx* c, int N, const void* states, const plan_edges* edges,
     return PLAN_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// FP64 canonical tables (control points, cost rows; the edge build's layout)
+// and the FP32 control-point table of the cut's durations, uploaded once per
+// distinct duration list.
+int upload_cut_tables(plan_ctx* c, int nT, const double* T) {
+    std::vector<double> Tv(T, T + nT);
+    if (Tv == c->cutT) return PLAN_OK;
+    const TabLayout& L = c->L;
+    const int g = c->model.gamma, p = c->model.degree, tg = L.tg;
+    const int f_stride = (p + 1) * tg;
+    if (c->cut_ev_live) cudaEventSynchronize(c->cut_ev);
+    if (nT > c->cut_nT_cap) {
+        if (c->h_cut64) cudaFreeHost(c->h_cut64);
+        if (c->h_cut32) cudaFreeHost(c->h_cut32);
+        c->h_cut64 = nullptr;
+        c->h_cut32 = nullptr;
+        c->cut_nT_cap = 0;
+        if (!dalloc(c, &c->d_cut64, (long long)NT_MAX * L.e_stride) || !dalloc(c, &c->d_cut32, (long long)NT_MAX * f_stride))
+            return PLAN_ERR_NO_MEMORY;
+        if (cudaMallocHost((void**)&c->h_cut64, sizeof(double) * (size_t)NT_MAX * L.e_stride) != cudaSuccess ||
+            cudaMallocHost((void**)&c->h_cut32, sizeof(float) * (size_t)NT_MAX * f_stride) != cudaSuccess)
+            return fail(c, PLAN_ERR_NO_MEMORY, "cudaMallocHost cut tables");
+        c->cut_nT_cap = NT_MAX;
+    }
+    std::vector<double> D((size_t)nT * (p + 1) * tg), H((size_t)nT * L.rax * tg), C((size_t)nT * g * p * tg);
+    exact_tables(g, p, c->model.interior, nT, T, D.data(), H.data(), C.data());
+    for (int t = 0; t < nT; ++t) {
+        const double* Dt = D.data() + (size_t)t * (p + 1) * tg;
+        const double* Ht = H.data() + (size_t)t * L.rax * tg;
+        const double* Ct = C.data() + (size_t)t * g * p * tg;
+        double* e = c->h_cut64 + (size_t)t * L.e_stride;
+        float* f = c->h_cut32 + (size_t)t * f_stride;
+        for (int i = 0; i < L.rax * tg; ++i) e[L.e_H + i] = Ht[i];
+        for (int i = 0; i < (p + 1) * tg; ++i) e[L.e_D + i] = Dt[i];
+        for (int i = 0; i < g * p * tg; ++i) e[L.e_C + i] = Ct[i];
+        for (int i = 0; i < (p + 1) * tg; ++i) f[i] = (float)Dt[i];
+    }
+    cudaError_t e1 = cudaMemcpyAsync(c->d_cut64, c->h_cut64, sizeof(double) * (size_t)nT * L.e_stride,
+                                     cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e2 = cudaMemcpyAsync(c->d_cut32, c->h_cut32, sizeof(float) * (size_t)nT * f_stride,
+                                     cudaMemcpyHostToDevice, c->stream);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return cuda_fail(c, e1 != cudaSuccess ? e1 : e2, "cut table upload");
+    cudaEventRecord(c->cut_ev, c->stream);
+    c->cut_ev_live = true;
+    c->cutT = Tv;
+    return PLAN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int plan_cut_edges(plan_ctx* c, int N, const void* states, int nT, const double* T, const plan_edges* in,
+                   const plan_obstacles* obst, const plan_edges* out) {
+    if (!c) return PLAN_ERR_INVALID_ARG;
+    if (!model_supported(c->model.m, c->model.gamma, c->model.degree) || c->model.m < 2 || c->model.m > 3)
+        return fail(c, PLAN_ERR_UNSUPPORTED, "keep-out cut not compiled for this (m, gamma, p)");
+    if (N < 0 || N > (1 << 20) || (N > 0 && !states)) return fail(c, PLAN_ERR_INVALID_ARG, "N out of range");
+    if (nT < 1 || nT > NT_MAX || !T) return fail(c, PLAN_ERR_INVALID_ARG, "nT must be 1..32 with a host T array");
+    for (int t = 0; t < nT; ++t)
+        if (!std::isfinite(T[t]) || !(T[t] > 0)) return fail(c, PLAN_ERR_INVALID_ARG, "durations must be finite and > 0");
+    if (!in || !in->row_off || !in->count || in->cap < 0 ||
+        (in->cap > 0 && (!in->col || !in->w || !in->tidx || !in->mask)))
+        return fail(c, PLAN_ERR_INVALID_ARG, "bad input CSR");
+    if (!out || !out->row_off || !out->count || out->cap < 0 ||
+        (out->cap > 0 && (!out->col || !out->w || !out->tidx || !out->mask)))
+        return fail(c, PLAN_ERR_INVALID_ARG, "bad output CSR");
+    if (out->row_off == in->row_off || (out->cap > 0 && in->cap > 0 && (out->col == in->col || out->w == in->w ||
+                                                                         out->tidx == in->tidx || out->mask == in->mask)))
+        return fail(c, PLAN_ERR_INVALID_ARG, "input and output CSR must not share arrays");
+    if (in->cap > (1LL << 31) - 2) return fail(c, PLAN_ERR_INVALID_ARG, "input CSR capacity above 2^31 - 2");
+    // A and b may be null when no obstacle has rows (the device checks it per obstacle)
+    if (!obst || obst->n < 0 || obst->n > (1 << 20) || (obst->n > 0 && !obst->off))
+        return fail(c, PLAN_ERR_INVALID_ARG, "bad obstacles");
+    if (obst->n > 0 && (obst->max_rows < 1 || obst->max_rows > CUT_RMAX))
+        return fail(c, PLAN_ERR_INVALID_ARG, "obstacle max_rows must be 1..16");
+    int rc = upload_cut_tables(c, nT, T);
+    if (rc != PLAN_OK) return rc;
+    const long long capE = in->cap > 0 ? in->cap : 1;
+    const long long nchunks = (capE + CUT_CHUNK - 1) / CUT_CHUNK;
+    if (capE > c->capCutE) {
+        if (!dalloc(c, &c->cut_src, capE) || !dalloc(c, &c->cut_hit, capE) || !dalloc(c, &c->cut_pos, capE + 1) ||
+            !dalloc(c, &c->cut_chunk, nchunks + 1)) {
+            c->capCutE = -1;
+            return PLAN_ERR_NO_MEMORY;
+        }
+        c->capCutE = capE;
+    }
+    const int maxr = obst->n > 0 ? obst->max_rows : 1;
+    const long long nob = obst->n > 0 ? obst->n : 1;
+    if (nob > c->capCutO || nob * maxr > c->capCutR) {
+        if (!dalloc(c, &c->cut_ocount, nob) || !dalloc(c, &c->cut_orow, 4 * nob * maxr)) {
+            c->capCutO = c->capCutR = -1;
+            return PLAN_ERR_NO_MEMORY;
+        }
+        c->capCutO = nob;
+        c->capCutR = nob * maxr;
+    }
+    const long long w32 = c->want_cut32 > 0 ? c->want_cut32 : (1LL << 18);
+    const long long w64 = c->want_cut64 > 0 ? c->want_cut64 : (1LL << 14);
+    if (w32 > c->cut32Cap) {
+        if (!dalloc(c, &c->cut_list32, w32)) {
+            c->cut32Cap = 0;
+            return PLAN_ERR_NO_MEMORY;
+        }
+        c->cut32Cap = w32;
+    }
+    if (w64 > c->cut64Cap) {
+        if (!dalloc(c, &c->cut_list64, w64)) {
+            c->cut64Cap = 0;
+            return PLAN_ERR_NO_MEMORY;
+        }
+        c->cut64Cap = w64;
+    }
+    CutParams C;
+    memset(&C, 0, sizeof(C));
+    C.m = c->model.m;
+    C.g = c->model.gamma;
+    C.p = c->model.degree;
+    C.nT = nT;
+    C.in_f32 = c->model.input == PLAN_IN_F32;
+    C.w_f64 = c->model.arith == PLAN_F64;
+    C.cost_mode = c->model.cost_mode;
+    C.N = N;
+    C.n_obst = obst->n;
+    C.max_orows = maxr;
+    C.states = states;
+    C.row_in = in->row_off;
+    C.col_in = in->col;
+    C.w_in = in->w;
+    C.t_in = in->tidx;
+    C.mask_in = in->mask;
+    C.count_in = in->count;
+    C.cap_in = in->cap;
+    C.row_out = out->row_off;
+    C.col_out = out->col;
+    C.w_out = out->w;
+    C.t_out = out->tidx;
+    C.mask_out = out->mask;
+    C.count_out = out->count;
+    C.cap_out = out->cap;
+    C.obst_off = obst->off;
+    C.A = obst->A;
+    C.b = obst->b;
+    C.orow = c->cut_orow;
+    C.ocount = c->cut_ocount;
+    C.tab64 = c->d_cut64;
+    C.tab32 = c->d_cut32;
+    C.L = c->L;
+    C.src = c->cut_src;
+    C.hit = c->cut_hit;
+    C.list32 = c->cut_list32;
+    C.cap32 = c->cut32Cap;
+    C.list64 = c->cut_list64;
+    C.cap64 = c->cut64Cap;
+    C.chunk = c->cut_chunk;
+    C.pos = c->cut_pos;
+    C.nchunks = nchunks;
+    C.info = c->d_info;
+    cudaError_t e = cudaMemsetAsync(&c->d_info->cut_units, 0, 8 * sizeof(unsigned long long), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset cut counters");
+    int launches = 0;
+    int ce = launch_cut(C, c->stream, c->num_sms, &launches);
+    c->launches += launches;
+    if (ce != 0) return cuda_fail(c, (cudaError_t)ce, "cut launch");
+    return PLAN_OK;
+}
+
 int plan_prepare_search_batched(plan_ctx* c, int Q, const plan_search_query* qs) {
     if (!c) return PLAN_ERR_INVALID_ARG;
     if (Q < 1 || Q > 65535 || !qs) return fail(c, PLAN_ERR_INVALID_ARG, "need 1..65535 queries");
@@ -962,6 +1158,10 @@ int plan_wait(plan_ctx* c, plan_info* info) {
             long long need = (long long)(d.need_rechecks > d.rechecks ? d.need_rechecks : d.rechecks);
             c->want_rechecks = need + need / 4 + 1024;
         }
+        if (d.detail == DET_CUTLIST) {
+            c->want_cut32 = (long long)(d.cut_lp + d.cut_lp / 4 + 4096);
+            c->want_cut64 = (long long)(d.cut_lp64 + d.cut_lp64 / 4 + 1024);
+        }
     }
     if (info) {
         memset(info, 0, sizeof(*info));
@@ -984,6 +1184,14 @@ int plan_wait(plan_ctx* c, plan_info* info) {
         info->work_free_rows = (int64_t)d.work[1];
         info->work_costs = (int64_t)d.work[2];
         info->screened = (int64_t)d.screened;
+        info->cut_units = (int64_t)d.cut_units;
+        info->cut_tests = (int64_t)d.cut_tests;
+        info->cut_box = (int64_t)d.cut_box;
+        info->cut_step1 = (int64_t)d.cut_step1;
+        info->cut_step2 = (int64_t)d.cut_step2;
+        info->cut_lp = (int64_t)d.cut_lp;
+        info->cut_lp64 = (int64_t)d.cut_lp64;
+        info->cut_ties = (int64_t)d.cut_ties;
     }
     return d.status;
 }

@@ -74,6 +74,15 @@ struct DevInfo {
     unsigned long long bar[3];       // grid-barrier words, used in rotation: arrivals | raised flags << 32
     int path_len;
     unsigned long long work[3];
+    // keep-out cut counters
+    unsigned long long cut_units;    // (edge, T) checked
+    unsigned long long cut_tests;    // (edge, T, obstacle) evaluated
+    unsigned long long cut_box;      // missed by the bounding-box screen
+    unsigned long long cut_step1;    // hit: a control point inside (FP32, certain)
+    unsigned long long cut_step2;    // missed: one separating facet (FP32, certain)
+    unsigned long long cut_lp;       // entries of the FP32 matrix-game list
+    unsigned long long cut_lp64;     // entries of the FP64 list
+    unsigned long long cut_ties;     // FP64 games without a certificate either way
 };
 
 enum Detail {
@@ -86,7 +95,9 @@ enum Detail {
     DET_PATHCAP = 6,
     DET_BARRIER = 7,
     DET_SWEEPS = 8,
-    DET_WALK = 9
+    DET_WALK = 9,
+    DET_CUTLIST = 10,
+    DET_CUTIN = 11
 };
 
 // One query of a batch (device array; host-known offsets into the shared
@@ -237,6 +248,51 @@ struct RefineParams {
     float* dT;             // [S]
 };
 
+// Keep-out cut of a built edge graph (plan_cut.cu).
+constexpr int CUT_RMAX = 16;     // rows per obstacle
+constexpr int CUT_CHUNK = 2048;  // edges per compaction chunk
+
+struct CutParams {
+    int m, g, p, nT, in_f32, w_f64, cost_mode;
+    int N, n_obst, max_orows;
+    const void* states;
+    // input CSR (from the edge build) and its count on the device
+    const int32_t* row_in;
+    const int32_t* col_in;
+    const void* w_in;
+    const uint8_t* t_in;
+    const uint32_t* mask_in;
+    const int64_t* count_in;
+    long long cap_in;
+    // output CSR
+    int32_t* row_out;
+    int32_t* col_out;
+    void* w_out;
+    uint8_t* t_out;
+    uint32_t* mask_out;
+    int64_t* count_out;
+    long long cap_out;
+    // obstacles (caller arrays) and their FP32 copies, max_orows rows per obstacle
+    const int32_t* obst_off;
+    const void* A;
+    const void* b;
+    float* orow;               // [n_obst * max_orows][4] {A_0, A_1, A_2 (0 when m = 2), b}, 16-byte aligned
+    int* ocount;               // [n_obst] rows of each obstacle
+    const double* tab64;       // [nT][L.e_stride] canonical tables (control points, cost rows)
+    const float* tab32;        // [nT][(p+1) * 2g] FP32 control-point table
+    TabLayout L;
+    int32_t* src;              // [cap_in] start vertex of each edge
+    uint32_t* hit;             // [cap_in] durations whose curve meets an obstacle
+    unsigned long long* list32;
+    long long cap32;
+    unsigned long long* list64;
+    long long cap64;
+    long long* chunk;          // [nchunks + 1] kept edges per chunk, then their exclusive prefix
+    int32_t* pos;              // [cap_in + 1] output index of each edge (exclusive prefix of kept)
+    long long nchunks;
+    DevInfo* info;
+};
+
 // Launchers (plan_build.cu / plan_search.cu / plan_refine.cu); return cudaError_t as int.
 int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_sm, void* ev_pair_begin,
                  void* ev_pair_end, int* launches);
@@ -247,5 +303,6 @@ bool model_supported(int m, int g, int p);
 bool tc_supported(int m, int g, int p);
 bool refine_supported(int m, int g, int p);
 int launch_refine(const RefineParams& R, void* stream, int* launches);
+int launch_cut(const CutParams& C, void* stream, int num_sms, int* launches);
 
 }  // namespace plan

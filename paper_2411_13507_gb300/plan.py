@@ -22,6 +22,7 @@ ARITH = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3}
 INPUT = {"f64": 0, "f32": 1}
 COST = {"state": 0, "pos": 1}
 DET_SLOTS, DET_RECHECK, DET_OUTPUT = 1, 2, 3
+DET_CUTLIST = 10
 
 _lib = None
 
@@ -51,7 +52,14 @@ class _Info(ctypes.Structure):
                 ("edges", ctypes.c_int64), ("search_iters", ctypes.c_int64), ("start", ctypes.c_int32),
                 ("goal", ctypes.c_int32), ("need_slots", ctypes.c_int64), ("need_rechecks", ctypes.c_int64),
                 ("work_reach_rows", ctypes.c_int64), ("work_free_rows", ctypes.c_int64), ("work_costs", ctypes.c_int64),
-                ("screened", ctypes.c_int64)]
+                ("screened", ctypes.c_int64), ("cut_units", ctypes.c_int64), ("cut_tests", ctypes.c_int64),
+                ("cut_box", ctypes.c_int64), ("cut_step1", ctypes.c_int64), ("cut_step2", ctypes.c_int64),
+                ("cut_lp", ctypes.c_int64), ("cut_lp64", ctypes.c_int64), ("cut_ties", ctypes.c_int64)]
+
+
+class _Obstacles(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("off", ctypes.c_void_p), ("max_rows", ctypes.c_int), ("A", ctypes.c_void_p),
+                ("b", ctypes.c_void_p)]
 
 
 class _Query(ctypes.Structure):
@@ -74,7 +82,7 @@ class _RefineW(ctypes.Structure):
 EXPORTS = ["plan_create", "plan_destroy", "plan_build_edges", "plan_search", "plan_wait", "plan_model_tables",
            "plan_set_search_limits", "plan_refine", "plan_prepare_batched", "plan_build_edges_batched",
            "plan_set_tile", "plan_autotune", "plan_prepare_search_batched", "plan_search_batched",
-           "plan_search_noalloc", "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
+           "plan_search_noalloc", "plan_cut_edges", "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
 
 
 def lib_path() -> str:
@@ -117,6 +125,9 @@ def load(build_if_stale: bool = True):
     lib.plan_search_batched.restype = i32
     lib.plan_search_noalloc.argtypes = [i32, i32, i32, i32, i32, vp, ctypes.POINTER(_Edges), dp, dp, vp, i32, vp, vp, vp, vp]
     lib.plan_search_noalloc.restype = i32
+    lib.plan_cut_edges.argtypes = [vp, i32, vp, i32, dp, ctypes.POINTER(_Edges), ctypes.POINTER(_Obstacles),
+                                   ctypes.POINTER(_Edges)]
+    lib.plan_cut_edges.restype = i32
     lib.plan_set_tile.argtypes = [vp, i32, i32, i32, i32]
     lib.plan_set_tile.restype = i32
     lib.plan_autotune.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
@@ -234,6 +245,32 @@ class DeviceProblem:
     goal_pos: np.ndarray
 
 
+@dataclass
+class DeviceObstacles:
+    """Convex obstacles {z : A z <= b} resident on the GPU."""
+    n: int
+    max_rows: int
+    off: "torch.Tensor"
+    A: "torch.Tensor"
+    b: "torch.Tensor"
+
+    def cstruct(self) -> _Obstacles:
+        return _Obstacles(int(self.n), self.off.data_ptr(), int(self.max_rows), self.A.data_ptr(), self.b.data_ptr())
+
+
+def obstacles_to_device(obs, input: str = "f64", device=None) -> DeviceObstacles:
+    """Upload generated obstacles (synth.Obstacles) to torch device tensors."""
+    import torch
+    dt = torch.float32 if input == "f32" else torch.float64
+    dev = device or torch.device("cuda")
+    off = np.asarray(obs.off, dtype=np.int32)
+    n = off.shape[0] - 1
+    max_rows = int(np.max(np.diff(off))) if n > 0 else 1
+    return DeviceObstacles(n=n, max_rows=max(1, max_rows), off=torch.as_tensor(off).to(dev),
+                           A=torch.as_tensor(np.ascontiguousarray(obs.A), dtype=dt).reshape(-1).to(dev).contiguous(),
+                           b=torch.as_tensor(np.ascontiguousarray(obs.b), dtype=dt).to(dev).contiguous())
+
+
 def to_device(prob, input: str = "f64", device=None) -> DeviceProblem:
     """Upload a generated problem (numpy arrays) to torch device tensors."""
     import torch
@@ -339,6 +376,29 @@ class Planner:
                 continue
             raise self._err(st, "build_edges")
         raise self._err(PLAN_ERR_CAPACITY, "build_edges: capacity retries exhausted")
+
+    def cut_edges_async(self, dp: DeviceProblem, graph: Graph, obst: DeviceObstacles, out: Graph) -> None:
+        T = dp.T
+        rc = self.lib.plan_cut_edges(self.ctx, dp.N, ctypes.c_void_p(dp.states.data_ptr()), int(T.shape[0]),
+                                     T.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(graph.cstruct()),
+                                     ctypes.byref(obst.cstruct()), ctypes.byref(out.cstruct()))
+        if rc != 0:
+            raise self._err(rc, "plan_cut_edges")
+
+    def cut_edges(self, dp: DeviceProblem, graph: Graph, obst: DeviceObstacles, out: Optional[Graph] = None) -> Graph:
+        """Keep-out cut of a built graph: a new CSR without the (edge, T) whose
+        curves may meet an obstacle (repeats once the game lists have grown)."""
+        if out is None:
+            out = self.alloc_graph(dp.N, max(1, graph.cap))
+        for _ in range(6):
+            self.cut_edges_async(dp, graph, obst, out)
+            st = self.wait()
+            if st == PLAN_OK:
+                return out
+            if st == PLAN_ERR_CAPACITY and self.last_info.detail == DET_CUTLIST:
+                continue
+            raise self._err(st, "cut_edges")
+        raise self._err(PLAN_ERR_CAPACITY, "cut_edges: capacity retries exhausted")
 
     def search_async(self, dp: DeviceProblem, graph: Graph, start_pos, goal_pos, out: dict) -> None:
         sp = np.ascontiguousarray(np.asarray(start_pos, dtype=np.float64))

@@ -258,8 +258,9 @@ def keepout_2d(seed: int = 1, N: int = 5000, n_obst: int = 500, T: float = 0.5, 
     (|v| <= 2, |a| <= 4, degree 5), one free box [0, width]^2, N states with
     uniform positions and velocities U[-1, 1], curves of one duration T (the
     defaults give about 5000 nodes and 46,000 edges, the scale of the paper's
-    maze and random-obstacle runs), and n_obst random convex obstacles with
-    sides U[0.01, 0.04] * width.  Returns (problem, obstacles)."""
+    maze and random-obstacle runs), and n_obst random convex obstacles (boxes
+    with sides U[0.005, 0.02] * width cut by up to 3 planes; at the defaults
+    they remove about 40% of the edges).  Returns (problem, obstacles)."""
     model = Model(2, 2, 5, (2.0, 4.0))
     rng = SplitMix64(seed, 2)
     states = np.zeros((N, 4))
@@ -272,7 +273,7 @@ def keepout_2d(seed: int = 1, N: int = 5000, n_obst: int = 500, T: float = 0.5, 
     prob = Problem(name="keepout_2d", seed=seed, model=model, dtype=dtype, states=_round(states, dtype),
                    T=_round(np.array([T], dtype=np.float64), dtype), poly_off=np.array([0, 4], dtype=np.int32),
                    A=A, b=b, start_pos=_round(sg[0], dtype), goal_pos=_round(sg[1], dtype), domain=(0.0, width))
-    return prob, obstacles(seed, n_obst, 2, (0.0, width), (0.01 * width, 0.04 * width), 3, dtype)
+    return prob, obstacles(seed, n_obst, 2, (0.0, width), (0.005 * width, 0.02 * width), 3, dtype)
 
 
 def double_integrator_2d(seed: int = 1, N: int = 512, K: int = 16, nT: int = 8,

@@ -24,7 +24,7 @@ def declared_functions():
 
 def test_header_declares_expected_entry_points():
     names = declared_functions()
-    for req in ("plan_create", "plan_build_edges", "plan_search", "plan_wait", "plan_destroy"):
+    for req in ("plan_create", "plan_build_edges", "plan_cut_edges", "plan_search", "plan_wait", "plan_destroy"):
         assert req in names
 
 
