@@ -47,10 +47,11 @@ def parse():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=0, help="rows of the oracle sample (0: auto)")
-    ap.add_argument("--form", default="plain", choices=["plain", "fp64", "tf32", "bf16", "batched", "refine"],
+    ap.add_argument("--form", default="plain", choices=["plain", "fp64", "tf32", "bf16", "batched", "refine", "cut"],
                     help="plain: 3-D FP32 workload (the default line); fp64: 2-D FP64 plain method; tf32/bf16: "
                          "precision form on the 2-D workload; batched: 256 uneven queries in one graph replay; "
-                         "refine: 65536-segment forward+backward")
+                         "refine: 65536-segment forward+backward; cut: keep-out cut of a 5000-state graph "
+                         "against 500 obstacles, then the search")
     ap.add_argument("--queries", type=int, default=256)
     ap.add_argument("--pipeline", type=int, default=-1,
                     help="FP32 pair kernel of the plain line: 0 screened, 1 warp-specialised, 2 unscreened "
@@ -302,6 +303,8 @@ def run_form(args):
                                     "N_total": sum(p.N for p in probs), "checks": checks,
                                     "candidates": int(info["candidates"]),
                                     "edges": int(info["edges"]), "rechecks": int(info["rechecks"]), "autotune": tune}})
+        elif args.form == "cut":
+            line.update(run_cut_form(args, stream, flush, dev))
         elif args.form == "refine":
             from paper_2411_13507_gb300 import refine as RF
             rb = synth.refine_segments(seed=args.seed, S=65536)
@@ -322,6 +325,138 @@ def run_form(args):
                          "ms_per_step": statistics.mean(ms),
                          "config": {"workload": "refine_segments", "segments": S}})
     return line
+
+
+def cut_cpu_baseline(prob, obs, budget_s=12.0):
+    """The exact keep-out cut oracle as it stands, on a bounded sample of rows."""
+    import oracle
+    from oracle import cut as OC
+    op = oracle.OracleProblem(prob)
+    csr = op.csr(with_detail=True)
+    t0 = time.perf_counter()
+    rows, step, units = [], max(1, prob.N // 400), 0
+    order = np.arange(0, prob.N, step)
+    done = 0
+    while done < len(order) and time.perf_counter() - t0 < budget_s:
+        r = order[done:done + 8]
+        done += len(r)
+        OC.cut(op, csr, obs.off, obs.A, obs.b, rows=r)
+        rows.extend(r.tolist())
+    dt = time.perf_counter() - t0
+    e = csr["all"]
+    sel = (e["mask"] != 0) & np.isin(e["i"], np.asarray(rows))
+    units = int(sum(bin(int(x)).count("1") for x in e["mask"][sel]))
+    tests = units * obs.n
+    return {"value": tests / dt, "unit": "tests/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(rows)} of {prob.N} rows ({units} (edge, T) x {obs.n} obstacles, {dt:.1f} s, "
+                      "numpy margins + exact rational games, one thread)"}
+
+
+def run_cut_form(args, stream, flush, dev):
+    """Keep-out cut (Sec. III-B, Algorithm 2): 2-D double integrator, 5000
+    states, one duration, about 46,000 edges, 500 random convex obstacles."""
+    import torch
+    from paper_2411_13507_gb300 import plan as P
+    from paper_2411_13507_gb300 import synth
+    prob, obs = synth.keepout_2d(seed=1)
+    cpu = None if args.no_cpu_baseline else cut_cpu_baseline(prob, obs)
+    pl = P.Planner.for_problem(prob, arith="f64", input="f64", stream=stream)
+    dp = P.to_device(prob, input="f64")
+    g = pl.build_edges(dp)
+    E_in = g.E
+    do = P.obstacles_to_device(obs, input="f64")
+    out = pl.cut_edges(dp, g, do)       # sizes the game lists
+    info = pl.info()
+    sbuf = pl.alloc_search(dp.N)
+    units, n_obst = int(info["cut_units"]), obs.n
+    tests = units * n_obst
+    pl.set_timing(True)
+    pl.timing(reset=True)
+    pl.cut_timing(reset=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t0 = time.time()
+        while clk.count() < 1 and time.time() - t0 < 10.0:
+            pl.cut_edges_async(dp, g, do, out)
+            torch.cuda.synchronize()
+        mark = max(0, clk.count() - 1)
+        pl.timing(reset=True)
+        pl.cut_timing(reset=True)
+        cms = timed(lambda: pl.cut_edges_async(dp, g, do, out), stream, args.steps, args.warmup, flush)
+        ct = pl.cut_timing(reset=True)
+        tm = pl.timing(reset=True)
+        t0 = time.time()
+        while clk.count() < mark + 2 and time.time() - t0 < 5.0:
+            pl.cut_edges_async(dp, g, do, out)
+            torch.cuda.synchronize()
+    clocks = clk.summary(since=mark)
+    assert pl.wait() == P.PLAN_OK
+    sms = timed(lambda: pl.search_async(dp, out, dp.start_pos, dp.goal_pos, sbuf), stream, args.steps,
+                args.warmup, flush)
+    assert pl.wait() == P.PLAN_OK
+    E_out = out.E
+    # end to end per replanning tick: the obstacles from pinned host memory,
+    # the cut, the search, the path and its cost back to the host
+    h_off = torch.from_numpy(np.asarray(obs.off, dtype=np.int32)).pin_memory()
+    h_A = torch.from_numpy(np.ascontiguousarray(obs.A, dtype=np.float64).reshape(-1)).pin_memory()
+    h_b = torch.from_numpy(np.ascontiguousarray(obs.b, dtype=np.float64)).pin_memory()
+    h_path = torch.empty(dp.N, dtype=torch.int32).pin_memory()
+    h_cost = torch.empty(1, dtype=torch.float64).pin_memory()
+    h_len = torch.empty(1, dtype=torch.int32).pin_memory()
+    bi = sum(t.numel() * t.element_size() for t in (h_off, h_A, h_b))
+    bo = h_path.numel() * 4 + 8 + 4
+    e2e = []
+    for s in range(args.warmup + args.steps):
+        flush.fill_(3.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        do.off.copy_(h_off, non_blocking=True)
+        do.A.copy_(h_A, non_blocking=True)
+        do.b.copy_(h_b, non_blocking=True)
+        pl.cut_edges_async(dp, g, do, out)
+        pl.search_async(dp, out, dp.start_pos, dp.goal_pos, sbuf)
+        h_path.copy_(sbuf["path"], non_blocking=True)
+        h_cost.copy_(sbuf["cost"], non_blocking=True)
+        h_len.copy_(sbuf["path_len"], non_blocking=True)
+        e1.record(stream)
+        st = pl.wait()
+        assert st in (P.PLAN_OK, P.PLAN_ERR_NO_PATH)
+        if s >= args.warmup:
+            e2e.append(e0.elapsed_time(e1))
+    cut_ms = statistics.mean(cms)
+    scan_ms = ct["scan_ms"] / max(1, ct["cuts"])
+    # roofline of the screening pass (the bounding-box test of every (edge, T)
+    # against every obstacle): ALU-bound, 2m comparisons and 2m - 1 ORs plus
+    # the mask bit per test, about 4m FP32 lane operations
+    m, NP = prob.model.m, prob.model.degree + 1
+    ex_ops = info["cut_tests"] * (4 * m)
+    peaks, peak_src = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * sm_max * 1e6 / 1e12
+    achieved = ex_ops / (scan_ms / 1e3) / 1e12
+    dense_ops = tests * float(np.mean(np.diff(obs.off))) * NP * (m + 2)
+    return {"metric": "keep-out cut decisions/sec ((edge, T) x obstacle), 2-D, 5000 states, 500 obstacles",
+            "value": tests * 1e3 / cut_ms, "unit": "tests/s", "dtype": "f32+f64",
+            "ms_per_step": cut_ms + statistics.mean(sms), "cut_ms_per_tick": cut_ms,
+            "search_ms_per_query": statistics.mean(sms), "gpu_launches": int(tm["launches"]),
+            "clocks": clocks,
+            "config": {"workload": "keepout_2d seed 1: 2-D double integrator (|v|<=2, |a|<=4, p=5), N=5000 in "
+                                   "[0,5]^2, T=0.5, 500 obstacles (boxes of side U[0.025, 0.1] cut by <= 3 planes)",
+                       "edges_in": E_in, "edges_out": E_out, "units": units, "obstacles": n_obst, "tests": tests,
+                       "box": info["cut_box"], "near": info["cut_near"], "step1": info["cut_step1"],
+                       "step2": info["cut_step2"], "games": info["cut_games"], "lp64": info["cut_lp64"],
+                       "ties": info["cut_ties"],
+                       "l2": "flushed before every timed call (256 MB write)",
+                       "paper_context": "cutHeuristic 72.0 ms on an RTX 4090 (Table 1; its graph size is not stated)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TOP/s",
+                         "frac": achieved / alu_peak, "traffic": None, "kernel": "k_cut_scan<2,2,5>",
+                         "kernel_ms": scan_ms, "ops_per_launch": ex_ops,
+                         "work_model": "executed FP32 lane ops: (edge, T, obstacle) box tests x 4m",
+                         "dense": {"ops_per_launch": dense_ops, "frac": dense_ops / (scan_ms / 1e3) / 1e12 / alu_peak,
+                                   "note": "every control point against every facet of every obstacle, (m+2) ops each"},
+                         "peak_note": f"FP32 lanes 152 SMs x 128 x {sm_max:.0f} MHz ({peak_src} clock)"},
+            "e2e": {"value": tests * 1e3 / statistics.mean(e2e), "unit": "tests/s", "h2d_bytes_per_step": bi,
+                    "d2h_bytes_per_step": bo, "ms_per_step": statistics.mean(e2e)},
+            "cpu_baseline": cpu}
 
 
 def main():

@@ -132,11 +132,12 @@ typedef struct {
      * screened pair kernel only; 0 otherwise) */
     int64_t screened;
     /* keep-out cut (plan_cut_edges): (edge, T) checked; (edge, T, obstacle)
-     * evaluated; of those, missed by the bounding-box screen, hit by a control
+     * screened; of those, missed by the obstacles' certified bounding boxes,
+     * and the rest (the pair list); of the listed pairs, hit by a control
      * point inside and missed by one separating facet (FP32, decided within
-     * error bands); entries of the FP32 matrix-game pass and of the FP64 pass;
+     * error bands), matrix games solved in FP32; entries of the FP64 pass;
      * FP64 games that no certificate decided (|delta*| at rounding level) */
-    int64_t cut_units, cut_tests, cut_box, cut_step1, cut_step2, cut_lp, cut_lp64, cut_ties;
+    int64_t cut_units, cut_tests, cut_box, cut_near, cut_step1, cut_step2, cut_games, cut_lp64, cut_ties;
 } plan_info;
 
 /* Create a context bound to the current CUDA device and the given stream
@@ -412,6 +413,11 @@ int plan_set_accounting(plan_ctx* ctx, int enable);
 int plan_set_timing(plan_ctx* ctx, int enable);
 int plan_timing(plan_ctx* ctx, double* pair_ms, int64_t* pair_launches, double* search_ms,
                 int64_t* search_launches, int64_t* total_launches, int reset);
+
+/* Timing of plan_cut_edges calls made while plan_set_timing is on: the
+ * summed milliseconds of the first (screening) pass and of whole calls, and
+ * the number of calls, since the last reset (synchronises the stream). */
+int plan_cut_timing(plan_ctx* ctx, double* scan_ms, double* cut_ms, int64_t* cuts, int reset);
 
 const char* plan_status_string(int status);
 const char* plan_last_error(plan_ctx* ctx);

@@ -116,17 +116,20 @@ struct plan_ctx {
     int32_t* cut_pos = nullptr;
     long long* cut_chunk = nullptr;
     float* cut_orow = nullptr;
+    float* cut_okb = nullptr;
+    float* cut_obox = nullptr;
     int* cut_ocount = nullptr;
     long long cut32Cap = 0, cut64Cap = 0, want_cut32 = 0, want_cut64 = 0;
     unsigned long long* cut_list32 = nullptr;
     unsigned long long* cut_list64 = nullptr;
+    float* cut_lamy = nullptr;
     // timing
     bool timing = false;
     bool accounting = false;
     int max_sweeps = 0;
     long long spin_limit = 0;
     std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pair, ev_search;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pair, ev_search, ev_scan, ev_cut;
     long long launches = 0;
 };
 
@@ -389,7 +392,7 @@ void plan_destroy(plan_ctx* c) {
                    c->resBits, c->resKey, c->emitPre, c->recheck, c->sdist, c->sbest, c->spred, c->sfront, c->slast, c->snear,
                    c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem, c->d_qMem, c->d_sqd, c->memOff,
                    c->d_cut64, c->d_cut32, c->cut_src, c->cut_hit, c->cut_pos, c->cut_chunk, c->cut_orow,
-                   c->cut_ocount, c->cut_list32, c->cut_list64};
+                   c->cut_ocount, c->cut_list32, c->cut_list64, c->cut_okb, c->cut_obox, c->cut_lamy};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_tab64) cudaFreeHost(c->h_tab64);
@@ -411,6 +414,11 @@ void plan_destroy(plan_ctx* c) {
         cudaEventDestroy(pr.first);
         cudaEventDestroy(pr.second);
     }
+    for (auto* lst : {&c->ev_scan, &c->ev_cut})
+        for (auto& pr : *lst) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     delete c;
 }
@@ -915,7 +923,8 @@ int plan_cut_edges(plan_ctx* c, int N, const void* states, int nT, const double*
     const int maxr = obst->n > 0 ? obst->max_rows : 1;
     const long long nob = obst->n > 0 ? obst->n : 1;
     if (nob > c->capCutO || nob * maxr > c->capCutR) {
-        if (!dalloc(c, &c->cut_ocount, nob) || !dalloc(c, &c->cut_orow, 4 * nob * maxr)) {
+        if (!dalloc(c, &c->cut_ocount, nob) || !dalloc(c, &c->cut_orow, 4 * nob * maxr) ||
+            !dalloc(c, &c->cut_okb, 2 * nob * maxr) || !dalloc(c, &c->cut_obox, 8 * nob)) {
             c->capCutO = c->capCutR = -1;
             return PLAN_ERR_NO_MEMORY;
         }
@@ -932,7 +941,7 @@ int plan_cut_edges(plan_ctx* c, int N, const void* states, int nT, const double*
         c->cut32Cap = w32;
     }
     if (w64 > c->cut64Cap) {
-        if (!dalloc(c, &c->cut_list64, w64)) {
+        if (!dalloc(c, &c->cut_list64, w64) || !dalloc(c, &c->cut_lamy, 32 * w64)) {
             c->cut64Cap = 0;
             return PLAN_ERR_NO_MEMORY;
         }
@@ -969,6 +978,8 @@ int plan_cut_edges(plan_ctx* c, int N, const void* states, int nT, const double*
     C.A = obst->A;
     C.b = obst->b;
     C.orow = c->cut_orow;
+    C.okb = c->cut_okb;
+    C.obox = c->cut_obox;
     C.ocount = c->cut_ocount;
     C.tab64 = c->d_cut64;
     C.tab32 = c->d_cut32;
@@ -979,14 +990,26 @@ int plan_cut_edges(plan_ctx* c, int N, const void* states, int nT, const double*
     C.cap32 = c->cut32Cap;
     C.list64 = c->cut_list64;
     C.cap64 = c->cut64Cap;
+    C.lamy = c->cut_lamy;
     C.chunk = c->cut_chunk;
     C.pos = c->cut_pos;
     C.nchunks = nchunks;
     C.info = c->d_info;
-    cudaError_t e = cudaMemsetAsync(&c->d_info->cut_units, 0, 8 * sizeof(unsigned long long), c->stream);
+    cudaError_t e = cudaMemsetAsync(&c->d_info->cut_units, 0, 9 * sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset cut counters");
+    cudaEvent_t s0 = nullptr, s1 = nullptr, c0 = nullptr, c1 = nullptr;
+    if (c->timing) {
+        s0 = take_event(c);
+        s1 = take_event(c);
+        c0 = take_event(c);
+        c1 = take_event(c);
+        c->ev_scan.emplace_back(s0, s1);
+        c->ev_cut.emplace_back(c0, c1);
+        cudaEventRecord(c0, c->stream);
+    }
     int launches = 0;
-    int ce = launch_cut(C, c->stream, c->num_sms, &launches);
+    int ce = launch_cut(C, c->stream, c->num_sms, &launches, s0, s1);
+    if (c->timing) cudaEventRecord(c1, c->stream);
     c->launches += launches;
     if (ce != 0) return cuda_fail(c, (cudaError_t)ce, "cut launch");
     return PLAN_OK;
@@ -1159,7 +1182,7 @@ int plan_wait(plan_ctx* c, plan_info* info) {
             c->want_rechecks = need + need / 4 + 1024;
         }
         if (d.detail == DET_CUTLIST) {
-            c->want_cut32 = (long long)(d.cut_lp + d.cut_lp / 4 + 4096);
+            c->want_cut32 = (long long)(d.cut_near + d.cut_near / 4 + 4096);
             c->want_cut64 = (long long)(d.cut_lp64 + d.cut_lp64 / 4 + 1024);
         }
     }
@@ -1187,9 +1210,10 @@ int plan_wait(plan_ctx* c, plan_info* info) {
         info->cut_units = (int64_t)d.cut_units;
         info->cut_tests = (int64_t)d.cut_tests;
         info->cut_box = (int64_t)d.cut_box;
+        info->cut_near = (int64_t)d.cut_near;
         info->cut_step1 = (int64_t)d.cut_step1;
         info->cut_step2 = (int64_t)d.cut_step2;
-        info->cut_lp = (int64_t)d.cut_lp;
+        info->cut_games = (int64_t)d.cut_games;
         info->cut_lp64 = (int64_t)d.cut_lp64;
         info->cut_ties = (int64_t)d.cut_ties;
     }
@@ -1247,6 +1271,35 @@ int plan_timing(plan_ctx* c, double* pair_ms, int64_t* pair_launches, double* se
         c->ev_pair.clear();
         c->ev_search.clear();
         c->launches = 0;
+    }
+    return PLAN_OK;
+}
+
+int plan_cut_timing(plan_ctx* c, double* scan_ms, double* cut_ms, int64_t* cuts, int reset) {
+    if (!c) return PLAN_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream sync");
+    double a = 0, b = 0;
+    for (auto& pr : c->ev_scan) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) a += ms;
+    }
+    for (auto& pr : c->ev_cut) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) b += ms;
+    }
+    cudaGetLastError();
+    if (scan_ms) *scan_ms = a;
+    if (cut_ms) *cut_ms = b;
+    if (cuts) *cuts = (int64_t)c->ev_cut.size();
+    if (reset) {
+        for (auto* lst : {&c->ev_scan, &c->ev_cut}) {
+            for (auto& pr : *lst) {
+                c->ev_pool.push_back(pr.first);
+                c->ev_pool.push_back(pr.second);
+            }
+            lst->clear();
+        }
     }
     return PLAN_OK;
 }

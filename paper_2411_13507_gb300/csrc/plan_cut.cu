@@ -14,20 +14,24 @@
 // margins (halves summed left to right without FMA, as in the edge build);
 // the FP32 passes take only the decisions that their error bands prove.
 //
-//  Pass A (k_cut_scan): one lane per (edge, T), the block's warps split the
-//    obstacles; FP32 control points, then per obstacle (i) a facet whose
-//    half-space misses the control points' bounding box -> miss, (ii) the
-//    margins with bands: a point certainly inside -> hit, a facet certainly
-//    separating -> miss, otherwise the entry joins the game list.
-//  Pass B (k_cut_lp32): the game solved by the simplex method in FP32.  Weak
-//    duality turns its solution into certificates: any lambda >= 0 with
-//    G^T lambda < 0 proves a hit, any y >= 0 with G y > 0 a miss; both are
-//    checked against G's error bands.  Uncertified entries go to pass C.
-//  Pass C (k_cut_lp64): canonical FP64 margins, Algorithm 2's two checks
-//    exactly, then the game in FP64 with certificates against the rounding of
-//    the check itself.  A game certified neither way has |delta*| at the
-//    rounding level: a tie, decided by the sign of the computed value and
-//    counted.
+//  Boxes (k_cut_obox): a certified bounding box of every obstacle, each side
+//    backed by a dual vector y >= 0 with A^T y = +-e_a (a certificate of the
+//    game for every curve beyond that side).
+//  Pass A (k_cut_scan): one lane per (edge, T); FP32 control points, their
+//    box against every obstacle's box within error bounds; the pairs that no
+//    box separates form the pair list.
+//  Pass B (k_cut_pair): one thread per listed pair: FP32 margins with bands,
+//    Algorithm 2's two checks (a point certainly inside -> hit, a facet
+//    certainly separating -> miss), else the game by the simplex method in
+//    registers.  Weak duality turns its solution into certificates: any
+//    lambda >= 0 with G^T lambda < 0 proves a hit, any y >= 0 with G y > 0 a
+//    miss; both are checked against G's error bands.  Uncertified entries go
+//    to pass C.
+//  Pass C (k_cut_lp64): one warp per entry (lane = facet): canonical FP64
+//    margins, Algorithm 2's two checks exactly, then the game in FP64 with
+//    certificates against the rounding of the check itself.  A game certified
+//    neither way has |delta*| at the rounding level: a tie, decided by the
+//    sign of the computed value and counted.
 //  Compaction: kept = mask & ~hit != 0; chunk counts, one scan, the fill (an
 //    edge whose cheapest duration was cut is re-costed in canonical FP64 over
 //    the durations left), the row offsets.
@@ -52,9 +56,9 @@ constexpr double U64 = 1.1102230246251565e-16;  // 2^-53
 // (m + 1 u) add up to at most 12 u for g, m <= 3; 32 u leaves room for the
 // rounding of the band itself and of the comparisons built on it.
 constexpr float KO = 32.f * U32;
-constexpr int SCAN_WARPS = 8;   // obstacle stripes per block of pass A
 constexpr int GAME_ITERS = 96;  // simplex pivots before an entry is handed on
 constexpr unsigned long long OBST_BITS = 20;
+constexpr int LAMY_STRIDE = 32;  // floats per FP64-list entry: lambda (p + 1 <= 16) then y (<= 16 rows)
 
 CDEV void cut_status(DevInfo* info, int code, int detail) {
     if (atomicCAS(&info->status, 0, code) == 0) atomicExch(&info->detail, detail);
@@ -149,7 +153,16 @@ CDEV void unit_points(const CutParams& C, long long i, long long j, int t, float
     }
 }
 
-// Facet row {A_0, A_1, A_2, b}: FP32 margin of point z and its band.
+// Facet row {A_0, A_1, A_2, b}: FP32 product A . z, margin A . z - b and band.
+// The comparisons s > b + band and s <= b - band used by the screening pass
+// round once more than s - b > band; the band's slack covers it.
+template <int M>
+CDEV float dot32(const float4& f, const float* z) {
+    float s = f.x * z[0];
+    s = fmaf(f.y, z[1], s);
+    if (M == 3) s = fmaf(f.z, z[2], s);
+    return s;
+}
 template <int M>
 CDEV float margin32(const float4& f, const float* z) {
     float s = f.x * z[0];
@@ -211,281 +224,488 @@ __global__ void __launch_bounds__(256) k_cut_prep(CutParams C, int row_blocks) {
         f.z = C.m == 3 ? ld32(C.A, r * C.m + 2, C.in_f32) : 0.f;
         f.w = ld32(C.b, r, C.in_f32);
         reinterpret_cast<float4*>(C.orow)[u] = f;
+        const float n1 = fabsf(f.x) + fabsf(f.y) + fabsf(f.z);
+        reinterpret_cast<float2*>(C.okb)[u] = make_float2(KO * n1, KO * fabsf(f.w));
     }
 }
 
 // ---------------------------------------------------------------------------
-// Pass A.  A block takes 32 (edge, T) units at a time (one per lane); warp 0
-// computes their control points into shared memory, then warp w scans the
-// obstacles w, w + 8, ... for all 32.  A unit found to hit stops every warp's
-// scan of it (shared flag).  Entries that no band decides are appended to the
-// game list (one atomic per warp and obstacle).
+// Certified bounding box of every obstacle, one warp per obstacle.  For a
+// direction d = +-e_a, any y >= 0 with A^T y = d bounds the obstacle:
+// d . z <= b^T y on O (weak duality), and it turns into a certificate of the
+// game: sum_r y_r G[l][r] = d . P_l - b^T y + (A^T y - d) . P_l.  The lanes
+// search all m-row subsets in FP32 for the dual-feasible one with the lowest
+// bound (the optimal vertex); lane d recomputes that subset's y in FP64,
+// clamps it to y >= 0 and keeps
+//   beta' = b^T y + 2^-48 sum_r y_r |b_r|                (rounded outward to FP32)
+//   c     = ||A^T y - d||_1 + 2^-47 sum_r y_r ||A_r||_1  (must be <= 2^-30),
+// which covers the residual, the rounding of b^T y and that of the canonical
+// FP64 margins.  A unit whose control points satisfy d . P_l > beta' + c S
+// for all l (checked as lo_a - e > hi bound, e = (16 u + 2^-29) S, in pass A)
+// misses the obstacle: y is a certificate.  A direction without a usable y
+// (unbounded obstacle, near-singular vertex) gets an infinite bound.
 // ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(128) k_cut_obox(CutParams C) {
+    if (block_edges(C) == 0) return;
+    const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const float finf = __int_as_float(0x7f800000);
+    for (long long o = gw; o < C.n_obst; o += nw) {
+        const int nr = C.ocount[o], r0 = C.obst_off[o];
+        const float4* rw = reinterpret_cast<const float4*>(C.orow) + o * C.max_orows;
+        float best[2 * M];
+        int bsub[2 * M];
+#pragma unroll
+        for (int d = 0; d < 2 * M; ++d) {
+            best[d] = finf;
+            bsub[d] = -1;
+        }
+        int nsub = nr;
+#pragma unroll
+        for (int k = 1; k < M; ++k) nsub *= nr;
+        for (int s = lane; s < nsub; s += 32) {
+            int idx[M], q = s;
+            bool inc = true;
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                idx[k] = q % nr;
+                q /= nr;
+                if (k > 0 && idx[k] <= idx[k - 1]) inc = false;
+            }
+            if (!inc) continue;
+            float a[M][M], bs[M], nrm = 1.f;
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                const float4 f = rw[idx[k]];
+                a[k][0] = f.x;
+                a[k][1] = f.y;
+                if (M == 3) a[k][M - 1] = f.z;
+                bs[k] = f.w;
+                nrm *= fabsf(f.x) + fabsf(f.y) + fabsf(f.z);
+            }
+            // y solves sum_k y_k a[k] = d: y = (a^T)^-1 d, i.e. row a of a^-1 ... via cofactors
+            float inv[M][M], det;
+            if (M == 2) {
+                det = a[0][0] * a[1][1] - a[0][1] * a[1][0];
+                inv[0][0] = a[1][1];
+                inv[0][1] = -a[0][1];
+                inv[1][0] = -a[1][0];
+                inv[1][1] = a[0][0];
+            } else {
+#pragma unroll
+                for (int i = 0; i < M; ++i)
+#pragma unroll
+                    for (int j = 0; j < M; ++j) {
+                        const int i1 = (i + 1) % M, i2 = (i + 2) % M, j1 = (j + 1) % M, j2 = (j + 2) % M;
+                        inv[j][i] = a[i1][j1] * a[i2][j2] - a[i1][j2] * a[i2][j1];  // adjugate
+                    }
+                det = a[0][0] * inv[0][0] + a[0][1] * inv[1][0] + a[0][M - 1] * inv[M - 1][0];
+            }
+            if (!(fabsf(det) > 1e-4f * nrm)) continue;
+            const float rdet = 1.f / det;
+            // a^T y = e_a  <=>  y_k = (a^-1)[a][k] = inv[a][k] / det
+#pragma unroll
+            for (int ax = 0; ax < M; ++ax)
+#pragma unroll
+                for (int sg = 0; sg < 2; ++sg) {
+                    bool ok = true;
+                    float bound = 0.f;
+#pragma unroll
+                    for (int k = 0; k < M; ++k) {
+                        const float yk = (sg ? -1.f : 1.f) * inv[ax][k] * rdet;
+                        ok = ok && yk >= -1e-6f;
+                        bound = fmaf(yk, bs[k], bound);
+                    }
+                    const int d = 2 * ax + sg;
+                    if (ok && bound < best[d]) {
+                        best[d] = bound;
+                        bsub[d] = s;
+                    }
+                }
+        }
+#pragma unroll
+        for (int d = 0; d < 2 * M; ++d)
+            for (int of = 16; of > 0; of >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best[d], of);
+                const int os = __shfl_xor_sync(0xffffffffu, bsub[d], of);
+                if (ob < best[d] || (ob == best[d] && os < bsub[d])) {
+                    best[d] = ob;
+                    bsub[d] = os;
+                }
+            }
+        float out = 0.f;
+        if (lane < 2 * M) {
+            const int d = lane, ax = d >> 1;
+            const double sgn = (d & 1) ? -1.0 : 1.0;
+            int sub = -1;
+#pragma unroll
+            for (int k = 0; k < 2 * M; ++k) sub = (k == d) ? bsub[k] : sub;
+            double bnd = __longlong_as_double(0x7FF0000000000000ll);  // +inf: no bound
+            if (sub >= 0) {
+                int idx[M], q = sub;
+                double a[M][M], bs[M];
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    idx[k] = q % nr;
+                    q /= nr;
+#pragma unroll
+                    for (int j = 0; j < M; ++j) a[k][j] = ld64(C.A, (long long)(r0 + idx[k]) * M + j, C.in_f32);
+                    bs[k] = ld64(C.b, r0 + idx[k], C.in_f32);
+                }
+                // solve a^T y = sgn e_ax by Cramer's rule in FP64
+                double y[M];
+                if (M == 2) {
+                    const double det = a[0][0] * a[1][1] - a[0][1] * a[1][0];
+                    const double e0 = ax == 0 ? sgn : 0.0, e1 = ax == 1 ? sgn : 0.0;
+                    // [a00 a10; a01 a11] y = e
+                    y[0] = (e0 * a[1][1] - a[1][0] * e1) / det;
+                    y[1] = (a[0][0] * e1 - e0 * a[0][1]) / det;
+                } else {
+                    double adj[M][M];
+#pragma unroll
+                    for (int i = 0; i < M; ++i)
+#pragma unroll
+                        for (int j = 0; j < M; ++j) {
+                            const int i1 = (i + 1) % M, i2 = (i + 2) % M, j1 = (j + 1) % M, j2 = (j + 2) % M;
+                            adj[j][i] = a[i1][j1] * a[i2][j2] - a[i1][j2] * a[i2][j1];
+                        }
+                    const double det = a[0][0] * adj[0][0] + a[0][1] * adj[1][0] + a[0][M - 1] * adj[M - 1][0];
+#pragma unroll
+                    for (int k = 0; k < M; ++k) y[k] = sgn * adj[ax][k] / det;
+                }
+                double beta = 0.0, yb = 0.0, y1 = 0.0, rho = 0.0;
+                bool fin = true;
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    y[k] = y[k] > 0.0 ? y[k] : 0.0;
+                    fin = fin && isfinite(y[k]);
+                    beta += y[k] * bs[k];
+                    yb += y[k] * fabs(bs[k]);
+                    double n1 = 0.0;
+#pragma unroll
+                    for (int j = 0; j < M; ++j) n1 += fabs(a[k][j]);
+                    y1 += y[k] * n1;
+                }
+#pragma unroll
+                for (int j = 0; j < M; ++j) {
+                    double w = 0.0;
+#pragma unroll
+                    for (int k = 0; k < M; ++k) w += y[k] * a[k][j];
+                    rho += fabs(w - (j == ax ? sgn : 0.0));
+                }
+                const double c = rho + 0x1p-47 * y1;
+                if (fin && isfinite(beta) && c <= 0x1p-30) bnd = beta + 0x1p-48 * yb;
+            }
+            // +e_ax: z_ax <= bnd (upper bound, rounded up); -e_ax: z_ax >= -bnd (rounded down)
+            out = (d & 1) ? __double2float_rd(-bnd) : __double2float_ru(bnd);
+        }
+        // lanes 0..2M-1 hold hi_0, lo_0, hi_1, lo_1, ...
+        float* ob = C.obox + o * 8;
+        if (lane < 2 * M) {
+            const int ax = lane >> 1;
+            if (M == 2) ob[(lane & 1) ? ax : 2 + ax] = out;
+            else ob[(lane & 1) ? ax : 4 + ax] = out;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pass A: a block of 8 warps takes 256 (edge, T) units (a lane each) and one
+// stripe of the obstacles.  Each warp computes its units' FP32 control
+// points (stripes of the same units repeat that small step); the block stages
+// the obstacles' certified boxes in shared memory, SCAN_TILE at a time, and
+// each lane tests its unit against them, eight per step: lo_a - e > hi_a(O)
+// or hi_a + e < lo_a(O) for some axis a, with e = (16 u + 2^-29) S covering
+// the FP32 control points and the bounds' own residual term.  Pairs that no
+// box separates go to the pair list through a per-warp buffer in shared
+// memory (one atomic per flush).
+// ---------------------------------------------------------------------------
+constexpr int SCAN_STEP = 8;
+constexpr int SCAN_TILE = 1024;  // obstacle boxes staged per block step (half for m = 3)
+constexpr int SCAN_BUF = 256;    // pair-list entries a warp gathers before one flush
+
+// Appends a warp's buffered entries to the pair list with one atomic.
+CDEV void flush_pairs(const CutParams& C, unsigned long long* buf, int n, int lane) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&C.info->cut_near, (unsigned long long)n);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int k = lane; k < n; k += 32)
+        if (base + k < (unsigned long long)C.cap32) C.list32[base + k] = buf[k];
+    __syncwarp();
+}
+
 template <int M, int G, int PD>
-__global__ void __launch_bounds__(256) k_cut_scan(CutParams C) {
-    constexpr int NP = PD + 1, PS = NP * M + 1;  // odd stride: lane-strided reads hit distinct banks
-    __shared__ float sP[32 * PS];
-    __shared__ float sS[32], sLo[32 * 4], sHi[32 * 4];
-    __shared__ int sState[32];  // 0 checking, 1 hit, 2 nothing to check
+__global__ void __launch_bounds__(256) k_cut_scan(CutParams C, int target_items) {
+    constexpr int NP = PD + 1, BW = M == 2 ? 1 : 2;  // float4 per staged box
+    constexpr int TILE = SCAN_TILE / BW;
+    __shared__ float4 sbox[TILE * BW];
+    __shared__ unsigned long long sbuf[8][SCAN_BUF];
     const long long E = block_edges(C);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long* buf = sbuf[warp];
+    int nbuf = 0;
     const long long units = E * C.nT;
-    unsigned long long n_units = 0, n_tests = 0, n_box = 0, n_s1 = 0, n_s2 = 0;
-    volatile int* vstate = sState;
-    for (long long g0 = (long long)blockIdx.x * 32; g0 < units; g0 += (long long)gridDim.x * 32) {
-        if (warp == 0) {
-            const long long u = g0 + lane;
-            int st = 2;
-            if (u < units) {
-                const long long e = u / C.nT;
-                const int t = (int)(u - e * C.nT);
-                if ((C.mask_in[e] >> t) & 1u) {
-                    float P[NP * M], S, lo[M], hi[M];
-                    unit_points<M, G, PD>(C, C.src[e], C.col_in[e], t, P, S, lo, hi);
+    const long long nbg = (units + 255) / 256;
+    // stripes of the obstacles when the 256-unit groups alone are too few to
+    // give every SM work (the same choice in every block)
+    int stripes = (int)((target_items + nbg - 1) / (nbg > 0 ? nbg : 1));
+    stripes = stripes < 1 ? 1 : (stripes > 16 ? 16 : stripes);
+    if (stripes > C.n_obst) stripes = C.n_obst > 0 ? C.n_obst : 1;
+    const int per = (C.n_obst + stripes - 1) / stripes;
+    unsigned long long n_units = 0, n_tests = 0, n_near = 0;
+    const float4* gbox = reinterpret_cast<const float4*>(C.obox);
+    for (long long item = blockIdx.x; item < nbg * stripes; item += gridDim.x) {
+        const long long bg = item / stripes;
+        const int sidx = (int)(item - bg * stripes);
+        const long long u = bg * 256 + threadIdx.x;
+        float le[M], he[M];
+        bool valid = false;
+        if (u < units) {
+            const long long e = u / C.nT;
+            const int t = (int)(u - e * C.nT);
+            if ((C.mask_in[e] >> t) & 1u) {
+                float P[NP * M], S, lo[M], hi[M];
+                unit_points<M, G, PD>(C, C.src[e], C.col_in[e], t, P, S, lo, hi);
+                const float ebox = (16.f * U32 + 0x1p-29f) * S;
 #pragma unroll
-                    for (int k = 0; k < NP * M; ++k) sP[lane * PS + k] = P[k];
-                    sS[lane] = S;
-#pragma unroll
-                    for (int a = 0; a < M; ++a) {
-                        sLo[lane * 4 + a] = lo[a];
-                        sHi[lane * 4 + a] = hi[a];
-                    }
-                    st = 0;
-                    ++n_units;
+                for (int a = 0; a < M; ++a) {
+                    le[a] = lo[a] - ebox;
+                    he[a] = hi[a] + ebox;
                 }
+                valid = true;
+                if (sidx == 0) ++n_units;
             }
-            sState[lane] = st;
         }
-        __syncthreads();
-        bool done = sState[lane] != 0;
-        float P[NP * M], lo[M], hi[M], S = 0.f;
+        if (!valid) {
 #pragma unroll
-        for (int k = 0; k < NP * M; ++k) P[k] = sP[lane * PS + k];
-#pragma unroll
-        for (int a = 0; a < M; ++a) {
-            lo[a] = sLo[lane * 4 + a];
-            hi[a] = sHi[lane * 4 + a];
+            for (int a = 0; a < M; ++a) {
+                le[a] = __int_as_float(0x7f800000);  // every box test says "far"
+                he[a] = -__int_as_float(0x7f800000);
+            }
         }
-        S = sS[lane];
-        for (int o = warp; o < C.n_obst; o += SCAN_WARPS) {
-            done = done || vstate[lane] != 0;
-            if (__all_sync(0xffffffffu, done)) break;
-            bool want = false;
-            if (!done) {
-                ++n_tests;
-                const int nr = __ldg(C.ocount + o);
-                const float4* rw = reinterpret_cast<const float4*>(C.orow) + (long long)o * C.max_orows;
-                // (i) bounding-box screen: the box corner lowest along A_r
-                bool sep = false;
-                for (int r = 0; r < nr && !sep; ++r) {
-                    const float4 f = __ldg(rw + r);
-                    float z[M];
-                    z[0] = f.x >= 0.f ? lo[0] : hi[0];
-                    z[1] = f.y >= 0.f ? lo[1] : hi[1];
-                    if (M == 3) z[M - 1] = f.z >= 0.f ? lo[M - 1] : hi[M - 1];
-                    sep = margin32<M>(f, z) > band32<M>(f, S);
-                }
-                if (sep) {
-                    ++n_box;
-                } else {
-                    // (ii) the margins: a facet above every band separates; a
-                    // point below every band is inside
-                    float gmax[NP];
+        const bool any_valid = __syncthreads_or(valid) != 0;
+        const int o0 = sidx * per, o1 = min(C.n_obst, o0 + per);
+        for (int t0 = o0; any_valid && t0 < o1; t0 += TILE) {
+            const int nt = min(TILE, o1 - t0);
+            __syncthreads();  // the previous tile is consumed
+            for (int k = threadIdx.x; k < nt * BW; k += blockDim.x) {
+                const int ob = k / BW, h = k - ob * BW;
+                sbox[k] = __ldg(gbox + 2 * (long long)(t0 + ob) + (M == 2 ? 0 : h));
+            }
+            __syncthreads();
+            for (int ob = 0; ob < nt; ob += SCAN_STEP) {
+                unsigned need = 0;
 #pragma unroll
-                    for (int l = 0; l < NP; ++l) gmax[l] = -__int_as_float(0x7f800000);
-                    bool sep2 = false;
-                    for (int r = 0; r < nr; ++r) {
-                        const float4 f = __ldg(rw + r);
-                        const float band = band32<M>(f, S);
-                        float mn = __int_as_float(0x7f800000);
-#pragma unroll
-                        for (int l = 0; l < NP; ++l) {
-                            const float gv = margin32<M>(f, P + l * M);
-                            mn = fminf(mn, gv);
-                            gmax[l] = fmaxf(gmax[l], gv + band);
-                        }
-                        if (mn > band) {
-                            sep2 = true;
-                            break;
-                        }
-                    }
-                    if (sep2) {
-                        ++n_s2;
-                    } else {
-                        bool in = false;
-#pragma unroll
-                        for (int l = 0; l < NP; ++l) in = in || gmax[l] <= 0.f;
-                        if (in) {
-                            ++n_s1;
-                            done = true;
-                            vstate[lane] = 1;
+                for (int k = 0; k < SCAN_STEP; ++k) {
+                    if (ob + k < nt) {
+                        const float4 b0 = sbox[(ob + k) * BW];
+                        bool far;
+                        if (M == 2) {
+                            far = le[0] > b0.z || le[1] > b0.w || he[0] < b0.x || he[1] < b0.y;
                         } else {
-                            want = true;
+                            const float4 b1 = sbox[(ob + k) * BW + 1];
+                            far = le[0] > b1.x || le[1] > b1.y || le[M - 1] > b1.z || he[0] < b0.x ||
+                                  he[1] < b0.y || he[M - 1] < b0.z;
                         }
+                        need |= far ? 0u : (1u << k);
                     }
                 }
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, want);
-            if (bal) {
-                const int leader = __ffs(bal) - 1;
-                unsigned long long base = 0;
-                if (lane == leader) base = atomicAdd(&C.info->cut_lp, (unsigned long long)__popc(bal));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                if (want) {
-                    const unsigned long long idx = base + __popc(bal & ((1u << lane) - 1u));
-                    if (idx < (unsigned long long)C.cap32)
-                        C.list32[idx] = ((unsigned long long)(g0 + lane) << OBST_BITS) | (unsigned long long)o;
+                if (valid) n_tests += min(SCAN_STEP, nt - ob);
+                if (__any_sync(0xffffffffu, need != 0u)) {
+                    const int cnt = __popc(need);
+                    int incl = cnt;
+                    for (int of = 1; of < 32; of <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, incl, of);
+                        if (lane >= of) incl += v;
+                    }
+                    const int total = __shfl_sync(0xffffffffu, incl, 31);
+                    if (nbuf + total > SCAN_BUF) {
+                        flush_pairs(C, buf, nbuf, lane);
+                        nbuf = 0;
+                    }
+                    int idx = nbuf + incl - cnt;
+                    for (unsigned bits = need; bits; bits &= bits - 1u, ++idx)
+                        buf[idx] = ((unsigned long long)u << OBST_BITS) |
+                                   (unsigned long long)(t0 + ob + __ffs(bits) - 1);
+                    __syncwarp();
+                    nbuf += total;
+                    n_near += cnt;
                 }
             }
         }
-        __syncthreads();
-        if (warp == 0 && sState[lane] == 1) {
-            const long long u = g0 + lane, e = u / C.nT;
-            atomicOr(&C.hit[e], 1u << (int)(u - e * C.nT));
-        }
-        __syncthreads();
     }
+    if (nbuf > 0) flush_pairs(C, buf, nbuf, lane);
     cut_block_add(&C.info->cut_units, n_units);
     cut_block_add(&C.info->cut_tests, n_tests);
-    cut_block_add(&C.info->cut_box, n_box);
-    cut_block_add(&C.info->cut_step1, n_s1);
-    cut_block_add(&C.info->cut_step2, n_s2);
+    cut_block_add(&C.info->cut_box, n_tests - n_near);
 }
 
 // ---------------------------------------------------------------------------
-// The matrix game of G (NP rows l, nr columns r, G[l * nr + r]) by the
-// simplex method with Bland's rule: with c = 1 - min G every payoff
-// M = G + c is >= 1; maximise sum_l u_l subject to sum_l M[l][r] u_l <= 1 for
-// every r, u >= 0 (the slack basis is feasible).  At the optimum
-// delta* = 1 / sum u - c, lambda = u (the row player's mix, unnormalised) and
-// y_r = minus the reduced cost of slack r (the column player's mix).  The
-// tableau lives in local memory with the row stride of the actual nr.
-// Returns false if GAME_ITERS pivots did not reach optimality; lambda and y
-// are then whatever the last basis gives (the caller only uses them as
-// certificate candidates).
+// The matrix game of G (NP rows l, nr <= RB columns r) by the simplex method.
+// With c = 1 - min G every payoff M = G + c is >= 1; maximise sum_l u_l
+// subject to sum_l M[l][r] u_l <= 1 for every r, u >= 0 (the slack basis is
+// feasible).  At the optimum delta* = 1 / sum u - c, lambda = u (the row
+// player's mix, unnormalised) and y_r = minus the reduced cost of slack r (the
+// column player's mix).  Entering column: the largest reduced cost for the
+// first GAME_DANTZIG pivots, then Bland's rule (lowest label; no cycling).
+//
+// Condensed tableau, one row per basic variable and one column per
+// non-basic one (labels: u_l -> l, slack s_r -> NP + r), held in registers:
+// every access with the pivot's row or column index is an unrolled select, so
+// nothing goes to local memory.  T enters as M^T (rows r >= nr zero), rhs as
+// 1 (0 for r >= nr, which never leave).  Returns false if GAME_ITERS pivots
+// did not reach optimality; lambda and y are then those of the last basis
+// (the caller uses them only as certificate candidates).
 // ---------------------------------------------------------------------------
-template <typename F, int NP>
-CDEV bool game_solve(const F* G, int nr, F* lam, F* y, F& value, F tol) {
-    constexpr int NCMAX = NP + CUT_RMAX + 1;
-    F tab[CUT_RMAX * NCMAX];
-    F obj[NCMAX];
-    int basis[CUT_RMAX];
-    const int nc = NP + nr + 1, rhs = NP + nr;
-    F gmin = G[0];
-    for (int k = 1; k < NP * nr; ++k) gmin = G[k] < gmin ? G[k] : gmin;
-    const F shift = F(1) - gmin;
-    for (int r = 0; r < nr; ++r) {
-        F* row = tab + r * nc;
-        for (int l = 0; l < NP; ++l) row[l] = G[l * nr + r] + shift;
-        for (int k = 0; k < nr; ++k) row[NP + k] = k == r ? F(1) : F(0);
-        row[rhs] = F(1);
-        basis[r] = NP + r;
+constexpr int GAME_DANTZIG = 24;
+
+template <typename F>
+CDEV F pos_part(F v) { return v > F(0) ? v : F(0); }
+
+template <typename F, int NP, int RB>
+CDEV bool game_reg(F (&T)[RB][NP], F (&rhs)[RB], F (&lam)[NP], F (&y)[RB], F tol) {
+    F d[NP];
+    int colLab[NP], rowLab[RB];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        d[j] = F(1);
+        colLab[j] = j;
     }
-    for (int j = 0; j < nc; ++j) obj[j] = j < NP ? F(1) : F(0);
+#pragma unroll
+    for (int i = 0; i < RB; ++i) rowLab[i] = NP + i;
     bool optimal = false;
     for (int it = 0; it < GAME_ITERS; ++it) {
-        int enter = -1;
-        for (int j = 0; j < NP + nr; ++j)
-            if (obj[j] > tol) {
-                enter = j;
-                break;
+        int c = -1, cl = 1 << 20;
+        F dbest = tol;
+        if (it < GAME_DANTZIG) {
+#pragma unroll
+            for (int j = 0; j < NP; ++j)
+                if (d[j] > dbest) {
+                    c = j;
+                    dbest = d[j];
+                }
+            if (c >= 0) {
+#pragma unroll
+                for (int j = 0; j < NP; ++j) cl = (j == c) ? colLab[j] : cl;
             }
-        if (enter < 0) {
+        } else {
+#pragma unroll
+            for (int j = 0; j < NP; ++j)
+                if (d[j] > tol && colLab[j] < cl) {
+                    c = j;
+                    cl = colLab[j];
+                }
+        }
+        if (c < 0) {
             optimal = true;
             break;
         }
-        int leave = -1;
+        F colc[RB];
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            F v = T[i][0];
+#pragma unroll
+            for (int j = 1; j < NP; ++j) v = (j == c) ? T[i][j] : v;
+            colc[i] = v;
+        }
+        int r = -1, rl = 1 << 20;
         F best = F(0);
-        for (int r = 0; r < nr; ++r) {
-            const F a = tab[r * nc + enter];
-            if (a > tol) {
-                const F ratio = tab[r * nc + rhs] / a;
-                if (leave < 0 || ratio < best || (ratio == best && basis[r] < basis[leave])) {
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+            if (colc[i] > tol) {
+                const F ratio = rhs[i] / colc[i];
+                if (r < 0 || ratio < best || (ratio == best && rowLab[i] < rl)) {
+                    r = i;
                     best = ratio;
-                    leave = r;
+                    rl = rowLab[i];
                 }
             }
-        }
-        if (leave < 0) break;  // unbounded: impossible with payoffs >= 1
-        F* prow = tab + leave * nc;
-        const F inv = F(1) / prow[enter];
-        for (int j = 0; j < nc; ++j) prow[j] *= inv;
-        prow[enter] = F(1);
-        for (int r = 0; r < nr; ++r) {
-            if (r == leave) continue;
-            F* row = tab + r * nc;
-            const F f = row[enter];
-            if (f != F(0)) {
-                for (int j = 0; j < nc; ++j) row[j] -= f * prow[j];
-                row[enter] = F(0);
+        if (r < 0) break;  // unbounded: impossible with payoffs >= 1
+        F rowr[NP], rhsr = rhs[0], p = colc[0];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) rowr[j] = T[0][j];
+#pragma unroll
+        for (int i = 1; i < RB; ++i)
+            if (i == r) {
+#pragma unroll
+                for (int j = 0; j < NP; ++j) rowr[j] = T[i][j];
+                rhsr = rhs[i];
+                p = colc[i];
             }
+        const F inv = F(1) / p;
+        F rs[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) rs[j] = (j == c) ? inv : rowr[j] * inv;
+        const F rhs_s = rhsr * inv;
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            const bool isr = i == r;
+            const F ci = colc[i];
+#pragma unroll
+            for (int j = 0; j < NP; ++j) T[i][j] = isr ? rs[j] : ((j == c) ? F(0) : T[i][j]) - ci * rs[j];
+            rhs[i] = isr ? rhs_s : rhs[i] - ci * rhs_s;
         }
-        const F f = obj[enter];
-        for (int j = 0; j < nc; ++j) obj[j] -= f * prow[j];
-        obj[enter] = F(0);
-        basis[leave] = enter;
+        F dc = d[0];
+#pragma unroll
+        for (int j = 1; j < NP; ++j) dc = (j == c) ? d[j] : dc;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) d[j] = ((j == c) ? F(0) : d[j]) - dc * rs[j];
+        int lr = rowLab[0];
+#pragma unroll
+        for (int i = 1; i < RB; ++i) lr = (i == r) ? rowLab[i] : lr;
+#pragma unroll
+        for (int i = 0; i < RB; ++i) rowLab[i] = (i == r) ? cl : rowLab[i];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) colLab[j] = (j == c) ? lr : colLab[j];
     }
+#pragma unroll
     for (int l = 0; l < NP; ++l) lam[l] = F(0);
-    F z = F(0);
-    for (int r = 0; r < nr; ++r)
-        if (basis[r] < NP) {
-            const F v = tab[r * nc + rhs];
-            lam[basis[r]] = v > F(0) ? v : F(0);
-        }
-    for (int l = 0; l < NP; ++l) z += lam[l];
-    for (int r = 0; r < nr; ++r) {
-        const F v = -obj[NP + r];
-        y[r] = v > F(0) ? v : F(0);
-    }
-    value = z > F(0) ? F(1) / z - shift : F(0);
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+        for (int l = 0; l < NP; ++l)
+            if (rowLab[i] == l) lam[l] = pos_part(rhs[i]);
+#pragma unroll
+    for (int i = 0; i < RB; ++i) y[i] = F(0);
+#pragma unroll
+    for (int j = 0; j < NP; ++j)
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+            if (colLab[j] == NP + i) y[i] = pos_part(-d[j]);
     return optimal;
 }
 
-// Certificates from a game solution, for margins known to within band[r] of
-// the canonical ones (band = 0 for the canonical margins themselves) and
-// evaluated with unit roundoff uu.  hit: lambda >= 0 with every
-// (G^T lambda)_r + (sum lambda) band_r below zero beyond the evaluation's own
-// rounding.  miss: y >= 0 with every (G y)_l - sum_r y_r band_r above zero.
-template <typename F, int NP>
-CDEV bool certify_hit(const F* G, int nr, const F* band, const F* lam, F uu) {
-    F L = F(0);
-    for (int l = 0; l < NP; ++l) L += lam[l];
-    if (!(L > F(0))) return false;
-    const F k = F(2 * (NP + 2)) * uu;
-    for (int r = 0; r < nr; ++r) {
-        F s = F(0), a = F(0);
-        for (int l = 0; l < NP; ++l) {
-            s += lam[l] * G[l * nr + r];
-            a += lam[l] * (G[l * nr + r] < F(0) ? -G[l * nr + r] : G[l * nr + r]);
-        }
-        if (!(s + L * band[r] + k * a < F(0))) return false;
-    }
-    return true;
-}
-template <typename F, int NP>
-CDEV bool certify_miss(const F* G, int nr, const F* band, const F* y, F uu) {
-    F Y = F(0);
-    for (int r = 0; r < nr; ++r) Y += y[r] * band[r];
-    const F k = F(2 * (nr + 2)) * uu;
-    for (int l = 0; l < NP; ++l) {
-        F s = F(0), a = F(0);
-        for (int r = 0; r < nr; ++r) {
-            s += y[r] * G[l * nr + r];
-            a += y[r] * (G[l * nr + r] < F(0) ? -G[l * nr + r] : G[l * nr + r]);
-        }
-        if (!(s - Y - k * a > F(0))) return false;
-    }
-    return true;
+// Canonical FP64 half sum (left to right from 0, no FMA).
+template <int G>
+CDEV double half64(const double* coef, const double* x, int stride) {
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < G; ++c) s = __dadd_rn(s, __dmul_rn(coef[c], x[c * stride]));
+    return s;
 }
 
 // ---------------------------------------------------------------------------
-// Pass B: one thread per game-list entry.
+// Pass B: one thread per listed (edge, T, obstacle).  FP32 margins with their
+// bands (b_r +- band_r against the products A_r . P_l):
+//   a control point below every facet's b - band -> hit (Algorithm 2, first);
+//   a facet above b + band at every control point -> miss (second);
+// otherwise the game in registers (RB >= every obstacle's row count), then
+// its certificates (weak duality; margins within band_r of the canonical):
+//   hit:  lambda >= 0, L = sum lambda > 0, and for every r
+//         sum_l lambda_l G[l][r] + L band_r + 2 (NP + 2) u sum_l lambda_l |G[l][r]| < 0;
+//   miss: y >= 0 and for every l
+//         sum_r y_r G[l][r] - sum_r y_r band_r - 2 (RB + 2) u sum_r y_r |G[l][r]| > 0.
+// Uncertified entries go to the FP64 list with lambda and y.  The margins are
+// recomputed for the checks rather than kept in registers.
 // ---------------------------------------------------------------------------
-template <int M, int G, int PD>
-__global__ void __launch_bounds__(128) k_cut_lp32(CutParams C) {
+template <int M, int G, int PD, int RB>
+__global__ void __launch_bounds__(128) k_cut_pair(CutParams C) {
     constexpr int NP = PD + 1;
-    const long long n = block_count(C.info, &C.info->cut_lp, C.cap32);
+    const long long n = block_count(C.info, &C.info->cut_near, C.cap32);
     const long long stride = (long long)gridDim.x * blockDim.x;
+    unsigned long long n_s1 = 0, n_s2 = 0, n_games = 0;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
         const unsigned long long en = C.list32[k];
         const long long u = (long long)(en >> OBST_BITS);
@@ -496,46 +716,148 @@ __global__ void __launch_bounds__(128) k_cut_lp32(CutParams C) {
         float P[NP * M], S, lo[M], hi[M];
         unit_points<M, G, PD>(C, C.src[e], C.col_in[e], t, P, S, lo, hi);
         const int nr = C.ocount[o];
-        const float4* rw = reinterpret_cast<const float4*>(C.orow) + (long long)o * C.max_orows;
-        float Gm[NP * CUT_RMAX], band[CUT_RMAX];
-        for (int r = 0; r < nr; ++r) {
-            const float4 f = rw[r];
-            band[r] = band32<M>(f, S);
+        const long long rb = (long long)o * C.max_orows;
+        const float4* rw = reinterpret_cast<const float4*>(C.orow) + rb;
+        const float2* kw = reinterpret_cast<const float2*>(C.okb) + rb;
+        float T[RB][NP], band[RB];
+        bool inside[NP], sep = false;
 #pragma unroll
-            for (int l = 0; l < NP; ++l) Gm[l * nr + r] = margin32<M>(f, P + l * M);
+        for (int l = 0; l < NP; ++l) inside[l] = true;
+        float gmin = __int_as_float(0x7f800000);
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+            float bd = 0.f;
+            if (i < nr) {
+                f = __ldg(rw + i);
+                const float2 kb = __ldg(kw + i);
+                bd = fmaf(kb.x, S, kb.y);
+            }
+            band[i] = bd;
+            bool above = i < nr;
+#pragma unroll
+            for (int l = 0; l < NP; ++l) {
+                const float sv = dot32<M>(f, P + l * M);
+                T[i][l] = sv - f.w;
+                if (i < nr) {
+                    gmin = fminf(gmin, sv - f.w);
+                    inside[l] = inside[l] && sv <= f.w - bd;
+                    above = above && sv > f.w + bd;
+                }
+            }
+            sep = sep || above;
         }
-        float lam[NP], y[CUT_RMAX], val;
-        game_solve<float, NP>(Gm, nr, lam, y, val, 1e-6f);
-        if (certify_hit<float, NP>(Gm, nr, band, lam, U32)) {
+        bool in = false;
+#pragma unroll
+        for (int l = 0; l < NP; ++l) in = in || inside[l];
+        if (in) {
+            ++n_s1;
             atomicOr(&C.hit[e], 1u << t);
-        } else if (!certify_miss<float, NP>(Gm, nr, band, y, U32)) {
+            continue;
+        }
+        if (sep) {
+            ++n_s2;
+            continue;
+        }
+        ++n_games;
+        const float shift = 1.f - gmin;
+        float rhs[RB];
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+#pragma unroll
+            for (int l = 0; l < NP; ++l) T[i][l] = i < nr ? T[i][l] + shift : 0.f;
+            rhs[i] = i < nr ? 1.f : 0.f;
+        }
+        float lam[NP], y[RB];
+        game_reg<float, NP, RB>(T, rhs, lam, y, 1e-6f);
+        float L = 0.f;
+#pragma unroll
+        for (int l = 0; l < NP; ++l) L += lam[l];
+        bool hit_ok = L > 0.f;
+        float ks[NP], ka[NP], Y = 0.f;
+#pragma unroll
+        for (int l = 0; l < NP; ++l) ks[l] = ka[l] = 0.f;
+        const float kh = 2.f * (NP + 2) * U32, km = 2.f * (RB + 2) * U32;
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            if (i < nr) {
+                const float4 f = __ldg(rw + i);
+                float s = 0.f, a = 0.f;
+#pragma unroll
+                for (int l = 0; l < NP; ++l) {
+                    const float g = margin32<M>(f, P + l * M);
+                    s = fmaf(lam[l], g, s);
+                    a = fmaf(lam[l], fabsf(g), a);
+                    ks[l] = fmaf(y[i], g, ks[l]);
+                    ka[l] = fmaf(y[i], fabsf(g), ka[l]);
+                }
+                hit_ok = hit_ok && (s + L * band[i] + kh * a < 0.f);
+                Y = fmaf(y[i], band[i], Y);
+            }
+        }
+        bool miss_ok = true;
+#pragma unroll
+        for (int l = 0; l < NP; ++l) miss_ok = miss_ok && (ks[l] - Y - km * ka[l] > 0.f);
+        if (hit_ok) {
+            atomicOr(&C.hit[e], 1u << t);
+        } else if (!miss_ok) {
+            // to the FP64 pass, with this game's mixes as certificate candidates
             const unsigned long long idx = atomicAdd(&C.info->cut_lp64, 1ull);
-            if (idx < (unsigned long long)C.cap64) C.list64[idx] = en;
+            if (idx < (unsigned long long)C.cap64) {
+                C.list64[idx] = en;
+                float* ly = C.lamy + idx * LAMY_STRIDE;
+#pragma unroll
+                for (int l = 0; l < NP; ++l) ly[l] = lam[l];
+#pragma unroll
+                for (int r = 0; r < RB; ++r) ly[NP + r] = r < nr ? y[r] : 0.f;
+            }
         }
     }
+    cut_block_add(&C.info->cut_step1, n_s1);
+    cut_block_add(&C.info->cut_step2, n_s2);
+    cut_block_add(&C.info->cut_games, n_games);
 }
 
 // ---------------------------------------------------------------------------
-// Pass C: canonical FP64 margins (the oracle's order: each control-point half
-// summed left to right from 0, halves added; facet products summed left to
-// right from 0, then b subtracted; no FMA), Algorithm 2's two checks, the
-// game with exact-rounding certificates, ties by the value's sign.
+// Pass C: one warp per entry.  Canonical FP64 margins (the oracle's order:
+// each control-point half summed left to right from 0, halves added; facet
+// products summed left to right from 0, then b subtracted; no FMA): lane k
+// computes control-point coordinate k, lane r then facet r's margins.
+// Algorithm 2's two checks exactly, then the FP32 game's mixes as
+// certificates, then the game itself with the warp as the tableau (lane r =
+// basic row r) and exact-rounding certificates; a game certified neither way
+// is a tie, decided by the sign of its computed value.
+// GB300's FP64 pipe is narrow, so the pass keeps its FP64 instruction count
+// low: the coordinates are computed once per warp, not once per lane, and the
+// reciprocals come from an FP32 estimate and two Newton steps.
 // ---------------------------------------------------------------------------
-template <int G>
-CDEV double half64(const double* coef, const double* x, int stride) {
-    double s = 0.0;
-#pragma unroll
-    for (int c = 0; c < G; ++c) s = __dadd_rn(s, __dmul_rn(coef[c], x[c * stride]));
-    return s;
+CDEV double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// 1 / x for the pivots (|x| within FP32 range): FP32 estimate, two Newton
+// steps (the pivot values only choose and scale pivots; the certificates
+// re-check whatever comes out).
+CDEV double rcp64(double x) {
+    double r = (double)__frcp_rn((float)x);
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
 }
 
 template <int M, int G, int PD>
 __global__ void __launch_bounds__(128) k_cut_lp64(CutParams C) {
     constexpr int N_ = M * G, NP = PD + 1, TG = 2 * G;
+    static_assert(NP * M <= 32, "one control-point coordinate per lane");
     const long long n = block_count(C.info, &C.info->cut_lp64, C.cap64);
-    const long long stride = (long long)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const double inf = __longlong_as_double(0x7FF0000000000000ll);
     unsigned long long n_ties = 0;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+    for (long long k = gw; k < n; k += nw) {
         const unsigned long long en = C.list64[k];
         const long long u = (long long)(en >> OBST_BITS);
         const int o = (int)(en & ((1ull << OBST_BITS) - 1ull));
@@ -543,58 +865,193 @@ __global__ void __launch_bounds__(128) k_cut_lp64(CutParams C) {
         const int t = (int)(u - e * C.nT);
         if ((*(volatile const uint32_t*)(C.hit + e) >> t) & 1u) continue;
         const long long i = C.src[e], j = C.col_in[e];
-        double xi[N_], xj[N_];
+        // lane k < NP * M: coordinate a = k % M of control point l = k / M
+        double pk = 0.0;
+        if (lane < NP * M) {
+            const int l = lane / M, a = lane - l * M;
+            const double* D = C.tab64 + (long long)t * C.L.e_stride + C.L.e_D + l * TG;
+            double xi[G], xj[G];
 #pragma unroll
-        for (int c = 0; c < N_; ++c) {
-            xi[c] = ld64(C.states, i * N_ + c, C.in_f32);
-            xj[c] = ld64(C.states, j * N_ + c, C.in_f32);
+            for (int c = 0; c < G; ++c) {
+                xi[c] = ld64(C.states, i * N_ + c * M + a, C.in_f32);
+                xj[c] = ld64(C.states, j * N_ + c * M + a, C.in_f32);
+            }
+            pk = __dadd_rn(half64<G>(D, xi, 1), half64<G>(D + G, xj, 1));
         }
-        const double* D = C.tab64 + (long long)t * C.L.e_stride + C.L.e_D;
         double P[NP * M];
 #pragma unroll
-        for (int l = 0; l < NP; ++l)
-#pragma unroll
-            for (int a = 0; a < M; ++a)
-                P[l * M + a] = __dadd_rn(half64<G>(D + l * TG, xi + a, M), half64<G>(D + l * TG + G, xj + a, M));
+        for (int q = 0; q < NP * M; ++q) P[q] = __shfl_sync(0xffffffffu, pk, q);
         const int r0 = C.obst_off[o], nr = C.ocount[o];
-        double Gm[NP * CUT_RMAX], zero[CUT_RMAX];
-        for (int r = 0; r < nr; ++r) {
-            zero[r] = 0.0;
-            const double br = ld64(C.b, r0 + r, C.in_f32);
+        const bool mine = lane < nr;
+        double g[NP];
+#pragma unroll
+        for (int l = 0; l < NP; ++l) g[l] = 0.0;
+        if (mine) {
+            const double br = ld64(C.b, r0 + lane, C.in_f32);
             double Ar[M];
 #pragma unroll
-            for (int a = 0; a < M; ++a) Ar[a] = ld64(C.A, (long long)(r0 + r) * M + a, C.in_f32);
+            for (int a = 0; a < M; ++a) Ar[a] = ld64(C.A, (long long)(r0 + lane) * M + a, C.in_f32);
 #pragma unroll
             for (int l = 0; l < NP; ++l) {
                 double s = 0.0;
 #pragma unroll
                 for (int a = 0; a < M; ++a) s = __dadd_rn(s, __dmul_rn(Ar[a], P[l * M + a]));
-                Gm[l * nr + r] = __dsub_rn(s, br);
+                g[l] = __dsub_rn(s, br);
             }
         }
         int verdict = 0;  // 1 hit, -1 miss
-        for (int l = 0; l < NP && verdict == 0; ++l) {  // a control point inside
-            bool in = true;
-            for (int r = 0; r < nr; ++r) in = in && Gm[l * nr + r] <= 0.0;
-            if (in) verdict = 1;
+#pragma unroll
+        for (int l = 0; l < NP; ++l)  // a control point with every margin <= 0
+            if (__ballot_sync(0xffffffffu, mine && !(g[l] <= 0.0)) == 0u) verdict = 1;
+        if (verdict == 0) {  // one facet with every margin > 0
+            bool out = mine;
+#pragma unroll
+            for (int l = 0; l < NP; ++l) out = out && g[l] > 0.0;
+            if (__ballot_sync(0xffffffffu, out) != 0u) verdict = -1;
         }
-        for (int r = 0; r < nr && verdict == 0; ++r) {  // one separating facet
-            bool out = true;
-            for (int l = 0; l < NP; ++l) out = out && Gm[l * nr + r] > 0.0;
-            if (out) verdict = -1;
+        if (verdict == 0 && k < C.cap64) {  // the FP32 game's mixes on the canonical margins
+            const float* ly = C.lamy + k * LAMY_STRIDE;
+            double L = 0.0, s = 0.0, a = 0.0;
+#pragma unroll
+            for (int l = 0; l < NP; ++l) {
+                const double lm = (double)ly[l];
+                L += lm;
+                s += lm * g[l];
+                a += lm * fabs(g[l]);
+            }
+            const double kh = 2.0 * (NP + 2) * U64, km = 2.0 * (32 + 2) * U64;
+            if (L > 0.0 && __ballot_sync(0xffffffffu, mine && !(s + kh * a < 0.0)) == 0u) verdict = 1;
+            if (verdict == 0) {
+                const double yr = mine ? (double)ly[NP + lane] : 0.0;
+                bool miss_ok = true;
+#pragma unroll
+                for (int l = 0; l < NP; ++l) {
+                    const double ks = warp_sum(yr * g[l]), ka = warp_sum(yr * fabs(g[l]));
+                    miss_ok = miss_ok && (ks - km * ka > 0.0);
+                }
+                if (miss_ok) verdict = -1;
+            }
         }
         if (verdict == 0) {
-            double lam[NP], y[CUT_RMAX], val;
-            game_solve<double, NP>(Gm, nr, lam, y, val, 1e-13);
-            if (certify_hit<double, NP>(Gm, nr, zero, lam, U64)) verdict = 1;
-            else if (certify_miss<double, NP>(Gm, nr, zero, y, U64)) verdict = -1;
+            double gmin = inf;
+#pragma unroll
+            for (int l = 0; l < NP; ++l) gmin = mine ? fmin(gmin, g[l]) : gmin;
+            for (int of = 16; of > 0; of >>= 1) gmin = fmin(gmin, __shfl_xor_sync(0xffffffffu, gmin, of));
+            const double shift = 1.0 - gmin;
+            double T[NP], rhs = mine ? 1.0 : 0.0, d[NP];
+            int colLab[NP], rowLab = NP + lane;
+#pragma unroll
+            for (int l = 0; l < NP; ++l) {
+                T[l] = mine ? g[l] + shift : 0.0;
+                d[l] = 1.0;
+                colLab[l] = l;
+            }
+            const double tol = 1e-13;
+            for (int it = 0; it < GAME_ITERS; ++it) {
+                int c = -1, cl = 1 << 20;
+                double dbest = tol;
+                if (it < GAME_DANTZIG) {
+#pragma unroll
+                    for (int l = 0; l < NP; ++l)
+                        if (d[l] > dbest) {
+                            c = l;
+                            dbest = d[l];
+                        }
+                    if (c >= 0) {
+#pragma unroll
+                        for (int l = 0; l < NP; ++l) cl = (l == c) ? colLab[l] : cl;
+                    }
+                } else {
+#pragma unroll
+                    for (int l = 0; l < NP; ++l)
+                        if (d[l] > tol && colLab[l] < cl) {
+                            c = l;
+                            cl = colLab[l];
+                        }
+                }
+                if (c < 0) break;
+                double colc = T[0];
+#pragma unroll
+                for (int l = 1; l < NP; ++l) colc = (l == c) ? T[l] : colc;
+                const bool ok = mine && colc > tol;
+                double best = ok ? rhs * rcp64(colc) : inf;
+                int bl = ok ? rowLab : (1 << 20), bi = lane;
+                for (int of = 16; of > 0; of >>= 1) {
+                    const double ob = __shfl_xor_sync(0xffffffffu, best, of);
+                    const int obl = __shfl_xor_sync(0xffffffffu, bl, of);
+                    const int obi = __shfl_xor_sync(0xffffffffu, bi, of);
+                    if (ob < best || (ob == best && obl < bl)) {
+                        best = ob;
+                        bl = obl;
+                        bi = obi;
+                    }
+                }
+                if (!(best < inf)) break;  // unbounded: impossible with payoffs >= 1
+                const int r = bi;
+                const double p = __shfl_sync(0xffffffffu, colc, r);
+                const double inv = rcp64(p);
+                double rs[NP];
+#pragma unroll
+                for (int l = 0; l < NP; ++l) {
+                    const double v = __shfl_sync(0xffffffffu, T[l], r);
+                    rs[l] = (l == c) ? inv : v * inv;
+                }
+                const double rhs_s = __shfl_sync(0xffffffffu, rhs, r) * inv;
+                const int lr = __shfl_sync(0xffffffffu, rowLab, r);
+                if (lane == r) {
+#pragma unroll
+                    for (int l = 0; l < NP; ++l) T[l] = rs[l];
+                    rhs = rhs_s;
+                    rowLab = cl;
+                } else {
+#pragma unroll
+                    for (int l = 0; l < NP; ++l) T[l] = ((l == c) ? 0.0 : T[l]) - colc * rs[l];
+                    rhs = rhs - colc * rhs_s;
+                }
+                double dc = d[0];
+#pragma unroll
+                for (int l = 1; l < NP; ++l) dc = (l == c) ? d[l] : dc;
+#pragma unroll
+                for (int l = 0; l < NP; ++l) {
+                    d[l] = ((l == c) ? 0.0 : d[l]) - dc * rs[l];
+                    colLab[l] = (l == c) ? lr : colLab[l];
+                }
+            }
+            double lam[NP], L = 0.0;
+#pragma unroll
+            for (int l = 0; l < NP; ++l) {
+                lam[l] = warp_sum(rowLab == l ? pos_part(rhs) : 0.0);
+                L += lam[l];
+            }
+            double yr = 0.0;  // this lane's facet weight
+#pragma unroll
+            for (int l = 0; l < NP; ++l)
+                if (colLab[l] == NP + lane) yr = pos_part(-d[l]);
+            if (!mine) yr = 0.0;
+            const double kh = 2.0 * (NP + 2) * U64, km = 2.0 * (32 + 2) * U64;
+            double s = 0.0, a = 0.0;
+#pragma unroll
+            for (int l = 0; l < NP; ++l) {
+                s += lam[l] * g[l];
+                a += lam[l] * fabs(g[l]);
+            }
+            const bool hit_ok = L > 0.0 && __ballot_sync(0xffffffffu, mine && !(s + kh * a < 0.0)) == 0u;
+            bool miss_ok = true;
+#pragma unroll
+            for (int l = 0; l < NP; ++l) {
+                const double ks = warp_sum(yr * g[l]), ka = warp_sum(yr * fabs(g[l]));
+                miss_ok = miss_ok && (ks - km * ka > 0.0);
+            }
+            if (hit_ok) verdict = 1;
+            else if (miss_ok) verdict = -1;
             else {
-                verdict = val <= 0.0 ? 1 : -1;
+                verdict = (L > 0.0 && 1.0 / L - shift <= 0.0) ? 1 : -1;
                 ++n_ties;
             }
         }
-        if (verdict == 1) atomicOr(&C.hit[e], 1u << t);
+        if (verdict == 1 && lane == 0) atomicOr(&C.hit[e], 1u << t);
     }
+    if (lane != 0) n_ties = 0;
     cut_block_add(&C.info->cut_ties, n_ties);
 }
 
@@ -689,7 +1146,7 @@ __global__ void __launch_bounds__(1024) k_cut_offsets(CutParams C) {
         C.chunk[nch] = total;
         if (!cut_failed(C.info)) {
             *C.count_out = total;
-            if (C.info->cut_lp > (unsigned long long)C.cap32 || C.info->cut_lp64 > (unsigned long long)C.cap64)
+            if (C.info->cut_near > (unsigned long long)C.cap32 || C.info->cut_lp64 > (unsigned long long)C.cap64)
                 cut_status(C.info, PLAN_ERR_CAPACITY, DET_CUTLIST);
             else if (total > C.cap_out)
                 cut_status(C.info, PLAN_ERR_CAPACITY, DET_OUTPUT);
@@ -793,19 +1250,20 @@ __global__ void k_cut_rows(CutParams C) {
 }
 
 template <int M, int G, int PD>
-int launch_cut_t(const CutParams& C, cudaStream_t st, int num_sms, int* launches) {
-    const int row_blocks = (int)((((long long)C.N * 32 + 255) / 256) < num_sms * 8 ? ((long long)C.N * 32 + 255) / 256
-                                                                                   : num_sms * 8);
+int launch_cut_t(const CutParams& C, cudaStream_t st, int num_sms, int* launches, cudaEvent_t e0, cudaEvent_t e1) {
+    const long long rb = ((long long)C.N * 32 + 255) / 256;
+    const int row_blocks = (int)(rb < num_sms * 8 ? (rb > 0 ? rb : 1) : num_sms * 8);
     const long long orows = (long long)C.n_obst * C.max_orows;
     const int obst_blocks = (int)((orows + 255) / 256);
-    const int prep_blocks = (row_blocks > 0 ? row_blocks : 1) + obst_blocks;
-    k_cut_prep<<<prep_blocks, 256, 0, st>>>(C, row_blocks > 0 ? row_blocks : 1);
-    const long long units = C.cap_in * C.nT;
-    long long ga = (units + 31) / 32;
-    if (ga > (long long)num_sms * 8) ga = (long long)num_sms * 8;
-    if (ga < 1) ga = 1;
-    k_cut_scan<M, G, PD><<<(int)ga, 256, 0, st>>>(C);
-    k_cut_lp32<M, G, PD><<<num_sms * 4, 128, 0, st>>>(C);
+    k_cut_prep<<<row_blocks + obst_blocks, 256, 0, st>>>(C, row_blocks);
+    if (C.n_obst > 0) k_cut_obox<M><<<(C.n_obst + 3) / 4, 128, 0, st>>>(C);
+    // pass A: a grid-stride loop over (256-unit group, obstacle stripe) items
+    const int ga = num_sms * 8;
+    if (e0) cudaEventRecord(e0, st);
+    k_cut_scan<M, G, PD><<<ga, 256, 0, st>>>(C, num_sms * 6);
+    if (e1) cudaEventRecord(e1, st);
+    if (C.max_orows <= 8) k_cut_pair<M, G, PD, 8><<<num_sms * 4, 128, 0, st>>>(C);
+    else k_cut_pair<M, G, PD, CUT_RMAX><<<num_sms * 4, 128, 0, st>>>(C);
     k_cut_lp64<M, G, PD><<<num_sms, 128, 0, st>>>(C);
     long long gc = C.nchunks < (long long)num_sms * 4 ? C.nchunks : (long long)num_sms * 4;
     if (gc < 1) gc = 1;
@@ -813,18 +1271,19 @@ int launch_cut_t(const CutParams& C, cudaStream_t st, int num_sms, int* launches
     k_cut_offsets<<<1, 1024, 0, st>>>(C);
     k_cut_fill<M, G, PD><<<(int)gc, FILL_THREADS, 0, st>>>(C);
     k_cut_rows<<<(int)((C.N + 1 + 255) / 256), 256, 0, st>>>(C);
-    *launches += 8;
+    *launches += C.n_obst > 0 ? 9 : 8;
     return (int)cudaGetLastError();
 }
 
 }  // namespace
 
-int launch_cut(const CutParams& C, void* stream, int num_sms, int* launches) {
+int launch_cut(const CutParams& C, void* stream, int num_sms, int* launches, void* ev_scan_begin, void* ev_scan_end) {
     cudaStream_t st = (cudaStream_t)stream;
-    if (C.m == 2 && C.g == 2 && C.p == 3) return launch_cut_t<2, 2, 3>(C, st, num_sms, launches);
-    if (C.m == 2 && C.g == 2 && C.p == 5) return launch_cut_t<2, 2, 5>(C, st, num_sms, launches);
-    if (C.m == 3 && C.g == 3 && C.p == 5) return launch_cut_t<3, 3, 5>(C, st, num_sms, launches);
-    if (C.m == 3 && C.g == 3 && C.p == 7) return launch_cut_t<3, 3, 7>(C, st, num_sms, launches);
+    cudaEvent_t e0 = (cudaEvent_t)ev_scan_begin, e1 = (cudaEvent_t)ev_scan_end;
+    if (C.m == 2 && C.g == 2 && C.p == 3) return launch_cut_t<2, 2, 3>(C, st, num_sms, launches, e0, e1);
+    if (C.m == 2 && C.g == 2 && C.p == 5) return launch_cut_t<2, 2, 5>(C, st, num_sms, launches, e0, e1);
+    if (C.m == 3 && C.g == 3 && C.p == 5) return launch_cut_t<3, 3, 5>(C, st, num_sms, launches, e0, e1);
+    if (C.m == 3 && C.g == 3 && C.p == 7) return launch_cut_t<3, 3, 7>(C, st, num_sms, launches, e0, e1);
     return (int)cudaErrorInvalidValue;
 }
 

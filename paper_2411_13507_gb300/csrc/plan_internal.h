@@ -74,13 +74,14 @@ struct DevInfo {
     unsigned long long bar[3];       // grid-barrier words, used in rotation: arrivals | raised flags << 32
     int path_len;
     unsigned long long work[3];
-    // keep-out cut counters
+    // keep-out cut counters (contiguous: cleared together)
     unsigned long long cut_units;    // (edge, T) checked
-    unsigned long long cut_tests;    // (edge, T, obstacle) evaluated
-    unsigned long long cut_box;      // missed by the bounding-box screen
+    unsigned long long cut_tests;    // (edge, T, obstacle) screened
+    unsigned long long cut_box;      // missed by the obstacles' certified boxes
+    unsigned long long cut_near;     // entries of the pair list (the rest)
     unsigned long long cut_step1;    // hit: a control point inside (FP32, certain)
     unsigned long long cut_step2;    // missed: one separating facet (FP32, certain)
-    unsigned long long cut_lp;       // entries of the FP32 matrix-game list
+    unsigned long long cut_games;    // matrix games solved in FP32
     unsigned long long cut_lp64;     // entries of the FP64 list
     unsigned long long cut_ties;     // FP64 games without a certificate either way
 };
@@ -277,6 +278,9 @@ struct CutParams {
     const void* A;
     const void* b;
     float* orow;               // [n_obst * max_orows][4] {A_0, A_1, A_2 (0 when m = 2), b}, 16-byte aligned
+    float* okb;                // [n_obst * max_orows][2] band coefficients {K ||A_r||_1, K |b_r|}
+    float* obox;               // [n_obst][8] certified bounds {lo_0, lo_1, lo_2, -, hi_0, hi_1, hi_2, -}
+                               // (m = 2: {lo_0, lo_1, hi_0, hi_1} in the first four)
     int* ocount;               // [n_obst] rows of each obstacle
     const double* tab64;       // [nT][L.e_stride] canonical tables (control points, cost rows)
     const float* tab32;        // [nT][(p+1) * 2g] FP32 control-point table
@@ -287,6 +291,7 @@ struct CutParams {
     long long cap32;
     unsigned long long* list64;
     long long cap64;
+    float* lamy;               // [cap64][32] the FP32 game's lambda and y of each FP64-list entry
     long long* chunk;          // [nchunks + 1] kept edges per chunk, then their exclusive prefix
     int32_t* pos;              // [cap_in + 1] output index of each edge (exclusive prefix of kept)
     long long nchunks;
@@ -303,6 +308,6 @@ bool model_supported(int m, int g, int p);
 bool tc_supported(int m, int g, int p);
 bool refine_supported(int m, int g, int p);
 int launch_refine(const RefineParams& R, void* stream, int* launches);
-int launch_cut(const CutParams& C, void* stream, int num_sms, int* launches);
+int launch_cut(const CutParams& C, void* stream, int num_sms, int* launches, void* ev_scan_begin, void* ev_scan_end);
 
 }  // namespace plan

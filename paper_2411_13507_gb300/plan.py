@@ -53,8 +53,9 @@ class _Info(ctypes.Structure):
                 ("goal", ctypes.c_int32), ("need_slots", ctypes.c_int64), ("need_rechecks", ctypes.c_int64),
                 ("work_reach_rows", ctypes.c_int64), ("work_free_rows", ctypes.c_int64), ("work_costs", ctypes.c_int64),
                 ("screened", ctypes.c_int64), ("cut_units", ctypes.c_int64), ("cut_tests", ctypes.c_int64),
-                ("cut_box", ctypes.c_int64), ("cut_step1", ctypes.c_int64), ("cut_step2", ctypes.c_int64),
-                ("cut_lp", ctypes.c_int64), ("cut_lp64", ctypes.c_int64), ("cut_ties", ctypes.c_int64)]
+                ("cut_box", ctypes.c_int64), ("cut_near", ctypes.c_int64), ("cut_step1", ctypes.c_int64),
+                ("cut_step2", ctypes.c_int64), ("cut_games", ctypes.c_int64), ("cut_lp64", ctypes.c_int64),
+                ("cut_ties", ctypes.c_int64)]
 
 
 class _Obstacles(ctypes.Structure):
@@ -82,7 +83,7 @@ class _RefineW(ctypes.Structure):
 EXPORTS = ["plan_create", "plan_destroy", "plan_build_edges", "plan_search", "plan_wait", "plan_model_tables",
            "plan_set_search_limits", "plan_refine", "plan_prepare_batched", "plan_build_edges_batched",
            "plan_set_tile", "plan_autotune", "plan_prepare_search_batched", "plan_search_batched",
-           "plan_search_noalloc", "plan_cut_edges", "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
+           "plan_search_noalloc", "plan_cut_edges", "plan_cut_timing", "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
 
 
 def lib_path() -> str:
@@ -128,6 +129,8 @@ def load(build_if_stale: bool = True):
     lib.plan_cut_edges.argtypes = [vp, i32, vp, i32, dp, ctypes.POINTER(_Edges), ctypes.POINTER(_Obstacles),
                                    ctypes.POINTER(_Edges)]
     lib.plan_cut_edges.restype = i32
+    lib.plan_cut_timing.argtypes = [vp, dp, dp, ctypes.POINTER(i64), i32]
+    lib.plan_cut_timing.restype = i32
     lib.plan_set_tile.argtypes = [vp, i32, i32, i32, i32]
     lib.plan_set_tile.restype = i32
     lib.plan_autotune.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
@@ -556,3 +559,10 @@ class Planner:
             raise self._err(rc, "plan_timing")
         return {"pair_ms": pm.value, "pair_launches": pl.value, "search_ms": sm.value,
                 "search_launches": sl.value, "launches": tl.value}
+
+    def cut_timing(self, reset: bool = True) -> dict:
+        a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        rc = self.lib.plan_cut_timing(self.ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n), 1 if reset else 0)
+        if rc != 0:
+            raise self._err(rc, "plan_cut_timing")
+        return {"scan_ms": a.value, "cut_ms": b.value, "cuts": n.value}

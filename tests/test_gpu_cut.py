@@ -51,8 +51,8 @@ def check(prob, obs, arith, input=None, rows=None):
     st = parity.compare_rows(gpu, orc, rows, prob.nT, arith)
     assert info["cut_ties"] == 0
     assert info["cut_units"] == int(sum(bin(int(x)).count("1") for x in csr["mask"]))
-    decided = info["cut_box"] + info["cut_step1"] + info["cut_step2"] + info["cut_lp"]
-    assert decided == info["cut_tests"]
+    assert info["cut_box"] + info["cut_near"] == info["cut_tests"]
+    assert info["cut_step1"] + info["cut_step2"] + info["cut_games"] <= info["cut_near"]
     return st, info, orc, gpu, g, out
 
 
@@ -62,7 +62,7 @@ def test_keepout_fp64_all_rows(seed):
     prob, obs = synth.keepout_2d(seed, N=600, n_obst=60)
     st, info, orc, gpu, g, out = check(prob, obs, "f64")
     assert 0 < len(gpu["col"]) < g.E
-    assert orc["steps"][3] > 0 and info["cut_lp"] > 0
+    assert orc["steps"][3] > 0 and info["cut_games"] > 0
 
 
 @pytest.mark.parametrize("seed", [1, 2])
@@ -187,3 +187,29 @@ def test_cut_then_search_matches_oracle():
     r = pl.search(dp, out)
     o = oracle.search(op, ocsr, prob.start_pos, prob.goal_pos)
     parity.compare_search(r, o, ocsr, "f64")
+
+
+def test_near_tie_games_go_through_the_fp64_pass():
+    """Curves that miss or graze an obstacle corner by 1e-7 (far inside the
+    FP32 bands): the FP32 passes cannot decide them, the canonical FP64 pass
+    must, and no game may end as a tie."""
+    prob, _ = synth.keepout_2d(11, N=60, n_obst=1, width=4.0)
+    prob.states[:, 2:] = 0.0                 # at rest: every curve is a segment
+    prob.model.bounds = (50.0, 500.0)        # every pair reachable
+    rng = np.random.default_rng(11)
+    A, b, off = [], [], [0]
+    for k in range(24):
+        i, j = rng.choice(prob.N, 2, replace=False)
+        p, q = prob.states[i, :2], prob.states[j, :2]
+        dvec = q - p
+        nrm = np.array([dvec[1], -dvec[0]]) / np.hypot(*dvec)
+        d = 1e-7 if k % 2 == 0 else -1e-7   # miss / overlap by 1e-7
+        c = 0.5 * (p + q) + d * nrm
+        sx, sy = np.sign(nrm[0]) or 1.0, np.sign(nrm[1]) or 1.0
+        # the quadrant at corner c facing away from the segment
+        A += [[sx, 0.0], [-sx, 0.0], [0.0, sy], [0.0, -sy]]
+        b += [sx * c[0] + 0.3, -sx * c[0], sy * c[1] + 0.3, -sy * c[1]]
+        off.append(off[-1] + 4)
+    obs = synth.Obstacles(np.array(off, dtype=np.int32), np.array(A), np.array(b))
+    st, info, orc, gpu, g, out = check(prob, obs, "f64")
+    assert info["cut_lp64"] > 0 and info["cut_ties"] == 0
