@@ -359,7 +359,6 @@ def run_cut_form(args, stream, flush, dev):
     from paper_2411_13507_gb300 import plan as P
     from paper_2411_13507_gb300 import synth
     prob, obs = synth.keepout_2d(seed=1)
-    cpu = None if args.no_cpu_baseline else cut_cpu_baseline(prob, obs)
     pl = P.Planner.for_problem(prob, arith="f64", input="f64", stream=stream)
     dp = P.to_device(prob, input="f64")
     g = pl.build_edges(dp)
@@ -422,6 +421,9 @@ def run_cut_form(args, stream, flush, dev):
         assert st in (P.PLAN_OK, P.PLAN_ERR_NO_PATH)
         if s >= args.warmup:
             e2e.append(e0.elapsed_time(e1))
+    # the oracle's bounded sample, after every GPU timing (its host threads
+    # must not share the cores with the launches being timed)
+    cpu = None if args.no_cpu_baseline else cut_cpu_baseline(prob, obs)
     cut_ms = statistics.mean(cms)
     scan_ms = ct["scan_ms"] / max(1, ct["cuts"])
     # roofline of the screening pass (the bounding-box test of every (edge, T)

@@ -119,10 +119,8 @@ struct plan_ctx {
     float* cut_okb = nullptr;
     float* cut_obox = nullptr;
     int* cut_ocount = nullptr;
-    long long cut32Cap = 0, cut64Cap = 0, want_cut32 = 0, want_cut64 = 0;
+    long long cut32Cap = 0, want_cut32 = 0;
     unsigned long long* cut_list32 = nullptr;
-    unsigned long long* cut_list64 = nullptr;
-    float* cut_lamy = nullptr;
     // timing
     bool timing = false;
     bool accounting = false;
@@ -392,7 +390,7 @@ void plan_destroy(plan_ctx* c) {
                    c->resBits, c->resKey, c->emitPre, c->recheck, c->sdist, c->sbest, c->spred, c->sfront, c->slast, c->snear,
                    c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem, c->d_qMem, c->d_sqd, c->memOff,
                    c->d_cut64, c->d_cut32, c->cut_src, c->cut_hit, c->cut_pos, c->cut_chunk, c->cut_orow,
-                   c->cut_ocount, c->cut_list32, c->cut_list64, c->cut_okb, c->cut_obox, c->cut_lamy};
+                   c->cut_ocount, c->cut_list32, c->cut_okb, c->cut_obox};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_tab64) cudaFreeHost(c->h_tab64);
@@ -932,20 +930,12 @@ int plan_cut_edges(plan_ctx* c, int N, const void* states, int nT, const double*
         c->capCutR = nob * maxr;
     }
     const long long w32 = c->want_cut32 > 0 ? c->want_cut32 : (1LL << 18);
-    const long long w64 = c->want_cut64 > 0 ? c->want_cut64 : (1LL << 14);
     if (w32 > c->cut32Cap) {
         if (!dalloc(c, &c->cut_list32, w32)) {
             c->cut32Cap = 0;
             return PLAN_ERR_NO_MEMORY;
         }
         c->cut32Cap = w32;
-    }
-    if (w64 > c->cut64Cap) {
-        if (!dalloc(c, &c->cut_list64, w64) || !dalloc(c, &c->cut_lamy, 32 * w64)) {
-            c->cut64Cap = 0;
-            return PLAN_ERR_NO_MEMORY;
-        }
-        c->cut64Cap = w64;
     }
     CutParams C;
     memset(&C, 0, sizeof(C));
@@ -988,9 +978,6 @@ int plan_cut_edges(plan_ctx* c, int N, const void* states, int nT, const double*
     C.hit = c->cut_hit;
     C.list32 = c->cut_list32;
     C.cap32 = c->cut32Cap;
-    C.list64 = c->cut_list64;
-    C.cap64 = c->cut64Cap;
-    C.lamy = c->cut_lamy;
     C.chunk = c->cut_chunk;
     C.pos = c->cut_pos;
     C.nchunks = nchunks;
@@ -1183,7 +1170,6 @@ int plan_wait(plan_ctx* c, plan_info* info) {
         }
         if (d.detail == DET_CUTLIST) {
             c->want_cut32 = (long long)(d.cut_near + d.cut_near / 4 + 4096);
-            c->want_cut64 = (long long)(d.cut_lp64 + d.cut_lp64 / 4 + 1024);
         }
     }
     if (info) {

@@ -14,7 +14,7 @@
 // margins (halves summed left to right without FMA, as in the edge build);
 // the FP32 passes take only the decisions that their error bands prove.
 //
-//  Boxes (k_cut_obox): a certified bounding box of every obstacle, each side
+//  Boxes (in k_cut_prep): a certified bounding box of every obstacle, each side
 //    backed by a dual vector y >= 0 with A^T y = +-e_a (a certificate of the
 //    game for every curve beyond that side).
 //  Pass A (k_cut_scan): one lane per (edge, T); FP32 control points, their
@@ -25,13 +25,12 @@
 //    certainly separating -> miss), else the game by the simplex method in
 //    registers.  Weak duality turns its solution into certificates: any
 //    lambda >= 0 with G^T lambda < 0 proves a hit, any y >= 0 with G y > 0 a
-//    miss; both are checked against G's error bands.  Uncertified entries go
-//    to pass C.
-//  Pass C (k_cut_lp64): one warp per entry (lane = facet): canonical FP64
-//    margins, Algorithm 2's two checks exactly, then the game in FP64 with
-//    certificates against the rounding of the check itself.  A game certified
-//    neither way has |delta*| at the rounding level: a tie, decided by the
-//    sign of the computed value and counted.
+//    miss; both are checked against G's error bands.
+//  FP64 settling (in pass B, by the whole warp): canonical FP64 margins,
+//    Algorithm 2's two checks exactly, the FP32 game's mixes as certificates,
+//    then the game in FP64 with certificates against the rounding of the
+//    check itself.  A game certified neither way has |delta*| at the rounding
+//    level: a tie, decided by the sign of the computed value and counted.
 //  Compaction: kept = mask & ~hit != 0; chunk counts, one scan, the fill (an
 //    edge whose cheapest duration was cut is re-costed in canonical FP64 over
 //    the durations left), the row offsets.
@@ -58,7 +57,6 @@ constexpr double U64 = 1.1102230246251565e-16;  // 2^-53
 constexpr float KO = 32.f * U32;
 constexpr int GAME_ITERS = 96;  // simplex pivots before an entry is handed on
 constexpr unsigned long long OBST_BITS = 20;
-constexpr int LAMY_STRIDE = 32;  // floats per FP64-list entry: lambda (p + 1 <= 16) then y (<= 16 rows)
 
 CDEV void cut_status(DevInfo* info, int code, int detail) {
     if (atomicCAS(&info->status, 0, code) == 0) atomicExch(&info->detail, detail);
@@ -178,59 +176,7 @@ CDEV float band32(const float4& f, float S) {
 }
 
 // ---------------------------------------------------------------------------
-// Prep: start vertex of every edge, cleared hit bits (one warp per row), and
-// the obstacles' FP32 rows, max_orows per obstacle, with row-count checks.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_cut_prep(CutParams C, int row_blocks) {
-    if ((int)blockIdx.x < row_blocks) {
-        const long long E = block_edges(C);
-        const int lane = threadIdx.x & 31;
-        const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        const long long nw = ((long long)row_blocks * blockDim.x) >> 5;
-        if (E == 0) return;
-        // the CSR must cover exactly edges 0..E-1 with end vertices below N
-        // (every later pass indexes states with them)
-        if (w0 == 0 && lane == 0 && (C.row_in[0] != 0 || (long long)C.row_in[C.N] != E))
-            cut_status(C.info, PLAN_ERR_INVALID_ARG, DET_CUTIN);
-        for (long long i = w0; i < C.N; i += nw) {
-            const long long a = C.row_in[i], b = C.row_in[i + 1];
-            if (a < 0 || b < a || b > E) {
-                if (lane == 0) cut_status(C.info, PLAN_ERR_INVALID_ARG, DET_CUTIN);
-                continue;
-            }
-            for (long long e = a + lane; e < b; e += 32) {
-                C.src[e] = (int32_t)i;
-                C.hit[e] = 0u;
-                if ((unsigned)C.col_in[e] >= (unsigned)C.N) cut_status(C.info, PLAN_ERR_INVALID_ARG, DET_CUTIN);
-            }
-        }
-        return;
-    }
-    const long long u = ((long long)blockIdx.x - row_blocks) * blockDim.x + threadIdx.x;
-    if (u >= (long long)C.n_obst * C.max_orows) return;
-    const int o = (int)(u / C.max_orows), k = (int)(u % C.max_orows);
-    const int r0 = C.obst_off[o], nr = C.obst_off[o + 1] - r0;
-    if (nr < 0 || nr > C.max_orows || r0 < 0 || (nr > 0 && (!C.A || !C.b))) {
-        if (k == 0) cut_status(C.info, nr > C.max_orows ? PLAN_ERR_UNSUPPORTED : PLAN_ERR_INVALID_ARG, DET_ROWS);
-        if (k == 0) C.ocount[o] = 0;
-        return;
-    }
-    if (k == 0) C.ocount[o] = nr;
-    if (k < nr) {
-        const long long r = r0 + k;
-        float4 f;
-        f.x = ld32(C.A, r * C.m, C.in_f32);
-        f.y = ld32(C.A, r * C.m + 1, C.in_f32);
-        f.z = C.m == 3 ? ld32(C.A, r * C.m + 2, C.in_f32) : 0.f;
-        f.w = ld32(C.b, r, C.in_f32);
-        reinterpret_cast<float4*>(C.orow)[u] = f;
-        const float n1 = fabsf(f.x) + fabsf(f.y) + fabsf(f.z);
-        reinterpret_cast<float2*>(C.okb)[u] = make_float2(KO * n1, KO * fabsf(f.w));
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Certified bounding box of every obstacle, one warp per obstacle.  For a
+// Certified bounding box of every obstacle (one warp per obstacle, in the prep).  For a
 // direction d = +-e_a, any y >= 0 with A^T y = d bounds the obstacle:
 // d . z <= b^T y on O (weak duality), and it turns into a certificate of the
 // game: sum_r y_r G[l][r] = d . P_l - b^T y + (A^T y - d) . P_l.  The lanes
@@ -246,15 +192,14 @@ __global__ void __launch_bounds__(256) k_cut_prep(CutParams C, int row_blocks) {
 // (unbounded obstacle, near-singular vertex) gets an infinite bound.
 // ---------------------------------------------------------------------------
 template <int M>
-__global__ void __launch_bounds__(128) k_cut_obox(CutParams C) {
-    if (block_edges(C) == 0) return;
+CDEV void obstacle_boxes(const CutParams& C, long long gw, long long nw) {
     const int lane = threadIdx.x & 31;
-    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const float finf = __int_as_float(0x7f800000);
     for (long long o = gw; o < C.n_obst; o += nw) {
-        const int nr = C.ocount[o], r0 = C.obst_off[o];
-        const float4* rw = reinterpret_cast<const float4*>(C.orow) + o * C.max_orows;
+        const int r0 = C.obst_off[o];
+        int nr = C.obst_off[o + 1] - r0;
+        // an obstacle the prep rejects (bad row count or arrays) keeps infinite bounds
+        if (nr < 0 || nr > C.max_orows || r0 < 0 || (nr > 0 && (!C.A || !C.b))) nr = 0;
         float best[2 * M];
         int bsub[2 * M];
 #pragma unroll
@@ -278,12 +223,14 @@ __global__ void __launch_bounds__(128) k_cut_obox(CutParams C) {
             float a[M][M], bs[M], nrm = 1.f;
 #pragma unroll
             for (int k = 0; k < M; ++k) {
-                const float4 f = rw[idx[k]];
-                a[k][0] = f.x;
-                a[k][1] = f.y;
-                if (M == 3) a[k][M - 1] = f.z;
-                bs[k] = f.w;
-                nrm *= fabsf(f.x) + fabsf(f.y) + fabsf(f.z);
+                float n1 = 0.f;
+#pragma unroll
+                for (int j = 0; j < M; ++j) {
+                    a[k][j] = ld32(C.A, (long long)(r0 + idx[k]) * M + j, C.in_f32);
+                    n1 += fabsf(a[k][j]);
+                }
+                bs[k] = ld32(C.b, r0 + idx[k], C.in_f32);
+                nrm *= n1;
             }
             // y solves sum_k y_k a[k] = d: y = (a^T)^-1 d, i.e. row a of a^-1 ... via cofactors
             float inv[M][M], det;
@@ -412,6 +359,66 @@ __global__ void __launch_bounds__(128) k_cut_obox(CutParams C) {
 }
 
 // ---------------------------------------------------------------------------
+// Prep, three kinds of blocks: start vertex of every edge and cleared hit bits
+// (one warp per row); the obstacles' FP32 rows, max_orows per obstacle, with
+// row-count checks; the obstacles' certified boxes (one warp per obstacle).
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(256) k_cut_prep(CutParams C, int row_blocks, int copy_blocks) {
+    if ((int)blockIdx.x >= row_blocks + copy_blocks) {  // certified boxes, one warp per obstacle
+        const long long gw = ((long long)(blockIdx.x - row_blocks - copy_blocks) * blockDim.x + threadIdx.x) >> 5;
+        const long long nw = ((long long)(gridDim.x - row_blocks - copy_blocks) * blockDim.x) >> 5;
+        obstacle_boxes<M>(C, gw, nw);
+        return;
+    }
+    if ((int)blockIdx.x < row_blocks) {
+        const long long E = block_edges(C);
+        const int lane = threadIdx.x & 31;
+        const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        const long long nw = ((long long)row_blocks * blockDim.x) >> 5;
+        if (E == 0) return;
+        // the CSR must cover exactly edges 0..E-1 with end vertices below N
+        // (every later pass indexes states with them)
+        if (w0 == 0 && lane == 0 && (C.row_in[0] != 0 || (long long)C.row_in[C.N] != E))
+            cut_status(C.info, PLAN_ERR_INVALID_ARG, DET_CUTIN);
+        for (long long i = w0; i < C.N; i += nw) {
+            const long long a = C.row_in[i], b = C.row_in[i + 1];
+            if (a < 0 || b < a || b > E) {
+                if (lane == 0) cut_status(C.info, PLAN_ERR_INVALID_ARG, DET_CUTIN);
+                continue;
+            }
+            for (long long e = a + lane; e < b; e += 32) {
+                C.src[e] = (int32_t)i;
+                C.hit[e] = 0u;
+                if ((unsigned)C.col_in[e] >= (unsigned)C.N) cut_status(C.info, PLAN_ERR_INVALID_ARG, DET_CUTIN);
+            }
+        }
+        return;
+    }
+    const long long u = ((long long)blockIdx.x - row_blocks) * blockDim.x + threadIdx.x;
+    if (u >= (long long)C.n_obst * C.max_orows) return;
+    const int o = (int)(u / C.max_orows), k = (int)(u % C.max_orows);
+    const int r0 = C.obst_off[o], nr = C.obst_off[o + 1] - r0;
+    if (nr < 0 || nr > C.max_orows || r0 < 0 || (nr > 0 && (!C.A || !C.b))) {
+        if (k == 0) cut_status(C.info, nr > C.max_orows ? PLAN_ERR_UNSUPPORTED : PLAN_ERR_INVALID_ARG, DET_ROWS);
+        if (k == 0) C.ocount[o] = 0;
+        return;
+    }
+    if (k == 0) C.ocount[o] = nr;
+    if (k < nr) {
+        const long long r = r0 + k;
+        float4 f;
+        f.x = ld32(C.A, r * C.m, C.in_f32);
+        f.y = ld32(C.A, r * C.m + 1, C.in_f32);
+        f.z = C.m == 3 ? ld32(C.A, r * C.m + 2, C.in_f32) : 0.f;
+        f.w = ld32(C.b, r, C.in_f32);
+        reinterpret_cast<float4*>(C.orow)[u] = f;
+        const float n1 = fabsf(f.x) + fabsf(f.y) + fabsf(f.z);
+        reinterpret_cast<float2*>(C.okb)[u] = make_float2(KO * n1, KO * fabsf(f.w));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Pass A: a block of 8 warps takes 256 (edge, T) units (a lane each) and one
 // stripe of the obstacles.  Each warp computes its units' FP32 control
 // points (stripes of the same units repeat that small step); the block stages
@@ -439,7 +446,7 @@ CDEV void flush_pairs(const CutParams& C, unsigned long long* buf, int n, int la
 template <int M, int G, int PD>
 __global__ void __launch_bounds__(256) k_cut_scan(CutParams C, int target_items) {
     constexpr int NP = PD + 1, BW = M == 2 ? 1 : 2;  // float4 per staged box
-    constexpr int TILE = SCAN_TILE / BW;
+    constexpr int TILE = SCAN_TILE / BW;  // a multiple of SCAN_STEP
     __shared__ float4 sbox[TILE * BW];
     __shared__ unsigned long long sbuf[8][SCAN_BUF];
     const long long E = block_edges(C);
@@ -487,32 +494,41 @@ __global__ void __launch_bounds__(256) k_cut_scan(CutParams C, int target_items)
         }
         const bool any_valid = __syncthreads_or(valid) != 0;
         const int o0 = sidx * per, o1 = min(C.n_obst, o0 + per);
+        if (valid && any_valid) n_tests += (unsigned long long)max(0, o1 - o0);
         for (int t0 = o0; any_valid && t0 < o1; t0 += TILE) {
             const int nt = min(TILE, o1 - t0);
+            const int ntp = (nt + SCAN_STEP - 1) / SCAN_STEP * SCAN_STEP;
             __syncthreads();  // the previous tile is consumed
-            for (int k = threadIdx.x; k < nt * BW; k += blockDim.x) {
+            // the tile, padded to whole steps with empty boxes (lo = +inf,
+            // hi = -inf: every test says "far")
+            for (int k = threadIdx.x; k < ntp * BW; k += blockDim.x) {
                 const int ob = k / BW, h = k - ob * BW;
-                sbox[k] = __ldg(gbox + 2 * (long long)(t0 + ob) + (M == 2 ? 0 : h));
+                float4 v;
+                if (ob < nt) {
+                    v = __ldg(gbox + 2 * (long long)(t0 + ob) + (M == 2 ? 0 : h));
+                } else {
+                    const float pinf = __int_as_float(0x7f800000);
+                    v = (M == 2) ? make_float4(pinf, pinf, -pinf, -pinf)
+                                 : (h == 0 ? make_float4(pinf, pinf, pinf, 0.f) : make_float4(-pinf, -pinf, -pinf, 0.f));
+                }
+                sbox[k] = v;
             }
             __syncthreads();
-            for (int ob = 0; ob < nt; ob += SCAN_STEP) {
+            for (int ob = 0; ob < ntp; ob += SCAN_STEP) {
                 unsigned need = 0;
 #pragma unroll
                 for (int k = 0; k < SCAN_STEP; ++k) {
-                    if (ob + k < nt) {
-                        const float4 b0 = sbox[(ob + k) * BW];
-                        bool far;
-                        if (M == 2) {
-                            far = le[0] > b0.z || le[1] > b0.w || he[0] < b0.x || he[1] < b0.y;
-                        } else {
-                            const float4 b1 = sbox[(ob + k) * BW + 1];
-                            far = le[0] > b1.x || le[1] > b1.y || le[M - 1] > b1.z || he[0] < b0.x ||
-                                  he[1] < b0.y || he[M - 1] < b0.z;
-                        }
-                        need |= far ? 0u : (1u << k);
+                    const float4 b0 = sbox[(ob + k) * BW];
+                    bool far;
+                    if (M == 2) {
+                        far = le[0] > b0.z || le[1] > b0.w || he[0] < b0.x || he[1] < b0.y;
+                    } else {
+                        const float4 b1 = sbox[(ob + k) * BW + 1];
+                        far = le[0] > b1.x || le[1] > b1.y || le[M - 1] > b1.z || he[0] < b0.x || he[1] < b0.y ||
+                              he[M - 1] < b0.z;
                     }
+                    need |= far ? 0u : (1u << k);
                 }
-                if (valid) n_tests += min(SCAN_STEP, nt - ob);
                 if (__any_sync(0xffffffffu, need != 0u)) {
                     const int cnt = __popc(need);
                     int incl = cnt;
@@ -536,7 +552,21 @@ __global__ void __launch_bounds__(256) k_cut_scan(CutParams C, int target_items)
             }
         }
     }
-    if (nbuf > 0) flush_pairs(C, buf, nbuf, lane);
+    // the block's buffered entries with one atomic for all eight warps
+    __shared__ int s_n[8];
+    __shared__ unsigned long long s_base;
+    if (lane == 0) s_n[warp] = nbuf;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < 8; ++w) tot += s_n[w];
+        s_base = tot ? atomicAdd(&C.info->cut_near, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long base = s_base;
+    for (int w = 0; w < warp; ++w) base += (unsigned long long)s_n[w];
+    for (int k = lane; k < nbuf; k += 32)
+        if (base + k < (unsigned long long)C.cap32) C.list32[base + k] = buf[k];
     cut_block_add(&C.info->cut_units, n_units);
     cut_block_add(&C.info->cut_tests, n_tests);
     cut_block_add(&C.info->cut_box, n_tests - n_near);
@@ -687,149 +717,18 @@ CDEV double half64(const double* coef, const double* x, int stride) {
 }
 
 // ---------------------------------------------------------------------------
-// Pass B: one thread per listed (edge, T, obstacle).  FP32 margins with their
-// bands (b_r +- band_r against the products A_r . P_l):
-//   a control point below every facet's b - band -> hit (Algorithm 2, first);
-//   a facet above b + band at every control point -> miss (second);
-// otherwise the game in registers (RB >= every obstacle's row count), then
-// its certificates (weak duality; margins within band_r of the canonical):
-//   hit:  lambda >= 0, L = sum lambda > 0, and for every r
-//         sum_l lambda_l G[l][r] + L band_r + 2 (NP + 2) u sum_l lambda_l |G[l][r]| < 0;
-//   miss: y >= 0 and for every l
-//         sum_r y_r G[l][r] - sum_r y_r band_r - 2 (RB + 2) u sum_r y_r |G[l][r]| > 0.
-// Uncertified entries go to the FP64 list with lambda and y.  The margins are
-// recomputed for the checks rather than kept in registers.
-// ---------------------------------------------------------------------------
-template <int M, int G, int PD, int RB>
-__global__ void __launch_bounds__(128) k_cut_pair(CutParams C) {
-    constexpr int NP = PD + 1;
-    const long long n = block_count(C.info, &C.info->cut_near, C.cap32);
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    unsigned long long n_s1 = 0, n_s2 = 0, n_games = 0;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-        const unsigned long long en = C.list32[k];
-        const long long u = (long long)(en >> OBST_BITS);
-        const int o = (int)(en & ((1ull << OBST_BITS) - 1ull));
-        const long long e = u / C.nT;
-        const int t = (int)(u - e * C.nT);
-        if ((*(volatile const uint32_t*)(C.hit + e) >> t) & 1u) continue;
-        float P[NP * M], S, lo[M], hi[M];
-        unit_points<M, G, PD>(C, C.src[e], C.col_in[e], t, P, S, lo, hi);
-        const int nr = C.ocount[o];
-        const long long rb = (long long)o * C.max_orows;
-        const float4* rw = reinterpret_cast<const float4*>(C.orow) + rb;
-        const float2* kw = reinterpret_cast<const float2*>(C.okb) + rb;
-        float T[RB][NP], band[RB];
-        bool inside[NP], sep = false;
-#pragma unroll
-        for (int l = 0; l < NP; ++l) inside[l] = true;
-        float gmin = __int_as_float(0x7f800000);
-#pragma unroll
-        for (int i = 0; i < RB; ++i) {
-            float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
-            float bd = 0.f;
-            if (i < nr) {
-                f = __ldg(rw + i);
-                const float2 kb = __ldg(kw + i);
-                bd = fmaf(kb.x, S, kb.y);
-            }
-            band[i] = bd;
-            bool above = i < nr;
-#pragma unroll
-            for (int l = 0; l < NP; ++l) {
-                const float sv = dot32<M>(f, P + l * M);
-                T[i][l] = sv - f.w;
-                if (i < nr) {
-                    gmin = fminf(gmin, sv - f.w);
-                    inside[l] = inside[l] && sv <= f.w - bd;
-                    above = above && sv > f.w + bd;
-                }
-            }
-            sep = sep || above;
-        }
-        bool in = false;
-#pragma unroll
-        for (int l = 0; l < NP; ++l) in = in || inside[l];
-        if (in) {
-            ++n_s1;
-            atomicOr(&C.hit[e], 1u << t);
-            continue;
-        }
-        if (sep) {
-            ++n_s2;
-            continue;
-        }
-        ++n_games;
-        const float shift = 1.f - gmin;
-        float rhs[RB];
-#pragma unroll
-        for (int i = 0; i < RB; ++i) {
-#pragma unroll
-            for (int l = 0; l < NP; ++l) T[i][l] = i < nr ? T[i][l] + shift : 0.f;
-            rhs[i] = i < nr ? 1.f : 0.f;
-        }
-        float lam[NP], y[RB];
-        game_reg<float, NP, RB>(T, rhs, lam, y, 1e-6f);
-        float L = 0.f;
-#pragma unroll
-        for (int l = 0; l < NP; ++l) L += lam[l];
-        bool hit_ok = L > 0.f;
-        float ks[NP], ka[NP], Y = 0.f;
-#pragma unroll
-        for (int l = 0; l < NP; ++l) ks[l] = ka[l] = 0.f;
-        const float kh = 2.f * (NP + 2) * U32, km = 2.f * (RB + 2) * U32;
-#pragma unroll
-        for (int i = 0; i < RB; ++i) {
-            if (i < nr) {
-                const float4 f = __ldg(rw + i);
-                float s = 0.f, a = 0.f;
-#pragma unroll
-                for (int l = 0; l < NP; ++l) {
-                    const float g = margin32<M>(f, P + l * M);
-                    s = fmaf(lam[l], g, s);
-                    a = fmaf(lam[l], fabsf(g), a);
-                    ks[l] = fmaf(y[i], g, ks[l]);
-                    ka[l] = fmaf(y[i], fabsf(g), ka[l]);
-                }
-                hit_ok = hit_ok && (s + L * band[i] + kh * a < 0.f);
-                Y = fmaf(y[i], band[i], Y);
-            }
-        }
-        bool miss_ok = true;
-#pragma unroll
-        for (int l = 0; l < NP; ++l) miss_ok = miss_ok && (ks[l] - Y - km * ka[l] > 0.f);
-        if (hit_ok) {
-            atomicOr(&C.hit[e], 1u << t);
-        } else if (!miss_ok) {
-            // to the FP64 pass, with this game's mixes as certificate candidates
-            const unsigned long long idx = atomicAdd(&C.info->cut_lp64, 1ull);
-            if (idx < (unsigned long long)C.cap64) {
-                C.list64[idx] = en;
-                float* ly = C.lamy + idx * LAMY_STRIDE;
-#pragma unroll
-                for (int l = 0; l < NP; ++l) ly[l] = lam[l];
-#pragma unroll
-                for (int r = 0; r < RB; ++r) ly[NP + r] = r < nr ? y[r] : 0.f;
-            }
-        }
-    }
-    cut_block_add(&C.info->cut_step1, n_s1);
-    cut_block_add(&C.info->cut_step2, n_s2);
-    cut_block_add(&C.info->cut_games, n_games);
-}
-
-// ---------------------------------------------------------------------------
-// Pass C: one warp per entry.  Canonical FP64 margins (the oracle's order:
-// each control-point half summed left to right from 0, halves added; facet
-// products summed left to right from 0, then b subtracted; no FMA): lane k
-// computes control-point coordinate k, lane r then facet r's margins.
-// Algorithm 2's two checks exactly, then the FP32 game's mixes as
-// certificates, then the game itself with the warp as the tableau (lane r =
-// basic row r) and exact-rounding certificates; a game certified neither way
-// is a tie, decided by the sign of its computed value.
-// GB300's FP64 pipe is narrow, so the pass keeps its FP64 instruction count
-// low: the coordinates are computed once per warp, not once per lane, and the
-// reciprocals come from an FP32 estimate and two Newton steps.
+// FP64 settling of one (edge, T, obstacle), by the whole warp.  Canonical
+// FP64 margins (the oracle's order: each control-point half summed left to
+// right from 0, halves added; facet products summed left to right from 0,
+// then b subtracted; no FMA): lane k computes control-point coordinate k, lane
+// r then facet r's margins.  Algorithm 2's two checks exactly, then the FP32
+// game's mixes (mix: lambda then y) as certificates, then the game itself with
+// the warp as the tableau (lane r = basic row r) and exact-rounding
+// certificates; a game certified neither way is a tie (|delta*| at rounding
+// level), decided by the sign of its computed value.  GB300's FP64 pipe is
+// narrow, so the FP64 instruction count stays low: the coordinates are
+// computed once per warp, not once per lane, and the reciprocals come from an
+// FP32 estimate and two Newton steps.  Returns 1 (hit) or -1 (miss).
 // ---------------------------------------------------------------------------
 CDEV double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -848,90 +747,83 @@ CDEV double rcp64(double x) {
 }
 
 template <int M, int G, int PD>
-__global__ void __launch_bounds__(128) k_cut_lp64(CutParams C) {
+CDEV int settle64(const CutParams& C, unsigned long long en, const float* mix, bool& tie) {
     constexpr int N_ = M * G, NP = PD + 1, TG = 2 * G;
     static_assert(NP * M <= 32, "one control-point coordinate per lane");
-    const long long n = block_count(C.info, &C.info->cut_lp64, C.cap64);
     const int lane = threadIdx.x & 31;
-    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const double inf = __longlong_as_double(0x7FF0000000000000ll);
-    unsigned long long n_ties = 0;
-    for (long long k = gw; k < n; k += nw) {
-        const unsigned long long en = C.list64[k];
-        const long long u = (long long)(en >> OBST_BITS);
-        const int o = (int)(en & ((1ull << OBST_BITS) - 1ull));
-        const long long e = u / C.nT;
-        const int t = (int)(u - e * C.nT);
-        if ((*(volatile const uint32_t*)(C.hit + e) >> t) & 1u) continue;
-        const long long i = C.src[e], j = C.col_in[e];
-        // lane k < NP * M: coordinate a = k % M of control point l = k / M
-        double pk = 0.0;
-        if (lane < NP * M) {
-            const int l = lane / M, a = lane - l * M;
-            const double* D = C.tab64 + (long long)t * C.L.e_stride + C.L.e_D + l * TG;
-            double xi[G], xj[G];
+    tie = false;
+    const long long u = (long long)(en >> OBST_BITS);
+    const int o = (int)(en & ((1ull << OBST_BITS) - 1ull));
+    const long long e = u / C.nT;
+    const int t = (int)(u - e * C.nT);
+    const long long i = C.src[e], j = C.col_in[e];
+    // lane k < NP * M: coordinate a = k % M of control point l = k / M
+    double pk = 0.0;
+    if (lane < NP * M) {
+        const int l = lane / M, a = lane - l * M;
+        const double* D = C.tab64 + (long long)t * C.L.e_stride + C.L.e_D + l * TG;
+        double xi[G], xj[G];
 #pragma unroll
-            for (int c = 0; c < G; ++c) {
-                xi[c] = ld64(C.states, i * N_ + c * M + a, C.in_f32);
-                xj[c] = ld64(C.states, j * N_ + c * M + a, C.in_f32);
-            }
-            pk = __dadd_rn(half64<G>(D, xi, 1), half64<G>(D + G, xj, 1));
+        for (int c = 0; c < G; ++c) {
+            xi[c] = ld64(C.states, i * N_ + c * M + a, C.in_f32);
+            xj[c] = ld64(C.states, j * N_ + c * M + a, C.in_f32);
         }
-        double P[NP * M];
+        pk = __dadd_rn(half64<G>(D, xi, 1), half64<G>(D + G, xj, 1));
+    }
+    double P[NP * M];
 #pragma unroll
-        for (int q = 0; q < NP * M; ++q) P[q] = __shfl_sync(0xffffffffu, pk, q);
-        const int r0 = C.obst_off[o], nr = C.ocount[o];
-        const bool mine = lane < nr;
-        double g[NP];
+    for (int q = 0; q < NP * M; ++q) P[q] = __shfl_sync(0xffffffffu, pk, q);
+    const int r0 = C.obst_off[o], nr = C.ocount[o];
+    const bool mine = lane < nr;
+    double g[NP];
 #pragma unroll
-        for (int l = 0; l < NP; ++l) g[l] = 0.0;
-        if (mine) {
-            const double br = ld64(C.b, r0 + lane, C.in_f32);
-            double Ar[M];
+    for (int l = 0; l < NP; ++l) g[l] = 0.0;
+    if (mine) {
+        const double br = ld64(C.b, r0 + lane, C.in_f32);
+        double Ar[M];
 #pragma unroll
-            for (int a = 0; a < M; ++a) Ar[a] = ld64(C.A, (long long)(r0 + lane) * M + a, C.in_f32);
+        for (int a = 0; a < M; ++a) Ar[a] = ld64(C.A, (long long)(r0 + lane) * M + a, C.in_f32);
+#pragma unroll
+        for (int l = 0; l < NP; ++l) {
+            double sv = 0.0;
+#pragma unroll
+            for (int a = 0; a < M; ++a) sv = __dadd_rn(sv, __dmul_rn(Ar[a], P[l * M + a]));
+            g[l] = __dsub_rn(sv, br);
+        }
+    }
+    int verdict = 0;  // 1 hit, -1 miss
+#pragma unroll
+    for (int l = 0; l < NP; ++l)  // a control point with every margin <= 0
+        if (__ballot_sync(0xffffffffu, mine && !(g[l] <= 0.0)) == 0u) verdict = 1;
+    if (verdict == 0) {  // one facet with every margin > 0
+        bool out = mine;
+#pragma unroll
+        for (int l = 0; l < NP; ++l) out = out && g[l] > 0.0;
+        if (__ballot_sync(0xffffffffu, out) != 0u) verdict = -1;
+    }
+    if (verdict == 0 && mix) {  // the FP32 game's mixes on the canonical margins
+        double L = 0.0, s = 0.0, a = 0.0;
+#pragma unroll
+        for (int l = 0; l < NP; ++l) {
+            const double lm = (double)mix[l];
+            L += lm;
+            s += lm * g[l];
+            a += lm * fabs(g[l]);
+        }
+        const double kh = 2.0 * (NP + 2) * U64, km = 2.0 * (32 + 2) * U64;
+        if (L > 0.0 && __ballot_sync(0xffffffffu, mine && !(s + kh * a < 0.0)) == 0u) verdict = 1;
+        if (verdict == 0) {
+            const double yr = mine ? (double)mix[NP + lane] : 0.0;
+            bool miss_ok = true;
 #pragma unroll
             for (int l = 0; l < NP; ++l) {
-                double s = 0.0;
-#pragma unroll
-                for (int a = 0; a < M; ++a) s = __dadd_rn(s, __dmul_rn(Ar[a], P[l * M + a]));
-                g[l] = __dsub_rn(s, br);
+                const double ks = warp_sum(yr * g[l]), ka = warp_sum(yr * fabs(g[l]));
+                miss_ok = miss_ok && (ks - km * ka > 0.0);
             }
+            if (miss_ok) verdict = -1;
         }
-        int verdict = 0;  // 1 hit, -1 miss
-#pragma unroll
-        for (int l = 0; l < NP; ++l)  // a control point with every margin <= 0
-            if (__ballot_sync(0xffffffffu, mine && !(g[l] <= 0.0)) == 0u) verdict = 1;
-        if (verdict == 0) {  // one facet with every margin > 0
-            bool out = mine;
-#pragma unroll
-            for (int l = 0; l < NP; ++l) out = out && g[l] > 0.0;
-            if (__ballot_sync(0xffffffffu, out) != 0u) verdict = -1;
-        }
-        if (verdict == 0 && k < C.cap64) {  // the FP32 game's mixes on the canonical margins
-            const float* ly = C.lamy + k * LAMY_STRIDE;
-            double L = 0.0, s = 0.0, a = 0.0;
-#pragma unroll
-            for (int l = 0; l < NP; ++l) {
-                const double lm = (double)ly[l];
-                L += lm;
-                s += lm * g[l];
-                a += lm * fabs(g[l]);
-            }
-            const double kh = 2.0 * (NP + 2) * U64, km = 2.0 * (32 + 2) * U64;
-            if (L > 0.0 && __ballot_sync(0xffffffffu, mine && !(s + kh * a < 0.0)) == 0u) verdict = 1;
-            if (verdict == 0) {
-                const double yr = mine ? (double)ly[NP + lane] : 0.0;
-                bool miss_ok = true;
-#pragma unroll
-                for (int l = 0; l < NP; ++l) {
-                    const double ks = warp_sum(yr * g[l]), ka = warp_sum(yr * fabs(g[l]));
-                    miss_ok = miss_ok && (ks - km * ka > 0.0);
-                }
-                if (miss_ok) verdict = -1;
-            }
-        }
+    }
         if (verdict == 0) {
             double gmin = inf;
 #pragma unroll
@@ -1046,12 +938,168 @@ __global__ void __launch_bounds__(128) k_cut_lp64(CutParams C) {
             else if (miss_ok) verdict = -1;
             else {
                 verdict = (L > 0.0 && 1.0 / L - shift <= 0.0) ? 1 : -1;
-                ++n_ties;
+                tie = true;
             }
         }
-        if (verdict == 1 && lane == 0) atomicOr(&C.hit[e], 1u << t);
+    return verdict;
+}
+
+// ---------------------------------------------------------------------------
+// Pass B: one lane per listed (edge, T, obstacle), the warp walking the list
+// in steps of 32.  FP32 margins with their bands (b_r +- band_r against the
+// products A_r . P_l):
+//   a control point below every facet's b - band -> hit (Algorithm 2, first);
+//   a facet above b + band at every control point -> miss (second);
+// otherwise the game in registers (RB >= every obstacle's row count), then
+// its certificates (weak duality; margins within band_r of the canonical):
+//   hit:  lambda >= 0, L = sum lambda > 0, and for every r
+//         sum_l lambda_l G[l][r] + L band_r + 2 (NP + 2) u sum_l lambda_l |G[l][r]| < 0;
+//   miss: y >= 0 and for every l
+//         sum_r y_r G[l][r] - sum_r y_r band_r - 2 (RB + 2) u sum_r y_r |G[l][r]| > 0.
+// The margins are recomputed for the checks rather than kept in registers.
+// Entries no FP32 certificate settles are then settled one by one by the
+// whole warp in FP64 (settle64), with the lane's lambda and y passed through
+// shared memory.
+// ---------------------------------------------------------------------------
+template <int M, int G, int PD, int RB>
+__global__ void __launch_bounds__(128) k_cut_pair(CutParams C) {
+    constexpr int NP = PD + 1;
+    static_assert(NP + RB <= 32, "lambda and y fit one warp-sized buffer");
+    __shared__ float s_mix[4][32];
+    const long long n = block_count(C.info, &C.info->cut_near, C.cap32);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    unsigned long long n_s1 = 0, n_s2 = 0, n_games = 0, n_64 = 0, n_ties = 0;
+    for (long long k0 = gw * 32; k0 < n; k0 += nw * 32) {
+        const long long k = k0 + lane;
+        unsigned long long en = 0;
+        bool need64 = false;
+        float lam[NP], y[RB];
+        long long e = 0;
+        int t = 0;
+        if (k < n) {
+            en = C.list32[k];
+            const long long u = (long long)(en >> OBST_BITS);
+            const int o = (int)(en & ((1ull << OBST_BITS) - 1ull));
+            e = u / C.nT;
+            t = (int)(u - e * C.nT);
+            if (!((*(volatile const uint32_t*)(C.hit + e) >> t) & 1u)) {
+                float P[NP * M], S, lo[M], hi[M];
+                unit_points<M, G, PD>(C, C.src[e], C.col_in[e], t, P, S, lo, hi);
+                const int nr = C.ocount[o];
+                const long long rb = (long long)o * C.max_orows;
+                const float4* rw = reinterpret_cast<const float4*>(C.orow) + rb;
+                const float2* kw = reinterpret_cast<const float2*>(C.okb) + rb;
+                float T[RB][NP], band[RB];
+                bool inside[NP], sep = false;
+#pragma unroll
+                for (int l = 0; l < NP; ++l) inside[l] = true;
+                float gmin = __int_as_float(0x7f800000);
+#pragma unroll
+                for (int i = 0; i < RB; ++i) {
+                    float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+                    float bd = 0.f;
+                    if (i < nr) {
+                        f = __ldg(rw + i);
+                        const float2 kb = __ldg(kw + i);
+                        bd = fmaf(kb.x, S, kb.y);
+                    }
+                    band[i] = bd;
+                    bool above = i < nr;
+#pragma unroll
+                    for (int l = 0; l < NP; ++l) {
+                        const float sv = dot32<M>(f, P + l * M);
+                        T[i][l] = sv - f.w;
+                        if (i < nr) {
+                            gmin = fminf(gmin, sv - f.w);
+                            inside[l] = inside[l] && sv <= f.w - bd;
+                            above = above && sv > f.w + bd;
+                        }
+                    }
+                    sep = sep || above;
+                }
+                bool in = false;
+#pragma unroll
+                for (int l = 0; l < NP; ++l) in = in || inside[l];
+                if (in) {
+                    ++n_s1;
+                    atomicOr(&C.hit[e], 1u << t);
+                } else if (sep) {
+                    ++n_s2;
+                } else {
+                    ++n_games;
+                    const float shift = 1.f - gmin;
+                    float rhs[RB];
+#pragma unroll
+                    for (int i = 0; i < RB; ++i) {
+#pragma unroll
+                        for (int l = 0; l < NP; ++l) T[i][l] = i < nr ? T[i][l] + shift : 0.f;
+                        rhs[i] = i < nr ? 1.f : 0.f;
+                    }
+                    game_reg<float, NP, RB>(T, rhs, lam, y, 1e-6f);
+                    float L = 0.f;
+#pragma unroll
+                    for (int l = 0; l < NP; ++l) L += lam[l];
+                    bool hit_ok = L > 0.f;
+                    float ks[NP], ka[NP], Y = 0.f;
+#pragma unroll
+                    for (int l = 0; l < NP; ++l) ks[l] = ka[l] = 0.f;
+                    const float kh = 2.f * (NP + 2) * U32, km = 2.f * (RB + 2) * U32;
+#pragma unroll
+                    for (int i = 0; i < RB; ++i) {
+                        if (i < nr) {
+                            const float4 f = __ldg(rw + i);
+                            float sm = 0.f, am = 0.f;
+#pragma unroll
+                            for (int l = 0; l < NP; ++l) {
+                                const float gv = margin32<M>(f, P + l * M);
+                                sm = fmaf(lam[l], gv, sm);
+                                am = fmaf(lam[l], fabsf(gv), am);
+                                ks[l] = fmaf(y[i], gv, ks[l]);
+                                ka[l] = fmaf(y[i], fabsf(gv), ka[l]);
+                            }
+                            hit_ok = hit_ok && (sm + L * band[i] + kh * am < 0.f);
+                            Y = fmaf(y[i], band[i], Y);
+                        }
+                    }
+                    bool miss_ok = true;
+#pragma unroll
+                    for (int l = 0; l < NP; ++l) miss_ok = miss_ok && (ks[l] - Y - km * ka[l] > 0.f);
+                    if (hit_ok) atomicOr(&C.hit[e], 1u << t);
+                    else if (!miss_ok) {
+                        need64 = true;
+#pragma unroll
+                        for (int r = 0; r < RB; ++r) y[r] = r < nr ? y[r] : 0.f;
+                    }
+                }
+            }
+        }
+        // entries no FP32 certificate settled: the whole warp, one at a time
+        for (unsigned todo = __ballot_sync(0xffffffffu, need64); todo; todo &= todo - 1u) {
+            const int src = __ffs(todo) - 1;
+            if (lane == src) {
+#pragma unroll
+                for (int l = 0; l < NP; ++l) s_mix[warp][l] = lam[l];
+#pragma unroll
+                for (int r = 0; r < RB; ++r) s_mix[warp][NP + r] = y[r];
+            }
+            __syncwarp();
+            const unsigned long long en_s = __shfl_sync(0xffffffffu, en, src);
+            bool tie;
+            const int v = settle64<M, G, PD>(C, en_s, s_mix[warp], tie);
+            if (lane == src) {
+                ++n_64;
+                n_ties += tie;
+                if (v == 1) atomicOr(&C.hit[e], 1u << t);
+            }
+            __syncwarp();
+        }
     }
-    if (lane != 0) n_ties = 0;
+    cut_block_add(&C.info->cut_step1, n_s1);
+    cut_block_add(&C.info->cut_step2, n_s2);
+    cut_block_add(&C.info->cut_games, n_games);
+    cut_block_add(&C.info->cut_lp64, n_64);
     cut_block_add(&C.info->cut_ties, n_ties);
 }
 
@@ -1146,7 +1194,7 @@ __global__ void __launch_bounds__(1024) k_cut_offsets(CutParams C) {
         C.chunk[nch] = total;
         if (!cut_failed(C.info)) {
             *C.count_out = total;
-            if (C.info->cut_near > (unsigned long long)C.cap32 || C.info->cut_lp64 > (unsigned long long)C.cap64)
+            if (C.info->cut_near > (unsigned long long)C.cap32)
                 cut_status(C.info, PLAN_ERR_CAPACITY, DET_CUTLIST);
             else if (total > C.cap_out)
                 cut_status(C.info, PLAN_ERR_CAPACITY, DET_OUTPUT);
@@ -1255,8 +1303,8 @@ int launch_cut_t(const CutParams& C, cudaStream_t st, int num_sms, int* launches
     const int row_blocks = (int)(rb < num_sms * 8 ? (rb > 0 ? rb : 1) : num_sms * 8);
     const long long orows = (long long)C.n_obst * C.max_orows;
     const int obst_blocks = (int)((orows + 255) / 256);
-    k_cut_prep<<<row_blocks + obst_blocks, 256, 0, st>>>(C, row_blocks);
-    if (C.n_obst > 0) k_cut_obox<M><<<(C.n_obst + 3) / 4, 128, 0, st>>>(C);
+    const int box_blocks = (C.n_obst + 7) / 8;
+    k_cut_prep<M><<<row_blocks + obst_blocks + box_blocks, 256, 0, st>>>(C, row_blocks, obst_blocks);
     // pass A: a grid-stride loop over (256-unit group, obstacle stripe) items
     const int ga = num_sms * 8;
     if (e0) cudaEventRecord(e0, st);
@@ -1264,14 +1312,13 @@ int launch_cut_t(const CutParams& C, cudaStream_t st, int num_sms, int* launches
     if (e1) cudaEventRecord(e1, st);
     if (C.max_orows <= 8) k_cut_pair<M, G, PD, 8><<<num_sms * 4, 128, 0, st>>>(C);
     else k_cut_pair<M, G, PD, CUT_RMAX><<<num_sms * 4, 128, 0, st>>>(C);
-    k_cut_lp64<M, G, PD><<<num_sms, 128, 0, st>>>(C);
     long long gc = C.nchunks < (long long)num_sms * 4 ? C.nchunks : (long long)num_sms * 4;
     if (gc < 1) gc = 1;
     k_cut_count<<<(int)gc, FILL_THREADS, 0, st>>>(C);
     k_cut_offsets<<<1, 1024, 0, st>>>(C);
     k_cut_fill<M, G, PD><<<(int)gc, FILL_THREADS, 0, st>>>(C);
     k_cut_rows<<<(int)((C.N + 1 + 255) / 256), 256, 0, st>>>(C);
-    *launches += C.n_obst > 0 ? 9 : 8;
+    *launches += 7;
     return (int)cudaGetLastError();
 }
 

@@ -82,7 +82,7 @@ struct DevInfo {
     unsigned long long cut_step1;    // hit: a control point inside (FP32, certain)
     unsigned long long cut_step2;    // missed: one separating facet (FP32, certain)
     unsigned long long cut_games;    // matrix games solved in FP32
-    unsigned long long cut_lp64;     // entries of the FP64 list
+    unsigned long long cut_lp64;     // entries settled in FP64
     unsigned long long cut_ties;     // FP64 games without a certificate either way
 };
 
@@ -287,11 +287,8 @@ struct CutParams {
     TabLayout L;
     int32_t* src;              // [cap_in] start vertex of each edge
     uint32_t* hit;             // [cap_in] durations whose curve meets an obstacle
-    unsigned long long* list32;
+    unsigned long long* list32;  // pair list: (edge * nT + T) << 20 | obstacle
     long long cap32;
-    unsigned long long* list64;
-    long long cap64;
-    float* lamy;               // [cap64][32] the FP32 game's lambda and y of each FP64-list entry
     long long* chunk;          // [nchunks + 1] kept edges per chunk, then their exclusive prefix
     int32_t* pos;              // [cap_in + 1] output index of each edge (exclusive prefix of kept)
     long long nchunks;
