@@ -239,6 +239,18 @@ int plan_search(plan_ctx* ctx, int N, const void* states, const plan_edges* edge
                 const double* start_pos, const double* goal_pos, int32_t* path, int path_cap,
                 int32_t* path_len, double* cost);
 
+/*
+ * plan_search with the start and goal positions read from device memory when
+ * the search runs (not when it is issued), so that a replanning loop can
+ * capture the search once in a CUDA graph and move start and goal between
+ * replays.
+ *   endpoints  device double [2][m]: start position, then goal position
+ *              (finite; not checked on the host)
+ * Everything else as plan_search.
+ */
+int plan_search_at(plan_ctx* ctx, int N, const void* states, const plan_edges* edges, const double* endpoints,
+                   int32_t* path, int path_cap, int32_t* path_len, double* cost);
+
 /* Bounds of the search kernel's device loops: at most max_sweeps frontier
  * sweeps (default N+1, the Bellman-Ford bound) and spin_limit polls of the
  * grid barrier (default 2^24).  0 keeps the default.  When a bound runs out

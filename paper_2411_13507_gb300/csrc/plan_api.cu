@@ -758,17 +758,25 @@ int plan_autotune(plan_ctx* c, int reps, int* best_tile, int* best_ctas, int* be
     return PLAN_OK;
 }
 
-int plan_search(plan_ctx* c, int N, const void* states, const plan_edges* edges, const double* start_pos,
-                const double* goal_pos, int32_t* path, int path_cap, int32_t* path_len, double* cost) {
+}  // extern "C"
+
+namespace {
+
+// plan_search and plan_search_at: start/goal from the host (start_pos,
+// goal_pos) or from device memory at run time (endpoints).
+int search_common(plan_ctx* c, int N, const void* states, const plan_edges* edges, const double* start_pos,
+                  const double* goal_pos, const double* endpoints, int32_t* path, int path_cap, int32_t* path_len,
+                  double* cost) {
     if (!c) return PLAN_ERR_INVALID_ARG;
     if (N < 1 || N > (1 << 20) || !states) return fail(c, PLAN_ERR_INVALID_ARG, "need N >= 1 states");
     if (!edges || !edges->row_off || !edges->count || edges->cap < 0 || (edges->cap > 0 && (!edges->col || !edges->w)))
         return fail(c, PLAN_ERR_INVALID_ARG, "bad CSR");
-    if (!start_pos || !goal_pos || !path || path_cap < 1 || !path_len || !cost)
+    if ((!endpoints && (!start_pos || !goal_pos)) || !path || path_cap < 1 || !path_len || !cost)
         return fail(c, PLAN_ERR_INVALID_ARG, "bad search output");
-    for (int a = 0; a < c->model.m; ++a)
-        if (!std::isfinite(start_pos[a]) || !std::isfinite(goal_pos[a]))
-            return fail(c, PLAN_ERR_INVALID_ARG, "start/goal must be finite");
+    if (!endpoints)
+        for (int a = 0; a < c->model.m; ++a)
+            if (!std::isfinite(start_pos[a]) || !std::isfinite(goal_pos[a]))
+                return fail(c, PLAN_ERR_INVALID_ARG, "start/goal must be finite");
     if (N > c->capS) {
         if (!dalloc(c, &c->sdist, N) || !dalloc(c, &c->sbest, N) || !dalloc(c, &c->spred, N) ||
             !dalloc(c, &c->sfront, 2LL * N))
@@ -794,10 +802,12 @@ int plan_search(plan_ctx* c, int N, const void* states, const plan_edges* edges,
     S.w = edges->w;
     S.count = edges->count;
     S.cap = edges->cap;
-    for (int a = 0; a < c->model.m; ++a) {
-        S.start[a] = start_pos[a];
-        S.goal[a] = goal_pos[a];
-    }
+    if (!endpoints)
+        for (int a = 0; a < c->model.m; ++a) {
+            S.start[a] = start_pos[a];
+            S.goal[a] = goal_pos[a];
+        }
+    S.endpoints = endpoints;
     S.dist = c->sdist;
     S.bestU = c->sbest;
     S.pred = c->spred;
@@ -825,6 +835,21 @@ int plan_search(plan_ctx* c, int N, const void* states, const plan_edges* edges,
     c->launches += launches;
     if (ce != 0) return cuda_fail(c, (cudaError_t)ce, "search launch");
     return PLAN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int plan_search(plan_ctx* c, int N, const void* states, const plan_edges* edges, const double* start_pos,
+                const double* goal_pos, int32_t* path, int path_cap, int32_t* path_len, double* cost) {
+    return search_common(c, N, states, edges, start_pos, goal_pos, nullptr, path, path_cap, path_len, cost);
+}
+
+int plan_search_at(plan_ctx* c, int N, const void* states, const plan_edges* edges, const double* endpoints,
+                   int32_t* path, int path_cap, int32_t* path_len, double* cost) {
+    if (!endpoints) return fail(c, PLAN_ERR_INVALID_ARG, "null endpoints");
+    return search_common(c, N, states, edges, nullptr, nullptr, endpoints, path, path_cap, path_len, cost);
 }
 
 }  // extern "C"

@@ -182,6 +182,7 @@ struct SearchParams {
     const int64_t* count;
     long long cap;
     double start[4], goal[4];
+    const double* endpoints;   // device [2][m] start then goal, read at run time instead of start/goal (or null)
     unsigned long long* dist;  // [N] bit patterns of non-negative doubles
     unsigned long long* bestU; // [N]
     int* pred;                 // [N]

@@ -181,6 +181,11 @@ __global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
     }
     unsigned long long kb[2] = {~0ull, ~0ull};
     int ki[2] = {0x7fffffff, 0x7fffffff};
+    double spos[4], gpos[4];
+    for (int a = 0; a < 4; ++a) {
+        spos[a] = P.endpoints ? (a < P.m ? P.endpoints[a] : 0.0) : P.start[a];
+        gpos[a] = P.endpoints ? (a < P.m ? P.endpoints[P.m + a] : 0.0) : P.goal[a];
+    }
     for (long long k = tid; k < nown; k += nt) {  // owned vertices: the FP64 work spreads over every SM
         const long long v = blockIdx.x + k * nb;
         P.dist[v] = DINF;
@@ -190,8 +195,8 @@ __global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
         double ds = 0.0, dg = 0.0;
         for (int a = 0; a < P.m; ++a) {
             const double x = ldd(P.states, v * P.n + a, P.in_f32);
-            const double ts = __dsub_rn(x, P.start[a]);
-            const double tg = __dsub_rn(x, P.goal[a]);
+            const double ts = __dsub_rn(x, spos[a]);
+            const double tg = __dsub_rn(x, gpos[a]);
             ds = __dadd_rn(ds, __dmul_rn(ts, ts));
             dg = __dadd_rn(dg, __dmul_rn(tg, tg));
         }

@@ -83,7 +83,7 @@ class _RefineW(ctypes.Structure):
 EXPORTS = ["plan_create", "plan_destroy", "plan_build_edges", "plan_search", "plan_wait", "plan_model_tables",
            "plan_set_search_limits", "plan_refine", "plan_prepare_batched", "plan_build_edges_batched",
            "plan_set_tile", "plan_autotune", "plan_prepare_search_batched", "plan_search_batched",
-           "plan_search_noalloc", "plan_cut_edges", "plan_cut_timing", "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
+           "plan_search_noalloc", "plan_cut_edges", "plan_cut_timing", "plan_search_at", "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
 
 
 def lib_path() -> str:
@@ -129,6 +129,8 @@ def load(build_if_stale: bool = True):
     lib.plan_cut_edges.argtypes = [vp, i32, vp, i32, dp, ctypes.POINTER(_Edges), ctypes.POINTER(_Obstacles),
                                    ctypes.POINTER(_Edges)]
     lib.plan_cut_edges.restype = i32
+    lib.plan_search_at.argtypes = [vp, i32, vp, ctypes.POINTER(_Edges), vp, vp, i32, vp, vp]
+    lib.plan_search_at.restype = i32
     lib.plan_cut_timing.argtypes = [vp, dp, dp, ctypes.POINTER(i64), i32]
     lib.plan_cut_timing.restype = i32
     lib.plan_set_tile.argtypes = [vp, i32, i32, i32, i32]
@@ -414,6 +416,16 @@ class Planner:
         if rc != 0:
             raise self._err(rc, "plan_search")
 
+    def search_at_async(self, dp: DeviceProblem, graph: Graph, endpoints, out: dict) -> None:
+        """plan_search_at: start and goal read from the device tensor
+        ``endpoints`` (float64 [2][m]) when the search runs."""
+        rc = self.lib.plan_search_at(self.ctx, dp.N, ctypes.c_void_p(dp.states.data_ptr()), ctypes.byref(graph.cstruct()),
+                                     ctypes.c_void_p(endpoints.data_ptr()), ctypes.c_void_p(out["path"].data_ptr()),
+                                     int(out["path"].shape[0]), ctypes.c_void_p(out["path_len"].data_ptr()),
+                                     ctypes.c_void_p(out["cost"].data_ptr()))
+        if rc != 0:
+            raise self._err(rc, "plan_search_at")
+
     def alloc_search(self, N: int, path_cap: Optional[int] = None) -> dict:
         import torch
         dev = torch.device("cuda")
@@ -566,3 +578,117 @@ class Planner:
         if rc != 0:
             raise self._err(rc, "plan_cut_timing")
         return {"scan_ms": a.value, "cut_ms": b.value, "cuts": n.value}
+
+
+class Replanner:
+    """The replanning loop of Alg. 1 (lines 3-4 every tick, the graph of line 2
+    fixed): each tick refreshes the obstacles and the start/goal positions on
+    the device from pinned host buffers, cuts the fixed graph against the
+    obstacles (plan_cut_edges), searches the cut graph (plan_search_at) and
+    copies the path back -- all replayed from one captured CUDA graph.
+
+    The obstacle arrays have a fixed capacity (n_max obstacles, rows_max >= 2m
+    rows each); a tick with fewer obstacles fills the other slots with unit
+    boxes at -1e12 in every axis, which the certified bounding boxes separate
+    from every curve."""
+
+    def __init__(self, planner: "Planner", dp: DeviceProblem, graph: Graph, n_max: int, rows_max: int,
+                 path_cap: Optional[int] = None):
+        import torch
+        if planner.stream.cuda_stream == 0:
+            raise ValueError("the planner needs its own stream (a graph cannot be captured on the default stream)")
+        self.pl, self.dp, self.graph = planner, dp, graph
+        self.m = int(planner.model.m)
+        self.n_max, self.rows_max = int(n_max), int(rows_max)
+        if self.rows_max < 2 * self.m:
+            raise ValueError("rows_max must be at least 2m (the padding boxes)")
+        dev = torch.device("cuda")
+        R = self.n_max * self.rows_max
+        adt = torch.float32 if planner.input == "f32" else torch.float64
+        self.h_off = torch.zeros(self.n_max + 1, dtype=torch.int32).pin_memory()
+        self.h_A = torch.zeros(R * self.m, dtype=adt).pin_memory()
+        self.h_b = torch.zeros(R, dtype=adt).pin_memory()
+        self.h_ends = torch.zeros(2 * self.m, dtype=torch.float64).pin_memory()
+        self.obst = DeviceObstacles(n=self.n_max, max_rows=self.rows_max,
+                                    off=torch.zeros(self.n_max + 1, dtype=torch.int32, device=dev),
+                                    A=torch.zeros(R * self.m, dtype=adt, device=dev),
+                                    b=torch.zeros(R, dtype=adt, device=dev))
+        self.ends = torch.zeros(2 * self.m, dtype=torch.float64, device=dev)
+        self.out = planner.alloc_graph(dp.N, graph.cap)
+        self.sbuf = planner.alloc_search(dp.N, path_cap)
+        self.h_path = torch.zeros(self.sbuf["path"].shape[0], dtype=torch.int32).pin_memory()
+        self.h_len = torch.zeros(1, dtype=torch.int32).pin_memory()
+        self.h_cost = torch.zeros(1, dtype=torch.float64).pin_memory()
+        self.cg = None
+
+    def _stage(self, obstacles, start_pos, goal_pos) -> None:
+        off = np.asarray(obstacles.off, dtype=np.int64)
+        n = off.shape[0] - 1
+        if n > self.n_max or (n > 0 and int(np.max(np.diff(off))) > self.rows_max):
+            raise ValueError("obstacles exceed the replanner's capacity")
+        A = np.asarray(obstacles.A, dtype=np.float64).reshape(-1, self.m)
+        b = np.asarray(obstacles.b, dtype=np.float64)
+        # far unit boxes in the unused slots: -1e12 <= z_a <= -1e12 + 1
+        pad = self.n_max - n
+        eye = np.concatenate([np.eye(self.m), -np.eye(self.m)])
+        bb = np.concatenate([np.full(self.m, -1e12 + 1.0), np.full(self.m, 1e12)])
+        A_all = np.concatenate([A, np.tile(eye, (pad, 1))]) if pad else A
+        b_all = np.concatenate([b, np.tile(bb, pad)]) if pad else b
+        off_all = np.concatenate([off, off[-1] + 2 * self.m * np.arange(1, pad + 1)]) if pad else off
+        R = b_all.shape[0]
+        self.h_off.numpy()[:] = 0
+        self.h_off.numpy()[:off_all.shape[0]] = off_all.astype(np.int32)
+        self.h_A.numpy()[:R * self.m] = A_all.reshape(-1)
+        self.h_b.numpy()[:R] = b_all
+        self.h_ends.numpy()[:self.m] = np.asarray(start_pos, dtype=np.float64)[:self.m]
+        self.h_ends.numpy()[self.m:] = np.asarray(goal_pos, dtype=np.float64)[:self.m]
+
+    def _issue(self) -> None:
+        o = self.obst
+        o.off.copy_(self.h_off, non_blocking=True)
+        o.A.copy_(self.h_A, non_blocking=True)
+        o.b.copy_(self.h_b, non_blocking=True)
+        self.ends.copy_(self.h_ends, non_blocking=True)
+        self.pl.cut_edges_async(self.dp, self.graph, o, self.out)
+        self.pl.search_at_async(self.dp, self.out, self.ends, self.sbuf)
+        self.h_path.copy_(self.sbuf["path"], non_blocking=True)
+        self.h_len.copy_(self.sbuf["path_len"], non_blocking=True)
+        self.h_cost.copy_(self.sbuf["cost"], non_blocking=True)
+
+    def capture(self, obstacles, start_pos, goal_pos) -> None:
+        """Size every scratch with one direct tick, then capture the tick."""
+        import torch
+        self._stage(obstacles, start_pos, goal_pos)
+        with torch.cuda.stream(self.pl.stream):
+            for _ in range(3):      # grow the cut's pair list if it must
+                self._issue()
+                st = self.pl.wait()
+                if st != PLAN_ERR_CAPACITY:
+                    break
+            self.cg = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.cg, stream=self.pl.stream):
+                self._issue()
+        self.pl.wait()
+
+    def tick_async(self, obstacles, start_pos, goal_pos) -> None:
+        import torch
+        self._stage(obstacles, start_pos, goal_pos)
+        with torch.cuda.stream(self.pl.stream):
+            self.cg.replay()
+
+    def result(self) -> dict:
+        """Waits for the tick; status, path (host list) and cost."""
+        st = self.pl.wait()
+        L = int(self.h_len.item())
+        return {"status": st, "path": self.h_path[:L].tolist() if st == PLAN_OK else None,
+                "cost": float(self.h_cost.item()), "edges": int(self.out.count.item()), "info": self.pl.info()}
+
+    def tick(self, obstacles, start_pos, goal_pos) -> dict:
+        self.tick_async(obstacles, start_pos, goal_pos)
+        r = self.result()
+        if r["status"] == PLAN_ERR_CAPACITY and r["info"].get("detail") == DET_CUTLIST:
+            # the pair list has grown at plan_wait: capture again and repeat
+            self.capture(obstacles, start_pos, goal_pos)
+            self.tick_async(obstacles, start_pos, goal_pos)
+            r = self.result()
+        return r
