@@ -48,12 +48,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=0, help="rows of the oracle sample (0: auto)")
     ap.add_argument("--form", default="plain",
-                    choices=["plain", "fp64", "tf32", "bf16", "batched", "refine", "cut", "replan"],
+                    choices=["plain", "fp64", "tf32", "bf16", "batched", "refine", "cut", "replan", "planes"],
                     help="plain: 3-D FP32 workload (the default line); fp64: 2-D FP64 plain method; tf32/bf16: "
                          "precision form on the 2-D workload; batched: 256 uneven queries in one graph replay; "
                          "refine: 65536-segment forward+backward; cut: keep-out cut of a 5000-state graph "
                          "against 500 obstacles, then the search; replan: the captured replanning tick "
-                         "(moving obstacles in, cut + search, path out)")
+                         "(moving obstacles in, cut + search, path out); planes: closest points and separating "
+                         "planes of 5000 nodes x 500 obstacles")
     ap.add_argument("--queries", type=int, default=256)
     ap.add_argument("--pipeline", type=int, default=-1,
                     help="FP32 pair kernel of the plain line: 0 screened, 1 warp-specialised, 2 unscreened "
@@ -309,6 +310,8 @@ def run_form(args):
             line.update(run_cut_form(args, stream, flush, dev))
         elif args.form == "replan":
             line.update(run_replan_form(args, stream, flush, dev))
+        elif args.form == "planes":
+            line.update(run_planes_form(args, stream, flush, dev))
         elif args.form == "refine":
             from paper_2411_13507_gb300 import refine as RF
             rb = synth.refine_segments(seed=args.seed, S=65536)
@@ -549,6 +552,70 @@ def run_replan_form(args, stream, flush, dev):
             "e2e": {"value": 1e3 / statistics.mean(wall), "unit": "ticks/s", "h2d_bytes_per_step": bi,
                     "d2h_bytes_per_step": bo, "ms_per_step": statistics.mean(wall)},
             "cpu_baseline": None}
+
+
+def run_planes_form(args, stream, flush, dev):
+    """closestPoint / adjacentHyperplane (Algorithm 2, Sec. III-D) for every
+    (node, obstacle) pair: the 5000 states of the keep-out workload against
+    its 500 obstacles, FP32, all-pairs outputs plus the nearest obstacle."""
+    import torch
+    from paper_2411_13507_gb300 import plan as P
+    from paper_2411_13507_gb300 import synth
+    prob, obs = synth.keepout_2d(seed=1, dtype="f32")
+    pl = P.Planner(2, 2, 5, (2.0, 4.0), arith="f32", input="f32", stream=stream)
+    pts = torch.as_tensor(np.ascontiguousarray(prob.states[:, :2], dtype=np.float32)).to(dev)
+    do = P.obstacles_to_device(obs, input="f32")
+    out = pl.obstacle_planes(pts, do)           # sizes scratch, allocates outputs
+    Pn, n = pts.shape[0], obs.n
+    pairs = Pn * n
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t0 = time.time()
+        while clk.count() < 1 and time.time() - t0 < 10.0:
+            pl.obstacle_planes_async(pts, do, out)
+            torch.cuda.synchronize()
+        mark = max(0, clk.count() - 1)
+        ms = timed(lambda: pl.obstacle_planes_async(pts, do, out), stream, args.steps, args.warmup, flush)
+        t0 = time.time()
+        while clk.count() < mark + 2 and time.time() - t0 < 5.0:
+            pl.obstacle_planes_async(pts, do, out)
+            torch.cuda.synchronize()
+    clocks = clk.summary(since=mark)
+    assert pl.wait() == P.PLAN_OK
+    # bytes the call must move: the outputs (closest m, plane m + 1, distance
+    # per pair; nearest index and distance per point) and the inputs
+    out_bytes = pairs * 4 * (2 + 3 + 1) + Pn * 8
+    in_bytes = Pn * 8 + int(np.asarray(obs.b).shape[0]) * 16 + (n + 1) * 4
+    mean_ms = statistics.mean(ms)
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = (out_bytes + in_bytes) / (mean_ms / 1e3) / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import planes as OP
+        t0 = time.perf_counter()
+        k = 0
+        A = np.asarray(obs.A, dtype=np.float32).astype(np.float64)
+        bb = np.asarray(obs.b, dtype=np.float32).astype(np.float64)
+        P32 = np.asarray(prob.states[:, :2], dtype=np.float32).astype(np.float64)
+        while time.perf_counter() - t0 < 10.0 and k < Pn:
+            OP.planes(P32[k:k + 1], obs.off, A, bb)
+            k += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": k * n / dt, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+               "sample": f"{k} of {Pn} nodes x {n} obstacles ({dt:.1f} s, numpy FP64 active-set enumeration)"}
+    return {"metric": "closest points + separating planes per second ((node, obstacle) pairs), 5000 nodes x 500 "
+                      "obstacles", "value": pairs * 1e3 / mean_ms, "unit": "pairs/s", "dtype": "f32",
+            "ms_per_step": mean_ms, "gpu_launches": 4, "clocks": clocks,
+            "config": {"workload": "keepout_2d seed 1 states (5000) against its 500 obstacles (4-7 rows)",
+                       "pairs": pairs,
+                       "l2": "flushed before every timed call (256 MB write)",
+                       "paper_context": "adjacentHyperplane 0.61 ms on an RTX 4090 (Table 1; counts not stated)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "kernel": "k_planes<2> (whole call)",
+                         "bytes_per_launch": out_bytes + in_bytes,
+                         "peak_note": f"copy bandwidth ({peak_src})",
+                         "note": "algorithmic bytes: 24 B of outputs per pair + 8 B per node + the inputs"},
+            "e2e": None, "cpu_baseline": cpu}
 
 
 def main():

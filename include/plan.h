@@ -309,6 +309,33 @@ typedef struct {
 int plan_cut_edges(plan_ctx* ctx, int N, const void* states, int nT, const double* T, const plan_edges* in,
                    const plan_obstacles* obst, const plan_edges* out);
 
+/*
+ * closestPoint and adjacentHyperplane (Algorithm 2; the separating hyperplane
+ * between a node and an obstacle of Sec. III-D): for every point p and
+ * obstacle o, the point z of o nearest to p (Euclidean projection onto
+ * {z : A z <= b}), its distance d, and the hyperplane through z with unit
+ * normal toward p, h = (p - z) / d, l = h . z (the obstacle lies in
+ * {h . z <= l}, p at distance d on the other side).  A point inside its
+ * obstacle: d = 0, z = p, h = 0, l = 0.  Also, per point, the nearest obstacle
+ * (ties to the lower index).  The obstacle's faces and edges (edges as
+ * segments) are computed in FP64 once per call; each (point, obstacle) then
+ * takes, in FP32, the nearest of the face projections that land inside the
+ * obstacle and of the edge segments' closest points.  Model: m = 2 or 3
+ * (gamma and degree do not matter).
+ *   P            number of points, 0 .. 1<<24
+ *   points       device [P][m], the model's input type
+ *   obst         obstacles (plan_obstacles, at most 16 rows each)
+ *   closest      device float [P][n][m] or NULL
+ *   plane        device float [P][n][m+1] (h, then l) or NULL
+ *   dist         device float [P][n] or NULL
+ *   nearest      device int32 [P] (-1 when n = 0) or NULL
+ *   nearest_dist device float [P] (+inf when n = 0) or NULL
+ * Errors: INVALID_ARG / UNSUPPORTED on the host; UNSUPPORTED on the device for
+ * an obstacle above max_rows.
+ */
+int plan_obstacle_planes(plan_ctx* ctx, int P, const void* points, const plan_obstacles* obst, float* closest,
+                         float* plane, float* dist, int32_t* nearest, float* nearest_dist);
+
 /* Weights of the refinement objective (defaults 1, 1, 0.1). */
 typedef struct {
     double w_snap;  /* weight of the snap energy */

@@ -121,6 +121,14 @@ struct plan_ctx {
     int* cut_ocount = nullptr;
     long long cut32Cap = 0, want_cut32 = 0;
     unsigned long long* cut_list32 = nullptr;
+    // closest points / planes
+    long long capPlO = -1, capPlR = -1, capPlE = -1, capPlP = -1;
+    float* pl_orow = nullptr;
+    float* pl_face = nullptr;
+    float* pl_edge = nullptr;
+    int* pl_nedge = nullptr;
+    int* pl_ocount = nullptr;
+    unsigned long long* pl_keys = nullptr;
     // timing
     bool timing = false;
     bool accounting = false;
@@ -390,7 +398,7 @@ void plan_destroy(plan_ctx* c) {
                    c->resBits, c->resKey, c->emitPre, c->recheck, c->sdist, c->sbest, c->spred, c->sfront, c->slast, c->snear,
                    c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem, c->d_qMem, c->d_sqd, c->memOff,
                    c->d_cut64, c->d_cut32, c->cut_src, c->cut_hit, c->cut_pos, c->cut_chunk, c->cut_orow,
-                   c->cut_ocount, c->cut_list32, c->cut_okb, c->cut_obox};
+                   c->cut_ocount, c->cut_list32, c->cut_okb, c->cut_obox, c->pl_orow, c->pl_face, c->pl_edge, c->pl_nedge, c->pl_ocount, c->pl_keys};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_tab64) cudaFreeHost(c->h_tab64);
@@ -1024,6 +1032,73 @@ int plan_cut_edges(plan_ctx* c, int N, const void* states, int nT, const double*
     if (c->timing) cudaEventRecord(c1, c->stream);
     c->launches += launches;
     if (ce != 0) return cuda_fail(c, (cudaError_t)ce, "cut launch");
+    return PLAN_OK;
+}
+
+int plan_obstacle_planes(plan_ctx* c, int P, const void* points, const plan_obstacles* obst, float* closest,
+                         float* plane, float* dist, int32_t* nearest, float* nearest_dist) {
+    if (!c) return PLAN_ERR_INVALID_ARG;
+    const int m = c->model.m;
+    if (m < 2 || m > 3) return fail(c, PLAN_ERR_UNSUPPORTED, "closest points for m = 2 or 3 only");
+    if (P < 0 || P > (1 << 24) || (P > 0 && !points)) return fail(c, PLAN_ERR_INVALID_ARG, "bad points");
+    if (!obst || obst->n < 0 || obst->n > (1 << 20) || (obst->n > 0 && !obst->off))
+        return fail(c, PLAN_ERR_INVALID_ARG, "bad obstacles");
+    if (obst->n > 0 && (obst->max_rows < 1 || obst->max_rows > CUT_RMAX))
+        return fail(c, PLAN_ERR_INVALID_ARG, "obstacle max_rows must be 1..16");
+    if ((long long)P * obst->n > (1LL << 40)) return fail(c, PLAN_ERR_INVALID_ARG, "too many (point, obstacle) pairs");
+    const int maxr = obst->n > 0 ? obst->max_rows : 1;
+    const long long nob = obst->n > 0 ? obst->n : 1;
+    const int max_edges = m == 2 ? maxr : (maxr * (maxr - 1)) / 2 > 0 ? (maxr * (maxr - 1)) / 2 : 1;
+    if (nob > c->capPlO || nob * maxr > c->capPlR || nob * max_edges > c->capPlE) {
+        if (!dalloc(c, &c->pl_ocount, nob) || !dalloc(c, &c->pl_orow, 4 * nob * maxr) ||
+            !dalloc(c, &c->pl_face, 4 * nob * maxr) || !dalloc(c, &c->pl_edge, 16 * nob * max_edges) ||
+            !dalloc(c, &c->pl_nedge, nob)) {
+            c->capPlO = c->capPlR = c->capPlE = -1;
+            return PLAN_ERR_NO_MEMORY;
+        }
+        c->capPlO = nob;
+        c->capPlR = nob * maxr;
+        c->capPlE = nob * max_edges;
+    }
+    const bool want_near = nearest || nearest_dist;
+    if (want_near && P > c->capPlP) {
+        if (!dalloc(c, &c->pl_keys, P)) {
+            c->capPlP = -1;
+            return PLAN_ERR_NO_MEMORY;
+        }
+        c->capPlP = P;
+    }
+    PlanesParams Q;
+    memset(&Q, 0, sizeof(Q));
+    Q.m = m;
+    Q.in_f32 = c->model.input == PLAN_IN_F32;
+    Q.P = P;
+    Q.n_obst = obst->n;
+    Q.max_orows = maxr;
+    Q.points = points;
+    Q.obst_off = obst->off;
+    Q.A = obst->A;
+    Q.b = obst->b;
+    Q.orow = c->pl_orow;
+    Q.max_edges = max_edges;
+    Q.face = c->pl_face;
+    Q.edge = c->pl_edge;
+    Q.nedge = c->pl_nedge;
+    Q.ocount = c->pl_ocount;
+    Q.closest = closest;
+    Q.plane = plane;
+    Q.dist = dist;
+    Q.nearest = nearest;
+    Q.nearest_dist = nearest_dist;
+    Q.keys = want_near ? c->pl_keys : nullptr;
+    Q.info = c->d_info;
+    cudaError_t e = cudaSuccess;
+    if (want_near && P > 0) e = cudaMemsetAsync(c->pl_keys, 0xff, sizeof(unsigned long long) * (size_t)P, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset planes scratch");
+    int launches = 0;
+    int ce = launch_planes(Q, c->stream, c->num_sms, &launches);
+    c->launches += launches;
+    if (ce != 0) return cuda_fail(c, (cudaError_t)ce, "planes launch");
     return PLAN_OK;
 }
 

@@ -296,6 +296,28 @@ struct CutParams {
     DevInfo* info;
 };
 
+// closestPoint / adjacentHyperplane (plan_planes.cu).
+struct PlanesParams {
+    int m, in_f32, P, n_obst, max_orows;
+    const void* points;        // [P][m], input type
+    const int32_t* obst_off;
+    const void* A;
+    const void* b;
+    int max_edges;             // edge slots per obstacle (max_orows in 2-D, max_orows (max_orows - 1) / 2 in 3-D)
+    float* orow;               // [n_obst * max_orows][4] {A_0, A_1, A_2, b}
+    float* face;               // [n_obst * max_orows][4] unit normal, offset
+    float* edge;               // [n_obst * max_edges][16] base point, t_lo; direction, t_hi; normals (see plan_planes.cu)
+    int* nedge;                // [n_obst] edges found
+    int* ocount;               // [n_obst]
+    float* closest;            // [P][n_obst][m] or null
+    float* plane;              // [P][n_obst][m+1] or null
+    float* dist;               // [P][n_obst] or null
+    int32_t* nearest;          // [P] or null
+    float* nearest_dist;       // [P] or null
+    unsigned long long* keys;  // [P] nearest keys (distance bits << 32 | obstacle), or null
+    DevInfo* info;
+};
+
 // Launchers (plan_build.cu / plan_search.cu / plan_refine.cu); return cudaError_t as int.
 int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_sm, void* ev_pair_begin,
                  void* ev_pair_end, int* launches);
@@ -307,5 +329,6 @@ bool tc_supported(int m, int g, int p);
 bool refine_supported(int m, int g, int p);
 int launch_refine(const RefineParams& R, void* stream, int* launches);
 int launch_cut(const CutParams& C, void* stream, int num_sms, int* launches, void* ev_scan_begin, void* ev_scan_end);
+int launch_planes(const PlanesParams& Q, void* stream, int num_sms, int* launches);
 
 }  // namespace plan

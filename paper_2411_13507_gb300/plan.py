@@ -83,7 +83,7 @@ class _RefineW(ctypes.Structure):
 EXPORTS = ["plan_create", "plan_destroy", "plan_build_edges", "plan_search", "plan_wait", "plan_model_tables",
            "plan_set_search_limits", "plan_refine", "plan_prepare_batched", "plan_build_edges_batched",
            "plan_set_tile", "plan_autotune", "plan_prepare_search_batched", "plan_search_batched",
-           "plan_search_noalloc", "plan_cut_edges", "plan_cut_timing", "plan_search_at", "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
+           "plan_search_noalloc", "plan_cut_edges", "plan_cut_timing", "plan_search_at", "plan_obstacle_planes", "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
 
 
 def lib_path() -> str:
@@ -129,6 +129,8 @@ def load(build_if_stale: bool = True):
     lib.plan_cut_edges.argtypes = [vp, i32, vp, i32, dp, ctypes.POINTER(_Edges), ctypes.POINTER(_Obstacles),
                                    ctypes.POINTER(_Edges)]
     lib.plan_cut_edges.restype = i32
+    lib.plan_obstacle_planes.argtypes = [vp, i32, vp, ctypes.POINTER(_Obstacles), vp, vp, vp, vp, vp]
+    lib.plan_obstacle_planes.restype = i32
     lib.plan_search_at.argtypes = [vp, i32, vp, ctypes.POINTER(_Edges), vp, vp, i32, vp, vp]
     lib.plan_search_at.restype = i32
     lib.plan_cut_timing.argtypes = [vp, dp, dp, ctypes.POINTER(i64), i32]
@@ -415,6 +417,34 @@ class Planner:
                                   ctypes.c_void_p(out["path_len"].data_ptr()), ctypes.c_void_p(out["cost"].data_ptr()))
         if rc != 0:
             raise self._err(rc, "plan_search")
+
+    def obstacle_planes_async(self, points, obst: DeviceObstacles, out: dict) -> None:
+        """plan_obstacle_planes into the device tensors of ``out`` (keys closest,
+        plane, dist, nearest, nearest_dist; any may be None)."""
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+        rc = self.lib.plan_obstacle_planes(self.ctx, int(points.shape[0]), ctypes.c_void_p(points.data_ptr()),
+                                           ctypes.byref(obst.cstruct()), ptr(out.get("closest")), ptr(out.get("plane")),
+                                           ptr(out.get("dist")), ptr(out.get("nearest")), ptr(out.get("nearest_dist")))
+        if rc != 0:
+            raise self._err(rc, "plan_obstacle_planes")
+
+    def obstacle_planes(self, points, obst: DeviceObstacles, nearest_only: bool = False) -> dict:
+        """Closest points, distances, separating planes (all pairs unless
+        nearest_only) and the nearest obstacle of every point."""
+        import torch
+        P, n, m = int(points.shape[0]), int(obst.n), int(self.model.m)
+        dev = points.device
+        out = {"nearest": torch.empty(P, dtype=torch.int32, device=dev),
+               "nearest_dist": torch.empty(P, dtype=torch.float32, device=dev)}
+        if not nearest_only:
+            out.update({"closest": torch.empty((P, n, m), dtype=torch.float32, device=dev),
+                        "plane": torch.empty((P, n, m + 1), dtype=torch.float32, device=dev),
+                        "dist": torch.empty((P, n), dtype=torch.float32, device=dev)})
+        self.obstacle_planes_async(points, obst, out)
+        st = self.wait()
+        if st != PLAN_OK:
+            raise self._err(st, "obstacle_planes")
+        return out
 
     def search_at_async(self, dp: DeviceProblem, graph: Graph, endpoints, out: dict) -> None:
         """plan_search_at: start and goal read from the device tensor
