@@ -62,8 +62,8 @@ def parse():
     return ap.parse_args()
 
 
-PAIR_KERNEL = {0: "k_pairs_fast<3,3,7,true> (screened)", 1: "k_pairs_ws<3,3,7>",
-               2: "k_pairs_fast<3,3,7,false> (unscreened)"}
+PAIR_KERNEL = {0: "k_pairs_sc<3,3,7> (screened)", 1: "k_pairs_ws<3,3,7>",
+               2: "k_pairs_fast<3,3,7> (unscreened)"}
 
 
 def workload(seed):
