@@ -176,25 +176,40 @@ __global__ void k_member(BuildParams P) {
     if (in) {
         const int r0 = Q.poly_off[k], r1 = Q.poly_off[k + 1];
         if (r1 - r0 > P.max_rows || r1 > Q.K * P.max_rows || r0 < 0) in = false;
-        for (int r = r0; r < r1 && in; ++r) {
-            const long long rg = Q.rowsOff + r;
-            float s = 0.f, mag = 0.f;
-            for (int a = 0; a < m; ++a) {
-                const float av = P.A32[rg * m + a];
-                s = fmaf(av, x32[a], s);
-                mag = fmaf(fabsf(av), fabsf(x32[a]), mag);
+        // four rows per step: their loads are issued together
+        for (int rb = r0; rb < r1 && in; rb += 4) {
+            float av[4][4], lim[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long rg = Q.rowsOff + rb + u;
+                const bool ok = rb + u < r1;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) av[u][a] = (ok && a < m) ? P.A32[rg * m + a] : 0.f;
+                lim[u] = ok ? P.blim32[rg] : 0.f;
             }
-            const float lim = P.blim32[rg];
-            const float d = s - lim;
-            const float band = KMEM * (mag + fabsf(lim));
-            if (!(d < -band)) {
-                if (d > band) {
-                    in = false;
-                } else {  // within the band (or NaN): canonical FP64 row
-                    double sd = 0.0;
-                    for (int a = 0; a < m; ++a)
-                        sd = __dadd_rn(sd, __dmul_rn(ldv(Q.A, (long long)r * m + a, P.in_f32), x64[a]));
-                    if (!(sd <= P.blim64[rg])) in = false;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (rb + u >= r1 || !in) break;
+                const long long rg = Q.rowsOff + rb + u;
+                float s = 0.f, mag = 0.f;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    if (a < m) {
+                        s = fmaf(av[u][a], x32[a], s);
+                        mag = fmaf(fabsf(av[u][a]), fabsf(x32[a]), mag);
+                    }
+                }
+                const float d = s - lim[u];
+                const float band = KMEM * (mag + fabsf(lim[u]));
+                if (!(d < -band)) {
+                    if (d > band) {
+                        in = false;
+                    } else {  // within the band (or NaN): canonical FP64 row
+                        double sd = 0.0;
+                        for (int a = 0; a < m; ++a)
+                            sd = __dadd_rn(sd, __dmul_rn(ldv(Q.A, (long long)(rb + u) * m + a, P.in_f32), x64[a]));
+                        if (!(sd <= P.blim64[rg])) in = false;
+                    }
                 }
             }
         }
@@ -212,7 +227,7 @@ __global__ void __launch_bounds__(1024) k_lists(BuildParams P) {
     const QueryDesc& Q = P.qd[q];
     const int k = (int)(blockIdx.x - P.pfxPoly[q]);
     __shared__ int warpTot[32];
-    __shared__ int s_base;
+    __shared__ int s_base, s_step;
     __shared__ float s_c[4];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (threadIdx.x == 0) s_base = 0;
@@ -221,32 +236,44 @@ __global__ void __launch_bounds__(1024) k_lists(BuildParams P) {
     const uint32_t bit = 1u << (k & 31);
     int* members = P.members + Q.listOff + (long long)k * Q.N;
     int* localIdx = P.localIdx + Q.listOff + (long long)k * Q.N;
-    for (int i0 = 0; i0 < Q.N; i0 += blockDim.x) {
-        const int i = i0 + threadIdx.x;
-        const bool mem = i < Q.N && (P.memMask[Q.maskOff + (long long)i * Q.W + w] & bit);
-        const unsigned bal = __ballot_sync(0xffffffffu, mem);
-        const int pre = __popc(bal & ((1u << lane) - 1u));
-        if (lane == 0) warpTot[wid] = __popc(bal);
+    constexpr int PER = 8;  // consecutive states per thread: one block step covers 8192 states
+    for (int i0 = 0; i0 < Q.N; i0 += blockDim.x * PER) {
+        const int ib = i0 + threadIdx.x * PER;
+        unsigned mine = 0;  // bit u: state ib + u is a member
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int i = ib + u;
+            if (i < Q.N && (P.memMask[Q.maskOff + (long long)i * Q.W + w] & bit)) mine |= 1u << u;
+        }
+        const int cnt = __popc(mine);
+        int inc = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) warpTot[wid] = inc;
         __syncthreads();
         if (wid == 0) {
             int v = lane < nw ? warpTot[lane] : 0;
-            int inc = v;
+            int wi = v;
             for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += y;
+                int y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
             }
-            if (lane < nw) warpTot[lane] = inc - v;
+            if (lane < nw) warpTot[lane] = wi - v;
+            if (lane == nw - 1) s_step = wi;  // the step's total
         }
         __syncthreads();
-        if (mem) {
-            const int pos = s_base + warpTot[wid] + pre;
+        int pos = s_base + warpTot[wid] + inc - cnt;
+        for (unsigned bits = mine; bits; bits &= bits - 1u, ++pos) {
+            const int i = ib + __ffs(bits) - 1;
             int npoly = 0;
             for (int w2 = 0; w2 < Q.W; ++w2) npoly += __popc(P.memMask[Q.maskOff + (long long)i * Q.W + w2]);
             members[pos] = i | (npoly > 1 ? MULTI_BIT : 0);
             localIdx[i] = pos;
         }
         __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) s_base += warpTot[wid] + pre + (mem ? 1 : 0);
+        if (threadIdx.x == 0) s_base += s_step;
         __syncthreads();
     }
     const int nk = s_base;
