@@ -251,6 +251,28 @@ int plan_search(plan_ctx* ctx, int N, const void* states, const plan_edges* edge
 int plan_search_at(plan_ctx* ctx, int N, const void* states, const plan_edges* edges, const double* endpoints,
                    int32_t* path, int path_cap, int32_t* path_len, double* cost);
 
+/*
+ * Goal-rooted search for a replanning loop (Alg. 1 line 4 every tick; Sec.
+ * III-C): start and goal vertices as plan_search_at (nearest to device
+ * endpoints [2][m]); then the distance of every vertex TO the goal vertex, the
+ * fixed point of d[u] = min over out-edges (u -> v) of (w + d[v]) in FP64,
+ * and the path from the start along the successors (the out-neighbour v
+ * minimising (w + d[v], v)); cost = d[start].  warm != 0: when the goal vertex
+ * and N equal those of the previous plan_search_to call on this context, every
+ * vertex whose successor chain to the goal still exists with weights no larger
+ * than before keeps its previous distance and the rest restart from +inf; the
+ * result equals a cold start (only the number of sweeps changes).  Rows of
+ * the CSR must be sorted by column (as plan_build_edges and plan_cut_edges
+ * write them).  One cooperative launch over every SM, like plan_search.
+ * Among equal-cost paths it may return another one than plan_search, and the
+ * cost may differ from plan_search's in the last bits (the path sum is
+ * rounded from the goal end).  N, states, edges, path, path_cap, path_len
+ * and cost as plan_search; endpoints as plan_search_at.  Device status as
+ * plan_search (NO_PATH, CAPACITY, TIMEOUT).
+ */
+int plan_search_to(plan_ctx* ctx, int N, const void* states, const plan_edges* edges, const double* endpoints,
+                   int warm, int32_t* path, int path_cap, int32_t* path_len, double* cost);
+
 /* Bounds of the search kernel's device loops: at most max_sweeps frontier
  * sweeps (default N+1, the Bellman-Ford bound) and spin_limit polls of the
  * grid barrier (default 2^24).  0 keeps the default.  When a bound runs out

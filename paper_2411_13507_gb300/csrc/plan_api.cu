@@ -121,6 +121,13 @@ struct plan_ctx {
     int* cut_ocount = nullptr;
     long long cut32Cap = 0, want_cut32 = 0;
     unsigned long long* cut_list32 = nullptr;
+    // goal-rooted search (kept between calls for the warm start)
+    long long capGoal = -1;
+    double* g_d = nullptr;
+    int* g_succ = nullptr;
+    double* g_wsucc = nullptr;
+    unsigned* g_anc = nullptr;
+    int* g_prev = nullptr;
     // closest points / planes
     long long capPlO = -1, capPlR = -1, capPlE = -1, capPlP = -1;
     float* pl_orow = nullptr;
@@ -398,7 +405,7 @@ void plan_destroy(plan_ctx* c) {
                    c->resBits, c->resKey, c->emitPre, c->recheck, c->sdist, c->sbest, c->spred, c->sfront, c->slast, c->snear,
                    c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem, c->d_qMem, c->d_sqd, c->memOff,
                    c->d_cut64, c->d_cut32, c->cut_src, c->cut_hit, c->cut_pos, c->cut_chunk, c->cut_orow,
-                   c->cut_ocount, c->cut_list32, c->cut_okb, c->cut_obox, c->pl_orow, c->pl_face, c->pl_edge, c->pl_nedge, c->pl_ocount, c->pl_keys};
+                   c->cut_ocount, c->cut_list32, c->cut_okb, c->cut_obox, c->pl_orow, c->pl_face, c->pl_edge, c->pl_nedge, c->pl_ocount, c->pl_keys, c->g_d, c->g_succ, c->g_wsucc, c->g_anc, c->g_prev};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_tab64) cudaFreeHost(c->h_tab64);
@@ -1032,6 +1039,70 @@ int plan_cut_edges(plan_ctx* c, int N, const void* states, int nT, const double*
     if (c->timing) cudaEventRecord(c1, c->stream);
     c->launches += launches;
     if (ce != 0) return cuda_fail(c, (cudaError_t)ce, "cut launch");
+    return PLAN_OK;
+}
+
+int plan_search_to(plan_ctx* c, int N, const void* states, const plan_edges* edges, const double* endpoints, int warm,
+                   int32_t* path, int path_cap, int32_t* path_len, double* cost) {
+    if (!c) return PLAN_ERR_INVALID_ARG;
+    if (N < 1 || N > (1 << 20) || !states) return fail(c, PLAN_ERR_INVALID_ARG, "need N >= 1 states");
+    if (!edges || !edges->row_off || !edges->count || edges->cap < 0 || (edges->cap > 0 && (!edges->col || !edges->w)))
+        return fail(c, PLAN_ERR_INVALID_ARG, "bad CSR");
+    if (!endpoints || !path || path_cap < 1 || !path_len || !cost) return fail(c, PLAN_ERR_INVALID_ARG, "bad search output");
+    if (N > c->capGoal) {
+        if (!dalloc(c, &c->g_d, N) || !dalloc(c, &c->g_succ, N) || !dalloc(c, &c->g_wsucc, N) ||
+            !dalloc(c, &c->g_anc, 2LL * N) || !dalloc(c, &c->g_prev, 2)) {
+            c->capGoal = -1;
+            return PLAN_ERR_NO_MEMORY;
+        }
+        c->capGoal = N;
+        cudaError_t e = cudaMemsetAsync(c->g_prev, 0xff, 2 * sizeof(int), c->stream);  // no previous call
+        if (e != cudaSuccess) return cuda_fail(c, e, "memset search state");
+    }
+    if (!c->snear && !dalloc(c, &c->snear, 4LL * SEARCH_MAX_BLOCKS)) return PLAN_ERR_NO_MEMORY;
+    if (c->num_sms > SEARCH_MAX_BLOCKS) return fail(c, PLAN_ERR_UNSUPPORTED, "more SMs than the search scratch holds");
+    GoalSearchParams G;
+    memset(&G, 0, sizeof(G));
+    G.N = N;
+    G.m = c->model.m;
+    G.n = c->model.m * c->model.gamma;
+    G.in_f32 = c->model.input == PLAN_IN_F32;
+    G.w_f64 = c->model.arith == PLAN_F64;
+    G.warm = warm != 0;
+    G.max_sweeps = c->max_sweeps > 0 ? c->max_sweeps : N + 1;
+    G.states = states;
+    G.row_off = edges->row_off;
+    G.col = edges->col;
+    G.w = edges->w;
+    G.count = edges->count;
+    G.cap = edges->cap;
+    G.endpoints = endpoints;
+    G.d = c->g_d;
+    G.succ = c->g_succ;
+    G.wsucc = c->g_wsucc;
+    G.anc = c->g_anc;
+    G.near_blk = c->snear;
+    G.prev = c->g_prev;
+    G.spin_limit = c->spin_limit > 0 ? c->spin_limit : (1LL << 24);
+    G.path = path;
+    G.path_cap = path_cap;
+    G.path_len = path_len;
+    G.cost = cost;
+    G.info = c->d_info;
+    cudaError_t e = cudaMemsetAsync(&c->d_info->bar[0], 0, sizeof(unsigned long long) * 3, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset barrier");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->timing) {
+        e0 = take_event(c);
+        e1 = take_event(c);
+        c->ev_search.emplace_back(e0, e1);
+        cudaEventRecord(e0, c->stream);
+    }
+    int launches = 0;
+    int ce = launch_search_to(G, c->stream, c->num_sms, &launches);
+    if (c->timing) cudaEventRecord(e1, c->stream);
+    c->launches += launches;
+    if (ce != 0) return cuda_fail(c, (cudaError_t)ce, "search launch");
     return PLAN_OK;
 }
 

@@ -296,6 +296,30 @@ struct CutParams {
     DevInfo* info;
 };
 
+// Goal-rooted search with a warm start (plan_search.cu).
+struct GoalSearchParams {
+    int N, m, n, in_f32, w_f64, warm, max_sweeps;
+    long long spin_limit;      // grid-barrier poll bound
+    const void* states;
+    const int32_t* row_off;
+    const int32_t* col;
+    const void* w;
+    const int64_t* count;
+    long long cap;
+    const double* endpoints;   // device [2][m]: start, goal positions
+    double* d;                 // [N] distance to the goal vertex (kept for the next call)
+    int* succ;                 // [N] next vertex toward the goal (kept)
+    double* wsucc;             // [N] weight of that edge (kept)
+    unsigned* anc;             // [2][N] pointer-jumping links, ancestor | chain ok << 31 (two buffers)
+    unsigned long long* near_blk;  // [4 * blocks] per-block nearest start/goal candidates
+    int* prev;                 // device [2]: goal vertex and N of the last call (-1 when none)
+    int32_t* path;
+    int path_cap;
+    int32_t* path_len;
+    double* cost;
+    DevInfo* info;
+};
+
 // closestPoint / adjacentHyperplane (plan_planes.cu).
 struct PlanesParams {
     int m, in_f32, P, n_obst, max_orows;
@@ -323,6 +347,7 @@ int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_s
                  void* ev_pair_end, int* launches);
 int launch_search(const SearchParams& P, void* stream, int num_sms, int* launches);
 int launch_search_batched(const BatchSearchParams& P, void* stream, int* launches);
+int launch_search_to(const GoalSearchParams& G, void* stream, int num_sms, int* launches);
 int launch_account(const BuildParams& P, void* stream, int num_sms, unsigned long long* work);
 bool model_supported(int m, int g, int p);
 bool tc_supported(int m, int g, int p);

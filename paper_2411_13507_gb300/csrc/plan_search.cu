@@ -587,6 +587,388 @@ __global__ void __launch_bounds__(1024) k_search_batched(BatchSearchParams B) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Goal-rooted search with a warm start (the replanning loop of Alg. 1: line 4
+// every tick on a graph that changes only where obstacles moved; Sec. III-C
+// distances and path).  One cooperative launch, one 1024-thread block per SM.
+//
+// d[u] = distance from u to the goal vertex: the fixed point of
+// d[u] = min over out-edges (u -> v) of fl(w + d[v]), d[goal] = 0, reached by
+// pull sweeps over the out-edges (no reverse graph); succ[u] = the
+// out-neighbour minimising (w + d[v], v).  With non-negative weights fl(w + x)
+// is monotone in x and >= x, so iterating from +inf converges to the greatest
+// fixed point, the minimum over paths of the right-to-left rounded path sum.
+//
+// Warm start: when the goal vertex and N are those of the previous call, a
+// vertex keeps its previous d when its successor chain to the goal still
+// exists with weights no larger than before; every other vertex restarts from
+// +inf.  A kept value was fl(old weight + old d of the successor) down the
+// whole chain, so it is at least the new chain's rounded sum, an upper bound
+// of the new fixed point; iterating the monotone sweep from any upper bound
+// reaches the same greatest fixed point, so the result equals a cold start and
+// only the number of sweeps changes.  The chains are checked by pointer
+// jumping (log rounds) on links packed as anc | ok << 31.  A call that stops
+// early leaves no warm state behind.
+//
+// Phases:
+//   0. every thread takes vertices v = gtid, gtid + threads, ...: nearest
+//      start/goal candidates and, when a warm start is possible, the link of v
+//      (ok when the out-edge (v, succ[v]) is still in v's row -- rows sorted by
+//      column, binary search -- with a weight <= the kept one and d[v] finite;
+//      the previous goal is its own ok ancestor);  grid barrier;
+//   1. every block reduces the candidates; warm start: pointer jumping in each
+//      block's shared memory (N <= TO_SMEM_N; else in global memory, one grid
+//      barrier per round) and d reset off the valid chains; cold: d = +inf,
+//      d[goal] = 0;  grid barrier;
+//   2. sweeps: one warp per vertex u (u = warp, warp + warps, ...), lanes over
+//      u's out-edges; each lane keeps its first edge of its first TO_KC
+//      vertices in registers across sweeps; grid barrier per sweep, whose
+//      raised count says whether any block lowered a distance;
+//   3. successors, same layout;  grid barrier;
+//   4. block 0 walks start -> goal along succ.
+// ---------------------------------------------------------------------------
+constexpr int TO_KC = 2;            // owned vertices per warp held in registers
+constexpr int TO_SMEM_N = 24576;    // pointer jumping in shared memory up to this N (8 bytes a vertex)
+constexpr unsigned TO_OK = 0x80000000u;
+
+namespace {
+DEVI double ldw(const GoalSearchParams& G, long long e) {
+    return G.w_f64 ? __ldg(&((const double*)G.w)[e]) : (double)__ldg(&((const float*)G.w)[e]);
+}
+
+// (c, v, w) lexicographic minimum (successor choice; w only breaks exact ties of duplicate columns)
+DEVI void keep_succ(double& c, int& v, double& w, double oc, int ov, double ow) {
+    if (oc < c || (oc == c && (ov < v || (ov == v && ow < w)))) {
+        c = oc;
+        v = ov;
+        w = ow;
+    }
+}
+
+// One pointer-jumping round over v = begin, begin + step, ... on packed links.
+template <bool GLOBAL>
+DEVI int jump_round(const unsigned* a0, unsigned* a1, int begin, int step, int N) {
+    int changed = 0;
+    for (int v = begin; v < N; v += step) {
+        const unsigned x = GLOBAL ? ((const volatile unsigned*)a0)[v] : a0[v];
+        const int a = (int)(x & ~TO_OK);
+        const unsigned y = GLOBAL ? ((const volatile unsigned*)a0)[a] : a0[a];
+        const unsigned z = (y & ~TO_OK) | (x & y & TO_OK);
+        if (GLOBAL) ((volatile unsigned*)a1)[v] = z;
+        else a1[v] = z;
+        changed |= z != x;
+    }
+    return changed;
+}
+}  // namespace
+
+__global__ void __launch_bounds__(1024, 1) k_search_to(GoalSearchParams G) {
+    extern __shared__ unsigned s_link[];   // [2][N] packed links (warm start, N <= TO_SMEM_N)
+    __shared__ unsigned long long s_kb[2][32];
+    __shared__ int s_ki[2][32];
+    __shared__ int s_prev[2];
+    const int N = G.N, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const unsigned nb = gridDim.x;
+    const int nthreads = (int)(nb * blockDim.x), gtid = (int)(blockIdx.x * blockDim.x) + tid;
+    const int nwarps = (int)(nb * (blockDim.x >> 5)), gw = gtid >> 5;
+    DevInfo* info = G.info;
+    int bar_round = 0;
+    const double inf = __longlong_as_double(DINF);
+    if (gtid == 0) {
+        const long long E = *G.count;
+        if (E < 0 || E > G.cap) set_status_s(info, PLAN_ERR_INVALID_ARG, DET_OUTPUT);
+    }
+    if (tid == 0) {
+        s_prev[0] = ((volatile int*)G.prev)[0];
+        s_prev[1] = ((volatile int*)G.prev)[1];
+    }
+    __syncthreads();
+    const int pg = s_prev[0];
+    const bool may_warm = G.warm && s_prev[1] == N && pg >= 0 && pg < N;
+
+    // phase 0
+    double sp[4], gp[4];
+    for (int a = 0; a < 4; ++a) {
+        sp[a] = a < G.m ? G.endpoints[a] : 0.0;
+        gp[a] = a < G.m ? G.endpoints[G.m + a] : 0.0;
+    }
+    unsigned long long kb[2] = {~0ull, ~0ull};
+    int ki[2] = {0x7fffffff, 0x7fffffff};
+    for (int v = gtid; v < N; v += nthreads) {
+        double ds = 0.0, dg = 0.0;
+        for (int a = 0; a < G.m; ++a) {
+            const double x = ldd(G.states, (long long)v * G.n + a, G.in_f32);
+            const double ts = __dsub_rn(x, sp[a]), tg = __dsub_rn(x, gp[a]);
+            ds = __dadd_rn(ds, __dmul_rn(ts, ts));
+            dg = __dadd_rn(dg, __dmul_rn(tg, tg));
+        }
+        keep_min(kb[0], ki[0], (unsigned long long)__double_as_longlong(ds), v);
+        keep_min(kb[1], ki[1], (unsigned long long)__double_as_longlong(dg), v);
+        if (may_warm) {
+            unsigned link = (unsigned)v;
+            if (v == pg) {
+                link |= TO_OK;
+            } else {
+                const int sv = G.succ[v];
+                if (sv >= 0 && sv < N && G.d[v] < inf) {
+                    const int r1 = __ldg(&G.row_off[v + 1]);
+                    int lo = __ldg(&G.row_off[v]), hi = r1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (__ldg(&G.col[mid]) < sv) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    if (lo < r1 && __ldg(&G.col[lo]) == sv && ldw(G, lo) <= G.wsucc[v]) link = (unsigned)sv | TO_OK;
+                }
+            }
+            G.anc[v] = link;
+        }
+    }
+    for (int h = 0; h < 2; ++h) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_down_sync(0xffffffffu, kb[h], o);
+            const int oi = __shfl_down_sync(0xffffffffu, ki[h], o);
+            keep_min(kb[h], ki[h], ob, oi);
+        }
+        if (lane == 0) {
+            s_kb[h][wid] = kb[h];
+            s_ki[h][wid] = ki[h];
+        }
+    }
+    __syncthreads();
+    if (tid < 2) {
+        unsigned long long b0 = ~0ull;
+        int i0 = 0x7fffffff;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) keep_min(b0, i0, s_kb[tid][w], s_ki[tid][w]);
+        G.near_blk[4 * blockIdx.x + 2 * tid] = b0;
+        G.near_blk[4 * blockIdx.x + 2 * tid + 1] = (unsigned long long)(unsigned)i0;
+    }
+    if (!grid_sync(info, nb, G.spin_limit, bar_round)) return;
+
+    // phase 1
+    if (tid < 64) {  // warp 0: start over the blocks' candidates; warp 1: goal
+        const int h = tid >> 5;
+        unsigned long long b0 = ~0ull;
+        int i0 = 0x7fffffff;
+        volatile unsigned long long* nbk = G.near_blk;
+        for (unsigned q = lane; q < nb; q += 32) keep_min(b0, i0, nbk[4 * q + 2 * h], (int)nbk[4 * q + 2 * h + 1]);
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_down_sync(0xffffffffu, b0, o);
+            const int oi = __shfl_down_sync(0xffffffffu, i0, o);
+            keep_min(b0, i0, ob, oi);
+        }
+        if (lane == 0) s_ki[h][0] = i0;
+    }
+    __syncthreads();
+    const int start = s_ki[0][0], goal = s_ki[1][0];
+    if (start < 0 || start >= N || goal < 0 || goal >= N) {
+        if (gtid == 0) set_status_s(info, PLAN_ERR_INVALID_ARG, DET_WALK);
+        return;
+    }
+    if (gtid == 0) ((volatile int*)G.prev)[0] = -1;  // d and succ are consistent again only when this call completes
+    const bool warm = may_warm && pg == goal;
+    if (warm) {
+        const unsigned* fin;
+        if (N <= TO_SMEM_N) {
+            unsigned* a0 = s_link;
+            unsigned* a1 = s_link + N;
+            for (int v = tid; v < N; v += blockDim.x) a0[v] = ((const volatile unsigned*)G.anc)[v];
+            __syncthreads();
+            for (int r = 0; r < 64; ++r) {
+                const int any = __syncthreads_or(jump_round<false>(a0, a1, tid, blockDim.x, N));
+                unsigned* t = a0;
+                a0 = a1;
+                a1 = t;
+                if (!any) break;
+            }
+            fin = a0;
+        } else {
+            unsigned* a0 = (unsigned*)G.anc;
+            unsigned* a1 = (unsigned*)G.anc + N;
+            for (int r = 0; r < 64; ++r) {
+                const int ch = __syncthreads_or(jump_round<true>(a0, a1, gtid, nthreads, N));
+                unsigned nraised = 0;
+                if (!grid_sync(info, nb, G.spin_limit, bar_round, ch != 0, &nraised)) return;
+                unsigned* t = a0;
+                a0 = a1;
+                a1 = t;
+                if (nraised == 0) break;
+            }
+            fin = a0;
+        }
+        const bool shared_fin = N <= TO_SMEM_N;
+        for (int v = gtid; v < N; v += nthreads) {
+            const unsigned x = shared_fin ? fin[v] : ((const volatile unsigned*)fin)[v];
+            if (v == goal) G.d[v] = 0.0;
+            else if (x != ((unsigned)goal | TO_OK)) G.d[v] = inf;
+        }
+    } else {
+        for (int v = gtid; v < N; v += nthreads) G.d[v] = v == goal ? 0.0 : inf;
+    }
+    if (!grid_sync(info, nb, G.spin_limit, bar_round)) return;
+
+    // phase 2: sweeps
+    volatile double* d = G.d;
+    int r_e1[TO_KC], r_col[TO_KC], r_next[TO_KC];
+    double r_w[TO_KC];
+#pragma unroll
+    for (int k = 0; k < TO_KC; ++k) {
+        const int u = gw + k * nwarps;
+        r_col[k] = -1;
+        r_w[k] = 0.0;
+        r_e1[k] = 0;
+        r_next[k] = 0;
+        if (u < N) {
+            const int e0 = __ldg(&G.row_off[u]);
+            r_e1[k] = __ldg(&G.row_off[u + 1]);
+            r_next[k] = e0 + 32 + lane;
+            if (e0 + lane < r_e1[k]) {
+                r_col[k] = __ldg(&G.col[e0 + lane]);
+                r_w[k] = ldw(G, e0 + lane);
+            }
+        }
+    }
+    int sweeps = 0;
+    for (;;) {
+        if (sweeps >= G.max_sweeps) {
+            if (gtid == 0) set_status_s(info, PLAN_ERR_TIMEOUT, DET_SWEEPS);
+            return;
+        }
+        ++sweeps;
+        int changed = 0;
+        for (int k = 0, u = gw; u < N; ++k, u += nwarps) {
+            double best = inf;
+            int e = 0, e1 = 0;
+            if (k < TO_KC) {
+                int c = -1;
+                double w = 0.0;
+#pragma unroll
+                for (int q = 0; q < TO_KC; ++q)
+                    if (q == k) {
+                        c = r_col[q];
+                        w = r_w[q];
+                        e = r_next[q];
+                        e1 = r_e1[q];
+                    }
+                if (c >= 0 && c < N) best = __dadd_rn(w, d[c]);
+            } else {
+                e = __ldg(&G.row_off[u]) + lane;
+                e1 = __ldg(&G.row_off[u + 1]);
+            }
+            for (; e < e1; e += 32) {
+                const int c = __ldg(&G.col[e]);
+                if (c < 0 || c >= N) continue;
+                const double x = __dadd_rn(ldw(G, e), d[c]);
+                if (x < best) best = x;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double y = __shfl_xor_sync(0xffffffffu, best, o);
+                if (y < best) best = y;
+            }
+            if (lane == 0 && u != goal && best < d[u]) {
+                d[u] = best;
+                changed = 1;
+            }
+        }
+        const int ch = __syncthreads_or(changed);
+        unsigned nraised = 0;
+        if (!grid_sync(info, nb, G.spin_limit, bar_round, ch != 0, &nraised)) return;
+        if (nraised == 0) break;
+    }
+
+    // phase 3: successors (ties to the lowest id) for the path and the next warm start
+    for (int k = 0, u = gw; u < N; ++k, u += nwarps) {
+        double bc = inf, bw = 0.0;
+        int bv = 0x7fffffff;
+        if (u != goal) {
+            int e = 0, e1 = 0;
+            if (k < TO_KC) {
+                int c = -1;
+                double w = 0.0;
+#pragma unroll
+                for (int q = 0; q < TO_KC; ++q)
+                    if (q == k) {
+                        c = r_col[q];
+                        w = r_w[q];
+                        e = r_next[q];
+                        e1 = r_e1[q];
+                    }
+                if (c >= 0 && c < N) keep_succ(bc, bv, bw, __dadd_rn(w, d[c]), c, w);
+            } else {
+                e = __ldg(&G.row_off[u]) + lane;
+                e1 = __ldg(&G.row_off[u + 1]);
+            }
+            for (; e < e1; e += 32) {
+                const int c = __ldg(&G.col[e]);
+                if (c < 0 || c >= N) continue;
+                const double w = ldw(G, e);
+                keep_succ(bc, bv, bw, __dadd_rn(w, d[c]), c, w);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double oc = __shfl_xor_sync(0xffffffffu, bc, o);
+            const int ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const double ow = __shfl_xor_sync(0xffffffffu, bw, o);
+            keep_succ(bc, bv, bw, oc, ov, ow);
+        }
+        if (lane == 0) {
+            G.succ[u] = bc < inf ? bv : -1;
+            G.wsucc[u] = bc < inf ? bw : 0.0;
+        }
+    }
+    if (!grid_sync(info, nb, G.spin_limit, bar_round)) return;
+
+    // phase 4: the path (block 0, thread 0)
+    if (gtid == 0) {
+        const volatile int* succ = G.succ;
+        info->start = start;
+        info->goal = goal;
+        info->search_iters = (unsigned long long)sweeps;
+        const double ds = d[start];
+        if (!(ds < inf)) {
+            *G.path_len = 0;
+            *G.cost = inf;
+            set_status_s(info, PLAN_ERR_NO_PATH, DET_NONE);
+        } else {
+            int v = start, L = 0;
+            bool ok = true;
+            for (;;) {
+                if (L < G.path_cap) G.path[L] = v;
+                ++L;
+                if (v == goal) break;
+                v = succ[v];
+                if (v < 0 || v >= N || L > N) {
+                    ok = false;
+                    break;
+                }
+            }
+            *G.path_len = L;
+            *G.cost = ds;
+            if (!ok) set_status_s(info, PLAN_ERR_TIMEOUT, DET_WALK);
+            else if (L > G.path_cap) set_status_s(info, PLAN_ERR_CAPACITY, DET_PATHCAP);
+        }
+        info->path_len = *G.path_len;
+        ((volatile int*)G.prev)[1] = N;
+        __threadfence();
+        ((volatile int*)G.prev)[0] = goal;
+    }
+}
+
+int launch_search_to(const GoalSearchParams& G, void* stream, int num_sms, int* launches) {
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t smem_max = (size_t)2 * TO_SMEM_N * sizeof(unsigned);
+    const size_t smem = G.warm && G.N <= TO_SMEM_N ? (size_t)2 * G.N * sizeof(unsigned) : 0;
+    cudaFuncSetAttribute(k_search_to, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_search_to, 1024, smem_max);
+    if (occ < 1) return (int)cudaErrorCooperativeLaunchTooLarge;
+    GoalSearchParams Q = G;
+    void* args[] = {&Q};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_search_to, dim3(num_sms), dim3(1024), args, smem, st);
+    ++*launches;
+    return (int)e;
+}
+
 int launch_search_batched(const BatchSearchParams& P, void* stream, int* launches) {
     if (P.Q <= 0) return 0;
     k_search_batched<<<P.Q, 1024, 0, (cudaStream_t)stream>>>(P);

@@ -83,7 +83,7 @@ class _RefineW(ctypes.Structure):
 EXPORTS = ["plan_create", "plan_destroy", "plan_build_edges", "plan_search", "plan_wait", "plan_model_tables",
            "plan_set_search_limits", "plan_refine", "plan_prepare_batched", "plan_build_edges_batched",
            "plan_set_tile", "plan_autotune", "plan_prepare_search_batched", "plan_search_batched",
-           "plan_search_noalloc", "plan_cut_edges", "plan_cut_timing", "plan_search_at", "plan_obstacle_planes", "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
+           "plan_search_noalloc", "plan_cut_edges", "plan_cut_timing", "plan_search_at", "plan_search_to", "plan_obstacle_planes", "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
 
 
 def lib_path() -> str:
@@ -132,6 +132,8 @@ def load(build_if_stale: bool = True):
     lib.plan_obstacle_planes.argtypes = [vp, i32, vp, ctypes.POINTER(_Obstacles), vp, vp, vp, vp, vp]
     lib.plan_obstacle_planes.restype = i32
     lib.plan_search_at.argtypes = [vp, i32, vp, ctypes.POINTER(_Edges), vp, vp, i32, vp, vp]
+    lib.plan_search_to.argtypes = [vp, i32, vp, ctypes.POINTER(_Edges), vp, i32, vp, i32, vp, vp]
+    lib.plan_search_to.restype = i32
     lib.plan_search_at.restype = i32
     lib.plan_cut_timing.argtypes = [vp, dp, dp, ctypes.POINTER(i64), i32]
     lib.plan_cut_timing.restype = i32
@@ -456,6 +458,16 @@ class Planner:
         if rc != 0:
             raise self._err(rc, "plan_search_at")
 
+    def search_to_async(self, dp: DeviceProblem, graph: Graph, endpoints, out: dict, warm: bool = True) -> None:
+        """plan_search_to: distances to the goal vertex, warm-started from the
+        previous call when the goal vertex is the same."""
+        rc = self.lib.plan_search_to(self.ctx, dp.N, ctypes.c_void_p(dp.states.data_ptr()), ctypes.byref(graph.cstruct()),
+                                     ctypes.c_void_p(endpoints.data_ptr()), 1 if warm else 0,
+                                     ctypes.c_void_p(out["path"].data_ptr()), int(out["path"].shape[0]),
+                                     ctypes.c_void_p(out["path_len"].data_ptr()), ctypes.c_void_p(out["cost"].data_ptr()))
+        if rc != 0:
+            raise self._err(rc, "plan_search_to")
+
     def alloc_search(self, N: int, path_cap: Optional[int] = None) -> dict:
         import torch
         dev = torch.device("cuda")
@@ -614,8 +626,10 @@ class Replanner:
     """The replanning loop of Alg. 1 (lines 3-4 every tick, the graph of line 2
     fixed): each tick refreshes the obstacles and the start/goal positions on
     the device from pinned host buffers, cuts the fixed graph against the
-    obstacles (plan_cut_edges), searches the cut graph (plan_search_at) and
-    copies the path back -- all replayed from one captured CUDA graph.
+    obstacles (plan_cut_edges), searches the cut graph and copies the path
+    back -- all replayed from one captured CUDA graph.  The search is the
+    goal-rooted plan_search_to warm-started from the previous tick (warm=True,
+    the default) or plan_search_at (warm=False).
 
     The obstacle arrays have a fixed capacity (n_max obstacles, rows_max >= 2m
     rows each); a tick with fewer obstacles fills the other slots with unit
@@ -623,11 +637,12 @@ class Replanner:
     from every curve."""
 
     def __init__(self, planner: "Planner", dp: DeviceProblem, graph: Graph, n_max: int, rows_max: int,
-                 path_cap: Optional[int] = None):
+                 path_cap: Optional[int] = None, warm: bool = True):
         import torch
         if planner.stream.cuda_stream == 0:
             raise ValueError("the planner needs its own stream (a graph cannot be captured on the default stream)")
         self.pl, self.dp, self.graph = planner, dp, graph
+        self.warm = bool(warm)   # goal-rooted search warm-started from the previous tick (else plan_search_at)
         self.m = int(planner.model.m)
         self.n_max, self.rows_max = int(n_max), int(rows_max)
         if self.rows_max < 2 * self.m:
@@ -680,7 +695,10 @@ class Replanner:
         o.b.copy_(self.h_b, non_blocking=True)
         self.ends.copy_(self.h_ends, non_blocking=True)
         self.pl.cut_edges_async(self.dp, self.graph, o, self.out)
-        self.pl.search_at_async(self.dp, self.out, self.ends, self.sbuf)
+        if self.warm:
+            self.pl.search_to_async(self.dp, self.out, self.ends, self.sbuf, warm=True)
+        else:
+            self.pl.search_at_async(self.dp, self.out, self.ends, self.sbuf)
         self.h_path.copy_(self.sbuf["path"], non_blocking=True)
         self.h_len.copy_(self.sbuf["path_len"], non_blocking=True)
         self.h_cost.copy_(self.sbuf["cost"], non_blocking=True)
