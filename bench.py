@@ -561,7 +561,7 @@ def run_replan_form(args, stream, flush, dev):
                                    "walk of 0.002 per tick; the start advances along the first plan)",
                        "first_plan_vertices": len(plan0),
                        "captured": "one CUDA graph per tick: 4 host-to-device copies, the cut (7 kernels), the "
-                                   "goal-rooted search warm-started from the previous tick (1 cooperative "
+                                   "goal-rooted search warm-started from the previous tick (1 launch, one 16-CTA cluster "
                                    "kernel), 3 device-to-host copies",
                        "edges_per_tick": [min(edges), max(edges)], "no_path_ticks": int(sum(s != 0 for s in stats)),
                        "l2": "flushed before every tick (256 MB write)",

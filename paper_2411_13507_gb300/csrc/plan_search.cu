@@ -628,6 +628,7 @@ __global__ void __launch_bounds__(1024) k_search_batched(BatchSearchParams B) {
 //   4. block 0 walks start -> goal along succ.
 // ---------------------------------------------------------------------------
 constexpr int TO_KC = 2;            // owned vertices per warp held in registers
+constexpr int TO_CLUSTER_MAX_N = 12288;   // on-chip variant (one cluster) up to this N
 constexpr int TO_SMEM_N = 24576;    // pointer jumping in shared memory up to this N (8 bytes a vertex)
 constexpr unsigned TO_OK = 0x80000000u;
 
@@ -954,8 +955,413 @@ __global__ void __launch_bounds__(1024, 1) k_search_to(GoalSearchParams G) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same goal-rooted search on chip, for graphs whose distances and rows fit
+// in the shared memory of one thread-block cluster (replanning graphs of some
+// thousands of vertices).  A dependent L2 round trip costs about 2 us on this
+// part and a software grid barrier about 1.3 us, against about 0.3 us for the
+// cluster barrier and tens of cycles for a shared-memory load, so every sweep
+// stays inside the cluster:
+//   - CTA r of the cluster owns the vertices [r V, (r+1) V), V = ceil(N / C),
+//     and holds their rows (columns, weights) in its shared memory (edges past
+//     its capacity are read from global memory);
+//   - every CTA holds a copy of all N distances; the owner of u writes each
+//     improvement of d[u] into every copy with distributed-shared-memory
+//     stores (one writer per entry; readers see the old or the new value, both
+//     upper bounds, as in the global kernel);
+//   - one cluster barrier per sweep, after every CTA has stored its
+//     "changed" flag into every CTA's flag slots (two slot sets by sweep
+//     parity: a CTA overwrites the set of sweep s only after the barrier of
+//     sweep s + 1, which every CTA passes only once it has read them).
+// The warm start computes the links of owned vertices (rows in shared
+// memory), broadcasts them, and every CTA runs the pointer jumping in its own
+// shared memory.  Every exit and every cluster barrier is reached by all CTAs
+// alike: each decision is taken from values identical in every CTA (the edge
+// count, the start and goal, the sweep count, the gathered flags).
+// A sweep is edge-parallel inside a CTA: every thread takes owned edges
+// (u -> c) and lowers best[u] (the bits of fl(w + d[c]); non-negative doubles
+// order like unsigned integers) with a shared-memory atomicMin; a vertex pass
+// then compares best[u] with d[u] and broadcasts the improvements.
+// Shared memory: d [N] doubles, links / successors [2N] u32, best [V] u64,
+// owned row offsets [V+1], owned columns [cap], their local source vertex
+// [cap] u16 and weights [cap].
+// ---------------------------------------------------------------------------
+namespace {
+DEVI unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+DEVI unsigned cl_map(unsigned a, unsigned rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+DEVI void cl_st_f64(unsigned a, double v) { asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory"); }
+DEVI void cl_st_u32(unsigned a, unsigned v) { asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory"); }
+DEVI void cl_st_u64(unsigned a, unsigned long long v) {
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+DEVI void cl_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+DEVI unsigned cl_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+DEVI unsigned cl_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+}  // namespace
+
+constexpr int TO_CL_MAX = 16;
+
+__global__ void __launch_bounds__(1024, 1) k_search_to_cluster(GoalSearchParams G, int ecap) {
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    __shared__ unsigned long long s_near[TO_CL_MAX][4];   // per CTA: start bits, id, goal bits, id
+    __shared__ int s_flag[2][TO_CL_MAX];
+    __shared__ unsigned s_rb_d[TO_CL_MAX];                 // d copy of every CTA (cluster addresses)
+    __shared__ unsigned long long s_kb[2][32];
+    __shared__ int s_ki[2][32];
+    __shared__ int s_prev[2], s_se[2];
+    const int N = G.N, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nt = blockDim.x;
+    const unsigned rank = cl_rank(), C = cl_size();
+    const int V = (N + (int)C - 1) / (int)C;
+    const int v0 = min(N, (int)rank * V), v1 = min(N, v0 + V), nv = v1 - v0;
+    double* s_d = (double*)s_raw;
+    unsigned* s_link = (unsigned*)(s_d + N);
+    unsigned long long* s_best = (unsigned long long*)(s_link + 2 * N);
+    int* s_ro = (int*)(s_best + V);
+    int* s_col = s_ro + (V + 1);
+    unsigned short* s_src = (unsigned short*)(s_col + ecap);
+    double* s_w = (double*)(((uintptr_t)(s_src + ecap) + 7) & ~(uintptr_t)7);
+    DevInfo* info = G.info;
+    const double inf = __longlong_as_double(DINF);
+    volatile double* vd = s_d;
+
+    cl_sync();  // every CTA of the cluster is running before any remote store
+    if (tid < (int)C) s_rb_d[tid] = cl_map(smem_addr(s_d), tid);
+    if (tid == 0) {
+        s_prev[0] = ((volatile int*)G.prev)[0];
+        s_prev[1] = ((volatile int*)G.prev)[1];
+        const long long E = *G.count;
+        s_se[0] = (E < 0 || E > G.cap) ? 1 : 0;
+        if (s_se[0] && rank == 0) set_status_s(info, PLAN_ERR_INVALID_ARG, DET_OUTPUT);
+    }
+    __syncthreads();
+    if (s_se[0]) {  // the same edge count in every CTA: all leave here
+        cl_sync();
+        return;
+    }
+    const int pg = s_prev[0];
+    const bool may_warm = G.warm && s_prev[1] == N && pg >= 0 && pg < N;
+
+    // phase 0: owned rows into shared memory; nearest candidates; links
+    const int eb = __ldg(&G.row_off[v0]), ee = __ldg(&G.row_off[v1]);
+    const int nloc = min(ee - eb, ecap);
+    for (int k = tid; k <= nv; k += nt) s_ro[k] = __ldg(&G.row_off[v0 + k]) - eb;
+    for (int i = tid; i < nloc; i += nt) {
+        s_col[i] = __ldg(&G.col[eb + i]);
+        s_w[i] = ldw(G, eb + i);
+    }
+    if (may_warm)
+        for (int v = tid; v < N; v += nt) s_d[v] = ((const volatile double*)G.d)[v];
+    double sp[4], gp[4];
+    for (int a = 0; a < 4; ++a) {
+        sp[a] = a < G.m ? G.endpoints[a] : 0.0;
+        gp[a] = a < G.m ? G.endpoints[G.m + a] : 0.0;
+    }
+    unsigned long long kb[2] = {~0ull, ~0ull};
+    int ki[2] = {0x7fffffff, 0x7fffffff};
+    for (int v = v0 + tid; v < v1; v += nt) {
+        double ds = 0.0, dg = 0.0;
+        for (int a = 0; a < G.m; ++a) {
+            const double x = ldd(G.states, (long long)v * G.n + a, G.in_f32);
+            const double ts = __dsub_rn(x, sp[a]), tg = __dsub_rn(x, gp[a]);
+            ds = __dadd_rn(ds, __dmul_rn(ts, ts));
+            dg = __dadd_rn(dg, __dmul_rn(tg, tg));
+        }
+        keep_min(kb[0], ki[0], (unsigned long long)__double_as_longlong(ds), v);
+        keep_min(kb[1], ki[1], (unsigned long long)__double_as_longlong(dg), v);
+    }
+    for (int h = 0; h < 2; ++h) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_down_sync(0xffffffffu, kb[h], o);
+            const int oi = __shfl_down_sync(0xffffffffu, ki[h], o);
+            keep_min(kb[h], ki[h], ob, oi);
+        }
+        if (lane == 0) {
+            s_kb[h][wid] = kb[h];
+            s_ki[h][wid] = ki[h];
+        }
+    }
+    __syncthreads();  // also: owned rows loaded
+    for (int k = tid; k < nv; k += nt) {   // local source vertex of every on-chip edge
+        const int r1 = min(s_ro[k + 1], nloc);
+        for (int i = s_ro[k]; i < r1; ++i) s_src[i] = (unsigned short)k;
+    }
+    if (tid < 2) {
+        unsigned long long b0 = ~0ull;
+        int i0 = 0x7fffffff;
+        for (int w = 0; w < (nt >> 5); ++w) keep_min(b0, i0, s_kb[tid][w], s_ki[tid][w]);
+        const unsigned a = smem_addr(&s_near[rank][2 * tid]);
+        for (unsigned q = 0; q < C; ++q) {
+            const unsigned ra = cl_map(a, q);
+            cl_st_u64(ra, b0);
+            cl_st_u64(ra + 8, (unsigned long long)(unsigned)i0);
+        }
+    }
+    if (may_warm) {
+        const unsigned la = smem_addr(s_link);
+        for (int v = v0 + tid; v < v1; v += nt) {
+            unsigned link = (unsigned)v;
+            if (v == pg) {
+                link |= TO_OK;
+            } else {
+                const int sv = G.succ[v];
+                if (sv >= 0 && sv < N && G.d[v] < inf) {
+                    const int k = v - v0, r1 = s_ro[k + 1];
+                    int lo = s_ro[k], hi = r1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        const int cm = mid < ecap ? s_col[mid] : __ldg(&G.col[eb + mid]);
+                        if (cm < sv) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    if (lo < r1) {
+                        const int cl = lo < ecap ? s_col[lo] : __ldg(&G.col[eb + lo]);
+                        const double wl = lo < ecap ? s_w[lo] : ldw(G, eb + lo);
+                        if (cl == sv && wl <= G.wsucc[v]) link = (unsigned)sv | TO_OK;
+                    }
+                }
+            }
+            for (unsigned q = 0; q < C; ++q) cl_st_u32(cl_map(la + 4u * v, q), link);
+        }
+    }
+    cl_sync();
+
+    // phase 1: start and goal (every CTA alike); warm: pointer jumping here; d
+    if (tid < 2) {
+        unsigned long long b0 = ~0ull;
+        int i0 = 0x7fffffff;
+        for (unsigned q = 0; q < C; ++q) keep_min(b0, i0, s_near[q][2 * tid], (int)s_near[q][2 * tid + 1]);
+        s_se[tid] = i0;
+    }
+    __syncthreads();
+    const int start = s_se[0], goal = s_se[1];
+    if (start < 0 || start >= N || goal < 0 || goal >= N) {
+        if (rank == 0 && tid == 0) set_status_s(info, PLAN_ERR_INVALID_ARG, DET_WALK);
+        cl_sync();
+        return;
+    }
+    if (rank == 0 && tid == 0) ((volatile int*)G.prev)[0] = -1;
+    const bool warm = may_warm && pg == goal;
+    if (warm) {
+        unsigned* a0 = s_link;
+        unsigned* a1 = s_link + N;
+        for (int r = 0; r < 64; ++r) {
+            const int any = __syncthreads_or(jump_round<false>(a0, a1, tid, nt, N));
+            unsigned* t = a0;
+            a0 = a1;
+            a1 = t;
+            if (!any) break;
+        }
+        for (int v = tid; v < N; v += nt)
+            if (v == goal) s_d[v] = 0.0;
+            else if (a0[v] != ((unsigned)goal | TO_OK)) s_d[v] = inf;
+    } else {
+        for (int v = tid; v < N; v += nt) s_d[v] = v == goal ? 0.0 : inf;
+    }
+    cl_sync();  // no copy is written by a sweep before every CTA has set it
+
+    // phase 2: sweeps
+    int sweeps = 0;
+    for (;;) {
+        if (sweeps >= G.max_sweeps) {
+            if (rank == 0 && tid == 0) set_status_s(info, PLAN_ERR_TIMEOUT, DET_SWEEPS);
+            return;  // the same count in every CTA; no remote access follows the last barrier
+        }
+        const int par = sweeps & 1;
+        ++sweeps;
+        int changed = 0;
+        for (int k = tid; k < nv; k += nt) s_best[k] = (unsigned long long)__double_as_longlong(vd[v0 + k]);
+        __syncthreads();
+        for (int i = tid; i < nloc; i += nt) {   // on-chip edges
+            const int c = s_col[i];
+            if (c < 0 || c >= N) continue;
+            const unsigned long long x = (unsigned long long)__double_as_longlong(__dadd_rn(s_w[i], vd[c]));
+            const int k = s_src[i];
+            if (x < ((volatile unsigned long long*)s_best)[k]) atomicMin(&s_best[k], x);
+        }
+        __syncthreads();
+        for (int k = tid; k < nv; k += nt) {
+            const int u = v0 + k;
+            if (u == goal) continue;
+            const double cur = vd[u];
+            double best = __longlong_as_double((long long)s_best[k]);
+            const int r1 = s_ro[k + 1];
+            for (int i = max(s_ro[k], nloc); i < r1; ++i) {   // edges past the on-chip capacity
+                const int c = __ldg(&G.col[eb + i]);
+                if (c < 0 || c >= N) continue;
+                const double x = __dadd_rn(ldw(G, eb + i), vd[c]);
+                if (x < best) best = x;
+            }
+            if (best < cur) {
+                for (unsigned q = 0; q < C; ++q) cl_st_f64(s_rb_d[q] + 8u * (unsigned)u, best);
+                changed = 1;
+            }
+        }
+        const int ch = __syncthreads_or(changed);
+        if (tid < (int)C) cl_st_u32(cl_map(smem_addr(&s_flag[par][rank]), tid), (unsigned)ch);
+        cl_sync();
+        int any = 0;
+        for (unsigned q = 0; q < C; ++q) any |= s_flag[par][q];
+        if (!any) break;
+    }
+
+    // phase 3: successors of owned vertices; d, succ, wsucc kept for the next
+    // call; successors also into CTA 0's link area for the walk
+    const unsigned succ0 = cl_map(smem_addr(s_link), 0);
+    for (int k = tid; k < nv; k += nt) {
+        const int u = v0 + k;
+        double bc = inf, bw = 0.0;
+        int bv = 0x7fffffff;
+        if (u != goal) {
+            const int r1 = s_ro[k + 1];
+            for (int i = s_ro[k]; i < r1; ++i) {
+                const int c = i < ecap ? s_col[i] : __ldg(&G.col[eb + i]);
+                if (c < 0 || c >= N) continue;
+                const double w = i < ecap ? s_w[i] : ldw(G, eb + i);
+                keep_succ(bc, bv, bw, __dadd_rn(w, vd[c]), c, w);
+            }
+        }
+        const int sv = bc < inf ? bv : -1;
+        G.succ[u] = sv;
+        G.wsucc[u] = bc < inf ? bw : 0.0;
+        G.d[u] = vd[u];
+        cl_st_u32(succ0 + 4u * (unsigned)u, (unsigned)sv);
+    }
+    cl_sync();
+
+    // phase 4: the path (CTA 0, thread 0)
+    if (rank == 0 && tid == 0) {
+        const volatile int* succ = (const volatile int*)s_link;
+        info->start = start;
+        info->goal = goal;
+        info->search_iters = (unsigned long long)sweeps;
+        const double ds = vd[start];
+        if (!(ds < inf)) {
+            *G.path_len = 0;
+            *G.cost = inf;
+            set_status_s(info, PLAN_ERR_NO_PATH, DET_NONE);
+        } else {
+            int v = start, L = 0;
+            bool ok = true;
+            for (;;) {
+                if (L < G.path_cap) G.path[L] = v;
+                ++L;
+                if (v == goal) break;
+                v = succ[v];
+                if (v < 0 || v >= N || L > N) {
+                    ok = false;
+                    break;
+                }
+            }
+            *G.path_len = L;
+            *G.cost = ds;
+            if (!ok) set_status_s(info, PLAN_ERR_TIMEOUT, DET_WALK);
+            else if (L > G.path_cap) set_status_s(info, PLAN_ERR_CAPACITY, DET_PATHCAP);
+        }
+        info->path_len = *G.path_len;
+        ((volatile int*)G.prev)[1] = N;
+        __threadfence();
+        ((volatile int*)G.prev)[0] = goal;
+    }
+}
+
+namespace {
+// Shared memory of the on-chip kernel for N vertices, cluster size C and ecap
+// edges a CTA.
+size_t cluster_smem(int N, int C, int ecap) {
+    const int V = (N + C - 1) / C;
+    size_t b = (size_t)8 * N + (size_t)8 * N + (size_t)8 * V + (size_t)4 * (V + 1) + (size_t)6 * ecap;
+    b = (b + 7) & ~(size_t)7;
+    return b + (size_t)8 * ecap;
+}
+
+struct ClusterChoice {
+    int dev = -1, optin = 0;
+    int ok16 = -1, ok8 = -1;   // -1 unknown, 0 no, 1 yes (at the largest shared memory)
+};
+std::mutex g_cl_mu;
+ClusterChoice g_cl[64];
+
+// Cluster size usable at the device's largest shared-memory size (16, 8 or 0).
+int cluster_size_for(int dev) {
+    std::lock_guard<std::mutex> lock(g_cl_mu);
+    if (dev < 0 || dev >= 64) return 0;
+    ClusterChoice& c = g_cl[dev];
+    if (c.dev != dev) {
+        c.dev = dev;
+        cudaDeviceGetAttribute(&c.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const int dyn = c.optin - 4096;   // room for the static shared memory
+        cudaFuncSetAttribute(k_search_to_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        cudaFuncSetAttribute(k_search_to_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        for (int C : {16, 8}) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(C);
+            cfg.blockDim = dim3(1024);
+            cfg.dynamicSmemBytes = dyn;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = C;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int ncl = 0;
+            const cudaError_t e = cudaOccupancyMaxActiveClusters(&ncl, k_search_to_cluster, &cfg);
+            if (e != cudaSuccess) cudaGetLastError();
+            (C == 16 ? c.ok16 : c.ok8) = (e == cudaSuccess && ncl >= 1) ? 1 : 0;
+        }
+    }
+    return c.ok16 == 1 ? 16 : c.ok8 == 1 ? 8 : 0;
+}
+}  // namespace
+
 int launch_search_to(const GoalSearchParams& G, void* stream, int num_sms, int* launches) {
     cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int C = G.N <= TO_CLUSTER_MAX_N ? cluster_size_for(dev) : 0;
+    if (C > 0) {
+        // owned edges a CTA keeps on chip: twice the even share of the CSR's
+        // capacity, within the device's shared memory (the rest from global memory)
+        const int dyn = g_cl[dev].optin - 4096;
+        const long long even = (G.cap + C - 1) / C;
+        long long ecap = 2 * even + 64;
+        const size_t base = cluster_smem(G.N, C, 0);
+        const long long fit = ((long long)dyn - (long long)base - 16) / 14;
+        if (ecap > fit) ecap = fit;
+        if (ecap >= even / 2 && ecap >= 64) {
+            const int ec = (int)ecap;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(C);
+            cfg.blockDim = dim3(1024);
+            cfg.dynamicSmemBytes = cluster_smem(G.N, C, ec);
+            cfg.stream = st;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = C;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            GoalSearchParams Q = G;
+            cudaError_t e = cudaLaunchKernelEx(&cfg, k_search_to_cluster, Q, ec);
+            ++*launches;
+            return (int)e;
+        }
+    }
     const size_t smem_max = (size_t)2 * TO_SMEM_N * sizeof(unsigned);
     const size_t smem = G.warm && G.N <= TO_SMEM_N ? (size_t)2 * G.N * sizeof(unsigned) : 0;
     cudaFuncSetAttribute(k_search_to, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);

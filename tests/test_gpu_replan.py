@@ -163,12 +163,14 @@ def _search_to(pl, dp, out, start, goal, warm):
             "cost": float(buf["cost"].item()), "info": pl.info()}
 
 
-def test_warm_start_after_a_stopped_call_and_above_the_shared_memory_size():
-    """N = 30000 (> 24576: the chains are checked in global memory, one grid
-    barrier per round).  A call stopped by the sweep limit leaves no warm
-    state: the next warm call equals a cold one.  Warm calls on moved
-    obstacles equal cold calls bit for bit."""
-    prob, obs = synth.keepout_2d(6, N=30000, n_obst=300, width=12.0)
+@pytest.mark.parametrize("N,width", [(16000, 8.8), (30000, 12.0)])
+def test_warm_start_after_a_stopped_call_on_the_cooperative_kernel(N, width):
+    """Graphs above the on-chip (one cluster) size run the cooperative kernel:
+    N = 16000 checks the chains in each block's shared memory, N = 30000 in
+    global memory with one grid barrier per round.  A call stopped by the
+    sweep limit leaves no warm state: the next warm call equals a cold one.
+    Warm calls on moved obstacles equal cold calls bit for bit."""
+    prob, obs = synth.keepout_2d(6, N=N, n_obst=300, width=width)
     pl, dp, g, ctx = setup(prob)
     pl2 = P.Planner.for_problem(prob, stream=pl.stream)
     rng = np.random.default_rng(6)
