@@ -358,6 +358,70 @@ int plan_cut_edges(plan_ctx* ctx, int N, const void* states, int nT, const doubl
 int plan_obstacle_planes(plan_ctx* ctx, int P, const void* points, const plan_obstacles* obst, float* closest,
                          float* plane, float* dist, int32_t* nearest, float* nearest_dist);
 
+/*
+ * adjacentHyperplane for the nearest obstacle only (Sec. III-D: the MPC keeps
+ * node k on its side of the plane between it and its closest obstacle): per
+ * point the nearest obstacle as plan_obstacle_planes finds it, then that
+ * pair's plane (h, l) with unit normal toward the point.  A point inside an
+ * obstacle, or with no obstacle at all, gets h = 0, l = 0 (no constraint).
+ *   nearest_plane  device float [P][m+1] (h, then l)
+ *   nearest        device int32 [P] or NULL (-1 when n = 0)
+ *   nearest_dist   device float [P] or NULL
+ * Everything else, and the errors, as plan_obstacle_planes.
+ */
+int plan_nearest_planes(plan_ctx* ctx, int P, const void* points, const plan_obstacles* obst, float* nearest_plane,
+                        int32_t* nearest, float* nearest_dist);
+
+/* MPC refinement QP (Sec. III-D, Eq. (MPC)) of a batch of B problems on the
+ * context's model (m <= 3, gamma <= 4, degree <= 9):
+ *   min  sum_{k<H} (x_k - r_k)'Q(x_k - r_k) + (x_{k+1} - x_k)'F(x_{k+1} - x_k)
+ *        + u_k'R u_k  +  (x_H - r_H)'V(x_H - r_H)
+ *   s.t. x_{k+1} = A x_k + B u_k (exact discretisation of the chain of
+ *        integrators, u the gamma-th derivative), x_0 = the given state,
+ *        x_H = r_H, Theorem 1's reach rows of duration dt on every segment
+ *        (the model's derivative bounds minus its tighten margin), every
+ *        control point of segment k (not x_0 itself) on the side h.z >= l of
+ *        plane k unless h = 0, and every control point but the first of a
+ *        segment inside the keep-in polytope A_d z <= b_d.
+ * x is derivative-major (positions, velocities, ...) as the graph's states.
+ * Weights are diagonal; Q, F, V have n = m gamma entries, R has m.  The
+ * problem is strictly convex; each is solved exactly (active-set method, in
+ * FP64) on the GPU. */
+typedef struct {
+    int horizon;              /* H segments, gamma <= H <= 64 / m */
+    double dt;                /* segment duration, > 0 */
+    const double* Q;          /* host [n] > 0: distance to the reference */
+    const double* F;          /* host [n] > 0: step between consecutive nodes (path length) */
+    const double* R;          /* host [m] > 0: input */
+    const double* V;          /* host [n] > 0: terminal */
+    int keepin_rows;          /* 0 .. 16 */
+    const double* keepin_A;   /* host [keepin_rows][m] or NULL */
+    const double* keepin_b;   /* host [keepin_rows] or NULL */
+} plan_mpc_params;
+
+enum { PLAN_MPC_OK = 0, PLAN_MPC_INFEASIBLE = 1, PLAN_MPC_ITERATION_LIMIT = 2 };
+
+/*
+ *   B       problems, 0 .. 1<<24
+ *   x0      device double [B][n]: measured state of every problem
+ *   ref     device double [B][H+1][n]: reference nodes r_0 .. r_H
+ *   planes  device float [B][H][m+1]: plane (h, l) of segment k (the output
+ *           of plan_nearest_planes at the nodes x_0 .. x_{H-1} of the
+ *           current iterate); h = 0 means no safety rows
+ *   x       device double [B][H+1][n]: optimal nodes (x_0 = x0)
+ *   u       device double [B][H][m]: optimal inputs
+ *   obj     device double [B]: optimal objective value
+ *   status  device int32 [B]: PLAN_MPC_OK, PLAN_MPC_INFEASIBLE or
+ *           PLAN_MPC_ITERATION_LIMIT (x, u, obj then describe the last iterate)
+ *   iters   device int32 [B] or NULL: active-set steps taken
+ * Asynchronous on the context stream; host errors INVALID_ARG (bad sizes or
+ * weights) and UNSUPPORTED (model or problem size); per-problem outcomes go
+ * to status, not to plan_wait.  An SQP refinement alternates
+ * plan_nearest_planes at the new nodes and plan_mpc_qp.
+ */
+int plan_mpc_qp(plan_ctx* ctx, int B, const plan_mpc_params* prm, const double* x0, const double* ref,
+                const float* planes, double* x, double* u, double* obj, int32_t* status, int32_t* iters);
+
 /* Weights of the refinement objective (defaults 1, 1, 0.1). */
 typedef struct {
     double w_snap;  /* weight of the snap energy */

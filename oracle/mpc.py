@@ -209,7 +209,9 @@ def solve_qp(P, q, Aeq, beq, Ain, bin_, max_iter: int = 20000, z0: Optional[np.n
     primal active-set method; the most negative multiplier leaves the working
     set and the first blocking row enters it, both on the lowest index among
     ties, and after 50 zero-length steps in a row the least index among the
-    negative multipliers leaves instead (against cycling)."""
+    negative multipliers leaves instead (against cycling).  After a full
+    unblocked step the point minimises the objective on the working set, so
+    the next solve only supplies the multipliers (its step is rounding)."""
     nz = P.shape[0]
     ne, ni = Aeq.shape[0], Ain.shape[0]
     rown = np.linalg.norm(Ain, axis=1) if ni else np.zeros(0)
@@ -235,6 +237,7 @@ def solve_qp(P, q, Aeq, beq, Ain, bin_, max_iter: int = 20000, z0: Optional[np.n
     allrows = np.concatenate([Aeq, Ain]) if ni else Aeq
     W = sorted(i - ne for i in _independent(allrows, [ne + i for i in act], list(range(ne))))
     zero_run = 0
+    at_min = False      # z minimises the objective on the working set (a full step was just taken)
     for it in range(max_iter):
         AW = np.concatenate([Aeq, Ain[W]]) if W else Aeq
         k = AW.shape[0]
@@ -246,8 +249,11 @@ def solve_qp(P, q, Aeq, beq, Ain, bin_, max_iter: int = 20000, z0: Optional[np.n
         rhs = np.concatenate([-grad, np.zeros(k)])
         sol = np.linalg.solve(K, rhs)
         step, lam = sol[:nz], sol[nz:]      # P step + AW' lam = -(P z + q): lam are the multipliers
-        gscale = 1.0 + np.abs(grad).max()
-        if np.abs(P @ step).max() <= 1e-11 * gscale:
+        # a zero step up to the solve's rounding: measured against the size of
+        # the stationarity terms (gradient and A_W' lam), or negligible next to z
+        gscale = 1.0 + np.abs(grad).max() + np.abs(AW.T @ lam).max()
+        if at_min or np.abs(P @ step).max() <= 1e-11 * gscale or np.abs(step).max() <= 1e-10 * (1.0 + np.abs(z).max()):
+            at_min = False
             mu = lam[ne:]
             neg = [j for j in range(len(W)) if mu[j] < -1e-10 * gscale]
             if not neg:
@@ -274,6 +280,8 @@ def solve_qp(P, q, Aeq, beq, Ain, bin_, max_iter: int = 20000, z0: Optional[np.n
         zero_run = zero_run + 1 if alpha == 0.0 else 0
         if block >= 0:
             W = sorted(W + [block])
+        else:
+            at_min = True   # in exact arithmetic the next step on this working set is zero
     return MAXITER, z, list(W), None, None
 
 

@@ -110,6 +110,13 @@ struct plan_ctx {
     float* h_cut32 = nullptr;
     cudaEvent_t cut_ev = nullptr;
     bool cut_ev_live = false;
+    // MPC refinement QP
+    double* d_mpc = nullptr;
+    double* h_mpc = nullptr;
+    int mpc_cap = 0;
+    cudaEvent_t mpc_ev = nullptr;
+    bool mpc_ev_live = false;
+    int smem_optin = 0;
     long long capCutE = -1, capCutO = -1, capCutR = -1;
     int32_t* cut_src = nullptr;
     uint32_t* cut_hit = nullptr;
@@ -136,6 +143,7 @@ struct plan_ctx {
     int* pl_nedge = nullptr;
     int* pl_ocount = nullptr;
     unsigned long long* pl_keys = nullptr;
+    int32_t* pl_near = nullptr;
     // timing
     bool timing = false;
     bool accounting = false;
@@ -387,6 +395,8 @@ int plan_create(plan_ctx** out, const plan_model* model, void* cuda_stream) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->sstage_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->cut_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->mpc_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     if (e != cudaSuccess) {
         cudaGetLastError();
         plan_destroy(c);
@@ -405,13 +415,15 @@ void plan_destroy(plan_ctx* c) {
                    c->resBits, c->resKey, c->emitPre, c->recheck, c->sdist, c->sbest, c->spred, c->sfront, c->slast, c->snear,
                    c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem, c->d_qMem, c->d_sqd, c->memOff,
                    c->d_cut64, c->d_cut32, c->cut_src, c->cut_hit, c->cut_pos, c->cut_chunk, c->cut_orow,
-                   c->cut_ocount, c->cut_list32, c->cut_okb, c->cut_obox, c->pl_orow, c->pl_face, c->pl_edge, c->pl_nedge, c->pl_ocount, c->pl_keys, c->g_d, c->g_succ, c->g_wsucc, c->g_anc, c->g_prev};
+                   c->cut_ocount, c->cut_list32, c->cut_okb, c->cut_obox, c->pl_orow, c->pl_face, c->pl_edge, c->pl_nedge, c->pl_ocount, c->pl_keys, c->pl_near, c->d_mpc, c->g_d, c->g_succ, c->g_wsucc, c->g_anc, c->g_prev};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_tab64) cudaFreeHost(c->h_tab64);
     if (c->h_tab32) cudaFreeHost(c->h_tab32);
     if (c->h_info) cudaFreeHost(c->h_info);
     if (c->h_cut64) cudaFreeHost(c->h_cut64);
+    if (c->h_mpc) cudaFreeHost(c->h_mpc);
+    if (c->mpc_ev) cudaEventDestroy(c->mpc_ev);
     if (c->h_cut32) cudaFreeHost(c->h_cut32);
     if (c->cut_ev) cudaEventDestroy(c->cut_ev);
     if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -1106,8 +1118,8 @@ int plan_search_to(plan_ctx* c, int N, const void* states, const plan_edges* edg
     return PLAN_OK;
 }
 
-int plan_obstacle_planes(plan_ctx* c, int P, const void* points, const plan_obstacles* obst, float* closest,
-                         float* plane, float* dist, int32_t* nearest, float* nearest_dist) {
+static int planes_common(plan_ctx* c, int P, const void* points, const plan_obstacles* obst, float* closest,
+                         float* plane, float* dist, int32_t* nearest, float* nearest_dist, float* nearest_plane) {
     if (!c) return PLAN_ERR_INVALID_ARG;
     const int m = c->model.m;
     if (m < 2 || m > 3) return fail(c, PLAN_ERR_UNSUPPORTED, "closest points for m = 2 or 3 only");
@@ -1131,14 +1143,15 @@ int plan_obstacle_planes(plan_ctx* c, int P, const void* points, const plan_obst
         c->capPlR = nob * maxr;
         c->capPlE = nob * max_edges;
     }
-    const bool want_near = nearest || nearest_dist;
+    const bool want_near = nearest || nearest_dist || nearest_plane;
     if (want_near && P > c->capPlP) {
-        if (!dalloc(c, &c->pl_keys, P)) {
+        if (!dalloc(c, &c->pl_keys, P) || !dalloc(c, &c->pl_near, P)) {
             c->capPlP = -1;
             return PLAN_ERR_NO_MEMORY;
         }
         c->capPlP = P;
     }
+    if (nearest_plane && !nearest) nearest = c->pl_near;   // the pair pass needs the indices
     PlanesParams Q;
     memset(&Q, 0, sizeof(Q));
     Q.m = m;
@@ -1162,6 +1175,7 @@ int plan_obstacle_planes(plan_ctx* c, int P, const void* points, const plan_obst
     Q.nearest = nearest;
     Q.nearest_dist = nearest_dist;
     Q.keys = want_near ? c->pl_keys : nullptr;
+    Q.nearest_plane = nearest_plane;
     Q.info = c->d_info;
     cudaError_t e = cudaSuccess;
     if (want_near && P > 0) e = cudaMemsetAsync(c->pl_keys, 0xff, sizeof(unsigned long long) * (size_t)P, c->stream);
@@ -1170,6 +1184,121 @@ int plan_obstacle_planes(plan_ctx* c, int P, const void* points, const plan_obst
     int ce = launch_planes(Q, c->stream, c->num_sms, &launches);
     c->launches += launches;
     if (ce != 0) return cuda_fail(c, (cudaError_t)ce, "planes launch");
+    return PLAN_OK;
+}
+
+int plan_obstacle_planes(plan_ctx* c, int P, const void* points, const plan_obstacles* obst, float* closest,
+                         float* plane, float* dist, int32_t* nearest, float* nearest_dist) {
+    return planes_common(c, P, points, obst, closest, plane, dist, nearest, nearest_dist, nullptr);
+}
+
+int plan_nearest_planes(plan_ctx* c, int P, const void* points, const plan_obstacles* obst, float* nearest_plane,
+                        int32_t* nearest, float* nearest_dist) {
+    if (c && P > 0 && !nearest_plane) return fail(c, PLAN_ERR_INVALID_ARG, "null nearest_plane");
+    return planes_common(c, P, points, obst, nullptr, nullptr, nullptr, nearest, nearest_dist, nearest_plane);
+}
+
+int plan_mpc_qp(plan_ctx* c, int B, const plan_mpc_params* prm, const double* x0, const double* ref,
+                const float* planes, double* x, double* u, double* obj, int32_t* status, int32_t* iters) {
+    if (!c) return PLAN_ERR_INVALID_ARG;
+    const int m = c->model.m, g = c->model.gamma, p = c->model.degree, n = m * g;
+    if (m < 1 || m > 3 || g < 1 || g > 4 || p < 2 * g - 1 || p > 9)
+        return fail(c, PLAN_ERR_UNSUPPORTED, "MPC QP for m <= 3, gamma <= 4, degree <= 9");
+    if (!prm) return fail(c, PLAN_ERR_INVALID_ARG, "null MPC parameters");
+    const int H = prm->horizon;
+    if (H < g || (long long)m * H > MPC_NV_MAX) return fail(c, PLAN_ERR_INVALID_ARG, "horizon must be gamma .. 64/m");
+    if (!std::isfinite(prm->dt) || !(prm->dt > 0.0)) return fail(c, PLAN_ERR_INVALID_ARG, "dt must be finite and > 0");
+    if (!prm->Q || !prm->F || !prm->R || !prm->V) return fail(c, PLAN_ERR_INVALID_ARG, "null weights");
+    for (int i = 0; i < n; ++i)
+        if (!(prm->Q[i] > 0.0) || !(prm->F[i] > 0.0) || !(prm->V[i] > 0.0) || !std::isfinite(prm->Q[i]) ||
+            !std::isfinite(prm->F[i]) || !std::isfinite(prm->V[i]))
+            return fail(c, PLAN_ERR_INVALID_ARG, "weights must be finite and > 0");
+    for (int i = 0; i < m; ++i)
+        if (!(prm->R[i] > 0.0) || !std::isfinite(prm->R[i])) return fail(c, PLAN_ERR_INVALID_ARG, "weights must be finite and > 0");
+    const int nk = prm->keepin_rows;
+    if (nk < 0 || nk > MPC_KEEP_MAX || (nk > 0 && (!prm->keepin_A || !prm->keepin_b)))
+        return fail(c, PLAN_ERR_INVALID_ARG, "keep-in rows must be 0..16 with host arrays");
+    for (int i = 0; i < nk * m; ++i)
+        if (!std::isfinite(prm->keepin_A[i])) return fail(c, PLAN_ERR_INVALID_ARG, "keep-in rows must be finite");
+    for (int i = 0; i < nk; ++i)
+        if (!std::isfinite(prm->keepin_b[i])) return fail(c, PLAN_ERR_INVALID_ARG, "keep-in rows must be finite");
+    if (B < 0 || B > (1 << 24)) return fail(c, PLAN_ERR_INVALID_ARG, "B out of range");
+    if (B > 0 && (!x0 || !ref || !planes || !x || !u || !obj || !status))
+        return fail(c, PLAN_ERR_INVALID_ARG, "null MPC array");
+    const int rax = reach_rows(g, p);
+    // warps (problems) per CTA: as many as the shared memory holds, at most 8
+    int W = 8;
+    while (W > 0 && mpc_smem(m, g, p, rax, nk, H, W) > (size_t)c->smem_optin) --W;
+    if (W == 0) return fail(c, PLAN_ERR_UNSUPPORTED, "MPC problem too large for shared memory");
+    // the table: per-axis transition A[c][c'] = dt^(c'-c)/(c'-c)!, input
+    // column B[c] = dt^(g-c)/(g-c)!, D and reach rows of duration dt, the
+    // bound of every reach row, weights, keep-in rows
+    const int ts = mpc_table_size(m, g, p, rax, nk);
+    if (ts > c->mpc_cap) {
+        if (c->mpc_ev_live) cudaEventSynchronize(c->mpc_ev);
+        if (c->h_mpc) cudaFreeHost(c->h_mpc);
+        c->h_mpc = nullptr;
+        c->mpc_cap = 0;
+        if (!dalloc(c, &c->d_mpc, ts)) return PLAN_ERR_NO_MEMORY;
+        if (cudaMallocHost((void**)&c->h_mpc, sizeof(double) * (size_t)ts) != cudaSuccess)
+            return fail(c, PLAN_ERR_NO_MEMORY, "pinned MPC table");
+        c->mpc_cap = ts;
+    }
+    if (c->mpc_ev_live) cudaEventSynchronize(c->mpc_ev);   // the previous upload has left the pinned buffer
+    std::vector<double> D((size_t)(p + 1) * 2 * g), Hr((size_t)rax * 2 * g), Cc((size_t)g * p * 2 * g);
+    const double dt = prm->dt;
+    exact_tables(g, p, c->model.interior, 1, &dt, D.data(), Hr.data(), Cc.data());
+    double* t = c->h_mpc;
+    int o = 0;
+    auto taylor = [&](int k) {  // dt^k / k!
+        double v = 1.0;
+        for (int i = 1; i <= k; ++i) v = v * dt / (double)i;
+        return v;
+    };
+    for (int r = 0; r < g; ++r)
+        for (int cc = 0; cc < g; ++cc) t[o++] = cc >= r ? taylor(cc - r) : 0.0;
+    for (int r = 0; r < g; ++r) t[o++] = taylor(g - r);
+    for (double v : D) t[o++] = v;
+    for (double v : Hr) t[o++] = v;
+    for (int ord = 1, r = 0; ord <= g; ++ord)
+        for (int j = 0; j <= p - ord; ++j, ++r) t[o++] = c->lim64[ord - 1];
+    for (int i = 0; i < n; ++i) t[o++] = prm->Q[i];
+    for (int i = 0; i < n; ++i) t[o++] = prm->F[i];
+    for (int i = 0; i < n; ++i) t[o++] = prm->V[i];
+    for (int i = 0; i < m; ++i) t[o++] = prm->R[i];
+    for (int i = 0; i < nk * m; ++i) t[o++] = prm->keepin_A[i];
+    for (int i = 0; i < nk; ++i) t[o++] = prm->keepin_b[i];
+    if (o != ts) return fail(c, PLAN_ERR_INVALID_ARG, "internal: MPC table size");
+    cudaError_t e = cudaMemcpyAsync(c->d_mpc, c->h_mpc, sizeof(double) * (size_t)ts, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "MPC table upload");
+    cudaEventRecord(c->mpc_ev, c->stream);
+    c->mpc_ev_live = true;
+    MpcParams M;
+    memset(&M, 0, sizeof(M));
+    M.B = B;
+    M.m = m;
+    M.g = g;
+    M.p = p;
+    M.H = H;
+    M.nv = m * H;
+    M.rax = rax;
+    M.nkeep = nk;
+    M.warps = W;
+    const long long rows = (long long)H * m * rax * 2 + (long long)H * (p + 1) + (long long)H * p * nk;
+    M.max_iter = (int)(4 * (rows + m * H) + 64);
+    M.tab = c->d_mpc;
+    M.x0 = x0;
+    M.ref = ref;
+    M.planes = planes;
+    M.x = x;
+    M.u = u;
+    M.obj = obj;
+    M.status = status;
+    M.iters = iters;
+    int launches = 0;
+    int ce = launch_mpc(M, c->stream, &launches);
+    c->launches += launches;
+    if (ce != 0) return cuda_fail(c, (cudaError_t)ce, "MPC launch");
     return PLAN_OK;
 }
 

@@ -339,8 +339,30 @@ struct PlanesParams {
     int32_t* nearest;          // [P] or null
     float* nearest_dist;       // [P] or null
     unsigned long long* keys;  // [P] nearest keys (distance bits << 32 | obstacle), or null
+    float* nearest_plane;      // [P][m+1] plane of the nearest obstacle (h = 0, l = 0 when none), or null
+    const int32_t* pair_obst;  // pair mode: [P] one obstacle per point (-1: none); outputs indexed by point
     DevInfo* info;
 };
+
+// MPC refinement QP (plan_mpc.cu): one warp per problem, FP64.
+constexpr int MPC_OK = 0, MPC_INFEASIBLE = 1, MPC_MAXITER = 2;
+constexpr int MPC_NV_MAX = 64;      // inputs per problem (m H)
+constexpr int MPC_KEEP_MAX = 16;    // keep-in rows
+struct MpcParams {
+    int B, m, g, p, H, nv, rax, nkeep, warps, max_iter;
+    const double* tab;      // device table: A, B, D, reach rows, their bounds, Q, F, V, R, keep-in rows
+    const double* x0;       // [B][n]
+    const double* ref;      // [B][H+1][n]
+    const float* planes;    // [B][H][m+1]
+    double* x;              // [B][H+1][n]
+    double* u;              // [B][H][m]
+    double* obj;            // [B]
+    int32_t* status;        // [B]
+    int32_t* iters;         // [B] or null
+};
+int mpc_table_size(int m, int g, int p, int rax, int nkeep);
+size_t mpc_smem(int m, int g, int p, int rax, int nkeep, int H, int W);
+int launch_mpc(const MpcParams& P, void* stream, int* launches);
 
 // Launchers (plan_build.cu / plan_search.cu / plan_refine.cu); return cudaError_t as int.
 int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_sm, void* ev_pair_begin,

@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(256) k_planes(PlanesParams Q) {
     if (threadIdx.x == 0) s_fail = p_failed(Q.info);
     __syncthreads();
     if (s_fail) return;
-    const long long total = (long long)Q.P * Q.n_obst;
+    const long long total = Q.pair_obst ? (long long)Q.P : (long long)Q.P * Q.n_obst;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
     const float inf = __int_as_float(0x7f800000);
@@ -273,9 +273,20 @@ __global__ void __launch_bounds__(256) k_planes(PlanesParams Q) {
         long long p = 0;
         int o = 0;
         unsigned long long key = ~0ull;
-        if (act) {
+        if (act && Q.pair_obst) {  // pair mode (no keys): the given obstacle of point k
+            p = k;
+            o = Q.pair_obst[k];
+            if (o < 0 || o >= Q.n_obst) {
+                if (Q.plane)
+                    for (int a = 0; a <= M; ++a) Q.plane[k * (M + 1) + a] = 0.f;
+                if (Q.dist) Q.dist[k] = inf;
+                continue;
+            }
+        } else if (act) {
             p = k / Q.n_obst;
             o = (int)(k - p * Q.n_obst);
+        }
+        if (act) {
             float v[M];
 #pragma unroll
             for (int a = 0; a < M; ++a) v[a] = pld32(Q.points, p * M + a, Q.in_f32);
@@ -470,6 +481,23 @@ int launch_planes(const PlanesParams& Q, void* stream, int num_sms, int* launche
     }
     if (Q.P > 0 && (Q.nearest || Q.nearest_dist)) {
         k_planes_nearest<<<(int)((Q.P + 255) / 256), 256, 0, st>>>(Q);
+        ++*launches;
+    }
+    if (Q.P > 0 && Q.nearest_plane && Q.nearest) {
+        // the plane of each point's nearest obstacle: the same per-pair work
+        // for the pairs (p, nearest[p]) only
+        PlanesParams Q2 = Q;
+        Q2.pair_obst = Q.nearest;
+        Q2.closest = nullptr;
+        Q2.dist = nullptr;
+        Q2.plane = Q.nearest_plane;
+        Q2.keys = nullptr;
+        Q2.nearest = nullptr;
+        Q2.nearest_dist = nullptr;
+        long long grid = (Q.P + 255) / 256;
+        if (grid > (long long)num_sms * 16) grid = (long long)num_sms * 16;
+        if (Q.m == 2) k_planes<2><<<(int)grid, 256, 0, st>>>(Q2);
+        else k_planes<3><<<(int)grid, 256, 0, st>>>(Q2);
         ++*launches;
     }
     return (int)cudaGetLastError();

@@ -80,10 +80,20 @@ class _RefineW(ctypes.Structure):
     _fields_ = [("w_snap", ctypes.c_double), ("mu", ctypes.c_double), ("delta", ctypes.c_double)]
 
 
+class _MpcParams(ctypes.Structure):
+    _fields_ = [("horizon", ctypes.c_int), ("dt", ctypes.c_double), ("Q", ctypes.c_void_p), ("F", ctypes.c_void_p),
+                ("R", ctypes.c_void_p), ("V", ctypes.c_void_p), ("keepin_rows", ctypes.c_int),
+                ("keepin_A", ctypes.c_void_p), ("keepin_b", ctypes.c_void_p)]
+
+
+PLAN_MPC_OK, PLAN_MPC_INFEASIBLE, PLAN_MPC_ITERATION_LIMIT = 0, 1, 2
+
+
 EXPORTS = ["plan_create", "plan_destroy", "plan_build_edges", "plan_search", "plan_wait", "plan_model_tables",
            "plan_set_search_limits", "plan_refine", "plan_prepare_batched", "plan_build_edges_batched",
            "plan_set_tile", "plan_autotune", "plan_prepare_search_batched", "plan_search_batched",
-           "plan_search_noalloc", "plan_cut_edges", "plan_cut_timing", "plan_search_at", "plan_search_to", "plan_obstacle_planes", "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
+           "plan_search_noalloc", "plan_cut_edges", "plan_cut_timing", "plan_search_at", "plan_search_to", "plan_obstacle_planes", "plan_nearest_planes", "plan_mpc_qp",
+           "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
 
 
 def lib_path() -> str:
@@ -131,6 +141,10 @@ def load(build_if_stale: bool = True):
     lib.plan_cut_edges.restype = i32
     lib.plan_obstacle_planes.argtypes = [vp, i32, vp, ctypes.POINTER(_Obstacles), vp, vp, vp, vp, vp]
     lib.plan_obstacle_planes.restype = i32
+    lib.plan_nearest_planes.argtypes = [vp, i32, vp, ctypes.POINTER(_Obstacles), vp, vp, vp]
+    lib.plan_nearest_planes.restype = i32
+    lib.plan_mpc_qp.argtypes = [vp, i32, ctypes.POINTER(_MpcParams), vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.plan_mpc_qp.restype = i32
     lib.plan_search_at.argtypes = [vp, i32, vp, ctypes.POINTER(_Edges), vp, vp, i32, vp, vp]
     lib.plan_search_to.argtypes = [vp, i32, vp, ctypes.POINTER(_Edges), vp, i32, vp, i32, vp, vp]
     lib.plan_search_to.restype = i32
@@ -447,6 +461,70 @@ class Planner:
         if st != PLAN_OK:
             raise self._err(st, "obstacle_planes")
         return out
+
+    def nearest_planes_async(self, points, obst: DeviceObstacles, plane, nearest=None, nearest_dist=None) -> None:
+        """plan_nearest_planes: per point the plane of its nearest obstacle
+        into ``plane`` (float32 [P][m+1])."""
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+        rc = self.lib.plan_nearest_planes(self.ctx, int(points.shape[0]), ctypes.c_void_p(points.data_ptr()),
+                                          ctypes.byref(obst.cstruct()), ptr(plane), ptr(nearest), ptr(nearest_dist))
+        if rc != 0:
+            raise self._err(rc, "plan_nearest_planes")
+
+    def mpc_params(self, horizon: int, dt: float, Q, F, R, V, keepin_A=None, keepin_b=None):
+        """plan_mpc_params with the host arrays kept alive on the returned object."""
+        n, m = int(self.model.m * self.model.gamma), int(self.model.m)
+        arrs = {k: np.ascontiguousarray(np.broadcast_to(np.asarray(v, dtype=np.float64), (sz,)))
+                for k, v, sz in (("Q", Q, n), ("F", F, n), ("R", R, m), ("V", V, n))}
+        nk = 0
+        if keepin_A is not None:
+            arrs["KA"] = np.ascontiguousarray(np.asarray(keepin_A, dtype=np.float64).reshape(-1, m))
+            arrs["Kb"] = np.ascontiguousarray(np.asarray(keepin_b, dtype=np.float64).reshape(-1))
+            nk = int(arrs["KA"].shape[0])
+        ptr = lambda a: a.ctypes.data if a is not None else None
+        prm = _MpcParams(int(horizon), float(dt), ptr(arrs["Q"]), ptr(arrs["F"]), ptr(arrs["R"]), ptr(arrs["V"]), nk,
+                         ptr(arrs.get("KA")), ptr(arrs.get("Kb")))
+        prm._keep = arrs
+        return prm
+
+    def alloc_mpc(self, B: int, horizon: int) -> dict:
+        import torch
+        dev = torch.device("cuda")
+        n, m = int(self.model.m * self.model.gamma), int(self.model.m)
+        return {"x": torch.empty((B, horizon + 1, n), dtype=torch.float64, device=dev),
+                "u": torch.empty((B, horizon, m), dtype=torch.float64, device=dev),
+                "obj": torch.empty(B, dtype=torch.float64, device=dev),
+                "status": torch.empty(B, dtype=torch.int32, device=dev),
+                "iters": torch.empty(B, dtype=torch.int32, device=dev)}
+
+    def mpc_qp_async(self, prm, x0, ref, planes, out: dict) -> None:
+        """plan_mpc_qp on device tensors: x0 float64 [B][n], ref float64
+        [B][H+1][n], planes float32 [B][H][m+1]; results into ``out``."""
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+        rc = self.lib.plan_mpc_qp(self.ctx, int(x0.shape[0]), ctypes.byref(prm), ptr(x0), ptr(ref), ptr(planes),
+                                  ptr(out["x"]), ptr(out["u"]), ptr(out["obj"]), ptr(out["status"]),
+                                  ptr(out.get("iters")))
+        if rc != 0:
+            raise self._err(rc, "plan_mpc_qp")
+
+    def mpc_refine_async(self, prm, x0, ref, obst: DeviceObstacles, out: dict, sqp_iters: int = 3,
+                         planes=None) -> None:
+        """The SQP refinement of Sec. III-D: planes of the nearest obstacles at
+        the nodes x_0 .. x_{H-1} of the current iterate (the reference first),
+        then the QP; sqp_iters rounds.  ``planes`` (float32 [B][H][m+1]) is
+        scratch, allocated when None."""
+        import torch
+        B, H, m = int(x0.shape[0]), int(prm.horizon), int(self.model.m)
+        if planes is None:
+            planes = torch.empty((B, H, m + 1), dtype=torch.float32, device=x0.device)
+        pts = ref
+        for _ in range(int(sqp_iters)):
+            nodes = pts[:, :H, :m].contiguous()     # node positions (a strided copy)
+            if self.input == "f32":
+                nodes = nodes.float()
+            self.nearest_planes_async(nodes.view(B * H, m), obst, planes.view(B * H, m + 1))
+            self.mpc_qp_async(prm, x0, ref, planes, out)
+            pts = out["x"]
 
     def search_at_async(self, dp: DeviceProblem, graph: Graph, endpoints, out: dict) -> None:
         """plan_search_at: start and goal read from the device tensor
