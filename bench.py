@@ -48,13 +48,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=0, help="rows of the oracle sample (0: auto)")
     ap.add_argument("--form", default="plain",
-                    choices=["plain", "fp64", "tf32", "bf16", "batched", "refine", "cut", "replan", "planes"],
+                    choices=["plain", "fp64", "tf32", "bf16", "batched", "refine", "cut", "replan", "planes", "mpc"],
                     help="plain: 3-D FP32 workload (the default line); fp64: 2-D FP64 plain method; tf32/bf16: "
                          "precision form on the 2-D workload; batched: 256 uneven queries in one graph replay; "
                          "refine: 65536-segment forward+backward; cut: keep-out cut of a 5000-state graph "
                          "against 500 obstacles, then the search; replan: the captured replanning tick "
                          "(moving obstacles in, cut + search, path out); planes: closest points and separating "
-                         "planes of 5000 nodes x 500 obstacles")
+                         "planes of 5000 nodes x 500 obstacles; mpc: SQP refinement (3 rounds of nearest planes + "
+                         "the MPC QP) of a batch of problems in the keep-out scene")
+    ap.add_argument("--mpc-batch", type=int, default=1024, help="MPC problems per step (form mpc)")
     ap.add_argument("--queries", type=int, default=256)
     ap.add_argument("--pipeline", type=int, default=-1,
                     help="FP32 pair kernel of the plain line: 0 screened, 1 warp-specialised, 2 unscreened "
@@ -312,6 +314,8 @@ def run_form(args):
             line.update(run_replan_form(args, stream, flush, dev))
         elif args.form == "planes":
             line.update(run_planes_form(args, stream, flush, dev))
+        elif args.form == "mpc":
+            line.update(run_mpc_form(args, stream, flush, dev))
         elif args.form == "refine":
             from paper_2411_13507_gb300 import refine as RF
             rb = synth.refine_segments(seed=args.seed, S=65536)
@@ -633,6 +637,134 @@ def run_planes_form(args, stream, flush, dev):
                          "peak_note": f"copy bandwidth ({peak_src})",
                          "note": "algorithmic bytes: 24 B of outputs per pair + 8 B per node + the inputs"},
             "e2e": None, "cpu_baseline": cpu}
+
+
+def run_mpc_form(args, stream, flush, dev):
+    """The MPC refinement of Sec. III-D (Eq. (MPC), solved SQP-style): a batch
+    of problems in the keep-out scene (2-D double integrator, degree 5, H = 10
+    segments of dt = 0.1, the free box [0, 5]^2 as keep-in polytope, its 500
+    obstacles); one step = three rounds of (plane of the nearest obstacle at
+    every current node, then the QP of every problem)."""
+    import torch
+    from paper_2411_13507_gb300 import plan as P
+    from paper_2411_13507_gb300 import synth
+    B, H, dt, rounds, width = int(args.mpc_batch), 10, 0.1, 3, 5.0
+    prob, obs = synth.keepout_2d(seed=1)
+    pl = P.Planner(2, 2, 5, (2.0, 4.0), arith="f64", input="f64", stream=stream)
+    do = P.obstacles_to_device(obs, input="f64")
+    # references whose every node keeps 0.05 from every obstacle (filtered
+    # once on the GPU with the nearest distances; untimed)
+    kept = []
+    for rep in range(8):       # candidate pools until B references keep their clearance
+        cand = synth.mpc_references(args.seed + 1000 * rep, 8 * B, H, dt, width)
+        pts = torch.tensor(np.ascontiguousarray(cand[:, :, :2].reshape(-1, 2)), dtype=torch.float64, device=dev)
+        tmp = torch.empty((pts.shape[0], 3), dtype=torch.float32, device=dev)
+        nd = torch.empty(pts.shape[0], dtype=torch.float32, device=dev)
+        pl.nearest_planes_async(pts, do, tmp, None, nd)
+        assert pl.wait() == P.PLAN_OK
+        keep = (nd.view(8 * B, H + 1).min(dim=1).values >= 0.05).cpu().numpy()
+        kept.append(cand[keep])
+        if sum(k.shape[0] for k in kept) >= B:
+            break
+    ref_np = np.concatenate(kept)[:B]
+    assert ref_np.shape[0] == B, "too few references with clearance"
+    Q, F, R, V = [1.0, 1.0, 0.1, 0.1], [0.5, 0.5, 0.05, 0.05], [0.05, 0.05], [2.0, 2.0, 2.0, 2.0]
+    KA = np.array([[1.0, 0.0], [-1.0, 0.0], [0.0, 1.0], [0.0, -1.0]])
+    Kb = np.array([width, 0.0, width, 0.0])
+    prm = pl.mpc_params(H, dt, Q, F, R, V, KA, Kb)
+    ref = torch.tensor(ref_np, dtype=torch.float64, device=dev)
+    x0 = ref[:, 0].contiguous()
+    out = pl.alloc_mpc(B, H)
+    planes = torch.empty((B, H, 3), dtype=torch.float32, device=dev)
+    step = lambda: pl.mpc_refine_async(prm, x0, ref, do, out, sqp_iters=rounds, planes=planes)
+    step()
+    assert pl.wait() == P.PLAN_OK
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t0 = time.time()
+        while clk.count() < 1 and time.time() - t0 < 10.0:
+            step()
+            torch.cuda.synchronize()
+        mark = max(0, clk.count() - 1)
+        ms = timed(step, stream, args.steps, args.warmup, flush)
+        qms = timed(lambda: pl.mpc_qp_async(prm, x0, ref, planes, out), stream, args.steps, args.warmup, flush)
+        t0 = time.time()
+        while clk.count() < mark + 2 and time.time() - t0 < 5.0:
+            step()
+            torch.cuda.synchronize()
+    clocks = clk.summary(since=mark)
+    assert pl.wait() == P.PLAN_OK
+    st = out["status"].cpu().numpy()
+    iters = out["iters"].cpu().numpy()
+    # end to end: references and states in from pinned host memory, the
+    # refinement, nodes and inputs back to pinned host memory
+    h_ref = torch.from_numpy(ref_np.copy()).pin_memory()
+    h_x0 = torch.from_numpy(np.ascontiguousarray(ref_np[:, 0])).pin_memory()
+    h_x = torch.empty(out["x"].shape, dtype=torch.float64).pin_memory()
+    h_u = torch.empty(out["u"].shape, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        ref.copy_(h_ref, non_blocking=True)
+        x0.copy_(h_x0, non_blocking=True)
+        step()
+        h_x.copy_(out["x"], non_blocking=True)
+        h_u.copy_(out["u"], non_blocking=True)
+    ems = timed(e2e_step, stream, args.steps, args.warmup, flush)
+    bi = h_ref.numel() * 8 + h_x0.numel() * 8
+    bo = h_x.numel() * 8 + h_u.numel() * 8
+    # FP64 work of the QP kernel (an estimate from the step counts): every
+    # active-set step scans every row (about 8 g operations a row: the row's
+    # value and magnitude over 2g states of one or all axes) and updates the
+    # factors (about 6 nv^2 operations)
+    m_, g_, p_ = 2, 2, 5
+    rax = sum(p_ - k + 1 for k in range(1, g_ + 1))
+    rows = H * m_ * rax * 2 + H * (p_ + 1) + H * p_ * 4
+    nv = m_ * H
+    flops = float(iters.sum()) * (rows * 8 * g_ + 6 * nv * nv)
+    qmean = statistics.mean(qms)
+    fp64_peak = 1.25e3   # GFLOP/s, nominal FP64 of the part
+    achieved = flops / (qmean / 1e3) / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import mpc as OM
+        from oracle import planes as OP
+        t0 = time.perf_counter()
+        k = 0
+        A = np.asarray(obs.A, dtype=np.float64)
+        bb = np.asarray(obs.b, dtype=np.float64)
+        while time.perf_counter() - t0 < 10.0 and k < B:
+            cur = ref_np[k]
+            for _ in range(rounds):
+                pr = OP.planes(cur[:H, :2], obs.off, A, bb)
+                pk = np.stack([pr["plane"][i, pr["nearest"][i]] for i in range(H)])
+                r = OM.mpc_qp(2, 2, 5, (2.0, 4.0), dt, ref_np[k, 0], ref_np[k], pk, Q, F, R, V, KA, Kb)
+                if r["status"] != OM.OK:
+                    break
+                cur = r["x"]
+            k += 1
+        dts = time.perf_counter() - t0
+        cpu = {"value": k / dts, "unit": "problems/s", "cores": 1, "kind": "oracle",
+               "sample": f"{k} of {B} problems x {rounds} SQP rounds ({dts:.1f} s, numpy FP64: all-pairs planes + "
+                         "primal active set)"}
+    mean_ms = statistics.mean(ms)
+    return {"metric": f"MPC refinements per second ({rounds} SQP rounds of nearest planes + QP), batch of {B} "
+                      "problems, keep-out scene", "value": B * 1e3 / mean_ms, "unit": "problems/s", "dtype": "f64",
+            "ms_per_step": mean_ms, "qp_ms_per_launch": qmean, "gpu_launches": 6 * rounds, "clocks": clocks,
+            "status_counts": {"ok": int((st == 0).sum()), "infeasible": int((st == 1).sum()),
+                              "iteration_limit": int((st == 2).sum())},
+            "active_set_steps_mean": float(iters.mean()),
+            "config": {"workload": f"mpc_references seed {args.seed} (B={B}, H={H}, dt={dt}, nodes 0.05 clear of "
+                                   "every obstacle) in keepout_2d seed 1 (500 obstacles, box [0,5]^2 as keep-in)",
+                       "rows_per_problem": rows, "inputs_per_problem": nv,
+                       "l2": "flushed before every timed step (256 MB write)",
+                       "paper_context": "MPC at 200 Hz (one problem, OSQP on a CPU)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s",
+                         "frac": achieved / fp64_peak, "traffic": None, "kernel": "k_mpc (one QP launch)",
+                         "peak_note": "nominal FP64 rate of the part (no measured FP64 peak)",
+                         "note": "FP64 work estimated from the active-set step counts; the solver is latency-bound "
+                                 "(one warp per problem, sequential active-set steps)"},
+            "e2e": {"value": B * 1e3 / statistics.mean(ems), "unit": "problems/s", "h2d_bytes_per_step": bi,
+                    "d2h_bytes_per_step": bo, "ms_per_step": statistics.mean(ems)},
+            "cpu_baseline": cpu}
 
 
 def main():

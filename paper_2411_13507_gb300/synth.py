@@ -22,6 +22,11 @@ Recipes (sizes follow the workloads the method is evaluated on):
   durations 8-16).
 * ``refine_segments``       -- degree-7 3-D segments for the smoothed-barrier
   refinement (interior control points N(0,1) around a straight line).
+* ``mpc_references``        -- reference nodes for the MPC refinement: each a
+  cubic polynomial in time per axis (random start inside the box, speed
+  U[0.2, 1], acceleration and jerk N(0, 0.5)) sampled at k dt with its
+  derivatives up to gamma - 1, kept when every sample stays in the inner 90%
+  of the box.
 
 Polytope recipe: an axis box (centre uniform in the domain, side uniform in
 [smin, smax] per axis) intersected with 0..max_cuts random half-spaces whose
@@ -371,3 +376,36 @@ def refine_segments(seed: int = 1, S: int = 65536, degree: int = 7, m: int = 3,
             rows += 1
         nrows[s] = rows
     return RefineBatch(P=P, T=T, A=A, b=b, nrows=nrows, bounds=tuple(bounds))
+
+
+def mpc_references(seed: int, B: int, H: int, dt: float, width: float = 5.0, m: int = 2, g: int = 2) -> np.ndarray:
+    """[B][H+1][m g] reference nodes (derivative-major: positions, then
+    velocities, ...): samples of cubic polynomials in time and their
+    derivatives (the recipe above)."""
+    rng = SplitMix64(seed, 11)
+    out = np.zeros((B, H + 1, m * g))
+    t = dt * np.arange(H + 1)
+    b = 0
+    while b < B:
+        p0 = rng.uniform(m, 0.1 * width, 0.9 * width)
+        d = rng.normal(m)
+        d = d / max(float(np.linalg.norm(d)), 1e-12)
+        v0 = d * float(rng.uniform(1, 0.2, 1.0)[0])
+        a0 = 0.5 * rng.normal(m)
+        j0 = 0.5 * rng.normal(m)
+        # derivative c of p0 + v0 t + a0 t^2 / 2 + j0 t^3 / 6
+        coef = [p0, v0, a0, j0]
+        nodes = np.zeros((H + 1, m * g))
+        for c in range(g):
+            val = np.zeros((H + 1, m))
+            for e in range(c, 4):
+                fac = 1.0
+                for q in range(e - c + 1, e + 1):
+                    fac *= q
+                val += np.outer(t ** (e - c), coef[e]) * (fac / np.prod(np.arange(1, e + 1), dtype=np.float64))
+            nodes[:, c * m:(c + 1) * m] = val
+        pos = nodes[:, :m]
+        if np.all(pos >= 0.05 * width) and np.all(pos <= 0.95 * width):
+            out[b] = nodes
+            b += 1
+    return out
