@@ -114,6 +114,9 @@ struct plan_ctx {
     double* d_mpc = nullptr;
     double* h_mpc = nullptr;
     int mpc_cap = 0;
+    double* d_mpcJ = nullptr;
+    long long mpc_jcap = 0;
+    std::vector<double> mpc_last;   // table and horizon whose factor d_mpcJ holds
     cudaEvent_t mpc_ev = nullptr;
     bool mpc_ev_live = false;
     int smem_optin = 0;
@@ -415,7 +418,7 @@ void plan_destroy(plan_ctx* c) {
                    c->resBits, c->resKey, c->emitPre, c->recheck, c->sdist, c->sbest, c->spred, c->sfront, c->slast, c->snear,
                    c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem, c->d_qMem, c->d_sqd, c->memOff,
                    c->d_cut64, c->d_cut32, c->cut_src, c->cut_hit, c->cut_pos, c->cut_chunk, c->cut_orow,
-                   c->cut_ocount, c->cut_list32, c->cut_okb, c->cut_obox, c->pl_orow, c->pl_face, c->pl_edge, c->pl_nedge, c->pl_ocount, c->pl_keys, c->pl_near, c->d_mpc, c->g_d, c->g_succ, c->g_wsucc, c->g_anc, c->g_prev};
+                   c->cut_ocount, c->cut_list32, c->cut_okb, c->cut_obox, c->pl_orow, c->pl_face, c->pl_edge, c->pl_nedge, c->pl_ocount, c->pl_keys, c->pl_near, c->d_mpc, c->d_mpcJ, c->g_d, c->g_succ, c->g_wsucc, c->g_anc, c->g_prev};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_tab64) cudaFreeHost(c->h_tab64);
@@ -1226,14 +1229,21 @@ int plan_mpc_qp(plan_ctx* c, int B, const plan_mpc_params* prm, const double* x0
     if (B > 0 && (!x0 || !ref || !planes || !x || !u || !obj || !status))
         return fail(c, PLAN_ERR_INVALID_ARG, "null MPC array");
     const int rax = reach_rows(g, p);
-    // warps (problems) per CTA: as many as the shared memory holds, at most 8
-    int W = 8;
-    while (W > 0 && mpc_smem(m, g, p, rax, nk, H, W) > (size_t)c->smem_optin) --W;
-    if (W == 0) return fail(c, PLAN_ERR_UNSUPPORTED, "MPC problem too large for shared memory");
+    // one warp (problem) per CTA: the FP64 pipe of every SM is the bound, and
+    // small CTAs let the scheduler spread the problems evenly over the SMs
+    const int W = 1;
+    if (mpc_smem(m, g, p, rax, nk, H, W) > (size_t)c->smem_optin ||
+        mpc_setup_smem(m, g, p, rax, nk, H) > (size_t)c->smem_optin)
+        return fail(c, PLAN_ERR_UNSUPPORTED, "MPC problem too large for shared memory");
     // the table: per-axis transition A[c][c'] = dt^(c'-c)/(c'-c)!, input
     // column B[c] = dt^(g-c)/(g-c)!, D and reach rows of duration dt, the
     // bound of every reach row, weights, keep-in rows
     const int ts = mpc_table_size(m, g, p, rax, nk);
+    if ((long long)m * H * m * H > c->mpc_jcap) {
+        c->mpc_last.clear();
+        if (!dalloc(c, &c->d_mpcJ, (long long)m * H * m * H)) return PLAN_ERR_NO_MEMORY;
+        c->mpc_jcap = (long long)m * H * m * H;
+    }
     if (ts > c->mpc_cap) {
         if (c->mpc_ev_live) cudaEventSynchronize(c->mpc_ev);
         if (c->h_mpc) cudaFreeHost(c->h_mpc);
@@ -1295,10 +1305,23 @@ int plan_mpc_qp(plan_ctx* c, int B, const plan_mpc_params* prm, const double* x0
     M.obj = obj;
     M.status = status;
     M.iters = iters;
+    M.J0 = c->d_mpcJ;
+    // the factor depends on the table (model, dt, weights, keep-in rows
+    // included, a superset) and the horizon only
+    std::vector<double> key(c->h_mpc, c->h_mpc + ts);
+    key.push_back((double)H);
+    key.push_back((double)m);
+    key.push_back((double)g);
+    key.push_back((double)p);
+    M.j0_ready = key == c->mpc_last ? 1 : 0;
     int launches = 0;
     int ce = launch_mpc(M, c->stream, &launches);
     c->launches += launches;
-    if (ce != 0) return cuda_fail(c, (cudaError_t)ce, "MPC launch");
+    if (ce != 0) {
+        c->mpc_last.clear();
+        return cuda_fail(c, (cudaError_t)ce, "MPC launch");
+    }
+    c->mpc_last.swap(key);
     return PLAN_OK;
 }
 

@@ -359,9 +359,12 @@ struct MpcParams {
     double* obj;            // [B]
     int32_t* status;        // [B]
     int32_t* iters;         // [B] or null
+    double* J0;             // [nv][nv] scratch: L^-T of the batch's Hessian
+    int j0_ready;           // J0 already holds the factor of this table (the setup kernel is skipped)
 };
 int mpc_table_size(int m, int g, int p, int rax, int nkeep);
 size_t mpc_smem(int m, int g, int p, int rax, int nkeep, int H, int W);
+size_t mpc_setup_smem(int m, int g, int p, int rax, int nkeep, int H);
 int launch_mpc(const MpcParams& P, void* stream, int* launches);
 
 // Launchers (plan_build.cu / plan_search.cu / plan_refine.cu); return cudaError_t as int.

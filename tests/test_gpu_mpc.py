@@ -209,3 +209,24 @@ def test_sqp_rounds_against_oracle():
     pl.mpc_refine_async(prm, x0, ref, do, out2, sqp_iters=3)
     assert pl.wait() == P.PLAN_OK
     assert np.array_equal(out2["x"].cpu().numpy(), last)
+
+
+def test_factor_cache_follows_the_weights():
+    """One context, three calls: weights W1, W2 (the Hessian's factor must be
+    recomputed), W1 again -- each against the oracle."""
+    insts = [cut_in(instance(40 + s), s) for s in range(4)]
+    i0 = insts[0]
+    H = i0["ref"].shape[0] - 1
+    pl = planner(2, 2, 5, i0["bounds"])
+    dev = torch.device("cuda")
+    x0 = torch.tensor(np.stack([t["x0"] for t in insts]), dtype=torch.float64, device=dev)
+    ref = torch.tensor(np.stack([t["ref"] for t in insts]), dtype=torch.float64, device=dev)
+    planes = torch.tensor(np.stack([t["planes"] for t in insts]), dtype=torch.float32, device=dev)
+    for Q in (i0["Q"], 3.0 * i0["Q"], i0["Q"]):
+        prm = pl.mpc_params(H, i0["dt"], Q, i0["F"], i0["R"], i0["V"])
+        out = pl.alloc_mpc(len(insts), H)
+        pl.mpc_qp_async(prm, x0, ref, planes, out)
+        assert pl.wait() == P.PLAN_OK
+        g = {k: v.cpu().numpy() for k, v in out.items()}
+        for b, t in enumerate(insts):
+            compare(g, b, dict(t, Q=Q))
