@@ -473,8 +473,8 @@ def run_cut_form(args, stream, flush, dev):
 
 
 def run_replan_form(args, stream, flush, dev):
-    """The replanning loop (Alg. 1 lines 3-4 per tick on the fixed graph of
-    line 2): 500 obstacles moving by a random walk and a moving start, each
+    """The replanning loop (Algorithm 1's cutGraph and findPath every tick on
+    the graph its buildGraph made once): 500 obstacles moving by a random walk and a moving start, each
     tick one replay of the captured graph (obstacles and start/goal copied in
     from pinned host memory, cut, search, path copied out), host-timed to the
     path in host memory."""

@@ -148,7 +148,7 @@ int plan_create(plan_ctx** out, const plan_model* model, void* cuda_stream);
 void plan_destroy(plan_ctx* ctx);
 
 /*
- * buildGraph + keep-in cut (Alg. 1 lines 2-3, Sec. III-A/B): for every ordered
+ * buildGraph + keep-in cut (Algorithm 1, Sec. III-A/B): for every ordered
  * pair of states sharing at least one free polytope and every duration T_t,
  * form the control points meeting the boundary conditions (Lemma 1, elevated
  * to degree p), test the hodograph control points against the bounds
@@ -220,7 +220,7 @@ int plan_autotune(plan_ctx* ctx, int reps, int* best_tile, int* best_ctas, int* 
                   double* best_ms);
 
 /*
- * findPath (Alg. 1 line 4, Sec. III-C, Problem 2): the start and goal vertices
+ * findPath (Algorithm 1, Sec. III-C, Problem 2): the start and goal vertices
  * are the states nearest (Euclidean, positions only; ties to the lowest id) to
  * start_pos and goal_pos; then shortest paths with Dijkstra semantics (FP64
  * accumulation dist[u] + w; predecessor = the earliest-settled vertex that
@@ -252,7 +252,7 @@ int plan_search_at(plan_ctx* ctx, int N, const void* states, const plan_edges* e
                    int32_t* path, int path_cap, int32_t* path_len, double* cost);
 
 /*
- * Goal-rooted search for a replanning loop (Alg. 1 line 4 every tick; Sec.
+ * Goal-rooted search for a replanning loop (Algorithm 1's findPath every tick; Sec.
  * III-C): start and goal vertices as plan_search_at (nearest to device
  * endpoints [2][m]); then the distance of every vertex TO the goal vertex, the
  * fixed point of d[u] = min over out-edges (u -> v) of (w + d[v]) in FP64,
@@ -291,7 +291,7 @@ typedef struct {
 } plan_obstacles;
 
 /*
- * cutGraph (Alg. 1 line 3, Sec. III-B, Algorithm 2 cutHeuristic, Cut-QP):
+ * cutGraph (Algorithm 1, Sec. III-B, Algorithm 2 cutHeuristic, Cut-QP):
  * remove from a built graph every (edge, duration) whose curve may meet an
  * obstacle.  By Property 1 a curve is collision-free when the convex hull of
  * its control points P_0..P_p misses the obstacle; with the margins

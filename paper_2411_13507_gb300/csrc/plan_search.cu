@@ -588,9 +588,9 @@ __global__ void __launch_bounds__(1024) k_search_batched(BatchSearchParams B) {
 }
 
 // ---------------------------------------------------------------------------
-// Goal-rooted search with a warm start (the replanning loop of Alg. 1: line 4
-// every tick on a graph that changes only where obstacles moved; Sec. III-C
-// distances and path).  One cooperative launch, one 1024-thread block per SM.
+// Goal-rooted search with a warm start (the replanning loop of Algorithm 1:
+// findPath every tick on a graph that changes only where obstacles moved;
+// Sec. III-C distances and path).  One cooperative launch, one 1024-thread block per SM.
 //
 // d[u] = distance from u to the goal vertex: the fixed point of
 // d[u] = min over out-edges (u -> v) of fl(w + d[v]), d[goal] = 0, reached by

@@ -701,8 +701,8 @@ class Planner:
 
 
 class Replanner:
-    """The replanning loop of Alg. 1 (lines 3-4 every tick, the graph of line 2
-    fixed): each tick refreshes the obstacles and the start/goal positions on
+    """The replanning loop of Algorithm 1 (cutGraph and findPath every tick, the
+    graph of buildGraph fixed): each tick refreshes the obstacles and the start/goal positions on
     the device from pinned host buffers, cuts the fixed graph against the
     obstacles (plan_cut_edges), searches the cut graph and copies the path
     back -- all replayed from one captured CUDA graph.  The search is the

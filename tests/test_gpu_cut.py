@@ -177,7 +177,7 @@ def test_obstacle_with_too_many_rows_is_unsupported():
 
 
 def test_cut_then_search_matches_oracle():
-    """findPath on the cut graph (Alg. 1 lines 3-4)."""
+    """findPath on the cut graph (Algorithm 1's cutGraph, then findPath)."""
     prob, obs = synth.keepout_2d(2, N=600, n_obst=60)
     pl, dp, g, out, info, E_in = run_cut(prob, obs, "f64")
     op = oracle.OracleProblem(prob)

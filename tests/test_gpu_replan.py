@@ -1,5 +1,5 @@
-"""The replanning loop (Alg. 1 lines 3-4 every tick on the fixed graph of line
-2): cut + search + path read-back replayed from one captured CUDA graph, with
+"""The replanning loop (Algorithm 1's cutGraph and findPath every tick on the
+graph its buildGraph made once): cut + search + path read-back replayed from one captured CUDA graph, with
 moving obstacles and start/goal positions refreshed from pinned host memory.
 Every tick must equal the direct (uncaptured) calls; two ticks are also
 compared with the exact oracle."""
