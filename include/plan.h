@@ -414,13 +414,16 @@ enum { PLAN_MPC_OK = 0, PLAN_MPC_INFEASIBLE = 1, PLAN_MPC_ITERATION_LIMIT = 2 };
  *   status  device int32 [B]: PLAN_MPC_OK, PLAN_MPC_INFEASIBLE or
  *           PLAN_MPC_ITERATION_LIMIT (x, u, obj then describe the last iterate)
  *   iters   device int32 [B] or NULL: active-set steps taken
+ *   nodes   device double [B][H][m] or NULL: the positions of x_0 .. x_{H-1}
+ *           (the points of the next round's plan_nearest_planes)
  * Asynchronous on the context stream; host errors INVALID_ARG (bad sizes or
  * weights) and UNSUPPORTED (model or problem size); per-problem outcomes go
  * to status, not to plan_wait.  An SQP refinement alternates
  * plan_nearest_planes at the new nodes and plan_mpc_qp.
  */
 int plan_mpc_qp(plan_ctx* ctx, int B, const plan_mpc_params* prm, const double* x0, const double* ref,
-                const float* planes, double* x, double* u, double* obj, int32_t* status, int32_t* iters);
+                const float* planes, double* x, double* u, double* obj, int32_t* status, int32_t* iters,
+                double* nodes);
 
 /* Weights of the refinement objective (defaults 1, 1, 0.1). */
 typedef struct {

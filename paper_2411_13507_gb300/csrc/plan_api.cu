@@ -1202,7 +1202,8 @@ int plan_nearest_planes(plan_ctx* c, int P, const void* points, const plan_obsta
 }
 
 int plan_mpc_qp(plan_ctx* c, int B, const plan_mpc_params* prm, const double* x0, const double* ref,
-                const float* planes, double* x, double* u, double* obj, int32_t* status, int32_t* iters) {
+                const float* planes, double* x, double* u, double* obj, int32_t* status, int32_t* iters,
+                double* nodes) {
     if (!c) return PLAN_ERR_INVALID_ARG;
     const int m = c->model.m, g = c->model.gamma, p = c->model.degree, n = m * g;
     if (m < 1 || m > 3 || g < 1 || g > 4 || p < 2 * g - 1 || p > 9)
@@ -1305,6 +1306,7 @@ int plan_mpc_qp(plan_ctx* c, int B, const plan_mpc_params* prm, const double* x0
     M.obj = obj;
     M.status = status;
     M.iters = iters;
+    M.nodes = nodes;
     M.J0 = c->d_mpcJ;
     // the factor depends on the table (model, dt, weights, keep-in rows
     // included, a superset) and the horizon only

@@ -359,6 +359,7 @@ struct MpcParams {
     double* obj;            // [B]
     int32_t* status;        // [B]
     int32_t* iters;         // [B] or null
+    double* nodes;          // [B][H][m] positions of x_0 .. x_{H-1}, or null
     double* J0;             // [nv][nv] scratch: L^-T of the batch's Hessian
     int j0_ready;           // J0 already holds the factor of this table (the setup kernel is skipped)
 };

@@ -692,6 +692,7 @@ __global__ void __launch_bounds__(256) k_mpc(MpcParams P) {
         for (int j = 0; j < k; ++j) s += Gam[(k * g + c) * H + j] * uv[a * H + j];
         xs[i] = s;
         P.x[b * (H + 1) * n + i] = s;
+        if (P.nodes && k < H && cm < m) P.nodes[(b * H + k) * m + cm] = s;   // positions of x_0 .. x_{H-1}
     }
     for (int i = lane; i < nv; i += 32) {
         const int a = i / H, j = i % H;

@@ -143,7 +143,7 @@ def load(build_if_stale: bool = True):
     lib.plan_obstacle_planes.restype = i32
     lib.plan_nearest_planes.argtypes = [vp, i32, vp, ctypes.POINTER(_Obstacles), vp, vp, vp]
     lib.plan_nearest_planes.restype = i32
-    lib.plan_mpc_qp.argtypes = [vp, i32, ctypes.POINTER(_MpcParams), vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.plan_mpc_qp.argtypes = [vp, i32, ctypes.POINTER(_MpcParams), vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.plan_mpc_qp.restype = i32
     lib.plan_search_at.argtypes = [vp, i32, vp, ctypes.POINTER(_Edges), vp, vp, i32, vp, vp]
     lib.plan_search_to.argtypes = [vp, i32, vp, ctypes.POINTER(_Edges), vp, i32, vp, i32, vp, vp]
@@ -495,7 +495,8 @@ class Planner:
                 "u": torch.empty((B, horizon, m), dtype=torch.float64, device=dev),
                 "obj": torch.empty(B, dtype=torch.float64, device=dev),
                 "status": torch.empty(B, dtype=torch.int32, device=dev),
-                "iters": torch.empty(B, dtype=torch.int32, device=dev)}
+                "iters": torch.empty(B, dtype=torch.int32, device=dev),
+                "nodes": torch.empty((B, horizon, m), dtype=torch.float64, device=dev)}
 
     def mpc_qp_async(self, prm, x0, ref, planes, out: dict) -> None:
         """plan_mpc_qp on device tensors: x0 float64 [B][n], ref float64
@@ -503,7 +504,7 @@ class Planner:
         ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
         rc = self.lib.plan_mpc_qp(self.ctx, int(x0.shape[0]), ctypes.byref(prm), ptr(x0), ptr(ref), ptr(planes),
                                   ptr(out["x"]), ptr(out["u"]), ptr(out["obj"]), ptr(out["status"]),
-                                  ptr(out.get("iters")))
+                                  ptr(out.get("iters")), ptr(out.get("nodes")))
         if rc != 0:
             raise self._err(rc, "plan_mpc_qp")
 
@@ -517,14 +518,14 @@ class Planner:
         B, H, m = int(x0.shape[0]), int(prm.horizon), int(self.model.m)
         if planes is None:
             planes = torch.empty((B, H, m + 1), dtype=torch.float32, device=x0.device)
-        pts = ref
+        if out.get("nodes") is None:
+            out["nodes"] = torch.empty((B, H, m), dtype=torch.float64, device=x0.device)
+        nodes = ref[:, :H, :m].contiguous()         # the reference's node positions (input marshalling)
         for _ in range(int(sqp_iters)):
-            nodes = pts[:, :H, :m].contiguous()     # node positions (a strided copy)
-            if self.input == "f32":
-                nodes = nodes.float()
-            self.nearest_planes_async(nodes.view(B * H, m), obst, planes.view(B * H, m + 1))
+            pts = nodes.float() if self.input == "f32" else nodes
+            self.nearest_planes_async(pts.view(B * H, m), obst, planes.view(B * H, m + 1))
             self.mpc_qp_async(prm, x0, ref, planes, out)
-            pts = out["x"]
+            nodes = out["nodes"]                    # positions of the new nodes, written by the QP kernel
 
     def search_at_async(self, dp: DeviceProblem, graph: Graph, endpoints, out: dict) -> None:
         """plan_search_at: start and goal read from the device tensor

@@ -200,6 +200,7 @@ def test_sqp_rounds_against_oracle():
         pl.mpc_qp_async(prm, x0, ref, planes, out)
         assert pl.wait() == P.PLAN_OK
         g = {k: v.cpu().numpy() for k, v in out.items()}
+        assert np.array_equal(g["nodes"], g["x"][:, :H, :2])   # the next round's points
         pn = planes.cpu().numpy().astype(np.float64)
         for b, t in enumerate(insts):
             compare(g, b, dict(t, planes=pn[b]))
