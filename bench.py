@@ -711,15 +711,18 @@ def run_mpc_form(args, stream, flush, dev):
     ems = timed(e2e_step, stream, args.steps, args.warmup, flush)
     bi = h_ref.numel() * 8 + h_x0.numel() * 8
     bo = h_x.numel() * 8 + h_u.numel() * 8
-    # FP64 work of the QP kernel (an estimate from the step counts): every
-    # active-set step scans every row (about 8 g operations a row: the row's
-    # value and magnitude over 2g states of one or all axes) and updates the
-    # factors (about 6 nv^2 operations)
+    # FP64 work of the QP kernel (a model from the step counts; the rows are
+    # screened in float and do not count): per problem the gradient
+    # (8 g (H+1) flops per input) and the unconstrained start (4 nv^2); per
+    # active-set step d = J'n (2 nv^2), z (about nv^2), the Householder update
+    # (about 2 nv^2), the back substitution and the node states
+    # (2 (H+1) n H / 2)
     m_, g_, p_ = 2, 2, 5
+    n_ = m_ * g_
     rax = sum(p_ - k + 1 for k in range(1, g_ + 1))
     rows = H * m_ * rax * 2 + H * (p_ + 1) + H * p_ * 4
     nv = m_ * H
-    flops = float(iters.sum()) * (rows * 8 * g_ + 6 * nv * nv)
+    flops = B * (8.0 * g_ * (H + 1) * nv + 4.0 * nv * nv) + float(iters.sum()) * (5.0 * nv * nv + (H + 1) * n_ * H)
     qmean = statistics.mean(qms)
     fp64_peak = 1.25e3   # GFLOP/s, nominal FP64 of the part
     achieved = flops / (qmean / 1e3) / 1e9
@@ -760,8 +763,9 @@ def run_mpc_form(args, stream, flush, dev):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s",
                          "frac": achieved / fp64_peak, "traffic": None, "kernel": "k_mpc (one QP launch)",
                          "peak_note": "nominal FP64 rate of the part (no measured FP64 peak)",
-                         "note": "FP64 work estimated from the active-set step counts; the solver is latency-bound "
-                                 "(one warp per problem, sequential active-set steps)"},
+                         "note": "FP64 flops modelled from the active-set step counts; comparisons, divisions and "
+                                 "square roots also occupy the FP64 pipe, which ncu measures 55% busy while active "
+                                 "(profiles/k_mpc_keepout_2d.md)"},
             "e2e": {"value": B * 1e3 / statistics.mean(ems), "unit": "problems/s", "h2d_bytes_per_step": bi,
                     "d2h_bytes_per_step": bo, "ms_per_step": statistics.mean(ems)},
             "cpu_baseline": cpu}
