@@ -751,7 +751,7 @@ def run_mpc_form(args, stream, flush, dev):
     mean_ms = statistics.mean(ms)
     return {"metric": f"MPC refinements per second ({rounds} SQP rounds of nearest planes + QP), batch of {B} "
                       "problems, keep-out scene", "value": B * 1e3 / mean_ms, "unit": "problems/s", "dtype": "f64",
-            "ms_per_step": mean_ms, "qp_ms_per_launch": qmean, "gpu_launches": 6 * rounds, "clocks": clocks,
+            "ms_per_step": mean_ms, "qp_ms_per_launch": qmean, "gpu_launches": 7 * rounds, "clocks": clocks,
             "status_counts": {"ok": int((st == 0).sum()), "infeasible": int((st == 1).sum()),
                               "iteration_limit": int((st == 2).sum())},
             "active_set_steps_mean": float(iters.mean()),

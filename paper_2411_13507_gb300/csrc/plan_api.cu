@@ -147,6 +147,7 @@ struct plan_ctx {
     int* pl_ocount = nullptr;
     unsigned long long* pl_keys = nullptr;
     int32_t* pl_near = nullptr;
+    float* pl_ub = nullptr;
     // timing
     bool timing = false;
     bool accounting = false;
@@ -418,7 +419,7 @@ void plan_destroy(plan_ctx* c) {
                    c->resBits, c->resKey, c->emitPre, c->recheck, c->sdist, c->sbest, c->spred, c->sfront, c->slast, c->snear,
                    c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem, c->d_qMem, c->d_sqd, c->memOff,
                    c->d_cut64, c->d_cut32, c->cut_src, c->cut_hit, c->cut_pos, c->cut_chunk, c->cut_orow,
-                   c->cut_ocount, c->cut_list32, c->cut_okb, c->cut_obox, c->pl_orow, c->pl_face, c->pl_edge, c->pl_nedge, c->pl_ocount, c->pl_keys, c->pl_near, c->d_mpc, c->d_mpcJ, c->g_d, c->g_succ, c->g_wsucc, c->g_anc, c->g_prev};
+                   c->cut_ocount, c->cut_list32, c->cut_okb, c->cut_obox, c->pl_orow, c->pl_face, c->pl_edge, c->pl_nedge, c->pl_ocount, c->pl_keys, c->pl_near, c->pl_ub, c->d_mpc, c->d_mpcJ, c->g_d, c->g_succ, c->g_wsucc, c->g_anc, c->g_prev};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_tab64) cudaFreeHost(c->h_tab64);
@@ -1148,7 +1149,7 @@ static int planes_common(plan_ctx* c, int P, const void* points, const plan_obst
     }
     const bool want_near = nearest || nearest_dist || nearest_plane;
     if (want_near && P > c->capPlP) {
-        if (!dalloc(c, &c->pl_keys, P) || !dalloc(c, &c->pl_near, P)) {
+        if (!dalloc(c, &c->pl_keys, P) || !dalloc(c, &c->pl_near, P) || !dalloc(c, &c->pl_ub, P)) {
             c->capPlP = -1;
             return PLAN_ERR_NO_MEMORY;
         }
@@ -1178,10 +1179,13 @@ static int planes_common(plan_ctx* c, int P, const void* points, const plan_obst
     Q.nearest = nearest;
     Q.nearest_dist = nearest_dist;
     Q.keys = want_near ? c->pl_keys : nullptr;
+    // nearest only (no per-pair output): prune pairs by distance bounds
+    Q.ub = want_near && !closest && !plane && !dist ? c->pl_ub : nullptr;
     Q.nearest_plane = nearest_plane;
     Q.info = c->d_info;
     cudaError_t e = cudaSuccess;
     if (want_near && P > 0) e = cudaMemsetAsync(c->pl_keys, 0xff, sizeof(unsigned long long) * (size_t)P, c->stream);
+    if (e == cudaSuccess && Q.ub && P > 0) e = cudaMemsetAsync(c->pl_ub, 0x7f, sizeof(float) * (size_t)P, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset planes scratch");
     int launches = 0;
     int ce = launch_planes(Q, c->stream, c->num_sms, &launches);

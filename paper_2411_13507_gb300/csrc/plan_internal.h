@@ -341,6 +341,7 @@ struct PlanesParams {
     unsigned long long* keys;  // [P] nearest keys (distance bits << 32 | obstacle), or null
     float* nearest_plane;      // [P][m+1] plane of the nearest obstacle (h = 0, l = 0 when none), or null
     const int32_t* pair_obst;  // pair mode: [P] one obstacle per point (-1: none); outputs indexed by point
+    float* ub;                 // nearest-only mode: [P] upper bound of the nearest distance (prunes far pairs), or null
     DevInfo* info;
 };
 

@@ -254,6 +254,49 @@ PDEV float pdot(const float4& f, const float* z) {
     return s;
 }
 
+// Nearest-only mode, pass A: per point an upper bound of its nearest
+// obstacle's distance -- the distance to one vertex (the first edge's start)
+// of every obstacle, min-reduced (non-negative floats order as their bits).
+template <int M>
+__global__ void __launch_bounds__(256) k_planes_ub(PlanesParams Q) {
+    const long long total = (long long)Q.P * Q.n_obst;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
+        const long long k = base + threadIdx.x;
+        const bool act = k < total;
+        long long p = 0;
+        unsigned ub = 0x7f7f7f7fu;
+        if (act) {
+            p = k / Q.n_obst;
+            const int o = (int)(k - p * Q.n_obst);
+            const float4* ew = reinterpret_cast<const float4*>(Q.edge) + EDGE_F4 * (long long)o * Q.max_edges;
+            if (Q.nedge[o] >= 1) {
+                const float4 e0 = __ldg(ew), e1 = __ldg(ew + 1);
+                if (fabsf(e0.w) < 3.0e38f) {   // an unbounded edge has no start vertex
+                    float d2 = 0.f;
+#pragma unroll
+                    for (int a = 0; a < M; ++a) {
+                        const float c = fmaf(e0.w, a == 0 ? e1.x : (a == 1 ? e1.y : e1.z),
+                                             a == 0 ? e0.x : (a == 1 ? e0.y : e0.z));
+                        const float t = pld32(Q.points, p * M + a, Q.in_f32) - c;
+                        d2 = fmaf(t, t, d2);
+                    }
+                    ub = __float_as_uint(sqrtf(d2));
+                }
+            }
+        }
+        // lanes of one point are consecutive obstacles: one atomic per run
+        const long long p0 = __shfl_sync(0xffffffffu, p, 0), p31 = __shfl_sync(0xffffffffu, p, 31);
+        if (p0 == p31 && __all_sync(0xffffffffu, act)) {
+            for (int of = 16; of > 0; of >>= 1) ub = min(ub, __shfl_xor_sync(0xffffffffu, ub, of));
+            if (lane == 0) atomicMin(reinterpret_cast<unsigned*>(Q.ub) + p, ub);
+        } else if (act && ub != 0x7f7f7f7fu) {
+            atomicMin(reinterpret_cast<unsigned*>(Q.ub) + p, ub);
+        }
+    }
+}
+
 // One thread per (point, obstacle), the obstacle index fastest (coalesced
 // stores of the point-major outputs); per point the nearest obstacle as a
 // 64-bit key (distance bits << 32 | obstacle), min-reduced per warp first.
@@ -286,7 +329,29 @@ __global__ void __launch_bounds__(256) k_planes(PlanesParams Q) {
             p = k / Q.n_obst;
             o = (int)(k - p * Q.n_obst);
         }
-        if (act) {
+        bool pruned = false;
+        if (act && Q.ub) {
+            // nearest-only mode: an obstacle whose distance lower bound (the
+            // largest signed distance to one of its facet planes) exceeds the
+            // point's upper bound (with room for float rounding) cannot be
+            // the nearest, nor tie with it
+            float v[M], vs = 1.f;
+#pragma unroll
+            for (int a = 0; a < M; ++a) {
+                v[a] = pld32(Q.points, p * M + a, Q.in_f32);
+                vs += fabsf(v[a]);
+            }
+            const int nr = Q.ocount[o];
+            const float4* fw = reinterpret_cast<const float4*>(Q.face) + (long long)o * Q.max_orows;
+            float lb = -inf;
+            for (int r = 0; r < nr; ++r) {
+                const float4 f = __ldg(fw + r);
+                lb = fmaxf(lb, pdot<M>(f, v) - f.w);
+            }
+            const float ub = Q.ub[p];
+            pruned = lb > fmaf(ub, 1.00001f, 1e-5f * vs);
+        }
+        if (act && !pruned) {
             float v[M];
 #pragma unroll
             for (int a = 0; a < M; ++a) v[a] = pld32(Q.points, p * M + a, Q.in_f32);
@@ -444,7 +509,7 @@ __global__ void __launch_bounds__(256) k_planes(PlanesParams Q) {
                     kk = ok < kk ? ok : kk;
                 }
                 if (lane == 0) atomicMin(Q.keys + p, kk);
-            } else if (act) {
+            } else if (act && !pruned) {
                 atomicMin(Q.keys + p, key);
             }
         }
@@ -475,6 +540,11 @@ int launch_planes(const PlanesParams& Q, void* stream, int num_sms, int* launche
     if (total > 0) {
         long long grid = (total + 255) / 256;
         if (grid > (long long)num_sms * 16) grid = (long long)num_sms * 16;
+        if (Q.ub) {
+            if (Q.m == 2) k_planes_ub<2><<<(int)grid, 256, 0, st>>>(Q);
+            else k_planes_ub<3><<<(int)grid, 256, 0, st>>>(Q);
+            ++*launches;
+        }
         if (Q.m == 2) k_planes<2><<<(int)grid, 256, 0, st>>>(Q);
         else k_planes<3><<<(int)grid, 256, 0, st>>>(Q);
         ++*launches;
@@ -492,6 +562,7 @@ int launch_planes(const PlanesParams& Q, void* stream, int num_sms, int* launche
         Q2.dist = nullptr;
         Q2.plane = Q.nearest_plane;
         Q2.keys = nullptr;
+        Q2.ub = nullptr;
         Q2.nearest = nullptr;
         Q2.nearest_dist = nullptr;
         long long grid = (Q.P + 255) / 256;

@@ -98,6 +98,11 @@ def test_planes_full_size_sampled_points():
     pts = prob.states[:, :2]
     gpu, info = run(2, pts, obs)
     compare(pts, obs, gpu, rows=range(0, prob.N, 50))
+    # the nearest-only mode prunes pairs by distance bounds: same nearest
+    # obstacle and distance bits as the all-pairs mode, for every node
+    near, _ = run(2, pts, obs, nearest_only=True)
+    assert np.array_equal(near["nearest"], gpu["nearest"])
+    assert np.array_equal(near["nearest_dist"], gpu["nearest_dist"])
 
 
 def test_points_inside_sixteen_row_obstacles_and_nearest_only():
