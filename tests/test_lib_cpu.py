@@ -24,7 +24,8 @@ def declared_functions():
 
 def test_header_declares_expected_entry_points():
     names = declared_functions()
-    for req in ("plan_create", "plan_build_edges", "plan_cut_edges", "plan_search", "plan_wait", "plan_destroy"):
+    for req in ("plan_create", "plan_build_edges", "plan_cut_edges", "plan_search", "plan_wait", "plan_destroy",
+                "plan_search_at", "plan_search_to", "plan_obstacle_planes", "plan_nearest_planes", "plan_mpc_qp"):
         assert req in names
 
 
