@@ -24,10 +24,11 @@ def kin_step(x, u, m, g, dt):
 
 
 def instance(seed, m=2, g=2, p=5, H=8, dt=0.1, planes_on=True, bounds=(2.0, 4.0, 30.0)):
-    """Feasible by construction: a reference from the kinematics under small
-    random inputs, x0 = r_0, and one plane per segment with a random normal
-    whose offset lies just below every control point of the reference
-    segment (so the reference itself satisfies every row)."""
+    """A reference from the kinematics under small random inputs, x0 = r_0,
+    and one plane per segment with a random normal whose offset lies just
+    below every control point of the reference segment: the reference
+    satisfies the dynamics and every plane row by construction, and its
+    reach rows at the bounds used (the pins check it)."""
     rng = np.random.default_rng(seed)
     n = m * g
     x = np.zeros(n)

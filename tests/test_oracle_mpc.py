@@ -213,3 +213,22 @@ def test_infeasible_mpc():
     inst["planes"][3, :m] = [1.0, 0.0]
     inst["planes"][3, m] = 1e3            # every point must have z_0 >= 1000
     assert solve(inst)["status"] == mpc.INFEASIBLE
+
+
+@pytest.mark.parametrize("seed,m,g,p", [(1, 2, 2, 5), (2, 2, 2, 5), (4, 3, 3, 7), (5, 3, 3, 7)])
+def test_optimum_is_no_worse_than_the_feasible_reference(seed, m, g, p):
+    """The reference trajectory (its nodes and the inputs that produce them)
+    satisfies every row, so the optimum's objective cannot exceed its own --
+    a check of optimality that does not use the solver's multipliers."""
+    inst = instance(seed, m=m, g=g, p=p)
+    r = solve(inst)
+    assert r["status"] == mpc.OK
+    qp = r["qp"]
+    H = inst["ref"].shape[0] - 1
+    A, B = mpc.discretize(m, g, inst["dt"])
+    u_ref = np.array([np.linalg.lstsq(B, inst["ref"][k + 1] - A @ inst["ref"][k], rcond=None)[0] for k in range(H)])
+    z_ref = np.concatenate([inst["ref"][1:].reshape(-1), u_ref.reshape(-1)])
+    assert np.abs(qp["Aeq"] @ z_ref - qp["beq"]).max() < 1e-10
+    assert (qp["Ain"] @ z_ref - qp["bin"]).max() <= 1e-12
+    assert r["obj"] <= objective(inst, inst["ref"], u_ref) + 1e-12
+
