@@ -150,6 +150,21 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def lane_peaks(dev):
+    """FP32 lane-op rates measured on this device (plan_measure_lane_rate) and the nominal figure."""
+    import torch
+    from paper_2411_13507_gb300 import plan as P
+    peaks, src = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    r = {"sms": sms, "addmax": P.measure_lane_rate(0)["lane_ops_per_s"], "fma": P.measure_lane_rate(1)["lane_ops_per_s"],
+         "nominal": sms * 128 * sm_max * 1e6}
+    r["note"] = (f"measured: FP32 add + |.|-max register chains on all {sms} SMs (plan_measure_lane_rate) "
+                 f"{r['addmax'] / 1e12:.2f} T/s; FMA chains {r['fma'] / 1e12:.2f} T/s; nominal {sms} SMs x 128 lanes "
+                 f"x {sm_max:.0f} MHz ({src} clock) = {r['nominal'] / 1e12:.2f} T/s")
+    return r
+
+
 def pair_kernel_counters():
     """DRAM traffic of the pair kernel from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
@@ -442,9 +457,8 @@ def run_cut_form(args, stream, flush, dev):
     # the mask bit per test, about 4m FP32 lane operations
     m, NP = prob.model.m, prob.model.degree + 1
     ex_ops = info["cut_tests"] * (4 * m)
-    peaks, peak_src = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = 152 * 128 * sm_max * 1e6 / 1e12
+    lanes = lane_peaks(dev)
+    alu_peak = lanes["addmax"] / 1e12
     achieved = ex_ops / (scan_ms / 1e3) / 1e12
     dense_ops = tests * float(np.mean(np.diff(obs.off))) * NP * (m + 2)
     return {"metric": "keep-out cut decisions/sec ((edge, T) x obstacle), 2-D, 5000 states, 500 obstacles",
@@ -466,7 +480,7 @@ def run_cut_form(args, stream, flush, dev):
                          "work_model": "executed FP32 lane ops: (edge, T, obstacle) box tests x 4m",
                          "dense": {"ops_per_launch": dense_ops, "frac": dense_ops / (scan_ms / 1e3) / 1e12 / alu_peak,
                                    "note": "every control point against every facet of every obstacle, (m+2) ops each"},
-                         "peak_note": f"FP32 lanes 152 SMs x 128 x {sm_max:.0f} MHz ({peak_src} clock)"},
+                         "peak_note": lanes["note"]},
             "e2e": {"value": tests * 1e3 / statistics.mean(e2e), "unit": "tests/s", "h2d_bytes_per_step": bi,
                     "d2h_bytes_per_step": bo, "ms_per_step": statistics.mean(e2e)},
             "cpu_baseline": cpu}
@@ -864,6 +878,7 @@ def main():
             pl.set_timing(False)
             untimed_until(lambda: clk.count() >= mark + 2, 5.0)
         clocks = clk.summary(since=mark)
+        lanes = lane_peaks(dev)
         build_ms = [a.elapsed_time(b) for a, b, _ in evs]
         search_ms = [b.elapsed_time(c) for _, b, c in evs]
         step_ms = [a.elapsed_time(c) for a, _, c in evs]
@@ -914,7 +929,6 @@ def main():
     # work per check = the dense separable form: every reach row (add, |.|,
     # compare, min), every free row (add, max), every cost segment (n adds, n
     # FMAs, sqrt, add); times the checks of one launch.
-    peaks, peak_src = measured_peaks()
     g, p, m = prob.model.gamma, prob.model.degree, prob.model.m
     n = m * g
     rax = sum(p - k + 1 for k in range(1, g + 1))
@@ -930,8 +944,8 @@ def main():
               + 2 * (m * rax + (p - 1) * rows_mean) * screened + p * (2 * n + 2) * int(info["feasible"]))
     pair_ms = tm["pair_ms"] / max(1, tm["pair_launches"])
     achieved = ops_per_launch / (pair_ms / 1e3) / 1e12
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = 152 * 128 * sm_max * 1e6 / 1e12
+    alu_peak = lanes["addmax"] / 1e12       # measured on this device (add + |.|-max chains)
+    ex_frac = ex_ops / (pair_ms / 1e3) / 1e12 / alu_peak
     counters, src_sha = pair_kernel_counters()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -945,13 +959,15 @@ def main():
         "gpu_launches": int(tm["launches"]),
         "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TOP/s",
-                     "frac": achieved / alu_peak,
+                     "frac": achieved / alu_peak, "hw_frac": ex_frac,
                      "traffic": counters.get("dram_bytes_per_launch") if counters else None,
                      "kernel": PAIR_KERNEL.get(args.pipeline, PAIR_KERNEL[0]), "kernel_ms": pair_ms,
                      "ops_per_check": ops_per_check, "ops_per_launch": ops_per_launch,
                      "work_model": "dense separable form per check (all reach, free and cost rows)",
-                     "peak_note": f"FP32 lanes 152 SMs x 128 x {sm_max:.0f} MHz (unit counts and max clock; {peak_src} clock)",
-                     "executed": {"ops_per_launch": ex_ops, "frac": ex_ops / (pair_ms / 1e3) / 1e12 / alu_peak,
+                     "peak_note": lanes["note"],
+                     "hw_frac_note": "executed lane-ops of the pair kernel / measured peak (hardware utilisation); "
+                                     "frac uses the dense separable work model",
+                     "executed": {"ops_per_launch": ex_ops, "frac": ex_frac,
                                   "screened_checks": screened,
                                   "note": "ops the screened kernel performs: screen rows of every pair and duration, "
                                           "all reach and free rows of the screened checks, costs of feasible ones"},

@@ -487,18 +487,27 @@ int plan_search_batched(plan_ctx* ctx);
  * allocate device memory while they plan.  The paper has no counterpart; it is
  * a deployment variant.  Typical callers: a replanning loop with a hard
  * per-tick deadline (cudaMalloc/cudaFree may block, and cudaFree synchronises
- * the whole device), code issuing work while a stream is being captured into
- * a CUDA graph, and processes whose device memory belongs to a pool allocator.
+ * the whole device), and processes whose device memory belongs to a pool
+ * allocator that the planner may not draw from.
  *
  * No context is needed and nothing is allocated: all scratch (status word,
  * grid-barrier counters, distance / predecessor / frontier arrays) lives in
- * one static device array sized for N <= 65536 vertices (about 1.4 MB, held by
- * every GPU that loads the library until the process exits).  The first call
- * on a device looks up that array's device address (cudaGetSymbolAddress) and
- * caches it; make that first call before any stream capture.  Every call on a
- * device shares the array and it keeps the last call's contents (the call
- * clears the status and barrier words itself), so calls whose work overlaps on
+ * one static device array sized for N <= 65536 vertices (about 1.9 MB:
+ * 65536 x 28 bytes of per-vertex arrays plus 32 KB of per-block candidates
+ * and the status block), held by every GPU that loads the library until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress, with that device current) and caches it for
+ * the life of the process; make that first call before any stream capture.
+ * The address belongs to the device's primary context (the CUDA runtime's):
+ * after cudaDeviceReset, or with another context current, the cached address
+ * is no longer valid, so do not call this entry point again in that process.
+ * Every call on a device shares the array and it keeps the last call's
+ * contents (the call clears the status and barrier words itself, and the
+ * kernel initialises the per-vertex arrays), so calls whose work overlaps on
  * the GPU race: issue them on one stream or order them with events.
+ * The device loops have fixed bounds: at most N+1 frontier sweeps (the
+ * Bellman-Ford bound) and 2^24 polls of a grid barrier; when one runs out the
+ * status is TIMEOUT (plan_set_search_limits does not apply here).
  *
  *   m, gamma     model (positions are the first m entries of each state)
  *   input        PLAN_IN_F64 / PLAN_IN_F32 storage of states
@@ -546,6 +555,18 @@ int plan_timing(plan_ctx* ctx, double* pair_ms, int64_t* pair_launches, double* 
  * summed milliseconds of the first (screening) pass and of whole calls, and
  * the number of calls, since the last reset (synchronises the stream). */
 int plan_cut_timing(plan_ctx* ctx, double* scan_ms, double* cut_ms, int64_t* cuts, int reset);
+
+/* Measurement helper (no counterpart in the paper): the sustained issue rate
+ * of the FP32 lane operations that make up the pair kernels' work, measured
+ * on the current device by a full-occupancy kernel of independent register
+ * chains timed with CUDA events (two launches; the second is timed).
+ *   mix   0: one add and one max of an absolute value per step (a reach or
+ *         free row of one pair); 1: one fused multiply-add per step
+ *   iters chain steps per thread, 1 .. 2^24 (about 2^16 runs for milliseconds)
+ *   lane_ops_per_s  host out: lane operations per second (an FMA counts one)
+ *   ms    host out (may be NULL): duration of the timed launch
+ * Synchronous; INVALID_ARG for bad arguments, CUDA if a launch fails. */
+int plan_measure_lane_rate(int mix, int iters, double* lane_ops_per_s, double* ms);
 
 const char* plan_status_string(int status);
 const char* plan_last_error(plan_ctx* ctx);

@@ -22,7 +22,7 @@ OBJ_DIR = os.path.join(OUT_DIR, "obj")
 LIB = os.path.join(OUT_DIR, "libplan.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["plan_api.cu", "plan_build.cu", "plan_search.cu", "plan_refine.cu", "plan_cut.cu", "plan_planes.cu", "plan_mpc.cu",
-           "plan_tables.cpp"]
+           "plan_probe.cu", "plan_tables.cpp"]
 
 
 def nvcc() -> str:

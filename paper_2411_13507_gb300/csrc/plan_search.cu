@@ -1404,12 +1404,11 @@ int launch_search(const SearchParams& P, void* stream, int num_sms, int* launche
 //
 // Some callers cannot allocate device memory when they plan: a replanning
 // loop that must answer within a few milliseconds (cudaMalloc and cudaFree
-// can block and cudaFree synchronises the device), code that runs while a
-// stream is being captured into a CUDA graph, or a process whose device
+// can block and cudaFree synchronises the device), or a process whose device
 // memory is owned entirely by a pool allocator.  This variant of the search
 // keeps all of its scratch -- the status word and grid-barrier counters, the
 // distance, predecessor and last-relaxed arrays -- in one file-scope __device__
-// array sized for NOALLOC_MAX_N vertices (about 1.8 MB), which every GPU that
+// array sized for NOALLOC_MAX_N vertices (about 1.9 MB), which every GPU that
 // loads the library holds until the process exits.  The caller passes only
 // inputs and outputs.
 // ---------------------------------------------------------------------------

@@ -93,7 +93,8 @@ EXPORTS = ["plan_create", "plan_destroy", "plan_build_edges", "plan_search", "pl
            "plan_set_search_limits", "plan_refine", "plan_prepare_batched", "plan_build_edges_batched",
            "plan_set_tile", "plan_autotune", "plan_prepare_search_batched", "plan_search_batched",
            "plan_search_noalloc", "plan_cut_edges", "plan_cut_timing", "plan_search_at", "plan_search_to", "plan_obstacle_planes", "plan_nearest_planes", "plan_mpc_qp",
-           "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_status_string", "plan_last_error", "plan_version"]
+           "plan_set_accounting", "plan_set_timing", "plan_timing", "plan_measure_lane_rate", "plan_status_string",
+           "plan_last_error", "plan_version"]
 
 
 def lib_path() -> str:
@@ -164,6 +165,8 @@ def load(build_if_stale: bool = True):
     lib.plan_set_timing.restype = i32
     lib.plan_timing.argtypes = [vp, dp, ctypes.POINTER(i64), dp, ctypes.POINTER(i64), ctypes.POINTER(i64), i32]
     lib.plan_timing.restype = i32
+    lib.plan_measure_lane_rate.argtypes = [i32, i32, dp, dp]
+    lib.plan_measure_lane_rate.restype = i32
     lib.plan_status_string.argtypes = [i32]
     lib.plan_status_string.restype = ctypes.c_char_p
     lib.plan_last_error.argtypes = [vp]
@@ -205,6 +208,17 @@ def model_tables(gamma: int, degree: int, T: Sequence[float], interior: str = "e
     if rc != 0:
         raise PlanError(rc)
     return {"D": D, "H": H, "C": C}
+
+
+def measure_lane_rate(mix: int = 0, iters: int = 1 << 16) -> dict:
+    """Sustained FP32 lane operations per second on the current device
+    (mix 0: add + |.|-max, the reach/free row pattern; 1: fused multiply-add)."""
+    lib = load()
+    r, ms = ctypes.c_double(), ctypes.c_double()
+    rc = lib.plan_measure_lane_rate(int(mix), int(iters), ctypes.byref(r), ctypes.byref(ms))
+    if rc != 0:
+        raise PlanError(rc, "plan_measure_lane_rate")
+    return {"lane_ops_per_s": r.value, "ms": ms.value}
 
 
 def search_noalloc(m: int, gamma: int, input: str, w_f64: bool, dp, graph, start_pos, goal_pos, out: dict,
@@ -713,7 +727,12 @@ class Replanner:
     The obstacle arrays have a fixed capacity (n_max obstacles, rows_max >= 2m
     rows each); a tick with fewer obstacles fills the other slots with unit
     boxes at -1e12 in every axis, which the certified bounding boxes separate
-    from every curve."""
+    from every curve.
+
+    One tick is in flight at a time: the pinned staging buffers feed the
+    tick's host-to-device copies, so a tick_async issued before the previous
+    tick has finished first waits for it (its result buffers then hold the
+    newer tick's path once that one completes)."""
 
     def __init__(self, planner: "Planner", dp: DeviceProblem, graph: Graph, n_max: int, rows_max: int,
                  path_cap: Optional[int] = None, warm: bool = True):
@@ -744,8 +763,13 @@ class Replanner:
         self.h_len = torch.zeros(1, dtype=torch.int32).pin_memory()
         self.h_cost = torch.zeros(1, dtype=torch.float64).pin_memory()
         self.cg = None
+        self._done = torch.cuda.Event()
+        self._inflight = False
 
     def _stage(self, obstacles, start_pos, goal_pos) -> None:
+        if self._inflight:           # the previous tick's copies still read the staging buffers
+            self._done.synchronize()
+            self._inflight = False
         off = np.asarray(obstacles.off, dtype=np.int64)
         n = off.shape[0] - 1
         if n > self.n_max or (n > 0 and int(np.max(np.diff(off))) > self.rows_max):
@@ -802,6 +826,8 @@ class Replanner:
         self._stage(obstacles, start_pos, goal_pos)
         with torch.cuda.stream(self.pl.stream):
             self.cg.replay()
+            self._done.record(self.pl.stream)
+        self._inflight = True
 
     def result(self) -> dict:
         """Waits for the tick; status, path (host list) and cost."""

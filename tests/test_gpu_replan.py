@@ -199,3 +199,23 @@ def test_warm_start_after_a_stopped_call_on_the_cooperative_kernel(N, width):
         c = _search_to(pl2, dp, out2, s, goal, warm=False)
         assert r["status"] == c["status"] and r["path"] == c["path"] and r["cost"] == c["cost"]
     ctx.__exit__(None, None, None)
+
+
+def test_back_to_back_ticks_keep_one_in_flight():
+    """Two tick_async calls without result() in between: the second waits for
+    the first tick's copies before it rewrites the staging buffers, and the
+    result equals a direct tick on the second obstacles."""
+    prob, obs = synth.keepout_2d(5, N=500, n_obst=50)
+    pl, dp, g, ctx = setup(prob)
+    pl2 = P.Planner.for_problem(prob, stream=pl.stream)
+    rp = P.Replanner(pl, dp, g, n_max=60, rows_max=8, warm=False)
+    rp.capture(obs, prob.start_pos, prob.goal_pos)
+    rng = np.random.default_rng(9)
+    obs2 = moved(obs, rng.normal(0.0, 0.05, size=(obs.n, 2)))
+    rp.tick_async(obs, prob.start_pos, prob.goal_pos)
+    rp.tick_async(obs2, prob.start_pos, prob.goal_pos)
+    r = rp.result()
+    d = direct(pl2, dp, g, obs2, prob.start_pos, prob.goal_pos)
+    assert r["status"] == d["status"] and r["path"] == d["path"] and r["edges"] == d["edges"]
+    assert r["cost"] == d["cost"]
+    ctx.__exit__(None, None, None)
