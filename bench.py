@@ -12,6 +12,10 @@ A step = plan_build_edges + plan_search on HBM-resident inputs; each step is
 timed with CUDA events on the planner's stream after an L2 flush (a 256 MB
 write) outside the events.  N > 1 (torchrun): every rank runs its own query
 (seed + rank; weak scaling, no data-path collective), times are max-reduced.
+With --shard rows the ranks instead split one query's source rows
+(plan_build_edges_shard), all-gather the CSR pieces over NCCL and each
+searches the whole graph (strong scaling; the build time includes the
+exchange).
 
 --impl reference times the FP64 CPU oracle (the plain definition) on the
 host cores on a bounded sample of the same workload.
@@ -58,6 +62,10 @@ def parse():
                          "the MPC QP) of a batch of problems in the keep-out scene")
     ap.add_argument("--mpc-batch", type=int, default=1024, help="MPC problems per step (form mpc)")
     ap.add_argument("--queries", type=int, default=256)
+    ap.add_argument("--shard", default="queries", choices=["queries", "rows"],
+                    help="N > 1: queries -- every rank builds and searches its own query (replicas, weak scaling); "
+                         "rows -- the ranks split one query's source rows (plan_build_edges_shard), exchange the CSR "
+                         "pieces (all-gather-v over NCCL) and each searches the whole graph (strong scaling)")
     ap.add_argument("--pipeline", type=int, default=-1,
                     help="FP32 pair kernel of the plain line: 0 screened, 1 warp-specialised, 2 unscreened "
                          "(-1: the library default)")
@@ -809,8 +817,9 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
+    shard_rows = args.shard == "rows" and world > 1
     # CPU baseline first (before heavy GPU work; threads, no fork)
-    prob = workload(args.seed + rank)
+    prob = workload(args.seed if shard_rows else args.seed + rank)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(prob, rows=args.cpu_sample_rows)
@@ -821,24 +830,51 @@ def main():
         if args.pipeline >= 0:
             pl.set_tile(0, 0, 0, args.pipeline)
         dp = P.to_device(prob, input="f32")
-        graph = pl.build_edges(dp)           # sizes scratch and the output CSR
-        sres = pl.search(dp, graph)
+        from paper_2411_13507_gb300 import shard
+        if shard_rows:
+            graph = pl.build_edges_shard(dp, rank, world)   # sizes scratch and this rank's output CSR
+        else:
+            graph = pl.build_edges(dp)                      # sizes scratch and the output CSR
         info = pl.info()
+
+        def exchanged():
+            """The whole graph from every rank's rows (all-gather-v over NCCL)."""
+            st = pl.wait()
+            assert st == P.PLAN_OK, f"shard build status {st}"
+            i = pl.last_info
+            g = shard.exchange(graph.row_off, graph.col, graph.w, graph.mask, graph.tidx, int(graph.count.item()),
+                               int(i.shard_lo), int(i.shard_hi), dp.N, dist)
+            E = g["count"]
+            return P.Graph(dp.N, g["row_off"], g["col"], g["w"], g["tidx"], g["mask"],
+                           torch.tensor([E], dtype=torch.int64, device=dev), max(E, 1))
+
+        sgraph = exchanged() if shard_rows else graph
+        sres = pl.search(dp, sgraph)
         cap = graph.cap
         # algorithmic work of this query (untimed counting launch)
         pl.set_accounting(True)
-        pl.build_edges(dp, graph=graph)
+        if shard_rows:
+            pl.build_edges_shard(dp, rank, world, graph=graph)
+        else:
+            pl.build_edges(dp, graph=graph)
         work = pl.info()
         pl.set_accounting(False)
         sbuf = pl.alloc_search(dp.N)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
         def step(evs):
+            """build (+ exchange of the row shards) | search; returns the graph searched"""
             evs[0].record(stream)
-            pl.build_edges_async(dp, graph)
+            if shard_rows:
+                pl.build_edges_shard_async(dp, graph, rank, world)
+                g = exchanged()
+            else:
+                pl.build_edges_async(dp, graph)
+                g = graph
             evs[1].record(stream)
-            pl.search_async(dp, graph, dp.start_pos, dp.goal_pos, sbuf)
+            pl.search_async(dp, g, dp.start_pos, dp.goal_pos, sbuf)
             evs[2].record(stream)
+            return g
 
         for _ in range(args.warmup):
             flush.fill_(1.0)
@@ -901,11 +937,16 @@ def main():
             dp.poly_off.copy_(h_off, non_blocking=True)
             dp.A.copy_(h_A, non_blocking=True)
             dp.b.copy_(h_b, non_blocking=True)
-            pl.build_edges_async(dp, graph)
-            pl.search_async(dp, graph, dp.start_pos, dp.goal_pos, sbuf)
+            if shard_rows:
+                pl.build_edges_shard_async(dp, graph, rank, world)
+                g = exchanged()
+            else:
+                pl.build_edges_async(dp, graph)
+                g = graph
+            pl.search_async(dp, g, dp.start_pos, dp.goal_pos, sbuf)
             h_path.copy_(sbuf["path"], non_blocking=True)
             h_cost[:1].copy_(sbuf["cost"], non_blocking=True)
-            h_E.copy_(graph.count, non_blocking=True)
+            h_E.copy_(g.count, non_blocking=True)
             e1.record(stream)
             st = pl.wait()
             assert st == P.PLAN_OK
@@ -950,9 +991,14 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_step / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config(prob, {"checks_per_query": checks, "candidates": int(info["candidates"]),
-                                "edges": int(info["edges"]), "rechecks": int(info["rechecks"])}),
+        "scaling": "strong" if shard_rows else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config(prob, {"checks_per_query": int(checks_all) if shard_rows else checks,
+                                "candidates": int(info["candidates"]),
+                                "edges": int(info["edges"]), "rechecks": int(info["rechecks"]),
+                                **({"parallelism": f"one query, source rows split over {world} GPUs "
+                                                   "(plan_build_edges_shard), CSR pieces all-gathered over NCCL, "
+                                                   "search replicated; build_ms includes the exchange"}
+                                   if shard_rows else {})}),
         "build_ms_per_query": 1e3 * t_build / args.steps,
         "search_ms_per_query": 1e3 * t_search / args.steps,
         "path_len": L,

@@ -138,6 +138,9 @@ typedef struct {
      * error bands), matrix games solved in FP32; entries of the FP64 pass;
      * FP64 games that no certificate decided (|delta*| at rounding level) */
     int64_t cut_units, cut_tests, cut_box, cut_near, cut_step1, cut_step2, cut_games, cut_lp64, cut_ties;
+    /* source rows [shard_lo, shard_hi) of the last plan_build_edges_shard
+     * (0, N for a whole build; of the first query for a batch) */
+    int32_t shard_lo, shard_hi;
 } plan_info;
 
 /* Create a context bound to the current CUDA device and the given stream
@@ -173,6 +176,31 @@ void plan_destroy(plan_ctx* ctx);
 int plan_build_edges(plan_ctx* ctx, int N, const void* states, int nT, const double* T, int K,
                      const int32_t* poly_off, int max_rows, const void* A, const void* b,
                      const plan_edges* out);
+
+/*
+ * One shard of plan_build_edges, for a build split over several GPUs
+ * (Algorithm 1's buildGraph at a size one GPU would split): the source rows
+ * are cut into nshard contiguous ranges of equal work, the work of row i
+ * being the number of (i, j) pair slots it has in its polytopes (the sum of
+ * the member counts of the polytopes holding state i; every duration costs
+ * the same).  The cut points are computed on the device from the membership,
+ * identically by every rank, so no exchange precedes the build.  This call
+ * computes every candidate pair (i, j) of the rows i of shard `shard` over
+ * every shared polytope and duration -- all polytopes, all columns j -- so its
+ * rows are final: they equal the rows of plan_build_edges bit for bit.
+ *   shard, nshard  0 <= shard < nshard <= 1024
+ *   out            caller-owned CSR over all N rows: row_off [N+1] is written
+ *                  for every row (rows outside the shard are empty), col / w /
+ *                  tidx / mask hold the shard's edges only, count = their number
+ * The rows of shard r precede those of shard r+1, so the whole graph is the
+ * concatenation of the shards' edges in shard order, with row_off the sum of
+ * the shards' row_off arrays.  plan_info.shard_lo / shard_hi report the rows;
+ * candidates, checks and feasible count the shard's rows only.  Everything
+ * else (arguments, errors, scratch growth) as plan_build_edges.
+ */
+int plan_build_edges_shard(plan_ctx* ctx, int N, const void* states, int nT, const double* T, int K,
+                           const int32_t* poly_off, int max_rows, const void* A, const void* b, int shard,
+                           int nshard, const plan_edges* out);
 
 /* One query of a batched edge build (same fields as plan_build_edges). */
 typedef struct {

@@ -47,6 +47,7 @@ struct plan_ctx {
     long long* d_qSlot = nullptr;
     long long* d_qItem = nullptr;
     long long* d_qMem = nullptr;
+    int* d_rowRange = nullptr;
     long long capQ = -1;
     char* h_stage = nullptr;
     size_t stage_cap = 0;
@@ -83,6 +84,7 @@ struct plan_ctx {
     int* itemOff = nullptr;
     int* ntile = nullptr;
     int* tsize = nullptr;
+    int* iRange = nullptr;
     int* memOff = nullptr;
     int* rowCount = nullptr;
     // device-sized scratch
@@ -294,7 +296,7 @@ int ensure_host_sized(plan_ctx* c, long long mask, long long list, long long k1,
     if (k1 > c->capK) {
         if (!dalloc(c, &c->counts, k1) || !dalloc(c, &c->centers, 4 * k1) || !dalloc(c, &c->resOff, k1) ||
             !dalloc(c, &c->itemOff, k1) || !dalloc(c, &c->ntile, k1) || !dalloc(c, &c->tsize, k1) ||
-            !dalloc(c, &c->memOff, k1))
+            !dalloc(c, &c->iRange, k1) || !dalloc(c, &c->memOff, k1))
             return PLAN_ERR_NO_MEMORY;
         c->capK = k1;
     }
@@ -415,9 +417,9 @@ void plan_destroy(plan_ctx* c) {
     if (!c) return;
     if (c->stream || c->d_info) cudaStreamSynchronize(c->stream);
     void* dev[] = {c->d_tab64, c->d_tab32, c->d_info, c->memMask, c->counts, c->members, c->localIdx, c->segKL, c->centers,
-                   c->blim64, c->A32, c->blim32, c->bc32, c->resOff, c->itemOff, c->ntile, c->tsize, c->rowCount,
+                   c->blim64, c->A32, c->blim32, c->bc32, c->resOff, c->itemOff, c->ntile, c->tsize, c->iRange, c->rowCount,
                    c->resBits, c->resKey, c->emitPre, c->recheck, c->sdist, c->sbest, c->spred, c->sfront, c->slast, c->snear,
-                   c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem, c->d_qMem, c->d_sqd, c->memOff,
+                   c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem, c->d_qMem, c->d_rowRange, c->d_sqd, c->memOff,
                    c->d_cut64, c->d_cut32, c->cut_src, c->cut_hit, c->cut_pos, c->cut_chunk, c->cut_orow,
                    c->cut_ocount, c->cut_list32, c->cut_okb, c->cut_obox, c->pl_orow, c->pl_face, c->pl_edge, c->pl_nedge, c->pl_ocount, c->pl_keys, c->pl_near, c->pl_ub, c->d_mpc, c->d_mpcJ, c->g_d, c->g_succ, c->g_wsucc, c->g_anc, c->g_prev};
     for (void* p : dev)
@@ -472,7 +474,7 @@ int check_query(plan_ctx* c, const plan_query& q) {
 }
 
 // Host work of a batch: validation, offsets, tables, scratch, descriptor upload.
-int prepare(plan_ctx* c, int Q, const plan_query* qs, int max_rows) {
+int prepare(plan_ctx* c, int Q, const plan_query* qs, int max_rows, int shard = 0, int nshard = 1) {
     if (!model_supported(c->model.m, c->model.gamma, c->model.degree))
         return fail(c, PLAN_ERR_UNSUPPORTED, "edge build not compiled for this (m, gamma, p)");
     if (Q < 1 || Q > 65535 || !qs) return fail(c, PLAN_ERR_INVALID_ARG, "need 1..65535 queries");
@@ -514,6 +516,8 @@ int prepare(plan_ctx* c, int Q, const plan_query* qs, int max_rows) {
         d.mask = in.out.mask;
         d.cap = in.out.cap;
         d.count = in.out.count;
+        d.shard = shard;
+        d.nshard = nshard;
         Tall.insert(Tall.end(), in.T, in.T + in.nT);
         pfx[0 * (Q + 1) + q] = mask;
         pfx[1 * (Q + 1) + q] = poly;
@@ -540,7 +544,7 @@ int prepare(plan_ctx* c, int Q, const plan_query* qs, int max_rows) {
     if (Q > c->capQ) {
         if (c->stage_live) cudaEventSynchronize(c->stage_ev);
         if (!dalloc(c, &c->d_qd, Q) || !dalloc(c, &c->d_pfx, 4LL * (Q + 1)) || !dalloc(c, &c->d_qSlot, Q + 1) ||
-            !dalloc(c, &c->d_qItem, Q + 1) || !dalloc(c, &c->d_qMem, Q + 1))
+            !dalloc(c, &c->d_qItem, Q + 1) || !dalloc(c, &c->d_qMem, Q + 1) || !dalloc(c, &c->d_rowRange, 2LL * Q))
             return PLAN_ERR_NO_MEMORY;
         c->capQ = Q;
         c->last_stage.clear();
@@ -648,6 +652,8 @@ int issue(plan_ctx* c) {
     P.itemOff = c->itemOff;
     P.ntile = c->ntile;
     P.tsize = c->tsize;
+    P.iRange = c->iRange;
+    P.rowRange = c->d_rowRange;
     P.memOff = c->memOff;
     P.resBits = c->resBits;
     P.resKey = c->resKey;
@@ -693,6 +699,28 @@ int plan_build_edges(plan_ctx* c, int N, const void* states, int nT, const doubl
     q.b = b;
     q.out = *out;
     int rc = prepare(c, 1, &q, max_rows);
+    if (rc != PLAN_OK) return rc;
+    return issue(c);
+}
+
+int plan_build_edges_shard(plan_ctx* c, int N, const void* states, int nT, const double* T, int K,
+                           const int32_t* poly_off, int max_rows, const void* A, const void* b, int shard, int nshard,
+                           const plan_edges* out) {
+    if (!c) return PLAN_ERR_INVALID_ARG;
+    if (!out) return fail(c, PLAN_ERR_INVALID_ARG, "bad output CSR");
+    if (nshard < 1 || nshard > 1024 || shard < 0 || shard >= nshard)
+        return fail(c, PLAN_ERR_INVALID_ARG, "need 0 <= shard < nshard <= 1024");
+    plan_query q;
+    q.N = N;
+    q.states = states;
+    q.nT = nT;
+    q.T = T;
+    q.K = K;
+    q.poly_off = poly_off;
+    q.A = A;
+    q.b = b;
+    q.out = *out;
+    int rc = prepare(c, 1, &q, max_rows, shard, nshard);
     if (rc != PLAN_OK) return rc;
     return issue(c);
 }
@@ -1531,6 +1559,8 @@ int plan_wait(plan_ctx* c, plan_info* info) {
         info->cut_games = (int64_t)d.cut_games;
         info->cut_lp64 = (int64_t)d.cut_lp64;
         info->cut_ties = (int64_t)d.cut_ties;
+        info->shard_lo = d.shard_lo;
+        info->shard_hi = d.shard_hi;
     }
     return d.status;
 }

@@ -116,6 +116,17 @@ constexpr int MULTI_BIT = (int)0x80000000u;
 DEVI int mem_id(int v) { return v & 0x7fffffff; }
 DEVI bool mem_multi(int v) { return v < 0; }
 
+// First position in an ascending member list whose state id is >= j.
+DEVI int lower_bound_members(const int* mem, int n, int j) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (mem_id(mem[mid]) < j) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // Largest q with pfx[q] <= x (pfx ascending, pfx[Q] > x): query of a global index.
 DEVI int find_q(const long long* pfx, int Q, long long x) {
     int lo = 0, hi = Q;
@@ -326,24 +337,101 @@ DEVI T block_exclusive_scan(T v, T* warpbuf, T* total) {
     return r;
 }
 
-// One CTA per query: balanced tiles and slot offsets of its polytopes.
+// Source-row range of a query's shard: the rows are cut into nshard
+// contiguous ranges of equal work, the work of row i being its pair slots
+// sum_{k holds i} n_k.  With S_i the work of rows < i and W the total, shard
+// r starts at the number of rows with S_i * nshard < W * r (S is
+// non-decreasing, so those rows form a prefix); the last shard ends at N.
+// Every rank computes the same cut points from the same membership.  One CTA
+// per query; every thread must call it.
+DEVI void shard_rows(const BuildParams& P, const QueryDesc& Q, int* s_counts, long long* wb, long long* tot,
+                     int& lo, int& hi) {
+    lo = 0;
+    hi = Q.N;
+    if (Q.nshard <= 1) return;
+    for (int k = threadIdx.x; k < Q.K; k += blockDim.x) s_counts[k] = P.counts[Q.kOff + k];
+    __syncthreads();
+    const uint32_t* mask = P.memMask + Q.maskOff;
+    auto row_work = [&](int i) -> long long {
+        long long w = 0;
+        if (i < Q.N)
+            for (int wd = 0; wd < Q.W; ++wd) {
+                uint32_t x = mask[(long long)i * Q.W + wd];
+                while (x) {
+                    w += s_counts[wd * 32 + __ffs(x) - 1];
+                    x &= x - 1u;
+                }
+            }
+        return w;
+    };
+    long long W = 0;
+    for (int i0 = 0; i0 < Q.N; i0 += blockDim.x) {
+        block_exclusive_scan<long long>(row_work(i0 + threadIdx.x), wb, tot);
+        W += *tot;
+        __syncthreads();
+    }
+    const long long tlo = W * Q.shard, thi = W * (Q.shard + 1);
+    long long carry = 0, nlo = 0, nhi = 0;
+    for (int i0 = 0; i0 < Q.N; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const long long ex = block_exclusive_scan<long long>(row_work(i), wb, tot);
+        const long long S = carry + ex;
+        const int blo = (i < Q.N && S * Q.nshard < tlo) ? 1 : 0;
+        const int bhi = (i < Q.N && S * Q.nshard < thi) ? 1 : 0;
+        carry += *tot;
+        __syncthreads();
+        block_exclusive_scan<long long>(blo, wb, tot);
+        nlo += *tot;
+        __syncthreads();
+        block_exclusive_scan<long long>(bhi, wb, tot);
+        nhi += *tot;
+        __syncthreads();
+    }
+    lo = (int)nlo;
+    hi = Q.shard + 1 == Q.nshard ? Q.N : (int)nhi;
+}
+
+// One CTA per query: the shard's row range, then balanced tiles and slot
+// offsets of its polytopes.  Every polytope keeps its full n_k x n_k slot
+// block; the i-tiles cover only the members whose ids lie in the row range
+// (a contiguous part of the ascending member list), the j-tiles all members.
 __global__ void __launch_bounds__(1024) k_setup(BuildParams P) {
     __shared__ long long wb[32];
     __shared__ long long tot;
+    __shared__ int s_counts[1024];
     const int q = blockIdx.x;
     const QueryDesc& Q = P.qd[q];
     const int tile = P.tile;
+    int rlo, rhi;
+    shard_rows(P, Q, s_counts, wb, &tot, rlo, rhi);
+    if (threadIdx.x == 0) {
+        P.rowRange[2 * q] = rlo;
+        P.rowRange[2 * q + 1] = rhi;
+        if (q == 0) {
+            P.info->shard_lo = rlo;
+            P.info->shard_hi = rhi;
+        }
+    }
     long long slots = 0, items = 0, mem = 0;
     long long carry_s = 0, carry_i = 0, carry_m = 0;
     for (int k0 = 0; k0 < Q.K; k0 += blockDim.x) {
         const int k = k0 + threadIdx.x;
         const long long nk = (k < Q.K) ? P.counts[Q.kOff + k] : 0;
         if (nk > NK_MAX) set_status(P.info, PLAN_ERR_UNSUPPORTED, DET_NK);
+        int a = 0, b = (int)nk;
+        if (Q.nshard > 1 && k < Q.K && nk <= NK_MAX) {
+            const int* ml = P.members + Q.listOff + (long long)k * Q.N;
+            a = lower_bound_members(ml, (int)nk, rlo);
+            b = lower_bound_members(ml, (int)nk, rhi);
+        }
         const int nt = nk > 0 ? (int)((nk + tile - 1) / tile) : 0;
         const int ts = nt ? (int)((nk + nt - 1) / nt) : 0;
+        const int ni = b - a;
+        const int nti = ni > 0 ? (ni + tile - 1) / tile : 0;
+        const int tsi = nti ? (ni + nti - 1) / nti : 0;
         const long long so = block_exclusive_scan<long long>(nk * nk, wb, &tot);
         slots = tot;
-        const long long io = block_exclusive_scan<long long>((long long)nt * nt, wb, &tot);
+        const long long io = block_exclusive_scan<long long>((long long)nti * nt, wb, &tot);
         items = tot;
         const long long mo = block_exclusive_scan<long long>(nk, wb, &tot);
         mem = tot;
@@ -351,8 +439,9 @@ __global__ void __launch_bounds__(1024) k_setup(BuildParams P) {
             P.memOff[Q.kOff + k] = (int)(carry_m + mo);
             P.resOff[Q.kOff + k] = carry_s + so;
             P.itemOff[Q.kOff + k] = (int)(carry_i + io);
-            P.ntile[Q.kOff + k] = nt;
-            P.tsize[Q.kOff + k] = ts;
+            P.ntile[Q.kOff + k] = nt | (nti << 16);
+            P.tsize[Q.kOff + k] = ts | (tsi << 16);
+            P.iRange[Q.kOff + k] = a | (b << 16);
         }
         carry_s += slots;
         carry_i += items;
@@ -427,12 +516,16 @@ DEVI Item item_decode(const BuildParams& P, long long item) {
         else hi = mid;
     }
     it.k = lo;
-    const int loc = local - io[lo], nt = P.ntile[Q.kOff + lo], ts = P.tsize[Q.kOff + lo];
+    const int loc = local - io[lo];
+    const int nt = P.ntile[Q.kOff + lo] & 0xffff, tsp = P.tsize[Q.kOff + lo];
+    const int ts = tsp & 0xffff, tsi = tsp >> 16;
+    const unsigned ir = (unsigned)P.iRange[Q.kOff + lo];
+    const int a = (int)(ir & 0xffffu), b = (int)(ir >> 16);
     it.nk = P.counts[Q.kOff + lo];
     const int ti = loc / nt, tj = loc % nt;
-    it.i0 = ti * ts;
+    it.i0 = a + ti * tsi;
     it.j0 = tj * ts;
-    it.TI = min(ts, it.nk - it.i0);
+    it.TI = min(tsi, b - it.i0);
     it.TJ = min(ts, it.nk - it.j0);
     it.base = P.qSlot[it.q] + P.resOff[Q.kOff + lo];
     return it;
@@ -854,7 +947,6 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
         const int ngi = ni4 >> 2, ngj = nj4 >> 2;
         const bool act = tid < ngi * ngj;
         const int gi = act ? tid / ngj : 0, gj = act ? tid % ngj : 0;
-        const bool diag_tile = (i0 == j0);
         uint32_t vmask = 0, dmask = 0;  // valid pairs, diagonal pairs
 #pragma unroll
         for (int qa = 0; qa < 4; ++qa)
@@ -862,7 +954,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
             for (int qb = 0; qb < 4; ++qb) {
                 const int li = 4 * gi + qa, lj = 4 * gj + qb;
                 if (act && li < TI && lj < TJ) vmask |= 1u << (qa * 4 + qb);
-                if (diag_tile && li == lj) dmask |= 1u << (qa * 4 + qb);
+                if (i0 + li == j0 + lj) dmask |= 1u << (qa * 4 + qb);  // a state paired with itself
             }
         for (int t = itc.t0; t < itc.t1; ++t) {
             const float* tab = tabs + ((t - itc.t0) & 1) * PT::FLOATS;
@@ -1246,14 +1338,13 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
         const int ngi = ni4 >> 2, ngj = nj4 >> 2;
         const bool act = tid < ngi * ngj;
         const int gi = act ? tid / ngj : 0, gj = act ? tid % ngj : 0;
-        const bool diag_tile = (i0 == j0);
         uint32_t live = 0;  // valid, off-diagonal pairs of this thread's micro-tile
 #pragma unroll
         for (int qa = 0; qa < 4; ++qa)
 #pragma unroll
             for (int qb = 0; qb < 4; ++qb) {
                 const int li = 4 * gi + qa, lj = 4 * gj + qb;
-                if (act && li < TI && lj < TJ && !(diag_tile && li == lj)) live |= 1u << (qa * 4 + qb);
+                if (act && li < TI && lj < TJ && i0 + li != j0 + lj) live |= 1u << (qa * 4 + qb);
             }
         for (int t = itc.t0; t < itc.t1; ++t) {
             const float* tab = tabs + ((t - itc.t0) & 1) * PT::FLOATS;
@@ -1728,7 +1819,6 @@ __global__ void __launch_bounds__(512, 1) k_pairs_ws(BuildParams P) {
             const int ngi = ni4 >> 2, ngj = nj4 >> 2;
             const bool act = ctid < ngi * ngj;
             const int gi = act ? ctid / ngj : 0, gj = act ? ctid % ngj : 0;
-            const bool diag_tile = (mt.i0 == mt.j0);
             uint32_t vmask = 0, dmask = 0;
 #pragma unroll
             for (int qa = 0; qa < 4; ++qa)
@@ -1736,7 +1826,7 @@ __global__ void __launch_bounds__(512, 1) k_pairs_ws(BuildParams P) {
                 for (int qb = 0; qb < 4; ++qb) {
                     const int li = 4 * gi + qa, lj = 4 * gj + qb;
                     if (act && li < mt.TI && lj < mt.TJ) vmask |= 1u << (qa * 4 + qb);
-                    if (diag_tile && li == lj) dmask |= 1u << (qa * 4 + qb);
+                    if (mt.i0 + li == mt.j0 + lj) dmask |= 1u << (qa * 4 + qb);  // a state paired with itself
                 }
             if (act) {
                 Item itd;
@@ -2020,7 +2110,6 @@ __global__ void __launch_bounds__(256, 2) k_pairs_tc(BuildParams P) {
         const int ngi = ni4 >> 2, ngj = nj4 >> 2;
         const bool act = tid < ngi * ngj;
         const int gi = act ? tid / ngj : 0, gj = act ? tid % ngj : 0;
-        const bool diag_tile = (i0 == j0);
         uint32_t vmask = 0, dmask = 0;
 #pragma unroll
         for (int qa = 0; qa < 4; ++qa)
@@ -2028,7 +2117,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_tc(BuildParams P) {
             for (int qb = 0; qb < 4; ++qb) {
                 const int li = 4 * gi + qa, lj = 4 * gj + qb;
                 if (act && li < TI && lj < TJ) vmask |= 1u << (qa * 4 + qb);
-                if (diag_tile && li == lj) dmask |= 1u << (qa * 4 + qb);
+                if (i0 + li == j0 + lj) dmask |= 1u << (qa * 4 + qb);  // a state paired with itself
             }
         for (int t = itc.t0; t < itc.t1; ++t) {
             for (int u = tid; u < L.f_stride; u += nthr) tab[u] = P.tab32[(long long)(Qd.tabOff + t) * L.f_stride + u];
@@ -2481,6 +2570,7 @@ __global__ void k_emit(BuildParams P) {
         const int* mem = V.members + (long long)k * Q.N;
         const int im = mem[sr.li];
         const int i = mem_id(im);
+        if (i < P.rowRange[2 * sr.q] || i >= P.rowRange[2 * sr.q + 1]) continue;  // another shard's row
         const long long base = V.slot0 + V.resOff[k] + (long long)sr.li * nk;
         int running = 0;
         for (int lg = 0; lg < nk; lg += 128) {
@@ -2558,16 +2648,6 @@ __global__ void __launch_bounds__(1024) k_scan(BuildParams P) {
     }
 }
 
-DEVI int lower_bound_members(const int* mem, int n, int j) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (mem_id(mem[mid]) < j) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
 DEVI void write_edge(const BuildParams& P, const QueryDesc& Q, long long o, int j, uint32_t bits,
                       unsigned long long key) {
     Q.col[o] = j;
@@ -2606,6 +2686,7 @@ __global__ void __launch_bounds__(256, 4) k_compact_fill(BuildParams P, int run_
             const int* mem = V.members + (long long)sr.k * Q.N;
             const int im = mem[sr.li];
             if (mem_multi(im)) continue;  // the row item handles it
+            if (mem_id(im) < P.rowRange[2 * sr.q] || mem_id(im) >= P.rowRange[2 * sr.q + 1]) continue;
             const int nk = V.counts[sr.k];
             const long long base = V.slot0 + V.resOff[sr.k] + (long long)sr.li * nk;
             const long long rbase = Q.row_off[mem_id(im)];
@@ -2634,6 +2715,7 @@ __global__ void __launch_bounds__(256, 4) k_compact_fill(BuildParams P, int run_
         const QView V(P, q);
         const QueryDesc& Q = *V.Q;
         const int i = (int)(row - P.pfxN[q]);
+        if (i < P.rowRange[2 * q] || i >= P.rowRange[2 * q + 1]) continue;  // another shard's row
         const int W = Q.W;
         int npoly = 0;
         for (int w = 0; w < W; ++w) npoly += __popc(V.mask[(long long)i * W + w]);
@@ -2822,7 +2904,7 @@ __global__ void k_account(BuildParams P, unsigned long long* work) {
         const long long loc = ls - V.resOff[k];
         const int li = (int)(loc / nk), lj = (int)(loc % nk);
         const int i = mem_id(V.members[(long long)k * Q.N + li]), j = mem_id(V.members[(long long)k * Q.N + lj]);
-        if (i == j) continue;
+        if (i == j || i < P.rowRange[2 * q] || i >= P.rowRange[2 * q + 1]) continue;
         int ns;
         if (owner_of(V, i, j, ns) != k) continue;
         float xi[N_], xj[N_];

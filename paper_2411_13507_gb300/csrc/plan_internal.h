@@ -84,6 +84,7 @@ struct DevInfo {
     unsigned long long cut_games;    // matrix games solved in FP32
     unsigned long long cut_lp64;     // entries settled in FP64
     unsigned long long cut_ties;     // FP64 games without a certificate either way
+    int shard_lo, shard_hi;          // source rows [lo, hi) of the first query's shard
 };
 
 enum Detail {
@@ -122,6 +123,7 @@ struct QueryDesc {
     uint32_t* mask;
     long long cap;
     int64_t* count;
+    int shard, nshard;         // rows of shard `shard` of `nshard` (equal-work contiguous ranges); 0, 1: all rows
 };
 
 // Everything a build kernel needs, passed by value.
@@ -162,8 +164,10 @@ struct BuildParams {
     long long* resOff;         // [kOff] slot offset of each polytope, relative to qSlot[q]
     int* memOff;               // [kOff] membership offset of each polytope, relative to qMem[q]
     int* itemOff;
-    int* ntile;
-    int* tsize;
+    int* ntile;                // j-tiles | i-tiles << 16 of each polytope
+    int* tsize;                // j-tile side | i-tile side << 16
+    int* iRange;               // members [a, b) of each polytope whose ids lie in the query's row range: a | b << 16
+    int* rowRange;             // [Q][2] row range [lo, hi) of each query's shard (written by k_setup)
     uint32_t* resBits;
     unsigned long long* resKey;
     int* emitPre;

@@ -55,7 +55,7 @@ class _Info(ctypes.Structure):
                 ("screened", ctypes.c_int64), ("cut_units", ctypes.c_int64), ("cut_tests", ctypes.c_int64),
                 ("cut_box", ctypes.c_int64), ("cut_near", ctypes.c_int64), ("cut_step1", ctypes.c_int64),
                 ("cut_step2", ctypes.c_int64), ("cut_games", ctypes.c_int64), ("cut_lp64", ctypes.c_int64),
-                ("cut_ties", ctypes.c_int64)]
+                ("cut_ties", ctypes.c_int64), ("shard_lo", ctypes.c_int32), ("shard_hi", ctypes.c_int32)]
 
 
 class _Obstacles(ctypes.Structure):
@@ -89,7 +89,7 @@ class _MpcParams(ctypes.Structure):
 PLAN_MPC_OK, PLAN_MPC_INFEASIBLE, PLAN_MPC_ITERATION_LIMIT = 0, 1, 2
 
 
-EXPORTS = ["plan_create", "plan_destroy", "plan_build_edges", "plan_search", "plan_wait", "plan_model_tables",
+EXPORTS = ["plan_create", "plan_destroy", "plan_build_edges", "plan_build_edges_shard", "plan_search", "plan_wait", "plan_model_tables",
            "plan_set_search_limits", "plan_refine", "plan_prepare_batched", "plan_build_edges_batched",
            "plan_set_tile", "plan_autotune", "plan_prepare_search_batched", "plan_search_batched",
            "plan_search_noalloc", "plan_cut_edges", "plan_cut_timing", "plan_search_at", "plan_search_to", "plan_obstacle_planes", "plan_nearest_planes", "plan_mpc_qp",
@@ -119,6 +119,8 @@ def load(build_if_stale: bool = True):
     lib.plan_destroy.restype = None
     lib.plan_build_edges.argtypes = [vp, i32, vp, i32, dp, i32, vp, i32, vp, vp, ctypes.POINTER(_Edges)]
     lib.plan_build_edges.restype = i32
+    lib.plan_build_edges_shard.argtypes = [vp, i32, vp, i32, dp, i32, vp, i32, vp, vp, i32, i32, ctypes.POINTER(_Edges)]
+    lib.plan_build_edges_shard.restype = i32
     lib.plan_search.argtypes = [vp, i32, vp, ctypes.POINTER(_Edges), dp, dp, vp, i32, vp, vp]
     lib.plan_search.restype = i32
     lib.plan_wait.argtypes = [vp, ctypes.POINTER(_Info)]
@@ -397,12 +399,31 @@ class Planner:
         if rc != 0:
             raise self._err(rc, "plan_build_edges")
 
-    def build_edges(self, dp: DeviceProblem, graph: Optional[Graph] = None, cap: Optional[int] = None) -> Graph:
+    def build_edges_shard_async(self, dp: DeviceProblem, graph: Graph, shard: int, nshard: int) -> None:
+        T = dp.T
+        rc = self.lib.plan_build_edges_shard(self.ctx, dp.N, ctypes.c_void_p(dp.states.data_ptr()), int(T.shape[0]),
+                                             T.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), dp.K,
+                                             ctypes.c_void_p(dp.poly_off.data_ptr()), dp.max_rows,
+                                             ctypes.c_void_p(dp.A.data_ptr()), ctypes.c_void_p(dp.b.data_ptr()),
+                                             int(shard), int(nshard), ctypes.byref(graph.cstruct()))
+        if rc != 0:
+            raise self._err(rc, "plan_build_edges_shard")
+
+    def build_edges_shard(self, dp: DeviceProblem, shard: int, nshard: int, graph: Optional[Graph] = None,
+                          cap: Optional[int] = None) -> Graph:
+        """The rows of one shard of the graph (plan_build_edges_shard), growing scratch/output on CAPACITY."""
+        return self.build_edges(dp, graph, cap, shard=(int(shard), int(nshard)))
+
+    def build_edges(self, dp: DeviceProblem, graph: Optional[Graph] = None, cap: Optional[int] = None,
+                    shard=None) -> Graph:
         """Build the feasible-edge graph, growing scratch/output and repeating on CAPACITY."""
         if graph is None:
             graph = self.alloc_graph(dp.N, cap if cap is not None else max(1024, 64 * dp.N))
         for _ in range(6):
-            self.build_edges_async(dp, graph)
+            if shard is None:
+                self.build_edges_async(dp, graph)
+            else:
+                self.build_edges_shard_async(dp, graph, *shard)
             st = self.wait()
             if st == PLAN_OK:
                 return graph
