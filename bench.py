@@ -158,8 +158,8 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def lane_peaks(dev):
-    """FP32 lane-op rates measured on this device (plan_measure_lane_rate) and the nominal figure."""
+def lane_peaks(dev, fp64=False):
+    """FP32 (and FP64) lane-op rates measured on this device (plan_measure_lane_rate) and the nominal figure."""
     import torch
     from paper_2411_13507_gb300 import plan as P
     peaks, src = measured_peaks()
@@ -170,6 +170,11 @@ def lane_peaks(dev):
     r["note"] = (f"measured: FP32 add + |.|-max register chains on all {sms} SMs (plan_measure_lane_rate) "
                  f"{r['addmax'] / 1e12:.2f} T/s; FMA chains {r['fma'] / 1e12:.2f} T/s; nominal {sms} SMs x 128 lanes "
                  f"x {sm_max:.0f} MHz ({src} clock) = {r['nominal'] / 1e12:.2f} T/s")
+    if fp64:
+        r["addmax64"] = P.measure_lane_rate(2, 1 << 10)["lane_ops_per_s"]
+        r["fma64"] = P.measure_lane_rate(3, 1 << 10)["lane_ops_per_s"]
+        r["note64"] = (f"measured: FP64 add + |.|-max register chains on all {sms} SMs (plan_measure_lane_rate) "
+                       f"{r['addmax64'] / 1e12:.3f} T/s; FP64 FMA chains {r['fma64'] / 1e12:.3f} T/s")
     return r
 
 
@@ -265,11 +270,74 @@ def timed(fn, stream, steps, warmup, flush=None):
     return ms
 
 
-def run_form(args):
-    """Lines for the other configurations (precision, batching, differentiation, FP64 plain)."""
+def clocked(fn, stream, steps, warmup, flush, before=None, after=None):
+    """timed() with the nvidia-smi sampler around the timed calls: fn runs
+    untimed until a sample has arrived, then the timed calls, then untimed
+    again until the next sample; returns (ms, clocks, after())."""
+    import torch
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t0 = time.time()
+        while clk.count() < 1 and time.time() - t0 < 10.0:
+            fn()
+            torch.cuda.synchronize()
+        mark = max(0, clk.count() - 1)
+        if before:
+            before()
+        ms = timed(fn, stream, steps, warmup, flush)
+        res = after() if after else None
+        t0 = time.time()
+        while clk.count() < mark + 2 and time.time() - t0 < 5.0:
+            fn()
+            torch.cuda.synchronize()
+    return ms, clk.summary(since=mark), res
+
+
+def ops_per_check(prob) -> float:
+    """Dense separable work per check (every reach, free and cost row)."""
+    g, p, m = prob.model.gamma, prob.model.degree, prob.model.m
+    n = m * g
+    rax = sum(p - k + 1 for k in range(1, g + 1))
+    rows_mean = float(np.mean(np.diff(prob.poly_off)))
+    return 4 * m * rax + 2 * (p - 1) * rows_mean + p * (2 * n + 2)
+
+
+def e2e_build_search(pl, dp, prob, graph, sbuf, stream, flush, steps, warmup, np_dtype):
+    """End to end through the C ABI: states and polytopes from pinned host
+    memory, plan_build_edges + plan_search, path and cost back to the host."""
     import torch
     from paper_2411_13507_gb300 import plan as P
-    from paper_2411_13507_gb300 import synth
+    h_states = torch.from_numpy(np.ascontiguousarray(prob.states, dtype=np_dtype)).pin_memory()
+    h_off = torch.from_numpy(np.asarray(prob.poly_off, dtype=np.int32)).pin_memory()
+    h_A = torch.from_numpy(np.ascontiguousarray(prob.A, dtype=np_dtype)).pin_memory()
+    h_b = torch.from_numpy(np.ascontiguousarray(prob.b, dtype=np_dtype)).pin_memory()
+    h_path = torch.empty(dp.N, dtype=torch.int32).pin_memory()
+    h_cost = torch.empty(1, dtype=torch.float64).pin_memory()
+    bi = sum(t.numel() * t.element_size() for t in (h_states, h_off, h_A, h_b))
+    ms = []
+    for s in range(warmup + steps):
+        flush.fill_(2.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dp.states.copy_(h_states, non_blocking=True)
+        dp.poly_off.copy_(h_off, non_blocking=True)
+        dp.A.copy_(h_A, non_blocking=True)
+        dp.b.copy_(h_b, non_blocking=True)
+        pl.build_edges_async(dp, graph)
+        pl.search_async(dp, graph, dp.start_pos, dp.goal_pos, sbuf)
+        h_path.copy_(sbuf["path"], non_blocking=True)
+        h_cost.copy_(sbuf["cost"], non_blocking=True)
+        e1.record(stream)
+        assert pl.wait() == P.PLAN_OK
+        if s >= warmup:
+            ms.append(e0.elapsed_time(e1))
+    return statistics.mean(ms), bi, h_path.numel() * 4 + 8
+
+
+def run_form(args):
+    """Lines for the other configurations (FP64 plain method, precision,
+    batching and differentiation forms), each with clocks, a roofline of its
+    dominant kernel, the oracle on the host cores and an end-to-end figure."""
+    import torch
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(device=dev)
@@ -278,59 +346,9 @@ def run_form(args):
             "vs_baseline": None, "data": "synthetic", "form": args.form}
     with torch.cuda.stream(stream):
         if args.form in ("fp64", "tf32", "bf16"):
-            prob = synth.double_integrator_2d(seed=1)
-            arith = {"fp64": "f64", "tf32": "tf32", "bf16": "bf16"}[args.form]
-            pl = P.Planner.for_problem(prob, arith=arith, input="f64", stream=stream)
-            dp = P.to_device(prob, input="f64")
-            g = pl.build_edges(dp)
-            info = pl.info()
-            sbuf = pl.alloc_search(dp.N)
-            pl.set_timing(True)
-            pl.timing(reset=True)
-            bms = timed(lambda: pl.build_edges_async(dp, g), stream, args.steps, args.warmup, flush)
-            t = pl.timing(reset=True)
-            sms = timed(lambda: pl.search_async(dp, g, dp.start_pos, dp.goal_pos, sbuf), stream, args.steps,
-                        args.warmup, flush)
-            assert pl.wait() == P.PLAN_OK
-            checks = info["checks"]
-            line.update({"metric": "edge-feasibility checks/sec, 2-D double integrator (N=512, K=16, nT=8, p=5)",
-                         "value": checks * 1e3 / statistics.mean(bms), "unit": UNIT, "dtype": arith,
-                         "ms_per_step": statistics.mean(bms) + statistics.mean(sms),
-                         "build_ms_per_query": statistics.mean(bms), "search_ms_per_query": statistics.mean(sms),
-                         "pair_kernel_ms": t["pair_ms"] / max(1, t["pair_launches"]),
-                         "config": {"workload": "double_integrator_2d seed 1", "checks": checks,
-                                    "rechecks": info["rechecks"], "recheck_frac": info["rechecks"] / max(1, checks),
-                                    "edges": info["edges"]}})
+            line.update(run_2d_form(args, stream, flush, dev))
         elif args.form == "batched":
-            probs = synth.batched_queries(seed=args.seed, Q=args.queries)
-            pl = P.Planner.for_problem(probs[0], arith="f32", input="f32", stream=stream)
-            dps = [P.to_device(p, input="f32") for p in probs]
-            graphs = pl.build_batched(dps)
-            info = pl.info()
-            from paper_2411_13507_gb300 import autotune
-            tune = autotune.tune(pl, f"batched{args.queries}", reps=2)
-            graphs = pl.build_batched(dps, graphs)      # re-prepare with the tuned tiles
-            outs = pl.alloc_search_batched(dps)
-            pl.prepare_search_batched(dps, graphs, outs)
-            cg = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(cg, stream=stream):
-                pl.build_batched_async()
-            sg = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(sg, stream=stream):
-                pl.search_batched_async()
-            bms = timed(cg.replay, stream, args.steps, args.warmup, flush)
-            sms = timed(sg.replay, stream, args.steps, args.warmup, flush)
-            assert pl.wait() == P.PLAN_OK
-            checks = int(info["checks"])
-            line.update({"metric": f"edge-feasibility checks/sec, {args.queries} uneven 3-D queries in one captured graph",
-                         "value": checks * 1e3 / statistics.mean(bms),
-                         "unit": UNIT, "dtype": "f32", "ms_per_step": statistics.mean(bms) + statistics.mean(sms),
-                         "build_ms_per_batch": statistics.mean(bms),
-                         "search_ms_per_query": statistics.mean(sms) / len(probs),
-                         "config": {"workload": f"batched_queries seed {args.seed}", "queries": len(probs),
-                                    "N_total": sum(p.N for p in probs), "checks": checks,
-                                    "candidates": int(info["candidates"]),
-                                    "edges": int(info["edges"]), "rechecks": int(info["rechecks"]), "autotune": tune}})
+            line.update(run_batched_form(args, stream, flush, dev))
         elif args.form == "cut":
             line.update(run_cut_form(args, stream, flush, dev))
         elif args.form == "replan":
@@ -340,25 +358,288 @@ def run_form(args):
         elif args.form == "mpc":
             line.update(run_mpc_form(args, stream, flush, dev))
         elif args.form == "refine":
-            from paper_2411_13507_gb300 import refine as RF
-            rb = synth.refine_segments(seed=args.seed, S=65536)
-            f = lambda x: torch.as_tensor(np.asarray(x, dtype=np.float32)).to(dev).contiguous()
-            Pt, Tt, At, bt = f(rb.P), f(rb.T), f(rb.A), f(rb.b)
-            nr = torch.as_tensor(rb.nrows, dtype=torch.int32).to(dev)
-            refiner = RF.Refiner(stream=stream)
-            up = torch.ones(Pt.shape[0], device=dev)
-
-            def fb():
-                refiner.forward(Pt, Tt, At, bt, nr)
-                refiner.backward(Pt, Tt, At, bt, nr, up)
-            ms = timed(fb, stream, args.steps, args.warmup, flush)
-            refiner.check()
-            S = Pt.shape[0]
-            line.update({"metric": "refinement segments/sec (forward + backward), 65536 degree-7 3-D segments",
-                         "value": S * 1e3 / statistics.mean(ms), "unit": "segments/s", "dtype": "f32",
-                         "ms_per_step": statistics.mean(ms),
-                         "config": {"workload": "refine_segments", "segments": S}})
+            line.update(run_refine_form(args, stream, flush, dev))
     return line
+
+
+def run_2d_form(args, stream, flush, dev):
+    """FP64 plain method and the precision form (TF32 / BF16 tensor-core
+    halves) on the 2-D double-integrator workload, with the FP64 and FP32 plain
+    forms timed on the same inputs."""
+    import torch
+    from paper_2411_13507_gb300 import plan as P
+    from paper_2411_13507_gb300 import synth
+    prob = synth.double_integrator_2d(seed=1)
+    arith = {"fp64": "f64", "tf32": "tf32", "bf16": "bf16"}[args.form]
+    pl = P.Planner.for_problem(prob, arith=arith, input="f64", stream=stream)
+    dp = P.to_device(prob, input="f64")
+    g = pl.build_edges(dp)
+    info = pl.info()
+    sbuf = pl.alloc_search(dp.N)
+    pl.set_timing(True)
+    bms, clocks, tm = clocked(lambda: pl.build_edges_async(dp, g), stream, args.steps, args.warmup, flush,
+                              before=lambda: pl.timing(reset=True), after=lambda: pl.timing(reset=True))
+    pl.set_timing(False)
+    sms = timed(lambda: pl.search_async(dp, g, dp.start_pos, dp.goal_pos, sbuf), stream, args.steps, args.warmup,
+                flush)
+    assert pl.wait() == P.PLAN_OK
+    checks = int(info["checks"])
+    build_ms = statistics.mean(bms)
+    # the plain forms on the same inputs
+    plain = {}
+    for ra in ("f64", "f32"):
+        if ra == arith:
+            continue
+        p2 = P.Planner.for_problem(prob, arith=ra, input="f64", stream=stream)
+        g2 = p2.build_edges(dp)
+        ms2 = timed(lambda: p2.build_edges_async(dp, g2), stream, args.steps, args.warmup, flush)
+        assert p2.wait() == P.PLAN_OK
+        plain[ra] = {"build_ms": statistics.mean(ms2), "checks_per_s": checks * 1e3 / statistics.mean(ms2),
+                     "speedup_of_this_form": statistics.mean(ms2) / build_ms}
+        p2.close()
+    e2e_ms, bi, bo = e2e_build_search(pl, dp, prob, g, sbuf, stream, flush, args.steps, args.warmup, np.float64)
+    lanes = lane_peaks(dev, fp64=True)
+    pair_ms = tm["pair_ms"] / max(1, tm["pair_launches"])
+    opc = ops_per_check(prob)
+    ach = opc * checks / (pair_ms / 1e3) / 1e12
+    if arith == "f64":
+        peak, pnote, kern = lanes["addmax64"] / 1e12, lanes["note64"], "k_pairs_f64<2,2,5>"
+    else:
+        peak, pnote, kern = lanes["addmax"] / 1e12, lanes["note"], f"k_pairs_tc<2,2,5,{arith}>"
+    cpu = None if args.no_cpu_baseline else cpu_baseline(prob)
+    return {"metric": "edge-feasibility checks/sec, 2-D double integrator (N=512, K=16, nT=8, p=5)",
+            "value": checks * 1e3 / build_ms, "unit": UNIT, "dtype": arith,
+            "ms_per_step": build_ms + statistics.mean(sms), "build_ms_per_query": build_ms,
+            "search_ms_per_query": statistics.mean(sms), "gpu_launches": int(tm["launches"]), "clocks": clocks,
+            "config": {"workload": "double_integrator_2d seed 1 (|v|<=2, |a|<=4, [0,10]^2, 16 polytopes of 4-8 rows, "
+                                   "512 states, p=5, 8 durations in [0.2, 2])", "checks": checks,
+                       "rechecks": info["rechecks"], "recheck_frac": info["rechecks"] / max(1, checks),
+                       "edges": info["edges"], "l2": "flushed before every timed call (256 MB write)"},
+            "vs_plain_forms": plain,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TOP/s", "frac": ach / peak,
+                         "traffic": None, "kernel": kern, "kernel_ms": pair_ms, "ops_per_check": opc,
+                         "ops_per_launch": opc * checks,
+                         "work_model": "dense separable form per check (all reach, free and cost rows)"
+                                       + ("" if arith == "f64" else "; the pair phase runs on the FP32 lanes, the "
+                                          "halves on the tensor cores (ncu: profiles/k_pairs_tc_double_integrator_2d.md)"),
+                         "peak_note": pnote},
+            "e2e": {"value": checks * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+                    "ms_per_step": e2e_ms},
+            "cpu_baseline": ({k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")} if cpu else None)}
+
+
+def run_batched_form(args, stream, flush, dev):
+    """Batching form: the uneven 3-D queries, the edge build in one replay of a
+    captured CUDA graph (one persistent pair launch) with autotuned tiles, the
+    batched search in another."""
+    import torch
+    from paper_2411_13507_gb300 import autotune
+    from paper_2411_13507_gb300 import plan as P
+    from paper_2411_13507_gb300 import synth
+    probs = synth.batched_queries(seed=args.seed, Q=args.queries)
+    pl = P.Planner.for_problem(probs[0], arith="f32", input="f32", stream=stream)
+    dps = [P.to_device(p, input="f32") for p in probs]
+    graphs = pl.build_batched(dps)
+    tune = autotune.tune(pl, f"batched{args.queries}", reps=2)
+    graphs = pl.build_batched(dps, graphs)      # re-prepare with the tuned tiles
+    info = pl.info()
+    outs = pl.alloc_search_batched(dps)
+    pl.prepare_search_batched(dps, graphs, outs)
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg, stream=stream):
+        pl.build_batched_async()
+    sg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(sg, stream=stream):
+        pl.search_batched_async()
+    bms, clocks, _ = clocked(cg.replay, stream, args.steps, args.warmup, flush)
+    sms = timed(sg.replay, stream, args.steps, args.warmup, flush)
+    assert pl.wait() == P.PLAN_OK
+    # the pair kernel's own time: the same launch outside the graph, with events
+    pl.set_timing(True)
+    pl.timing(reset=True)
+    timed(pl.build_batched_async, stream, max(3, args.steps // 2), 1, flush)
+    tm = pl.timing(reset=True)
+    pl.set_timing(False)
+    assert pl.wait() == P.PLAN_OK
+    # end to end: every query's inputs from pinned host memory, the two
+    # replays, every query's path length, cost and status back
+    hin = []
+    for p, dp in zip(probs, dps):
+        hin.append([(torch.from_numpy(np.ascontiguousarray(p.states, dtype=np.float32)).pin_memory(), dp.states),
+                    (torch.from_numpy(np.asarray(p.poly_off, dtype=np.int32)).pin_memory(), dp.poly_off),
+                    (torch.from_numpy(np.ascontiguousarray(p.A, dtype=np.float32)).pin_memory(), dp.A),
+                    (torch.from_numpy(np.ascontiguousarray(p.b, dtype=np.float32)).pin_memory(), dp.b)])
+    hout = [(torch.empty(1, dtype=torch.int32).pin_memory(), o["path_len"]) for o in outs] + \
+           [(torch.empty(1, dtype=torch.float64).pin_memory(), o["cost"]) for o in outs]
+    bi = sum(h.numel() * h.element_size() for q in hin for h, _ in q)
+    bo = sum(h.numel() * h.element_size() for h, _ in hout)
+    e2e = []
+    for s in range(args.warmup + args.steps):
+        flush.fill_(2.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for q in hin:
+            for h, d in q:
+                d.copy_(h, non_blocking=True)
+        cg.replay()
+        sg.replay()
+        for h, d in hout:
+            h.copy_(d, non_blocking=True)
+        e1.record(stream)
+        assert pl.wait() == P.PLAN_OK
+        if s >= args.warmup:
+            e2e.append(e0.elapsed_time(e1))
+    checks = int(info["checks"])
+    build_ms = statistics.mean(bms)
+    pair_ms = tm["pair_ms"] / max(1, tm["pair_launches"])
+    lanes = lane_peaks(dev)
+    # dense work: per-query candidates are not reported separately, so the
+    # model's rows use the batch's mean polytope size (every query has p = 7, m = 3)
+    rows_mean = float(np.mean(np.concatenate([np.diff(p.poly_off) for p in probs])))
+    m, gg, pp = 3, 3, 7
+    rax = sum(pp - k + 1 for k in range(1, gg + 1))
+    opc = 4 * m * rax + 2 * (pp - 1) * rows_mean + pp * (2 * m * gg + 2)
+    ach = opc * checks / (pair_ms / 1e3) / 1e12
+    peak = lanes["addmax"] / 1e12
+    screened = int(info.get("screened", 0))
+    ex_ops = 2 * 3 * m * checks + 2 * (m * rax + (pp - 1) * rows_mean) * screened + pp * (2 * m * gg + 2) * int(info["feasible"])
+    cpu = None if args.no_cpu_baseline else batched_cpu_baseline(probs)
+    return {"metric": f"edge-feasibility checks/sec, {args.queries} uneven 3-D queries in one captured graph",
+            "value": checks * 1e3 / build_ms, "unit": UNIT, "dtype": "f32",
+            "ms_per_step": build_ms + statistics.mean(sms), "build_ms_per_batch": build_ms,
+            "search_ms_per_query": statistics.mean(sms) / len(probs), "gpu_launches": int(tm["launches"]),
+            "clocks": clocks,
+            "config": {"workload": f"batched_queries seed {args.seed}: 3-D triple integrator, states log-uniform in "
+                                   "512-16384, 8-128 polytopes, 8-16 durations, p=7", "queries": len(probs),
+                       "N_total": sum(p.N for p in probs), "checks": checks, "candidates": int(info["candidates"]),
+                       "edges": int(info["edges"]), "rechecks": int(info["rechecks"]), "autotune": tune,
+                       "l2": "flushed before every timed replay (256 MB write)"},
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TOP/s", "frac": ach / peak,
+                         "hw_frac": ex_ops / (pair_ms / 1e3) / 1e12 / peak, "traffic": None,
+                         "kernel": "k_pairs_sc<3,3,7> (one persistent launch for the batch)", "kernel_ms": pair_ms,
+                         "ops_per_check": opc, "ops_per_launch": opc * checks,
+                         "work_model": "dense separable form per check, rows at the batch's mean polytope size; "
+                                       "hw_frac: executed lane-ops (screen rows of every check, all rows of the "
+                                       "screened ones, costs of the feasible ones) / measured peak",
+                         "peak_note": lanes["note"]},
+            "e2e": {"value": checks * 1e3 / statistics.mean(e2e), "unit": UNIT, "h2d_bytes_per_step": bi,
+                    "d2h_bytes_per_step": bo, "ms_per_step": statistics.mean(e2e)},
+            "cpu_baseline": cpu}
+
+
+def batched_cpu_baseline(probs, budget_s=12.0):
+    """The FP64 oracle on a bounded sample of the batch: every 16th query,
+    rows spread over each, until about budget_s of CPU time."""
+    import oracle
+    t_all, checks = 0.0, 0
+    qs = list(range(0, len(probs), 16))
+    per_q = budget_s / len(qs)
+    rows_used = 0
+    for q in qs:
+        p = probs[q]
+        op = oracle.OracleProblem(p)
+        op.membership()
+        probe = np.arange(0, p.N, max(1, p.N // 8), dtype=np.int32)[:8]
+        t0 = time.perf_counter()
+        op.edges(probe, with_detail=False)
+        per_row = max(time.perf_counter() - t0, 1e-4) / len(probe)
+        n = int(min(p.N, max(8, per_q / per_row)))
+        sel = np.linspace(0, p.N - 1, n).astype(np.int32)
+        t0 = time.perf_counter()
+        e = op.edges(sel, with_detail=False)
+        t_all += time.perf_counter() - t0
+        checks += int(e["i"].shape[0]) * p.nT
+        rows_used += n
+    return {"value": checks / t_all, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{rows_used} rows of {len(qs)} queries (every 16th), {checks} checks, {t_all:.1f} s, "
+                      "FP64 C oracle, OpenMP"}
+
+
+def run_refine_form(args, stream, flush, dev):
+    """Differentiation form: forward + hand-written backward of the refinement
+    objective for 65536 degree-7 3-D segments."""
+    import torch
+    from paper_2411_13507_gb300 import plan as P
+    from paper_2411_13507_gb300 import refine as RF
+    from paper_2411_13507_gb300 import synth
+    rb = synth.refine_segments(seed=args.seed, S=65536)
+    f = lambda x: torch.as_tensor(np.asarray(x, dtype=np.float32)).to(dev).contiguous()
+    Pt, Tt, At, bt = f(rb.P), f(rb.T), f(rb.A), f(rb.b)
+    nr = torch.as_tensor(rb.nrows, dtype=torch.int32).to(dev)
+    refiner = RF.Refiner(stream=stream)
+    up = torch.ones(Pt.shape[0], device=dev)
+    S = Pt.shape[0]
+    res = {}
+
+    def fb():
+        res["loss"] = refiner.forward(Pt, Tt, At, bt, nr)
+        res["dP"], res["dT"] = refiner.backward(Pt, Tt, At, bt, nr, up)
+    refiner.planner.set_timing(True)
+    ms, clocks, tm = clocked(fb, stream, args.steps, args.warmup, flush,
+                             before=lambda: refiner.planner.timing(reset=True),
+                             after=lambda: refiner.planner.timing(reset=True))
+    refiner.check()
+    # end to end: segments from pinned host memory, forward + backward, loss and gradients back
+    hin = [(torch.from_numpy(np.ascontiguousarray(x, dtype=dt)).pin_memory(), d) for x, dt, d in
+           ((rb.P, np.float32, Pt), (rb.T, np.float32, Tt), (rb.A, np.float32, At), (rb.b, np.float32, bt),
+            (rb.nrows, np.int32, nr))]
+    h_loss = torch.empty(S, dtype=torch.float32).pin_memory()
+    h_dP = torch.empty(tuple(Pt.shape), dtype=torch.float32).pin_memory()
+    h_dT = torch.empty(S, dtype=torch.float32).pin_memory()
+    e2e = []
+    for s in range(args.warmup + args.steps):
+        flush.fill_(2.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for h, d in hin:
+            d.copy_(h, non_blocking=True)
+        fb()
+        h_loss.copy_(res["loss"], non_blocking=True)
+        h_dP.copy_(res["dP"], non_blocking=True)
+        h_dT.copy_(res["dT"], non_blocking=True)
+        e1.record(stream)
+        refiner.check()
+        if s >= args.warmup:
+            e2e.append(e0.elapsed_time(e1))
+    bi = sum(h.numel() * h.element_size() for h, _ in hin)
+    bo = (h_loss.numel() + h_dP.numel() + h_dT.numel()) * 4
+    # roofline: HBM bytes of the two launches (each reads the segments; the
+    # forward writes the loss, the backward reads the upstream gradient and
+    # writes dP, dT)
+    rmax = At.shape[1]
+    seg_in = (Pt[0].numel() + 1 + rmax * 3 + rmax) * 4 + 4
+    bytes_call = S * (2 * seg_in + 4 + 4 + (Pt[0].numel() + 1) * 4)
+    step_ms = statistics.mean(ms)
+    peaks, src = measured_peaks()
+    ach = bytes_call / (step_ms / 1e3) / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import refine as OR
+        n = 4096
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < 8.0:
+            OR.loss_and_grad(rb.P[:n], rb.T[:n], rb.A[:n], rb.b[:n], rb.nrows[:n], rb.bounds)
+            reps += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": reps * n / dt, "unit": "segments/s", "cores": 1, "kind": "oracle",
+               "sample": f"{reps} x {n} segments, {dt:.1f} s (FP64 numpy oracle, loss and gradient)"}
+    return {"metric": "refinement segments/sec (forward + backward), 65536 degree-7 3-D segments",
+            "value": S * 1e3 / step_ms, "unit": "segments/s", "dtype": "f32", "ms_per_step": step_ms,
+            "gpu_launches": int(tm["launches"]), "clocks": clocks,
+            "config": {"workload": "refine_segments: 65536 degree-7 3-D segments (end points on a random line, "
+                                   "interior points N(0,1) about it, T ~ U[0.2, 2], one polytope of <= 12 rows each)",
+                       "segments": S, "l2": "flushed before every timed step (256 MB write)"},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                         "frac": ach / float(peaks["hbm_gbs"]), "traffic": None,
+                         "kernel": "k_refine<3,3,7> forward + backward", "kernel_ms": step_ms,
+                         "bytes_per_step": bytes_call,
+                         "work_model": "segments read by both launches, loss written, upstream gradient read, "
+                                       "dP and dT written",
+                         "peak_note": f"copy bandwidth ({src})"},
+            "e2e": {"value": S * 1e3 / statistics.mean(e2e), "unit": "segments/s", "h2d_bytes_per_step": bi,
+                    "d2h_bytes_per_step": bo, "ms_per_step": statistics.mean(e2e)},
+            "cpu_baseline": cpu}
 
 
 def cut_cpu_baseline(prob, obs, budget_s=12.0):

@@ -585,11 +585,12 @@ int plan_timing(plan_ctx* ctx, double* pair_ms, int64_t* pair_launches, double* 
 int plan_cut_timing(plan_ctx* ctx, double* scan_ms, double* cut_ms, int64_t* cuts, int reset);
 
 /* Measurement helper (no counterpart in the paper): the sustained issue rate
- * of the FP32 lane operations that make up the pair kernels' work, measured
+ * of the FP32 (or FP64) lane operations that make up the pair kernels' work, measured
  * on the current device by a full-occupancy kernel of independent register
  * chains timed with CUDA events (two launches; the second is timed).
  *   mix   0: one add and one max of an absolute value per step (a reach or
- *         free row of one pair); 1: one fused multiply-add per step
+ *         free row of one pair); 1: one fused multiply-add per step; 2 and 3:
+ *         the same in FP64 (the canonical FP64 pair kernel)
  *   iters chain steps per thread, 1 .. 2^24 (about 2^16 runs for milliseconds)
  *   lane_ops_per_s  host out: lane operations per second (an FMA counts one)
  *   ms    host out (may be NULL): duration of the timed launch

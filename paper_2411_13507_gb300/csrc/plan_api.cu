@@ -619,7 +619,9 @@ int issue(plan_ctx* c) {
     P.tile = (c->model.arith == PLAN_F64) ? TILE64
              : (c->model.arith == PLAN_F32) ? (c->tile > 0 ? c->tile : TILE)
                                             : TILE;  // tensor-core form: 64-state tiles, 256 threads
-    P.tchunks = (c->model.arith == PLAN_F64) ? 1 : (c->tchunks > 0 ? c->tchunks : 2);
+    // FP64: one duration per item by default (the canonical kernel is bound by
+    // the narrow FP64 pipe; small problems need the items to fill every SM)
+    P.tchunks = c->tchunks > 0 ? c->tchunks : (c->model.arith == PLAN_F64 ? 8 : 2);
     P.pipeline = c->pipeline;
     P.eps = c->model.tighten;
     P.qd = c->d_qd;

@@ -558,7 +558,6 @@ DEVI ItemT item_decode_chunk(const BuildParams& P, long long item) {
 __global__ void k_zero_slots(BuildParams P) {
     long long n = 0;
     if (block_failed(P.info, &P.info->slots, &n)) return;
-    if (P.arith == PLAN_F64) n = 0;  // the FP64 kernel writes every result slot itself
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
         P.resBits[s] = 0u;
         P.resKey[s] = KEY_NONE;
@@ -2298,7 +2297,12 @@ __global__ void __launch_bounds__(256) k_pairs_f64(BuildParams P) {
         __syncthreads();
         const long long item = s_item;
         if (item >= nitems) break;
-        const Item itd = item_decode(P, item);
+        const ItemT itc = item_decode_chunk(P, item);
+        const Item& itd = itc.it;
+        if (itc.t0 >= itc.t1) {  // empty chunk (nT < number of chunks)
+            __syncthreads();     // everyone has read s_item before it is rewritten
+            continue;
+        }
         const QueryDesc& Qd = P.qd[itd.q];
         const int k = itd.k, i0 = itd.i0, j0 = itd.j0, TI = itd.TI, TJ = itd.TJ, nk = itd.nk;
         const int r0 = Qd.poly_off[k], nr = Qd.poly_off[k + 1] - r0;
@@ -2318,7 +2322,7 @@ __global__ void __launch_bounds__(256) k_pairs_f64(BuildParams P) {
             bts[u] = 0;
         }
         __syncthreads();
-        for (int t = 0; t < Qd.nT; ++t) {
+        for (int t = itc.t0; t < itc.t1; ++t) {
             for (int u = tid; u < L.e_stride; u += nthr) tab[u] = P.tab64[(long long)(Qd.tabOff + t) * L.e_stride + u];
             __syncthreads();
             for (int u = tid; u < (TI + TJ) * M; u += nthr) {
@@ -2387,13 +2391,16 @@ __global__ void __launch_bounds__(256) k_pairs_f64(BuildParams P) {
             }
             __syncthreads();
         }
+        // merge this chunk of durations into the pair slots (other chunks of
+        // the same tile merge theirs: OR of the bits, min of cost | T)
         const long long base = itd.base;
         for (int pp = tid; pp < TI * TJ; pp += nthr) {
             const int li = pp / TJ, lj = pp % TJ;
             const int q = li * T + lj;
+            if (!bbits[q]) continue;
             const long long slot = base + (long long)(i0 + li) * nk + (j0 + lj);
-            P.resBits[slot] = bbits[q];
-            P.resKey[slot] = bbits[q] ? key_f64(bcs[q], bts[q]) : KEY_NONE;
+            atomicOr(&P.resBits[slot], bbits[q]);
+            atomicMin(&P.resKey[slot], key_f64(bcs[q], bts[q]));
         }
         __syncthreads();
     }

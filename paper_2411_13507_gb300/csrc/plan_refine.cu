@@ -66,20 +66,42 @@ DEVI void adj_diff(float (&g)[8][M], int len) {
 
 }  // namespace
 
+// Odd per-segment strides of the shared-memory stages: consecutive threads'
+// rows then fall in different banks.
+__host__ __device__ constexpr int odd_stride(int n) { return n | 1; }
+
+// One block holds blockDim.x consecutive segments.  Their control points,
+// polytope rows and bounds are staged in shared memory by coalesced loads of
+// the contiguous [S][..] arrays (each thread then reads its own segment's
+// rows there), and the gradient leaves the same way.
 template <int M, int G, int PD, bool GRAD>
 __global__ void __launch_bounds__(128) k_refine(RefineParams R) {
     constexpr int L = PD + 1;
-    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (s >= R.S) return;
+    constexpr int NP = L * M, SP = odd_stride(NP);
+    extern __shared__ float smr[];
+    const int SB = blockDim.x;
+    const int NA = R.rmax * M, SA = odd_stride(NA), SBb = odd_stride(R.rmax);
+    float* sP = smr;                 // [SB][SP]
+    float* sA = sP + SB * SP;        // [SB][SA]
+    float* sb = sA + SB * SA;        // [SB][SBb]
+    const long long s0 = blockIdx.x * (long long)SB;
+    const int nseg = (int)min((long long)SB, R.S - s0);
+    for (int u = threadIdx.x; u < nseg * NP; u += SB) sP[(u / NP) * SP + u % NP] = R.P[s0 * NP + u];
+    for (int u = threadIdx.x; u < nseg * NA; u += SB) sA[(u / NA) * SA + u % NA] = R.A[s0 * NA + u];
+    for (int u = threadIdx.x; u < nseg * R.rmax; u += SB) sb[(u / R.rmax) * SBb + u % R.rmax] = R.b[s0 * R.rmax + u];
+    __syncthreads();
+    const int t = threadIdx.x;
+    const long long s = s0 + t;
+    const bool live = t < nseg;
     float P[8][M];
 #pragma unroll
     for (int l = 0; l < L; ++l)
 #pragma unroll
-        for (int a = 0; a < M; ++a) P[l][a] = R.P[(s * L + l) * M + a];
-    const float T = R.T[s];
+        for (int a = 0; a < M; ++a) P[l][a] = live ? sP[t * SP + l * M + a] : 0.f;
+    const float T = live ? R.T[s] : 1.f;
     const float Ti = 1.f / T;
     const float mu = R.mu, delta = R.delta, ld = logf(R.delta), ws = R.w_snap;
-    const float up = GRAD ? R.grad_loss[s] : 1.f;
+    const float up = (GRAD && live) ? R.grad_loss[s] : 1.f;
     float loss = 0.f, dT = 0.f;
     float dP[8][M];
 #pragma unroll
@@ -129,12 +151,12 @@ __global__ void __launch_bounds__(128) k_refine(RefineParams R) {
         }
     }
     // free-space margins of the interior control points
-    const int nr = min(R.nrows[s], R.rmax);
+    const int nr = live ? min(R.nrows[s], R.rmax) : 0;
     for (int r = 0; r < nr; ++r) {
         float Ar[M];
 #pragma unroll
-        for (int a = 0; a < M; ++a) Ar[a] = R.A[(s * R.rmax + r) * M + a];
-        const float br = R.b[s * R.rmax + r];
+        for (int a = 0; a < M; ++a) Ar[a] = sA[t * SA + r * M + a];
+        const float br = sb[t * SBb + r];
 #pragma unroll
         for (int l = 1; l < PD; ++l) {
             float dot = 0.f;
@@ -198,29 +220,42 @@ __global__ void __launch_bounds__(128) k_refine(RefineParams R) {
             dT += ws * (-7.f) * J * Ti * up;
         }
     }
-    if (R.loss) R.loss[s] = loss;
+    if (R.loss && live) R.loss[s] = loss;
     if (GRAD) {
+        __syncthreads();  // every thread has read its rows of sP
+        if (live) {
 #pragma unroll
-        for (int l = 0; l < L; ++l)
+            for (int l = 0; l < L; ++l)
 #pragma unroll
-            for (int a = 0; a < M; ++a) R.dP[(s * L + l) * M + a] = dP[l][a];
-        R.dT[s] = dT;
+                for (int a = 0; a < M; ++a) sP[t * SP + l * M + a] = dP[l][a];
+            R.dT[s] = dT;
+        }
+        __syncthreads();
+        for (int u = threadIdx.x; u < nseg * NP; u += SB) R.dP[s0 * NP + u] = sP[(u / NP) * SP + u % NP];
     }
+}
+
+// Segments per block and dynamic shared memory of k_refine.
+static int refine_block(int rmax) { return rmax <= 16 ? 128 : 32; }
+static size_t refine_smem(int m, int p, int rmax) {
+    return sizeof(float) * (size_t)refine_block(rmax) * (odd_stride((p + 1) * m) + odd_stride(rmax * m) + odd_stride(rmax));
 }
 
 bool refine_supported(int m, int g, int p) { return (m == 3 && g == 3 && p == 7) || (m == 2 && g == 2 && p == 5); }
 
 int launch_refine(const RefineParams& R, void* stream, int* launches) {
     cudaStream_t st = (cudaStream_t)stream;
-    const unsigned nb = (unsigned)((R.S + 127) / 128);
+    const int sb = refine_block(R.rmax);
+    const unsigned nb = (unsigned)((R.S + sb - 1) / sb);
     if (R.S == 0) return 0;
     const bool grad = R.grad_loss != nullptr;
+    const size_t smem = refine_smem(R.m, R.p, R.rmax);  // <= 48 KB for rmax <= 64
     if (R.m == 3 && R.g == 3 && R.p == 7) {
-        if (grad) k_refine<3, 3, 7, true><<<nb, 128, 0, st>>>(R);
-        else k_refine<3, 3, 7, false><<<nb, 128, 0, st>>>(R);
+        if (grad) k_refine<3, 3, 7, true><<<nb, sb, smem, st>>>(R);
+        else k_refine<3, 3, 7, false><<<nb, sb, smem, st>>>(R);
     } else if (R.m == 2 && R.g == 2 && R.p == 5) {
-        if (grad) k_refine<2, 2, 5, true><<<nb, 128, 0, st>>>(R);
-        else k_refine<2, 2, 5, false><<<nb, 128, 0, st>>>(R);
+        if (grad) k_refine<2, 2, 5, true><<<nb, sb, smem, st>>>(R);
+        else k_refine<2, 2, 5, false><<<nb, sb, smem, st>>>(R);
     } else {
         return (int)cudaErrorInvalidValue;
     }

@@ -213,8 +213,9 @@ def model_tables(gamma: int, degree: int, T: Sequence[float], interior: str = "e
 
 
 def measure_lane_rate(mix: int = 0, iters: int = 1 << 16) -> dict:
-    """Sustained FP32 lane operations per second on the current device
-    (mix 0: add + |.|-max, the reach/free row pattern; 1: fused multiply-add)."""
+    """Sustained lane operations per second on the current device (mix 0: FP32
+    add + |.|-max, the reach/free row pattern; 1: FP32 fused multiply-add; 2, 3:
+    the same in FP64)."""
     lib = load()
     r, ms = ctypes.c_double(), ctypes.c_double()
     rc = lib.plan_measure_lane_rate(int(mix), int(iters), ctypes.byref(r), ctypes.byref(ms))
@@ -752,8 +753,8 @@ class Replanner:
 
     One tick is in flight at a time: the pinned staging buffers feed the
     tick's host-to-device copies, so a tick_async issued before the previous
-    tick has finished first waits for it (its result buffers then hold the
-    newer tick's path once that one completes)."""
+    tick's result() first waits for that tick and drops its result (status
+    and path); result() then reports the newer tick alone."""
 
     def __init__(self, planner: "Planner", dp: DeviceProblem, graph: Graph, n_max: int, rows_max: int,
                  path_cap: Optional[int] = None, warm: bool = True):
@@ -784,12 +785,11 @@ class Replanner:
         self.h_len = torch.zeros(1, dtype=torch.int32).pin_memory()
         self.h_cost = torch.zeros(1, dtype=torch.float64).pin_memory()
         self.cg = None
-        self._done = torch.cuda.Event()
         self._inflight = False
 
     def _stage(self, obstacles, start_pos, goal_pos) -> None:
         if self._inflight:           # the previous tick's copies still read the staging buffers
-            self._done.synchronize()
+            self.pl.wait()           # ... and its device status must not mix with the next tick's
             self._inflight = False
         off = np.asarray(obstacles.off, dtype=np.int64)
         n = off.shape[0] - 1
@@ -847,12 +847,12 @@ class Replanner:
         self._stage(obstacles, start_pos, goal_pos)
         with torch.cuda.stream(self.pl.stream):
             self.cg.replay()
-            self._done.record(self.pl.stream)
         self._inflight = True
 
     def result(self) -> dict:
         """Waits for the tick; status, path (host list) and cost."""
         st = self.pl.wait()
+        self._inflight = False
         L = int(self.h_len.item())
         return {"status": st, "path": self.h_path[:L].tolist() if st == PLAN_OK else None,
                 "cost": float(self.h_cost.item()), "edges": int(self.out.count.item()), "info": self.pl.info()}

@@ -203,8 +203,9 @@ def test_warm_start_after_a_stopped_call_on_the_cooperative_kernel(N, width):
 
 def test_back_to_back_ticks_keep_one_in_flight():
     """Two tick_async calls without result() in between: the second waits for
-    the first tick's copies before it rewrites the staging buffers, and the
-    result equals a direct tick on the second obstacles."""
+    the first tick before it rewrites the staging buffers and drops the first
+    tick's status, and the result equals a direct tick on the second
+    obstacles."""
     prob, obs = synth.keepout_2d(5, N=500, n_obst=50)
     pl, dp, g, ctx = setup(prob)
     pl2 = P.Planner.for_problem(prob, stream=pl.stream)
@@ -212,6 +213,8 @@ def test_back_to_back_ticks_keep_one_in_flight():
     rp.capture(obs, prob.start_pos, prob.goal_pos)
     rng = np.random.default_rng(9)
     obs2 = moved(obs, rng.normal(0.0, 0.05, size=(obs.n, 2)))
+    rp.tick(obs2, prob.start_pos, prob.goal_pos)      # sizes the cut's lists for both obstacle sets
+    rp.tick(obs, prob.start_pos, prob.goal_pos)
     rp.tick_async(obs, prob.start_pos, prob.goal_pos)
     rp.tick_async(obs2, prob.start_pos, prob.goal_pos)
     r = rp.result()
