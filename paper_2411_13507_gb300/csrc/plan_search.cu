@@ -1383,44 +1383,47 @@ int launch_search_batched(const BatchSearchParams& P, void* stream, int* launche
 }
 
 // ---------------------------------------------------------------------------
-// findPath on chip (Sec. III-C, Problem 2), for graphs of up to
-// SEARCH_CLUSTER_MAX_N vertices: the computation of k_search -- nearest start
-// and goal, Bellman-Ford sweeps to the fixed point (the minimum over paths of
-// the left-to-right rounded path sum), predecessor = minimum (dist[u], u) over
-// the in-neighbours attaining dist[v], the walk -- inside one thread-block
-// cluster, so that every sweep costs cluster barriers and shared-memory
-// traffic instead of grid barriers and L2 round trips:
+// findPath on chip (Sec. III-C, Problem 2), for graphs whose distances fit in
+// the shared memory of one thread-block cluster: the computation of k_search
+// -- nearest start and goal, Bellman-Ford sweeps to the fixed point (the
+// minimum over paths of the left-to-right rounded path sum), predecessor =
+// minimum (dist[u], u) over the in-neighbours attaining dist[v], the walk --
+// with cluster barriers and shared-memory traffic in place of grid barriers
+// and L2 round trips:
 //   - CTA r owns the vertices [r V, (r+1) V), V = ceil(N / C); it keeps the
 //     rows of its vertices in shared memory as far as they fit (the rest is
-//     read from global memory) and a copy of all N distances;
+//     read from global memory), a copy of all N distances and an array of N
+//     local candidates;
 //   - a sweep relaxes the out-edges of the owned frontier (vertices whose
-//     distance fell below the one they last relaxed from), edge-parallel; a
-//     candidate fl(d[u] + w) below the local copy of d[c] goes to c's owner by
-//     a distributed-shared-memory atomicMin (non-negative doubles order like
-//     their bit patterns); after a cluster barrier each owner takes its
-//     candidates that improve, writes them into every CTA's copy and raises
-//     its flag; a second cluster barrier ends the sweep;
-//   - predecessors: owners of reached u test their out-edges (u -> c) for
-//     fl(d[u] + w) = d[c] and send the minimum d[u] to c's owner, then, after
-//     a barrier, the minimum u among those attaining it;
-//   - the owners store their predecessors into CTA 0, which walks goal -> start.
+//     distance fell below the one they last relaxed from), edge-parallel,
+//     into the CTA's own candidate array with shared-memory atomicMin
+//     (non-negative doubles order like their bit patterns); after a cluster
+//     barrier each owner reads the C candidates of each of its vertices with
+//     distributed-shared-memory loads, writes an improvement into every CTA's
+//     distance copy and raises its flag; a second cluster barrier ends the
+//     sweep.  Only loads and stores cross CTAs, no atomics;
+//   - predecessors: the same gather for the minimum d[u] over the tight
+//     in-edges (fl(d[u] + w) = d[c], from the local copy), then for the
+//     minimum u among those attaining it;
+//   - CTA 0 collects the predecessors and walks goal -> start.
 // Every copy entry has one writer (its owner) and is written only between the
-// two barriers of a sweep, when nothing reads it.  Every exit and barrier is
-// taken on values identical in every CTA (edge count, start, goal, sweep
-// count, gathered flags), so all CTAs reach every cluster barrier.
+// two barriers of a sweep, when nothing reads it; a candidate array is
+// written only by its CTA and read by others only between barriers.  Every
+// exit and barrier is taken on values identical in every CTA (edge count,
+// start, goal, sweep count, gathered flags), so all CTAs reach every cluster
+// barrier.
 // ---------------------------------------------------------------------------
 constexpr int SEARCH_CLUSTER_MAX_N = 12288;
 
 namespace {
-DEVI void cl_red_min_u64(unsigned a, unsigned long long v) {
-    asm volatile("red.relaxed.cluster.shared::cluster.min.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
-}
-DEVI void cl_red_min_u32(unsigned a, unsigned v) {
-    asm volatile("red.relaxed.cluster.shared::cluster.min.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
 DEVI unsigned long long cl_ld_u64(unsigned a) {
     unsigned long long v;
     asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+    return v;
+}
+DEVI unsigned cl_ld_u32(unsigned a) {
+    unsigned v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
     return v;
 }
 }  // namespace
@@ -1429,11 +1432,10 @@ __global__ void __launch_bounds__(1024, 1) k_search_cluster(SearchParams P, int 
     extern __shared__ __align__(16) unsigned char s_raw[];
     __shared__ unsigned long long s_near[TO_CL_MAX][4];   // per CTA: start bits, id, goal bits, id
     __shared__ int s_flag[2][TO_CL_MAX];
-    __shared__ unsigned s_rb_d[TO_CL_MAX], s_rb_cand[TO_CL_MAX], s_rb_best[TO_CL_MAX], s_rb_pred[TO_CL_MAX];
+    __shared__ unsigned s_rb_d[TO_CL_MAX], s_rb_loc[TO_CL_MAX], s_rb_best[TO_CL_MAX], s_rb_last[TO_CL_MAX];
     __shared__ unsigned long long s_kb[2][32];
     __shared__ int s_ki[2][32];
     __shared__ int s_se[2], s_bad, s_nf;
-    __shared__ unsigned long long s_dgoal;
     __shared__ int s_v[1024], s_e0[1024], s_pre[1025], s_wsum[33];
     __shared__ unsigned long long s_dv[1024];
     const int N = P.N, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nt = blockDim.x;
@@ -1442,21 +1444,21 @@ __global__ void __launch_bounds__(1024, 1) k_search_cluster(SearchParams P, int 
     const int v0 = min(N, (int)rank * V), v1 = min(N, v0 + V), nv = v1 - v0;
     const int ws = P.w_f64 ? 8 : 4;
     unsigned long long* s_d = (unsigned long long*)s_raw;       // [N] distance bits (copy)
-    unsigned long long* s_cand = s_d + N;                       // [V] best candidate of owned vertex
-    unsigned long long* s_last = s_cand + V;                    // [V] distance it last relaxed from
+    unsigned long long* s_loc = s_d + N;                        // [N] this CTA's candidates
+    unsigned long long* s_last = s_loc + N;                     // [V] distance an owned vertex last relaxed from
     unsigned long long* s_best = s_last + V;                    // [V] minimum d[u] of attaining in-neighbours
-    unsigned* s_pred = (unsigned*)(s_best + V);                 // [V]
-    int* s_ro = (int*)(s_pred + V);                             // [V+1] owned row offsets (local)
+    int* s_ro = (int*)(s_best + V);                             // [V+1] owned row offsets (local)
     int* s_col = s_ro + (V + 1);                                // [ecap]
     unsigned char* s_w = (unsigned char*)(((uintptr_t)(s_col + ecap) + 7) & ~(uintptr_t)7);  // [ecap] weights
+    unsigned* s_locu = (unsigned*)s_loc;                        // the candidate array as u32 [N] (predecessors)
     DevInfo* info = P.info;
 
     cl_sync();  // every CTA of the cluster is running before any remote access
     if (tid < (int)C) {
         s_rb_d[tid] = cl_map(smem_addr(s_d), tid);
-        s_rb_cand[tid] = cl_map(smem_addr(s_cand), tid);
+        s_rb_loc[tid] = cl_map(smem_addr(s_loc), tid);
         s_rb_best[tid] = cl_map(smem_addr(s_best), tid);
-        s_rb_pred[tid] = cl_map(smem_addr(s_pred), tid);
+        s_rb_last[tid] = cl_map(smem_addr(s_last), tid);
     }
     if (tid == 0) {
         const long long E = *P.count;
@@ -1478,13 +1480,11 @@ __global__ void __launch_bounds__(1024, 1) k_search_cluster(SearchParams P, int 
         if (ws == 8) ((double*)s_w)[i] = __ldg(&((const double*)P.w)[eb + i]);
         else ((float*)s_w)[i] = __ldg(&((const float*)P.w)[eb + i]);
     }
-    for (int v = tid; v < N; v += nt) s_d[v] = DINF;
-    for (int k = tid; k < nv; k += nt) {
-        s_cand[k] = DINF;
-        s_last[k] = DINF;
-        s_best[k] = ~0ull;
-        s_pred[k] = 0x7fffffffu;
+    for (int v = tid; v < N; v += nt) {
+        s_d[v] = DINF;
+        s_loc[v] = DINF;
     }
+    for (int k = tid; k < nv; k += nt) s_last[k] = DINF;
     double sp[4], gp[4];
     for (int a = 0; a < 4; ++a) {
         sp[a] = P.endpoints ? (a < P.m ? P.endpoints[a] : 0.0) : P.start[a];
@@ -1545,12 +1545,39 @@ __global__ void __launch_bounds__(1024, 1) k_search_cluster(SearchParams P, int 
     if (tid == 0) s_d[start] = 0ull;  // every CTA's own copy
     __syncthreads();
 
-    // phase 2: sweeps
     auto weight = [&](int i) -> double {  // owned edge i (local index)
         if (i < nloc) return ws == 8 ? ((const double*)s_w)[i] : (double)((const float*)s_w)[i];
         return ws == 8 ? __ldg(&((const double*)P.w)[eb + i]) : (double)__ldg(&((const float*)P.w)[eb + i]);
     };
     auto column = [&](int i) -> int { return i < nloc ? s_col[i] : __ldg(&P.col[eb + i]); };
+    // Lists the owned vertices of [k0, k0 + nt) that pass `take` with their
+    // distance, and returns how many out-edges they have (block-uniform).
+    auto list_owned = [&](int k0, bool frontier) -> int {
+        if (tid == 0) s_nf = 0;
+        __syncthreads();
+        const int k = k0 + tid;
+        if (k < nv) {
+            const unsigned long long dv = s_d[v0 + k];
+            const int e0 = s_ro[k], e1 = s_ro[k + 1];
+            bool take = dv < DINF;
+            if (frontier) {
+                take = dv < s_last[k];
+                if (take) s_last[k] = dv;
+            }
+            if (take && e1 > e0) {
+                const int i = atomicAdd(&s_nf, 1);
+                s_v[i] = v0 + k;
+                s_e0[i] = e0;
+                s_pre[i] = e1 - e0;
+                s_dv[i] = dv;
+            }
+        }
+        __syncthreads();
+        const int nf = s_nf;
+        return nf == 0 ? 0 : block_scan_degrees(s_pre, nf, s_wsum);
+    };
+
+    // phase 2: sweeps
     int sweeps = 0;
     for (;;) {
         if (sweeps >= P.max_sweeps) {
@@ -1560,27 +1587,8 @@ __global__ void __launch_bounds__(1024, 1) k_search_cluster(SearchParams P, int 
         const int par = sweeps & 1;
         ++sweeps;
         for (int k0 = 0; k0 < nv; k0 += nt) {
-            if (tid == 0) s_nf = 0;
-            __syncthreads();
-            const int k = k0 + tid;
-            if (k < nv) {
-                const unsigned long long dv = s_d[v0 + k];
-                if (dv < s_last[k]) {
-                    s_last[k] = dv;
-                    const int e0 = s_ro[k], e1 = s_ro[k + 1];
-                    if (e1 > e0) {
-                        const int i = atomicAdd(&s_nf, 1);
-                        s_v[i] = v0 + k;
-                        s_e0[i] = e0;
-                        s_pre[i] = e1 - e0;
-                        s_dv[i] = dv;
-                    }
-                }
-            }
-            __syncthreads();
+            const int tot = list_owned(k0, true);
             const int nf = s_nf;
-            if (nf == 0) continue;
-            const int tot = block_scan_degrees(s_pre, nf, s_wsum);
             for (int q = tid; q < tot; q += nt) {
                 const int i = find_entry(s_pre, nf, q);
                 const int e = s_e0[i] + (q - s_pre[i]);
@@ -1588,19 +1596,21 @@ __global__ void __launch_bounds__(1024, 1) k_search_cluster(SearchParams P, int 
                 if (c < 0 || c >= N) continue;
                 const unsigned long long x = (unsigned long long)__double_as_longlong(
                     __dadd_rn(__longlong_as_double((long long)s_dv[i]), weight(e)));
-                if (x < ((volatile unsigned long long*)s_d)[c]) {
-                    const unsigned o = (unsigned)(c / V);
-                    cl_red_min_u64(s_rb_cand[o] + 8u * (unsigned)(c - (int)o * V), x);
-                }
+                if (x < s_d[c] && x < ((volatile unsigned long long*)s_loc)[c]) atomicMin(&s_loc[c], x);
             }
             __syncthreads();  // the lists are rebuilt by the next chunk
         }
-        cl_sync();  // every candidate has reached its owner
+        cl_sync();  // every CTA's candidates are complete
         int changed = 0;
         for (int k = tid; k < nv; k += nt) {
-            const unsigned long long x = s_cand[k];
-            if (x < s_d[v0 + k]) {
-                for (unsigned q = 0; q < C; ++q) cl_st_u64(s_rb_d[q] + 8u * (unsigned)(v0 + k), x);
+            const unsigned off = 8u * (unsigned)(v0 + k);
+            unsigned long long m = ~0ull;
+            for (unsigned q = 0; q < C; ++q) {
+                const unsigned long long x = cl_ld_u64(s_rb_loc[q] + off);
+                m = x < m ? x : m;
+            }
+            if (m < s_d[v0 + k]) {
+                for (unsigned q = 0; q < C; ++q) cl_st_u64(s_rb_d[q] + off, m);
                 changed = 1;
             }
         }
@@ -1612,28 +1622,18 @@ __global__ void __launch_bounds__(1024, 1) k_search_cluster(SearchParams P, int 
         if (!any) break;
     }
 
-    // phase 3: predecessors (two passes over the out-edges of reached owned vertices)
-    if (tid == 0) s_dgoal = s_d[goal];
+    // phase 3: predecessors.  Pass 0: minimum d[u] over the tight in-edges of
+    // every vertex, gathered into s_best by its owner; pass 1: minimum u among
+    // those attaining it, gathered into s_last (as u32) by the owner.
     for (int pass = 0; pass < 2; ++pass) {
+        for (int v = tid; v < N; v += nt) {
+            if (pass == 0) s_loc[v] = ~0ull;
+            else s_locu[v] = 0x7fffffffu;
+        }
+        __syncthreads();
         for (int k0 = 0; k0 < nv; k0 += nt) {
-            if (tid == 0) s_nf = 0;
-            __syncthreads();
-            const int k = k0 + tid;
-            if (k < nv) {
-                const unsigned long long dv = s_d[v0 + k];
-                const int e0 = s_ro[k], e1 = s_ro[k + 1];
-                if (dv < DINF && e1 > e0) {
-                    const int i = atomicAdd(&s_nf, 1);
-                    s_v[i] = v0 + k;
-                    s_e0[i] = e0;
-                    s_pre[i] = e1 - e0;
-                    s_dv[i] = dv;
-                }
-            }
-            __syncthreads();
+            const int tot = list_owned(k0, false);
             const int nf = s_nf;
-            if (nf == 0) continue;
-            const int tot = block_scan_degrees(s_pre, nf, s_wsum);
             for (int q = tid; q < tot; q += nt) {
                 const int i = find_entry(s_pre, nf, q);
                 const int e = s_e0[i] + (q - s_pre[i]);
@@ -1643,25 +1643,54 @@ __global__ void __launch_bounds__(1024, 1) k_search_cluster(SearchParams P, int 
                 const unsigned long long x =
                     (unsigned long long)__double_as_longlong(__dadd_rn(__longlong_as_double((long long)dvb), weight(e)));
                 if (x != s_d[c]) continue;
-                const unsigned o = (unsigned)(c / V), off = 8u * (unsigned)(c - (int)o * V);
-                if (pass == 0) cl_red_min_u64(s_rb_best[o] + off, dvb);
-                else if (cl_ld_u64(s_rb_best[o] + off) == dvb) cl_red_min_u32(s_rb_pred[o] + off / 2, (unsigned)s_v[i]);
+                if (pass == 0) {
+                    atomicMin(&s_loc[c], dvb);
+                } else {
+                    const unsigned o = (unsigned)(c / V);
+                    if (cl_ld_u64(s_rb_best[o] + 8u * (unsigned)(c - (int)o * V)) == dvb)
+                        atomicMin(&s_locu[c], (unsigned)s_v[i]);
+                }
             }
             __syncthreads();
         }
-        cl_sync();
+        cl_sync();  // every CTA's candidates are complete
+        for (int k = tid; k < nv; k += nt) {
+            const unsigned v = (unsigned)(v0 + k);
+            if (pass == 0) {
+                unsigned long long m = ~0ull;
+                for (unsigned q = 0; q < C; ++q) {
+                    const unsigned long long x = cl_ld_u64(s_rb_loc[q] + 8u * v);
+                    m = x < m ? x : m;
+                }
+                s_best[k] = m;
+            } else {
+                unsigned m = 0x7fffffffu;
+                for (unsigned q = 0; q < C; ++q) {
+                    const unsigned x = cl_ld_u32(s_rb_loc[q] + 4u * v);
+                    m = x < m ? x : m;
+                }
+                s_last[k] = m;
+            }
+        }
+        cl_sync();  // gathered before the candidate arrays are reset or read
     }
 
-    // phase 4: predecessors into CTA 0 (over its distance copy, no longer read), then the walk
-    const unsigned walk0 = cl_map(smem_addr(s_d), 0);
-    for (int k = tid; k < nv; k += nt) cl_st_u32(walk0 + 4u * (unsigned)(v0 + k), s_pred[k]);
-    cl_sync();
-    if (rank != 0 || tid != 0) return;
-    const unsigned* pr = (const unsigned*)s_d;
+    // phase 4: CTA 0 collects the predecessors (over its candidate array) and walks
+    if (rank == 0) {
+        for (int v = tid; v < N; v += nt) {
+            const unsigned o = (unsigned)(v / V);
+            s_locu[v] = (unsigned)cl_ld_u64(s_rb_last[o] + 8u * (unsigned)(v - (int)o * V));
+        }
+    }
+    cl_sync();  // the owners stay until CTA 0 has read their predecessors
+    if (rank != 0) return;
+    __syncthreads();
+    if (tid != 0) return;
+    const unsigned* pr = s_locu;
     info->start = start;
     info->goal = goal;
     info->search_iters = (unsigned long long)sweeps;
-    const unsigned long long dg = s_dgoal;
+    const unsigned long long dg = s_d[goal];
     if (dg >= DINF) {
         *P.path_len = 0;
         *P.cost = __longlong_as_double((long long)DINF);
@@ -1702,7 +1731,7 @@ namespace {
 // cached edges a CTA and ws-byte weights.
 size_t search_cluster_smem(int N, int C, int ecap, int ws) {
     const int V = (N + C - 1) / C;
-    size_t b = (size_t)8 * N + (size_t)8 * 3 * V + (size_t)4 * V + (size_t)4 * (V + 1) + (size_t)4 * ecap;
+    size_t b = (size_t)16 * N + (size_t)8 * 2 * V + (size_t)4 * (V + 1) + (size_t)4 * ecap;
     b = (b + 7) & ~(size_t)7;
     return b + (size_t)ws * ecap;
 }
