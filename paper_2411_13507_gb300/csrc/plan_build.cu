@@ -1422,10 +1422,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                 const int li = v >> 8, lj = v & 255;
                 const float* ul = UL + li * SU;
                 const float* ur = UR + lj * SU;
-                const float bandR = KR * (magR[li] + magR[T + lj]);
                 float r4[4] = {0.f, 0.f, 0.f, 0.f};
-                // a pair that certainly fails stops loading its rows (the
-                // lanes still running then issue fewer shared-memory wavefronts)
 #pragma unroll
                 for (int qd = 0; qd < RQ; ++qd) {
                     const float4 a = *reinterpret_cast<const float4*>(ul + 4 * qd);
@@ -1434,9 +1431,9 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                     r4[1] = fmaxf(r4[1], fabsf(a.y + b.y));
                     r4[2] = fmaxf(r4[2], fabsf(a.z + b.z));
                     r4[3] = fmaxf(r4[3], fabsf(a.w + b.w));
-                    if ((qd & 1) && qd + 1 < RQ && fmaxf(fmaxf(r4[0], r4[1]), fmaxf(r4[2], r4[3])) > 1.f + bandR) break;
                 }
                 const float rm = fmaxf(fmaxf(r4[0], r4[1]), fmaxf(r4[2], r4[3]));
+                const float bandR = KR * (magR[li] + magR[T + lj]);
                 int outcome = 0;  // 0 certain failure, 1 certainly feasible, 2 ambiguous
                 if (rm <= 1.f + bandR) {
                     const bool rpass = rm <= 1.f - bandR;

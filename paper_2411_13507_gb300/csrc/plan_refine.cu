@@ -1,4 +1,4 @@
-// Differentiable refinement objective for sm_103a: four lanes per Bezier
+// Differentiable refinement objective for sm_103a: one thread per Bezier
 // segment, forward (loss) and hand-written backward (d loss / d control points
 // and d loss / d T) of
 //
@@ -66,152 +66,80 @@ DEVI void adj_diff(float (&g)[8][M], int len) {
 
 }  // namespace
 
-// Four lanes per segment, 32 segments per 128-thread block.  The reach rows
-// and the snap energy separate over the axes (Theorem 1 per axis; the
-// integral of the squared fourth derivative is the sum of the axes'
-// integrals), so lane a < m takes axis a of both; the free rows mix the axes,
-// and lane q takes rows q, q + 4, ... of the polytope.  The segment's control
-// points, rows and bounds are staged in shared memory by coalesced loads; the
-// lanes' partial losses and gradients are summed with shuffles inside the
-// group of four.
-constexpr int REF_LANES = 4;
-constexpr int REF_SEGS = 32;   // segments per block
-
 template <int M, int G, int PD, bool GRAD>
-__global__ void __launch_bounds__(REF_LANES * REF_SEGS) k_refine(RefineParams R) {
+__global__ void __launch_bounds__(128) k_refine(RefineParams R) {
     constexpr int L = PD + 1;
-    constexpr int NP = L * M;
-    static_assert(M <= REF_LANES, "one lane per axis");
-    extern __shared__ float smr[];
-    const int NA = R.rmax * M;
-    float* sP = smr;                    // [REF_SEGS][NP]
-    float* sA = sP + REF_SEGS * NP;     // [REF_SEGS][NA]
-    float* sb = sA + REF_SEGS * NA;     // [REF_SEGS][rmax]
-    const long long s0 = blockIdx.x * (long long)REF_SEGS;
-    const int nseg = (int)min((long long)REF_SEGS, R.S - s0);
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    for (int u = tid; u < nseg * NP; u += nthr) sP[u] = R.P[s0 * NP + u];
-    for (int u = tid; u < nseg * NA; u += nthr) sA[u] = R.A[s0 * NA + u];
-    for (int u = tid; u < nseg * R.rmax; u += nthr) sb[u] = R.b[s0 * R.rmax + u];
-    __syncthreads();
-    const int lane = tid & (REF_LANES - 1), sl = tid / REF_LANES;
-    const long long s = s0 + sl;
-    const bool live = sl < nseg;
-    const float* Ps = sP + sl * NP;
-    const float T = live ? R.T[s] : 1.f;
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= R.S) return;
+    float P[8][M];
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+#pragma unroll
+        for (int a = 0; a < M; ++a) P[l][a] = R.P[(s * L + l) * M + a];
+    const float T = R.T[s];
     const float Ti = 1.f / T;
     const float mu = R.mu, delta = R.delta, ld = logf(R.delta), ws = R.w_snap;
-    const float up = (GRAD && live) ? R.grad_loss[s] : 1.f;
+    const float up = GRAD ? R.grad_loss[s] : 1.f;
     float loss = 0.f, dT = 0.f;
-    float dP[8][M];  // this lane's share of d loss / d P
+    float dP[8][M];
 #pragma unroll
     for (int l = 0; l < 8; ++l)
 #pragma unroll
         for (int a = 0; a < M; ++a) dP[l][a] = 0.f;
 
-    if (live && lane < M) {
-        const int a = lane;
-        float Pa[8];
+    // reach margins
 #pragma unroll
-        for (int l = 0; l < 8; ++l) Pa[l] = l < L ? Ps[l * M + a] : 0.f;
-        float ga[8];  // gradient of this axis' reach and snap terms
+    for (int k = 1; k <= G; ++k) {
+        float d[8][M];
 #pragma unroll
-        for (int l = 0; l < 8; ++l) ga[l] = 0.f;
-        // reach margins of axis a
+        for (int l = 0; l < 8; ++l)
 #pragma unroll
-        for (int k = 1; k <= G; ++k) {
-            float d[8][1];
+            for (int a = 0; a < M; ++a) d[l][a] = l < L ? P[l][a] : 0.f;
 #pragma unroll
-            for (int l = 0; l < 8; ++l) d[l][0] = Pa[l];
+        for (int it = 0; it < k; ++it) fwd_diff<M, L>(d, L - it);
+        float sk = fact_f(PD) / fact_f(PD - k);
 #pragma unroll
-            for (int it = 0; it < k; ++it) fwd_diff<1, L>(d, L - it);
-            float sk = fact_f(PD) / fact_f(PD - k);
+        for (int it = 0; it < k; ++it) sk *= Ti;
+        const float ck = R.bound[k - 1];
+        const int nk = L - k;
+        float g[8][M];
 #pragma unroll
-            for (int it = 0; it < k; ++it) sk *= Ti;
-            const float ck = R.bound[k - 1];
-            const int nk = L - k;
-            float g[8][1];
+        for (int j = 0; j < 8; ++j)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                g[j][0] = 0.f;
+            for (int a = 0; a < M; ++a) {
+                g[j][a] = 0.f;
                 if (j < nk) {
-                    const float Q = sk * d[j][0];
+                    const float Q = sk * d[j][a];
                     const float m1 = ck - Q, m2 = ck + Q;
                     loss += mu * (phi_f(m1, delta, ld) + phi_f(m2, delta, ld));
                     if (GRAD) {
                         const float gQ = mu * (dphi_f(m2, delta) - dphi_f(m1, delta)) * up;
-                        g[j][0] = gQ * sk;
+                        g[j][a] = gQ * sk;
                         dT += gQ * Q * (-(float)k) * Ti;
                     }
                 }
             }
-            if (GRAD) {
-#pragma unroll
-                for (int it = k; it >= 1; --it) adj_diff<1, L>(g, L - it);
-#pragma unroll
-                for (int l = 0; l < L; ++l) ga[l] += g[l][0];
-            }
-        }
-        // snap energy of axis a
-        {
-            constexpr int q = PD - 4;
-            float d4[8][1];
-#pragma unroll
-            for (int l = 0; l < 8; ++l) d4[l][0] = Pa[l];
-#pragma unroll
-            for (int it = 0; it < 4; ++it) fwd_diff<1, L>(d4, L - it);
-            float c = fact_f(PD) / fact_f(PD - 4);
-            c = c * c;
-            float t7 = Ti * Ti * Ti;
-            t7 = t7 * t7 * Ti;
-            c *= t7;
-            float quad = 0.f;
-            float gd[8][1];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) gd[j][0] = 0.f;
-#pragma unroll
-            for (int j = 0; j <= q; ++j)
-#pragma unroll
-                for (int l = 0; l <= q; ++l) {
-                    const float Gjl = (float)(comb_i(q, j) * comb_i(q, l)) / (float)((2 * q + 1) * comb_i(2 * q, j + l));
-                    quad = fmaf(Gjl * d4[j][0], d4[l][0], quad);
-                    if (GRAD) gd[j][0] = fmaf(Gjl, d4[l][0], gd[j][0]);
-                }
-            const float J = c * quad;
-            loss += ws * J;
-            if (GRAD) {
-                const float f = ws * c * 2.f * up;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) gd[j][0] = (j <= q) ? gd[j][0] * f : 0.f;
-#pragma unroll
-                for (int it = 4; it >= 1; --it) adj_diff<1, L>(gd, L - it);
-#pragma unroll
-                for (int l = 0; l < L; ++l) ga[l] += gd[l][0];
-                dT += ws * (-7.f) * J * Ti * up;
-            }
-        }
         if (GRAD) {
+#pragma unroll
+            for (int it = k; it >= 1; --it) adj_diff<M, L>(g, L - it);
 #pragma unroll
             for (int l = 0; l < L; ++l)
 #pragma unroll
-                for (int b = 0; b < M; ++b)
-                    if (b == a) dP[l][b] += ga[l];
+                for (int a = 0; a < M; ++a) dP[l][a] += g[l][a];
         }
     }
-    // free-space margins of the interior control points: rows lane, lane + 4, ...
-    const int nr = live ? min(R.nrows[s], R.rmax) : 0;
-    const float* As = sA + sl * NA;
-    const float* bs = sb + sl * R.rmax;
-    for (int r = lane; r < nr; r += REF_LANES) {
+    // free-space margins of the interior control points
+    const int nr = min(R.nrows[s], R.rmax);
+    for (int r = 0; r < nr; ++r) {
         float Ar[M];
 #pragma unroll
-        for (int a = 0; a < M; ++a) Ar[a] = As[r * M + a];
-        const float br = bs[r];
+        for (int a = 0; a < M; ++a) Ar[a] = R.A[(s * R.rmax + r) * M + a];
+        const float br = R.b[s * R.rmax + r];
 #pragma unroll
         for (int l = 1; l < PD; ++l) {
             float dot = 0.f;
 #pragma unroll
-            for (int a = 0; a < M; ++a) dot = fmaf(Ar[a], Ps[l * M + a], dot);
+            for (int a = 0; a < M; ++a) dot = fmaf(Ar[a], P[l][a], dot);
             const float mg = br - dot;
             loss += mu * phi_f(mg, delta, ld);
             if (GRAD) {
@@ -221,55 +149,78 @@ __global__ void __launch_bounds__(REF_LANES * REF_SEGS) k_refine(RefineParams R)
             }
         }
     }
-    // sums over the four lanes of the segment (groups of four consecutive lanes)
+    // snap energy
+    {
+        constexpr int q = PD - 4;
+        float d4[8][M];
 #pragma unroll
-    for (int o = 1; o < REF_LANES; o <<= 1) {
-        loss += __shfl_xor_sync(0xffffffffu, loss, o);
+        for (int l = 0; l < 8; ++l)
+#pragma unroll
+            for (int a = 0; a < M; ++a) d4[l][a] = l < L ? P[l][a] : 0.f;
+#pragma unroll
+        for (int it = 0; it < 4; ++it) fwd_diff<M, L>(d4, L - it);
+        float c = fact_f(PD) / fact_f(PD - 4);
+        c = c * c;
+        float t7 = Ti * Ti * Ti;
+        t7 = t7 * t7 * Ti;
+        c *= t7;
+        float quad = 0.f;
+        float gd[8][M];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int a = 0; a < M; ++a) gd[j][a] = 0.f;
+#pragma unroll
+        for (int j = 0; j <= q; ++j)
+#pragma unroll
+            for (int l = 0; l <= q; ++l) {
+                const float Gjl = (float)(comb_i(q, j) * comb_i(q, l)) / (float)((2 * q + 1) * comb_i(2 * q, j + l));
+#pragma unroll
+                for (int a = 0; a < M; ++a) {
+                    quad = fmaf(Gjl * d4[j][a], d4[l][a], quad);
+                    if (GRAD) gd[j][a] = fmaf(Gjl, d4[l][a], gd[j][a]);
+                }
+            }
+        const float J = c * quad;
+        loss += ws * J;
         if (GRAD) {
-            dT += __shfl_xor_sync(0xffffffffu, dT, o);
+            const float f = ws * c * 2.f * up;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+#pragma unroll
+                for (int a = 0; a < M; ++a) gd[j][a] = (j <= q) ? gd[j][a] * f : 0.f;
+#pragma unroll
+            for (int it = 4; it >= 1; --it) adj_diff<M, L>(gd, L - it);
 #pragma unroll
             for (int l = 0; l < L; ++l)
 #pragma unroll
-                for (int a = 0; a < M; ++a) dP[l][a] += __shfl_xor_sync(0xffffffffu, dP[l][a], o);
+                for (int a = 0; a < M; ++a) dP[l][a] += gd[l][a];
+            dT += ws * (-7.f) * J * Ti * up;
         }
     }
-    if (live && lane == 0) {
-        if (R.loss) R.loss[s] = loss;
-        if (GRAD) R.dT[s] = dT;
-    }
+    if (R.loss) R.loss[s] = loss;
     if (GRAD) {
-        __syncthreads();  // every lane has read its rows of sP
-        if (live && lane == 0) {
 #pragma unroll
-            for (int l = 0; l < L; ++l)
+        for (int l = 0; l < L; ++l)
 #pragma unroll
-                for (int a = 0; a < M; ++a) sP[sl * NP + l * M + a] = dP[l][a];
-        }
-        __syncthreads();
-        for (int u = tid; u < nseg * NP; u += nthr) R.dP[s0 * NP + u] = sP[u];
+            for (int a = 0; a < M; ++a) R.dP[(s * L + l) * M + a] = dP[l][a];
+        R.dT[s] = dT;
     }
-}
-
-// Dynamic shared memory of k_refine (<= 32 x (30 + 4 x 64) x 4 B = 36.6 KB).
-static size_t refine_smem(int m, int p, int rmax) {
-    return sizeof(float) * (size_t)REF_SEGS * ((p + 1) * m + rmax * m + rmax);
 }
 
 bool refine_supported(int m, int g, int p) { return (m == 3 && g == 3 && p == 7) || (m == 2 && g == 2 && p == 5); }
 
 int launch_refine(const RefineParams& R, void* stream, int* launches) {
     cudaStream_t st = (cudaStream_t)stream;
-    const unsigned nb = (unsigned)((R.S + REF_SEGS - 1) / REF_SEGS);
+    const unsigned nb = (unsigned)((R.S + 127) / 128);
     if (R.S == 0) return 0;
     const bool grad = R.grad_loss != nullptr;
-    const size_t smem = refine_smem(R.m, R.p, R.rmax);
-    const int nt = REF_LANES * REF_SEGS;
     if (R.m == 3 && R.g == 3 && R.p == 7) {
-        if (grad) k_refine<3, 3, 7, true><<<nb, nt, smem, st>>>(R);
-        else k_refine<3, 3, 7, false><<<nb, nt, smem, st>>>(R);
+        if (grad) k_refine<3, 3, 7, true><<<nb, 128, 0, st>>>(R);
+        else k_refine<3, 3, 7, false><<<nb, 128, 0, st>>>(R);
     } else if (R.m == 2 && R.g == 2 && R.p == 5) {
-        if (grad) k_refine<2, 2, 5, true><<<nb, nt, smem, st>>>(R);
-        else k_refine<2, 2, 5, false><<<nb, nt, smem, st>>>(R);
+        if (grad) k_refine<2, 2, 5, true><<<nb, 128, 0, st>>>(R);
+        else k_refine<2, 2, 5, false><<<nb, 128, 0, st>>>(R);
     } else {
         return (int)cudaErrorInvalidValue;
     }

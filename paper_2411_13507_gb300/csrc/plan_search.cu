@@ -1383,8 +1383,8 @@ int launch_search_batched(const BatchSearchParams& P, void* stream, int* launche
 }
 
 // ---------------------------------------------------------------------------
-// findPath on chip (Sec. III-C, Problem 2), for graphs whose distances fit in
-// the shared memory of one thread-block cluster: the computation of k_search
+// findPath on chip (Sec. III-C, Problem 2), for graphs whose distances and
+// (most of whose) rows fit in the shared memory of one thread-block cluster: the computation of k_search
 // -- nearest start and goal, Bellman-Ford sweeps to the fixed point (the
 // minimum over paths of the left-to-right rounded path sum), predecessor =
 // minimum (dist[u], u) over the in-neighbours attaining dist[v], the walk --
@@ -1781,9 +1781,13 @@ bool launch_search_cluster(const SearchParams& P, cudaStream_t st, int* launches
     const int dyn = g_scl[dev].optin - 32768;
     const size_t base = search_cluster_smem(P.N, C, 0, ws);
     if ((long long)base + 64 > dyn) return false;
-    // owned edges a CTA keeps on chip: what fits, up to twice the even share of the capacity
+    // owned edges a CTA keeps on chip: what fits, up to twice the even share
+    // of the capacity.  Edges past it come from global memory, one load at a
+    // time for the 16 SMs of the cluster -- much slower than the cooperative
+    // kernel's 152 -- so only graphs whose rows mostly fit go on chip.
     long long ecap = ((long long)dyn - (long long)base - 16) / (4 + ws);
     const long long even = (P.cap + C - 1) / C;
+    if (ecap < even / 2 + 64) return false;
     if (ecap > 2 * even + 64) ecap = 2 * even + 64;
     if (ecap > (1 << 30)) ecap = 1 << 30;
     const int ec = (int)ecap;
