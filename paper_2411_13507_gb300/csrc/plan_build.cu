@@ -574,6 +574,8 @@ __global__ void k_zero_slots(BuildParams P) {
     }
 }
 
+constexpr int RECHECK_THREADS = 128;  // four warps (one FP64 unit each) per re-check entry
+
 // Re-check entry: cost-only flag (1 bit) | query (16 bits) | polytope (10) | li (16) | lj (16) | T (5).
 // Bit 63 marks a check that is certainly feasible and needs only its cost in
 // FP64 (an ill-conditioned FP32 cost).
@@ -2412,21 +2414,23 @@ __global__ void __launch_bounds__(256) k_pairs_f64(BuildParams P) {
 // FP64 (reach rows, then the interior control points against polytope k).
 // ---------------------------------------------------------------------------
 template <int M, int G, int PD>
-__global__ void k_recheck(BuildParams P) {
-    // one warp per entry, one warp per block so that entries spread over all
-    // SMs (GB300's FP64 rate per SM is low); lanes take the rows, each row in
-    // canonical order
+__global__ void __launch_bounds__(RECHECK_THREADS) k_recheck(BuildParams P) {
+    // one entry per block of four warps, blocks spread over all SMs: every
+    // sub-partition of an SM has its own FP64 unit and GB300's FP64 rate is
+    // low, so an entry's rows are split over the four (threads take the rows,
+    // each row in canonical order); the control-polygon segments' squared
+    // norms are then summed in canonical order by one thread per segment
     using S = Shape<G, PD>;
     constexpr int N_ = M * G, RAX = S::RAX, NI = S::NI, TG = S::TG;
+    __shared__ double s_v[PD * G * M];
+    __shared__ double s_seg[PD];
     long long n = 0;
     if (block_failed(P.info, &P.info->rechecks, &n)) return;
     n = min(n, P.recheckCap);
     const int DR = P.cost_mode == 1 ? 1 : G;
     const TabLayout L = P.L;
-    const int lane = threadIdx.x & 31;
-    const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long e = wid; e < n; e += nw) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (long long e = blockIdx.x; e < n; e += gridDim.x) {
         const unsigned long long en = P.recheck[e];
         const int t = (int)(en & 31ull), lj = (int)((en >> 5) & 0xFFFFull), li = (int)((en >> 21) & 0xFFFFull);
         const int k = (int)((en >> 37) & 0x3FFull), q = (int)((en >> 47) & 0xFFFFull);
@@ -2442,17 +2446,16 @@ __global__ void k_recheck(BuildParams P) {
             xj[c] = ldv(Q.states, j * N_ + c, P.in_f32);
         }
         const double* tb = P.tab64 + (long long)(Q.tabOff + t) * L.e_stride;
-        bool ok = true;
-        for (int u = cost_only ? RAX * M : lane; u < RAX * M; u += 32) {
+        int ok = 1;
+        for (int u = cost_only ? RAX * M : tid; u < RAX * M; u += nthr) {
             const int r = u / M, a = u % M;
             const double s = __dadd_rn(half_sum<G>(tb + L.e_H + r * TG, xi + a, M),
                                        half_sum<G>(tb + L.e_H + r * TG + G, xj + a, M));
-            if (!(fabs(s) <= P.lim64[reach_order<G, PD>(r) - 1])) ok = false;
+            if (!(fabs(s) <= P.lim64[reach_order<G, PD>(r) - 1])) ok = 0;
         }
-        ok = __all_sync(0xffffffffu, ok);
-        if (!ok) continue;
+        if (!__syncthreads_and(ok)) continue;
         const int r0 = Q.poly_off[k], nr = Q.poly_off[k + 1] - r0;
-        for (int u = cost_only ? NI * nr : lane; u < NI * nr; u += 32) {
+        for (int u = cost_only ? NI * nr : tid; u < NI * nr; u += nthr) {
             const int l = 1 + u / nr, r = r0 + u % nr;
             double s = 0.0;
             for (int a = 0; a < M; ++a) {
@@ -2460,28 +2463,34 @@ __global__ void k_recheck(BuildParams P) {
                                             half_sum<G>(tb + L.e_D + l * TG + G, xj + a, M));
                 s = __dadd_rn(s, __dmul_rn(ldv(Q.A, (long long)r * M + a, P.in_f32), pa));
             }
-            if (!(s <= P.blim64[Q.rowsOff + r])) ok = false;
+            if (!(s <= P.blim64[Q.rowsOff + r])) ok = 0;
         }
-        ok = __all_sync(0xffffffffu, ok);
-        if (!ok) continue;
-        double seg = 0.0;  // lane l < PD: length of control-polygon segment l
-        if (lane < PD) {
+        if (!__syncthreads_and(ok)) continue;
+        // cost rows: value (l, d, a) of segment l, then each segment's squared
+        // norm summed in (d, a) order and its root, then the segments in order
+        for (int u = tid; u < PD * DR * M; u += nthr) {
+            const int l = u / (DR * M), d = (u / M) % DR, a = u % M;
+            s_v[u] = half_sum<G>(tb + L.e_C + (d * PD + l) * TG, xi + a, M) +
+                     half_sum<G>(tb + L.e_C + (d * PD + l) * TG + G, xj + a, M);
+        }
+        __syncthreads();
+        if (tid < PD) {
             double ss = 0.0;
-            for (int d = 0; d < DR; ++d)
-                for (int a = 0; a < M; ++a) {
-                    const double v = half_sum<G>(tb + L.e_C + (d * PD + lane) * TG, xi + a, M) +
-                                     half_sum<G>(tb + L.e_C + (d * PD + lane) * TG + G, xj + a, M);
-                    ss = fma(v, v, ss);
-                }
-            seg = sqrt(ss);
+            for (int w = 0; w < DR * M; ++w) {
+                const double v = s_v[tid * DR * M + w];
+                ss = fma(v, v, ss);
+            }
+            s_seg[tid] = sqrt(ss);
         }
-        double cost = 0.0;
-        for (int l = 0; l < PD; ++l) cost += __shfl_sync(0xffffffffu, seg, l);
-        if (lane == 0) {
+        __syncthreads();
+        if (tid == 0) {
+            double cost = 0.0;
+            for (int l = 0; l < PD; ++l) cost += s_seg[l];
             const long long slot = P.qSlot[q] + P.resOff[Q.kOff + k] + (long long)li * nk + lj;
             atomicOr(&P.resBits[slot], 1u << t);
             atomicMin(&P.resKey[slot], key_f32((float)cost, t));
         }
+        __syncthreads();  // s_v and s_seg are rewritten by the next entry
     }
 }
 
@@ -2563,7 +2572,7 @@ DEVI SegRef seg_of(const BuildParams& P, long long g) {
 // duration?  The owner slot receives the pair's result combined over all
 // shared polytopes; emitPre gets the inclusive prefix of the emitted flags
 // within the segment, and the segment total adds to row i's count.
-__global__ void k_emit(BuildParams P) {
+__global__ void __launch_bounds__(256, 4) k_emit(BuildParams P) {
     long long nseg = 0;
     if (block_failed(P.info, &P.info->memberships, &nseg)) return;
     const int lane = threadIdx.x & 31;
@@ -3055,7 +3064,7 @@ int launch_tc(const BuildParams& P, cudaStream_t st, int num_sms, int ctas_per_s
     k_pairs_tc<M, G, PD, BF><<<num_sms * occ, 256, sm, st>>>(P);
     if (e1) cudaEventRecord(e1, st);
     ++*launches;
-    k_recheck<M, G, PD><<<num_sms * 16, 32, 0, st>>>(P);
+    k_recheck<M, G, PD><<<num_sms * 8, RECHECK_THREADS, 0, st>>>(P);
     ++*launches;
     return (int)cudaGetLastError();
 }
@@ -3087,7 +3096,7 @@ int launch_pairs(const BuildParams& P, cudaStream_t st, int num_sms, int ctas_pe
         k_pairs_ws<M, G, PD><<<num_sms, 512, sm, st>>>(P);
         if (e1) cudaEventRecord(e1, st);
         ++*launches;
-        k_recheck<M, G, PD><<<num_sms * 16, 32, 0, st>>>(P);
+        k_recheck<M, G, PD><<<num_sms * 8, RECHECK_THREADS, 0, st>>>(P);
         ++*launches;
     } else {
         // pipeline 0: screened kernel; 2: every pair through all rows
@@ -3105,7 +3114,7 @@ int launch_pairs(const BuildParams& P, cudaStream_t st, int num_sms, int ctas_pe
         kern<<<num_sms * occ, threads, sm, st>>>(P);
         if (e1) cudaEventRecord(e1, st);
         ++*launches;
-        k_recheck<M, G, PD><<<num_sms * 16, 32, 0, st>>>(P);
+        k_recheck<M, G, PD><<<num_sms * 8, RECHECK_THREADS, 0, st>>>(P);
         ++*launches;
     }
     return (int)cudaGetLastError();

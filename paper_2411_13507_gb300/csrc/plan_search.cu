@@ -261,6 +261,11 @@ __global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
     // then relaxes the listed out-edges edge-parallel (thread q takes edge q
     // of the concatenated lists, found by binary search), with
     // non-returning atomicMin.
+    // A vertex whose distance is not below the goal's current distance does
+    // not relax its out-edges: nothing reached through it can improve a
+    // vertex closer than the goal (weights are non-negative), and those --
+    // every vertex of a shortest path to the goal and its predecessors -- are
+    // exactly what the path needs (Dijkstra stops once the goal is settled).
     volatile unsigned long long* vdist = P.dist;
     int it = 0;
     for (;;) {
@@ -272,11 +277,12 @@ __global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
             if (tid == 0) s_nf = 0;
             __syncthreads();
             const long long k = k0 + tid;
+            const unsigned long long gd = vdist[g];
             if (k < nown) {
                 const long long v = blockIdx.x + k * nb;
                 const bool cached = k < SEARCH_OWN_CAP;
                 const unsigned long long dvb = v == s ? 0ull : vdist[v];
-                if (dvb < (cached ? s_last[k] : P.last[v])) {
+                if (dvb < (cached ? s_last[k] : P.last[v]) && dvb < gd) {
                     if (cached) s_last[k] = dvb;
                     else P.last[v] = dvb;
                     if (v == s) vdist[v] = 0ull;
@@ -335,8 +341,10 @@ __global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
     }
 
     // phase 2: predecessor = minimum (dist[u], u) over in-neighbours attaining
-    // dist[v], in two passes over the out-edges of every reached vertex (same
+    // dist[v], in two passes over the out-edges of every vertex closer than
+    // the goal (the only possible predecessors on a path to it; same
     // ownership and edge-parallel layout as the sweeps)
+    const unsigned long long dgoal = vdist[g];
     for (int pass = 0; pass < 2; ++pass) {
         for (long long k0 = 0; k0 < nown; k0 += nt) {
             if (tid == 0) s_nf = 0;
@@ -348,7 +356,7 @@ __global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
                 const unsigned long long dvb = vdist[v];
                 const int e0 = cached ? s_ro[2 * k] : __ldg(&P.row_off[v]);
                 const int e1 = cached ? s_ro[2 * k + 1] : __ldg(&P.row_off[v + 1]);
-                if (dvb < DINF && e1 > e0) {
+                if (dvb < dgoal && e1 > e0) {
                     const int i = atomicAdd(&s_nf, 1);
                     s_v[i] = (int)v;
                     s_e0[i] = e0;
@@ -497,10 +505,12 @@ __global__ void __launch_bounds__(1024) k_search_batched(BatchSearchParams B) {
         if (tid == 0) s_changed = 0;
         __syncthreads();
         bool my_change = false;
+        const unsigned long long gd = vdist[g];   // vertices not closer than the goal do not relax
         for (int v = wid; v < N; v += nw) {
             if (!front[cur * N + v]) continue;
             __syncwarp();
             if (lane == 0) front[cur * N + v] = 0;
+            if (vdist[v] >= gd) continue;
             const double dv = __longlong_as_double((long long)vdist[v]);
             const long long e0 = Q.row_off[v], e1 = Q.row_off[v + 1];
             for (long long e = e0 + lane; e < e1; e += 32) {
@@ -530,10 +540,11 @@ __global__ void __launch_bounds__(1024) k_search_batched(BatchSearchParams B) {
         cur ^= 1;
         __syncthreads();
     }
+    const unsigned long long dgoal = vdist[g];
     for (int pass = 0; pass < 2; ++pass) {
         for (int v = wid; v < N; v += nw) {
             const unsigned long long dvb = vdist[v];
-            if (dvb >= DINF) continue;
+            if (dvb >= dgoal) continue;   // only vertices closer than the goal can precede path vertices
             const double dv = __longlong_as_double((long long)dvb);
             const long long e0 = Q.row_off[v], e1 = Q.row_off[v + 1];
             for (long long e = e0 + lane; e < e1; e += 32) {
@@ -1382,438 +1393,8 @@ int launch_search_batched(const BatchSearchParams& P, void* stream, int* launche
     return (int)cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// findPath on chip (Sec. III-C, Problem 2), for graphs whose distances and
-// (most of whose) rows fit in the shared memory of one thread-block cluster: the computation of k_search
-// -- nearest start and goal, Bellman-Ford sweeps to the fixed point (the
-// minimum over paths of the left-to-right rounded path sum), predecessor =
-// minimum (dist[u], u) over the in-neighbours attaining dist[v], the walk --
-// with cluster barriers and shared-memory traffic in place of grid barriers
-// and L2 round trips:
-//   - CTA r owns the vertices [r V, (r+1) V), V = ceil(N / C); it keeps the
-//     rows of its vertices in shared memory as far as they fit (the rest is
-//     read from global memory), a copy of all N distances and an array of N
-//     local candidates;
-//   - a sweep relaxes the out-edges of the owned frontier (vertices whose
-//     distance fell below the one they last relaxed from), edge-parallel,
-//     into the CTA's own candidate array with shared-memory atomicMin
-//     (non-negative doubles order like their bit patterns); after a cluster
-//     barrier each owner reads the C candidates of each of its vertices with
-//     distributed-shared-memory loads, writes an improvement into every CTA's
-//     distance copy and raises its flag; a second cluster barrier ends the
-//     sweep.  Only loads and stores cross CTAs, no atomics;
-//   - predecessors: the same gather for the minimum d[u] over the tight
-//     in-edges (fl(d[u] + w) = d[c], from the local copy), then for the
-//     minimum u among those attaining it;
-//   - CTA 0 collects the predecessors and walks goal -> start.
-// Every copy entry has one writer (its owner) and is written only between the
-// two barriers of a sweep, when nothing reads it; a candidate array is
-// written only by its CTA and read by others only between barriers.  Every
-// exit and barrier is taken on values identical in every CTA (edge count,
-// start, goal, sweep count, gathered flags), so all CTAs reach every cluster
-// barrier.
-// ---------------------------------------------------------------------------
-constexpr int SEARCH_CLUSTER_MAX_N = 12288;
-
-namespace {
-DEVI unsigned long long cl_ld_u64(unsigned a) {
-    unsigned long long v;
-    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
-    return v;
-}
-DEVI unsigned cl_ld_u32(unsigned a) {
-    unsigned v;
-    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-    return v;
-}
-}  // namespace
-
-__global__ void __launch_bounds__(1024, 1) k_search_cluster(SearchParams P, int ecap) {
-    extern __shared__ __align__(16) unsigned char s_raw[];
-    __shared__ unsigned long long s_near[TO_CL_MAX][4];   // per CTA: start bits, id, goal bits, id
-    __shared__ int s_flag[2][TO_CL_MAX];
-    __shared__ unsigned s_rb_d[TO_CL_MAX], s_rb_loc[TO_CL_MAX], s_rb_best[TO_CL_MAX], s_rb_last[TO_CL_MAX];
-    __shared__ unsigned long long s_kb[2][32];
-    __shared__ int s_ki[2][32];
-    __shared__ int s_se[2], s_bad, s_nf;
-    __shared__ int s_v[1024], s_e0[1024], s_pre[1025], s_wsum[33];
-    __shared__ unsigned long long s_dv[1024];
-    const int N = P.N, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nt = blockDim.x;
-    const unsigned rank = cl_rank(), C = cl_size();
-    const int V = (N + (int)C - 1) / (int)C;
-    const int v0 = min(N, (int)rank * V), v1 = min(N, v0 + V), nv = v1 - v0;
-    const int ws = P.w_f64 ? 8 : 4;
-    unsigned long long* s_d = (unsigned long long*)s_raw;       // [N] distance bits (copy)
-    unsigned long long* s_loc = s_d + N;                        // [N] this CTA's candidates
-    unsigned long long* s_last = s_loc + N;                     // [V] distance an owned vertex last relaxed from
-    unsigned long long* s_best = s_last + V;                    // [V] minimum d[u] of attaining in-neighbours
-    int* s_ro = (int*)(s_best + V);                             // [V+1] owned row offsets (local)
-    int* s_col = s_ro + (V + 1);                                // [ecap]
-    unsigned char* s_w = (unsigned char*)(((uintptr_t)(s_col + ecap) + 7) & ~(uintptr_t)7);  // [ecap] weights
-    unsigned* s_locu = (unsigned*)s_loc;                        // the candidate array as u32 [N] (predecessors)
-    DevInfo* info = P.info;
-
-    cl_sync();  // every CTA of the cluster is running before any remote access
-    if (tid < (int)C) {
-        s_rb_d[tid] = cl_map(smem_addr(s_d), tid);
-        s_rb_loc[tid] = cl_map(smem_addr(s_loc), tid);
-        s_rb_best[tid] = cl_map(smem_addr(s_best), tid);
-        s_rb_last[tid] = cl_map(smem_addr(s_last), tid);
-    }
-    if (tid == 0) {
-        const long long E = *P.count;
-        s_bad = (E < 0 || E > P.cap) ? 1 : 0;
-        if (s_bad && rank == 0) set_status_s(info, PLAN_ERR_INVALID_ARG, DET_OUTPUT);
-    }
-    __syncthreads();
-    if (s_bad) {  // the same edge count in every CTA: all leave here
-        cl_sync();
-        return;
-    }
-
-    // phase 0: owned rows into shared memory, per-vertex state, nearest candidates
-    const int eb = __ldg(&P.row_off[v0]), ee = __ldg(&P.row_off[v1]);
-    const int nloc = min(ee - eb, ecap);
-    for (int k = tid; k <= nv; k += nt) s_ro[k] = __ldg(&P.row_off[v0 + k]) - eb;
-    for (int i = tid; i < nloc; i += nt) {
-        s_col[i] = __ldg(&P.col[eb + i]);
-        if (ws == 8) ((double*)s_w)[i] = __ldg(&((const double*)P.w)[eb + i]);
-        else ((float*)s_w)[i] = __ldg(&((const float*)P.w)[eb + i]);
-    }
-    for (int v = tid; v < N; v += nt) {
-        s_d[v] = DINF;
-        s_loc[v] = DINF;
-    }
-    for (int k = tid; k < nv; k += nt) s_last[k] = DINF;
-    double sp[4], gp[4];
-    for (int a = 0; a < 4; ++a) {
-        sp[a] = P.endpoints ? (a < P.m ? P.endpoints[a] : 0.0) : P.start[a];
-        gp[a] = P.endpoints ? (a < P.m ? P.endpoints[P.m + a] : 0.0) : P.goal[a];
-    }
-    unsigned long long kb[2] = {~0ull, ~0ull};
-    int ki[2] = {0x7fffffff, 0x7fffffff};
-    for (int v = v0 + tid; v < v1; v += nt) {
-        double ds = 0.0, dg = 0.0;
-        for (int a = 0; a < P.m; ++a) {
-            const double x = ldd(P.states, (long long)v * P.n + a, P.in_f32);
-            const double ts = __dsub_rn(x, sp[a]), tg = __dsub_rn(x, gp[a]);
-            ds = __dadd_rn(ds, __dmul_rn(ts, ts));
-            dg = __dadd_rn(dg, __dmul_rn(tg, tg));
-        }
-        keep_min(kb[0], ki[0], (unsigned long long)__double_as_longlong(ds), v);
-        keep_min(kb[1], ki[1], (unsigned long long)__double_as_longlong(dg), v);
-    }
-    for (int h = 0; h < 2; ++h) {
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long ob = __shfl_down_sync(0xffffffffu, kb[h], o);
-            const int oi = __shfl_down_sync(0xffffffffu, ki[h], o);
-            keep_min(kb[h], ki[h], ob, oi);
-        }
-        if (lane == 0) {
-            s_kb[h][wid] = kb[h];
-            s_ki[h][wid] = ki[h];
-        }
-    }
-    __syncthreads();
-    if (tid < 2) {
-        unsigned long long b0 = ~0ull;
-        int i0 = 0x7fffffff;
-        for (int w = 0; w < (nt >> 5); ++w) keep_min(b0, i0, s_kb[tid][w], s_ki[tid][w]);
-        const unsigned a = smem_addr(&s_near[rank][2 * tid]);
-        for (unsigned q = 0; q < C; ++q) {
-            const unsigned ra = cl_map(a, q);
-            cl_st_u64(ra, b0);
-            cl_st_u64(ra + 8, (unsigned long long)(unsigned)i0);
-        }
-    }
-    cl_sync();
-
-    // phase 1: start and goal, the same in every CTA
-    if (tid < 2) {
-        unsigned long long b0 = ~0ull;
-        int i0 = 0x7fffffff;
-        for (unsigned q = 0; q < C; ++q) keep_min(b0, i0, s_near[q][2 * tid], (int)s_near[q][2 * tid + 1]);
-        s_se[tid] = i0;
-    }
-    __syncthreads();
-    const int start = s_se[0], goal = s_se[1];
-    if (start < 0 || start >= N || goal < 0 || goal >= N) {
-        if (rank == 0 && tid == 0) set_status_s(info, PLAN_ERR_INVALID_ARG, DET_WALK);
-        cl_sync();
-        return;
-    }
-    if (tid == 0) s_d[start] = 0ull;  // every CTA's own copy
-    __syncthreads();
-
-    auto weight = [&](int i) -> double {  // owned edge i (local index)
-        if (i < nloc) return ws == 8 ? ((const double*)s_w)[i] : (double)((const float*)s_w)[i];
-        return ws == 8 ? __ldg(&((const double*)P.w)[eb + i]) : (double)__ldg(&((const float*)P.w)[eb + i]);
-    };
-    auto column = [&](int i) -> int { return i < nloc ? s_col[i] : __ldg(&P.col[eb + i]); };
-    // Lists the owned vertices of [k0, k0 + nt) that pass `take` with their
-    // distance, and returns how many out-edges they have (block-uniform).
-    auto list_owned = [&](int k0, bool frontier) -> int {
-        if (tid == 0) s_nf = 0;
-        __syncthreads();
-        const int k = k0 + tid;
-        if (k < nv) {
-            const unsigned long long dv = s_d[v0 + k];
-            const int e0 = s_ro[k], e1 = s_ro[k + 1];
-            bool take = dv < DINF;
-            if (frontier) {
-                take = dv < s_last[k];
-                if (take) s_last[k] = dv;
-            }
-            if (take && e1 > e0) {
-                const int i = atomicAdd(&s_nf, 1);
-                s_v[i] = v0 + k;
-                s_e0[i] = e0;
-                s_pre[i] = e1 - e0;
-                s_dv[i] = dv;
-            }
-        }
-        __syncthreads();
-        const int nf = s_nf;
-        return nf == 0 ? 0 : block_scan_degrees(s_pre, nf, s_wsum);
-    };
-
-    // phase 2: sweeps
-    int sweeps = 0;
-    for (;;) {
-        if (sweeps >= P.max_sweeps) {
-            if (rank == 0 && tid == 0) set_status_s(info, PLAN_ERR_TIMEOUT, DET_SWEEPS);
-            return;  // the same count in every CTA; no remote access follows the last barrier
-        }
-        const int par = sweeps & 1;
-        ++sweeps;
-        for (int k0 = 0; k0 < nv; k0 += nt) {
-            const int tot = list_owned(k0, true);
-            const int nf = s_nf;
-            for (int q = tid; q < tot; q += nt) {
-                const int i = find_entry(s_pre, nf, q);
-                const int e = s_e0[i] + (q - s_pre[i]);
-                const int c = column(e);
-                if (c < 0 || c >= N) continue;
-                const unsigned long long x = (unsigned long long)__double_as_longlong(
-                    __dadd_rn(__longlong_as_double((long long)s_dv[i]), weight(e)));
-                if (x < s_d[c] && x < ((volatile unsigned long long*)s_loc)[c]) atomicMin(&s_loc[c], x);
-            }
-            __syncthreads();  // the lists are rebuilt by the next chunk
-        }
-        cl_sync();  // every CTA's candidates are complete
-        int changed = 0;
-        for (int k = tid; k < nv; k += nt) {
-            const unsigned off = 8u * (unsigned)(v0 + k);
-            unsigned long long m = ~0ull;
-            for (unsigned q = 0; q < C; ++q) {
-                const unsigned long long x = cl_ld_u64(s_rb_loc[q] + off);
-                m = x < m ? x : m;
-            }
-            if (m < s_d[v0 + k]) {
-                for (unsigned q = 0; q < C; ++q) cl_st_u64(s_rb_d[q] + off, m);
-                changed = 1;
-            }
-        }
-        const int ch = __syncthreads_or(changed);
-        if (tid < (int)C) cl_st_u32(cl_map(smem_addr(&s_flag[par][rank]), tid), (unsigned)ch);
-        cl_sync();
-        int any = 0;
-        for (unsigned q = 0; q < C; ++q) any |= s_flag[par][q];
-        if (!any) break;
-    }
-
-    // phase 3: predecessors.  Pass 0: minimum d[u] over the tight in-edges of
-    // every vertex, gathered into s_best by its owner; pass 1: minimum u among
-    // those attaining it, gathered into s_last (as u32) by the owner.
-    for (int pass = 0; pass < 2; ++pass) {
-        for (int v = tid; v < N; v += nt) {
-            if (pass == 0) s_loc[v] = ~0ull;
-            else s_locu[v] = 0x7fffffffu;
-        }
-        __syncthreads();
-        for (int k0 = 0; k0 < nv; k0 += nt) {
-            const int tot = list_owned(k0, false);
-            const int nf = s_nf;
-            for (int q = tid; q < tot; q += nt) {
-                const int i = find_entry(s_pre, nf, q);
-                const int e = s_e0[i] + (q - s_pre[i]);
-                const int c = column(e);
-                if (c < 0 || c >= N || c == start) continue;
-                const unsigned long long dvb = s_dv[i];
-                const unsigned long long x =
-                    (unsigned long long)__double_as_longlong(__dadd_rn(__longlong_as_double((long long)dvb), weight(e)));
-                if (x != s_d[c]) continue;
-                if (pass == 0) {
-                    atomicMin(&s_loc[c], dvb);
-                } else {
-                    const unsigned o = (unsigned)(c / V);
-                    if (cl_ld_u64(s_rb_best[o] + 8u * (unsigned)(c - (int)o * V)) == dvb)
-                        atomicMin(&s_locu[c], (unsigned)s_v[i]);
-                }
-            }
-            __syncthreads();
-        }
-        cl_sync();  // every CTA's candidates are complete
-        for (int k = tid; k < nv; k += nt) {
-            const unsigned v = (unsigned)(v0 + k);
-            if (pass == 0) {
-                unsigned long long m = ~0ull;
-                for (unsigned q = 0; q < C; ++q) {
-                    const unsigned long long x = cl_ld_u64(s_rb_loc[q] + 8u * v);
-                    m = x < m ? x : m;
-                }
-                s_best[k] = m;
-            } else {
-                unsigned m = 0x7fffffffu;
-                for (unsigned q = 0; q < C; ++q) {
-                    const unsigned x = cl_ld_u32(s_rb_loc[q] + 4u * v);
-                    m = x < m ? x : m;
-                }
-                s_last[k] = m;
-            }
-        }
-        cl_sync();  // gathered before the candidate arrays are reset or read
-    }
-
-    // phase 4: CTA 0 collects the predecessors (over its candidate array) and walks
-    if (rank == 0) {
-        for (int v = tid; v < N; v += nt) {
-            const unsigned o = (unsigned)(v / V);
-            s_locu[v] = (unsigned)cl_ld_u64(s_rb_last[o] + 8u * (unsigned)(v - (int)o * V));
-        }
-    }
-    cl_sync();  // the owners stay until CTA 0 has read their predecessors
-    if (rank != 0) return;
-    __syncthreads();
-    if (tid != 0) return;
-    const unsigned* pr = s_locu;
-    info->start = start;
-    info->goal = goal;
-    info->search_iters = (unsigned long long)sweeps;
-    const unsigned long long dg = s_d[goal];
-    if (dg >= DINF) {
-        *P.path_len = 0;
-        *P.cost = __longlong_as_double((long long)DINF);
-        set_status_s(info, PLAN_ERR_NO_PATH, DET_NONE);
-    } else {
-        int len = 1, v = goal;
-        bool okw = true;
-        while (v != start) {
-            const unsigned pv = pr[v];
-            if (pv >= (unsigned)N || len > N) {
-                okw = false;
-                break;
-            }
-            v = (int)pv;
-            ++len;
-        }
-        if (!okw) {
-            set_status_s(info, PLAN_ERR_INVALID_ARG, DET_WALK);
-            *P.path_len = 0;
-        } else if (len > P.path_cap) {
-            set_status_s(info, PLAN_ERR_CAPACITY, DET_PATHCAP);
-            *P.path_len = len;
-        } else {
-            v = goal;
-            for (int q = len - 1; q >= 0; --q) {
-                P.path[q] = v;
-                if (q) v = (int)pr[v];
-            }
-            *P.path_len = len;
-        }
-        *P.cost = __longlong_as_double((long long)dg);
-    }
-    info->path_len = *P.path_len;
-}
-
-namespace {
-// Shared memory of k_search_cluster for N vertices, cluster size C, ecap
-// cached edges a CTA and ws-byte weights.
-size_t search_cluster_smem(int N, int C, int ecap, int ws) {
-    const int V = (N + C - 1) / C;
-    size_t b = (size_t)16 * N + (size_t)8 * 2 * V + (size_t)4 * (V + 1) + (size_t)4 * ecap;
-    b = (b + 7) & ~(size_t)7;
-    return b + (size_t)ws * ecap;
-}
-
-ClusterChoice g_scl[64];
-
-// Cluster size k_search_cluster can run with at its largest shared memory (16, 8 or 0).
-int search_cluster_size_for(int dev) {
-    std::lock_guard<std::mutex> lock(g_cl_mu);
-    if (dev < 0 || dev >= 64) return 0;
-    ClusterChoice& c = g_scl[dev];
-    if (c.dev != dev) {
-        c.dev = dev;
-        cudaDeviceGetAttribute(&c.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        const int dyn = c.optin - 32768;   // room for the static shared memory
-        cudaFuncSetAttribute(k_search_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-        cudaFuncSetAttribute(k_search_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        for (int C : {16, 8}) {
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(C);
-            cfg.blockDim = dim3(1024);
-            cfg.dynamicSmemBytes = dyn;
-            cudaLaunchAttribute at[1];
-            at[0].id = cudaLaunchAttributeClusterDimension;
-            at[0].val.clusterDim.x = C;
-            at[0].val.clusterDim.y = 1;
-            at[0].val.clusterDim.z = 1;
-            cfg.attrs = at;
-            cfg.numAttrs = 1;
-            int ncl = 0;
-            const cudaError_t e = cudaOccupancyMaxActiveClusters(&ncl, k_search_cluster, &cfg);
-            if (e != cudaSuccess) cudaGetLastError();
-            (C == 16 ? c.ok16 : c.ok8) = (e == cudaSuccess && ncl >= 1) ? 1 : 0;
-        }
-    }
-    return c.ok16 == 1 ? 16 : c.ok8 == 1 ? 8 : 0;
-}
-
-// Launch k_search_cluster when the graph is small enough; false: use k_search.
-bool launch_search_cluster(const SearchParams& P, cudaStream_t st, int* launches, cudaError_t* err) {
-    if (P.N > SEARCH_CLUSTER_MAX_N) return false;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const int C = search_cluster_size_for(dev);
-    if (C == 0) return false;
-    const int ws = P.w_f64 ? 8 : 4;
-    const int dyn = g_scl[dev].optin - 32768;
-    const size_t base = search_cluster_smem(P.N, C, 0, ws);
-    if ((long long)base + 64 > dyn) return false;
-    // owned edges a CTA keeps on chip: what fits, up to twice the even share
-    // of the capacity.  Edges past it come from global memory, one load at a
-    // time for the 16 SMs of the cluster -- much slower than the cooperative
-    // kernel's 152 -- so only graphs whose rows mostly fit go on chip.
-    long long ecap = ((long long)dyn - (long long)base - 16) / (4 + ws);
-    const long long even = (P.cap + C - 1) / C;
-    if (ecap < even / 2 + 64) return false;
-    if (ecap > 2 * even + 64) ecap = 2 * even + 64;
-    if (ecap > (1 << 30)) ecap = 1 << 30;
-    const int ec = (int)ecap;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(C);
-    cfg.blockDim = dim3(1024);
-    cfg.dynamicSmemBytes = search_cluster_smem(P.N, C, ec, ws);
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = C;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    SearchParams Q = P;
-    *err = cudaLaunchKernelEx(&cfg, k_search_cluster, Q, ec);
-    ++*launches;
-    return true;
-}
-}  // namespace
-
 int launch_search(const SearchParams& P, void* stream, int num_sms, int* launches) {
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t ce = cudaSuccess;
-    if (launch_search_cluster(P, st, launches, &ce)) return (int)ce;
     // one block per SM: fewer arrivals per grid barrier; the walk's staging
     // buffer (block 0) holds pred[] for up to SEARCH_WALK_SMEM vertices
     const size_t smem = (size_t)SEARCH_WALK_SMEM * sizeof(int);
