@@ -3160,19 +3160,25 @@ int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_s
     if (P.totN > 0) {
         cudaMemsetAsync(P.rowCount, 0, sizeof(int) * (size_t)P.totN, st);
         if (P.totPoly > 0) {
-            k_emit<<<num_sms * 16, 256, 0, st>>>(P);
+            // persistent: four CTAs per SM (its register bound), each warp
+            // looping over row segments, so that warps finishing early do not
+            // hold a CTA slot that a new CTA could use
+            k_emit<<<num_sms * 4, 256, 0, st>>>(P);
             ++*launches;
         }
     }
     k_scan<<<P.Q, 1024, 0, st>>>(P);
     ++*launches;
     if (P.totN > 0 && P.totPoly > 0) {
-        // staged ids and slot indices per warp (a row holds fewer than N entries)
-        const int run_cap = 2 * (P.maxN < 1024 ? (P.maxN > 32 ? P.maxN : 32) : 1024);
+        // staged ids and slot indices per warp (a row holds fewer than N
+        // entries; rows with more than run_cap / 2 use the binary-search
+        // path): at most 32 KB a CTA, so that four CTAs (the register
+        // bound) fit on an SM
+        const int run_cap = 2 * (P.maxN < 512 ? (P.maxN > 32 ? P.maxN : 32) : 512);
         const size_t smem = ((size_t)8 * run_cap * sizeof(int) + 1023) & ~(size_t)1023;
         const cudaError_t ea = cudaFuncSetAttribute(k_compact_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (ea != cudaSuccess) return (int)ea;
-        k_compact_fill<<<num_sms * 16, 256, smem, st>>>(P, run_cap);
+        k_compact_fill<<<num_sms * 4, 256, smem, st>>>(P, run_cap);
         ++*launches;
     }
     return (int)cudaGetLastError();

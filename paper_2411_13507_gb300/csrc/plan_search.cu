@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
     __shared__ unsigned long long s_kb[2][32];
     __shared__ int s_ki[2][32];
     __shared__ int s_nf;                        // listed vertices of this round
+    __shared__ unsigned long long s_gd;         // the goal's distance as this block last read it
     __shared__ int s_v[1024], s_e0[1024];       // vertex, first out-edge
     __shared__ int s_pre[1025];                 // out-degree, then its exclusive prefix
     __shared__ unsigned long long s_dv[1024];   // distance the vertex relaxes from
@@ -274,10 +275,13 @@ __global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
         // pick up what other blocks relaxed meanwhile
         for (int rep = 0; rep < SWEEP_ROUNDS; ++rep)
         for (long long k0 = 0; k0 < nown; k0 += nt) {
-            if (tid == 0) s_nf = 0;
+            if (tid == 0) {
+                s_nf = 0;
+                s_gd = vdist[g];  // one read per block: same-address reads queue at one L2 slice
+            }
             __syncthreads();
             const long long k = k0 + tid;
-            const unsigned long long gd = vdist[g];
+            const unsigned long long gd = s_gd;
             if (k < nown) {
                 const long long v = blockIdx.x + k * nb;
                 const bool cached = k < SEARCH_OWN_CAP;
@@ -344,7 +348,9 @@ __global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
     // dist[v], in two passes over the out-edges of every vertex closer than
     // the goal (the only possible predecessors on a path to it; same
     // ownership and edge-parallel layout as the sweeps)
-    const unsigned long long dgoal = vdist[g];
+    if (tid == 0) s_gd = vdist[g];
+    __syncthreads();
+    const unsigned long long dgoal = s_gd;
     for (int pass = 0; pass < 2; ++pass) {
         for (long long k0 = 0; k0 < nown; k0 += nt) {
             if (tid == 0) s_nf = 0;
