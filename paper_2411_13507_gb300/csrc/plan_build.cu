@@ -167,10 +167,7 @@ __global__ void k_prep(BuildParams P) {
 // A1 membership: bit k of state i set iff A_k x_i^(0) <= b_k - eps on every
 // row (canonical FP64 decision; FP32 first, FP64 only inside the band).
 // ---------------------------------------------------------------------------
-__global__ void k_member(BuildParams P) {
-    const long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;  // one warp per (state, word)
-    const int lane = threadIdx.x & 31;
-    if (block_failed(P.info, nullptr, nullptr) || t >= P.totMask) return;
+DEVI void member_word(const BuildParams& P, long long t, int lane) {
     const int q = find_q(P.pfxMask, P.Q, t);
     const QueryDesc& Q = P.qd[q];
     const long long loc = t - P.pfxMask[q];
@@ -227,6 +224,16 @@ __global__ void k_member(BuildParams P) {
     }
     const uint32_t word = __ballot_sync(0xffffffffu, in);
     if (lane == 0) P.memMask[Q.maskOff + (long long)i * Q.W + w] = word;
+}
+
+__global__ void __launch_bounds__(256, 4) k_member(BuildParams P) {
+    const int lane = threadIdx.x & 31;
+    if (block_failed(P.info, nullptr, nullptr)) return;
+    // one warp per (state, word), persistent: a single wave of CTAs loops
+    // over the items (each is a short chain of dependent loads)
+    for (long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; t < P.totMask;
+         t += ((long long)gridDim.x * blockDim.x) >> 5)
+        member_word(P, t, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -3137,7 +3144,8 @@ int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_s
         ++*launches;
     }
     if (P.totMask > 0) {  // also writes the (zero) masks of queries without polytopes
-        k_member<<<(unsigned)((P.totMask * 32 + 255) / 256), 256, 0, st>>>(P);
+        const long long need = (P.totMask * 32 + 255) / 256;
+        k_member<<<(unsigned)(need < num_sms * 4 ? need : num_sms * 4), 256, 0, st>>>(P);
         ++*launches;
     }
     if (P.totPoly > 0) {
@@ -3160,10 +3168,7 @@ int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_s
     if (P.totN > 0) {
         cudaMemsetAsync(P.rowCount, 0, sizeof(int) * (size_t)P.totN, st);
         if (P.totPoly > 0) {
-            // persistent: four CTAs per SM (its register bound), each warp
-            // looping over row segments, so that warps finishing early do not
-            // hold a CTA slot that a new CTA could use
-            k_emit<<<num_sms * 4, 256, 0, st>>>(P);
+            k_emit<<<num_sms * 16, 256, 0, st>>>(P);
             ++*launches;
         }
     }

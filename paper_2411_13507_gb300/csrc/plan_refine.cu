@@ -1,5 +1,5 @@
 // Differentiable refinement objective for sm_103a: one thread per Bezier
-// segment, forward (loss) and hand-written backward (d loss / d control points
+// segment (the axes one after the other), forward (loss) and hand-written backward (d loss / d control points
 // and d loss / d T) of
 //
 //   loss = w_snap J_snap + mu sum_r phi_delta(margin_r)
@@ -71,64 +71,112 @@ __global__ void __launch_bounds__(128) k_refine(RefineParams R) {
     constexpr int L = PD + 1;
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (s >= R.S) return;
-    float P[8][M];
-#pragma unroll
-    for (int l = 0; l < L; ++l)
-#pragma unroll
-        for (int a = 0; a < M; ++a) P[l][a] = R.P[(s * L + l) * M + a];
+    const float* Ps = R.P + s * L * M;
     const float T = R.T[s];
     const float Ti = 1.f / T;
     const float mu = R.mu, delta = R.delta, ld = logf(R.delta), ws = R.w_snap;
     const float up = GRAD ? R.grad_loss[s] : 1.f;
     float loss = 0.f, dT = 0.f;
-    float dP[8][M];
-#pragma unroll
-    for (int l = 0; l < 8; ++l)
-#pragma unroll
-        for (int a = 0; a < M; ++a) dP[l][a] = 0.f;
+    float* dPs = GRAD ? R.dP + s * L * M : nullptr;
 
-    // reach margins
+    // Reach margins and snap energy separate over the axes (Theorem 1 per
+    // axis; the snap integral is the sum of the axes' integrals): one axis
+    // at a time keeps few values live.  Its gradient goes straight to dP.
+#pragma unroll 1
+    for (int a = 0; a < M; ++a) {
+        float Pa[8][1];
 #pragma unroll
-    for (int k = 1; k <= G; ++k) {
-        float d[8][M];
+        for (int l = 0; l < 8; ++l) Pa[l][0] = l < L ? Ps[l * M + a] : 0.f;
+        float ga[8];
 #pragma unroll
-        for (int l = 0; l < 8; ++l)
+        for (int l = 0; l < 8; ++l) ga[l] = 0.f;
 #pragma unroll
-            for (int a = 0; a < M; ++a) d[l][a] = l < L ? P[l][a] : 0.f;
+        for (int k = 1; k <= G; ++k) {
+            float d[8][1];
 #pragma unroll
-        for (int it = 0; it < k; ++it) fwd_diff<M, L>(d, L - it);
-        float sk = fact_f(PD) / fact_f(PD - k);
+            for (int l = 0; l < 8; ++l) d[l][0] = Pa[l][0];
 #pragma unroll
-        for (int it = 0; it < k; ++it) sk *= Ti;
-        const float ck = R.bound[k - 1];
-        const int nk = L - k;
-        float g[8][M];
+            for (int it = 0; it < k; ++it) fwd_diff<1, L>(d, L - it);
+            float sk = fact_f(PD) / fact_f(PD - k);
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
+            for (int it = 0; it < k; ++it) sk *= Ti;
+            const float ck = R.bound[k - 1];
+            const int nk = L - k;
+            float g[8][1];
 #pragma unroll
-            for (int a = 0; a < M; ++a) {
-                g[j][a] = 0.f;
+            for (int j = 0; j < 8; ++j) {
+                g[j][0] = 0.f;
                 if (j < nk) {
-                    const float Q = sk * d[j][a];
+                    const float Q = sk * d[j][0];
                     const float m1 = ck - Q, m2 = ck + Q;
                     loss += mu * (phi_f(m1, delta, ld) + phi_f(m2, delta, ld));
                     if (GRAD) {
                         const float gQ = mu * (dphi_f(m2, delta) - dphi_f(m1, delta)) * up;
-                        g[j][a] = gQ * sk;
+                        g[j][0] = gQ * sk;
                         dT += gQ * Q * (-(float)k) * Ti;
                     }
                 }
             }
+            if (GRAD) {
+#pragma unroll
+                for (int it = k; it >= 1; --it) adj_diff<1, L>(g, L - it);
+#pragma unroll
+                for (int l = 0; l < L; ++l) ga[l] += g[l][0];
+            }
+        }
+        {
+            constexpr int q = PD - 4;
+            float d4[8][1];
+#pragma unroll
+            for (int l = 0; l < 8; ++l) d4[l][0] = Pa[l][0];
+#pragma unroll
+            for (int it = 0; it < 4; ++it) fwd_diff<1, L>(d4, L - it);
+            float c = fact_f(PD) / fact_f(PD - 4);
+            c = c * c;
+            float t7 = Ti * Ti * Ti;
+            t7 = t7 * t7 * Ti;
+            c *= t7;
+            float quad = 0.f;
+            float gd[8][1];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) gd[j][0] = 0.f;
+#pragma unroll
+            for (int j = 0; j <= q; ++j)
+#pragma unroll
+                for (int l = 0; l <= q; ++l) {
+                    const float Gjl = (float)(comb_i(q, j) * comb_i(q, l)) / (float)((2 * q + 1) * comb_i(2 * q, j + l));
+                    quad = fmaf(Gjl * d4[j][0], d4[l][0], quad);
+                    if (GRAD) gd[j][0] = fmaf(Gjl, d4[l][0], gd[j][0]);
+                }
+            const float J = c * quad;
+            loss += ws * J;
+            if (GRAD) {
+                const float f = ws * c * 2.f * up;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) gd[j][0] = (j <= q) ? gd[j][0] * f : 0.f;
+#pragma unroll
+                for (int it = 4; it >= 1; --it) adj_diff<1, L>(gd, L - it);
+#pragma unroll
+                for (int l = 0; l < L; ++l) ga[l] += gd[l][0];
+                dT += ws * (-7.f) * J * Ti * up;
+            }
+        }
         if (GRAD) {
 #pragma unroll
-            for (int it = k; it >= 1; --it) adj_diff<M, L>(g, L - it);
-#pragma unroll
-            for (int l = 0; l < L; ++l)
-#pragma unroll
-                for (int a = 0; a < M; ++a) dP[l][a] += g[l][a];
+            for (int l = 0; l < L; ++l) dPs[l * M + a] = ga[l];
         }
     }
-    // free-space margins of the interior control points
+    // free-space margins of the interior control points (every axis)
+    float P[8][M];
+#pragma unroll
+    for (int l = 1; l < PD; ++l)
+#pragma unroll
+        for (int a = 0; a < M; ++a) P[l][a] = Ps[l * M + a];
+    float df[8][M];
+#pragma unroll
+    for (int l = 0; l < 8; ++l)
+#pragma unroll
+        for (int a = 0; a < M; ++a) df[l][a] = 0.f;
     const int nr = min(R.nrows[s], R.rmax);
     for (int r = 0; r < nr; ++r) {
         float Ar[M];
@@ -145,65 +193,16 @@ __global__ void __launch_bounds__(128) k_refine(RefineParams R) {
             if (GRAD) {
                 const float gm = mu * dphi_f(mg, delta) * up;
 #pragma unroll
-                for (int a = 0; a < M; ++a) dP[l][a] -= gm * Ar[a];
+                for (int a = 0; a < M; ++a) df[l][a] -= gm * Ar[a];
             }
-        }
-    }
-    // snap energy
-    {
-        constexpr int q = PD - 4;
-        float d4[8][M];
-#pragma unroll
-        for (int l = 0; l < 8; ++l)
-#pragma unroll
-            for (int a = 0; a < M; ++a) d4[l][a] = l < L ? P[l][a] : 0.f;
-#pragma unroll
-        for (int it = 0; it < 4; ++it) fwd_diff<M, L>(d4, L - it);
-        float c = fact_f(PD) / fact_f(PD - 4);
-        c = c * c;
-        float t7 = Ti * Ti * Ti;
-        t7 = t7 * t7 * Ti;
-        c *= t7;
-        float quad = 0.f;
-        float gd[8][M];
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-#pragma unroll
-            for (int a = 0; a < M; ++a) gd[j][a] = 0.f;
-#pragma unroll
-        for (int j = 0; j <= q; ++j)
-#pragma unroll
-            for (int l = 0; l <= q; ++l) {
-                const float Gjl = (float)(comb_i(q, j) * comb_i(q, l)) / (float)((2 * q + 1) * comb_i(2 * q, j + l));
-#pragma unroll
-                for (int a = 0; a < M; ++a) {
-                    quad = fmaf(Gjl * d4[j][a], d4[l][a], quad);
-                    if (GRAD) gd[j][a] = fmaf(Gjl, d4[l][a], gd[j][a]);
-                }
-            }
-        const float J = c * quad;
-        loss += ws * J;
-        if (GRAD) {
-            const float f = ws * c * 2.f * up;
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-#pragma unroll
-                for (int a = 0; a < M; ++a) gd[j][a] = (j <= q) ? gd[j][a] * f : 0.f;
-#pragma unroll
-            for (int it = 4; it >= 1; --it) adj_diff<M, L>(gd, L - it);
-#pragma unroll
-            for (int l = 0; l < L; ++l)
-#pragma unroll
-                for (int a = 0; a < M; ++a) dP[l][a] += gd[l][a];
-            dT += ws * (-7.f) * J * Ti * up;
         }
     }
     if (R.loss) R.loss[s] = loss;
     if (GRAD) {
 #pragma unroll
-        for (int l = 0; l < L; ++l)
+        for (int l = 1; l < PD; ++l)
 #pragma unroll
-            for (int a = 0; a < M; ++a) R.dP[(s * L + l) * M + a] = dP[l][a];
+            for (int a = 0; a < M; ++a) dPs[l * M + a] += df[l][a];
         R.dT[s] = dT;
     }
 }
