@@ -41,7 +41,8 @@ typedef enum {
 
 /* Arithmetic of the edge-build margins. */
 typedef enum {
-    PLAN_F64 = 0,   /* canonical FP64 evaluation (no re-check needed) */
+    PLAN_F64 = 0,   /* FP64 results: bits of the canonical FP64 margins, costs in canonical FP64
+                       (weights are doubles); see plan_set_tile for the two routes */
     PLAN_F32 = 1,   /* FP32 margins; any margin within its error band re-checked in FP64 */
     PLAN_TF32 = 2,  /* control-point products on tensor cores, TF32 inputs, FP32 accumulate, FP64 re-check */
     PLAN_BF16 = 3   /* as TF32 with BF16 inputs */
@@ -240,7 +241,14 @@ int plan_build_edges_batched(plan_ctx* ctx);
  * warps compute the next duration's halves while consumer warps reduce the
  * current one; used with 64-state tiles when its two stages fit in shared
  * memory; 2: one warp group, every 4x4 block through all rows).  Results do
- * not depend on the choice.  plan_autotune times every candidate on the prepared batch (reps launches
+ * not depend on the choice.  An FP64 model (PLAN_F64) runs these FP32
+ * kernels too -- every margin within its rounding band of zero is re-checked
+ * in canonical FP64, so the bits are the FP64 ones -- and then computes the
+ * cost of every emitted edge and duration in canonical FP64 (the weight is
+ * the cheapest, ties to the lower duration index); pipeline 3 (FP64 models
+ * only) runs the canonical FP64 pair kernel instead (every margin and cost in
+ * FP64, 32-state tiles, chunks 0 = 8).  Both FP64 routes give the same graph
+ * bit for bit.  plan_autotune times every candidate on the prepared batch (reps launches
  * each, synchronising) and keeps the fastest; it reports the choice and its
  * mean pair-kernel time. */
 int plan_set_tile(plan_ctx* ctx, int tile, int ctas_per_sm, int tchunks, int pipeline);

@@ -40,7 +40,7 @@ struct plan_ctx {
     std::vector<QueryDesc> hq;
     std::vector<long long> pfx;       // 4 x (Q+1): mask, poly, rows, N
     long long totMask = 0, totPoly = 0, totRows = 0, totN = 0, totList = 0, totK1 = 0;
-    int maxK = 0, maxN = 0;
+    int maxK = 0, maxN = 0, maxT = 0;
     std::vector<double> Tall;
     QueryDesc* d_qd = nullptr;
     long long* d_pfx = nullptr;
@@ -490,9 +490,10 @@ int prepare(plan_ctx* c, int Q, const plan_query* qs, int max_rows, int shard = 
     std::vector<long long> pfx(4 * (size_t)(Q + 1), 0);
     std::vector<double> Tall;
     long long mask = 0, poly = 0, rows = 0, nrow = 0, list = 0, k1 = 0;
-    int maxK = 0, maxN = 0;
+    int maxK = 0, maxN = 0, maxT = 0;
     for (int q = 0; q < Q; ++q) {
         const plan_query& in = qs[q];
+        if (in.nT > maxT) maxT = in.nT;
         QueryDesc& d = hq[q];
         memset(&d, 0, sizeof(d));
         d.N = in.N;
@@ -592,6 +593,7 @@ int prepare(plan_ctx* c, int Q, const plan_query* qs, int max_rows, int shard = 
     c->totK1 = k1;
     c->maxK = maxK;
     c->maxN = maxN;
+    c->maxT = maxT;
     c->last_nT = Q == 1 ? qs[0].nT : 0;
     return PLAN_OK;
 }
@@ -614,15 +616,23 @@ int issue(plan_ctx* c) {
     P.p = c->model.degree;
     P.cost_mode = c->model.cost_mode;
     P.in_f32 = c->model.input == PLAN_IN_F32;
-    P.arith = c->model.arith;
+    // FP64 model: by default the FP32 pair kernels decide the bits (banded
+    // margins re-checked in canonical FP64, so the bits are the FP64 ones) and
+    // a canonical FP64 pass computes the costs of the emitted edges; pipeline
+    // PLAN_PIPE_FP64 runs the canonical FP64 pair kernel instead
+    const bool canonical64 = c->model.arith == PLAN_F64 && c->pipeline == PIPE_FP64;
+    P.arith = (c->model.arith == PLAN_F64 && !canonical64) ? PLAN_F32 : c->model.arith;
+    P.w64 = c->model.arith == PLAN_F64;
+    P.cost64 = c->model.arith == PLAN_F64 && !canonical64;
+    P.maxT = c->maxT;
     P.max_rows = c->b_max_rows;
-    P.tile = (c->model.arith == PLAN_F64) ? TILE64
-             : (c->model.arith == PLAN_F32) ? (c->tile > 0 ? c->tile : TILE)
-                                            : TILE;  // tensor-core form: 64-state tiles, 256 threads
-    // FP64: one duration per item by default (the canonical kernel is bound by
-    // the narrow FP64 pipe; small problems need the items to fill every SM)
-    P.tchunks = c->tchunks > 0 ? c->tchunks : (c->model.arith == PLAN_F64 ? 8 : 2);
-    P.pipeline = c->pipeline;
+    P.tile = (P.arith == PLAN_F64) ? TILE64
+             : (P.arith == PLAN_F32) ? (c->tile > 0 ? c->tile : TILE)
+                                     : TILE;  // tensor-core form: 64-state tiles, 256 threads
+    // the canonical FP64 kernel: one duration per item by default (it is bound
+    // by the narrow FP64 pipe; small problems need the items to fill every SM)
+    P.tchunks = c->tchunks > 0 ? c->tchunks : (P.arith == PLAN_F64 ? 8 : 2);
+    P.pipeline = canonical64 ? 0 : c->pipeline;
     P.eps = c->model.tighten;
     P.qd = c->d_qd;
     P.pfxMask = c->d_pfx;
@@ -739,7 +749,7 @@ int plan_build_edges_batched(plan_ctx* c) {
 
 int plan_set_tile(plan_ctx* c, int tile, int ctas_per_sm, int tchunks, int pipeline) {
     if (!c || tile < 0 || ctas_per_sm < 0 || ctas_per_sm > 8 || tchunks < 0 || tchunks > NT_MAX || pipeline < 0 ||
-        pipeline > 2)
+        pipeline > PIPE_FP64 || (pipeline == PIPE_FP64 && c->model.arith != PLAN_F64))
         return PLAN_ERR_INVALID_ARG;
     c->pipeline = pipeline;
     if (tile != 0 && (tile < 8 || tile > TILE || (tile & 3))) return fail(c, PLAN_ERR_INVALID_ARG, "tile must be 8..64, multiple of 4");
@@ -753,10 +763,10 @@ int plan_autotune(plan_ctx* c, int reps, int* best_tile, int* best_ctas, int* be
                   double* best_ms) {
     if (!c || reps < 1) return PLAN_ERR_INVALID_ARG;
     if (c->bQ < 1) return fail(c, PLAN_ERR_INVALID_ARG, "prepare a batch first");
-    if (c->model.arith != PLAN_F32) {  // the FP64 and tensor-core kernels have fixed tiles
-        if (best_tile) *best_tile = c->model.arith == PLAN_F64 ? TILE64 : TILE;
+    if (c->model.arith != PLAN_F32 && c->model.arith != PLAN_F64) {  // the tensor-core kernel has fixed tiles
+        if (best_tile) *best_tile = TILE;
         if (best_ctas) *best_ctas = 0;
-        if (best_chunks) *best_chunks = c->model.arith == PLAN_F64 ? 1 : 2;
+        if (best_chunks) *best_chunks = 2;
         if (best_pipeline) *best_pipeline = 0;
         return PLAN_OK;
     }

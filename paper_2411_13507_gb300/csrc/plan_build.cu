@@ -582,6 +582,7 @@ __global__ void k_zero_slots(BuildParams P) {
 }
 
 constexpr int RECHECK_THREADS = 128;  // four warps (one FP64 unit each) per re-check entry
+constexpr int COST64_WARPS = 4;       // warps (rows in flight) per CTA of the FP64 cost pass
 
 // Re-check entry: cost-only flag (1 bit) | query (16 bits) | polytope (10) | li (16) | lj (16) | T (5).
 // Bit 63 marks a check that is certainly feasible and needs only its cost in
@@ -741,7 +742,7 @@ DEVI void pair_phase(const BuildParams& P, const Item& itd, int t, int T, int gi
                     for (int q = 0; q < 16; ++q) {
                         if ((feas >> q) & 1u) {
                             const int li = i0 + 4 * gi + (q >> 2), lj = j0 + 4 * gj + (q & 3);
-                            if (mL[q >> 2] + mR[q & 3] <= COST_RHO * cs[q]) {
+                            if (P.cost64 || mL[q >> 2] + mR[q & 3] <= COST_RHO * cs[q]) {
                                 const long long slot = itd.base + (long long)li * itd.nk + lj;
                                 atomicOr(&P.resBits[slot], 1u << t);
                                 atomicMin(&P.resKey[slot], key_f32(cs[q], t));
@@ -1515,7 +1516,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                         }
                         cs += sqrtf(ss);
                     }
-                    if (magC[li] + magC[T + lj] <= COST_RHO * cs) {
+                    if (P.cost64 || magC[li] + magC[T + lj] <= COST_RHO * cs) {  // FP64 models re-cost every edge anyway
                         const long long slot = itd.base + (long long)(i0 + li) * itd.nk + (j0 + lj);
                         atomicOr(&P.resBits[slot], 1u << t);
                         atomicMin(&P.resKey[slot], key_f32(cs, t));
@@ -2677,6 +2678,7 @@ DEVI void write_edge(const BuildParams& P, const QueryDesc& Q, long long o, int 
     Q.mask[o] = bits;
     Q.tidx[o] = (uint8_t)(key & 31ull);
     if (P.arith == PLAN_F64) ((double*)Q.w)[o] = __longlong_as_double((long long)(key & ~31ull));
+    else if (P.w64) ((double*)Q.w)[o] = (double)__uint_as_float((unsigned)(key >> 32));  // replaced by k_cost64
     else ((float*)Q.w)[o] = __uint_as_float((unsigned)(key >> 32));
 }
 
@@ -2889,6 +2891,78 @@ __global__ void __launch_bounds__(256, 4) k_compact_fill(BuildParams P, int run_
             }
         }
         __syncwarp();  // the runs are rebuilt by this warp's next row
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Canonical FP64 costs of an FP64 model built by the FP32 pair kernels: for
+// every emitted edge (i, j) and every duration t of its mask, the control-
+// polygon length in the FP64 kernel's order -- each cost row (segment l,
+// derivative d, axis a) the start half plus the end half, each half summed
+// left to right without FMA; per segment the squared norm in (d, a) order
+// with FMA, its root; the segments summed in order -- and the weight = the
+// cheapest duration by the key (cost bits with the low five cleared | t),
+// as the FP64 kernel's slot merge takes it.  One warp per row: the start
+// halves of every duration are computed once per row by the lanes (one entry
+// each) into shared memory, each lane then takes edges.
+// ---------------------------------------------------------------------------
+template <int M, int G, int PD>
+__global__ void __launch_bounds__(COST64_WARPS * 32) k_cost64(BuildParams P) {
+    constexpr int N_ = M * G, TG = 2 * G;
+    extern __shared__ __align__(16) double s_kl[];   // [COST64_WARPS][maxT][E]
+    if (block_failed(P.info, nullptr, nullptr)) return;
+    const TabLayout L = P.L;
+    const int DR = P.cost_mode == 1 ? 1 : G;
+    const int E = PD * DR * M;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double* kl = s_kl + (size_t)wib * P.maxT * E;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; row < P.totN; row += nwarps) {
+        const int q = find_q(P.pfxN, P.Q, row);
+        const QueryDesc& Q = P.qd[q];
+        const int i = (int)(row - P.pfxN[q]);
+        const int e0 = Q.row_off[i], e1 = Q.row_off[i + 1];
+        if (e1 <= e0) continue;  // warp-uniform
+        double xi[N_];
+#pragma unroll
+        for (int c = 0; c < N_; ++c) xi[c] = ldv(Q.states, (long long)i * N_ + c, P.in_f32);
+        for (int u = lane; u < Q.nT * E; u += 32) {
+            const int t = u / E, r = u % E;
+            const int l = r / (DR * M), d = (r / M) % DR, a = r % M;
+            const double* tb = P.tab64 + (long long)(Q.tabOff + t) * L.e_stride;
+            kl[u] = half_sum<G>(tb + L.e_C + (d * PD + l) * TG, xi + a, M);
+        }
+        __syncwarp();
+        for (int e = e0 + lane; e < e1; e += 32) {
+            const int j = Q.col[e];
+            uint32_t bits = Q.mask[e];
+            double xj[N_];
+#pragma unroll
+            for (int c = 0; c < N_; ++c) xj[c] = ldv(Q.states, (long long)j * N_ + c, P.in_f32);
+            unsigned long long best = KEY_NONE;
+            while (bits) {
+                const int t = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                const double* tb = P.tab64 + (long long)(Q.tabOff + t) * L.e_stride;
+                const double* klt = kl + t * E;
+                double cost = 0.0;
+                for (int l = 0; l < PD; ++l) {
+                    double ss = 0.0;
+                    for (int d = 0; d < DR; ++d)
+                        for (int a = 0; a < M; ++a) {
+                            const double v = klt[(l * DR + d) * M + a] +
+                                             half_sum<G>(tb + L.e_C + (d * PD + l) * TG + G, xj + a, M);
+                            ss = fma(v, v, ss);
+                        }
+                    cost += sqrt(ss);
+                }
+                const unsigned long long key = key_f64(cost, t);
+                if (key < best) best = key;
+            }
+            ((double*)Q.w)[e] = __longlong_as_double((long long)(best & ~31ull));
+            Q.tidx[e] = (uint8_t)(best & 31ull);
+        }
+        __syncwarp();  // the start halves are rewritten for the next row
     }
 }
 
@@ -3135,6 +3209,20 @@ bool model_supported(int m, int g, int p) {
 // N<=256 accumulator, which the 2-D models fit.
 bool tc_supported(int m, int g, int p) { return m == 2 && g == 2 && (p == 3 || p == 5); }
 
+template <int M, int G, int PD>
+int launch_cost64(const BuildParams& P, cudaStream_t st, int num_sms) {
+    const int DR = P.cost_mode == 1 ? 1 : G;
+    const size_t smem = sizeof(double) * (size_t)COST64_WARPS * (P.maxT > 0 ? P.maxT : 1) * PD * DR * M;
+    if (smem > 48 * 1024) {
+        const cudaError_t ea = cudaFuncSetAttribute(k_cost64<M, G, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (ea != cudaSuccess) return (int)ea;
+    }
+    const long long need = (P.totN + COST64_WARPS - 1) / COST64_WARPS;
+    const long long grid = need < (long long)num_sms * 16 ? need : (long long)num_sms * 16;
+    k_cost64<M, G, PD><<<(unsigned)(grid > 0 ? grid : 1), COST64_WARPS * 32, smem, st>>>(P);
+    return (int)cudaGetLastError();
+}
+
 int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_sm, void* ev0, void* ev1, int* launches) {
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t e0 = (cudaEvent_t)ev0, e1 = (cudaEvent_t)ev1;
@@ -3185,6 +3273,15 @@ int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_s
         if (ea != cudaSuccess) return (int)ea;
         k_compact_fill<<<num_sms * 4, 256, smem, st>>>(P, run_cap);
         ++*launches;
+        if (P.cost64) {
+            int rc = 0;
+            if (P.m == 2 && P.g == 2 && P.p == 3) rc = launch_cost64<2, 2, 3>(P, st, num_sms);
+            else if (P.m == 2 && P.g == 2 && P.p == 5) rc = launch_cost64<2, 2, 5>(P, st, num_sms);
+            else if (P.m == 3 && P.g == 3 && P.p == 5) rc = launch_cost64<3, 3, 5>(P, st, num_sms);
+            else if (P.m == 3 && P.g == 3 && P.p == 7) rc = launch_cost64<3, 3, 7>(P, st, num_sms);
+            if (rc) return rc;
+            ++*launches;
+        }
     }
     return (int)cudaGetLastError();
 }

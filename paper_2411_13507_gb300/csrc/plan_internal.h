@@ -12,6 +12,7 @@ constexpr int NT_MAX = 32;      // durations per call (one bit each in the mask)
 constexpr int TILE = 64;        // tile side of the FP32 pair kernel (states per side)
 constexpr int TILE64 = 32;      // tile side of the FP64 pair kernel
 constexpr int NK_MAX = 65535;   // members per polytope (16-bit local index in re-check entries)
+constexpr int PIPE_FP64 = 3;    // plan_set_tile pipeline: the canonical FP64 pair kernel (FP64 models)
 
 // Host: FP64 tables (see plan_tables.cpp).
 int reach_rows(int g, int p);
@@ -136,6 +137,9 @@ struct BuildParams {
     int tile;                  // tile side of the pair kernel (autotuned, <= TILE)
     int tchunks;               // duration chunks per tile (work items = tiles x tchunks)
     int pipeline;              // FP32 pair kernel: 0 screened, 1 warp-specialised (64-state tiles), 2 unscreened
+    int w64;                   // output weights are doubles (FP64 model)
+    int cost64;                // FP64 model on the FP32 pair kernels: canonical FP64 cost pass after compaction
+    int maxT;                  // most durations of any query
     double eps;
     const QueryDesc* qd;       // [Q]
     const long long* pfxMask;  // [Q+1] prefix of N*W        (membership threads)
