@@ -44,8 +44,9 @@ typedef enum {
     PLAN_F64 = 0,   /* FP64 results: bits of the canonical FP64 margins, costs in canonical FP64
                        (weights are doubles); see plan_set_tile for the two routes */
     PLAN_F32 = 1,   /* FP32 margins; any margin within its error band re-checked in FP64 */
-    PLAN_TF32 = 2,  /* control-point products on tensor cores, TF32 inputs, FP32 accumulate, FP64 re-check */
-    PLAN_BF16 = 3   /* as TF32 with BF16 inputs */
+    PLAN_TF32 = 2,  /* control-point products on tensor cores, TF32 inputs, FP32 accumulate, FP64 re-check;
+                       2-D models only (m = 2; plan_create returns UNSUPPORTED otherwise) */
+    PLAN_BF16 = 3   /* as TF32 with BF16 inputs (2-D models only) */
 } plan_arith;
 
 /* Storage type of states, A and b. */

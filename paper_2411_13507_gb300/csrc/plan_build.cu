@@ -167,9 +167,15 @@ __global__ void k_prep(BuildParams P) {
 // A1 membership: bit k of state i set iff A_k x_i^(0) <= b_k - eps on every
 // row (canonical FP64 decision; FP32 first, FP64 only inside the band).
 // ---------------------------------------------------------------------------
-DEVI void member_word(const BuildParams& P, long long t, int lane) {
+// sA32 / sLim / sOff: the FP32 rows, bounds and row offsets of query 0 staged
+// in shared memory (single-query builds), or null to read global memory.
+DEVI void member_word(const BuildParams& P, long long t, int lane, const float* sA32, const float* sLim,
+                      const int* sOff) {
     const int q = find_q(P.pfxMask, P.Q, t);
     const QueryDesc& Q = P.qd[q];
+    const float* A32 = sA32 ? sA32 : P.A32 + Q.rowsOff * P.m;
+    const float* lim32 = sA32 ? sLim : P.blim32 + Q.rowsOff;
+    const int* poff = sA32 ? sOff : Q.poly_off;
     const long long loc = t - P.pfxMask[q];
     const int i = (int)(loc / Q.W), w = (int)(loc % Q.W);
     const int m = P.m, n = P.m * P.g;
@@ -182,18 +188,17 @@ DEVI void member_word(const BuildParams& P, long long t, int lane) {
     const int k = w * 32 + lane;  // this lane's polytope
     bool in = k < Q.K;
     if (in) {
-        const int r0 = Q.poly_off[k], r1 = Q.poly_off[k + 1];
+        const int r0 = poff[k], r1 = poff[k + 1];
         if (r1 - r0 > P.max_rows || r1 > Q.K * P.max_rows || r0 < 0) in = false;
         // four rows per step: their loads are issued together
         for (int rb = r0; rb < r1 && in; rb += 4) {
             float av[4][4], lim[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const long long rg = Q.rowsOff + rb + u;
                 const bool ok = rb + u < r1;
 #pragma unroll
-                for (int a = 0; a < 4; ++a) av[u][a] = (ok && a < m) ? P.A32[rg * m + a] : 0.f;
-                lim[u] = ok ? P.blim32[rg] : 0.f;
+                for (int a = 0; a < 4; ++a) av[u][a] = (ok && a < m) ? A32[(long long)(rb + u) * m + a] : 0.f;
+                lim[u] = ok ? lim32[rb + u] : 0.f;
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -226,14 +231,36 @@ DEVI void member_word(const BuildParams& P, long long t, int lane) {
     if (lane == 0) P.memMask[Q.maskOff + (long long)i * Q.W + w] = word;
 }
 
-__global__ void __launch_bounds__(256, 4) k_member(BuildParams P) {
+__global__ void __launch_bounds__(256, 4) k_member(BuildParams P, int stage_rows) {
+    extern __shared__ __align__(16) float s_rows[];
     const int lane = threadIdx.x & 31;
     if (block_failed(P.info, nullptr, nullptr)) return;
+    // a single query whose rows fit (stage_rows > 0): its FP32 rows, bounds
+    // and row offsets go to shared memory once per CTA, so that a lane's row
+    // loads are shared-memory loads instead of L2 round trips
+    const float *sA32 = nullptr, *sLim = nullptr;
+    const int* sOff = nullptr;
+    if (stage_rows > 0) {
+        const QueryDesc& Q = P.qd[0];
+        const int R = Q.poly_off[Q.K];
+        float* a = s_rows;
+        float* l = a + (size_t)stage_rows * P.m;
+        int* o = reinterpret_cast<int*>(l + stage_rows);
+        if (R <= stage_rows) {
+            for (int u = threadIdx.x; u < R * P.m; u += blockDim.x) a[u] = P.A32[Q.rowsOff * P.m + u];
+            for (int u = threadIdx.x; u < R; u += blockDim.x) l[u] = P.blim32[Q.rowsOff + u];
+            for (int u = threadIdx.x; u <= Q.K; u += blockDim.x) o[u] = Q.poly_off[u];
+            sA32 = a;
+            sLim = l;
+            sOff = o;
+        }
+        __syncthreads();
+    }
     // one warp per (state, word), persistent: a single wave of CTAs loops
     // over the items (each is a short chain of dependent loads)
     for (long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; t < P.totMask;
          t += ((long long)gridDim.x * blockDim.x) >> 5)
-        member_word(P, t, lane);
+        member_word(P, t, lane, sA32, sLim, sOff);
 }
 
 // ---------------------------------------------------------------------------
@@ -582,7 +609,7 @@ __global__ void k_zero_slots(BuildParams P) {
 }
 
 constexpr int RECHECK_THREADS = 128;  // four warps (one FP64 unit each) per re-check entry
-constexpr int COST64_WARPS = 4;       // warps (rows in flight) per CTA of the FP64 cost pass
+constexpr int COST64_WARPS = 4;       // warps per CTA (one row) of the FP64 cost pass
 
 // Re-check entry: cost-only flag (1 bit) | query (16 bits) | polytope (10) | li (16) | lj (16) | T (5).
 // Bit 63 marks a check that is certainly feasible and needs only its cost in
@@ -2902,38 +2929,37 @@ __global__ void __launch_bounds__(256, 4) k_compact_fill(BuildParams P, int run_
 // left to right without FMA; per segment the squared norm in (d, a) order
 // with FMA, its root; the segments summed in order -- and the weight = the
 // cheapest duration by the key (cost bits with the low five cleared | t),
-// as the FP64 kernel's slot merge takes it.  One warp per row: the start
-// halves of every duration are computed once per row by the lanes (one entry
-// each) into shared memory, each lane then takes edges.
+// as the FP64 kernel's slot merge takes it.  One CTA of four warps per row,
+// one warp on each SM sub-partition and its FP64 unit: the start halves of
+// every duration are computed once per row into shared memory, then each
+// thread takes edges.
 // ---------------------------------------------------------------------------
 template <int M, int G, int PD>
 __global__ void __launch_bounds__(COST64_WARPS * 32) k_cost64(BuildParams P) {
     constexpr int N_ = M * G, TG = 2 * G;
-    extern __shared__ __align__(16) double s_kl[];   // [COST64_WARPS][maxT][E]
+    extern __shared__ __align__(16) double s_kl[];   // [maxT][E]
     if (block_failed(P.info, nullptr, nullptr)) return;
     const TabLayout L = P.L;
     const int DR = P.cost_mode == 1 ? 1 : G;
     const int E = PD * DR * M;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    double* kl = s_kl + (size_t)wib * P.maxT * E;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; row < P.totN; row += nwarps) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (long long row = blockIdx.x; row < P.totN; row += gridDim.x) {
         const int q = find_q(P.pfxN, P.Q, row);
         const QueryDesc& Q = P.qd[q];
         const int i = (int)(row - P.pfxN[q]);
         const int e0 = Q.row_off[i], e1 = Q.row_off[i + 1];
-        if (e1 <= e0) continue;  // warp-uniform
+        if (e1 <= e0) continue;  // block-uniform
         double xi[N_];
 #pragma unroll
         for (int c = 0; c < N_; ++c) xi[c] = ldv(Q.states, (long long)i * N_ + c, P.in_f32);
-        for (int u = lane; u < Q.nT * E; u += 32) {
+        for (int u = tid; u < Q.nT * E; u += nthr) {
             const int t = u / E, r = u % E;
             const int l = r / (DR * M), d = (r / M) % DR, a = r % M;
             const double* tb = P.tab64 + (long long)(Q.tabOff + t) * L.e_stride;
-            kl[u] = half_sum<G>(tb + L.e_C + (d * PD + l) * TG, xi + a, M);
+            s_kl[u] = half_sum<G>(tb + L.e_C + (d * PD + l) * TG, xi + a, M);
         }
-        __syncwarp();
-        for (int e = e0 + lane; e < e1; e += 32) {
+        __syncthreads();
+        for (int e = e0 + tid; e < e1; e += nthr) {
             const int j = Q.col[e];
             uint32_t bits = Q.mask[e];
             double xj[N_];
@@ -2944,7 +2970,7 @@ __global__ void __launch_bounds__(COST64_WARPS * 32) k_cost64(BuildParams P) {
                 const int t = __ffs(bits) - 1;
                 bits &= bits - 1u;
                 const double* tb = P.tab64 + (long long)(Q.tabOff + t) * L.e_stride;
-                const double* klt = kl + t * E;
+                const double* klt = s_kl + t * E;
                 double cost = 0.0;
                 for (int l = 0; l < PD; ++l) {
                     double ss = 0.0;
@@ -2962,7 +2988,7 @@ __global__ void __launch_bounds__(COST64_WARPS * 32) k_cost64(BuildParams P) {
             ((double*)Q.w)[e] = __longlong_as_double((long long)(best & ~31ull));
             Q.tidx[e] = (uint8_t)(best & 31ull);
         }
-        __syncwarp();  // the start halves are rewritten for the next row
+        __syncthreads();  // the start halves are rewritten for the next row
     }
 }
 
@@ -3212,13 +3238,8 @@ bool tc_supported(int m, int g, int p) { return m == 2 && g == 2 && (p == 3 || p
 template <int M, int G, int PD>
 int launch_cost64(const BuildParams& P, cudaStream_t st, int num_sms) {
     const int DR = P.cost_mode == 1 ? 1 : G;
-    const size_t smem = sizeof(double) * (size_t)COST64_WARPS * (P.maxT > 0 ? P.maxT : 1) * PD * DR * M;
-    if (smem > 48 * 1024) {
-        const cudaError_t ea = cudaFuncSetAttribute(k_cost64<M, G, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (ea != cudaSuccess) return (int)ea;
-    }
-    const long long need = (P.totN + COST64_WARPS - 1) / COST64_WARPS;
-    const long long grid = need < (long long)num_sms * 16 ? need : (long long)num_sms * 16;
+    const size_t smem = sizeof(double) * (size_t)(P.maxT > 0 ? P.maxT : 1) * PD * DR * M;  // <= 16 KB
+    const long long grid = P.totN < (long long)num_sms * 16 ? P.totN : (long long)num_sms * 16;
     k_cost64<M, G, PD><<<(unsigned)(grid > 0 ? grid : 1), COST64_WARPS * 32, smem, st>>>(P);
     return (int)cudaGetLastError();
 }
@@ -3233,7 +3254,11 @@ int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_s
     }
     if (P.totMask > 0) {  // also writes the (zero) masks of queries without polytopes
         const long long need = (P.totMask * 32 + 255) / 256;
-        k_member<<<(unsigned)(need < num_sms * 4 ? need : num_sms * 4), 256, 0, st>>>(P);
+        // single query: its rows (up to K * max_rows) staged in shared memory when they fit in 32 KB
+        const long long rows = P.Q == 1 ? P.totRows : 0;
+        const size_t rb = (size_t)rows * (P.m + 1) * sizeof(float) + (size_t)(P.maxK + 1) * sizeof(int);
+        const int stage = (rows > 0 && rb <= 32 * 1024) ? (int)rows : 0;
+        k_member<<<(unsigned)(need < num_sms * 4 ? need : num_sms * 4), 256, stage ? rb : 0, st>>>(P, stage);
         ++*launches;
     }
     if (P.totPoly > 0) {

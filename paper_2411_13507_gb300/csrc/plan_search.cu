@@ -82,7 +82,11 @@ DEVI double ldd(const void* p, long long i, int f32) {
 }
 }  // namespace
 
-constexpr int SWEEP_ROUNDS = 2;
+// check-and-relax rounds of the cooperative search per grid barrier
+#ifndef PLAN_SEARCH_ROUNDS
+#define PLAN_SEARCH_ROUNDS 2
+#endif
+constexpr int SWEEP_ROUNDS = PLAN_SEARCH_ROUNDS;
 
 // (bits, id) pairs ordered lexicographically: the nearest vertex, ties to the lowest id
 DEVI void keep_min(unsigned long long& kb, int& ki, unsigned long long ob, int oi) {
