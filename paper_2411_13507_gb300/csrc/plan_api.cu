@@ -94,6 +94,8 @@ struct plan_ctx {
     unsigned long long* resKey = nullptr;
     int* emitPre = nullptr;
     unsigned long long* recheck = nullptr;
+    double* half64 = nullptr;         // FP64 cost halves of every state, duration and side (FP64 cost pass)
+    long long half64Cap = 0;
     // search scratch
     long long capS = -1;
     unsigned long long* sdist = nullptr;
@@ -418,7 +420,7 @@ void plan_destroy(plan_ctx* c) {
     if (c->stream || c->d_info) cudaStreamSynchronize(c->stream);
     void* dev[] = {c->d_tab64, c->d_tab32, c->d_info, c->memMask, c->counts, c->members, c->localIdx, c->segKL, c->centers,
                    c->blim64, c->A32, c->blim32, c->bc32, c->resOff, c->itemOff, c->ntile, c->tsize, c->iRange, c->rowCount,
-                   c->resBits, c->resKey, c->emitPre, c->recheck, c->sdist, c->sbest, c->spred, c->sfront, c->slast, c->snear,
+                   c->resBits, c->resKey, c->emitPre, c->recheck, c->half64, c->sdist, c->sbest, c->spred, c->sfront, c->slast, c->snear,
                    c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem, c->d_qMem, c->d_rowRange, c->d_sqd, c->memOff,
                    c->d_cut64, c->d_cut32, c->cut_src, c->cut_hit, c->cut_pos, c->cut_chunk, c->cut_orow,
                    c->cut_ocount, c->cut_list32, c->cut_okb, c->cut_obox, c->pl_orow, c->pl_face, c->pl_edge, c->pl_nedge, c->pl_ocount, c->pl_keys, c->pl_near, c->pl_ub, c->d_mpc, c->d_mpcJ, c->g_d, c->g_succ, c->g_wsucc, c->g_anc, c->g_prev};
@@ -558,6 +560,19 @@ int prepare(plan_ctx* c, int Q, const plan_query* qs, int max_rows, int shard = 
     if (want_r == 0) want_r = 1 << 16;
     rc = ensure_device_sized(c, want_s, want_r);
     if (rc != PLAN_OK) return rc;
+    if (c->model.arith == PLAN_F64) {
+        // the FP64 cost pass: both cost halves of every state and duration
+        const int DR = c->model.cost_mode == PLAN_COST_POS ? 1 : c->model.gamma;
+        const long long need = nrow * (long long)maxT * 2 * c->model.degree * DR * c->model.m;
+        if (need > c->half64Cap) {
+            if (c->stage_live) cudaEventSynchronize(c->stage_ev);
+            if (!dalloc(c, &c->half64, need)) {
+                c->half64Cap = 0;
+                return PLAN_ERR_NO_MEMORY;
+            }
+            c->half64Cap = need;
+        }
+    }
     // descriptors + prefixes, uploaded only when they changed
     const size_t bytes = sizeof(QueryDesc) * Q + sizeof(long long) * pfx.size();
     std::vector<char> blob(bytes);
@@ -625,6 +640,7 @@ int issue(plan_ctx* c) {
     P.w64 = c->model.arith == PLAN_F64;
     P.cost64 = c->model.arith == PLAN_F64 && !canonical64;
     P.maxT = c->maxT;
+    P.half64 = c->half64;
     P.max_rows = c->b_max_rows;
     P.tile = (P.arith == PLAN_F64) ? TILE64
              : (P.arith == PLAN_F32) ? (c->tile > 0 ? c->tile : TILE)

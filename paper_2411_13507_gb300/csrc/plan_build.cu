@@ -609,7 +609,6 @@ __global__ void k_zero_slots(BuildParams P) {
 }
 
 constexpr int RECHECK_THREADS = 128;  // four warps (one FP64 unit each) per re-check entry
-constexpr int COST64_WARPS = 4;       // warps per CTA (one row) of the FP64 cost pass
 
 // Re-check entry: cost-only flag (1 bit) | query (16 bits) | polytope (10) | li (16) | lj (16) | T (5).
 // Bit 63 marks a check that is certainly feasible and needs only its cost in
@@ -2929,57 +2928,68 @@ __global__ void __launch_bounds__(256, 4) k_compact_fill(BuildParams P, int run_
 // left to right without FMA; per segment the squared norm in (d, a) order
 // with FMA, its root; the segments summed in order -- and the weight = the
 // cheapest duration by the key (cost bits with the low five cleared | t),
-// as the FP64 kernel's slot merge takes it.  One CTA of four warps per row,
-// one warp on each SM sub-partition and its FP64 unit: the start halves of
-// every duration are computed once per row into shared memory, then each
-// thread takes edges.
+// as the FP64 kernel's slot merge takes it.  The halves depend on one state
+// and one duration only, so k_halves64 computes both halves of every state
+// and duration once (half64 [state][t][side][row]); k_cost64 then adds,
+// squares and takes roots per (edge, duration), one warp per row with the
+// lanes over its edges (the start state's halves are the same for the warp).
 // ---------------------------------------------------------------------------
 template <int M, int G, int PD>
-__global__ void __launch_bounds__(COST64_WARPS * 32) k_cost64(BuildParams P) {
+__global__ void __launch_bounds__(256) k_halves64(BuildParams P) {
     constexpr int N_ = M * G, TG = 2 * G;
-    extern __shared__ __align__(16) double s_kl[];   // [maxT][E]
     if (block_failed(P.info, nullptr, nullptr)) return;
     const TabLayout L = P.L;
     const int DR = P.cost_mode == 1 ? 1 : G;
     const int E = PD * DR * M;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    for (long long row = blockIdx.x; row < P.totN; row += gridDim.x) {
+    const long long per = (long long)P.maxT * 2 * E;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < P.totN * per;
+         u += (long long)gridDim.x * blockDim.x) {
+        const long long row = u / per;
+        const int rem = (int)(u % per), t = rem / (2 * E), side = (rem / E) & 1, r = rem % E;
+        const int q = find_q(P.pfxN, P.Q, row);
+        const QueryDesc& Q = P.qd[q];
+        if (t >= Q.nT) continue;
+        const long long i = row - P.pfxN[q];
+        const int l = r / (DR * M), d = (r / M) % DR, a = r % M;
+        double x[N_];
+#pragma unroll
+        for (int c = 0; c < N_; ++c) x[c] = ldv(Q.states, i * N_ + c, P.in_f32);
+        const double* tb = P.tab64 + (long long)(Q.tabOff + t) * L.e_stride;
+        P.half64[u] = half_sum<G>(tb + L.e_C + (d * PD + l) * TG + side * G, x + a, M);
+    }
+}
+
+template <int M, int G, int PD>
+__global__ void __launch_bounds__(256) k_cost64(BuildParams P) {
+    if (block_failed(P.info, nullptr, nullptr)) return;
+    const int DR = P.cost_mode == 1 ? 1 : G;
+    const int E = PD * DR * M;
+    const long long per = (long long)P.maxT * 2 * E;
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; row < P.totN; row += nwarps) {
         const int q = find_q(P.pfxN, P.Q, row);
         const QueryDesc& Q = P.qd[q];
         const int i = (int)(row - P.pfxN[q]);
         const int e0 = Q.row_off[i], e1 = Q.row_off[i + 1];
-        if (e1 <= e0) continue;  // block-uniform
-        double xi[N_];
-#pragma unroll
-        for (int c = 0; c < N_; ++c) xi[c] = ldv(Q.states, (long long)i * N_ + c, P.in_f32);
-        for (int u = tid; u < Q.nT * E; u += nthr) {
-            const int t = u / E, r = u % E;
-            const int l = r / (DR * M), d = (r / M) % DR, a = r % M;
-            const double* tb = P.tab64 + (long long)(Q.tabOff + t) * L.e_stride;
-            s_kl[u] = half_sum<G>(tb + L.e_C + (d * PD + l) * TG, xi + a, M);
-        }
-        __syncthreads();
-        for (int e = e0 + tid; e < e1; e += nthr) {
+        const double* hi = P.half64 + row * per;
+        for (int e = e0 + lane; e < e1; e += 32) {
             const int j = Q.col[e];
+            const double* hj = P.half64 + (P.pfxN[q] + j) * per;
             uint32_t bits = Q.mask[e];
-            double xj[N_];
-#pragma unroll
-            for (int c = 0; c < N_; ++c) xj[c] = ldv(Q.states, (long long)j * N_ + c, P.in_f32);
             unsigned long long best = KEY_NONE;
             while (bits) {
                 const int t = __ffs(bits) - 1;
                 bits &= bits - 1u;
-                const double* tb = P.tab64 + (long long)(Q.tabOff + t) * L.e_stride;
-                const double* klt = s_kl + t * E;
+                const double* kl = hi + (long long)t * 2 * E;      // start half (side 0) of state i
+                const double* kr = hj + (long long)t * 2 * E + E;  // end half (side 1) of state j
                 double cost = 0.0;
                 for (int l = 0; l < PD; ++l) {
                     double ss = 0.0;
-                    for (int d = 0; d < DR; ++d)
-                        for (int a = 0; a < M; ++a) {
-                            const double v = klt[(l * DR + d) * M + a] +
-                                             half_sum<G>(tb + L.e_C + (d * PD + l) * TG + G, xj + a, M);
-                            ss = fma(v, v, ss);
-                        }
+                    for (int w = 0; w < DR * M; ++w) {
+                        const double v = kl[l * DR * M + w] + kr[l * DR * M + w];
+                        ss = fma(v, v, ss);
+                    }
                     cost += sqrt(ss);
                 }
                 const unsigned long long key = key_f64(cost, t);
@@ -2988,7 +2998,6 @@ __global__ void __launch_bounds__(COST64_WARPS * 32) k_cost64(BuildParams P) {
             ((double*)Q.w)[e] = __longlong_as_double((long long)(best & ~31ull));
             Q.tidx[e] = (uint8_t)(best & 31ull);
         }
-        __syncthreads();  // the start halves are rewritten for the next row
     }
 }
 
@@ -3238,9 +3247,11 @@ bool tc_supported(int m, int g, int p) { return m == 2 && g == 2 && (p == 3 || p
 template <int M, int G, int PD>
 int launch_cost64(const BuildParams& P, cudaStream_t st, int num_sms) {
     const int DR = P.cost_mode == 1 ? 1 : G;
-    const size_t smem = sizeof(double) * (size_t)(P.maxT > 0 ? P.maxT : 1) * PD * DR * M;  // <= 16 KB
-    const long long grid = P.totN < (long long)num_sms * 16 ? P.totN : (long long)num_sms * 16;
-    k_cost64<M, G, PD><<<(unsigned)(grid > 0 ? grid : 1), COST64_WARPS * 32, smem, st>>>(P);
+    const long long n = P.totN * (long long)P.maxT * 2 * PD * DR * M;
+    const long long hb = (n + 255) / 256;
+    k_halves64<M, G, PD><<<(unsigned)(hb < (long long)num_sms * 8 ? (hb > 0 ? hb : 1) : (long long)num_sms * 8), 256, 0, st>>>(P);
+    const long long cb = (P.totN * 32 + 255) / 256;
+    k_cost64<M, G, PD><<<(unsigned)(cb < (long long)num_sms * 8 ? (cb > 0 ? cb : 1) : (long long)num_sms * 8), 256, 0, st>>>(P);
     return (int)cudaGetLastError();
 }
 
@@ -3305,7 +3316,7 @@ int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_s
             else if (P.m == 3 && P.g == 3 && P.p == 5) rc = launch_cost64<3, 3, 5>(P, st, num_sms);
             else if (P.m == 3 && P.g == 3 && P.p == 7) rc = launch_cost64<3, 3, 7>(P, st, num_sms);
             if (rc) return rc;
-            ++*launches;
+            *launches += 2;
         }
     }
     return (int)cudaGetLastError();

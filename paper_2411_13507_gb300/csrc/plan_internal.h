@@ -140,6 +140,7 @@ struct BuildParams {
     int w64;                   // output weights are doubles (FP64 model)
     int cost64;                // FP64 model on the FP32 pair kernels: canonical FP64 cost pass after compaction
     int maxT;                  // most durations of any query
+    double* half64;            // [totN][maxT][2][p * DR * m] FP64 cost halves (FP64 cost pass)
     double eps;
     const QueryDesc* qd;       // [Q]
     const long long* pfxMask;  // [Q+1] prefix of N*W        (membership threads)

@@ -84,7 +84,7 @@ DEVI double ldd(const void* p, long long i, int f32) {
 
 // check-and-relax rounds of the cooperative search per grid barrier
 #ifndef PLAN_SEARCH_ROUNDS
-#define PLAN_SEARCH_ROUNDS 2
+#define PLAN_SEARCH_ROUNDS 4
 #endif
 constexpr int SWEEP_ROUNDS = PLAN_SEARCH_ROUNDS;
 
