@@ -2931,8 +2931,7 @@ __global__ void __launch_bounds__(256, 4) k_compact_fill(BuildParams P, int run_
 // as the FP64 kernel's slot merge takes it.  The halves depend on one state
 // and one duration only, so k_halves64 computes both halves of every state
 // and duration once (half64 [state][t][side][row]); k_cost64 then adds,
-// squares and takes roots per (edge, duration), one warp per row with the
-// lanes over its edges (the start state's halves are the same for the warp).
+// squares and takes roots per (edge, duration), one thread per edge.
 // ---------------------------------------------------------------------------
 template <int M, int G, int PD>
 __global__ void __launch_bounds__(256) k_halves64(BuildParams P) {
@@ -2965,39 +2964,43 @@ __global__ void __launch_bounds__(256) k_cost64(BuildParams P) {
     const int DR = P.cost_mode == 1 ? 1 : G;
     const int E = PD * DR * M;
     const long long per = (long long)P.maxT * 2 * E;
-    const int lane = threadIdx.x & 31;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; row < P.totN; row += nwarps) {
-        const int q = find_q(P.pfxN, P.Q, row);
-        const QueryDesc& Q = P.qd[q];
-        const int i = (int)(row - P.pfxN[q]);
-        const int e0 = Q.row_off[i], e1 = Q.row_off[i + 1];
-        const double* hi = P.half64 + row * per;
-        for (int e = e0 + lane; e < e1; e += 32) {
-            const int j = Q.col[e];
-            const double* hj = P.half64 + (P.pfxN[q] + j) * per;
-            uint32_t bits = Q.mask[e];
-            unsigned long long best = KEY_NONE;
-            while (bits) {
-                const int t = __ffs(bits) - 1;
-                bits &= bits - 1u;
-                const double* kl = hi + (long long)t * 2 * E;      // start half (side 0) of state i
-                const double* kr = hj + (long long)t * 2 * E + E;  // end half (side 1) of state j
-                double cost = 0.0;
-                for (int l = 0; l < PD; ++l) {
-                    double ss = 0.0;
-                    for (int w = 0; w < DR * M; ++w) {
-                        const double v = kl[l * DR * M + w] + kr[l * DR * M + w];
-                        ss = fma(v, v, ss);
-                    }
-                    cost += sqrt(ss);
-                }
-                const unsigned long long key = key_f64(cost, t);
-                if (key < best) best = key;
-            }
-            ((double*)Q.w)[e] = __longlong_as_double((long long)(best & ~31ull));
-            Q.tidx[e] = (uint8_t)(best & 31ull);
+    // one thread per edge (blocks of query blockIdx.y): full warps, since the
+    // narrow FP64 pipe is what bounds this pass
+    const int q = blockIdx.y;
+    const QueryDesc& Q = P.qd[q];
+    const long long E_q = *Q.count;
+    const int N = Q.N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < E_q; e += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = N;  // the row of edge e: largest i with row_off[i] <= e
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (Q.row_off[mid] <= e) lo = mid;
+            else hi = mid;
         }
+        const int i = lo, j = Q.col[e];
+        const double* hi64 = P.half64 + (P.pfxN[q] + i) * per;
+        const double* hj64 = P.half64 + (P.pfxN[q] + j) * per;
+        uint32_t bits = Q.mask[e];
+        unsigned long long best = KEY_NONE;
+        while (bits) {
+            const int t = __ffs(bits) - 1;
+            bits &= bits - 1u;
+            const double* kl = hi64 + (long long)t * 2 * E;      // start half (side 0) of state i
+            const double* kr = hj64 + (long long)t * 2 * E + E;  // end half (side 1) of state j
+            double cost = 0.0;
+            for (int l = 0; l < PD; ++l) {
+                double ss = 0.0;
+                for (int w = 0; w < DR * M; ++w) {
+                    const double v = kl[l * DR * M + w] + kr[l * DR * M + w];
+                    ss = fma(v, v, ss);
+                }
+                cost += sqrt(ss);
+            }
+            const unsigned long long key = key_f64(cost, t);
+            if (key < best) best = key;
+        }
+        ((double*)Q.w)[e] = __longlong_as_double((long long)(best & ~31ull));
+        Q.tidx[e] = (uint8_t)(best & 31ull);
     }
 }
 
@@ -3250,8 +3253,9 @@ int launch_cost64(const BuildParams& P, cudaStream_t st, int num_sms) {
     const long long n = P.totN * (long long)P.maxT * 2 * PD * DR * M;
     const long long hb = (n + 255) / 256;
     k_halves64<M, G, PD><<<(unsigned)(hb < (long long)num_sms * 8 ? (hb > 0 ? hb : 1) : (long long)num_sms * 8), 256, 0, st>>>(P);
-    const long long cb = (P.totN * 32 + 255) / 256;
-    k_cost64<M, G, PD><<<(unsigned)(cb < (long long)num_sms * 8 ? (cb > 0 ? cb : 1) : (long long)num_sms * 8), 256, 0, st>>>(P);
+    // blocks per query: about four CTAs per SM over the batch, at least one
+    const int bx = (int)((long long)num_sms * 4 / P.Q > 0 ? (long long)num_sms * 4 / P.Q : 1);
+    k_cost64<M, G, PD><<<dim3((unsigned)bx, (unsigned)P.Q), 256, 0, st>>>(P);
     return (int)cudaGetLastError();
 }
 
