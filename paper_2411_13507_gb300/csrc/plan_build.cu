@@ -167,15 +167,12 @@ __global__ void k_prep(BuildParams P) {
 // A1 membership: bit k of state i set iff A_k x_i^(0) <= b_k - eps on every
 // row (canonical FP64 decision; FP32 first, FP64 only inside the band).
 // ---------------------------------------------------------------------------
-// sA32 / sLim / sOff: the FP32 rows, bounds and row offsets of query 0 staged
-// in shared memory (single-query builds), or null to read global memory.
-DEVI void member_word(const BuildParams& P, long long t, int lane, const float* sA32, const float* sLim,
-                      const int* sOff) {
+DEVI void member_word(const BuildParams& P, long long t, int lane) {
     const int q = find_q(P.pfxMask, P.Q, t);
     const QueryDesc& Q = P.qd[q];
-    const float* A32 = sA32 ? sA32 : P.A32 + Q.rowsOff * P.m;
-    const float* lim32 = sA32 ? sLim : P.blim32 + Q.rowsOff;
-    const int* poff = sA32 ? sOff : Q.poly_off;
+    const float* A32 = P.A32 + Q.rowsOff * P.m;
+    const float* lim32 = P.blim32 + Q.rowsOff;
+    const int* poff = Q.poly_off;
     const long long loc = t - P.pfxMask[q];
     const int i = (int)(loc / Q.W), w = (int)(loc % Q.W);
     const int m = P.m, n = P.m * P.g;
@@ -231,36 +228,14 @@ DEVI void member_word(const BuildParams& P, long long t, int lane, const float* 
     if (lane == 0) P.memMask[Q.maskOff + (long long)i * Q.W + w] = word;
 }
 
-__global__ void __launch_bounds__(256, 4) k_member(BuildParams P, int stage_rows) {
-    extern __shared__ __align__(16) float s_rows[];
+__global__ void __launch_bounds__(256, 4) k_member(BuildParams P) {
     const int lane = threadIdx.x & 31;
     if (block_failed(P.info, nullptr, nullptr)) return;
-    // a single query whose rows fit (stage_rows > 0): its FP32 rows, bounds
-    // and row offsets go to shared memory once per CTA, so that a lane's row
-    // loads are shared-memory loads instead of L2 round trips
-    const float *sA32 = nullptr, *sLim = nullptr;
-    const int* sOff = nullptr;
-    if (stage_rows > 0) {
-        const QueryDesc& Q = P.qd[0];
-        const int R = Q.poly_off[Q.K];
-        float* a = s_rows;
-        float* l = a + (size_t)stage_rows * P.m;
-        int* o = reinterpret_cast<int*>(l + stage_rows);
-        if (R <= stage_rows) {
-            for (int u = threadIdx.x; u < R * P.m; u += blockDim.x) a[u] = P.A32[Q.rowsOff * P.m + u];
-            for (int u = threadIdx.x; u < R; u += blockDim.x) l[u] = P.blim32[Q.rowsOff + u];
-            for (int u = threadIdx.x; u <= Q.K; u += blockDim.x) o[u] = Q.poly_off[u];
-            sA32 = a;
-            sLim = l;
-            sOff = o;
-        }
-        __syncthreads();
-    }
     // one warp per (state, word), persistent: a single wave of CTAs loops
     // over the items (each is a short chain of dependent loads)
     for (long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; t < P.totMask;
          t += ((long long)gridDim.x * blockDim.x) >> 5)
-        member_word(P, t, lane, sA32, sLim, sOff);
+        member_word(P, t, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -3269,11 +3244,7 @@ int launch_build(const BuildParams& P, void* stream, int num_sms, int ctas_per_s
     }
     if (P.totMask > 0) {  // also writes the (zero) masks of queries without polytopes
         const long long need = (P.totMask * 32 + 255) / 256;
-        // single query: its rows (up to K * max_rows) staged in shared memory when they fit in 32 KB
-        const long long rows = P.Q == 1 ? P.totRows : 0;
-        const size_t rb = (size_t)rows * (P.m + 1) * sizeof(float) + (size_t)(P.maxK + 1) * sizeof(int);
-        const int stage = (rows > 0 && rb <= 32 * 1024) ? (int)rows : 0;
-        k_member<<<(unsigned)(need < num_sms * 4 ? need : num_sms * 4), 256, stage ? rb : 0, st>>>(P, stage);
+        k_member<<<(unsigned)(need < num_sms * 4 ? need : num_sms * 4), 256, 0, st>>>(P);
         ++*launches;
     }
     if (P.totPoly > 0) {
