@@ -3228,9 +3228,11 @@ int launch_cost64(const BuildParams& P, cudaStream_t st, int num_sms) {
     const long long n = P.totN * (long long)P.maxT * 2 * PD * DR * M;
     const long long hb = (n + 255) / 256;
     k_halves64<M, G, PD><<<(unsigned)(hb < (long long)num_sms * 8 ? (hb > 0 ? hb : 1) : (long long)num_sms * 8), 256, 0, st>>>(P);
-    // blocks per query: about four CTAs per SM over the batch, at least one
-    const int bx = (int)((long long)num_sms * 4 / P.Q > 0 ? (long long)num_sms * 4 / P.Q : 1);
-    k_cost64<M, G, PD><<<dim3((unsigned)bx, (unsigned)P.Q), 256, 0, st>>>(P);
+    // blocks per query: about eight two-warp CTAs per SM over the batch, at
+    // least one; small CTAs spread a small graph's edges over every SM's
+    // FP64 units (the CTAs past the edges exit at once)
+    const int bx = (int)((long long)num_sms * 8 / P.Q > 0 ? (long long)num_sms * 8 / P.Q : 1);
+    k_cost64<M, G, PD><<<dim3((unsigned)bx, (unsigned)P.Q), 64, 0, st>>>(P);
     return (int)cudaGetLastError();
 }
 
