@@ -1113,16 +1113,23 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dist = None
-    if world > 1:
+    shard_rows = args.shard == "rows"
+    if world > 1 or shard_rows:
+        # --shard rows on one GPU still runs the whole sharded path: one shard,
+        # the NCCL exchange with a world of one, the search on the merged graph
         import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if world == 1:
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            os.environ.setdefault("MASTER_PORT", str(29500 + (os.getpid() % 1000)))
+            dist.init_process_group("nccl", rank=0, world_size=1)
+        else:
+            dist.init_process_group("nccl")
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
-    shard_rows = args.shard == "rows" and world > 1
     # CPU baseline first (before heavy GPU work; threads, no fork)
     prob = workload(args.seed if shard_rows else args.seed + rank)
     cpu = None

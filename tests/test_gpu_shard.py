@@ -104,3 +104,23 @@ def test_precision_form_shards():
         merged, _, _ = build_sharded(pl, dp, 3)
         same(merged, single)
         pl.close()
+
+
+def test_row_shards_at_the_benchmark_size():
+    """The 3-D benchmark workload (N = 8192, K = 64, nT = 16) in four shards:
+    the merged graph equals the single build bit for bit, and the shards'
+    work is balanced (each within 5% of a quarter of the candidates)."""
+    prob = synth.triple_integrator_3d(seed=2)
+    pl = P.Planner.for_problem(prob, arith="f32", input="f32")
+    dp = P.to_device(prob, input="f32")
+    single = pl.build_edges(dp)
+    cand = int(pl.info()["candidates"])
+    per = []
+    for r in range(4):
+        pl.build_edges_shard(dp, r, 4)
+        per.append(int(pl.info()["candidates"]))
+    merged, ranges, c = build_sharded(pl, dp, 4)
+    same(merged, single)
+    assert c == cand and sum(per) == cand
+    assert max(per) <= 1.05 * cand / 4, per
+    pl.close()
