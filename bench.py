@@ -248,7 +248,7 @@ def run_reference(args):
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": f"~{len(rng_rows[0])} rows of {prob.N} per step, {args.steps} steps"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    emit(line)
     return 0
 
 
@@ -1098,13 +1098,33 @@ def run_mpc_form(args, stream, flush, dev):
             "cpu_baseline": cpu}
 
 
+_RESULT = None
+
+
+def claim_stdout():
+    """Keep the process's standard output for the one result line: from here on
+    anything else written to fd 1 (NCCL's version banner, library messages)
+    goes to stderr, and emit() writes to a duplicate of the original fd 1."""
+    global _RESULT
+    sys.stdout.flush()
+    _RESULT = os.fdopen(os.dup(1), "w")
+    os.dup2(2, 1)
+
+
+def emit(line):
+    out = _RESULT or sys.stdout
+    out.write(json.dumps(line) + "\n")
+    out.flush()
+
+
 def main():
     args = parse()
+    claim_stdout()
     if args.impl == "reference":
         return run_reference(args)
     if args.form != "plain":
         line = run_form(args)
-        print(json.dumps(line), flush=True)
+        emit(line)
         return 0
     import torch
     from paper_2411_13507_gb300 import plan as P
@@ -1338,7 +1358,7 @@ def main():
         "cpu_baseline": ({k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")} if cpu else None),
     }
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        emit(line)
     if dist:
         dist.destroy_process_group()
     pl.close()
