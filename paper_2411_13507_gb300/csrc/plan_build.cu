@@ -1234,6 +1234,30 @@ DEVI float cost_segments(const float (&x)[M * G], const float* tab, int DR, int 
     return mag;
 }
 
+// Control-polygon length of one pair from its cost halves: per segment the
+// root of the sum of squares of (left + right) over PL padded rows, in row
+// order, summed over the PD segments in order (both loops unrolled).
+template <int PD, int PL>
+DEVI float pair_cost(const float* cl, const float* cr) {
+    float cs = 0.f;
+#pragma unroll
+    for (int l = 0; l < PD; ++l) {
+        float ss = 0.f;
+#pragma unroll
+        for (int q = 0; q < PL; q += 4) {
+            const float4 a = *reinterpret_cast<const float4*>(cl + l * PL + q);
+            const float4 b = *reinterpret_cast<const float4*>(cr + l * PL + q);
+            const float d0 = a.x + b.x, d1 = a.y + b.y, d2 = a.z + b.z, d3 = a.w + b.w;
+            ss = fmaf(d0, d0, ss);
+            ss = fmaf(d1, d1, ss);
+            ss = fmaf(d2, d2, ss);
+            ss = fmaf(d3, d3, ss);
+        }
+        cs += sqrtf(ss);
+    }
+    return cs;
+}
+
 template <int M, int G, int PD>
 __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
     using S = Shape<G, PD>;
@@ -1245,6 +1269,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
     extern __shared__ __align__(16) float sm[];
     const int DR = P.cost_mode == 1 ? 1 : G;
     const int PL = (DR * M + 3) & ~3;  // cost rows of one segment, padded with zeros
+    constexpr int PLG = (G * M + 3) & ~3;  // PL of the full cost (DR = G); 4 for DR = 1
     const int SF = sc_free_stride(NI, P.max_rows, PD, PL);
     float* UL = sm;                  // [T][SU] reach halves, start states
     float* UR = UL + T * SU;         //          end states
@@ -1427,7 +1452,6 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
             // 3. every reach and free row of the screened pairs
             const int n1 = s_n1;
             if (tid == 0) nscreened += (unsigned long long)n1;
-            const int FQ = NI * nrp;
             for (int e = tid; e < n1; e += nthr) {
                 const int v = list1[e];
                 const int li = v >> 8, lj = v & 255;
@@ -1452,14 +1476,17 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                     const float* fl = FL + li * SF;
                     const float* fr = FR + lj * SF;
                     float f4[4] = {NEG_INF, NEG_INF, NEG_INF, NEG_INF};
-#pragma unroll 2
-                    for (int r = 0; r < FQ; r += 4) {
-                        const float4 a = *reinterpret_cast<const float4*>(fl + r);
-                        const float4 b = *reinterpret_cast<const float4*>(fr + r);
-                        f4[0] = fmaxf(f4[0], a.x + b.x);
-                        f4[1] = fmaxf(f4[1], a.y + b.y);
-                        f4[2] = fmaxf(f4[2], a.z + b.z);
-                        f4[3] = fmaxf(f4[3], a.w + b.w);
+                    // row quads of all NI interior points per pass: 2 NI loads in flight
+                    for (int rq = 0; rq < nrp; rq += 4) {
+#pragma unroll
+                        for (int l = 0; l < NI; ++l) {
+                            const float4 a = *reinterpret_cast<const float4*>(fl + l * nrp + rq);
+                            const float4 b = *reinterpret_cast<const float4*>(fr + l * nrp + rq);
+                            f4[0] = fmaxf(f4[0], a.x + b.x);
+                            f4[1] = fmaxf(f4[1], a.y + b.y);
+                            f4[2] = fmaxf(f4[2], a.z + b.z);
+                            f4[3] = fmaxf(f4[3], a.w + b.w);
+                        }
                     }
                     const float fm = fmaxf(fmaxf(f4[0], f4[1]), fmaxf(f4[2], f4[3]));
                     const float bandF = KF * (magF[li] + magF[T + lj]);
@@ -1502,21 +1529,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                     const int li = v >> 8, lj = v & 255;
                     const float* cl = FL + li * SF;
                     const float* cr = FR + lj * SF;
-                    float cs = 0.f;
-#pragma unroll
-                    for (int l = 0; l < PD; ++l) {
-                        float ss = 0.f;
-                        for (int q = 0; q < PL; q += 4) {
-                            const float4 a = *reinterpret_cast<const float4*>(cl + l * PL + q);
-                            const float4 b = *reinterpret_cast<const float4*>(cr + l * PL + q);
-                            const float d0 = a.x + b.x, d1 = a.y + b.y, d2 = a.z + b.z, d3 = a.w + b.w;
-                            ss = fmaf(d0, d0, ss);
-                            ss = fmaf(d1, d1, ss);
-                            ss = fmaf(d2, d2, ss);
-                            ss = fmaf(d3, d3, ss);
-                        }
-                        cs += sqrtf(ss);
-                    }
+                    const float cs = PL == PLG ? pair_cost<PD, PLG>(cl, cr) : pair_cost<PD, 4>(cl, cr);
                     if (P.cost64 || magC[li] + magC[T + lj] <= COST_RHO * cs) {  // FP64 models re-cost every edge anyway
                         const long long slot = itd.base + (long long)(i0 + li) * itd.nk + (j0 + lj);
                         atomicOr(&P.resBits[slot], 1u << t);
