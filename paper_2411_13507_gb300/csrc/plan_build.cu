@@ -1234,6 +1234,52 @@ DEVI float cost_segments(const float (&x)[M * G], const float* tab, int DR, int 
     return mag;
 }
 
+// The next item for a block, or past the end once the build has failed.
+DEVI long long take_item(DevInfo* info) {
+    const long long it = (long long)atomicAdd(&info->ticket, 1u);
+    return has_failed(info) ? 0x7fffffffffffLL : it;
+}
+
+// Half H of one staged state: elements [H*EH, (H+1)*EH) of the XS-float row
+// (positions centred on the polytope, FP32; zero for padding states and
+// padding elements), and the maxima over the axes of the derivatives whose
+// M elements lie in this half.
+template <int M, int G, int XS, int H>
+DEVI void stage_state_half(const void* states, bool in_f32, long long id, bool valid, const float (&cx)[M],
+                           float* xrow, float* xa) {
+    constexpr int N_ = M * G, EH = XS / 2;
+    static_assert(XS % 2 == 0 && EH % M == 0, "a derivative's axes lie in one half of the staged state");
+    float v[EH];
+#pragma unroll
+    for (int q = 0; q < EH; ++q) {
+        const int e = H * EH + q;
+        float x = 0.f;
+        if (valid && e < N_) {
+            if (e < M) {
+                if (in_f32) x = ((const float*)states)[id * N_ + e] - cx[e < M ? e : 0];
+                else x = (float)(((const double*)states)[id * N_ + e] - (double)cx[e < M ? e : 0]);
+            } else {
+                x = ldf(states, id * N_ + e, in_f32);
+            }
+        }
+        v[q] = x;
+    }
+#pragma unroll
+    for (int q = 0; q < EH; ++q) xrow[H * EH + q] = v[q];
+#pragma unroll
+    for (int c = 0; c < G; ++c) {
+        if (c * M >= H * EH && c * M < (H + 1) * EH) {
+            float mx = 0.f;
+#pragma unroll
+            for (int a = 0; a < M; ++a) {
+                const int q = c * M + a - H * EH;  // in [0, EH) inside this branch
+                mx = fmaxf(mx, fabsf(v[q >= 0 && q < EH ? q : 0]));
+            }
+            xa[c] = mx;
+        }
+    }
+}
+
 // Control-polygon length of one pair from its cost halves: per segment the
 // root of the sum of squares of (left + right) over PL padded rows, in row
 // order, summed over the PD segments in order (both loops unrolled).
@@ -1297,10 +1343,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
     const float NEG_INF = -__int_as_float(0x7f800000);
 
     for (;;) {
-        if (tid == 0) {
-            const long long it = (long long)atomicAdd(&P.info->ticket, 1u);
-            s_item = has_failed(P.info) ? 0x7fffffffffffLL : it;  // one decision for the whole block
-        }
+        if (tid == 0) s_item = take_item(P.info);
         __syncthreads();
         const long long item = s_item;
         if (item >= nitems) break;
@@ -1325,49 +1368,42 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
         float cx[M];
 #pragma unroll
         for (int a = 0; a < M; ++a) cx[a] = P.centers[(long long)(Qd.kOff + k) * 4 + a];
-        for (int u = tid; u < S2 * XS; u += nthr) {
-            const int s = u / XS, e = u % XS;
+        // two threads per state (the second S2 threads take the second
+        // halves), each loading the member id once and half of the state's
+        // elements, all of its loads in flight together; each also writes the
+        // per-derivative maxima over the axes of its half
+        for (int u = tid; u < 2 * S2; u += nthr) {
+            const bool hi = u >= S2;  // warp-uniform halves for whole tiles
+            const int s = hi ? u - S2 : u;
             const bool right = s >= ni4;
             const int ls = right ? s - ni4 : s;
-            const int lidx = (right ? j0 : i0) + ls;
-            float v = 0.f;
-            if (e < N_ && ls < (right ? TJ : TI)) {
-                const long long id = mem_id(members[lidx]);
-                if (e < M) {
-                    if (P.in_f32) v = ((const float*)Qd.states)[id * N_ + e] - cx[e];
-                    else v = (float)(((const double*)Qd.states)[id * N_ + e] - (double)cx[e]);
-                } else {
-                    v = ldf(Qd.states, id * N_ + e, P.in_f32);
-                }
-            }
-            xs[(right ? T + ls : ls) * XS + e] = v;
+            const bool valid = ls < (right ? TJ : TI);
+            const long long id = valid ? mem_id(members[(right ? j0 : i0) + ls]) : 0;
+            const int row = right ? T + ls : ls;
+            if (hi) stage_state_half<M, G, XS, 1>(Qd.states, P.in_f32, id, valid, cx, xs + row * XS, xab + row * G);
+            else stage_state_half<M, G, XS, 0>(Qd.states, P.in_f32, id, valid, cx, xs + row * XS, xab + row * G);
         }
-        stage_table<G, PD>(tabs, P.tab32 + (long long)(Qd.tabOff + itc.t0) * fst, tid, nthr);
-        __syncthreads();
-        for (int s = tid; s < S2; s += nthr) {
-            const bool right = s >= ni4;
-            const int ls = right ? s - ni4 : s;
-            const float* x = xs + (right ? T + ls : ls) * XS;
-            float* xa = xab + (right ? T + ls : ls) * G;
-#pragma unroll
-            for (int c = 0; c < G; ++c) {
-                float mx = 0.f;
-#pragma unroll
-                for (int a = 0; a < M; ++a) mx = fmaxf(mx, fabsf(x[c * M + a]));
-                xa[c] = mx;
-            }
-        }
-        if (tid == 0) {
+        if (tid < 32) {  // band scalars of the polytope's rows (warp 0, rows from global memory)
             float rn = 0.f, bm = 0.f;
-            for (int r = 0; r < nr; ++r) {
+            for (int r = tid; r < nr; r += 32) {
                 float s1 = 0.f;
-                for (int a = 0; a < M; ++a) s1 += fabsf(Ab[r * 4 + a]);
+#pragma unroll
+                for (int a = 0; a < M; ++a) s1 += fabsf(P.A32[(rg0 + r) * M + a]);
                 rn = fmaxf(rn, s1);
-                bm = fmaxf(bm, fabsf(Ab[r * 4 + M]));
+                bm = fmaxf(bm, fabsf(P.bc32[rg0 + r]));
             }
-            s_rown1 = rn * 1.0001f;
-            s_bmax = bm;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                rn = fmaxf(rn, __shfl_xor_sync(0xffffffffu, rn, o));
+                bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+            }
+            if (tid == 0) {
+                s_rown1 = rn * 1.0001f;
+                s_bmax = bm;
+            }
         }
+        stage_table_async<G, PD>(tabs, P.tab32 + (long long)(Qd.tabOff + itc.t0) * fst, tid, nthr);
+        cp_async_wait_all();
         __syncthreads();
 
         const int ngi = ni4 >> 2, ngj = nj4 >> 2;
@@ -1427,6 +1463,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
             if (t + 1 < itc.t1)
                 stage_table_async<G, PD>(tabs + ((t + 1 - itc.t0) & 1) * PT::FLOATS,
                                          P.tab32 + (long long)(Qd.tabOff + t + 1) * fst, tid, nthr);
+
             // 2. screen and list 1 (positions by a warp prefix of the survivor
             // counts and one shared atomic per warp; the block is whole warps)
             {
