@@ -20,6 +20,7 @@
 // result) is: each half summed left to right without FMA, then the two
 // halves added; see the FP64 kernel and the re-check kernel.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -42,6 +43,19 @@ constexpr float KU = 5.9604644775390625e-08f;  // 2^-24
 constexpr float KR = 16.f * KU;
 constexpr float KF = 24.f * KU;
 constexpr float KMEM = 16.f * KU;
+// Half-precision screen.  The screen row-axes of the reach halves are rounded
+// to FP16 and summed in FP16.  Each of those three roundings errs by at most
+// 2^-11 of its result (2^-25 absolute below the normal range), so the FP16 sum
+// is within 2^-10 (1 + 2^-11) (|u| + |w|) + 3 * 2^-25 of the exact sum u + w of
+// the FP32 halves, and the reach band already bounds that sum's distance to
+// the exact margin; |u| <= magR of its state (the band magnitude bounds every
+// reach row-axis).
+// The screen therefore widens the reach band by KH = 2^-9 times the magnitude
+// sum (1.999 times the bound) plus EH = 2^-20, and rejects nothing whose magnitude
+// sum exceeds MAGH (there the FP16 values could overflow).
+constexpr float KH = 1.953125e-03f;         // 2^-9
+constexpr float EH = 9.5367431640625e-07f;  // 2^-20
+constexpr float MAGH = 16384.f;
 // FP32 cost conditioning.  A cost is a sum of segment norms of (start half +
 // end half) rows; its rounding error stays below about 1.2 u times the sum of
 // |half| over all rows (measured over every feasible check of the 2-D and 3-D
@@ -780,23 +794,30 @@ struct Screen {
     static constexpr int index(int rr) { return rr == row(0) ? 0 : (rr == row(1) ? 1 : (rr == row(2) ? 2 : -1)); }
 };
 
-// The screen of one 4x4 micro-tile on the screen row-axes, stored [row][state]
-// (row si*M + a): returns the live pairs that do not certainly fail there.
+// The screen of one 4x4 micro-tile on the screen row-axes in FP16, stored
+// [row][state]: start states as (h, h) pairs, end states as single halves, so
+// one packed add gives two pairs' sums.  Returns the live pairs that do not
+// certainly fail there (the band of the FP32 sum widened by the FP16 error).
 template <int M, int G, int PD>
-DEVI uint32_t screen_tile(int T, int gi, int gj, uint32_t live, const float* SCL, const float* SCR, const float* magR) {
-    float rm[16];
+DEVI uint32_t screen_tile(int T, int gi, int gj, uint32_t live, const __half2* SCL, const __half* SCR, const float* magR) {
+    __half2 rm[8];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) rm[q] = 0.f;
+    for (int q = 0; q < 8; ++q) rm[q] = __float2half2_rn(0.f);
 #pragma unroll
     for (int r = 0; r < Screen<G, PD>::NS * M; ++r) {
-        const float4 u = *reinterpret_cast<const float4*>(SCL + r * T + 4 * gi);
-        const float4 w = *reinterpret_cast<const float4*>(SCR + r * T + 4 * gj);
-        const float uu[4] = {u.x, u.y, u.z, u.w};
-        const float ww[4] = {w.x, w.y, w.z, w.w};
+        const uint4 ul = *reinterpret_cast<const uint4*>(SCL + r * T + 4 * gi);
+        const uint2 wr = *reinterpret_cast<const uint2*>(SCR + r * T + 4 * gj);
+        const unsigned uw[4] = {ul.x, ul.y, ul.z, ul.w};
+        const unsigned ww[2] = {wr.x, wr.y};
 #pragma unroll
         for (int qa = 0; qa < 4; ++qa)
 #pragma unroll
-            for (int qb = 0; qb < 4; ++qb) rm[qa * 4 + qb] = fmaxf(rm[qa * 4 + qb], fabsf(uu[qa] + ww[qb]));
+            for (int h = 0; h < 2; ++h) {
+                __half2 u2, w2;
+                __builtin_memcpy(&u2, &uw[qa], 4);
+                __builtin_memcpy(&w2, &ww[h], 4);
+                rm[qa * 2 + h] = __hmax2(rm[qa * 2 + h], __habs2(__hadd2(u2, w2)));
+            }
     }
     uint32_t fail = 0;
 #pragma unroll
@@ -804,8 +825,10 @@ DEVI uint32_t screen_tile(int T, int gi, int gj, uint32_t live, const float* SCL
 #pragma unroll
         for (int qb = 0; qb < 4; ++qb) {
             const int q = qa * 4 + qb;
-            const float band = KR * (magR[4 * gi + qa] + magR[T + 4 * gj + qb]);
-            if (!(rm[q] <= 1.f + band)) fail |= 1u << q;
+            const __half2 m2 = rm[qa * 2 + (qb >> 1)];
+            const float r = (qb & 1) ? __high2float(m2) : __low2float(m2);
+            const float ms = magR[4 * gi + qa] + magR[T + 4 * gj + qb];
+            if (!(r <= 1.f + (KR + KH) * ms + EH) && ms <= MAGH) fail |= 1u << q;
         }
     return live & ~fail;
 }
@@ -1110,8 +1133,9 @@ struct ScShape {
 
 // Reach halves of one state for quads [Q0, Q1): row-axis q = rr*M + a holds
 // sum_c H[rr][side][c] x[c][a]; rows past RR are 0 (neutral in max |u + w|).
+// The screen row-axes also go, rounded to FP16, to the screen arrays dS.
 template <int M, int G, int PD, int Q0, int Q1>
-DEVI void reach_quads(const float (&x)[M * G], const float* trow, float* dU, float* dS, int T) {
+DEVI void reach_quads(const float (&x)[M * G], const float* trow, float* dU, void* dS, int ls, bool right, int T) {
     constexpr int RR = ScShape<M, G, PD>::RR;
 #pragma unroll
     for (int qd = Q0; qd < Q1; ++qd) {
@@ -1129,7 +1153,11 @@ DEVI void reach_quads(const float (&x)[M * G], const float* trow, float* dU, flo
                 if (G > 3) v = fmaf(h.w, x[3 * M + a], v);
                 w[j] = v;
                 const int si = Screen<G, PD>::index(rr);
-                if (si >= 0) dS[(si * M + a) * T] = v;
+                if (si >= 0) {  // screen row-axis in FP16: (h, h) for start states, h for end states
+                    const __half hv = __float2half_rn(v);
+                    if (right) reinterpret_cast<__half*>(dS)[(si * M + a) * T + ls] = hv;
+                    else reinterpret_cast<__half2*>(dS)[(si * M + a) * T + ls] = __halves2half2(hv, hv);
+                }
             }
         }
         *reinterpret_cast<float4*>(dU + 4 * qd) = make_float4(w[0], w[1], w[2], w[3]);
@@ -1321,9 +1349,9 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
     float* UR = UL + T * SU;         //          end states
     float* FL = UR + T * SU;         // [T][SF] free halves, then cost halves
     float* FR = FL + T * SF;
-    float* SCL = FR + T * SF;        // [NS][T] screen row-axes
-    float* SCR = SCL + NS * T;
-    float* magR = SCR + NS * T;      // [2T] band magnitudes
+    __half2* SCL = reinterpret_cast<__half2*>(FR + T * SF);       // [NS][T] screen row-axes, start states: (h, h)
+    __half* SCR = reinterpret_cast<__half*>(FR + T * SF + NS * T);  // [NS][T] end states (half of the space used)
+    float* magR = FR + T * SF + 2 * NS * T;                          // [2T] band magnitudes
     float* magF = magR + 2 * T;
     float* magC = magF + 2 * T;      // [2T] sum of |cost half| per state-side (cost conditioning)
     float* xs = magC + 2 * T;        // [2T][XS] centred states
@@ -1435,11 +1463,11 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                 load_state<M, G, PD>(x, xs + (right ? T + ls : ls) * XS);
                 const float* trow = tab + (right ? 4 : 0);
                 float* dU = (right ? UR : UL) + ls * SU;
-                float* dS = (right ? SCR : SCL) + ls;
+                void* dS = right ? (void*)SCR : (void*)SCL;
                 float* dF = (right ? FR : FL) + ls * SF;
                 if (!second) {
                     magC[(right ? T : 0) + ls] = 0.f;  // summed by the cost-halves units
-                    reach_quads<M, G, PD, 0, RH>(x, trow, dU, dS, T);
+                    reach_quads<M, G, PD, 0, RH>(x, trow, dU, dS, ls, right, T);
                     free_points<M, G, PD, 0, NI / 2>(x, tab, Ab, nr, nrp, right, dF, NEG_INF);
                     const float* xa = xab + (right ? T + ls : ls) * G;
                     const float* hc = tab + PT::ROW_HC * 8 + (right ? 4 : 0);
@@ -1453,7 +1481,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                     magR[(right ? T : 0) + ls] = mr;
                     magF[(right ? T : 0) + ls] = md * s_rown1 + (right ? 0.f : s_bmax);
                 } else {
-                    reach_quads<M, G, PD, RH, RQ>(x, trow, dU, dS, T);
+                    reach_quads<M, G, PD, RH, RQ>(x, trow, dU, dS, ls, right, T);
                     free_points<M, G, PD, NI / 2, NI>(x, tab, Ab, nr, nrp, right, dF, NEG_INF);
                 }
             }
