@@ -82,6 +82,7 @@ struct plan_ctx {
     float* bc32 = nullptr;
     long long* resOff = nullptr;
     int* itemOff = nullptr;
+    int* kPerm = nullptr;
     int* ntile = nullptr;
     int* tsize = nullptr;
     int* iRange = nullptr;
@@ -297,7 +298,7 @@ int ensure_host_sized(plan_ctx* c, long long mask, long long list, long long k1,
     }
     if (k1 > c->capK) {
         if (!dalloc(c, &c->counts, k1) || !dalloc(c, &c->centers, 4 * k1) || !dalloc(c, &c->resOff, k1) ||
-            !dalloc(c, &c->itemOff, k1) || !dalloc(c, &c->ntile, k1) || !dalloc(c, &c->tsize, k1) ||
+            !dalloc(c, &c->itemOff, k1) || !dalloc(c, &c->kPerm, k1) || !dalloc(c, &c->ntile, k1) || !dalloc(c, &c->tsize, k1) ||
             !dalloc(c, &c->iRange, k1) || !dalloc(c, &c->memOff, k1))
             return PLAN_ERR_NO_MEMORY;
         c->capK = k1;
@@ -419,7 +420,7 @@ void plan_destroy(plan_ctx* c) {
     if (!c) return;
     if (c->stream || c->d_info) cudaStreamSynchronize(c->stream);
     void* dev[] = {c->d_tab64, c->d_tab32, c->d_info, c->memMask, c->counts, c->members, c->localIdx, c->segKL, c->centers,
-                   c->blim64, c->A32, c->blim32, c->bc32, c->resOff, c->itemOff, c->ntile, c->tsize, c->iRange, c->rowCount,
+                   c->blim64, c->A32, c->blim32, c->bc32, c->resOff, c->itemOff, c->kPerm, c->ntile, c->tsize, c->iRange, c->rowCount,
                    c->resBits, c->resKey, c->emitPre, c->recheck, c->half64, c->sdist, c->sbest, c->spred, c->sfront, c->slast, c->snear,
                    c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem, c->d_qMem, c->d_rowRange, c->d_sqd, c->memOff,
                    c->d_cut64, c->d_cut32, c->cut_src, c->cut_hit, c->cut_pos, c->cut_chunk, c->cut_orow,
@@ -678,6 +679,7 @@ int issue(plan_ctx* c) {
     P.bc32 = c->bc32;
     P.resOff = c->resOff;
     P.itemOff = c->itemOff;
+    P.kPerm = c->kPerm;
     P.ntile = c->ntile;
     P.tsize = c->tsize;
     P.iRange = c->iRange;

@@ -422,6 +422,7 @@ __global__ void __launch_bounds__(1024) k_setup(BuildParams P) {
     __shared__ long long wb[32];
     __shared__ long long tot;
     __shared__ int s_counts[1024];
+    __shared__ int s_items[1024];
     const int q = blockIdx.x;
     const QueryDesc& Q = P.qd[q];
     const int tile = P.tile;
@@ -437,6 +438,7 @@ __global__ void __launch_bounds__(1024) k_setup(BuildParams P) {
     }
     long long slots = 0, items = 0, mem = 0;
     long long carry_s = 0, carry_i = 0, carry_m = 0;
+    int my_key = 0, my_items = 0;  // tile area and items of this thread's polytope (K <= blockDim.x)
     for (int k0 = 0; k0 < Q.K; k0 += blockDim.x) {
         const int k = k0 + threadIdx.x;
         const long long nk = (k < Q.K) ? P.counts[Q.kOff + k] : 0;
@@ -465,10 +467,36 @@ __global__ void __launch_bounds__(1024) k_setup(BuildParams P) {
             P.ntile[Q.kOff + k] = nt | (nti << 16);
             P.tsize[Q.kOff + k] = ts | (tsi << 16);
             P.iRange[Q.kOff + k] = a | (b << 16);
+            my_items = nti * nt;
+            my_key = my_items > 0 ? ts * tsi : 0;
         }
         carry_s += slots;
         carry_i += items;
         carry_m += mem;
+    }
+    // Item order: polytopes by tile area, largest first (ties by index), so
+    // that the last items the blocks take are the smallest ones; itemOff is
+    // the prefix of the items in that order.  More polytopes than threads
+    // keep the index order.
+    if (Q.K <= (int)blockDim.x) {
+        const int k = threadIdx.x;
+        __syncthreads();  // s_counts is free again (shard_rows)
+        if (k < Q.K) s_counts[k] = my_key;
+        __syncthreads();
+        if (k < Q.K) {
+            int rank = 0;
+            for (int k2 = 0; k2 < Q.K; ++k2) {
+                const int o = s_counts[k2];
+                rank += (o > my_key || (o == my_key && k2 < k)) ? 1 : 0;
+            }
+            P.kPerm[Q.kOff + rank] = k;
+            s_items[rank] = my_items;
+        }
+        __syncthreads();
+        const long long io = block_exclusive_scan<long long>(k < Q.K ? (long long)s_items[k] : 0ll, wb, &tot);
+        if (k < Q.K) P.itemOff[Q.kOff + k] = (int)io;
+    } else {
+        for (int k = threadIdx.x; k < Q.K; k += blockDim.x) P.kPerm[Q.kOff + k] = k;
     }
     if (threadIdx.x == 0) {
         P.resOff[Q.kOff + Q.K] = carry_s;
@@ -538,19 +566,20 @@ DEVI Item item_decode(const BuildParams& P, long long item) {
         if (io[mid] <= local) lo = mid;
         else hi = mid;
     }
-    it.k = lo;
+    const int k = P.kPerm[Q.kOff + lo];  // position lo of the item order
+    it.k = k;
     const int loc = local - io[lo];
-    const int nt = P.ntile[Q.kOff + lo] & 0xffff, tsp = P.tsize[Q.kOff + lo];
+    const int nt = P.ntile[Q.kOff + k] & 0xffff, tsp = P.tsize[Q.kOff + k];
     const int ts = tsp & 0xffff, tsi = tsp >> 16;
-    const unsigned ir = (unsigned)P.iRange[Q.kOff + lo];
+    const unsigned ir = (unsigned)P.iRange[Q.kOff + k];
     const int a = (int)(ir & 0xffffu), b = (int)(ir >> 16);
-    it.nk = P.counts[Q.kOff + lo];
+    it.nk = P.counts[Q.kOff + k];
     const int ti = loc / nt, tj = loc % nt;
     it.i0 = a + ti * tsi;
     it.j0 = tj * ts;
     it.TI = min(tsi, b - it.i0);
     it.TJ = min(ts, it.nk - it.j0);
-    it.base = P.qSlot[it.q] + P.resOff[Q.kOff + lo];
+    it.base = P.qSlot[it.q] + P.resOff[Q.kOff + k];
     return it;
 }
 

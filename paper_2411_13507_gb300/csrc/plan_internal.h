@@ -168,7 +168,8 @@ struct BuildParams {
     float* bc32;
     long long* resOff;         // [kOff] slot offset of each polytope, relative to qSlot[q]
     int* memOff;               // [kOff] membership offset of each polytope, relative to qMem[q]
-    int* itemOff;
+    int* itemOff;              // [kOff + p] first item of the p-th polytope of the item order (prefix, + total)
+    int* kPerm;                // [kOff + p] polytope at position p of the item order (tile area, largest first)
     int* ntile;                // j-tiles | i-tiles << 16 of each polytope
     int* tsize;                // j-tile side | i-tile side << 16
     int* iRange;               // members [a, b) of each polytope whose ids lie in the query's row range: a | b << 16
