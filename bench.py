@@ -304,9 +304,23 @@ def ops_per_check(prob) -> float:
     return 4 * m * rax + 2 * (p - 1) * rows_mean + p * (2 * n + 2)
 
 
-def e2e_build_search(pl, dp, prob, graph, sbuf, stream, flush, steps, warmup, np_dtype):
+def captured_build(pl, dp, graph, stream):
+    """The query prepared once as a batch of one (plan_prepare_batched) and its
+    build launches (plan_build_edges_batched) captured into one CUDA graph:
+    returns the graph (replay() runs one build) and its kernels per replay."""
+    import torch
+    pl.build_batched([dp], [graph])
+    pl.timing(reset=True)
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg, stream=stream):
+        pl.build_batched_async()
+    return cg, int(pl.timing(reset=True)["launches"])
+
+
+def e2e_build_search(pl, dp, prob, graph, sbuf, stream, flush, steps, warmup, np_dtype, build=None):
     """End to end through the C ABI: states and polytopes from pinned host
-    memory, plan_build_edges + plan_search, path and cost back to the host."""
+    memory, the build (the replayed graph when given, else plan_build_edges)
+    + plan_search, path and cost back to the host."""
     import torch
     from paper_2411_13507_gb300 import plan as P
     h_states = torch.from_numpy(np.ascontiguousarray(prob.states, dtype=np_dtype)).pin_memory()
@@ -325,7 +339,10 @@ def e2e_build_search(pl, dp, prob, graph, sbuf, stream, flush, steps, warmup, np
         dp.poly_off.copy_(h_off, non_blocking=True)
         dp.A.copy_(h_A, non_blocking=True)
         dp.b.copy_(h_b, non_blocking=True)
-        pl.build_edges_async(dp, graph)
+        if build is not None:
+            build()
+        else:
+            pl.build_edges_async(dp, graph)
         pl.search_async(dp, graph, dp.start_pos, dp.goal_pos, sbuf)
         h_path.copy_(sbuf["path"], non_blocking=True)
         h_cost.copy_(sbuf["cost"], non_blocking=True)
@@ -379,9 +396,14 @@ def run_2d_form(args, stream, flush, dev):
     g = pl.build_edges(dp)
     info = pl.info()
     sbuf = pl.alloc_search(dp.N)
+    cg, nrep = captured_build(pl, dp, g, stream)
+    bms, clocks, _ = clocked(cg.replay, stream, args.steps, args.warmup, flush)
+    assert pl.wait() == P.PLAN_OK
+    # the pair kernel's own time and the launched build: the same launches one by one
     pl.set_timing(True)
-    bms, clocks, tm = clocked(lambda: pl.build_edges_async(dp, g), stream, args.steps, args.warmup, flush,
-                              before=lambda: pl.timing(reset=True), after=lambda: pl.timing(reset=True))
+    pl.timing(reset=True)
+    bl = timed(pl.build_batched_async, stream, args.steps, args.warmup, flush)
+    tm = pl.timing(reset=True)
     pl.set_timing(False)
     sms = timed(lambda: pl.search_async(dp, g, dp.start_pos, dp.goal_pos, sbuf), stream, args.steps, args.warmup,
                 flush)
@@ -395,12 +417,14 @@ def run_2d_form(args, stream, flush, dev):
             continue
         p2 = P.Planner.for_problem(prob, arith=ra, input="f64", stream=stream)
         g2 = p2.build_edges(dp)
-        ms2 = timed(lambda: p2.build_edges_async(dp, g2), stream, args.steps, args.warmup, flush)
+        cg2, _ = captured_build(p2, dp, g2, stream)
+        ms2 = timed(cg2.replay, stream, args.steps, args.warmup, flush)
         assert p2.wait() == P.PLAN_OK
         plain[ra] = {"build_ms": statistics.mean(ms2), "checks_per_s": checks * 1e3 / statistics.mean(ms2),
                      "speedup_of_this_form": statistics.mean(ms2) / build_ms}
         p2.close()
-    e2e_ms, bi, bo = e2e_build_search(pl, dp, prob, g, sbuf, stream, flush, args.steps, args.warmup, np.float64)
+    e2e_ms, bi, bo = e2e_build_search(pl, dp, prob, g, sbuf, stream, flush, args.steps, args.warmup, np.float64,
+                                      build=cg.replay)
     lanes = lane_peaks(dev, fp64=True)
     pair_ms = tm["pair_ms"] / max(1, tm["pair_launches"])
     opc = ops_per_check(prob)
@@ -413,9 +437,12 @@ def run_2d_form(args, stream, flush, dev):
         p3 = P.Planner.for_problem(prob, arith="f64", input="f64", stream=stream)
         p3.set_tile(0, 0, 0, 3)
         g3 = p3.build_edges(dp)
+        cg3, _ = captured_build(p3, dp, g3, stream)
+        ms3 = timed(cg3.replay, stream, args.steps, args.warmup, flush)
+        assert p3.wait() == P.PLAN_OK
         p3.set_timing(True)
         p3.timing(reset=True)
-        ms3 = timed(lambda: p3.build_edges_async(dp, g3), stream, args.steps, args.warmup, flush)
+        timed(p3.build_batched_async, stream, args.steps, args.warmup, flush)
         t3 = p3.timing(reset=True)
         assert p3.wait() == P.PLAN_OK
         k3 = t3["pair_ms"] / max(1, t3["pair_launches"])
@@ -433,11 +460,14 @@ def run_2d_form(args, stream, flush, dev):
     return {"metric": "edge-feasibility checks/sec, 2-D double integrator (N=512, K=16, nT=8, p=5)",
             "value": checks * 1e3 / build_ms, "unit": UNIT, "dtype": arith,
             "ms_per_step": build_ms + statistics.mean(sms), "build_ms_per_query": build_ms,
-            "search_ms_per_query": statistics.mean(sms), "gpu_launches": int(tm["launches"]), "clocks": clocks,
+            "search_ms_per_query": statistics.mean(sms), "gpu_launches": args.steps * nrep, "clocks": clocks,
+            "build_ms_launched": statistics.mean(bl),
             "config": {"workload": "double_integrator_2d seed 1 (|v|<=2, |a|<=4, [0,10]^2, 16 polytopes of 4-8 rows, "
                                    "512 states, p=5, 8 durations in [0.2, 2])", "checks": checks,
                        "rechecks": info["rechecks"], "recheck_frac": info["rechecks"] / max(1, checks),
-                       "edges": info["edges"], "l2": "flushed before every timed call (256 MB write)"},
+                       "edges": info["edges"], "l2": "flushed before every timed call (256 MB write)",
+                       "build": "the query prepared once as a batch of one, its build launches replayed as one "
+                                "captured CUDA graph (every arm)"},
             "vs_plain_forms": plain, **({"canonical_fp64_route": canonical} if canonical else {}),
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TOP/s", "frac": ach / peak,
                          "traffic": None, "kernel": kern, "kernel_ms": pair_ms, "ops_per_check": opc,
