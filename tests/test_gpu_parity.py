@@ -171,6 +171,15 @@ def test_states_in_many_polytopes():
     check_full(prob, "f32", input="f64")
 
 
+def test_maximum_polytope_count():
+    """K = 1024 polytopes (the largest K a query takes): the item order ranks
+    every polytope by tile area, with many ties and many polytopes without
+    members or items; the graph equals the oracle's all the same."""
+    prob = synth.double_integrator_2d(4, N=300, K=1024, nT=4)
+    st, info, _ = check_full(prob, "f32", input="f64")
+    assert info["edges"] > 0
+
+
 @pytest.mark.parametrize("arith", ["f64", "f32"])
 def test_minsnap_interior_points(arith):
     """Interior control points of minimal (gamma+1)-th-derivative energy
