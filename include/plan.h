@@ -235,7 +235,10 @@ int plan_build_edges_batched(plan_ctx* ctx);
 
 /* FP32 pair-kernel configuration: tile side (8..64, multiple of 4; 0 = 64),
  * CTAs per SM (0 = as many as fit), duration chunks per tile (work items are
- * tiles x chunks, longest durations first; 0 = 2) and pipeline (0, the
+ * tiles x chunks, longest durations first, largest tiles first; 0 = chosen
+ * per build on the device once the tile count is known: enough chunks for
+ * about eight items per SM, one to the most durations of any query) and
+ * pipeline (0, the
  * default: one warp group that screens every 4x4 block of pairs on the few
  * reach rows that mix both boundary states and runs the surviving pairs,
  * compacted, through all rows; 1: the warp-specialised kernel -- producer
@@ -248,7 +251,7 @@ int plan_build_edges_batched(plan_ctx* ctx);
  * cost of every emitted edge and duration in canonical FP64 (the weight is
  * the cheapest, ties to the lower duration index); pipeline 3 (FP64 models
  * only) runs the canonical FP64 pair kernel instead (every margin and cost in
- * FP64, 32-state tiles, chunks 0 = 8).  Both FP64 routes give the same graph
+ * FP64, 32-state tiles).  Both FP64 routes give the same graph
  * bit for bit.  plan_autotune times every candidate on the prepared batch (reps launches
  * each, synchronising) and keeps the fastest; it reports the choice and its
  * mean pair-kernel time. */

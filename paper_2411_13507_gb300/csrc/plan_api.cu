@@ -55,7 +55,7 @@ struct plan_ctx {
     bool stage_live = false;
     std::vector<char> last_stage;
     int tile = 0, ctas_per_sm = 0;    // pair-kernel configuration (0 = default)
-    int tchunks = 0;                  // duration chunks per tile (0 = default 2)
+    int tchunks = 0;                  // duration chunks per tile (0 = chosen per build)
     int pipeline = 0;                 // screened one-group FP32 pair kernel
     // batched search
     int sQ = 0;
@@ -649,6 +649,8 @@ int issue(plan_ctx* c) {
     // the canonical FP64 kernel: one duration per item by default (it is bound
     // by the narrow FP64 pipe; small problems need the items to fill every SM)
     P.tchunks = c->tchunks > 0 ? c->tchunks : (P.arith == PLAN_F64 ? 8 : 2);
+    // default chunking: about eight items per SM once the tile count is known
+    P.itemTarget = c->tchunks > 0 ? 0 : 8 * c->num_sms;
     P.pipeline = canonical64 ? 0 : c->pipeline;
     P.eps = c->model.tighten;
     P.qd = c->d_qd;

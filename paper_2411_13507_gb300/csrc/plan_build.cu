@@ -540,7 +540,16 @@ __global__ void __launch_bounds__(1024) k_batch(BuildParams P) {
         P.qItem[0] = 0;
         P.qMem[0] = 0;
         P.info->slots = cs;
-        P.info->items = ci * P.tchunks;
+        // chunks per tile: the set value, or by default enough for about
+        // itemTarget items -- one to the most durations of any query
+        int tch = P.tchunks;
+        if (P.itemTarget > 0) {
+            const long long want = ci > 0 ? (P.itemTarget + ci - 1) / ci : 1;
+            const int most = P.maxT > 0 ? P.maxT : 1;
+            tch = (int)(want < 1 ? 1 : (want > most ? most : want));
+        }
+        P.info->tchunks = tch;
+        P.info->items = ci * tch;
         if (cs > P.slotCap) {
             P.info->need_slots = cs;
             set_status(P.info, PLAN_ERR_CAPACITY, DET_SLOTS);
@@ -594,12 +603,13 @@ struct ItemT {
 
 DEVI ItemT item_decode_chunk(const BuildParams& P, long long item) {
     const long long tiles = P.qItem[P.Q];
-    const int c = P.tchunks - 1 - (int)(item / tiles);
+    const int tch = P.itemTarget > 0 ? P.info->tchunks : P.tchunks;  // chunks of this build (k_batch)
+    const int c = tch - 1 - (int)(item / tiles);
     ItemT r;
     r.it = item_decode(P, item % tiles);
     const int nT = P.qd[r.it.q].nT;
-    r.t0 = (c * nT) / P.tchunks;
-    r.t1 = ((c + 1) * nT) / P.tchunks;
+    r.t0 = (c * nT) / tch;
+    r.t1 = ((c + 1) * nT) / tch;
     return r;
 }
 

@@ -86,6 +86,7 @@ struct DevInfo {
     unsigned long long cut_lp64;     // entries settled in FP64
     unsigned long long cut_ties;     // FP64 games without a certificate either way
     int shard_lo, shard_hi;          // source rows [lo, hi) of the first query's shard
+    int tchunks;                     // duration chunks per tile of this build (k_batch)
 };
 
 enum Detail {
@@ -136,6 +137,7 @@ struct BuildParams {
     int cost_mode, in_f32, arith, max_rows;
     int tile;                  // tile side of the pair kernel (autotuned, <= TILE)
     int tchunks;               // duration chunks per tile (work items = tiles x tchunks)
+    int itemTarget;            // > 0: k_batch picks the chunks per tile for about this many items
     int pipeline;              // FP32 pair kernel: 0 screened, 1 warp-specialised (64-state tiles), 2 unscreened
     int w64;                   // output weights are doubles (FP64 model)
     int cost64;                // FP64 model on the FP32 pair kernels: canonical FP64 cost pass after compaction
