@@ -133,3 +133,42 @@ def test_batched_search_matches_oracle():
         kinds.append(parity.compare_search({"start": r["path"][0], "goal": r["path"][-1], "path": r["path"],
                                             "cost": r["cost"]}, orc, csr, "f32"))
     assert len(kinds) == 6
+
+
+def test_one_query_replay_equals_build_edges():
+    """One query prepared as a batch of one and its build replayed from a
+    captured graph (the default benchmark step) gives plan_build_edges' graph
+    bit for bit, also after its states and polytope bounds change in place."""
+    prob = synth.triple_integrator_3d(seed=4, N=1500, K=12, nT=6)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        pl = P.Planner.for_problem(prob, arith="f32", input="f32", stream=stream)
+        dp = P.to_device(prob, input="f32")
+        g = pl.build_edges(dp, cap=400 * prob.N)
+        ref = g.to_numpy()
+        pl.build_batched([dp], [g])
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg, stream=stream):
+            pl.build_batched_async()
+        g.count.zero_()
+        g.col.zero_()
+        cg.replay()
+        stream.synchronize()
+        assert pl.wait() == P.PLAN_OK
+        same_graph(g.to_numpy(), ref)
+        # states moved and every bound loosened, in place
+        rng = np.random.default_rng(5)
+        prob.states = (prob.states + rng.normal(0.0, 0.05, prob.states.shape)).astype(prob.states.dtype)
+        prob.b = (prob.b + 0.25).astype(prob.b.dtype)
+        dp.states.copy_(torch.as_tensor(prob.states, dtype=torch.float32))
+        dp.b.copy_(torch.as_tensor(prob.b, dtype=torch.float32))
+        cg.replay()
+        stream.synchronize()
+        assert pl.wait() == P.PLAN_OK
+        moved = g.to_numpy()
+    fresh = P.Planner.for_problem(prob, arith="f32", input="f32")
+    gf = fresh.build_edges(P.to_device(prob, input="f32"))
+    same_graph(moved, gf.to_numpy())
+    assert len(moved["col"]) != len(ref["col"])  # the replay did follow the new inputs
+    csr = oracle.OracleProblem(prob).csr(with_detail=True)
+    parity.compare_full(moved, csr, prob.N, prob.nT, "f32")
