@@ -41,6 +41,10 @@ namespace plan {
 // re-evaluated in canonical FP64.
 constexpr float KU = 5.9604644775390625e-08f;  // 2^-24
 constexpr float KR = 16.f * KU;
+// (The screened kernel forms P = start half + end half of each interior
+// control point and then A_r . P - b_r: the halves' chains, one add, m
+// products and sums and the bound -- fewer roundings than the bound below
+// allows, over the same magnitude.)
 constexpr float KF = 24.f * KU;
 constexpr float KMEM = 16.f * KU;
 // Half-precision screen.  The screen row-axes of the reach halves are rounded
@@ -1154,8 +1158,8 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
 __host__ __device__ constexpr int pad_odd4(int n) { return ((n + 3) / 8) * 8 + 4; }  // >= n, = 4 mod 8
 
 // per-state stride of the free / cost halves (both live in the same rows)
-__host__ __device__ inline int sc_free_stride(int NI, int max_rows, int PD, int PL) {
-    const int fr = NI * ((max_rows + 3) & ~3), cr = PD * PL;
+__host__ __device__ inline int sc_free_stride(int NI, int M, int PD, int PL) {
+    const int fr = (NI * M + 3) & ~3, cr = PD * PL;  // interior points' halves, or cost halves
     return pad_odd4(fr > cr ? fr : cr);
 }
 
@@ -1219,50 +1223,27 @@ DEVI void load_state(float (&x)[M * G], const float* xr) {
     for (int e = 0; e < M * G; ++e) x[e] = v[e];
 }
 
-// Free halves of one state for interior control points [L0, L1): the point
-// P_l = sum_c D[l][side][c] x[c] per axis, then every polytope row
-// A_r . P_l (- b_r for the start side) in rows l*nrp + r, four rows per
-// 16-byte store; rows r >= nr are padding, neutral in max(u + w).
+// Interior control-point halves of one state for points [L0, L1): point l's
+// coordinate a, sum_c D[l][side][c] x[c][a], at dP[l * M + a]; the unit that
+// ends at NI also zeroes the padding up to the next 16-byte quad.
 template <int M, int G, int PD, int L0, int L1>
-DEVI void free_points(const float (&x)[M * G], const float* tab, const float* Ab, int nr, int nrp, bool right,
-                      float* dF, float neg_inf) {
-    constexpr int NL = L1 - L0;
-    float pt[NL > 0 ? NL : 1][M];
+DEVI void point_halves(const float (&x)[M * G], const float* tab, bool right, float* dP) {
+    constexpr int NI = Shape<G, PD>::NI, NP = (NI * M + 3) & ~3;
 #pragma unroll
-    for (int l = 0; l < NL; ++l) {
-        const float4 dd = *reinterpret_cast<const float4*>(tab + (PadTab<G, PD>::ROW_D + L0 + l) * 8 + (right ? 4 : 0));
+    for (int l = L0; l < L1; ++l) {
+        const float4 dd = *reinterpret_cast<const float4*>(tab + (PadTab<G, PD>::ROW_D + l) * 8 + (right ? 4 : 0));
 #pragma unroll
         for (int a = 0; a < M; ++a) {
             float w = dd.x * x[a];
             if (G > 1) w = fmaf(dd.y, x[M + a], w);
             if (G > 2) w = fmaf(dd.z, x[2 * M + a], w);
             if (G > 3) w = fmaf(dd.w, x[3 * M + a], w);
-            pt[l][a] = w;
+            dP[l * M + a] = w;
         }
     }
-    for (int rq = 0; rq < nrp; rq += 4) {
-        float w4[NL > 0 ? NL : 1][4];
+    if (L1 == NI) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int r = rq + j;
-            if (r < nr) {
-                const float4 ab = *reinterpret_cast<const float4*>(Ab + r * 4);
-#pragma unroll
-                for (int l = 0; l < NL; ++l) {
-                    float w = ab.x * pt[l][0];
-                    w = fmaf(ab.y, pt[l][1], w);
-                    if (M > 2) w = fmaf(ab.z, pt[l][2], w);
-                    if (!right) w -= (M > 2 ? ab.w : ab.z);
-                    w4[l][j] = w;
-                }
-            } else {
-#pragma unroll
-                for (int l = 0; l < NL; ++l) w4[l][j] = right ? 0.f : neg_inf;
-            }
-        }
-#pragma unroll
-        for (int l = 0; l < NL; ++l)
-            *reinterpret_cast<float4*>(dF + (L0 + l) * nrp + rq) = make_float4(w4[l][0], w4[l][1], w4[l][2], w4[l][3]);
+        for (int e = NI * M; e < NP; ++e) dP[e] = 0.f;
     }
 }
 
@@ -1383,10 +1364,10 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
     const int DR = P.cost_mode == 1 ? 1 : G;
     const int PL = (DR * M + 3) & ~3;  // cost rows of one segment, padded with zeros
     constexpr int PLG = (G * M + 3) & ~3;  // PL of the full cost (DR = G); 4 for DR = 1
-    const int SF = sc_free_stride(NI, P.max_rows, PD, PL);
+    const int SF = sc_free_stride(NI, M, PD, PL);
     float* UL = sm;                  // [T][SU] reach halves, start states
     float* UR = UL + T * SU;         //          end states
-    float* FL = UR + T * SU;         // [T][SF] free halves, then cost halves
+    float* FL = UR + T * SU;         // [T][SF] interior control-point halves, then cost halves
     float* FR = FL + T * SF;
     __half2* SCL = reinterpret_cast<__half2*>(FR + T * SF);       // [NS][T] screen row-axes, start states: (h, h)
     __half* SCR = reinterpret_cast<__half*>(FR + T * SF + NS * T);  // [NS][T] end states (half of the space used)
@@ -1425,7 +1406,6 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
         const int ni4 = (TI + 3) & ~3, nj4 = (TJ + 3) & ~3;
         const int S2 = ni4 + nj4;
         const int r0 = Qd.poly_off[k], nr = Qd.poly_off[k + 1] - r0;
-        const int nrp = (nr + 3) & ~3;
         const long long rg0 = Qd.rowsOff + r0;
         for (int u = tid; u < nr * 4; u += nthr) {
             const int r = u >> 2, c = u & 3;
@@ -1507,7 +1487,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                 if (!second) {
                     magC[(right ? T : 0) + ls] = 0.f;  // summed by the cost-halves units
                     reach_quads<M, G, PD, 0, RH>(x, trow, dU, dS, ls, right, T);
-                    free_points<M, G, PD, 0, NI / 2>(x, tab, Ab, nr, nrp, right, dF, NEG_INF);
+                    point_halves<M, G, PD, 0, NI / 2>(x, tab, right, dF);
                     const float* xa = xab + (right ? T + ls : ls) * G;
                     const float* hc = tab + PT::ROW_HC * 8 + (right ? 4 : 0);
                     const float* dc = tab + PT::ROW_DC * 8 + (right ? 4 : 0);
@@ -1521,7 +1501,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                     magF[(right ? T : 0) + ls] = md * s_rown1 + (right ? 0.f : s_bmax);
                 } else {
                     reach_quads<M, G, PD, RH, RQ>(x, trow, dU, dS, ls, right, T);
-                    free_points<M, G, PD, NI / 2, NI>(x, tab, Ab, nr, nrp, right, dF, NEG_INF);
+                    point_halves<M, G, PD, NI / 2, NI>(x, tab, right, dF);
                 }
             }
             __syncthreads();
@@ -1577,22 +1557,34 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                 if (rm <= 1.f + bandR) {
                     const bool rpass = rm <= 1.f - bandR;
                     rp_cnt += rpass ? 1u : 0u;
-                    const float* fl = FL + li * SF;
-                    const float* fr = FR + lj * SF;
-                    float f4[4] = {NEG_INF, NEG_INF, NEG_INF, NEG_INF};
-                    // row quads of all NI interior points per pass: 2 NI loads in flight
-                    for (int rq = 0; rq < nrp; rq += 4) {
+                    // interior control points P_l = start half + end half, then
+                    // every polytope row A_r . P_l - b_r (rows broadcast from Ab)
+                    constexpr int NPQ = (NI * M + 3) / 4;
+                    const float* pl_ = FL + li * SF;
+                    const float* pr_ = FR + lj * SF;
+                    float pt[4 * NPQ];
+#pragma unroll
+                    for (int q = 0; q < NPQ; ++q) {
+                        const float4 a = *reinterpret_cast<const float4*>(pl_ + 4 * q);
+                        const float4 c = *reinterpret_cast<const float4*>(pr_ + 4 * q);
+                        pt[4 * q] = a.x + c.x;
+                        pt[4 * q + 1] = a.y + c.y;
+                        pt[4 * q + 2] = a.z + c.z;
+                        pt[4 * q + 3] = a.w + c.w;
+                    }
+                    float f2[2] = {NEG_INF, NEG_INF};
+                    for (int r = 0; r < nr; ++r) {
+                        const float4 ab = *reinterpret_cast<const float4*>(Ab + r * 4);
+                        const float br = M > 2 ? ab.w : ab.z;
 #pragma unroll
                         for (int l = 0; l < NI; ++l) {
-                            const float4 a = *reinterpret_cast<const float4*>(fl + l * nrp + rq);
-                            const float4 b = *reinterpret_cast<const float4*>(fr + l * nrp + rq);
-                            f4[0] = fmaxf(f4[0], a.x + b.x);
-                            f4[1] = fmaxf(f4[1], a.y + b.y);
-                            f4[2] = fmaxf(f4[2], a.z + b.z);
-                            f4[3] = fmaxf(f4[3], a.w + b.w);
+                            float w = ab.x * pt[l * M];
+                            w = fmaf(ab.y, pt[l * M + 1], w);
+                            if (M > 2) w = fmaf(ab.z, pt[l * M + 2], w);
+                            f2[l & 1] = fmaxf(f2[l & 1], w - br);
                         }
                     }
-                    const float fm = fmaxf(fmaxf(f4[0], f4[1]), fmaxf(f4[2], f4[3]));
+                    const float fm = fmaxf(f2[0], f2[1]);
                     const float bandF = KF * (magF[li] + magF[T + lj]);
                     if (fm <= bandF) outcome = (rpass && fm <= -bandF) ? 1 : 2;
                 }
@@ -3228,7 +3220,7 @@ size_t smem_sc(const BuildParams& P) {
     using SS = ScShape<M, G, PD>;
     const int DR = P.cost_mode == 1 ? 1 : G;
     const size_t T = (size_t)P.tile;
-    const size_t SF = (size_t)sc_free_stride(Shape<G, PD>::NI, P.max_rows, PD, (DR * M + 3) & ~3);
+    const size_t SF = (size_t)sc_free_stride(Shape<G, PD>::NI, M, PD, (DR * M + 3) & ~3);
     size_t f = T * (2 * SS::SU + 2 * SF + 2 * SS::NS + 6) + 2 * T * (SS::XS + G) + 2 * PadTab<G, PD>::FLOATS + RMAX * 4;
     return f * sizeof(float) + 2 * T * T * sizeof(uint16_t);
 }
