@@ -1158,8 +1158,8 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
 __host__ __device__ constexpr int pad_odd4(int n) { return ((n + 3) / 8) * 8 + 4; }  // >= n, = 4 mod 8
 
 // per-state stride of the free / cost halves (both live in the same rows)
-__host__ __device__ inline int sc_free_stride(int NI, int M, int PD, int PL) {
-    const int fr = (NI * M + 3) & ~3, cr = PD * PL;  // interior points' halves, or cost halves
+__host__ __device__ inline int sc_free_stride(int NI, int M, int PD, int DR) {
+    const int fr = (NI * M + 3) & ~3, cr = (PD * DR * M + 3) & ~3;  // interior points' halves, or cost halves
     return pad_odd4(fr > cr ? fr : cr);
 }
 
@@ -1247,40 +1247,46 @@ DEVI void point_halves(const float (&x)[M * G], const float* tab, bool right, fl
     }
 }
 
-// Cost halves of one state for segments [L0, L1): segment l holds rows
-// e = d*M + a (d < DR) of sum_c C[d][l][side][c] x[c][a], zero-padded to PL.
-// Returns the sum of |half| over the rows written.
-template <int M, int G, int PD, int L0, int L1>
-DEVI float cost_segments(const float (&x)[M * G], const float* tab, int DR, int PL, bool right, float* dC) {
-    constexpr int PLM = (G * M + 3) & ~3;
+// Cost halves of one state, packed: row e = d*M + a (d < DR) of segment l,
+// sum_c C[d][l][side][c] x[c][a], at float l * DR * M + e; this unit writes
+// floats [F0, F1) (both multiples of four, the last unit's range ends on the
+// zero padding after PD * DR * M) and returns the sum of |half| over them.
+template <int M, int G, int PD, int DR, int F0, int F1>
+DEVI float cost_rows(const float (&x)[M * G], const float* tab, bool right, float* dC) {
+    constexpr int DRM = DR * M, NF = PD * DRM;
+    static_assert(F0 % 4 == 0 && F1 % 4 == 0 && F1 > F0, "cost halves are stored in 16-byte quads");
     float mag = 0.f;
+    float v[F1 - F0];
 #pragma unroll
-    for (int l = L0; l < L1; ++l) {
-        float val[PLM];
-#pragma unroll
-        for (int e = 0; e < PLM; ++e) val[e] = 0.f;
-#pragma unroll
-        for (int d = 0; d < G; ++d) {
-            if (d < DR) {
-                const float4 h =
-                    *reinterpret_cast<const float4*>(tab + (PadTab<G, PD>::ROW_C + d * PD + l) * 8 + (right ? 4 : 0));
-#pragma unroll
-                for (int a = 0; a < M; ++a) {
-                    float w = h.x * x[a];
-                    if (G > 1) w = fmaf(h.y, x[M + a], w);
-                    if (G > 2) w = fmaf(h.z, x[2 * M + a], w);
-                    if (G > 3) w = fmaf(h.w, x[3 * M + a], w);
-                    val[d * M + a] = w;
-                    mag += fabsf(w);
-                }
-            }
+    for (int f = F0; f < F1; ++f) {
+        float w = 0.f;
+        if (f < NF) {
+            const int l = f / DRM, e = f % DRM, d = e / M, a = e % M;
+            const float4 h =
+                *reinterpret_cast<const float4*>(tab + (PadTab<G, PD>::ROW_C + d * PD + l) * 8 + (right ? 4 : 0));
+            w = h.x * x[a];
+            if (G > 1) w = fmaf(h.y, x[M + a], w);
+            if (G > 2) w = fmaf(h.z, x[2 * M + a], w);
+            if (G > 3) w = fmaf(h.w, x[3 * M + a], w);
+            mag += fabsf(w);
         }
-#pragma unroll
-        for (int e = 0; e < PLM; e += 4)
-            if (e < PL) *reinterpret_cast<float4*>(dC + l * PL + e) = make_float4(val[e], val[e + 1], val[e + 2], val[e + 3]);
+        v[f - F0] = w;
     }
+#pragma unroll
+    for (int q = 0; q < (F1 - F0) / 4; ++q)
+        *reinterpret_cast<float4*>(dC + F0 + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     return mag;
 }
+
+// The split of a state's packed cost halves between its two units: at the
+// segment boundary (PD + 1) / 2 rounded down to a quad, the rest to the end
+// of the padding.
+template <int M, int PD, int DR>
+struct CostSplit {
+    static constexpr int NP = (PD * DR * M + 3) & ~3;
+    static constexpr int FS0 = (((PD + 1) / 2) * DR * M) & ~3;
+    static constexpr int FS = FS0 > 0 ? FS0 : (NP > 4 ? 4 : NP);
+};
 
 // The next item for a block, or past the end once the build has failed.
 DEVI long long take_item(DevInfo* info) {
@@ -1328,27 +1334,29 @@ DEVI void stage_state_half(const void* states, bool in_f32, long long id, bool v
     }
 }
 
-// Control-polygon length of one pair from its cost halves: per segment the
-// root of the sum of squares of (left + right) over PL padded rows, in row
-// order, summed over the PD segments in order (both loops unrolled).
-template <int PD, int PL>
+// Control-polygon length of one pair from its packed cost halves: per
+// segment the root of the sum of squares of (start + end half) over its DRM
+// rows in row order, summed over the PD segments in order.
+template <int PD, int DRM>
 DEVI float pair_cost(const float* cl, const float* cr) {
+    constexpr int NF = PD * DRM, NQ = (NF + 3) / 4;
+    float ss[PD];
+#pragma unroll
+    for (int l = 0; l < PD; ++l) ss[l] = 0.f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const float4 a = *reinterpret_cast<const float4*>(cl + 4 * q);
+        const float4 b = *reinterpret_cast<const float4*>(cr + 4 * q);
+        const float d[4] = {a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int f = 4 * q + j;
+            if (f < NF) ss[f / DRM] = fmaf(d[j], d[j], ss[f / DRM]);
+        }
+    }
     float cs = 0.f;
 #pragma unroll
-    for (int l = 0; l < PD; ++l) {
-        float ss = 0.f;
-#pragma unroll
-        for (int q = 0; q < PL; q += 4) {
-            const float4 a = *reinterpret_cast<const float4*>(cl + l * PL + q);
-            const float4 b = *reinterpret_cast<const float4*>(cr + l * PL + q);
-            const float d0 = a.x + b.x, d1 = a.y + b.y, d2 = a.z + b.z, d3 = a.w + b.w;
-            ss = fmaf(d0, d0, ss);
-            ss = fmaf(d1, d1, ss);
-            ss = fmaf(d2, d2, ss);
-            ss = fmaf(d3, d3, ss);
-        }
-        cs += sqrtf(ss);
-    }
+    for (int l = 0; l < PD; ++l) cs += sqrtf(ss[l]);
     return cs;
 }
 
@@ -1362,9 +1370,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
     const int T = P.tile;  // tile side (multiple of 4, <= TILE)
     extern __shared__ __align__(16) float sm[];
     const int DR = P.cost_mode == 1 ? 1 : G;
-    const int PL = (DR * M + 3) & ~3;  // cost rows of one segment, padded with zeros
-    constexpr int PLG = (G * M + 3) & ~3;  // PL of the full cost (DR = G); 4 for DR = 1
-    const int SF = sc_free_stride(NI, M, PD, PL);
+    const int SF = sc_free_stride(NI, M, PD, DR);
     float* UL = sm;                  // [T][SU] reach halves, start states
     float* UR = UL + T * SU;         //          end states
     float* FL = UR + T * SU;         // [T][SF] interior control-point halves, then cost halves
@@ -1614,8 +1620,12 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                     float x[N_];
                     load_state<M, G, PD>(x, xs + (right ? T + ls : ls) * XS);
                     float* dC = (right ? FR : FL) + ls * SF;
-                    const float mg = !second ? cost_segments<M, G, PD, 0, (PD + 1) / 2>(x, tab, DR, PL, right, dC)
-                                             : cost_segments<M, G, PD, (PD + 1) / 2, PD>(x, tab, DR, PL, right, dC);
+                    using CSG = CostSplit<M, PD, G>;
+                    using CS1 = CostSplit<M, PD, 1>;
+                    const float mg = DR == G ? (!second ? cost_rows<M, G, PD, G, 0, CSG::FS>(x, tab, right, dC)
+                                                        : cost_rows<M, G, PD, G, CSG::FS, CSG::NP>(x, tab, right, dC))
+                                             : (!second ? cost_rows<M, G, PD, 1, 0, CS1::FS>(x, tab, right, dC)
+                                                        : cost_rows<M, G, PD, 1, CS1::FS, CS1::NP>(x, tab, right, dC));
                     atomicAdd(&magC[(right ? T : 0) + ls], mg);  // two units per state-side
                 }
                 __syncthreads();
@@ -1625,7 +1635,7 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                     const int li = v >> 8, lj = v & 255;
                     const float* cl = FL + li * SF;
                     const float* cr = FR + lj * SF;
-                    const float cs = PL == PLG ? pair_cost<PD, PLG>(cl, cr) : pair_cost<PD, 4>(cl, cr);
+                    const float cs = DR == G ? pair_cost<PD, G * M>(cl, cr) : pair_cost<PD, M>(cl, cr);
                     if (P.cost64 || magC[li] + magC[T + lj] <= COST_RHO * cs) {  // FP64 models re-cost every edge anyway
                         const long long slot = itd.base + (long long)(i0 + li) * itd.nk + (j0 + lj);
                         atomicOr(&P.resBits[slot], 1u << t);
@@ -3220,7 +3230,7 @@ size_t smem_sc(const BuildParams& P) {
     using SS = ScShape<M, G, PD>;
     const int DR = P.cost_mode == 1 ? 1 : G;
     const size_t T = (size_t)P.tile;
-    const size_t SF = (size_t)sc_free_stride(Shape<G, PD>::NI, M, PD, (DR * M + 3) & ~3);
+    const size_t SF = (size_t)sc_free_stride(Shape<G, PD>::NI, M, PD, DR);
     size_t f = T * (2 * SS::SU + 2 * SF + 2 * SS::NS + 6) + 2 * T * (SS::XS + G) + 2 * PadTab<G, PD>::FLOATS + RMAX * 4;
     return f * sizeof(float) + 2 * T * T * sizeof(uint16_t);
 }
