@@ -1371,9 +1371,10 @@ def main():
     ops_per_check = 4 * m * rax + 2 * (p - 1) * rows_mean + p * (2 * n + 2)
     ops_per_launch = ops_per_check * checks
     sc_ops = (2 * work["work_reach_rows"] + 2 * work["work_free_rows"] + work["work_costs"] * p * (2 * n + 2))
-    # work the screened kernel executes: the screen rows (3 reach rows per axis)
-    # of every ordered pair in every polytope and duration, every reach and free
-    # row of the pairs it passes on, one cost per feasible check
+    # the dense model restricted to what the screened kernel evaluates: the
+    # screen rows (3 reach rows per axis) of every ordered pair in every
+    # polytope and duration, every reach and free row of the pairs it passes
+    # on, one cost per feasible check (each counted as in the dense model)
     screened = int(info.get("screened", 0))
     ex_ops = (2 * 3 * m * (int(info["slots"]) - int(info["memberships"])) * prob.nT
               + 2 * (m * rax + (p - 1) * rows_mean) * screened + p * (2 * n + 2) * int(info["feasible"]))
@@ -1408,12 +1409,13 @@ def main():
                      "ops_per_check": ops_per_check, "ops_per_launch": ops_per_launch,
                      "work_model": "dense separable form per check (all reach, free and cost rows)",
                      "peak_note": lanes["note"],
-                     "hw_frac_note": "executed lane-ops of the pair kernel / measured peak (hardware utilisation); "
-                                     "frac uses the dense separable work model",
+                     "hw_frac_note": "the dense model's ops over what the pair kernel evaluates / measured peak "
+                                     "(closer to hardware utilisation); frac uses the whole dense separable work model",
                      "executed": {"ops_per_launch": ex_ops, "frac": ex_frac,
                                   "screened_checks": screened,
-                                  "note": "ops the screened kernel performs: screen rows of every pair and duration, "
-                                          "all reach and free rows of the screened checks, costs of feasible ones"},
+                                  "note": "the dense model's ops restricted to what the screened kernel evaluates: "
+                                          "screen rows of every pair and duration, all reach and free rows of the "
+                                          "screened checks, costs of feasible ones"},
                      "short_circuit": {"ops_per_launch": sc_ops, "frac": sc_ops / (pair_ms / 1e3) / 1e12 / alu_peak,
                                        "note": "work left after the early exits (reach rows up to the first violated "
                                                "one, free rows of reach-passing checks, costs of feasible ones)",
