@@ -1139,28 +1139,31 @@ __global__ void __launch_bounds__(256, 2) k_pairs_fast(BuildParams P) {
 }
 
 // ---------------------------------------------------------------------------
-// Screened FP32 pair kernel (the default one).  Same persistent item loop and
-// the same arithmetic as the one-group kernel, in five phases per duration:
-//   1. halves, stored per state ([state][row], rows padded to 16-byte quads,
-//      per-state stride = 4 mod 8 floats so that quad loads of different
-//      states fall in different bank groups); the screen row-axes are also
-//      stored [row][state] for the micro-tile screen;
+// Screened FP32 pair kernel (the default one).  Same persistent item loop as
+// the one-group kernel, in four phases per duration:
+//   1. reach halves, stored per state ([state][row], rows padded to 16-byte
+//      quads, per-state stride = 4 mod 8 floats so that quad loads of
+//      different states fall in different bank groups); the screen row-axes
+//      also in FP16, stored [row][state] for the micro-tile screen; the
+//      interior control points' halves; the cost rows' magnitudes;
 //   2. screen of every 4x4 micro-tile; pairs that do not certainly fail are
 //      appended to list 1 (shared memory);
-//   3. every reach and free row of the list-1 pairs, one pair per thread, four
-//      rows per 16-byte load; feasible pairs go to list 2, ambiguous ones to
+//   3. every reach row of the list-1 pairs (four per 16-byte load) and, for
+//      those that pass, every polytope row at every interior control point,
+//      one pair per thread; feasible pairs go to list 2, ambiguous ones to
 //      the FP64 re-check;
-//   4. cost halves of this duration, written over the free halves;
-//   5. costs of the list-2 pairs and the atomic merge into the pair slots.
-// Maxima are order-free and every sum keeps the reference order, so slots,
-// costs and re-check entries equal those of the other FP32 kernels.
+//   4. costs of the list-2 pairs from their two staged states and the atomic
+//      merge into the pair slots.
+// Maxima are order-free and the reach sums and costs keep the reference
+// order, so slots and costs equal those of the other FP32 kernels; the free
+// margins take fewer roundings within the same band, so only the set of
+// ambiguous margins re-checked in FP64 can differ.
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int pad_odd4(int n) { return ((n + 3) / 8) * 8 + 4; }  // >= n, = 4 mod 8
 
-// per-state stride of the free / cost halves (both live in the same rows)
-__host__ __device__ inline int sc_free_stride(int NI, int M, int PD, int DR) {
-    const int fr = (NI * M + 3) & ~3, cr = (PD * DR * M + 3) & ~3;  // interior points' halves, or cost halves
-    return pad_odd4(fr > cr ? fr : cr);
+// per-state stride of the interior control points' halves
+__host__ __device__ inline int sc_free_stride(int NI, int M) {
+    return pad_odd4((NI * M + 3) & ~3);  // the interior control points' halves
 }
 
 template <int M, int G, int PD>
@@ -1247,40 +1250,33 @@ DEVI void point_halves(const float (&x)[M * G], const float* tab, bool right, fl
     }
 }
 
-// Cost halves of one state, packed: row e = d*M + a (d < DR) of segment l,
-// sum_c C[d][l][side][c] x[c][a], at float l * DR * M + e; this unit writes
-// floats [F0, F1) (both multiples of four, the last unit's range ends on the
-// zero padding after PD * DR * M) and returns the sum of |half| over them.
+// Sum of |cost half| of one state over the floats [F0, F1) of its packed
+// cost rows (row e = d*M + a, d < DR, of segment l at float l * DR * M + e:
+// sum_c C[d][l][side][c] x[c][a]), in float order; nothing is stored.
 template <int M, int G, int PD, int DR, int F0, int F1>
-DEVI float cost_rows(const float (&x)[M * G], const float* tab, bool right, float* dC) {
+DEVI float cost_mag(const float (&x)[M * G], const float* tab, bool right) {
     constexpr int DRM = DR * M, NF = PD * DRM;
-    static_assert(F0 % 4 == 0 && F1 % 4 == 0 && F1 > F0, "cost halves are stored in 16-byte quads");
+    static_assert(F1 > F0, "each unit takes some of the cost rows");
     float mag = 0.f;
-    float v[F1 - F0];
 #pragma unroll
     for (int f = F0; f < F1; ++f) {
-        float w = 0.f;
         if (f < NF) {
             const int l = f / DRM, e = f % DRM, d = e / M, a = e % M;
             const float4 h =
                 *reinterpret_cast<const float4*>(tab + (PadTab<G, PD>::ROW_C + d * PD + l) * 8 + (right ? 4 : 0));
-            w = h.x * x[a];
+            float w = h.x * x[a];
             if (G > 1) w = fmaf(h.y, x[M + a], w);
             if (G > 2) w = fmaf(h.z, x[2 * M + a], w);
             if (G > 3) w = fmaf(h.w, x[3 * M + a], w);
             mag += fabsf(w);
         }
-        v[f - F0] = w;
     }
-#pragma unroll
-    for (int q = 0; q < (F1 - F0) / 4; ++q)
-        *reinterpret_cast<float4*>(dC + F0 + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     return mag;
 }
 
-// The split of a state's packed cost halves between its two units: at the
-// segment boundary (PD + 1) / 2 rounded down to a quad, the rest to the end
-// of the padding.
+// The split of a state's cost rows (counted as packed floats) between its
+// two units for the magnitude sums: at the segment boundary (PD + 1) / 2
+// rounded down to a quad, the rest to the end of the padding.
 template <int M, int PD, int DR>
 struct CostSplit {
     static constexpr int NP = (PD * DR * M + 3) & ~3;
@@ -1334,34 +1330,44 @@ DEVI void stage_state_half(const void* states, bool in_f32, long long id, bool v
     }
 }
 
-// Control-polygon length of one pair from its packed cost halves: per
-// segment the root of the sum of squares of (start + end half) over its DRM
-// rows in row order, summed over the PD segments in order.
-template <int PD, int DRM>
-DEVI float pair_cost(const float* cl, const float* cr) {
-    constexpr int NF = PD * DRM, NQ = (NF + 3) / 4;
-    float ss[PD];
-#pragma unroll
-    for (int l = 0; l < PD; ++l) ss[l] = 0.f;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const float4 a = *reinterpret_cast<const float4*>(cl + 4 * q);
-        const float4 b = *reinterpret_cast<const float4*>(cr + 4 * q);
-        const float d[4] = {a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int f = 4 * q + j;
-            if (f < NF) ss[f / DRM] = fmaf(d[j], d[j], ss[f / DRM]);
-        }
-    }
+// Control-polygon length of one pair from its two staged states: per
+// segment l the root of the sum of squares, over rows e = d*M + a (d < DR) in
+// order, of start half + end half (each sum_c C[d][l][side][c] x[c][a], the
+// table rows broadcast), summed over the PD segments in order.
+template <int M, int G, int PD, int DR>
+DEVI float pair_cost_states(const float* xi, const float* xj, const float* tab) {
+    float a[M * G], b[M * G];
+    load_state<M, G, PD>(a, xi);
+    load_state<M, G, PD>(b, xj);
     float cs = 0.f;
 #pragma unroll
-    for (int l = 0; l < PD; ++l) cs += sqrtf(ss[l]);
+    for (int l = 0; l < PD; ++l) {
+        float ss = 0.f;
+#pragma unroll
+        for (int d = 0; d < DR; ++d) {
+            const float4 hl = *reinterpret_cast<const float4*>(tab + (PadTab<G, PD>::ROW_C + d * PD + l) * 8);
+            const float4 hr = *reinterpret_cast<const float4*>(tab + (PadTab<G, PD>::ROW_C + d * PD + l) * 8 + 4);
+#pragma unroll
+            for (int q = 0; q < M; ++q) {
+                float cl = hl.x * a[q];
+                if (G > 1) cl = fmaf(hl.y, a[M + q], cl);
+                if (G > 2) cl = fmaf(hl.z, a[2 * M + q], cl);
+                if (G > 3) cl = fmaf(hl.w, a[3 * M + q], cl);
+                float cr = hr.x * b[q];
+                if (G > 1) cr = fmaf(hr.y, b[M + q], cr);
+                if (G > 2) cr = fmaf(hr.z, b[2 * M + q], cr);
+                if (G > 3) cr = fmaf(hr.w, b[3 * M + q], cr);
+                const float dv = cl + cr;
+                ss = fmaf(dv, dv, ss);
+            }
+        }
+        cs += sqrtf(ss);
+    }
     return cs;
 }
 
 template <int M, int G, int PD>
-__global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
+__global__ void __launch_bounds__(256, 3) k_pairs_sc(BuildParams P) {
     using S = Shape<G, PD>;
     using PT = PadTab<G, PD>;
     using SS = ScShape<M, G, PD>;
@@ -1370,17 +1376,18 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
     const int T = P.tile;  // tile side (multiple of 4, <= TILE)
     extern __shared__ __align__(16) float sm[];
     const int DR = P.cost_mode == 1 ? 1 : G;
-    const int SF = sc_free_stride(NI, M, PD, DR);
+    const int SF = sc_free_stride(NI, M);
     float* UL = sm;                  // [T][SU] reach halves, start states
     float* UR = UL + T * SU;         //          end states
-    float* FL = UR + T * SU;         // [T][SF] interior control-point halves, then cost halves
+    float* FL = UR + T * SU;         // [T][SF] interior control-point halves
     float* FR = FL + T * SF;
     __half2* SCL = reinterpret_cast<__half2*>(FR + T * SF);       // [NS][T] screen row-axes, start states: (h, h)
     __half* SCR = reinterpret_cast<__half*>(FR + T * SF + NS * T);  // [NS][T] end states (half of the space used)
     float* magR = FR + T * SF + 2 * NS * T;                          // [2T] band magnitudes
     float* magF = magR + 2 * T;
-    float* magC = magF + 2 * T;      // [2T] sum of |cost half| per state-side (cost conditioning)
-    float* xs = magC + 2 * T;        // [2T][XS] centred states
+    float* magC = magF + 2 * T;      // [2T] sum of |cost half| per state-side (cost conditioning):
+    float* magC2 = magC + 2 * T;     //      first unit's rows, second unit's rows
+    float* xs = magC2 + 2 * T;       // [2T][XS] centred states
     float* xab = xs + 2 * T * XS;    // [2T][G] per-derivative maxima over the axes
     float* tabs = xab + 2 * T * G;   // two padded duration tables
     float* Ab = tabs + 2 * PT::FLOATS;  // [RMAX][4]: A_r, then b_r
@@ -1491,7 +1498,6 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                 void* dS = right ? (void*)SCR : (void*)SCL;
                 float* dF = (right ? FR : FL) + ls * SF;
                 if (!second) {
-                    magC[(right ? T : 0) + ls] = 0.f;  // summed by the cost-halves units
                     reach_quads<M, G, PD, 0, RH>(x, trow, dU, dS, ls, right, T);
                     point_halves<M, G, PD, 0, NI / 2>(x, tab, right, dF);
                     const float* xa = xab + (right ? T + ls : ls) * G;
@@ -1509,6 +1515,14 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
                     reach_quads<M, G, PD, RH, RQ>(x, trow, dU, dS, ls, right, T);
                     point_halves<M, G, PD, NI / 2, NI>(x, tab, right, dF);
                 }
+                // the cost rows' magnitudes (cost conditioning), one part per unit
+                using CSG = CostSplit<M, PD, G>;
+                using CS1 = CostSplit<M, PD, 1>;
+                const float mg = DR == G ? (!second ? cost_mag<M, G, PD, G, 0, CSG::FS>(x, tab, right)
+                                                    : cost_mag<M, G, PD, G, CSG::FS, CSG::NP>(x, tab, right))
+                                         : (!second ? cost_mag<M, G, PD, 1, 0, CS1::FS>(x, tab, right)
+                                                    : cost_mag<M, G, PD, 1, CS1::FS, CS1::NP>(x, tab, right));
+                (second ? magC2 : magC)[(right ? T : 0) + ls] = mg;
             }
             __syncthreads();
 
@@ -1609,40 +1623,22 @@ __global__ void __launch_bounds__(256, 2) k_pairs_sc(BuildParams P) {
             __syncthreads();
 
             const int n2 = s_n2;
-            if (n2 > 0) {
-                // 4. cost halves of this duration over the free halves: two
-                // units per state (segments [0, (PD+1)/2) and the rest)
-                for (int u = tid; u < 2 * S2; u += nthr) {
-                    const bool second = u >= S2;
-                    const int s = second ? u - S2 : u;
-                    const bool right = s >= ni4;
-                    const int ls = right ? s - ni4 : s;
-                    float x[N_];
-                    load_state<M, G, PD>(x, xs + (right ? T + ls : ls) * XS);
-                    float* dC = (right ? FR : FL) + ls * SF;
-                    using CSG = CostSplit<M, PD, G>;
-                    using CS1 = CostSplit<M, PD, 1>;
-                    const float mg = DR == G ? (!second ? cost_rows<M, G, PD, G, 0, CSG::FS>(x, tab, right, dC)
-                                                        : cost_rows<M, G, PD, G, CSG::FS, CSG::NP>(x, tab, right, dC))
-                                             : (!second ? cost_rows<M, G, PD, 1, 0, CS1::FS>(x, tab, right, dC)
-                                                        : cost_rows<M, G, PD, 1, CS1::FS, CS1::NP>(x, tab, right, dC));
-                    atomicAdd(&magC[(right ? T : 0) + ls], mg);  // two units per state-side
-                }
-                __syncthreads();
-                // 5. costs of the feasible pairs (segment sums in row order)
-                for (int e = tid; e < n2; e += nthr) {
-                    const int v = list2[e];
-                    const int li = v >> 8, lj = v & 255;
-                    const float* cl = FL + li * SF;
-                    const float* cr = FR + lj * SF;
-                    const float cs = DR == G ? pair_cost<PD, G * M>(cl, cr) : pair_cost<PD, M>(cl, cr);
-                    if (P.cost64 || magC[li] + magC[T + lj] <= COST_RHO * cs) {  // FP64 models re-cost every edge anyway
-                        const long long slot = itd.base + (long long)(i0 + li) * itd.nk + (j0 + lj);
-                        atomicOr(&P.resBits[slot], 1u << t);
-                        atomicMin(&P.resKey[slot], key_f32(cs, t));
-                    } else {
-                        append_recheck(P, itd.q, k, i0 + li, j0 + lj, t, true);  // ill-conditioned FP32 cost
-                    }
+            // 4. costs of the feasible pairs from their two staged states (per
+            // segment the sum of squares in row order)
+            for (int e = tid; e < n2; e += nthr) {
+                const int v = list2[e];
+                const int li = v >> 8, lj = v & 255;
+                const float* xi = xs + li * XS;
+                const float* xj = xs + (T + lj) * XS;
+                const float cs = DR == G ? pair_cost_states<M, G, PD, G>(xi, xj, tab)
+                                         : pair_cost_states<M, G, PD, 1>(xi, xj, tab);
+                const float mc = (magC[li] + magC2[li]) + (magC[T + lj] + magC2[T + lj]);
+                if (P.cost64 || mc <= COST_RHO * cs) {  // FP64 models re-cost every edge anyway
+                    const long long slot = itd.base + (long long)(i0 + li) * itd.nk + (j0 + lj);
+                    atomicOr(&P.resBits[slot], 1u << t);
+                    atomicMin(&P.resKey[slot], key_f32(cs, t));
+                } else {
+                    append_recheck(P, itd.q, k, i0 + li, j0 + lj, t, true);  // ill-conditioned FP32 cost
                 }
             }
             cp_async_wait_all();  // the next duration's table
@@ -3230,8 +3226,8 @@ size_t smem_sc(const BuildParams& P) {
     using SS = ScShape<M, G, PD>;
     const int DR = P.cost_mode == 1 ? 1 : G;
     const size_t T = (size_t)P.tile;
-    const size_t SF = (size_t)sc_free_stride(Shape<G, PD>::NI, M, PD, DR);
-    size_t f = T * (2 * SS::SU + 2 * SF + 2 * SS::NS + 6) + 2 * T * (SS::XS + G) + 2 * PadTab<G, PD>::FLOATS + RMAX * 4;
+    const size_t SF = (size_t)sc_free_stride(Shape<G, PD>::NI, M);
+    size_t f = T * (2 * SS::SU + 2 * SF + 2 * SS::NS + 8) + 2 * T * (SS::XS + G) + 2 * PadTab<G, PD>::FLOATS + RMAX * 4;
     return f * sizeof(float) + 2 * T * T * sizeof(uint16_t);
 }
 
