@@ -101,6 +101,8 @@ struct plan_ctx {
     long long capS = -1;
     unsigned long long* sdist = nullptr;
     unsigned long long* sbest = nullptr;
+    unsigned long long* sbest16 = nullptr;  // [N][2] predecessor pairs of plan_search
+    long long capS16 = -1;
     int* spred = nullptr;
     unsigned char* sfront = nullptr;
     long long capLast = -1;
@@ -421,7 +423,7 @@ void plan_destroy(plan_ctx* c) {
     if (c->stream || c->d_info) cudaStreamSynchronize(c->stream);
     void* dev[] = {c->d_tab64, c->d_tab32, c->d_info, c->memMask, c->counts, c->members, c->localIdx, c->segKL, c->centers,
                    c->blim64, c->A32, c->blim32, c->bc32, c->resOff, c->itemOff, c->kPerm, c->ntile, c->tsize, c->iRange, c->rowCount,
-                   c->resBits, c->resKey, c->emitPre, c->recheck, c->half64, c->sdist, c->sbest, c->spred, c->sfront, c->slast, c->snear,
+                   c->resBits, c->resKey, c->emitPre, c->recheck, c->half64, c->sdist, c->sbest, c->sbest16, c->spred, c->sfront, c->slast, c->snear,
                    c->d_qd, c->d_pfx, c->d_qSlot, c->d_qItem, c->d_qMem, c->d_rowRange, c->d_sqd, c->memOff,
                    c->d_cut64, c->d_cut32, c->cut_src, c->cut_hit, c->cut_pos, c->cut_chunk, c->cut_orow,
                    c->cut_ocount, c->cut_list32, c->cut_okb, c->cut_obox, c->pl_orow, c->pl_face, c->pl_edge, c->pl_nedge, c->pl_ocount, c->pl_keys, c->pl_near, c->pl_ub, c->d_mpc, c->d_mpcJ, c->g_d, c->g_succ, c->g_wsucc, c->g_anc, c->g_prev};
@@ -874,6 +876,10 @@ int search_common(plan_ctx* c, int N, const void* states, const plan_edges* edge
             return PLAN_ERR_NO_MEMORY;
         c->capS = N;
     }
+    if (N > c->capS16) {
+        if (!dalloc(c, &c->sbest16, 2LL * N)) return PLAN_ERR_NO_MEMORY;
+        c->capS16 = N;
+    }
     if (N > c->capLast) {
         if (!dalloc(c, &c->slast, N)) return PLAN_ERR_NO_MEMORY;
         c->capLast = N;
@@ -901,6 +907,7 @@ int search_common(plan_ctx* c, int N, const void* states, const plan_edges* edge
     S.endpoints = endpoints;
     S.dist = c->sdist;
     S.bestU = c->sbest;
+    S.best16 = c->sbest16;
     S.pred = c->spred;
     S.last = c->slast;
     S.near_blk = c->snear;

@@ -198,6 +198,7 @@ struct SearchParams {
     unsigned long long* dist;  // [N] bit patterns of non-negative doubles
     unsigned long long* bestU; // [N]
     int* pred;                 // [N]
+    unsigned long long* best16;  // [N][2] (dist[u] bits, u) of each vertex's predecessor, 16-byte aligned, or null
     unsigned long long* last;  // [N] distance each vertex last relaxed its out-edges from
     unsigned long long* near_blk;  // [4][blocks] per-block nearest candidates (bits, id) for start, goal
     int32_t* path;

@@ -88,6 +88,26 @@ DEVI double ldd(const void* p, long long i, int f32) {
 #endif
 constexpr int SWEEP_ROUNDS = PLAN_SEARCH_ROUNDS;
 
+// A vertex's predecessor candidate: the bits of dist[u] and u, ordered
+// lexicographically (the nearer in-neighbour, ties to the lower id).
+struct alignas(16) DistPred {
+    unsigned long long d, u;
+};
+
+// Lowers *a to (d, u) if that pair is smaller: a compare-and-swap loop that
+// retries only when another thread changed *a in between (lock-free: every
+// failed swap means a smaller pair was stored by someone else).
+DEVI void min_dist_pred(DistPred* a, unsigned long long d, unsigned long long u) {
+    const volatile unsigned long long* va = reinterpret_cast<const volatile unsigned long long*>(a);
+    DistPred cur{va[0], va[1]};  // a torn read only costs one failed swap
+    while (d < cur.d || (d == cur.d && u < cur.u)) {
+        const DistPred want{d, u};
+        const DistPred old = atomicCAS(a, cur, want);
+        if (old.d == cur.d && old.u == cur.u) return;
+        cur = old;
+    }
+}
+
 // (bits, id) pairs ordered lexicographically: the nearest vertex, ties to the lowest id
 DEVI void keep_min(unsigned long long& kb, int& ki, unsigned long long ob, int oi) {
     if (ob < kb || (ob == kb && oi < ki)) {
@@ -195,8 +215,13 @@ __global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
         const long long v = blockIdx.x + k * nb;
         P.dist[v] = DINF;
         P.last[v] = DINF;
-        P.bestU[v] = ~0ull;
-        P.pred[v] = 0x7fffffff;
+        if (P.best16) {
+            P.best16[2 * v] = ~0ull;
+            P.best16[2 * v + 1] = ~0ull;
+        } else {
+            P.bestU[v] = ~0ull;
+            P.pred[v] = 0x7fffffff;
+        }
         double ds = 0.0, dg = 0.0;
         for (int a = 0; a < P.m; ++a) {
             const double x = ldd(P.states, v * P.n + a, P.in_f32);
@@ -349,13 +374,16 @@ __global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
     }
 
     // phase 2: predecessor = minimum (dist[u], u) over in-neighbours attaining
-    // dist[v], in two passes over the out-edges of every vertex closer than
-    // the goal (the only possible predecessors on a path to it; same
-    // ownership and edge-parallel layout as the sweeps)
+    // dist[v], over the out-edges of every vertex closer than the goal (the
+    // only possible predecessors on a path to it; same ownership and
+    // edge-parallel layout as the sweeps): one pass of 16-byte lexicographic
+    // minima when best16 is given, else two passes (minimum dist[u], then
+    // minimum u among those attaining it)
     if (tid == 0) s_gd = vdist[g];
     __syncthreads();
     const unsigned long long dgoal = s_gd;
-    for (int pass = 0; pass < 2; ++pass) {
+    const int npass = P.best16 ? 1 : 2;
+    for (int pass = 0; pass < npass; ++pass) {
         for (long long k0 = 0; k0 < nown; k0 += nt) {
             if (tid == 0) s_nf = 0;
             __syncthreads();
@@ -388,7 +416,8 @@ __global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
                 const unsigned long long nd =
                     (unsigned long long)__double_as_longlong(__dadd_rn(__longlong_as_double((long long)dvb), w));
                 if (nd != vdist[u]) continue;
-                if (pass == 0) atomicMin(&P.bestU[u], dvb);
+                if (P.best16) min_dist_pred(reinterpret_cast<DistPred*>(P.best16 + 2LL * u), dvb, (unsigned long long)s_v[i]);
+                else if (pass == 0) atomicMin(&P.bestU[u], dvb);
                 else if (((volatile unsigned long long*)P.bestU)[u] == dvb) atomicMin(&P.pred[u], s_v[i]);
             }
             __syncthreads();
@@ -400,11 +429,16 @@ __global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
     if (blockIdx.x != 0) return;
     const bool staged = N <= P.walk_smem;
     if (staged) {
-        for (int v = threadIdx.x; v < N; v += blockDim.x) s_pred[v] = ((volatile int*)P.pred)[v];
+        for (int v = threadIdx.x; v < N; v += blockDim.x)
+            s_pred[v] = P.best16 ? (int)((volatile unsigned long long*)P.best16)[2 * v + 1] : ((volatile int*)P.pred)[v];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const int* pr = staged ? s_pred : P.pred;
+        // the predecessor of v (an unset one reads as -1 or INT_MAX, out of range)
+        auto pr = [&](int v) -> int {
+            if (staged) return s_pred[v];
+            return P.best16 ? (int)P.best16[2LL * v + 1] : P.pred[v];
+        };
         info->search_iters = (unsigned long long)it;
         const unsigned long long dg = vdist[g];
         if (dg >= DINF) {
@@ -415,7 +449,7 @@ __global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
             int len = 1, v = g;
             bool okw = true;
             while (v != s) {
-                v = pr[v];
+                v = pr(v);
                 if (v < 0 || v >= N || len > N) {
                     okw = false;
                     break;
@@ -432,7 +466,7 @@ __global__ void __launch_bounds__(1024, 1) k_search(SearchParams P) {
                 v = g;
                 for (int q = len - 1; q >= 0; --q) {
                     P.path[q] = v;
-                    if (q) v = pr[v];
+                    if (q) v = pr(v);
                 }
                 *P.path_len = len;
             }
