@@ -1395,7 +1395,7 @@ __global__ void __launch_bounds__(256, 3) k_pairs_sc(BuildParams P) {
     uint16_t* list2 = list1 + T * T;                                 // feasible pairs
     __shared__ long long s_item;
     __shared__ float s_rown1, s_bmax;
-    __shared__ int s_n1, s_n2;
+    __shared__ int s_n1[2], s_n2[2];  // list lengths, by duration parity
 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const long long nitems = (long long)P.info->items;
@@ -1463,6 +1463,10 @@ __global__ void __launch_bounds__(256, 3) k_pairs_sc(BuildParams P) {
             }
         }
         stage_table_async<G, PD>(tabs, P.tab32 + (long long)(Qd.tabOff + itc.t0) * fst, tid, nthr);
+        if (tid == 0) {
+            s_n1[0] = s_n1[1] = 0;
+            s_n2[0] = s_n2[1] = 0;
+        }
         cp_async_wait_all();
         __syncthreads();
 
@@ -1478,11 +1482,14 @@ __global__ void __launch_bounds__(256, 3) k_pairs_sc(BuildParams P) {
                 if (act && li < TI && lj < TJ && i0 + li != j0 + lj) live |= 1u << (qa * 4 + qb);
             }
         for (int t = itc.t0; t < itc.t1; ++t) {
-            const float* tab = tabs + ((t - itc.t0) & 1) * PT::FLOATS;
-            if (tid == 0) {  // last read before the previous duration's closing barrier
-                s_n1 = 0;
-                s_n2 = 0;
-            }
+            // Three block barriers per duration.  The costs of duration t
+            // (phase 4) read only the staged states, table t, the cost
+            // magnitudes and list 2, which duration t+1 rewrites only after
+            // its first barrier (magnitudes in phase 2, the table buffer by the
+            // prefetch for t+2, list 2 in phase 3) -- so duration t+1's halves
+            // overlap the slowest warps' costs of duration t.
+            const int par = (t - itc.t0) & 1;
+            const float* tab = tabs + par * PT::FLOATS;
             // 1. halves: two units per state, each loading the state once --
             // the first takes reach quads [0, RH), interior points [0, NI/2)
             // and the band magnitudes, the second the rest
@@ -1515,7 +1522,28 @@ __global__ void __launch_bounds__(256, 3) k_pairs_sc(BuildParams P) {
                     reach_quads<M, G, PD, RH, RQ>(x, trow, dU, dS, ls, right, T);
                     point_halves<M, G, PD, NI / 2, NI>(x, tab, right, dF);
                 }
-                // the cost rows' magnitudes (cost conditioning), one part per unit
+            }
+            __syncthreads();
+
+            // the next duration's table goes to the other buffer meanwhile (its
+            // last reader, the costs of duration t-1, finished before the barrier
+            // above); the list lengths of duration t+1 are cleared
+            if (t + 1 < itc.t1)
+                stage_table_async<G, PD>(tabs + ((t + 1 - itc.t0) & 1) * PT::FLOATS,
+                                         P.tab32 + (long long)(Qd.tabOff + t + 1) * fst, tid, nthr);
+            if (tid == 0) {
+                s_n1[par ^ 1] = 0;
+                s_n2[par ^ 1] = 0;
+            }
+            // the cost rows' magnitudes of this duration (cost conditioning), one
+            // part per unit
+            for (int u = tid; u < 2 * S2; u += nthr) {
+                const bool second = u >= S2;
+                const int s = second ? u - S2 : u;
+                const bool right = s >= ni4;
+                const int ls = right ? s - ni4 : s;
+                float x[N_];
+                load_state<M, G, PD>(x, xs + (right ? T + ls : ls) * XS);
                 using CSG = CostSplit<M, PD, G>;
                 using CS1 = CostSplit<M, PD, 1>;
                 const float mg = DR == G ? (!second ? cost_mag<M, G, PD, G, 0, CSG::FS>(x, tab, right)
@@ -1524,12 +1552,6 @@ __global__ void __launch_bounds__(256, 3) k_pairs_sc(BuildParams P) {
                                                     : cost_mag<M, G, PD, 1, CS1::FS, CS1::NP>(x, tab, right));
                 (second ? magC2 : magC)[(right ? T : 0) + ls] = mg;
             }
-            __syncthreads();
-
-            // the next duration's table goes to the other buffer meanwhile
-            if (t + 1 < itc.t1)
-                stage_table_async<G, PD>(tabs + ((t + 1 - itc.t0) & 1) * PT::FLOATS,
-                                         P.tab32 + (long long)(Qd.tabOff + t + 1) * fst, tid, nthr);
 
             // 2. screen and list 1 (positions by a warp prefix of the survivor
             // counts and one shared atomic per warp; the block is whole warps)
@@ -1543,7 +1565,7 @@ __global__ void __launch_bounds__(256, 3) k_pairs_sc(BuildParams P) {
                     if ((tid & 31) >= o) inc += y;
                 }
                 int wbase = 0;
-                if ((tid & 31) == 31 && inc) wbase = atomicAdd(&s_n1, inc);
+                if ((tid & 31) == 31 && inc) wbase = atomicAdd(&s_n1[par], inc);
                 int pos = __shfl_sync(0xffffffffu, wbase, 31) + inc - cnt;
                 while (surv) {
                     const int q = __ffs(surv) - 1;
@@ -1554,7 +1576,7 @@ __global__ void __launch_bounds__(256, 3) k_pairs_sc(BuildParams P) {
             __syncthreads();
 
             // 3. every reach and free row of the screened pairs
-            const int n1 = s_n1;
+            const int n1 = s_n1[par];
             if (tid == 0) nscreened += (unsigned long long)n1;
             for (int e = tid; e < n1; e += nthr) {
                 const int v = list1[e];
@@ -1614,15 +1636,16 @@ __global__ void __launch_bounds__(256, 3) k_pairs_sc(BuildParams P) {
                 if (fb) {
                     const int lane = tid & 31, leader = __ffs(fb) - 1;
                     int b2 = 0;
-                    if (lane == leader) b2 = atomicAdd(&s_n2, __popc(fb));
+                    if (lane == leader) b2 = atomicAdd(&s_n2[par], __popc(fb));
                     b2 = __shfl_sync(am, b2, leader);
                     if (outcome == 1) list2[b2 + __popc(fb & ((1u << lane) - 1u))] = (uint16_t)v;
                 }
                 if (outcome == 2) append_recheck(P, itd.q, k, i0 + li, j0 + lj, t);
             }
+            cp_async_wait_all();  // the next duration's table, visible after this barrier
             __syncthreads();
 
-            const int n2 = s_n2;
+            const int n2 = s_n2[par];
             // 4. costs of the feasible pairs from their two staged states (per
             // segment the sum of squares in row order)
             for (int e = tid; e < n2; e += nthr) {
@@ -1641,8 +1664,6 @@ __global__ void __launch_bounds__(256, 3) k_pairs_sc(BuildParams P) {
                     append_recheck(P, itd.q, k, i0 + li, j0 + lj, t, true);  // ill-conditioned FP32 cost
                 }
             }
-            cp_async_wait_all();  // the next duration's table
-            __syncthreads();
         }
     }
     block_add(&P.info->reach_pass, rp_cnt);
