@@ -86,7 +86,7 @@ struct DevInfo {
     unsigned long long cut_lp64;     // entries settled in FP64
     unsigned long long cut_ties;     // FP64 games without a certificate either way
     int shard_lo, shard_hi;          // source rows [lo, hi) of the first query's shard
-    int tchunks;                     // duration chunks per tile of this build (k_batch)
+    int tchunks;                     // duration chunks per tile of the current edge build (k_batch)
 };
 
 enum Detail {
